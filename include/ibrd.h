@@ -1,0 +1,165 @@
+/*
+ * ibrd.h -- C ABI of the GB300 reactive-blob reaction-diffusion library.
+ *
+ * The library solves the linear systems of the minimally-resolved blob model
+ * (Bhalla, Griffith, Patankar, Donev; arXiv:1306.3159) on a periodic,
+ * cell-centred 3-D grid, entirely on one NVIDIA GB300 GPU:
+ *
+ *   reaction-limited (Eq. unsteady_system, Eq. steady_state):
+ *       (alpha I - chi L + S kappa J) c = g
+ *   diffusion-limited saddle point (Eq. saddle_point):
+ *       A c + zeta S lambda = g,   xi J c = f,   A = alpha I - chi L
+ *
+ * with alpha = 1/dt (alpha = 0: steady state), L the 7-point Laplacian
+ * (Sec. III.A), J the tensor-product Peskin-kernel averaging operator
+ * (Sec. III.A, Eq. tensor_product) and S = h^-3 J^T the spreading operator.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Grid: n_x x n_y x n_z cells of spacing h; the domain is [0, n h) per axis
+ *   and periodic; cell (i, j, k) has centre ((i+1/2)h, (j+1/2)h, (k+1/2)h).
+ * - Fields are contiguous FP64 arrays of n_x*n_y*n_z values, index
+ *   i + n_x*(j + n_y*k) (x fastest).
+ * - Blob arrays are contiguous FP64 arrays of N values, in the order the blobs
+ *   were given to ibrd_set_blobs.
+ * - Every pointer argument is a DEVICE pointer on the device that was current
+ *   when the handle was created, caller-owned; the library never frees it.
+ *   All work is ordered on the stream given to ibrd_grid_create. Entry points
+ *   that return a status synchronize that stream only where stated.
+ * - No exception crosses the ABI. On failure a call returns a non-zero status;
+ *   ibrd_last_error(handle) then returns a message owned by the handle.
+ * - A handle is not thread-safe: calls on one handle must not overlap.
+ */
+#ifndef IBRD_H
+#define IBRD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ibrd_grid_s* ibrd_grid;
+
+typedef enum {
+  IBRD_OK = 0,
+  IBRD_ERR_ARG = 1,            /* invalid argument or size */
+  IBRD_ERR_CUDA = 2,           /* a CUDA runtime call failed */
+  IBRD_ERR_OOM = 3,            /* device allocation failed */
+  IBRD_ERR_NOT_CONVERGED = 4,  /* max_iter reached; best iterate written */
+  IBRD_ERR_BREAKDOWN = 5,      /* Krylov breakdown before convergence */
+  IBRD_ERR_NONFINITE = 6,      /* NaN/Inf in an input or a residual */
+  IBRD_ERR_TIMEOUT = 7,        /* reserved: bounded device wait expired */
+  IBRD_ERR_STATE = 8           /* call needs state not set (e.g. no blobs) */
+} ibrd_status;
+
+enum { IBRD_PESKIN4 = 4, IBRD_PESKIN3 = 3 };          /* kernel width w */
+enum { IBRD_FP64 = 0, IBRD_MIXED_FP32 = 1 };          /* precision */
+enum { IBRD_PRECOND_SCHUR = 0, IBRD_PRECOND_DIAG = 1 }; /* saddle preconditioner */
+
+/* Solver options. ibrd_default_opts fills the defaults noted here. */
+typedef struct {
+  double tol;        /* relative true residual ||b - K x||_2 / ||b||_2 (1e-8) */
+  int max_iter;      /* total outer FGMRES iterations (1000) */
+  int restart;       /* FGMRES restart length (30, Sec. III.E Figs. 3, 5) */
+  int mg_cycles;     /* n: V-cycles per approximate Helmholtz solve (1) */
+  int schur_inner;   /* m: inner Krylov iterations of the approximate Schur
+                        preconditioner (5, Sec. III.E / Appendix A) */
+  int precond;       /* IBRD_PRECOND_SCHUR (default) or IBRD_PRECOND_DIAG */
+  double zeta;       /* scaling zeta of Eq. saddle_point (1) */
+  double xi;         /* scaling xi; <= 0 selects zeta / h^3 (Eq. saddle_point) */
+  int nu1, nu2;      /* red-black Gauss-Seidel sweeps before/after (2, 2) */
+  int precision;     /* IBRD_FP64 or IBRD_MIXED_FP32; -1 = the handle's */
+  int use_guess;     /* 1: c (and lambda) hold an initial guess; 0: start at 0 */
+} ibrd_solve_opts;
+
+/* Solve report. residual_history, if non-NULL, is a caller-owned HOST array
+   of history_cap doubles that receives the relative residual estimate after
+   each outer iteration (history_len entries are written). */
+typedef struct {
+  int status;          /* same value the solve returned */
+  int outer_iters;     /* outer FGMRES iterations */
+  int inner_iters;     /* inner Schur Krylov iterations (saddle) */
+  int vcycles;         /* V-cycles applied (the paper's cost proxy, Sec. III.E) */
+  double rel_residual; /* final relative true residual */
+  double sum_lambda;   /* sum_i lambda_i (saddle) or sum_i kappa_i (J c)_i */
+  double cbar;         /* mean of c over all cells (Sec. IV.A) */
+  double rate_K;       /* K = sum_i lambda_i / (N cbar) (Sec. I.A) */
+  double seconds;      /* wall time of the solve on the host clock */
+  double* residual_history;
+  int history_len;
+  int history_cap;
+} ibrd_solve_info;
+
+/* Fill *opts with the defaults listed in ibrd_solve_opts. */
+void ibrd_default_opts(ibrd_solve_opts* opts);
+
+/* Create a handle for an n_x x n_y x n_z periodic grid (each side >= 4) with
+   spacing h > 0, diffusion coefficient chi > 0 (Sec. I.A) and shift
+   alpha >= 0 (alpha = 1/dt of Eq. unsteady_system; 0 = steady state,
+   Eq. steady_state). kernel is IBRD_PESKIN4 (Sec. III.A, Delta V = (8/3)^3 h^3)
+   or IBRD_PESKIN3 (Delta V = 8 h^3). precision is the default precision of
+   solves. stream is a cudaStream_t (NULL = legacy default stream). The
+   multigrid hierarchy halves every side while all sides are even and >= 4;
+   the coarsest level must hold at most 512 cells (else IBRD_ERR_ARG).
+   On success *out owns device workspaces until ibrd_grid_destroy. */
+ibrd_status ibrd_grid_create(ibrd_grid* out, int nx, int ny, int nz, double h, double chi,
+                             double alpha, int kernel, int precision, void* stream);
+
+/* Release a handle and all its device memory. NULL is ignored. */
+void ibrd_grid_destroy(ibrd_grid g);
+
+/* Set the blob configuration Q = {q_1..q_N} (Sec. II.A): q is a device array
+   of N x 3 FP64 values (x, y, z per blob, AoS). Positions are wrapped into the
+   periodic box. Computes each blob's 1-D kernel weights and bins blobs by
+   8 x 8 x 8 cell tile for spreading. N >= 0; N = 0 clears the blobs.
+   Synchronizes the stream (it reads back the number of occupied tiles). */
+ibrd_status ibrd_set_blobs(ibrd_grid g, const double* q, int n_blobs);
+
+/* y = A c = alpha c - chi L c (Sec. III.A, Eq. Helmholtz). c and y must not
+   overlap. */
+ibrd_status ibrd_apply_L(ibrd_grid g, const double* c, double* y);
+
+/* One multigrid V-cycle (FP64) for A x = rhs (Sec. III.E): red-black
+   Gauss-Seidel (nu1 = nu2 = 2), 8-cell-mean restriction, trilinear
+   cell-centred prolongation, exact coarsest solve. With alpha = 0 the
+   right-hand side is projected to mean zero and the result is returned with
+   mean zero (the restricted inverse of Appendix A). zero_initial_guess != 0
+   ignores the incoming x. rhs and x must not overlap. */
+ibrd_status ibrd_vcycle(ibrd_grid g, const double* rhs, double* x, int zero_initial_guess);
+
+/* grid_out (+)= S lambda, (S lambda)_k = h^-3 sum_i phi(q_i - r_k) lambda_i
+   (Sec. III.A). accumulate = 0 overwrites grid_out (zero away from blobs).
+   Deterministic: each cell sums its blobs in increasing blob index. */
+ibrd_status ibrd_spread(ibrd_grid g, const double* lambda, double* grid_out, int accumulate);
+
+/* out_n = J c, (J c)_i = sum_k phi(q_i - r_k) c_k (Sec. III.A). */
+ibrd_status ibrd_interp(ibrd_grid g, const double* c, double* out_n);
+
+/* Solve (alpha I - chi L + S diag(kappa) J) c = g (Eq. unsteady_system; with
+   alpha = 0, Eq. steady_state) by right-preconditioned flexible GMRES whose
+   preconditioner is opts->mg_cycles V-cycles of (sigma I - chi L), sigma =
+   alpha if alpha > 0 else sum_i kappa_i / V_Omega (Sec. III.E,
+   Eq. Pinv_Poisson). kappa: N rates >= 0 (device). g: source field. c: in
+   (if opts->use_guess) / out. With alpha = 0 at least one kappa_i must be
+   positive. info may be NULL. Synchronizes the stream. */
+ibrd_status ibrd_solve_reaction(ibrd_grid g, const double* kappa, const double* rhs, double* c,
+                                const ibrd_solve_opts* opts, ibrd_solve_info* info);
+
+/* Solve the saddle point A c + zeta S lambda = g, xi J c = f (Eq. saddle_point)
+   by flexible GMRES on [c; lambda] preconditioned with the approximate Schur
+   complement (or diagonal) preconditioner of Sec. III.E and Appendix A,
+   including its null-space handling when alpha = 0. f may be NULL (f = 0).
+   c, lambda: in (if opts->use_guess) / out. Requires N >= 1. info may be NULL.
+   Synchronizes the stream. */
+ibrd_status ibrd_solve_saddle(ibrd_grid g, const double* rhs, const double* f, double* c,
+                              double* lambda, const ibrd_solve_opts* opts, ibrd_solve_info* info);
+
+/* Message of the last failed call on this handle ("" if none). */
+const char* ibrd_last_error(ibrd_grid g);
+
+/* Static name of a status code. */
+const char* ibrd_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IBRD_H */

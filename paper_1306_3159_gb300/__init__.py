@@ -1,0 +1,21 @@
+"""GB300-native solver for the minimally-resolved reactive-blob model.
+
+Python binding of ``libibrd`` (C ABI in ``include/ibrd.h``). The functions
+below marshal arguments only: every arithmetic step runs in the library's CUDA
+kernels. Fields and blob arrays are CUDA ``torch`` tensors (FP64, contiguous);
+their device pointers and the current torch stream are passed to the library.
+Importing this package does not need a GPU; calling into it does, and a
+missing or unloadable library raises ``ImportError``/``RuntimeError``: there is
+no CPU fallback.
+"""
+from ._abi import (IBRD_FP64, IBRD_MIXED_FP32, IBRD_PESKIN3, IBRD_PESKIN4, IBRD_PRECOND_DIAG,
+                   IBRD_PRECOND_SCHUR, IbrdError, Grid, SolveOpts, load_library, EXPORTED,
+                   ibrd_apply_L, ibrd_grid_create, ibrd_grid_destroy, ibrd_interp, ibrd_set_blobs,
+                   ibrd_solve_reaction, ibrd_solve_saddle, ibrd_spread, ibrd_vcycle, ibrd_last_error,
+                   ibrd_default_opts)
+
+__all__ = ["IBRD_FP64", "IBRD_MIXED_FP32", "IBRD_PESKIN3", "IBRD_PESKIN4", "IBRD_PRECOND_DIAG",
+           "IBRD_PRECOND_SCHUR", "IbrdError", "Grid", "SolveOpts", "load_library", "EXPORTED",
+           "ibrd_apply_L", "ibrd_grid_create", "ibrd_grid_destroy", "ibrd_interp", "ibrd_set_blobs",
+           "ibrd_solve_reaction", "ibrd_solve_saddle", "ibrd_spread", "ibrd_vcycle", "ibrd_last_error",
+           "ibrd_default_opts"]

@@ -1,0 +1,260 @@
+"""ctypes binding of libibrd (argument marshalling only).
+
+Each ``ibrd_*`` function here has the name and argument order of the C entry
+point in ``include/ibrd.h``; tensors are passed by device pointer.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libibrd.so")
+
+IBRD_PESKIN4, IBRD_PESKIN3 = 4, 3
+IBRD_FP64, IBRD_MIXED_FP32 = 0, 1
+IBRD_PRECOND_SCHUR, IBRD_PRECOND_DIAG = 0, 1
+
+STATUS = {0: "IBRD_OK", 1: "IBRD_ERR_ARG", 2: "IBRD_ERR_CUDA", 3: "IBRD_ERR_OOM", 4: "IBRD_ERR_NOT_CONVERGED",
+          5: "IBRD_ERR_BREAKDOWN", 6: "IBRD_ERR_NONFINITE", 7: "IBRD_ERR_TIMEOUT", 8: "IBRD_ERR_STATE"}
+
+# Every entry point declared in include/ibrd.h.
+EXPORTED = ["ibrd_default_opts", "ibrd_grid_create", "ibrd_grid_destroy", "ibrd_set_blobs", "ibrd_apply_L",
+            "ibrd_vcycle", "ibrd_spread", "ibrd_interp", "ibrd_solve_reaction", "ibrd_solve_saddle",
+            "ibrd_last_error", "ibrd_status_string"]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("restart", ctypes.c_int),
+                ("mg_cycles", ctypes.c_int), ("schur_inner", ctypes.c_int), ("precond", ctypes.c_int),
+                ("zeta", ctypes.c_double), ("xi", ctypes.c_double), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
+                ("precision", ctypes.c_int), ("use_guess", ctypes.c_int)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("outer_iters", ctypes.c_int), ("inner_iters", ctypes.c_int),
+                ("vcycles", ctypes.c_int), ("rel_residual", ctypes.c_double), ("sum_lambda", ctypes.c_double),
+                ("cbar", ctypes.c_double), ("rate_K", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("residual_history", ctypes.POINTER(ctypes.c_double)), ("history_len", ctypes.c_int),
+                ("history_cap", ctypes.c_int)]
+
+
+class IbrdError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libibrd.so (built by ``paper_1306_3159_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libibrd.so not built at {path}; run paper_1306_3159_gb300/build.py")
+    lib = ctypes.CDLL(path)
+    vp, i, d, P = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.POINTER
+    lib.ibrd_default_opts.argtypes = [P(SolveOpts)]
+    lib.ibrd_default_opts.restype = None
+    lib.ibrd_grid_create.argtypes = [P(vp), i, i, i, d, d, d, i, i, vp]
+    lib.ibrd_grid_create.restype = i
+    lib.ibrd_grid_destroy.argtypes = [vp]
+    lib.ibrd_grid_destroy.restype = None
+    lib.ibrd_set_blobs.argtypes = [vp, vp, i]
+    lib.ibrd_set_blobs.restype = i
+    lib.ibrd_apply_L.argtypes = [vp, vp, vp]
+    lib.ibrd_apply_L.restype = i
+    lib.ibrd_vcycle.argtypes = [vp, vp, vp, i]
+    lib.ibrd_vcycle.restype = i
+    lib.ibrd_spread.argtypes = [vp, vp, vp, i]
+    lib.ibrd_spread.restype = i
+    lib.ibrd_interp.argtypes = [vp, vp, vp]
+    lib.ibrd_interp.restype = i
+    lib.ibrd_solve_reaction.argtypes = [vp, vp, vp, vp, P(SolveOpts), P(SolveInfo)]
+    lib.ibrd_solve_reaction.restype = i
+    lib.ibrd_solve_saddle.argtypes = [vp, vp, vp, vp, vp, P(SolveOpts), P(SolveInfo)]
+    lib.ibrd_solve_saddle.restype = i
+    lib.ibrd_last_error.argtypes = [vp]
+    lib.ibrd_last_error.restype = ctypes.c_char_p
+    lib.ibrd_status_string.argtypes = [i]
+    lib.ibrd_status_string.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch tensor")
+    if not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA float64 tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _check(g, st: int):
+    if st != 0:
+        msg = ibrd_last_error(g) if g else ""
+        raise IbrdError(st, msg)
+
+
+def _stream(stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def ibrd_default_opts(**kw) -> SolveOpts:
+    o = SolveOpts()
+    load_library().ibrd_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def ibrd_grid_create(nx, ny, nz, h=1.0, chi=1.0, alpha=0.0, kernel=IBRD_PESKIN4, precision=IBRD_FP64, stream=None):
+    lib = load_library()
+    g = ctypes.c_void_p()
+    st = lib.ibrd_grid_create(ctypes.byref(g), int(nx), int(ny), int(nz), float(h), float(chi), float(alpha),
+                              int(kernel), int(precision), _stream(stream))
+    if st != 0:
+        raise IbrdError(st, "ibrd_grid_create rejected its arguments")
+    return g
+
+
+def ibrd_grid_destroy(g):
+    load_library().ibrd_grid_destroy(g)
+
+
+def ibrd_last_error(g) -> str:
+    return load_library().ibrd_last_error(g).decode()
+
+
+def ibrd_set_blobs(g, q, n=None):
+    n = int(q.shape[0]) if n is None else int(n)
+    _check(g, load_library().ibrd_set_blobs(g, _ptr(q) if n else None, n))
+
+
+def ibrd_apply_L(g, c, y):
+    _check(g, load_library().ibrd_apply_L(g, _ptr(c), _ptr(y)))
+
+
+def ibrd_vcycle(g, rhs, x, zero_initial_guess=True):
+    _check(g, load_library().ibrd_vcycle(g, _ptr(rhs), _ptr(x), int(bool(zero_initial_guess))))
+
+
+def ibrd_spread(g, lam, out, accumulate=False):
+    _check(g, load_library().ibrd_spread(g, _ptr(lam), _ptr(out), int(bool(accumulate))))
+
+
+def ibrd_interp(g, c, out):
+    _check(g, load_library().ibrd_interp(g, _ptr(c), _ptr(out)))
+
+
+def _info(history_cap):
+    import numpy as np
+    info = SolveInfo()
+    hist = np.zeros(max(1, history_cap), dtype=np.float64)
+    info.residual_history = hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    info.history_cap = history_cap
+    return info, hist
+
+
+def _info_dict(info, hist):
+    return {"status": info.status, "outer_iters": info.outer_iters, "inner_iters": info.inner_iters,
+            "vcycles": info.vcycles, "rel_residual": info.rel_residual, "sum_lambda": info.sum_lambda,
+            "cbar": info.cbar, "rate_K": info.rate_K, "seconds": info.seconds,
+            "history": hist[:info.history_len].copy()}
+
+
+def ibrd_solve_reaction(g, kappa, rhs, c, opts: SolveOpts | None = None, history_cap=4096, raise_on_error=True):
+    info, hist = _info(history_cap)
+    st = load_library().ibrd_solve_reaction(g, _ptr(kappa), _ptr(rhs), _ptr(c),
+                                            ctypes.byref(opts) if opts is not None else None, ctypes.byref(info))
+    if raise_on_error:
+        _check(g, st)
+    out = _info_dict(info, hist)
+    out["status"] = st
+    return out
+
+
+def ibrd_solve_saddle(g, rhs, f, c, lam, opts: SolveOpts | None = None, history_cap=4096, raise_on_error=True):
+    info, hist = _info(history_cap)
+    st = load_library().ibrd_solve_saddle(g, _ptr(rhs), _ptr(f), _ptr(c), _ptr(lam),
+                                          ctypes.byref(opts) if opts is not None else None, ctypes.byref(info))
+    if raise_on_error:
+        _check(g, st)
+    out = _info_dict(info, hist)
+    out["status"] = st
+    return out
+
+
+class Grid:
+    """Owning wrapper of an ``ibrd_grid`` handle."""
+
+    def __init__(self, nx, ny, nz, h=1.0, chi=1.0, alpha=0.0, kernel=IBRD_PESKIN4, precision=IBRD_FP64,
+                 stream=None):
+        self.dims = (int(nx), int(ny), int(nz))
+        self.h, self.chi, self.alpha = float(h), float(chi), float(alpha)
+        self.handle = ibrd_grid_create(nx, ny, nz, h, chi, alpha, kernel, precision, stream)
+        self.n_blobs = 0
+
+    def close(self):
+        if self.handle is not None:
+            ibrd_grid_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def field(self, fill=0.0):
+        import torch
+        nx, ny, nz = self.dims
+        return torch.full((nz, ny, nx), float(fill), dtype=torch.float64, device="cuda")
+
+    def set_blobs(self, q):
+        self.n_blobs = int(q.shape[0])
+        ibrd_set_blobs(self.handle, q)
+
+    def apply_L(self, c, y=None):
+        y = self.field() if y is None else y
+        ibrd_apply_L(self.handle, c, y)
+        return y
+
+    def vcycle(self, rhs, x=None, zero_initial_guess=True):
+        x = self.field() if x is None else x
+        ibrd_vcycle(self.handle, rhs, x, zero_initial_guess)
+        return x
+
+    def spread(self, lam, out=None, accumulate=False):
+        out = self.field() if out is None else out
+        ibrd_spread(self.handle, lam, out, accumulate)
+        return out
+
+    def interp(self, c, out=None):
+        import torch
+        out = torch.zeros(self.n_blobs, dtype=torch.float64, device="cuda") if out is None else out
+        ibrd_interp(self.handle, c, out)
+        return out
+
+    def solve_reaction(self, kappa, rhs, c=None, **kw):
+        c = self.field() if c is None else c
+        info = ibrd_solve_reaction(self.handle, kappa, rhs, c, ibrd_default_opts(**kw))
+        return c, info
+
+    def solve_saddle(self, rhs, f=None, c=None, lam=None, **kw):
+        import torch
+        c = self.field() if c is None else c
+        lam = torch.zeros(self.n_blobs, dtype=torch.float64, device="cuda") if lam is None else lam
+        info = ibrd_solve_saddle(self.handle, rhs, f, c, lam, ibrd_default_opts(**kw))
+        return c, lam, info

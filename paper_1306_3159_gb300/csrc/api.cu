@@ -1,0 +1,918 @@
+// C ABI of libibrd and the host-side drivers: multigrid V-cycle level loop,
+// flexible GMRES, the reaction-limited and saddle-point operators, and the
+// approximate Schur-complement preconditioner of Appendix A.
+//
+// Every arithmetic step runs in the CUDA kernels of grid_kernels.cu,
+// blob_kernels.cu and krylov_kernels.cu; the host only sequences launches and
+// reads back scalars (norms, residual estimates) to steer the iteration.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "internal.h"
+
+namespace ibrd {
+
+struct ArgError {
+  ibrd_status code;
+  std::string msg;
+};
+
+namespace {
+
+// Device scalar slots.
+enum Slot {
+  S_BB = 0,   // ||b||^2
+  S_SQ,       // ||w||^2 after orthogonalisation
+  S_RES,      // residual estimate |g_{j+1}|
+  S_MEAN,     // mean of a field (V-cycle projection)
+  S_MEANX,    // mean of the V-cycle result
+  S_GSUM,     // sum of g (saddle preconditioner)
+  S_LBAR,     // lambda-bar of Appendix A
+  S_CBAR,     // c-bar of Appendix A
+  S_TMP,      // scratch
+  S_TMP2,
+  S_NORM,     // sqrt of S_SQ
+  S_COUNT = 32
+};
+
+__global__ void k_scalar_affine(double* dst, const double* src, double a) {
+  if (threadIdx.x == 0) *dst = a * (*src);
+}
+
+__global__ void k_check_rates(const double* __restrict__ k, int n, int* __restrict__ flag) {
+  int bad = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    bad |= !(isfinite(k[i]) && k[i] >= 0.0);
+  bad = __syncthreads_or(bad);
+  if (bad && threadIdx.x == 0) atomicOr(flag, 1);
+}
+
+__global__ void k_set_gvec(double* gvec, int m, const double* beta) {
+  const int i = threadIdx.x;
+  if (i <= m) gvec[i] = (i == 0) ? *beta : 0.0;
+}
+
+template <typename T>
+struct Hier {
+  std::vector<T*> x, b;                       // levels >= 1 (index = level)
+  T* f0 = nullptr;                            // level-0 scratch fields (mixed path)
+  T* f1 = nullptr;
+  std::vector<std::pair<double, T*>> tables;  // coarsest Green's tables by shift
+};
+
+struct Level {
+  Dims d;
+  double h;
+};
+
+}  // namespace
+}  // namespace ibrd
+
+using namespace ibrd;
+
+struct ibrd_grid_s {
+  int dev = 0;
+  Dims d{};
+  double h = 1, chi = 1, alpha = 0;
+  int kernel = 4;
+  int precision = IBRD_FP64;
+  cudaStream_t s = nullptr;
+  std::vector<Level> levels;
+  Hier<double> h64;
+  Hier<float> h32;
+  BlobSet blobs;
+  double* scal = nullptr;       // S_COUNT device scalars
+  double* partial = nullptr;    // kRedBlocks * kDotGroup
+  double* host = nullptr;       // pinned host scalars
+  int* dflag = nullptr;
+  // Krylov workspace
+  double* V = nullptr;
+  double* Z = nullptr;
+  size_t vlen = 0;
+  int vcap = 0;
+  double *H = nullptr, *cs = nullptr, *sn = nullptr, *gvec = nullptr, *yv = nullptr, *hb2 = nullptr;
+  int hcap = 0;
+  double *xs = nullptr, *bs = nullptr;  // saddle [c; lambda] solution and rhs
+  size_t xs_cap = 0;
+  // preconditioner workspaces (FP64 and FP32 fields)
+  double *p64[4] = {nullptr, nullptr, nullptr, nullptr};
+  float *p32[4] = {nullptr, nullptr, nullptr, nullptr};
+  // N-vector workspaces
+  double *nv[4] = {nullptr, nullptr, nullptr, nullptr};
+  double *U = nullptr, *Hs = nullptr, *scs = nullptr, *ssn = nullptr, *sg = nullptr;
+  int ncap = -1, ucap = 0;
+  double gamma_diag = 0.0;      // M_11 for the diagonal preconditioner
+  bool gamma_valid = false;
+  // counters of the current solve
+  long vcycles = 0;
+  long inner = 0;
+  std::string err;
+};
+
+namespace ibrd {
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+template <typename T>
+T* dalloc(size_t n) {
+  T* p = nullptr;
+  IBRD_CUDA(cudaMalloc(&p, sizeof(T) * (n ? n : 1)));
+  return p;
+}
+
+double host_scalar(ibrd_grid g, int slot) {
+  IBRD_CUDA(cudaMemcpyAsync(g->host, g->scal + slot, sizeof(double), cudaMemcpyDeviceToHost, g->s));
+  IBRD_CUDA(cudaStreamSynchronize(g->s));
+  return g->host[0];
+}
+
+// S = h^-3 J^T (Sec. III.A): the spreading kernels take h^-3 in their scale.
+double inv_h3(ibrd_grid g) { return 1.0 / (g->h * g->h * g->h); }
+
+Stencil stencil(double h, double chi, double shift) {
+  const double off = chi / (h * h);
+  return Stencil{shift + 6.0 * off, off};
+}
+
+template <typename T>
+Hier<T>& hier(ibrd_grid g);
+template <>
+Hier<double>& hier<double>(ibrd_grid g) { return g->h64; }
+template <>
+Hier<float>& hier<float>(ibrd_grid g) { return g->h32; }
+
+template <typename T>
+void ensure_hier(ibrd_grid g) {
+  Hier<T>& H = hier<T>(g);
+  if (!H.x.empty()) return;
+  const size_t L = g->levels.size();
+  H.x.assign(L, nullptr);
+  H.b.assign(L, nullptr);
+  for (size_t l = 1; l < L; ++l) {
+    H.x[l] = dalloc<T>(g->levels[l].d.n());
+    H.b[l] = dalloc<T>(g->levels[l].d.n());
+  }
+}
+
+template <typename T>
+const T* coarse_table(ibrd_grid g, double shift) {
+  Hier<T>& H = hier<T>(g);
+  for (auto& e : H.tables)
+    if (e.first == shift) return e.second;
+  const Level& lc = g->levels.back();
+  T* t = dalloc<T>(lc.d.n());
+  launch_coarse_table<T>(t, lc.d, stencil(lc.h, g->chi, shift), shift == 0.0 ? 1 : 0, g->s);
+  H.tables.emplace_back(shift, t);
+  return t;
+}
+
+// One V-cycle on level l for A_l x = b - bshift (bshift nullable).
+template <typename T>
+void vcycle_level(ibrd_grid g, int l, const T* b, const double* bshift, T* x, bool zero, double shift, int nu1,
+                  int nu2) {
+  Hier<T>& H = hier<T>(g);
+  const Level& lv = g->levels[l];
+  const Stencil st = stencil(lv.h, g->chi, shift);
+  if (l == (int)g->levels.size() - 1) {
+    // Exact coarsest solve. A constant shift of b only changes the mean, which
+    // the singular pseudo-inverse ignores; the nonsingular case never shifts.
+    launch_coarse_solve<T>(coarse_table<T>(g, shift), b, x, lv.d, g->s);
+    return;
+  }
+  if (nu1 == 0 && zero) IBRD_CUDA(cudaMemsetAsync(x, 0, sizeof(T) * lv.d.n(), g->s));
+  for (int sweep = 0; sweep < nu1; ++sweep) {
+    if (sweep == 0 && zero)
+      launch_rbgs_zero<T>(x, b, bshift, lv.d, st, g->s);
+    else
+      launch_rbgs<T>(x, b, bshift, lv.d, st, 0, g->s);
+    launch_rbgs<T>(x, b, bshift, lv.d, st, 1, g->s);
+  }
+  launch_residual_restrict<T>(x, b, bshift, H.b[l + 1], lv.d, st, g->s);
+  vcycle_level<T>(g, l + 1, H.b[l + 1], nullptr, H.x[l + 1], true, shift, nu1, nu2);
+  launch_prolong_add<T>(H.x[l + 1], x, lv.d, g->s);
+  for (int sweep = 0; sweep < nu2; ++sweep) {
+    launch_rbgs<T>(x, b, bshift, lv.d, st, 0, g->s);
+    launch_rbgs<T>(x, b, bshift, lv.d, st, 1, g->s);
+  }
+}
+
+// One V-cycle on the finest level for (shift I - chi L) x = b. When shift is
+// 0 (periodic, singular) the right-hand side is taken with its mean removed
+// and the result is returned with mean zero.
+template <typename T>
+void vcycle(ibrd_grid g, const T* b, T* x, bool zero, double shift, int nu1, int nu2) {
+  ensure_hier<T>(g);
+  const Dims d = g->d;
+  const double* bshift = nullptr;
+  if (shift == 0.0) {
+    launch_sum<T>(b, d.n(), g->partial, g->scal + S_MEAN, 1.0 / (double)d.n(), g->s);
+    bshift = g->scal + S_MEAN;
+  }
+  vcycle_level<T>(g, 0, b, bshift, x, zero, shift, nu1, nu2);
+  if (shift == 0.0) {
+    launch_sum<T>(x, d.n(), g->partial, g->scal + S_MEANX, 1.0 / (double)d.n(), g->s);
+    launch_sub_scalar<T>(x, d.n(), g->scal + S_MEANX, g->s);
+  }
+  g->vcycles++;
+}
+
+template <typename T>
+void vcycles(ibrd_grid g, const T* b, T* x, bool zero, double shift, int n, int nu1, int nu2) {
+  for (int i = 0; i < n; ++i) vcycle<T>(g, b, x, zero && i == 0, shift, nu1, nu2);
+}
+
+// ---------------------------------------------------------------- Krylov
+struct LinOp {
+  virtual ~LinOp() = default;
+  virtual void apply(const double* x, double* y) = 0;
+  virtual void precond(const double* v, double* z) = 0;
+};
+
+void ensure_krylov(ibrd_grid g, size_t n, int restart) {
+  if (g->vlen != n || g->vcap < restart) {
+    cudaFree(g->V);
+    cudaFree(g->Z);
+    g->V = g->Z = nullptr;
+    g->V = dalloc<double>(n * (restart + 1));
+    g->Z = dalloc<double>(n * restart);
+    g->vlen = n;
+    g->vcap = restart;
+  }
+  if (g->hcap < restart) {
+    cudaFree(g->H);
+    cudaFree(g->cs);
+    cudaFree(g->sn);
+    cudaFree(g->gvec);
+    cudaFree(g->yv);
+    cudaFree(g->hb2);
+    g->H = dalloc<double>((size_t)(restart + 1) * restart);
+    g->cs = dalloc<double>(restart);
+    g->sn = dalloc<double>(restart);
+    g->gvec = dalloc<double>(restart + 1);
+    g->yv = dalloc<double>(restart);
+    g->hb2 = dalloc<double>(restart + 1);
+    g->hcap = restart;
+  }
+}
+
+// w (= V[j+1]) <- w - sum_{i<=j} h_i V[i], h written into H[:, j]; returns
+// ||w||^2 after orthogonalisation in S_SQ. Classical Gram-Schmidt with a
+// second pass when the norm drops below 1/sqrt(2) of its value (DGKS test).
+double orthogonalize(ibrd_grid g, int j, size_t n, int ldh, double* ww_out) {
+  double* V = g->V;
+  double* w = V + (size_t)(j + 1) * n;
+  double* hcol = g->H + (size_t)j * ldh;
+  const int nb = j + 1;  // basis vectors V[0..j]
+  // pass 1: dots of V[0..j+1] (the last is <w, w>)
+  for (int g0 = 0; g0 < nb + 1; g0 += kDotGroup) {
+    const int m = std::min(kDotGroup, nb + 1 - g0);
+    launch_multidot(V + (size_t)g0 * n, n, m, w, n, g->partial, g->s);
+    launch_reduce_partials(g->partial, m, hcol + g0, g->s);
+  }
+  IBRD_CUDA(cudaMemcpyAsync(g->scal + S_TMP, hcol + nb, sizeof(double), cudaMemcpyDeviceToDevice, g->s));
+  for (int g0 = 0; g0 < nb; g0 += kDotGroup) {
+    const int m = std::min(kDotGroup, nb - g0);
+    const bool last = g0 + m >= nb;
+    launch_multi_axpy(w, V + (size_t)g0 * n, n, m, hcol + g0, -1.0, n, last ? g->partial : nullptr, g->s);
+  }
+  launch_reduce_partials(g->partial, 1, g->scal + S_SQ, g->s);
+  IBRD_CUDA(cudaMemcpyAsync(g->host, g->scal + S_TMP, sizeof(double) * 1, cudaMemcpyDeviceToHost, g->s));
+  IBRD_CUDA(cudaMemcpyAsync(g->host + 1, g->scal + S_SQ, sizeof(double) * 1, cudaMemcpyDeviceToHost, g->s));
+  IBRD_CUDA(cudaStreamSynchronize(g->s));
+  const double ww = g->host[0];
+  double sq = g->host[1];
+  if (ww_out) *ww_out = ww;
+  if (sq < 0.5 * ww) {
+    // pass 2
+    for (int g0 = 0; g0 < nb; g0 += kDotGroup) {
+      const int m = std::min(kDotGroup, nb - g0);
+      launch_multidot(V + (size_t)g0 * n, n, m, w, n, g->partial, g->s);
+      launch_reduce_partials(g->partial, m, g->hb2 + g0, g->s);
+    }
+    for (int g0 = 0; g0 < nb; g0 += kDotGroup) {
+      const int m = std::min(kDotGroup, nb - g0);
+      const bool last = g0 + m >= nb;
+      launch_multi_axpy(w, V + (size_t)g0 * n, n, m, g->hb2 + g0, -1.0, n, last ? g->partial : nullptr, g->s);
+    }
+    launch_reduce_partials(g->partial, 1, g->scal + S_SQ, g->s);
+    launch_vec_add_small(hcol, g->hb2, nb, g->s);
+    sq = host_scalar(g, S_SQ);
+  }
+  return sq;
+}
+
+struct SolveResult {
+  ibrd_status st = IBRD_OK;
+  int iters = 0;
+  double rel = 0;
+};
+
+// Right-preconditioned flexible GMRES (Saad 1993) with true-residual restarts.
+SolveResult fgmres(ibrd_grid g, LinOp& op, const double* b, double* x, size_t n, const ibrd_solve_opts& o,
+                   bool zero_guess, ibrd_solve_info* info) {
+  SolveResult R;
+  const int m = std::max(1, o.restart);
+  ensure_krylov(g, n, m);
+  const int ldh = m + 1;
+  double* V = g->V;
+  double* Z = g->Z;
+  launch_dot(b, b, n, g->partial, g->scal + S_BB, 1.0, g->s);
+  const double bnorm = std::sqrt(host_scalar(g, S_BB));
+  if (!std::isfinite(bnorm)) {
+    R.st = IBRD_ERR_NONFINITE;
+    return R;
+  }
+  if (bnorm == 0.0) {
+    IBRD_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, g->s));
+    return R;
+  }
+  // r0 = b - K x0
+  if (zero_guess) {
+    IBRD_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, g->s));
+    IBRD_CUDA(cudaMemcpyAsync(V, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, g->s));
+  } else {
+    op.apply(x, V);
+    launch_axpby(1.0, b, -1.0, V, n, g->s);
+  }
+  launch_dot(V, V, n, g->partial, g->scal + S_TMP2, 1.0, g->s);
+  launch_sqrt_scalar(g->scal + S_TMP2, g->scal + S_NORM, g->s);
+  double beta = std::sqrt(host_scalar(g, S_TMP2));
+  int hist = 0;
+  while (true) {
+    R.rel = beta / bnorm;
+    if (!std::isfinite(R.rel)) {
+      R.st = IBRD_ERR_NONFINITE;
+      break;
+    }
+    if (R.rel <= o.tol) break;
+    if (R.iters >= o.max_iter) {
+      R.st = IBRD_ERR_NOT_CONVERGED;
+      break;
+    }
+    // V[0] = r / beta, gvec = [beta, 0, ...]
+    launch_scale_by_inv(V, V, n, g->scal + S_NORM, 1.0, g->s);
+    k_set_gvec<<<1, 64, 0, g->s>>>(g->gvec, m, g->scal + S_NORM);
+    check_launch("set_gvec");
+    int k = 0;
+    bool breakdown = false;
+    for (int j = 0; j < m; ++j) {
+      op.precond(V + (size_t)j * n, Z + (size_t)j * n);
+      op.apply(Z + (size_t)j * n, V + (size_t)(j + 1) * n);
+      double ww = 0;
+      const double sq = orthogonalize(g, j, n, ldh, &ww);
+      double* hcol = g->H + (size_t)j * ldh;
+      launch_sqrt_scalar(g->scal + S_SQ, hcol + j + 1, g->s);
+      const bool tiny = !(sq > 1e-28 * ww) || sq <= 0.0;
+      if (!tiny) launch_scale_by_inv(V + (size_t)(j + 1) * n, V + (size_t)(j + 1) * n, n, hcol + j + 1, 1.0, g->s);
+      launch_givens(g->H, ldh, j, g->cs, g->sn, g->gvec, g->scal + S_RES, g->s);
+      const double res = host_scalar(g, S_RES);
+      k = j + 1;
+      R.iters++;
+      if (info && info->residual_history && hist < info->history_cap) info->residual_history[hist++] = res / bnorm;
+      if (!std::isfinite(res) || !std::isfinite(sq)) {
+        R.st = IBRD_ERR_NONFINITE;
+        break;
+      }
+      if (tiny) {
+        breakdown = true;
+        break;
+      }
+      if (res / bnorm <= o.tol || R.iters >= o.max_iter) break;
+    }
+    if (R.st == IBRD_ERR_NONFINITE) break;
+    // x += Z y
+    launch_backsolve(g->H, ldh, k, g->gvec, g->yv, g->s);
+    for (int g0 = 0; g0 < k; g0 += kDotGroup) {
+      const int mm = std::min(kDotGroup, k - g0);
+      launch_multi_axpy(x, Z + (size_t)g0 * n, n, mm, g->yv + g0, 1.0, n, nullptr, g->s);
+    }
+    // true residual
+    op.apply(x, V);
+    launch_axpby(1.0, b, -1.0, V, n, g->s);
+    launch_dot(V, V, n, g->partial, g->scal + S_TMP2, 1.0, g->s);
+    launch_sqrt_scalar(g->scal + S_TMP2, g->scal + S_NORM, g->s);
+    beta = std::sqrt(host_scalar(g, S_TMP2));
+    if (breakdown && beta / bnorm > o.tol) {
+      R.rel = beta / bnorm;
+      // an invariant subspace was found but the true residual disagrees:
+      // restart once more unless nothing changes
+      if (R.iters >= o.max_iter) {
+        R.st = IBRD_ERR_BREAKDOWN;
+        break;
+      }
+    }
+  }
+  if (info) info->history_len = hist;
+  return R;
+}
+
+// ---------------------------------------------------------------- workspaces
+template <typename T>
+T* pfield(ibrd_grid g, int i);
+template <>
+double* pfield<double>(ibrd_grid g, int i) {
+  if (!g->p64[i]) g->p64[i] = dalloc<double>(g->d.n());
+  return g->p64[i];
+}
+template <>
+float* pfield<float>(ibrd_grid g, int i) {
+  if (!g->p32[i]) g->p32[i] = dalloc<float>(g->d.n());
+  return g->p32[i];
+}
+
+void ensure_nvec(ibrd_grid g, int m) {
+  const int n = g->blobs.n;
+  if (g->ncap != n) {
+    for (auto& p : g->nv) {
+      cudaFree(p);
+      p = nullptr;
+    }
+    for (auto& p : g->nv) p = dalloc<double>(std::max(n, 1));
+    cudaFree(g->U);
+    g->U = nullptr;
+    g->ucap = 0;
+    g->ncap = n;
+  }
+  if (g->ucap < m) {
+    cudaFree(g->U);
+    cudaFree(g->Hs);
+    cudaFree(g->scs);
+    cudaFree(g->ssn);
+    cudaFree(g->sg);
+    g->U = dalloc<double>((size_t)(m + 1) * std::max(n, 1));
+    g->Hs = dalloc<double>((size_t)(m + 1) * m);
+    g->scs = dalloc<double>(m);
+    g->ssn = dalloc<double>(m);
+    g->sg = dalloc<double>(m + 1);
+    g->ucap = m;
+  }
+}
+
+// ---------------------------------------------------------------- operators
+// B c = alpha c - chi L c + S (kappa * J c)  (Eq. unsteady_system / steady_state)
+template <typename T>
+struct ReactionOp : LinOp {
+  ibrd_grid g;
+  const double* kappa;
+  double sigma;
+  ibrd_solve_opts o;
+  ReactionOp(ibrd_grid g_, const double* k_, double sg, const ibrd_solve_opts& o_) : g(g_), kappa(k_), sigma(sg), o(o_) {}
+  void apply(const double* x, double* y) override {
+    launch_interp<double>(g->blobs, g->d, x, 1.0, g->nv[0], g->s);
+    launch_apply_A<double>(x, y, g->d, stencil(g->h, g->chi, g->alpha), g->s);
+    launch_spread<double>(g->blobs, g->d, g->nv[0], kappa, inv_h3(g), y, 1, g->s);
+  }
+  // n V-cycles of (sigma I - chi L) (Eq. Pinv_Poisson)
+  void precond(const double* v, double* z) override {
+    if (sizeof(T) == 8) {
+      vcycles<double>(g, v, z, true, sigma, o.mg_cycles, o.nu1, o.nu2);
+    } else {
+      float* b32 = pfield<float>(g, 0);
+      float* x32 = pfield<float>(g, 1);
+      launch_convert<double, float>(v, b32, g->d.n(), 1.0, nullptr, g->s);
+      vcycles<float>(g, b32, x32, true, sigma, o.mg_cycles, o.nu1, o.nu2);
+      launch_convert<float, double>(x32, z, g->d.n(), 1.0, nullptr, g->s);
+    }
+  }
+};
+
+// K [c; lambda] = [A c + zeta S lambda; xi J c]  (Eq. saddle_point)
+template <typename T>
+struct SaddleOp : LinOp {
+  ibrd_grid g;
+  ibrd_solve_opts o;
+  double zeta, xi;
+  bool singular;
+  SaddleOp(ibrd_grid g_, const ibrd_solve_opts& o_, double z, double x) : g(g_), o(o_), zeta(z), xi(x) {
+    singular = (g->alpha == 0.0);
+  }
+  void apply(const double* x, double* y) override {
+    const size_t nc = g->d.n();
+    launch_apply_A<double>(x, y, g->d, stencil(g->h, g->chi, g->alpha), g->s);
+    launch_spread<double>(g->blobs, g->d, x + nc, nullptr, zeta * inv_h3(g), y, 1, g->s);
+    launch_interp<double>(g->blobs, g->d, x, xi, y + nc, g->s);
+  }
+  // Appendix A, steps 1-5, with A~_n^-1 = n V-cycles and, for the approximate
+  // Schur complement, m GMRES iterations on J A~_1^-1 S.
+  void precond(const double* v, double* z) override {
+    const size_t nc = g->d.n();
+    const int N = g->blobs.n;
+    const double* vc = v;
+    const double* vf = v + nc;
+    double* zc = z;
+    double* zl = z + nc;
+    T* gt = pfield<T>(g, 0);   // g~
+    T* cs = pfield<T>(g, 1);   // c~* then c~
+    const double volume = (double)nc * g->h * g->h * g->h;
+    const double shift = g->alpha;
+    // step 1: g~ = g - alpha V N^-1 S <g>, c~* = A~_n^-1 g~
+    launch_convert<double, T>(vc, gt, nc, 1.0, nullptr, g->s);
+    if (singular) {
+      launch_sum<double>(vc, nc, g->partial, g->scal + S_GSUM, 1.0, g->s);
+      // zeta S (lambda-bar 1) = (V / (N N_c)) sum(g) S 1
+      launch_spread_const<T>(g->blobs, g->d, g->scal + S_GSUM, -volume / ((double)N * (double)nc) * inv_h3(g), gt,
+                             g->s);
+      k_scalar_affine<<<1, 1, 0, g->s>>>(g->scal + S_LBAR, g->scal + S_GSUM, volume / (zeta * N * (double)nc));
+      check_launch("lbar");
+    }
+    vcycles<T>(g, gt, cs, true, shift, o.mg_cycles, o.nu1, o.nu2);
+    // step 2: rhs = (zeta xi)^-1 (xi J c~* - f)
+    double* rhs = g->nv[0];
+    double* lam = g->nv[1];
+    launch_interp<T>(g->blobs, g->d, cs, 1.0 / zeta, rhs, g->s);
+    launch_axpby(-1.0 / (zeta * xi), vf, 1.0, rhs, N, g->s);
+    if (o.precond == IBRD_PRECOND_DIAG) {
+      launch_convert<double, double>(rhs, lam, N, 1.0 / g->gamma_diag, nullptr, g->s);
+      if (singular) {
+        launch_sum<double>(lam, N, g->partial, g->scal + S_TMP, 1.0 / N, g->s);
+        launch_sub_scalar<double>(lam, N, g->scal + S_TMP, g->s);
+      }
+    } else {
+      const int m = std::max(1, o.schur_inner);
+      T* fs = pfield<T>(g, 2);
+      T* fx = pfield<T>(g, 3);
+      launch_small_start(rhs, g->U, N, g->sg, m, g->s);
+      for (int j = 0; j < m; ++j) {
+        launch_spread<T>(g->blobs, g->d, g->U + (size_t)j * N, nullptr, inv_h3(g), fs, 0, g->s);
+        vcycle<T>(g, fs, fx, true, shift, o.nu1, o.nu2);
+        launch_interp<T>(g->blobs, g->d, fx, 1.0, g->U + (size_t)(j + 1) * N, g->s);
+        launch_small_arnoldi(g->U, N, j, g->Hs, m + 1, g->scs, g->ssn, g->sg, g->s);
+        g->inner++;
+      }
+      launch_small_finish(g->U, N, m, g->Hs, m + 1, g->sg, lam, singular ? 1 : 0, g->s);
+    }
+    // step 3: c~ = A~_n^-1 (g~ - zeta S lambda~) from c~*
+    launch_spread<T>(g->blobs, g->d, lam, nullptr, -zeta * inv_h3(g), gt, 1, g->s);
+    vcycles<T>(g, gt, cs, false, shift, o.mg_cycles, o.nu1, o.nu2);
+    // steps 4-5
+    if (singular) {
+      double* t = g->nv[2];
+      launch_interp<T>(g->blobs, g->d, cs, 1.0, t, g->s);
+      launch_axpby(1.0 / xi, vf, -1.0, t, N, g->s);
+      launch_sum<double>(t, N, g->partial, g->scal + S_CBAR, 1.0 / N, g->s);
+      launch_convert<double, double>(lam, zl, N, 1.0, g->scal + S_LBAR, g->s);
+      launch_convert<T, double>(cs, zc, nc, 1.0, g->scal + S_CBAR, g->s);
+    } else {
+      IBRD_CUDA(cudaMemcpyAsync(zl, lam, sizeof(double) * N, cudaMemcpyDeviceToDevice, g->s));
+      launch_convert<T, double>(cs, zc, nc, 1.0, nullptr, g->s);
+    }
+  }
+};
+
+// M_11 = (J A^-1 S)_11 of blob 0 by V-cycle iteration to convergence (used by
+// the diagonal preconditioner, Eq. Schur_diagonal).
+double compute_gamma(ibrd_grid g, const ibrd_solve_opts& o) {
+  const size_t nc = g->d.n();
+  double* e = pfield<double>(g, 0);
+  double* x = pfield<double>(g, 1);
+  double* unit = g->nv[3];
+  IBRD_CUDA(cudaMemsetAsync(unit, 0, sizeof(double) * g->blobs.n, g->s));
+  const double one = 1.0;
+  IBRD_CUDA(cudaMemcpyAsync(unit, &one, sizeof(double), cudaMemcpyHostToDevice, g->s));
+  launch_spread<double>(g->blobs, g->d, unit, nullptr, inv_h3(g), e, 0, g->s);
+  for (int it = 0; it < 40; ++it) vcycle<double>(g, e, x, it == 0, g->alpha, o.nu1, o.nu2);
+  launch_interp<double>(g->blobs, g->d, x, 1.0, g->nv[2], g->s);
+  IBRD_CUDA(cudaMemcpyAsync(g->host, g->nv[2], sizeof(double), cudaMemcpyDeviceToHost, g->s));
+  IBRD_CUDA(cudaStreamSynchronize(g->s));
+  (void)nc;
+  return g->host[0];
+}
+
+ibrd_status fail(ibrd_grid g, ibrd_status st, const std::string& msg) {
+  if (g) g->err = msg;
+  return st;
+}
+
+template <typename F>
+ibrd_status guarded(ibrd_grid g, const char* name, F&& f) {
+  if (!g) return IBRD_ERR_ARG;
+  DeviceGuard dg(g->dev);
+  try {
+    g->err.clear();
+    return f();
+  } catch (const ArgError& e) {
+    return fail(g, e.code, std::string(name) + ": " + e.msg);
+  } catch (const CudaError& e) {
+    const ibrd_status st = (e.code == cudaErrorMemoryAllocation) ? IBRD_ERR_OOM : IBRD_ERR_CUDA;
+    cudaGetLastError();
+    return fail(g, st, std::string(name) + ": " + e.what + ": " + cudaGetErrorString(e.code));
+  } catch (const std::bad_alloc&) {
+    return fail(g, IBRD_ERR_OOM, std::string(name) + ": host allocation failed");
+  }
+}
+
+ibrd_solve_opts resolve_opts(ibrd_grid g, const ibrd_solve_opts* in) {
+  ibrd_solve_opts o;
+  ibrd_default_opts(&o);
+  if (in) o = *in;
+  if (o.precision < 0) o.precision = g->precision;
+  if (o.xi <= 0.0) o.xi = o.zeta / (g->h * g->h * g->h);
+  if (!(o.tol > 0.0) || o.restart < 1 || o.restart > 60 || o.max_iter < 0 || o.mg_cycles < 1 ||
+      o.schur_inner < 1 || o.schur_inner > 60 || o.nu1 < 0 || o.nu2 < 0 || !(o.zeta != 0.0) ||
+      (o.precision != IBRD_FP64 && o.precision != IBRD_MIXED_FP32) ||
+      (o.precond != IBRD_PRECOND_SCHUR && o.precond != IBRD_PRECOND_DIAG))
+    throw ArgError{IBRD_ERR_ARG, "invalid solver options"};
+  return o;
+}
+
+void fill_info(ibrd_solve_info* info, const SolveResult& R, ibrd_grid g, double t0) {
+  if (!info) return;
+  info->status = R.st;
+  info->outer_iters = R.iters;
+  info->inner_iters = (int)g->inner;
+  info->vcycles = (int)g->vcycles;
+  info->rel_residual = R.rel;
+  info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count() - t0;
+}
+
+double now_s() { return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count(); }
+
+// sum over all cells and N-vector reductions for the report
+void report(ibrd_grid g, const double* c, const double* lam_or_null, const double* kappa, ibrd_solve_info* info) {
+  if (!info) return;
+  const size_t nc = g->d.n();
+  const int N = g->blobs.n;
+  launch_sum<double>(c, nc, g->partial, g->scal + S_TMP, 1.0 / (double)nc, g->s);
+  if (lam_or_null) {
+    launch_sum<double>(lam_or_null, N, g->partial, g->scal + S_TMP2, 1.0, g->s);
+  } else if (N > 0) {
+    launch_interp<double>(g->blobs, g->d, c, 1.0, g->nv[2], g->s);
+    launch_dot(g->nv[2], kappa, N, g->partial, g->scal + S_TMP2, 1.0, g->s);
+  }
+  IBRD_CUDA(cudaMemcpyAsync(g->host, g->scal + S_TMP, sizeof(double) * 2, cudaMemcpyDeviceToHost, g->s));
+  IBRD_CUDA(cudaStreamSynchronize(g->s));
+  info->cbar = g->host[0];
+  info->sum_lambda = N > 0 ? g->host[1] : 0.0;
+  info->rate_K = (N > 0 && info->cbar != 0.0) ? info->sum_lambda / (N * info->cbar) : 0.0;
+}
+
+}  // namespace
+}  // namespace ibrd
+
+// ================================================================ C ABI
+extern "C" {
+
+void ibrd_default_opts(ibrd_solve_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->tol = 1e-8;
+  o->max_iter = 1000;
+  o->restart = 30;
+  o->mg_cycles = 1;
+  o->schur_inner = 5;
+  o->precond = IBRD_PRECOND_SCHUR;
+  o->zeta = 1.0;
+  o->xi = 0.0;
+  o->nu1 = 2;
+  o->nu2 = 2;
+  o->precision = -1;
+  o->use_guess = 0;
+}
+
+const char* ibrd_status_string(int st) {
+  switch (st) {
+    case IBRD_OK: return "IBRD_OK";
+    case IBRD_ERR_ARG: return "IBRD_ERR_ARG";
+    case IBRD_ERR_CUDA: return "IBRD_ERR_CUDA";
+    case IBRD_ERR_OOM: return "IBRD_ERR_OOM";
+    case IBRD_ERR_NOT_CONVERGED: return "IBRD_ERR_NOT_CONVERGED";
+    case IBRD_ERR_BREAKDOWN: return "IBRD_ERR_BREAKDOWN";
+    case IBRD_ERR_NONFINITE: return "IBRD_ERR_NONFINITE";
+    case IBRD_ERR_TIMEOUT: return "IBRD_ERR_TIMEOUT";
+    case IBRD_ERR_STATE: return "IBRD_ERR_STATE";
+    default: return "IBRD_UNKNOWN";
+  }
+}
+
+const char* ibrd_last_error(ibrd_grid g) { return g ? g->err.c_str() : "null handle"; }
+
+void ibrd_grid_destroy(ibrd_grid g) {
+  if (!g) return;
+  DeviceGuard dg(g->dev);
+  auto F = [](void* p) { if (p) cudaFree(p); };
+  for (auto p : g->h64.x) F(p);
+  for (auto p : g->h64.b) F(p);
+  for (auto p : g->h32.x) F(p);
+  for (auto p : g->h32.b) F(p);
+  for (auto& e : g->h64.tables) F(e.second);
+  for (auto& e : g->h32.tables) F(e.second);
+  BlobSet& b = g->blobs;
+  F(b.q); F(b.idx); F(b.w64); F(b.w32); F(b.tile_count); F(b.tile_offset); F(b.tile_cursor); F(b.tile_blobs);
+  F(b.active); F(b.d_meta);
+  F(g->scal); F(g->partial); F(g->dflag);
+  if (g->host) cudaFreeHost(g->host);
+  F(g->V); F(g->Z); F(g->H); F(g->cs); F(g->sn); F(g->gvec); F(g->yv); F(g->hb2); F(g->xs); F(g->bs);
+  for (auto p : g->p64) F(p);
+  for (auto p : g->p32) F(p);
+  for (auto p : g->nv) F(p);
+  F(g->U); F(g->Hs); F(g->scs); F(g->ssn); F(g->sg);
+  delete g;
+}
+
+ibrd_status ibrd_grid_create(ibrd_grid* out, int nx, int ny, int nz, double h, double chi, double alpha, int kernel,
+                             int precision, void* stream) {
+  if (!out) return IBRD_ERR_ARG;
+  *out = nullptr;
+  if (nx < 4 || ny < 4 || nz < 4 || !(h > 0.0) || !(chi > 0.0) || !(alpha >= 0.0) || !std::isfinite(h) ||
+      !std::isfinite(chi) || !std::isfinite(alpha) || (kernel != IBRD_PESKIN4 && kernel != IBRD_PESKIN3) ||
+      (precision != IBRD_FP64 && precision != IBRD_MIXED_FP32))
+    return IBRD_ERR_ARG;
+  if ((double)nx * ny * nz > 4.0e9) return IBRD_ERR_ARG;
+  ibrd_grid g = new (std::nothrow) ibrd_grid_s();
+  if (!g) return IBRD_ERR_OOM;
+  cudaGetDevice(&g->dev);
+  g->d = Dims{nx, ny, nz};
+  g->h = h;
+  g->chi = chi;
+  g->alpha = alpha;
+  g->kernel = kernel;
+  g->precision = precision;
+  g->s = (cudaStream_t)stream;
+  g->blobs.width = kernel;
+  // multigrid levels: halve while every side is even and >= 4
+  g->levels.push_back(Level{g->d, h});
+  while (true) {
+    const Level& l = g->levels.back();
+    if (l.d.nx % 2 == 0 && l.d.ny % 2 == 0 && l.d.nz % 2 == 0 && l.d.nx >= 4 && l.d.ny >= 4 && l.d.nz >= 4)
+      g->levels.push_back(Level{Dims{l.d.nx / 2, l.d.ny / 2, l.d.nz / 2}, 2.0 * l.h});
+    else
+      break;
+  }
+  if (g->levels.back().d.n() > 512) {
+    delete g;
+    return IBRD_ERR_ARG;
+  }
+  ibrd_status st = guarded(g, "ibrd_grid_create", [&]() {
+    g->scal = dalloc<double>(S_COUNT);
+    g->partial = dalloc<double>((size_t)kRedBlocks * kDotGroup);
+    g->dflag = dalloc<int>(4);
+    IBRD_CUDA(cudaMallocHost(&g->host, sizeof(double) * 64));
+    IBRD_CUDA(cudaMemsetAsync(g->scal, 0, sizeof(double) * S_COUNT, g->s));
+    blobs_setup(g->blobs, g->d, g->h, nullptr, 0, g->s);
+    return IBRD_OK;
+  });
+  if (st != IBRD_OK) {
+    ibrd_grid_destroy(g);
+    return st;
+  }
+  *out = g;
+  return IBRD_OK;
+}
+
+ibrd_status ibrd_set_blobs(ibrd_grid g, const double* q, int n) {
+  return guarded(g, "ibrd_set_blobs", [&]() {
+    if (n < 0 || (n > 0 && !q)) throw ArgError{IBRD_ERR_ARG, "bad blob array"};
+    IBRD_CUDA(cudaMemsetAsync(g->dflag, 0, sizeof(int), g->s));
+    if (n > 0) launch_nonfinite<double>(q, (size_t)3 * n, g->dflag, g->s);
+    int flag = 0;
+    IBRD_CUDA(cudaMemcpyAsync(&flag, g->dflag, sizeof(int), cudaMemcpyDeviceToHost, g->s));
+    IBRD_CUDA(cudaStreamSynchronize(g->s));
+    if (flag) throw ArgError{IBRD_ERR_NONFINITE, "non-finite blob position"};
+    blobs_setup(g->blobs, g->d, g->h, q, n, g->s);
+    g->gamma_valid = false;
+    return IBRD_OK;
+  });
+}
+
+ibrd_status ibrd_apply_L(ibrd_grid g, const double* c, double* y) {
+  return guarded(g, "ibrd_apply_L", [&]() {
+    if (!c || !y || c == y) throw ArgError{IBRD_ERR_ARG, "null or aliased field"};
+    launch_apply_A<double>(c, y, g->d, stencil(g->h, g->chi, g->alpha), g->s);
+    return IBRD_OK;
+  });
+}
+
+ibrd_status ibrd_vcycle(ibrd_grid g, const double* rhs, double* x, int zero) {
+  return guarded(g, "ibrd_vcycle", [&]() {
+    if (!rhs || !x || rhs == x) throw ArgError{IBRD_ERR_ARG, "null or aliased field"};
+    vcycle<double>(g, rhs, x, zero != 0, g->alpha, 2, 2);
+    return IBRD_OK;
+  });
+}
+
+ibrd_status ibrd_spread(ibrd_grid g, const double* lam, double* out, int accumulate) {
+  return guarded(g, "ibrd_spread", [&]() {
+    if (!out || (g->blobs.n > 0 && !lam)) throw ArgError{IBRD_ERR_ARG, "null pointer"};
+    launch_spread<double>(g->blobs, g->d, lam, nullptr, inv_h3(g), out, accumulate, g->s);
+    return IBRD_OK;
+  });
+}
+
+ibrd_status ibrd_interp(ibrd_grid g, const double* c, double* out) {
+  return guarded(g, "ibrd_interp", [&]() {
+    if (!c || (g->blobs.n > 0 && !out)) throw ArgError{IBRD_ERR_ARG, "null pointer"};
+    launch_interp<double>(g->blobs, g->d, c, 1.0, out, g->s);
+    return IBRD_OK;
+  });
+}
+
+ibrd_status ibrd_solve_reaction(ibrd_grid g, const double* kappa, const double* rhs, double* c,
+                                const ibrd_solve_opts* opts, ibrd_solve_info* info) {
+  return guarded(g, "ibrd_solve_reaction", [&]() {
+    const double t0 = now_s();
+    const ibrd_solve_opts o = resolve_opts(g, opts);
+    const int N = g->blobs.n;
+    if (!rhs || !c || (N > 0 && !kappa)) throw ArgError{IBRD_ERR_ARG, "null pointer"};
+    g->vcycles = 0;
+    g->inner = 0;
+    ensure_nvec(g, o.schur_inner);
+    double sigma = g->alpha;
+    if (N > 0) {
+      IBRD_CUDA(cudaMemsetAsync(g->dflag, 0, sizeof(int), g->s));
+      k_check_rates<<<std::min(1024, (N + 255) / 256), 256, 0, g->s>>>(kappa, N, g->dflag);
+      check_launch("check_rates");
+      int flag = 0;
+      IBRD_CUDA(cudaMemcpyAsync(&flag, g->dflag, sizeof(int), cudaMemcpyDeviceToHost, g->s));
+      launch_sum<double>(kappa, N, g->partial, g->scal + S_TMP, 1.0, g->s);
+      const double ksum = host_scalar(g, S_TMP);
+      if (flag) throw ArgError{IBRD_ERR_NONFINITE, "kappa must be finite and >= 0"};
+      if (g->alpha == 0.0) sigma = ksum / ((double)g->d.n() * g->h * g->h * g->h);
+    }
+    if (!(sigma > 0.0)) throw ArgError{IBRD_ERR_ARG, "steady reaction system needs some kappa > 0"};
+    SolveResult R;
+    if (o.precision == IBRD_FP64) {
+      ReactionOp<double> op(g, kappa, sigma, o);
+      R = fgmres(g, op, rhs, c, g->d.n(), o, !o.use_guess, info);
+    } else {
+      ReactionOp<float> op(g, kappa, sigma, o);
+      R = fgmres(g, op, rhs, c, g->d.n(), o, !o.use_guess, info);
+    }
+    report(g, c, nullptr, kappa, info);
+    fill_info(info, R, g, t0);
+    if (R.st != IBRD_OK) g->err = std::string("ibrd_solve_reaction: ") + ibrd_status_string(R.st);
+    return R.st;
+  });
+}
+
+ibrd_status ibrd_solve_saddle(ibrd_grid g, const double* rhs, const double* f, double* c, double* lambda,
+                              const ibrd_solve_opts* opts, ibrd_solve_info* info) {
+  return guarded(g, "ibrd_solve_saddle", [&]() {
+    const double t0 = now_s();
+    const ibrd_solve_opts o = resolve_opts(g, opts);
+    const int N = g->blobs.n;
+    if (N < 1) throw ArgError{IBRD_ERR_STATE, "saddle solve needs at least one blob"};
+    if (!rhs || !c || !lambda) throw ArgError{IBRD_ERR_ARG, "null pointer"};
+    g->vcycles = 0;
+    g->inner = 0;
+    ensure_nvec(g, o.schur_inner);
+    const size_t nc = g->d.n();
+    const size_t n = nc + N;
+    if (g->xs_cap < n) {
+      cudaFree(g->xs);
+      cudaFree(g->bs);
+      g->xs = g->bs = nullptr;
+      g->xs = dalloc<double>(n);
+      g->bs = dalloc<double>(n);
+      g->xs_cap = n;
+    }
+    IBRD_CUDA(cudaMemcpyAsync(g->bs, rhs, sizeof(double) * nc, cudaMemcpyDeviceToDevice, g->s));
+    if (f)
+      IBRD_CUDA(cudaMemcpyAsync(g->bs + nc, f, sizeof(double) * N, cudaMemcpyDeviceToDevice, g->s));
+    else
+      IBRD_CUDA(cudaMemsetAsync(g->bs + nc, 0, sizeof(double) * N, g->s));
+    if (o.use_guess) {
+      IBRD_CUDA(cudaMemcpyAsync(g->xs, c, sizeof(double) * nc, cudaMemcpyDeviceToDevice, g->s));
+      IBRD_CUDA(cudaMemcpyAsync(g->xs + nc, lambda, sizeof(double) * N, cudaMemcpyDeviceToDevice, g->s));
+    }
+    if (o.precond == IBRD_PRECOND_DIAG && !g->gamma_valid) {
+      g->gamma_diag = compute_gamma(g, o);
+      g->gamma_valid = true;
+      g->vcycles = 0;
+    }
+    SolveResult R;
+    if (o.precision == IBRD_FP64) {
+      SaddleOp<double> op(g, o, o.zeta, o.xi);
+      R = fgmres(g, op, g->bs, g->xs, n, o, !o.use_guess, info);
+    } else {
+      SaddleOp<float> op(g, o, o.zeta, o.xi);
+      R = fgmres(g, op, g->bs, g->xs, n, o, !o.use_guess, info);
+    }
+    IBRD_CUDA(cudaMemcpyAsync(c, g->xs, sizeof(double) * nc, cudaMemcpyDeviceToDevice, g->s));
+    IBRD_CUDA(cudaMemcpyAsync(lambda, g->xs + nc, sizeof(double) * N, cudaMemcpyDeviceToDevice, g->s));
+    report(g, c, lambda, nullptr, info);
+    fill_info(info, R, g, t0);
+    if (R.st != IBRD_OK) g->err = std::string("ibrd_solve_saddle: ") + ibrd_status_string(R.st);
+    return R.st;
+  });
+}
+
+}  // extern "C"

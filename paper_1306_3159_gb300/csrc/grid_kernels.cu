@@ -1,0 +1,440 @@
+// Grid kernels: 7-point periodic Helmholtz operator (Sec. III.A, Eq. Helmholtz),
+// the multigrid pieces of the V-cycle (Sec. III.E: red-black Gauss-Seidel,
+// 8-cell-mean restriction, trilinear cell-centred prolongation, exact
+// coarsest solve) and streaming vector kernels (reductions, conversions).
+//
+// Layout: fields are [nz][ny][nx], x fastest, periodic in every direction.
+// FP64 arithmetic on GB300 is bound by the FP64 pipe (about 0.6 T FMA/s), so
+// the FP64 kernels minimise FP64 instructions per cell; the FP32 kernels are
+// bound by HBM and keep one read of each input and one write per output.
+#include <cmath>
+
+#include "internal.h"
+
+namespace ibrd {
+namespace {
+
+constexpr int BX = 32, BY = 8, ZCH = 16;
+
+__device__ __forceinline__ int wrap_dec(int i, int n) { return i == 0 ? n - 1 : i - 1; }
+__device__ __forceinline__ int wrap_inc(int i, int n) { return i == n - 1 ? 0 : i + 1; }
+
+template <typename T>
+__device__ __forceinline__ T bval(const T* __restrict__ b, size_t p, const double* __restrict__ bshift) {
+  return bshift ? b[p] - (T)(*bshift) : b[p];
+}
+
+// y = A x (RESID = false) or y = b - A x (RESID = true); 2.5D z-march with the
+// z-neighbours kept in registers and x/y neighbours served by L1.
+template <typename T, bool RESID>
+__global__ void __launch_bounds__(BX* BY) k_apply(const T* __restrict__ x, const T* __restrict__ b,
+                                                  T* __restrict__ y, int nx, int ny, int nz, T diag, T off) {
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y;
+  if (i >= nx || j >= ny) return;
+  const int k0 = blockIdx.z * ZCH;
+  const int k1 = min(k0 + ZCH, nz);
+  const int im = wrap_dec(i, nx), ip = wrap_inc(i, nx);
+  const size_t plane = (size_t)nx * ny;
+  const size_t rj = (size_t)j * nx, rjm = (size_t)wrap_dec(j, ny) * nx, rjp = (size_t)wrap_inc(j, ny) * nx;
+  T xm = x[(size_t)wrap_dec(k0, nz) * plane + rj + i];
+  T x0 = x[(size_t)k0 * plane + rj + i];
+  for (int k = k0; k < k1; ++k) {
+    const size_t base = (size_t)k * plane;
+    const T xp = x[(size_t)wrap_inc(k, nz) * plane + rj + i];
+    const T s = ((x[base + rj + im] + x[base + rj + ip]) + (x[base + rjm + i] + x[base + rjp + i])) + (xm + xp);
+    const T v = diag * x0 - off * s;
+    if (RESID)
+      y[base + rj + i] = b[base + rj + i] - v;
+    else
+      y[base + rj + i] = v;
+    xm = x0;
+    x0 = xp;
+  }
+}
+
+// Red-black Gauss-Seidel half sweep. Each thread owns an x-pair (2p, 2p+1)
+// of a row and marches in z; at plane k exactly one cell of the pair has the
+// active colour. Requires even nx, ny, nz (true on every smoothed level).
+template <typename T>
+__global__ void __launch_bounds__(BX* BY) k_rbgs(T* __restrict__ x, const T* __restrict__ b,
+                                                 const double* __restrict__ bshift, int nx, int ny, int nz,
+                                                 T inv_diag, T off, int colour) {
+  const int p = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y;
+  const int np = nx >> 1;
+  if (p >= np || j >= ny) return;
+  const int k0 = blockIdx.z * ZCH;
+  const int k1 = min(k0 + ZCH, nz);
+  const size_t plane = (size_t)nx * ny;
+  const size_t rj = (size_t)j * nx, rjm = (size_t)wrap_dec(j, ny) * nx, rjp = (size_t)wrap_inc(j, ny) * nx;
+  const T sh = bshift ? (T)(*bshift) : (T)0;
+  for (int k = k0; k < k1; ++k) {
+    const int par = (colour + j + k) & 1;
+    const int ia = 2 * p + par;
+    const int iw = wrap_dec(ia, nx), ie = wrap_inc(ia, nx);
+    const size_t base = (size_t)k * plane;
+    const T s = ((x[base + rj + iw] + x[base + rj + ie]) + (x[base + rjm + ia] + x[base + rjp + ia])) +
+                (x[(size_t)wrap_dec(k, nz) * plane + rj + ia] + x[(size_t)wrap_inc(k, nz) * plane + rj + ia]);
+    x[base + rj + ia] = ((b[base + rj + ia] - sh) + off * s) * inv_diag;
+  }
+}
+
+// First red half sweep from x = 0: red cells (b - shift)/diag, black cells 0.
+template <typename T>
+__global__ void k_rbgs_zero(T* __restrict__ x, const T* __restrict__ b, const double* __restrict__ bshift,
+                            int nx, int ny, int nz, T inv_diag) {
+  const size_t n = (size_t)nx * ny * nz;
+  const T sh = bshift ? (T)(*bshift) : (T)0;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(q % nx);
+    const size_t r = q / nx;
+    const int j = (int)(r % ny);
+    const int k = (int)(r / ny);
+    x[q] = ((i + j + k) & 1) ? (T)0 : (b[q] - sh) * inv_diag;
+  }
+}
+
+// Coarse cell (I, J, K) receives the mean of the residual b - shift - A x over
+// its 8 fine children.
+template <typename T>
+__global__ void k_residual_restrict(const T* __restrict__ x, const T* __restrict__ b,
+                                    const double* __restrict__ bshift, T* __restrict__ bc, int nx, int ny,
+                                    int nz, T diag, T off) {
+  const int nxc = nx >> 1, nyc = ny >> 1, nzc = nz >> 1;
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y * blockDim.y + threadIdx.y;
+  const int K = blockIdx.z * blockDim.z + threadIdx.z;
+  if (I >= nxc || J >= nyc || K >= nzc) return;
+  const size_t plane = (size_t)nx * ny;
+  const T sh = bshift ? (T)(*bshift) : (T)0;
+  T acc = 0;
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const int k = 2 * K + c;
+    const size_t pk = (size_t)k * plane, pkm = (size_t)wrap_dec(k, nz) * plane, pkp = (size_t)wrap_inc(k, nz) * plane;
+#pragma unroll
+    for (int bb = 0; bb < 2; ++bb) {
+      const int j = 2 * J + bb;
+      const size_t rj = (size_t)j * nx, rjm = (size_t)wrap_dec(j, ny) * nx, rjp = (size_t)wrap_inc(j, ny) * nx;
+#pragma unroll
+      for (int a = 0; a < 2; ++a) {
+        const int i = 2 * I + a;
+        const T s = ((x[pk + rj + wrap_dec(i, nx)] + x[pk + rj + wrap_inc(i, nx)]) +
+                     (x[pk + rjm + i] + x[pk + rjp + i])) +
+                    (x[pkm + rj + i] + x[pkp + rj + i]);
+        acc += (b[pk + rj + i] - sh) - (diag * x[pk + rj + i] - off * s);
+      }
+    }
+  }
+  bc[((size_t)K * nyc + J) * nxc + I] = acc * (T)0.125;
+}
+
+// x_fine += trilinear cell-centred interpolation of the coarse correction.
+template <typename T>
+__global__ void k_prolong_add(const T* __restrict__ xc, T* __restrict__ x, int nx, int ny, int nz) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z * blockDim.z + threadIdx.z;
+  if (i >= nx || j >= ny || k >= nz) return;
+  const int nxc = nx >> 1, nyc = ny >> 1, nzc = nz >> 1;
+  const int I = i >> 1, J = j >> 1, K = k >> 1;
+  const int I2 = (i & 1) ? wrap_inc(I, nxc) : wrap_dec(I, nxc);
+  const int J2 = (j & 1) ? wrap_inc(J, nyc) : wrap_dec(J, nyc);
+  const int K2 = (k & 1) ? wrap_inc(K, nzc) : wrap_dec(K, nzc);
+  const size_t pc = (size_t)nxc * nyc;
+  const size_t zA = (size_t)K * pc, zB = (size_t)K2 * pc;
+  const size_t yA = (size_t)J * nxc, yB = (size_t)J2 * nxc;
+  const T w3 = (T)0.75, w1 = (T)0.25;
+  const T rAA = w3 * xc[zA + yA + I] + w1 * xc[zA + yA + I2];
+  const T rAB = w3 * xc[zA + yB + I] + w1 * xc[zA + yB + I2];
+  const T rBA = w3 * xc[zB + yA + I] + w1 * xc[zB + yA + I2];
+  const T rBB = w3 * xc[zB + yB + I] + w1 * xc[zB + yB + I2];
+  const T pA = w3 * rAA + w1 * rAB;
+  const T pB = w3 * rBA + w1 * rBB;
+  x[((size_t)k * ny + j) * nx + i] += w3 * pA + w1 * pB;
+}
+
+// Dense circulant solve on the coarsest grid (at most 512 cells, one block).
+template <typename T>
+__global__ void k_coarse_solve(const T* __restrict__ table, const T* __restrict__ b, T* __restrict__ x, int nx,
+                               int ny, int nz) {
+  __shared__ T sb[512];
+  const int n = nx * ny * nz;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) sb[t] = b[t];
+  __syncthreads();
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    const int ix = t % nx, iy = (t / nx) % ny, iz = t / (nx * ny);
+    T acc = 0;
+    for (int u = 0; u < n; ++u) {
+      const int jx = u % nx, jy = (u / nx) % ny, jz = u / (nx * ny);
+      const int dx = ix - jx + (ix < jx ? nx : 0);
+      const int dy = iy - jy + (iy < jy ? ny : 0);
+      const int dz = iz - jz + (iz < jz ? nz : 0);
+      acc += table[(dz * ny + dy) * nx + dx] * sb[u];
+    }
+    x[t] = acc;
+  }
+}
+
+template <typename T>
+__global__ void k_coarse_table(T* __restrict__ table, int nx, int ny, int nz, double diag, double off,
+                               int singular) {
+  const int n = nx * ny * nz;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int dx = t % nx, dy = (t / nx) % ny, dz = t / (nx * ny);
+  const double twopi = 6.283185307179586476925286766559;
+  // eigenvalue of diag I - off * (sum of 6 shifts): diag - 2 off sum_d cos(2 pi k_d / n_d)
+  double acc = 0.0;
+  for (int u = 0; u < n; ++u) {
+    if (singular && u == 0) continue;
+    const int kx = u % nx, ky = (u / nx) % ny, kz = u / (nx * ny);
+    const double lam = diag - 2.0 * off * (cos(twopi * kx / nx) + cos(twopi * ky / ny) + cos(twopi * kz / nz));
+    const double ph = twopi * ((double)kx * dx / nx + (double)ky * dy / ny + (double)kz * dz / nz);
+    acc += cos(ph) / lam;
+  }
+  table[t] = (T)(acc / n);
+}
+
+// ---------------------------------------------------------------- reductions
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block sum of v (blockDim.x == kRedThreads); result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double sw[32];
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sw[wid] = v;
+  __syncthreads();
+  v = (threadIdx.x < (blockDim.x >> 5)) ? sw[threadIdx.x] : 0.0;
+  if (wid == 0) v = warp_sum(v);
+  __syncthreads();
+  return v;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) k_sum_partial(const T* __restrict__ x, size_t n,
+                                                             double* __restrict__ partial) {
+  double acc = 0.0;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (sizeof(T) == 4) {
+    // FP32 input: sum runs of 16 strided values in FP32, fold into FP64.
+    while (i < n) {
+      float f = 0.f;
+#pragma unroll 4
+      for (int r = 0; r < 16 && i < n; ++r, i += stride) f += (float)x[i];
+      acc += (double)f;
+    }
+  } else {
+    for (; i < n; i += stride) acc += (double)x[i];
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_dot_partial(const double* __restrict__ x,
+                                                             const double* __restrict__ y, size_t n,
+                                                             double* __restrict__ partial) {
+  double acc = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    acc = fma(x[i], y[i], acc);
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_finalize(const double* __restrict__ partial, int np,
+                                                          double* __restrict__ out, double scale) {
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) acc += partial[i];
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) *out = acc * scale;
+}
+
+template <typename T>
+__global__ void k_sub_scalar(T* __restrict__ x, size_t n, const double* __restrict__ m) {
+  const T v = (T)(*m);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    x[i] -= v;
+}
+
+template <typename Tx, typename Ty>
+__global__ void k_convert(const Tx* __restrict__ x, Ty* __restrict__ y, size_t n, double a,
+                          const double* __restrict__ shift) {
+  const double sh = shift ? *shift : 0.0;
+  if (a == 1.0 && sh == 0.0) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+      y[i] = (Ty)x[i];
+  } else if (sizeof(Ty) == 4 && sizeof(Tx) == 4) {
+    const float af = (float)a, sf = (float)sh;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+      y[i] = (Ty)(af * (float)x[i] + sf);
+  } else {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+      y[i] = (Ty)(a * (double)x[i] + sh);
+  }
+}
+
+__global__ void k_axpby(double a, const double* __restrict__ x, double b, double* __restrict__ y, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    y[i] = (b == 0.0) ? a * x[i] : fma(a, x[i], b * y[i]);
+}
+
+__global__ void k_scale_by_inv(const double* __restrict__ x, double* __restrict__ y, size_t n,
+                               const double* __restrict__ den, double num) {
+  __shared__ double f;
+  if (threadIdx.x == 0) f = num / *den;
+  __syncthreads();
+  const double ff = f;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    y[i] = x[i] * ff;
+}
+
+template <typename T>
+__global__ void k_nonfinite(const T* __restrict__ x, size_t n, int* __restrict__ flag) {
+  int bad = 0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    bad |= !isfinite(x[i]);
+  bad = __syncthreads_or(bad);
+  if (bad && threadIdx.x == 0) atomicOr(flag, 1);
+}
+
+inline int stream_blocks(size_t n, int threads) {
+  size_t b = (n + threads - 1) / threads;
+  const size_t cap = 152 * 16;
+  return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- launchers
+template <typename T>
+void launch_apply_A(const T* x, T* y, Dims d, Stencil st, cudaStream_t s) {
+  dim3 g((d.nx + BX - 1) / BX, (d.ny + BY - 1) / BY, (d.nz + ZCH - 1) / ZCH);
+  k_apply<T, false><<<g, dim3(BX, BY), 0, s>>>(x, nullptr, y, d.nx, d.ny, d.nz, (T)st.diag, (T)st.off);
+  check_launch("apply_A");
+}
+
+template <typename T>
+void launch_residual(const T* x, const T* b, T* y, Dims d, Stencil st, cudaStream_t s) {
+  dim3 g((d.nx + BX - 1) / BX, (d.ny + BY - 1) / BY, (d.nz + ZCH - 1) / ZCH);
+  k_apply<T, true><<<g, dim3(BX, BY), 0, s>>>(x, b, y, d.nx, d.ny, d.nz, (T)st.diag, (T)st.off);
+  check_launch("residual");
+}
+
+template <typename T>
+void launch_rbgs(T* x, const T* b, const double* bshift, Dims d, Stencil st, int colour, cudaStream_t s) {
+  const int np = d.nx / 2;
+  dim3 g((np + BX - 1) / BX, (d.ny + BY - 1) / BY, (d.nz + ZCH - 1) / ZCH);
+  k_rbgs<T><<<g, dim3(BX, BY), 0, s>>>(x, b, bshift, d.nx, d.ny, d.nz, (T)(1.0 / st.diag), (T)st.off, colour);
+  check_launch("rbgs");
+}
+
+template <typename T>
+void launch_rbgs_zero(T* x, const T* b, const double* bshift, Dims d, Stencil st, cudaStream_t s) {
+  k_rbgs_zero<T><<<stream_blocks(d.n(), 256), 256, 0, s>>>(x, b, bshift, d.nx, d.ny, d.nz, (T)(1.0 / st.diag));
+  check_launch("rbgs_zero");
+}
+
+template <typename T>
+void launch_residual_restrict(const T* x, const T* b, const double* bshift, T* bc, Dims d, Stencil st,
+                              cudaStream_t s) {
+  const int nxc = d.nx / 2, nyc = d.ny / 2, nzc = d.nz / 2;
+  dim3 blk(nxc >= 32 ? 32 : nxc, 4, 2);
+  dim3 g((nxc + blk.x - 1) / blk.x, (nyc + blk.y - 1) / blk.y, (nzc + blk.z - 1) / blk.z);
+  k_residual_restrict<T><<<g, blk, 0, s>>>(x, b, bshift, bc, d.nx, d.ny, d.nz, (T)st.diag, (T)st.off);
+  check_launch("residual_restrict");
+}
+
+template <typename T>
+void launch_prolong_add(const T* xc, T* x, Dims d, cudaStream_t s) {
+  dim3 blk(d.nx >= 64 ? 64 : d.nx, 2, 2);
+  dim3 g((d.nx + blk.x - 1) / blk.x, (d.ny + blk.y - 1) / blk.y, (d.nz + blk.z - 1) / blk.z);
+  k_prolong_add<T><<<g, blk, 0, s>>>(xc, x, d.nx, d.ny, d.nz);
+  check_launch("prolong_add");
+}
+
+template <typename T>
+void launch_coarse_solve(const T* table, const T* b, T* x, Dims dc, cudaStream_t s) {
+  k_coarse_solve<T><<<1, 256, 0, s>>>(table, b, x, dc.nx, dc.ny, dc.nz);
+  check_launch("coarse_solve");
+}
+
+template <typename T>
+void launch_coarse_table(T* table, Dims dc, Stencil st, int singular, cudaStream_t s) {
+  const int n = (int)dc.n();
+  k_coarse_table<T><<<(n + 127) / 128, 128, 0, s>>>(table, dc.nx, dc.ny, dc.nz, st.diag, st.off, singular);
+  check_launch("coarse_table");
+}
+
+template <typename T>
+void launch_sum(const T* x, size_t n, double* partial, double* out, double scale, cudaStream_t s) {
+  k_sum_partial<T><<<kRedBlocks, kRedThreads, 0, s>>>(x, n, partial);
+  check_launch("sum_partial");
+  k_finalize<<<1, kRedThreads, 0, s>>>(partial, kRedBlocks, out, scale);
+  check_launch("finalize");
+}
+
+void launch_dot(const double* x, const double* y, size_t n, double* partial, double* out, double scale,
+                cudaStream_t s) {
+  k_dot_partial<<<kRedBlocks, kRedThreads, 0, s>>>(x, y, n, partial);
+  check_launch("dot_partial");
+  k_finalize<<<1, kRedThreads, 0, s>>>(partial, kRedBlocks, out, scale);
+  check_launch("finalize");
+}
+
+template <typename T>
+void launch_sub_scalar(T* x, size_t n, const double* mean, cudaStream_t s) {
+  k_sub_scalar<T><<<stream_blocks(n, 256), 256, 0, s>>>(x, n, mean);
+  check_launch("sub_scalar");
+}
+
+template <typename Tx, typename Ty>
+void launch_convert(const Tx* x, Ty* y, size_t n, double a, const double* shift, cudaStream_t s) {
+  k_convert<Tx, Ty><<<stream_blocks(n, 256), 256, 0, s>>>(x, y, n, a, shift);
+  check_launch("convert");
+}
+
+void launch_axpby(double a, const double* x, double b, double* y, size_t n, cudaStream_t s) {
+  k_axpby<<<stream_blocks(n, 256), 256, 0, s>>>(a, x, b, y, n);
+  check_launch("axpby");
+}
+
+void launch_scale_by_inv(const double* x, double* y, size_t n, const double* den, double num, cudaStream_t s) {
+  k_scale_by_inv<<<stream_blocks(n, 256), 256, 0, s>>>(x, y, n, den, num);
+  check_launch("scale_by_inv");
+}
+
+template <typename T>
+void launch_nonfinite(const T* x, size_t n, int* flag, cudaStream_t s) {
+  k_nonfinite<T><<<stream_blocks(n, 256), 256, 0, s>>>(x, n, flag);
+  check_launch("nonfinite");
+}
+
+#define IBRD_INST(T)                                                                                   \
+  template void launch_apply_A<T>(const T*, T*, Dims, Stencil, cudaStream_t);                         \
+  template void launch_residual<T>(const T*, const T*, T*, Dims, Stencil, cudaStream_t);              \
+  template void launch_rbgs<T>(T*, const T*, const double*, Dims, Stencil, int, cudaStream_t);        \
+  template void launch_rbgs_zero<T>(T*, const T*, const double*, Dims, Stencil, cudaStream_t);        \
+  template void launch_residual_restrict<T>(const T*, const T*, const double*, T*, Dims, Stencil,     \
+                                            cudaStream_t);                                            \
+  template void launch_prolong_add<T>(const T*, T*, Dims, cudaStream_t);                             \
+  template void launch_coarse_solve<T>(const T*, const T*, T*, Dims, cudaStream_t);                   \
+  template void launch_coarse_table<T>(T*, Dims, Stencil, int, cudaStream_t);                         \
+  template void launch_sum<T>(const T*, size_t, double*, double*, double, cudaStream_t);              \
+  template void launch_sub_scalar<T>(T*, size_t, const double*, cudaStream_t);                        \
+  template void launch_nonfinite<T>(const T*, size_t, int*, cudaStream_t);
+IBRD_INST(double)
+IBRD_INST(float)
+#undef IBRD_INST
+template void launch_convert<double, float>(const double*, float*, size_t, double, const double*, cudaStream_t);
+template void launch_convert<float, double>(const float*, double*, size_t, double, const double*, cudaStream_t);
+template void launch_convert<double, double>(const double*, double*, size_t, double, const double*, cudaStream_t);
+template void launch_convert<float, float>(const float*, float*, size_t, double, const double*, cudaStream_t);
+
+}  // namespace ibrd

@@ -1,0 +1,169 @@
+// Internal declarations shared by the CUDA translation units of libibrd.
+// Not part of the public ABI (include/ibrd.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/ibrd.h"
+
+namespace ibrd {
+
+// ---------------------------------------------------------------- errors
+struct CudaError {
+  cudaError_t code;
+  const char* what;
+};
+
+#define IBRD_CUDA(call)                                         \
+  do {                                                          \
+    cudaError_t e_ = (call);                                    \
+    if (e_ != cudaSuccess) throw ::ibrd::CudaError{e_, #call};  \
+  } while (0)
+
+// Check the last launch (asynchronous errors surface at the next sync).
+inline void check_launch(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) throw CudaError{e, what};
+}
+
+// ---------------------------------------------------------------- geometry
+struct Dims {
+  int nx, ny, nz;
+  size_t n() const { return (size_t)nx * ny * nz; }
+};
+
+// Coefficients of A_l = alpha I - chi L_{h_l}: diag = alpha + 6 chi/h^2,
+// off = chi/h^2, so (A x)_k = diag x_k - off * sum_{6 neighbours} x.
+struct Stencil {
+  double diag, off;
+};
+
+// ---------------------------------------------------------------- reductions
+// Deterministic two-stage reductions use a fixed grid of kRedBlocks blocks.
+constexpr int kRedBlocks = 608;   // 4 x 152 SMs
+constexpr int kRedThreads = 256;
+
+// ---------------------------------------------------------------- grid kernels
+// All launchers enqueue on `s` and check the launch.
+template <typename T>
+void launch_apply_A(const T* x, T* y, Dims d, Stencil st, cudaStream_t s);
+// y = b - A x
+template <typename T>
+void launch_residual(const T* x, const T* b, T* y, Dims d, Stencil st, cudaStream_t s);
+// Red-black Gauss-Seidel half sweep on `colour` (0 = red: (i+j+k) even).
+// bshift (nullable, device scalar): uses b - *bshift in place of b.
+template <typename T>
+void launch_rbgs(T* x, const T* b, const double* bshift, Dims d, Stencil st, int colour, cudaStream_t s);
+// First red half sweep from a zero guess: x_red = (b - shift)/diag, x_black = 0.
+template <typename T>
+void launch_rbgs_zero(T* x, const T* b, const double* bshift, Dims d, Stencil st, cudaStream_t s);
+// bc = mean over 8 children of (b - shift - A x) on the fine grid d.
+template <typename T>
+void launch_residual_restrict(const T* x, const T* b, const double* bshift, T* bc, Dims d,
+                              Stencil st, cudaStream_t s);
+// x (fine, dims d) += trilinear prolongation of xc (coarse dims d/2).
+template <typename T>
+void launch_prolong_add(const T* xc, T* x, Dims d, cudaStream_t s);
+// Coarsest exact solve x = G b with the circulant table G (dc.n() entries).
+template <typename T>
+void launch_coarse_solve(const T* table, const T* b, T* x, Dims dc, cudaStream_t s);
+// table(d) = sum_{k} cos(2 pi k.d / n) / (n lambda_k), lambda_k eigenvalues of
+// A_c; the k = 0 mode is dropped when singular != 0.
+template <typename T>
+void launch_coarse_table(T* table, Dims dc, Stencil st, int singular, cudaStream_t s);
+
+// ---------------------------------------------------------------- vector kernels
+// Sum of x[0..n) into partials (kRedBlocks doubles); then finalize into *out.
+template <typename T>
+void launch_sum(const T* x, size_t n, double* partial, double* out, double scale, cudaStream_t s);
+// out[0] = scale * sum(x*y)
+void launch_dot(const double* x, const double* y, size_t n, double* partial, double* out, double scale,
+                cudaStream_t s);
+// x[i] -= *mean (device scalar)
+template <typename T>
+void launch_sub_scalar(T* x, size_t n, const double* mean, cudaStream_t s);
+// y = (Ty)(a * x + shift), shift from device scalar (nullable)
+template <typename Tx, typename Ty>
+void launch_convert(const Tx* x, Ty* y, size_t n, double a, const double* shift, cudaStream_t s);
+// y = a x + b y (host scalars)
+void launch_axpby(double a, const double* x, double b, double* y, size_t n, cudaStream_t s);
+// y = x * (num / *den)  (device scalar den, host num)
+void launch_scale_by_inv(const double* x, double* y, size_t n, const double* den, double num, cudaStream_t s);
+// flag = any non-finite in x (writes 1 into *flag if so; *flag must start 0)
+template <typename T>
+void launch_nonfinite(const T* x, size_t n, int* flag, cudaStream_t s);
+
+// ---------------------------------------------------------------- blob kernels
+constexpr int kTile = 8;  // spreading tile edge (cells)
+
+struct BlobSet {
+  int n = 0;
+  int cap = 0;
+  int width = 4;             // kernel width w (3 or 4)
+  double* q = nullptr;       // N x 3 wrapped positions
+  int* idx = nullptr;        // N x 3 x 4 wrapped cell indices (axis-major)
+  double* w64 = nullptr;     // N x 3 x 4 weights
+  float* w32 = nullptr;      // FP32 copy
+  // tile binning
+  int ntx = 0, nty = 0, ntz = 0, ntiles = 0;
+  int* tile_count = nullptr;   // ntiles
+  int* tile_offset = nullptr;  // ntiles + 1
+  int* tile_cursor = nullptr;  // ntiles
+  int* tile_blobs = nullptr;   // pairs (blob index per (tile, blob) pair)
+  int pair_cap = 0;
+  int* active = nullptr;       // active tile ids (ntiles capacity)
+  int n_active = 0;
+  int* d_meta = nullptr;       // [0] = pairs, [1] = active tiles
+};
+
+void blobs_setup(BlobSet& b, Dims d, double h, const double* q_in, int n, cudaStream_t s);
+// out (+)= scale * sum_b coef_b lam_b phi_b  (coef nullable = 1);
+// lam, coef FP64 device N-vectors; out field of type T.
+template <typename T>
+void launch_spread(const BlobSet& b, Dims d, const double* lam, const double* coef, double scale, T* out,
+                   int accumulate, cudaStream_t s);
+// Spread a constant *cval (device scalar) times scale to all blobs.
+template <typename T>
+void launch_spread_const(const BlobSet& b, Dims d, const double* cval, double scale, T* out, cudaStream_t s);
+// out[b] = scale * (J x)_b  (FP64 output)
+template <typename T>
+void launch_interp(const BlobSet& b, Dims d, const T* x, double scale, double* out, cudaStream_t s);
+
+// ---------------------------------------------------------------- Krylov kernels
+constexpr int kDotGroup = 8;
+// partial[g * kRedBlocks + blk] for g < nvec (nvec <= kDotGroup)
+void launch_multidot(const double* V, size_t ldv, int nvec, const double* w, size_t n, double* partial,
+                     cudaStream_t s);
+// out[g] = sum_blk partial[g*kRedBlocks + blk]   (g < nvec)
+void launch_reduce_partials(const double* partial, int nvec, double* out, cudaStream_t s);
+// w += sign * sum_g coef[g] V[g]; optional partial sums of squares of new w.
+void launch_multi_axpy(double* w, const double* V, size_t ldv, int nvec, const double* coef, double sign,
+                       size_t n, double* partial_sq, cudaStream_t s);
+// Givens step j on column H[:, j] (ldh = restart + 1): rotations cs/sn,
+// residual vector gvec; writes |gvec[j+1]| to *res.
+void launch_givens(double* H, int ldh, int j, double* cs, double* sn, double* gvec, double* res,
+                   cudaStream_t s);
+// Back substitution y = R^{-1} g for the leading k x k block.
+void launch_backsolve(const double* H, int ldh, int k, const double* gvec, double* y, cudaStream_t s);
+// Combine two dot results: h[i] += h2[i] for i < n (device).
+void launch_vec_add_small(double* h, const double* h2, int n, cudaStream_t s);
+// *dst = sqrt(*src)
+void launch_sqrt_scalar(const double* src, double* dst, cudaStream_t s);
+
+// Small-vector (length N) GMRES for the approximate Schur complement: one
+// block does the Arnoldi step on U (rows of length n, ldu) with small
+// Hessenberg Hs (ldh = m + 1), including Givens rotations.
+// Step j: w (= U[j+1]) orthogonalized against U[0..j] by MGS, normalized.
+void launch_small_arnoldi(double* U, int n, int j, double* Hs, int ldh, double* cs, double* sn,
+                          double* gvec, cudaStream_t s);
+// U[0] = r / ||r||, gvec = [||r||, 0, ...] (r may alias U[0])
+void launch_small_start(const double* r, double* U0, int n, double* gvec, int m, cudaStream_t s);
+// x = U[0..k) y where y = R^{-1} g (solved inside); subtract mean if project.
+void launch_small_finish(const double* U, int n, int k, const double* Hs, int ldh, const double* gvec,
+                         double* x, int project_mean, cudaStream_t s);
+
+}  // namespace ibrd

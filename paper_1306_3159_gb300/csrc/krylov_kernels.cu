@@ -1,0 +1,310 @@
+// Krylov kernels for flexible GMRES (Sec. III.E: "FGMRES" outer solver) and
+// the small inner GMRES of the approximate Schur-complement preconditioner
+// (Appendix A, step 2b).
+//
+// Outer vectors live on the grid (plus the N blob unknowns for the saddle
+// point) and are FP64. Orthogonalisation is classical Gram-Schmidt with a
+// conditional second pass, done as fused multi-dot / multi-axpy streams over
+// up to 8 basis vectors at a time with deterministic two-stage reductions.
+// The Hessenberg matrix, Givens rotations and the least-squares update stay on
+// the device; the host only reads the residual estimate.
+#include <cmath>
+
+#include "internal.h"
+
+namespace ibrd {
+namespace {
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block sum, result valid in thread 0 of the block. Safe to call repeatedly.
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double sw[32];
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sw[wid] = v;
+  __syncthreads();
+  v = (threadIdx.x < (blockDim.x >> 5)) ? sw[threadIdx.x] : 0.0;
+  if (wid == 0) v = warp_sum(v);
+  return v;
+}
+
+// Block sum broadcast to all threads.
+__device__ __forceinline__ double block_sum_all(double v) {
+  __shared__ double s_res;
+  v = block_sum(v);
+  if (threadIdx.x == 0) s_res = v;
+  __syncthreads();
+  const double r = s_res;
+  __syncthreads();
+  return r;
+}
+
+template <int NV>
+__global__ void __launch_bounds__(kRedThreads) k_multidot(const double* __restrict__ V, size_t ldv,
+                                                          const double* __restrict__ w, size_t n,
+                                                          double* __restrict__ partial) {
+  double acc[NV];
+#pragma unroll
+  for (int g = 0; g < NV; ++g) acc[g] = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double wi = w[i];
+#pragma unroll
+    for (int g = 0; g < NV; ++g) acc[g] = fma(V[g * ldv + i], wi, acc[g]);
+  }
+#pragma unroll
+  for (int g = 0; g < NV; ++g) {
+    const double s = block_sum(acc[g]);
+    if (threadIdx.x == 0) partial[g * kRedBlocks + blockIdx.x] = s;
+  }
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_reduce_partials(const double* __restrict__ partial,
+                                                                 double* __restrict__ out) {
+  // blockIdx.x = vector g
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < kRedBlocks; i += blockDim.x) acc += partial[blockIdx.x * kRedBlocks + i];
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) out[blockIdx.x] = acc;
+}
+
+template <int NV, bool SQ>
+__global__ void __launch_bounds__(kRedThreads) k_multi_axpy(double* __restrict__ w, const double* __restrict__ V,
+                                                            size_t ldv, const double* __restrict__ coef,
+                                                            double sign, size_t n, double* __restrict__ partial_sq) {
+  double c[NV];
+#pragma unroll
+  for (int g = 0; g < NV; ++g) c[g] = sign * coef[g];
+  double sq = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    double wi = w[i];
+#pragma unroll
+    for (int g = 0; g < NV; ++g) wi = fma(c[g], V[g * ldv + i], wi);
+    w[i] = wi;
+    if (SQ) sq = fma(wi, wi, sq);
+  }
+  if (SQ) {
+    sq = block_sum(sq);
+    if (threadIdx.x == 0) partial_sq[blockIdx.x] = sq;
+  }
+}
+
+__global__ void k_givens(double* __restrict__ H, int ldh, int j, double* __restrict__ cs, double* __restrict__ sn,
+                         double* __restrict__ gvec, double* __restrict__ res) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double* h = H + (size_t)j * ldh;
+  for (int i = 0; i < j; ++i) {
+    const double t = cs[i] * h[i] + sn[i] * h[i + 1];
+    h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
+    h[i] = t;
+  }
+  const double a = h[j], b = h[j + 1];
+  const double r = hypot(a, b);
+  double c = 1.0, s = 0.0;
+  if (r > 0.0) {
+    c = a / r;
+    s = b / r;
+  }
+  h[j] = r;
+  h[j + 1] = 0.0;
+  cs[j] = c;
+  sn[j] = s;
+  const double gj = gvec[j];
+  gvec[j + 1] = -s * gj;
+  gvec[j] = c * gj;
+  *res = fabs(gvec[j + 1]);
+}
+
+__global__ void k_backsolve(const double* __restrict__ H, int ldh, int k, const double* __restrict__ gvec,
+                            double* __restrict__ y) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int i = k - 1; i >= 0; --i) {
+    double t = gvec[i];
+    for (int l = i + 1; l < k; ++l) t -= H[(size_t)l * ldh + i] * y[l];
+    const double d = H[(size_t)i * ldh + i];
+    y[i] = d != 0.0 ? t / d : 0.0;
+  }
+}
+
+__global__ void k_vec_add_small(double* __restrict__ h, const double* __restrict__ h2, int n) {
+  const int i = threadIdx.x;
+  if (i < n) h[i] += h2[i];
+}
+
+__global__ void k_sqrt_scalar(const double* __restrict__ src, double* __restrict__ dst) {
+  if (threadIdx.x == 0) *dst = sqrt(fmax(*src, 0.0));
+}
+
+// ---------------------------------------------------------------- small GMRES
+constexpr int kSmallThreads = 1024;
+
+__global__ void __launch_bounds__(kSmallThreads) k_small_start(const double* __restrict__ r, double* __restrict__ U0,
+                                                                int n, double* __restrict__ gvec, int m) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s = fma(r[i], r[i], s);
+  const double nrm = sqrt(block_sum_all(s));
+  const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) U0[i] = r[i] * inv;
+  if (threadIdx.x <= m) gvec[threadIdx.x] = (threadIdx.x == 0) ? nrm : 0.0;
+}
+
+// Arnoldi step j: w = U[j+1] holds (J A~^-1 S) U[j]; modified Gram-Schmidt
+// against U[0..j], normalise, then one Givens rotation.
+__global__ void __launch_bounds__(kSmallThreads) k_small_arnoldi(double* __restrict__ U, int n, int j,
+                                                                  double* __restrict__ Hs, int ldh,
+                                                                  double* __restrict__ cs, double* __restrict__ sn,
+                                                                  double* __restrict__ gvec) {
+  double* w = U + (size_t)(j + 1) * n;
+  double* h = Hs + (size_t)j * ldh;
+  for (int i = 0; i <= j; ++i) {
+    const double* u = U + (size_t)i * n;
+    double s = 0.0;
+    for (int t = threadIdx.x; t < n; t += blockDim.x) s = fma(u[t], w[t], s);
+    const double hij = block_sum_all(s);
+    for (int t = threadIdx.x; t < n; t += blockDim.x) w[t] -= hij * u[t];
+    if (threadIdx.x == 0) h[i] = hij;
+    __syncthreads();
+  }
+  double s = 0.0;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) s = fma(w[t], w[t], s);
+  const double nrm = sqrt(block_sum_all(s));
+  const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) w[t] *= inv;
+  if (threadIdx.x == 0) {
+    h[j + 1] = nrm;
+    for (int i = 0; i < j; ++i) {
+      const double tt = cs[i] * h[i] + sn[i] * h[i + 1];
+      h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
+      h[i] = tt;
+    }
+    const double a = h[j], b = h[j + 1];
+    const double r = hypot(a, b);
+    double c = 1.0, sg = 0.0;
+    if (r > 0.0) {
+      c = a / r;
+      sg = b / r;
+    }
+    h[j] = r;
+    h[j + 1] = 0.0;
+    cs[j] = c;
+    sn[j] = sg;
+    const double gj = gvec[j];
+    gvec[j + 1] = -sg * gj;
+    gvec[j] = c * gj;
+  }
+}
+
+__global__ void __launch_bounds__(kSmallThreads) k_small_finish(const double* __restrict__ U, int n, int k,
+                                                                 const double* __restrict__ Hs, int ldh,
+                                                                 const double* __restrict__ gvec,
+                                                                 double* __restrict__ x, int project_mean) {
+  __shared__ double y[64];
+  if (threadIdx.x == 0) {
+    for (int i = k - 1; i >= 0; --i) {
+      double t = gvec[i];
+      for (int l = i + 1; l < k; ++l) t -= Hs[(size_t)l * ldh + i] * y[l];
+      const double d = Hs[(size_t)i * ldh + i];
+      y[i] = d != 0.0 ? t / d : 0.0;
+    }
+  }
+  __syncthreads();
+  double s = 0.0;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    double v = 0.0;
+    for (int l = 0; l < k; ++l) v = fma(y[l], U[(size_t)l * n + t], v);
+    x[t] = v;
+    s += v;
+  }
+  if (project_mean) {
+    const double mean = block_sum_all(s) / n;
+    for (int t = threadIdx.x; t < n; t += blockDim.x) x[t] -= mean;
+  }
+}
+
+}  // namespace
+
+void launch_multidot(const double* V, size_t ldv, int nvec, const double* w, size_t n, double* partial,
+                     cudaStream_t s) {
+  switch (nvec) {
+#define IBRD_CASE(k) \
+  case k: k_multidot<k><<<kRedBlocks, kRedThreads, 0, s>>>(V, ldv, w, n, partial); break;
+    IBRD_CASE(1) IBRD_CASE(2) IBRD_CASE(3) IBRD_CASE(4) IBRD_CASE(5) IBRD_CASE(6) IBRD_CASE(7) IBRD_CASE(8)
+#undef IBRD_CASE
+    default: return;
+  }
+  check_launch("multidot");
+}
+
+void launch_reduce_partials(const double* partial, int nvec, double* out, cudaStream_t s) {
+  if (nvec <= 0) return;
+  k_reduce_partials<<<nvec, kRedThreads, 0, s>>>(partial, out);
+  check_launch("reduce_partials");
+}
+
+void launch_multi_axpy(double* w, const double* V, size_t ldv, int nvec, const double* coef, double sign, size_t n,
+                       double* partial_sq, cudaStream_t s) {
+  if (partial_sq) {
+    switch (nvec) {
+#define IBRD_CASE(k)                                                                                       \
+  case k:                                                                                                  \
+    k_multi_axpy<k, true><<<kRedBlocks, kRedThreads, 0, s>>>(w, V, ldv, coef, sign, n, partial_sq); break;
+      IBRD_CASE(1) IBRD_CASE(2) IBRD_CASE(3) IBRD_CASE(4) IBRD_CASE(5) IBRD_CASE(6) IBRD_CASE(7) IBRD_CASE(8)
+#undef IBRD_CASE
+      default: return;
+    }
+  } else {
+    switch (nvec) {
+#define IBRD_CASE(k)                                                                                        \
+  case k:                                                                                                   \
+    k_multi_axpy<k, false><<<kRedBlocks, kRedThreads, 0, s>>>(w, V, ldv, coef, sign, n, nullptr); break;
+      IBRD_CASE(1) IBRD_CASE(2) IBRD_CASE(3) IBRD_CASE(4) IBRD_CASE(5) IBRD_CASE(6) IBRD_CASE(7) IBRD_CASE(8)
+#undef IBRD_CASE
+      default: return;
+    }
+  }
+  check_launch("multi_axpy");
+}
+
+void launch_givens(double* H, int ldh, int j, double* cs, double* sn, double* gvec, double* res, cudaStream_t s) {
+  k_givens<<<1, 32, 0, s>>>(H, ldh, j, cs, sn, gvec, res);
+  check_launch("givens");
+}
+
+void launch_backsolve(const double* H, int ldh, int k, const double* gvec, double* y, cudaStream_t s) {
+  k_backsolve<<<1, 32, 0, s>>>(H, ldh, k, gvec, y);
+  check_launch("backsolve");
+}
+
+void launch_vec_add_small(double* h, const double* h2, int n, cudaStream_t s) {
+  k_vec_add_small<<<1, 64, 0, s>>>(h, h2, n);
+  check_launch("vec_add_small");
+}
+
+void launch_sqrt_scalar(const double* src, double* dst, cudaStream_t s) {
+  k_sqrt_scalar<<<1, 32, 0, s>>>(src, dst);
+  check_launch("sqrt_scalar");
+}
+
+void launch_small_start(const double* r, double* U0, int n, double* gvec, int m, cudaStream_t s) {
+  k_small_start<<<1, kSmallThreads, 0, s>>>(r, U0, n, gvec, m);
+  check_launch("small_start");
+}
+
+void launch_small_arnoldi(double* U, int n, int j, double* Hs, int ldh, double* cs, double* sn, double* gvec,
+                          cudaStream_t s) {
+  k_small_arnoldi<<<1, kSmallThreads, 0, s>>>(U, n, j, Hs, ldh, cs, sn, gvec);
+  check_launch("small_arnoldi");
+}
+
+void launch_small_finish(const double* U, int n, int k, const double* Hs, int ldh, const double* gvec, double* x,
+                         int project_mean, cudaStream_t s) {
+  k_small_finish<<<1, kSmallThreads, 0, s>>>(U, n, k, Hs, ldh, gvec, x, project_mean);
+  check_launch("small_finish");
+}
+
+}  // namespace ibrd

@@ -1,0 +1,69 @@
+"""Host-side checks of the C ABI: the library builds, loads without a GPU and
+exports every entry point that include/ibrd.h declares."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "ibrd.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ibrd_\w+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1306_3159_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_paper_boundary():
+    names = _declared()
+    for want in ["ibrd_grid_create", "ibrd_apply_L", "ibrd_vcycle", "ibrd_spread", "ibrd_interp",
+                 "ibrd_solve_reaction", "ibrd_solve_saddle"]:
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_binding_lists_every_symbol():
+    from paper_1306_3159_gb300 import EXPORTED
+    assert sorted(EXPORTED) == _declared()
+
+
+def test_default_opts_and_status_strings(lib):
+    import paper_1306_3159_gb300 as p
+    o = p.ibrd_default_opts()
+    assert o.tol == 1e-8 and o.restart == 30 and o.mg_cycles == 1 and o.schur_inner == 5
+    assert o.nu1 == 2 and o.nu2 == 2 and o.zeta == 1.0
+    lib.ibrd_status_string.restype = ctypes.c_char_p
+    assert lib.ibrd_status_string(0) == b"IBRD_OK"
+    assert lib.ibrd_status_string(4) == b"IBRD_ERR_NOT_CONVERGED"
+
+
+def test_create_rejects_bad_arguments_without_touching_gpu(lib):
+    # Argument validation happens before any CUDA call.
+    import paper_1306_3159_gb300 as p
+    for args in [(3, 8, 8, 1.0, 1.0, 0.0), (8, 8, 8, -1.0, 1.0, 0.0), (8, 8, 8, 1.0, 0.0, 0.0),
+                 (8, 8, 8, 1.0, 1.0, -0.5), (9, 9, 9, 1.0, 1.0, 0.0)]:
+        with pytest.raises(p.IbrdError) as e:
+            p.ibrd_grid_create(*args, stream=0)
+        assert e.value.status == 1
+
+
+def test_no_oracle_import_in_product():
+    """The product package never imports the oracle."""
+    pkg = os.path.join(ROOT, "paper_1306_3159_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".h", ".cuh")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt, f

@@ -1,0 +1,170 @@
+"""Solve-level parity of the CUDA path with the FP64 oracle's exact solutions.
+
+The GPU solves to a relative true residual of 1e-13 (FP64); the solution error
+is then bounded by the condition number times the residual, and the test
+requires the 1e-11 relative error stated as the FP64 target. The mixed FP32
+path solves to 1e-10 and must be within 1e-8 of the exact solution.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import direct, operators as op, outputs
+from synthetic import workload, loguniform_rates, lattice_positions, rsa_positions
+from tests.gpu_util import dev, host, rel_l2, rel_max
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ibrd():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_1306_3159_gb300 import build
+    build.build()
+    import paper_1306_3159_gb300 as p
+    return p
+
+
+@pytest.fixture(scope="module")
+def small():
+    w = workload("small")
+    M = direct.schur_matrix(w.q, w.dims, w.h, w.chi, 0.0)
+    return w, M
+
+
+def _grid(ibrd, w, alpha=0.0, kernel=4):
+    g = ibrd.Grid(*w.dims, h=w.h, chi=w.chi, alpha=alpha, kernel=kernel)
+    g.set_blobs(dev(w.q))
+    return g
+
+
+@pytest.mark.parametrize("precision,tol,err", [(0, 1e-13, 1e-11), (1, 1e-10, 1e-8)])
+def test_saddle_small(ibrd, small, precision, tol, err):
+    w, M = small
+    c_ref, lam_ref, _ = direct.solve_saddle(w.q, w.g, w.h, w.chi, 0.0, M=M)
+    g = _grid(ibrd, w)
+    c, lam, info = g.solve_saddle(dev(w.g), tol=tol, precision=precision, max_iter=400)
+    assert info["rel_residual"] <= tol
+    assert rel_l2(host(c), c_ref) < err
+    assert rel_l2(host(lam), lam_ref) < err
+    # Appendix A solvability: sum lambda = h^3 sum g / zeta
+    assert abs(info["sum_lambda"] - w.g.sum()) < 1e-9 * w.g.sum()
+    K_ref = outputs.overall_rate(lam_ref, c_ref)
+    assert abs(info["rate_K"] - K_ref) < err * abs(K_ref)
+
+
+@pytest.mark.parametrize("precision,tol,err", [(0, 1e-13, 1e-11), (1, 1e-10, 1e-8)])
+@pytest.mark.parametrize("alpha", [0.0, 0.2])
+def test_reaction_small(ibrd, small, precision, tol, err, alpha):
+    w, M0 = small
+    M = M0 if alpha == 0.0 else None
+    c_ref, u_ref, _ = direct.solve_reaction(w.q, w.kappa, w.g, w.h, w.chi, alpha, M=M)
+    g = _grid(ibrd, w, alpha)
+    c, info = g.solve_reaction(dev(w.kappa), dev(w.g), tol=tol, precision=precision, max_iter=400)
+    assert info["rel_residual"] <= tol
+    assert rel_l2(host(c), c_ref) < err
+    assert abs(info["sum_lambda"] - u_ref.sum()) < err * abs(u_ref.sum())
+
+
+def test_saddle_alpha_positive_nonunit_scales(ibrd):
+    """alpha > 0, h != 1, chi != 1, zeta != 1 and a nonzero f."""
+    dims, h, chi, alpha, zeta = (24, 16, 20), 0.5, 1.7, 0.8, 0.3
+    q = rsa_positions(12, dims, h, 3.0 * h, 12)
+    rng = np.random.default_rng(13)
+    gsrc = rng.standard_normal((20, 16, 24))
+    f = 0.1 * rng.standard_normal(12)
+    c_ref, lam_ref, _ = direct.solve_saddle(q, gsrc, h, chi, alpha, zeta=zeta, f=f)
+    g = ibrd.Grid(*dims, h=h, chi=chi, alpha=alpha)
+    g.set_blobs(dev(q))
+    c, lam, info = g.solve_saddle(dev(gsrc), f=dev(f), tol=1e-13, zeta=zeta, max_iter=400)
+    assert rel_l2(host(c), c_ref) < 1e-11
+    assert rel_l2(host(lam), lam_ref) < 1e-11
+
+
+def test_saddle_tiny_single_blob(ibrd):
+    """32^3, one blob at a sub-cell offset from the box centre, tol 1e-10."""
+    w = workload("tiny")
+    c_ref, lam_ref, _ = direct.solve_saddle(w.q, w.g, w.h, w.chi, 0.0)
+    g = _grid(ibrd, w)
+    c, lam, info = g.solve_saddle(dev(w.g), tol=1e-13, max_iter=400)
+    assert rel_l2(host(c), c_ref) < 1e-11
+    assert abs(host(lam)[0] - lam_ref[0]) < 1e-11 * abs(lam_ref[0])
+
+
+def test_saddle_diagonal_preconditioner(ibrd, small):
+    w, M = small
+    c_ref, lam_ref, _ = direct.solve_saddle(w.q, w.g, w.h, w.chi, 0.0, M=M)
+    g = _grid(ibrd, w)
+    c, lam, info = g.solve_saddle(dev(w.g), tol=1e-13, precond=1, restart=60, max_iter=2000)
+    assert rel_l2(host(lam), lam_ref) < 1e-11
+
+
+def test_single_blob_finite_rate_shift(ibrd):
+    """Sec. III.D: c_P - c_0 = 1/kappa, a constant field (one periodic blob)."""
+    L = 16
+    q = np.array([[7.3, 8.6, 8.1]])
+    gsrc = np.full((L, L, L), 1.0 / L ** 3)
+    g = ibrd.Grid(L, L, L)
+    g.set_blobs(dev(q))
+    c0, lam, _ = g.solve_saddle(dev(gsrc), tol=1e-13, max_iter=400)
+    for kappa in (0.5, 7.0):
+        cP, _ = g.solve_reaction(dev(np.array([kappa])), dev(gsrc), tol=1e-13, max_iter=400)
+        d = host(cP) - host(c0)
+        assert np.abs(d - 1.0 / kappa).max() < 1e-9
+
+
+def test_guess_and_not_converged(ibrd, small):
+    w, _ = small
+    g = _grid(ibrd, w)
+    import paper_1306_3159_gb300 as p
+    c = g.field()
+    lam = dev(np.zeros(len(w.q)))
+    info = p.ibrd_solve_saddle(g.handle, dev(w.g), None, c, lam, p.ibrd_default_opts(tol=1e-14, max_iter=2),
+                               raise_on_error=False)
+    assert info["status"] == 4 and info["outer_iters"] == 2
+    # restart from the returned iterate
+    info2 = p.ibrd_solve_saddle(g.handle, dev(w.g), None, c, lam,
+                                p.ibrd_default_opts(tol=1e-9, max_iter=400, use_guess=1))
+    assert info2["status"] == 0 and info2["rel_residual"] <= 1e-9
+
+
+def test_nonfinite_source_reported(ibrd, small):
+    w, _ = small
+    g = _grid(ibrd, w)
+    bad = w.g.copy()
+    bad[1, 2, 3] = np.nan
+    import paper_1306_3159_gb300 as p
+    info = p.ibrd_solve_reaction(g.handle, dev(w.kappa), dev(bad), g.field(), p.ibrd_default_opts(),
+                                 raise_on_error=False)
+    assert info["status"] == 6
+    with pytest.raises(p.IbrdError) as e:
+        g.solve_reaction(dev(-w.kappa), dev(w.g))
+    assert e.value.status == 6
+
+
+def _residual_oracle(q, kappa, gsrc, c, lam, h, chi, alpha, zeta=1.0):
+    """Relative true residual of a GPU solution, computed with the oracle's
+    operator definitions (a property that holds at any size)."""
+    dims = gsrc.shape[::-1]
+    if lam is None:
+        r = gsrc - (op.apply_A(c, h, chi, alpha) + op.spread(kappa * op.interp(c, q, h), q, dims, h))
+        return np.linalg.norm(r) / np.linalg.norm(gsrc)
+    r1 = gsrc - (op.apply_A(c, h, chi, alpha) + zeta * op.spread(lam, q, dims, h))
+    r2 = -(zeta / h ** 3) * op.interp(c, q, h)
+    return math.sqrt(np.sum(r1 ** 2) + np.sum(r2 ** 2)) / np.linalg.norm(gsrc)
+
+
+def test_full_size_properties(ibrd):
+    """256^3 with 4096 RSA blobs (spacing 4h), as timed by the benchmark: the
+    oracle recomputes the true residual of both solves, and the Appendix A
+    balance sum(lambda) = h^3 sum(g) holds."""
+    w = workload("scale")
+    g = _grid(ibrd, w)
+    c, lam, info = g.solve_saddle(dev(w.g), tol=1e-8, precision=1, max_iter=2000)
+    ch, lh = host(c), host(lam)
+    assert _residual_oracle(w.q, None, w.g, ch, lh, 1.0, 1.0, 0.0) < 2e-8
+    assert abs(lh.sum() - w.g.sum()) < 1e-6 * w.g.sum()
+    c2, info2 = g.solve_reaction(dev(w.kappa), dev(w.g), tol=1e-8, precision=1, max_iter=2000)
+    assert _residual_oracle(w.q, w.kappa, w.g, host(c2), None, 1.0, 1.0, 0.0) < 2e-8
