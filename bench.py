@@ -1,0 +1,439 @@
+#!/usr/bin/env python
+"""Benchmark of the blob-model solve on one GB300.
+
+Workload: 256^3 periodic grid (h = 1, chi = 1), 4096 blobs placed by seeded
+random sequential addition with minimum spacing 4h, uniform unit source,
+steady state (alpha = 0), Peskin 4-point kernel. One step = blob setup
+(weights + tile binning) + the reaction-limited solve (rates log-uniform in
+[0.1, 10]) + the diffusion-limited saddle-point solve, each to a relative true
+residual of 1e-8. The timed ("chosen") path runs FP32 multigrid and FP32
+spreading/averaging inside FP64 flexible GMRES; the plain FP64 path is timed
+beside it.
+
+Prints one JSON line (rank 0). `value` is seconds per step (lower is better).
+`--impl reference` times the FP64 CPU oracle (direct Schur-complement solve)
+on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "solve time at rel. residual 1e-8, 256³+4096 blobs: plain vs chosen; % HBM peak"
+UNIT = "s"
+WORKLOAD = "scale"
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- peaks
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+FP64_PEAK_TFLOPS = 1.2   # FP64 FMA rate of GB300 (recipe: 1.25 TFLOP/s nominal)
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1306_3159_gb300", "csrc"))):
+        h.update(open(os.path.join(ROOT, "paper_1306_3159_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(kernel_class: str):
+    """DRAM bytes per finest-level launch from the committed ncu summary, if
+    it was taken on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    e = d.get("classes", {}).get(kernel_class)
+    return e
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1306_3159_gb300 import build as pbuild
+    pbuild.build()
+    import paper_1306_3159_gb300 as p
+    from synthetic import workload
+
+    w = workload(WORKLOAD)
+    nx, ny, nz = w.dims
+    N = len(w.q)
+    stream = torch.cuda.current_stream()
+    grid = p.Grid(nx, ny, nz, h=w.h, chi=w.chi, alpha=0.0, precision=p.IBRD_MIXED_FP32,
+                  stream=stream.cuda_stream)
+    # pinned host inputs / outputs (end-to-end leg) and resident device copies
+    q_h = torch.from_numpy(w.q).pin_memory()
+    k_h = torch.from_numpy(w.kappa).pin_memory()
+    g_h = torch.from_numpy(w.g).pin_memory()
+    q_d, k_d, g_d = q_h.cuda(), k_h.cuda(), g_h.cuda()
+    c_r = grid.field()
+    c_s = grid.field()
+    lam = torch.zeros(N, dtype=torch.float64, device="cuda")
+    out_cr = torch.empty_like(g_h).pin_memory()
+    out_cs = torch.empty_like(g_h).pin_memory()
+    out_l = torch.empty(N, dtype=torch.float64).pin_memory()
+    tol = 1e-8
+    infos = {}
+
+    def step(precision, qd=q_d, kd=k_d, gd=g_d):
+        grid.set_blobs(qd)
+        _, ir = grid.solve_reaction(kd, gd, c_r, tol=tol, precision=precision, max_iter=3000)
+        _, _, isd = grid.solve_saddle(gd, c=c_s, lam=lam, tol=tol, precision=precision, max_iter=3000)
+        infos[precision] = (ir, isd)
+
+    def step_e2e(precision):
+        q_d.copy_(q_h, non_blocking=True)
+        k_d.copy_(k_h, non_blocking=True)
+        g_d.copy_(g_h, non_blocking=True)
+        step(precision)
+        out_cr.copy_(c_r, non_blocking=True)
+        out_cs.copy_(c_s, non_blocking=True)
+        out_l.copy_(lam, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def timed(fn, k):
+        barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        return max_over_ranks(e0.elapsed_time(e1) / 1e3 / k)
+
+    chosen = p.IBRD_MIXED_FP32
+    plain = p.IBRD_FP64
+    if args.ncu_step:
+        # profiler range around one chosen step (ncu --profile-from-start off)
+        for _ in range(args.warmup):
+            step(chosen)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        step(chosen)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        log("[bench] ncu step done")
+        return
+    log(f"[bench] warmup {args.warmup} steps")
+    for _ in range(args.warmup):
+        step(chosen)
+    # one profiling step with every class timed picks the dominant class
+    p.ibrd_profile_read(grid.handle, reset=True)
+    p.ibrd_profile_enable(grid.handle, True)
+    step(chosen)
+    prof_all = p.ibrd_profile_read(grid.handle, reset=True)
+    dom_name, dom = max(prof_all["classes"].items(), key=lambda kv: kv[1]["ms"])
+    # timed region: the dominant class keeps its per-launch events
+    p.ibrd_profile_enable(grid.handle, 1 << dom["id"])
+    sampler = ClockSampler(local)
+    sampler.start()
+    t_step = timed(lambda: step(chosen), args.steps)
+    clocks = sampler.stop()
+    prof_timed = p.ibrd_profile_read(grid.handle, reset=True)
+    p.ibrd_profile_enable(grid.handle, 0)
+    ir, isd = infos[chosen]
+    # plain FP64 arm (same workload)
+    k_plain = max(1, args.steps // 2)
+    step(plain)
+    t_plain = timed(lambda: step(plain), k_plain)
+    ir64, is64 = infos[plain]
+    # end-to-end through host buffers
+    step_e2e(chosen)
+    t_e2e = timed(lambda: step_e2e(chosen), max(1, args.steps // 2))
+
+    dc = prof_timed["classes"].get(dom_name, dom)
+    peaks = measured_peaks()
+    fp32_or_bytes = dom_name.endswith("f32") or dom_name in ("dot", "axpy", "vector")
+    achieved_gbs = dc["bytes"] / (dc["ms"] * 1e-3) / 1e9 if dc["ms"] > 0 else 0.0
+    traffic = committed_traffic(dom_name)
+    roofline = {"bound": "hbm", "kernel_class": dom_name, "achieved": round(achieved_gbs, 1),
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(achieved_gbs / peaks["hbm_gbs"], 4),
+                "peak_source": f"{peaks['source']} hbm_gbs (copy)",
+                "traffic": traffic["dram_bytes_per_launch"] if traffic else None,
+                "algorithmic_bytes_per_launch": dc["bytes"] / max(1, dc["launches"]),
+                "launches_timed": dc["timed"], "avg_launch_us": dc["ms"] * 1e3 / max(1, dc["timed"]),
+                "share_of_step": round(dom["ms"] / max(1e-9, sum(v["ms"] for v in prof_all["classes"].values())), 4)}
+    if not fp32_or_bytes:
+        roofline["note"] = "FP64 kernel: FP64 pipe bound on GB300 (1.2 TFLOP/s), see alu_roofline"
+    breakdown = {k: {"ms_per_step": round(v["ms"], 3), "launches": v["launches"],
+                     "GBps": round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1) if v["ms"] > 0 else None}
+                 for k, v in sorted(prof_all["classes"].items(), key=lambda kv: -kv[1]["ms"])}
+
+    def solve_summary(i):
+        return {"outer_iters": i["outer_iters"], "inner_iters": i["inner_iters"], "vcycles": i["vcycles"],
+                "rel_residual": i["rel_residual"], "rate_K": i["rate_K"], "cbar": i["cbar"]}
+
+    h2d = (q_h.numel() + k_h.numel() + g_h.numel()) * 8
+    d2h = (out_cr.numel() + out_cs.numel() + out_l.numel()) * 8
+    result = {
+        "metric": METRIC, "value": round(t_step, 6), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(t_step * 1e3, 3), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
+        "data": "synthetic (seeded RSA suspension; the paper's external datasets are not used)",
+        "config": {"workload": "256^3 periodic grid, 4096 RSA blobs (spacing 4h), uniform source, steady; "
+                               "reaction (kappa log-uniform [0.1,10]) + saddle solves to rel. residual 1e-8",
+                   "grid": [nx, ny, nz], "blobs": N, "tol": tol, "precision": "FP32 multigrid + spread/interp "
+                   "in FP64 FGMRES(30)", "preconditioner": "approximate Schur m=5, n=1 (saddle); 1 V-cycle (reaction)",
+                   "parallelism": f"replicas x{world}",
+                   "l2": "no flush: working set > L2 (one FP64 field is 134 MB, a step streams hundreds of fields)"},
+        "gpu_launches": prof_timed["launches"] // max(1, args.steps) * args.steps,
+        "gpu_launches_per_step": prof_timed["launches"] / max(1, args.steps),
+        "solves": {"reaction": solve_summary(ir), "saddle": solve_summary(isd)},
+        "plain_fp64": {"s_per_step": round(t_plain, 6), "steps": k_plain,
+                       "reaction": solve_summary(ir64), "saddle": solve_summary(is64),
+                       "chosen_speedup": round(t_plain / t_step, 3)},
+        "e2e": {"value": round(t_e2e, 6), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "roofline": roofline, "kernel_breakdown": breakdown, "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline_sample(columns=args.cpu_columns)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_kernel_case(args):
+    """FP32 V-cycles on a 256^3 field (about 0.3 GB on the device) with a
+    profiler range around one V-cycle: the small case for full ncu captures of
+    the multigrid kernels."""
+    import torch
+    from paper_1306_3159_gb300 import build as pbuild
+    pbuild.build()
+    import paper_1306_3159_gb300 as p
+    n = 256
+    grid = p.Grid(n, n, n, stream=torch.cuda.current_stream().cuda_stream)
+    b = torch.randn((n, n, n), dtype=torch.float32, device="cuda", generator=torch.Generator("cuda").manual_seed(1))
+    b -= b.mean()
+    x = torch.zeros_like(b)
+    for _ in range(3):
+        grid.vcycle_f32(b, x)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    grid.vcycle_f32(b, x)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    log("[bench] kernel case done")
+
+
+# ---------------------------------------------------------------- oracle arm
+def _oracle_sample(columns: int):
+    """Time the FP64 oracle on a bounded sample of the workload and scale it
+    to one full step. The oracle solves each system directly: N Green's
+    function (FFT) solves build the Schur matrix M = J G S (shared by both
+    solves), then one dense (N+1) LU per solve and one final Green's solve per
+    solve. The sample times `columns` of the N columns and one dense LU."""
+    import numpy as np
+    from oracle import operators as op
+    from synthetic import workload
+
+    w = workload(WORKLOAD)
+    q = w.q
+    dims = w.dims
+    N = len(q)
+    t0 = time.perf_counter()
+    for j in range(columns):
+        e = np.zeros(N)
+        e[j] = 1.0
+        col = op.green_apply(op.spread(e, q, dims, w.h), w.h, w.chi, 0.0)
+        op.interp(col, q, w.h)
+    t_col = (time.perf_counter() - t0) / columns
+    rng = np.random.default_rng(0)
+    A = rng.standard_normal((N + 1, N + 1)) + (N + 1) * np.eye(N + 1)
+    t0 = time.perf_counter()
+    np.linalg.solve(A, rng.standard_normal(N + 1))
+    t_lu = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    op.green_apply(w.g - op.spread(np.ones(N), q, dims, w.h), w.h, w.chi, 0.0)
+    t_final = time.perf_counter() - t0
+    total = N * t_col + 2 * t_lu + 2 * t_final
+    return {"value": total, "t_col": t_col, "t_lu": t_lu, "t_final": t_final, "columns": columns, "N": N}
+
+
+def cpu_baseline_sample(columns=3):
+    """Run the oracle sample in a child process pinned to one BLAS/FFT thread."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", str(columns)],
+                       capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": r.stderr[-400:]}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": round(d["value"], 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{d['columns']} of {d['N']} Schur-complement columns (FFT Green's solves at 256^3), one "
+                      f"dense (N+1) LU and one final Green's solve, scaled to a full step (M once, 2 LU, 2 final "
+                      f"solves): t_col={d['t_col']:.3f}s t_lu={d['t_lu']:.3f}s t_final={d['t_final']:.3f}s"}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    # each step: a bounded sample (one Schur column) scaled to a full step
+    vals = []
+    for i in range(args.warmup + args.steps):
+        d = json.loads(_oracle_sample_json(1))
+        if i >= args.warmup:
+            vals.append(d["value"])
+    v = statistics.median(vals)
+    res = {"metric": METRIC, "value": round(v, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(v * 1e3, 1), "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": "256^3 periodic grid, 4096 RSA blobs (spacing 4h), uniform source, steady; "
+                                  "reaction + saddle solves (exact, direct Schur elimination)"},
+           "cpu_baseline": {"value": round(v, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": "per step: 1 of 4096 Schur columns + one dense (N+1) LU + one final "
+                                      "Green's solve, scaled to the full step"},
+           "e2e": {"value": round(v, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(res), flush=True)
+
+
+def _oracle_sample_json(columns):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", str(columns)],
+                       capture_output=True, text=True, env=env, check=True)
+    return r.stdout.strip().splitlines()[-1]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-columns", type=int, default=3)
+    ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--ncu-step", action="store_true", help="profiler range around one step, then exit")
+    ap.add_argument("--kernel-case", action="store_true", help="FP32 V-cycles at 256^3 for ncu, then exit")
+    args = ap.parse_args()
+    if args.oracle_sample:
+        print(json.dumps(_oracle_sample(args.oracle_sample)), flush=True)
+        return
+    if args.warmup < 3:
+        log("[bench] warmup raised to 3 (minimum)")
+        args.warmup = 3
+    if args.kernel_case:
+        run_kernel_case(args)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -126,6 +126,10 @@ ibrd_status ibrd_apply_L(ibrd_grid g, const double* c, double* y);
    ignores the incoming x. rhs and x must not overlap. */
 ibrd_status ibrd_vcycle(ibrd_grid g, const double* rhs, double* x, int zero_initial_guess);
 
+/* The same V-cycle with FP32 fields and FP32 arithmetic (the multigrid used
+   inside the mixed-precision solves). rhs, x: FP32 device fields. */
+ibrd_status ibrd_vcycle_f32(ibrd_grid g, const float* rhs, float* x, int zero_initial_guess);
+
 /* grid_out (+)= S lambda, (S lambda)_k = h^-3 sum_i phi(q_i - r_k) lambda_i
    (Sec. III.A). accumulate = 0 overwrites grid_out (zero away from blobs).
    Deterministic: each cell sums its blobs in increasing blob index. */
@@ -152,6 +156,33 @@ ibrd_status ibrd_solve_reaction(ibrd_grid g, const double* kappa, const double* 
    Synchronizes the stream. */
 ibrd_status ibrd_solve_saddle(ibrd_grid g, const double* rhs, const double* f, double* c,
                               double* lambda, const ibrd_solve_opts* opts, ibrd_solve_info* info);
+
+/* Launch profiler (not in the paper: instrumentation of this library).
+   Every kernel the library launches is counted per kernel class; with timing
+   enabled each launch is also bracketed by CUDA events on the handle's stream,
+   which adds a few microseconds of host time per launch. */
+#define IBRD_PROF_NCLASS 19
+typedef struct {
+  long long launches;                 /* kernels launched since the last reset */
+  int nclass;                         /* number of classes filled (<= IBRD_PROF_NCLASS) */
+  int overflow;                       /* 1 if the event pool ran out (times partial) */
+  long long count[IBRD_PROF_NCLASS];  /* launches per class */
+  long long timed[IBRD_PROF_NCLASS];  /* timed launches per class */
+  double ms[IBRD_PROF_NCLASS];        /* summed event time per class, milliseconds */
+  double bytes[IBRD_PROF_NCLASS];     /* summed algorithmic bytes per class: each
+                                         input read once, each output written once */
+} ibrd_profile;
+
+/* Time the launches of every class c with bit c set in class_mask (0 turns
+   timing off). Counting is always on. */
+ibrd_status ibrd_profile_enable(ibrd_grid g, unsigned class_mask);
+
+/* Synchronize the handle's stream and report counts and times since the last
+   reset; reset != 0 clears them. */
+ibrd_status ibrd_profile_read(ibrd_grid g, ibrd_profile* out, int reset);
+
+/* Static name of profiler class cls ("" if out of range). */
+const char* ibrd_profile_class_name(int cls);
 
 /* Message of the last failed call on this handle ("" if none). */
 const char* ibrd_last_error(ibrd_grid g);

@@ -20,8 +20,11 @@ STATUS = {0: "IBRD_OK", 1: "IBRD_ERR_ARG", 2: "IBRD_ERR_CUDA", 3: "IBRD_ERR_OOM"
 
 # Every entry point declared in include/ibrd.h.
 EXPORTED = ["ibrd_default_opts", "ibrd_grid_create", "ibrd_grid_destroy", "ibrd_set_blobs", "ibrd_apply_L",
-            "ibrd_vcycle", "ibrd_spread", "ibrd_interp", "ibrd_solve_reaction", "ibrd_solve_saddle",
-            "ibrd_last_error", "ibrd_status_string"]
+            "ibrd_vcycle", "ibrd_vcycle_f32", "ibrd_spread", "ibrd_interp", "ibrd_solve_reaction", "ibrd_solve_saddle",
+            "ibrd_last_error", "ibrd_status_string", "ibrd_profile_enable", "ibrd_profile_read",
+            "ibrd_profile_class_name"]
+
+PROF_NCLASS = 19
 
 
 class SolveOpts(ctypes.Structure):
@@ -37,6 +40,12 @@ class SolveInfo(ctypes.Structure):
                 ("cbar", ctypes.c_double), ("rate_K", ctypes.c_double), ("seconds", ctypes.c_double),
                 ("residual_history", ctypes.POINTER(ctypes.c_double)), ("history_len", ctypes.c_int),
                 ("history_cap", ctypes.c_int)]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_longlong), ("nclass", ctypes.c_int), ("overflow", ctypes.c_int),
+                ("count", ctypes.c_longlong * PROF_NCLASS), ("timed", ctypes.c_longlong * PROF_NCLASS),
+                ("ms", ctypes.c_double * PROF_NCLASS), ("bytes", ctypes.c_double * PROF_NCLASS)]
 
 
 class IbrdError(RuntimeError):
@@ -69,6 +78,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ibrd_apply_L.restype = i
     lib.ibrd_vcycle.argtypes = [vp, vp, vp, i]
     lib.ibrd_vcycle.restype = i
+    lib.ibrd_vcycle_f32.argtypes = [vp, vp, vp, i]
+    lib.ibrd_vcycle_f32.restype = i
     lib.ibrd_spread.argtypes = [vp, vp, vp, i]
     lib.ibrd_spread.restype = i
     lib.ibrd_interp.argtypes = [vp, vp, vp]
@@ -81,18 +92,24 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ibrd_last_error.restype = ctypes.c_char_p
     lib.ibrd_status_string.argtypes = [i]
     lib.ibrd_status_string.restype = ctypes.c_char_p
+    lib.ibrd_profile_enable.argtypes = [vp, ctypes.c_uint]
+    lib.ibrd_profile_enable.restype = i
+    lib.ibrd_profile_read.argtypes = [vp, P(Profile), i]
+    lib.ibrd_profile_read.restype = i
+    lib.ibrd_profile_class_name.argtypes = [i]
+    lib.ibrd_profile_class_name.restype = ctypes.c_char_p
     _lib = lib
     return lib
 
 
-def _ptr(t):
+def _ptr(t, dtype="float64"):
     if t is None:
         return None
     import torch
     if not isinstance(t, torch.Tensor):
         raise TypeError("expected a torch tensor")
-    if not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
-        raise ValueError("expected a contiguous CUDA float64 tensor")
+    if not t.is_cuda or t.dtype != getattr(torch, dtype) or not t.is_contiguous():
+        raise ValueError(f"expected a contiguous CUDA {dtype} tensor")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -150,6 +167,11 @@ def ibrd_vcycle(g, rhs, x, zero_initial_guess=True):
     _check(g, load_library().ibrd_vcycle(g, _ptr(rhs), _ptr(x), int(bool(zero_initial_guess))))
 
 
+def ibrd_vcycle_f32(g, rhs, x, zero_initial_guess=True):
+    _check(g, load_library().ibrd_vcycle_f32(g, _ptr(rhs, "float32"), _ptr(x, "float32"),
+                                             int(bool(zero_initial_guess))))
+
+
 def ibrd_spread(g, lam, out, accumulate=False):
     _check(g, load_library().ibrd_spread(g, _ptr(lam), _ptr(out), int(bool(accumulate))))
 
@@ -196,6 +218,35 @@ def ibrd_solve_saddle(g, rhs, f, c, lam, opts: SolveOpts | None = None, history_
     return out
 
 
+PROF_ALL = (1 << PROF_NCLASS) - 1
+
+
+def profile_class_names():
+    lib = load_library()
+    return [lib.ibrd_profile_class_name(c).decode() for c in range(PROF_NCLASS)]
+
+
+def ibrd_profile_enable(g, class_mask=PROF_ALL):
+    """Time the kernel classes in class_mask (bit per class; True = all)."""
+    if class_mask is True:
+        class_mask = PROF_ALL
+    _check(g, load_library().ibrd_profile_enable(g, int(class_mask)))
+
+
+def ibrd_profile_read(g, reset=True) -> dict:
+    """Launch counts and event times per kernel class since the last reset."""
+    lib = load_library()
+    pr = Profile()
+    _check(g, lib.ibrd_profile_read(g, ctypes.byref(pr), int(bool(reset))))
+    classes = {}
+    for c in range(pr.nclass):
+        if pr.count[c]:
+            classes[lib.ibrd_profile_class_name(c).decode()] = {
+                "id": c, "launches": int(pr.count[c]), "timed": int(pr.timed[c]), "ms": float(pr.ms[c]),
+                "bytes": float(pr.bytes[c])}
+    return {"launches": int(pr.launches), "overflow": bool(pr.overflow), "classes": classes}
+
+
 class Grid:
     """Owning wrapper of an ``ibrd_grid`` handle."""
 
@@ -234,6 +285,12 @@ class Grid:
     def vcycle(self, rhs, x=None, zero_initial_guess=True):
         x = self.field() if x is None else x
         ibrd_vcycle(self.handle, rhs, x, zero_initial_guess)
+        return x
+
+    def vcycle_f32(self, rhs, x=None, zero_initial_guess=True):
+        import torch
+        x = torch.zeros_like(rhs) if x is None else x
+        ibrd_vcycle_f32(self.handle, rhs, x, zero_initial_guess)
         return x
 
     def spread(self, lam, out=None, accumulate=False):

@@ -73,6 +73,62 @@ struct Level {
 };
 
 }  // namespace
+
+// Launch profiler of one handle: counts every launch and, when timing is on,
+// brackets each launch with a pair of CUDA events on the launch stream.
+struct Profiler {
+  bool timing = false;
+  unsigned mask = 0;      // classes timed when timing is on
+  bool overflow = false;
+  long long launches = 0;
+  long long count[P_NCLASS] = {};
+  double bytes[P_NCLASS] = {};
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  std::vector<std::pair<int, size_t>> pending;
+  int open_cls = -1;
+  size_t open_idx = 0;
+};
+
+namespace {
+thread_local Profiler* t_prof = nullptr;
+constexpr size_t kMaxEvents = 1 << 20;
+}  // namespace
+
+void prof_begin(int cls, cudaStream_t s) {
+  Profiler* p = t_prof;
+  if (!p || !p->timing || p->overflow || !((p->mask >> cls) & 1u)) return;
+  if (p->used + 2 > p->pool.size()) {
+    if (p->pool.size() + 4096 > kMaxEvents) {
+      p->overflow = true;
+      return;
+    }
+    for (int i = 0; i < 4096; ++i) {
+      cudaEvent_t e;
+      IBRD_CUDA(cudaEventCreate(&e));
+      p->pool.push_back(e);
+    }
+  }
+  IBRD_CUDA(cudaEventRecord(p->pool[p->used], s));
+  p->open_idx = p->used;
+  p->open_cls = cls;
+  p->used += 2;
+}
+
+void prof_end(int cls, cudaStream_t s, const char* what, double bytes) {
+  check_launch(what);
+  Profiler* p = t_prof;
+  if (!p) return;
+  p->launches++;
+  p->count[cls]++;
+  p->bytes[cls] += bytes;
+  if (p->open_cls == cls) {
+    IBRD_CUDA(cudaEventRecord(p->pool[p->open_idx + 1], s));
+    p->pending.emplace_back(cls, p->open_idx);
+    p->open_cls = -1;
+  }
+}
+
 }  // namespace ibrd
 
 using namespace ibrd;
@@ -113,6 +169,7 @@ struct ibrd_grid_s {
   // counters of the current solve
   long vcycles = 0;
   long inner = 0;
+  Profiler prof;
   std::string err;
 };
 
@@ -370,8 +427,9 @@ SolveResult fgmres(ibrd_grid g, LinOp& op, const double* b, double* x, size_t n,
     }
     // V[0] = r / beta, gvec = [beta, 0, ...]
     launch_scale_by_inv(V, V, n, g->scal + S_NORM, 1.0, g->s);
+    prof_begin(P_SMALL, g->s);
     k_set_gvec<<<1, 64, 0, g->s>>>(g->gvec, m, g->scal + S_NORM);
-    check_launch("set_gvec");
+    prof_end(P_SMALL, g->s, "set_gvec");
     int k = 0;
     bool breakdown = false;
     for (int j = 0; j < m; ++j) {
@@ -531,8 +589,9 @@ struct SaddleOp : LinOp {
       // zeta S (lambda-bar 1) = (V / (N N_c)) sum(g) S 1
       launch_spread_const<T>(g->blobs, g->d, g->scal + S_GSUM, -volume / ((double)N * (double)nc) * inv_h3(g), gt,
                              g->s);
+      prof_begin(P_SMALL, g->s);
       k_scalar_affine<<<1, 1, 0, g->s>>>(g->scal + S_LBAR, g->scal + S_GSUM, volume / (zeta * N * (double)nc));
-      check_launch("lbar");
+      prof_end(P_SMALL, g->s, "lbar");
     }
     vcycles<T>(g, gt, cs, true, shift, o.mg_cycles, o.nu1, o.nu2);
     // step 2: rhs = (zeta xi)^-1 (xi J c~* - f)
@@ -602,10 +661,17 @@ ibrd_status fail(ibrd_grid g, ibrd_status st, const std::string& msg) {
   return st;
 }
 
+struct ProfScope {
+  Profiler* prev;
+  explicit ProfScope(Profiler* p) : prev(t_prof) { t_prof = p; }
+  ~ProfScope() { t_prof = prev; }
+};
+
 template <typename F>
 ibrd_status guarded(ibrd_grid g, const char* name, F&& f) {
   if (!g) return IBRD_ERR_ARG;
   DeviceGuard dg(g->dev);
+  ProfScope ps(&g->prof);
   try {
     g->err.clear();
     return f();
@@ -725,6 +791,7 @@ void ibrd_grid_destroy(ibrd_grid g) {
   for (auto p : g->p32) F(p);
   for (auto p : g->nv) F(p);
   F(g->U); F(g->Hs); F(g->scs); F(g->ssn); F(g->sg);
+  for (auto e : g->prof.pool) cudaEventDestroy(e);
   delete g;
 }
 
@@ -809,6 +876,14 @@ ibrd_status ibrd_vcycle(ibrd_grid g, const double* rhs, double* x, int zero) {
   });
 }
 
+ibrd_status ibrd_vcycle_f32(ibrd_grid g, const float* rhs, float* x, int zero) {
+  return guarded(g, "ibrd_vcycle_f32", [&]() {
+    if (!rhs || !x || rhs == x) throw ArgError{IBRD_ERR_ARG, "null or aliased field"};
+    vcycle<float>(g, rhs, x, zero != 0, g->alpha, 2, 2);
+    return IBRD_OK;
+  });
+}
+
 ibrd_status ibrd_spread(ibrd_grid g, const double* lam, double* out, int accumulate) {
   return guarded(g, "ibrd_spread", [&]() {
     if (!out || (g->blobs.n > 0 && !lam)) throw ArgError{IBRD_ERR_ARG, "null pointer"};
@@ -838,8 +913,9 @@ ibrd_status ibrd_solve_reaction(ibrd_grid g, const double* kappa, const double* 
     double sigma = g->alpha;
     if (N > 0) {
       IBRD_CUDA(cudaMemsetAsync(g->dflag, 0, sizeof(int), g->s));
+      prof_begin(P_SETUP, g->s);
       k_check_rates<<<std::min(1024, (N + 255) / 256), 256, 0, g->s>>>(kappa, N, g->dflag);
-      check_launch("check_rates");
+      prof_end(P_SETUP, g->s, "check_rates");
       int flag = 0;
       IBRD_CUDA(cudaMemcpyAsync(&flag, g->dflag, sizeof(int), cudaMemcpyDeviceToHost, g->s));
       launch_sum<double>(kappa, N, g->partial, g->scal + S_TMP, 1.0, g->s);
@@ -912,6 +988,52 @@ ibrd_status ibrd_solve_saddle(ibrd_grid g, const double* rhs, const double* f, d
     fill_info(info, R, g, t0);
     if (R.st != IBRD_OK) g->err = std::string("ibrd_solve_saddle: ") + ibrd_status_string(R.st);
     return R.st;
+  });
+}
+
+static const char* kProfNames[P_NCLASS] = {
+    "apply_f64",    "apply_f32",    "rbgs_f64",   "rbgs_f32",   "restrict_f64", "restrict_f32", "prolong_f64",
+    "prolong_f32",  "coarse",       "spread_f64", "spread_f32", "interp_f64",   "interp_f32",   "dot",
+    "axpy",         "reduce",       "vector",     "small",      "setup"};
+
+const char* ibrd_profile_class_name(int cls) { return (cls >= 0 && cls < P_NCLASS) ? kProfNames[cls] : ""; }
+
+ibrd_status ibrd_profile_enable(ibrd_grid g, unsigned class_mask) {
+  return guarded(g, "ibrd_profile_enable", [&]() {
+    g->prof.timing = class_mask != 0;
+    g->prof.mask = class_mask;
+    return IBRD_OK;
+  });
+}
+
+ibrd_status ibrd_profile_read(ibrd_grid g, ibrd_profile* out, int reset) {
+  return guarded(g, "ibrd_profile_read", [&]() {
+    if (!out) throw ArgError{IBRD_ERR_ARG, "null output"};
+    Profiler& p = g->prof;
+    IBRD_CUDA(cudaStreamSynchronize(g->s));
+    std::memset(out, 0, sizeof(*out));
+    out->launches = p.launches;
+    out->nclass = P_NCLASS;
+    out->overflow = p.overflow ? 1 : 0;
+    for (int c = 0; c < P_NCLASS; ++c) {
+      out->count[c] = p.count[c];
+      out->bytes[c] = p.bytes[c];
+    }
+    for (auto& e : p.pending) {
+      float ms = 0.f;
+      IBRD_CUDA(cudaEventElapsedTime(&ms, p.pool[e.second], p.pool[e.second + 1]));
+      out->ms[e.first] += ms;
+      out->timed[e.first] += 1;
+    }
+    if (reset) {
+      p.launches = 0;
+      for (auto& c : p.count) c = 0;
+      for (auto& b : p.bytes) b = 0.0;
+      p.pending.clear();
+      p.used = 0;
+      p.overflow = false;
+    }
+    return IBRD_OK;
   });
 }
 

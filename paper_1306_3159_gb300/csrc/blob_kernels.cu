@@ -272,14 +272,17 @@ void blobs_setup(BlobSet& b, Dims d, double h, const double* q_in, int n, cudaSt
   IBRD_CUDA(cudaMemsetAsync(b.tile_count, 0, sizeof(int) * nt, s));
   IBRD_CUDA(cudaMemsetAsync(b.tile_cursor, 0, sizeof(int) * nt, s));
   if (n > 0) {
+    prof_begin(P_SETUP, s);
     k_blob_prep<<<(n + 127) / 128, 128, 0, s>>>(q_in, n, d.nx, d.ny, d.nz, h, b.width, b.q, b.idx, b.w64, b.w32);
-    check_launch("blob_prep");
+    prof_end(P_SETUP, s, "blob_prep");
+    prof_begin(P_SETUP, s);
     k_tile_pairs<false><<<(n + 127) / 128, 128, 0, s>>>(b.idx, n, b.ntx, b.nty, b.tile_count, nullptr, nullptr,
                                                          nullptr);
-    check_launch("tile_count");
+    prof_end(P_SETUP, s, "tile_count");
   }
+  prof_begin(P_SETUP, s);
   k_scan_tiles<<<1, 1024, 0, s>>>(b.tile_count, nt, b.tile_offset, b.active, b.d_meta);
-  check_launch("scan_tiles");
+  prof_end(P_SETUP, s, "scan_tiles");
   int meta[2];
   IBRD_CUDA(cudaMemcpyAsync(meta, b.d_meta, sizeof(meta), cudaMemcpyDeviceToHost, s));
   IBRD_CUDA(cudaStreamSynchronize(s));
@@ -291,12 +294,14 @@ void blobs_setup(BlobSet& b, Dims d, double h, const double* q_in, int n, cudaSt
     b.pair_cap = meta[0];
   }
   if (n > 0) {
+    prof_begin(P_SETUP, s);
     k_tile_pairs<true><<<(n + 127) / 128, 128, 0, s>>>(b.idx, n, b.ntx, b.nty, nullptr, b.tile_offset,
                                                         b.tile_cursor, b.tile_blobs);
-    check_launch("tile_fill");
+    prof_end(P_SETUP, s, "tile_fill");
     if (b.n_active > 0) {
+      prof_begin(P_SETUP, s);
       k_tile_sort<<<(b.n_active + 127) / 128, 128, 0, s>>>(b.active, b.n_active, b.tile_offset, b.tile_blobs);
-      check_launch("tile_sort");
+      prof_end(P_SETUP, s, "tile_sort");
     }
   }
 }
@@ -306,6 +311,8 @@ void launch_spread(const BlobSet& b, Dims d, const double* lam, const double* co
                    int accumulate, cudaStream_t s) {
   if (!accumulate) IBRD_CUDA(cudaMemsetAsync(out, 0, sizeof(T) * d.n(), s));
   if (b.n == 0 || b.n_active == 0) return;
+  const int c = pcls<T>(P_SPREAD64, P_SPREAD32);
+  prof_begin(c, s);
   if (sizeof(T) == 8)
     k_spread<T, double><<<b.n_active, dim3(kTile, kTile, kTile), 0, s>>>(
         b.active, b.tile_offset, b.tile_blobs, b.idx, b.w64, lam, nullptr, coef, scale, out, 1, d.nx, d.ny, d.nz,
@@ -314,12 +321,14 @@ void launch_spread(const BlobSet& b, Dims d, const double* lam, const double* co
     k_spread<T, float><<<b.n_active, dim3(kTile, kTile, kTile), 0, s>>>(
         b.active, b.tile_offset, b.tile_blobs, b.idx, b.w32, lam, nullptr, coef, scale, out, 1, d.nx, d.ny, d.nz,
         b.ntx, b.nty);
-  check_launch("spread");
+  prof_end(c, s, "spread", (double)b.n * (64.0 * 2.0 * sizeof(T) + 48.0 + 12.0 * sizeof(T) + 16.0));
 }
 
 template <typename T>
 void launch_spread_const(const BlobSet& b, Dims d, const double* cval, double scale, T* out, cudaStream_t s) {
   if (b.n == 0 || b.n_active == 0) return;
+  const int c = pcls<T>(P_SPREAD64, P_SPREAD32);
+  prof_begin(c, s);
   if (sizeof(T) == 8)
     k_spread<T, double><<<b.n_active, dim3(kTile, kTile, kTile), 0, s>>>(
         b.active, b.tile_offset, b.tile_blobs, b.idx, b.w64, nullptr, cval, nullptr, scale, out, 1, d.nx, d.ny,
@@ -328,7 +337,7 @@ void launch_spread_const(const BlobSet& b, Dims d, const double* cval, double sc
     k_spread<T, float><<<b.n_active, dim3(kTile, kTile, kTile), 0, s>>>(
         b.active, b.tile_offset, b.tile_blobs, b.idx, b.w32, nullptr, cval, nullptr, scale, out, 1, d.nx, d.ny,
         d.nz, b.ntx, b.nty);
-  check_launch("spread_const");
+  prof_end(c, s, "spread_const", (double)b.n * (64.0 * 2.0 * sizeof(T) + 48.0 + 12.0 * sizeof(T)));
 }
 
 template <typename T>
@@ -336,11 +345,13 @@ void launch_interp(const BlobSet& b, Dims d, const T* x, double scale, double* o
   if (b.n == 0) return;
   const int threads = 256;
   const int blocks = (int)(((size_t)b.n * 32 + threads - 1) / threads);
+  const int c = pcls<T>(P_INTERP64, P_INTERP32);
+  prof_begin(c, s);
   if (sizeof(T) == 8)
     k_interp<T, double><<<blocks, threads, 0, s>>>(b.idx, b.w64, x, scale, out, b.n, d.nx, d.ny);
   else
     k_interp<T, float><<<blocks, threads, 0, s>>>(b.idx, b.w32, x, scale, out, b.n, d.nx, d.ny);
-  check_launch("interp");
+  prof_end(c, s, "interp", (double)b.n * (64.0 * sizeof(T) + 48.0 + 12.0 * sizeof(T) + 8.0));
 }
 
 template void launch_spread<double>(const BlobSet&, Dims, const double*, const double*, double, double*, int,

@@ -316,29 +316,37 @@ inline int stream_blocks(size_t n, int threads) {
 template <typename T>
 void launch_apply_A(const T* x, T* y, Dims d, Stencil st, cudaStream_t s) {
   dim3 g((d.nx + BX - 1) / BX, (d.ny + BY - 1) / BY, (d.nz + ZCH - 1) / ZCH);
+  const int c = pcls<T>(P_APPLY64, P_APPLY32);
+  prof_begin(c, s);
   k_apply<T, false><<<g, dim3(BX, BY), 0, s>>>(x, nullptr, y, d.nx, d.ny, d.nz, (T)st.diag, (T)st.off);
-  check_launch("apply_A");
+  prof_end(c, s, "apply_A", 2.0 * sizeof(T) * d.n());
 }
 
 template <typename T>
 void launch_residual(const T* x, const T* b, T* y, Dims d, Stencil st, cudaStream_t s) {
   dim3 g((d.nx + BX - 1) / BX, (d.ny + BY - 1) / BY, (d.nz + ZCH - 1) / ZCH);
+  const int c = pcls<T>(P_APPLY64, P_APPLY32);
+  prof_begin(c, s);
   k_apply<T, true><<<g, dim3(BX, BY), 0, s>>>(x, b, y, d.nx, d.ny, d.nz, (T)st.diag, (T)st.off);
-  check_launch("residual");
+  prof_end(c, s, "residual", 3.0 * sizeof(T) * d.n());
 }
 
 template <typename T>
 void launch_rbgs(T* x, const T* b, const double* bshift, Dims d, Stencil st, int colour, cudaStream_t s) {
   const int np = d.nx / 2;
   dim3 g((np + BX - 1) / BX, (d.ny + BY - 1) / BY, (d.nz + ZCH - 1) / ZCH);
+  const int c = pcls<T>(P_RBGS64, P_RBGS32);
+  prof_begin(c, s);
   k_rbgs<T><<<g, dim3(BX, BY), 0, s>>>(x, b, bshift, d.nx, d.ny, d.nz, (T)(1.0 / st.diag), (T)st.off, colour);
-  check_launch("rbgs");
+  prof_end(c, s, "rbgs", 1.5 * sizeof(T) * d.n());
 }
 
 template <typename T>
 void launch_rbgs_zero(T* x, const T* b, const double* bshift, Dims d, Stencil st, cudaStream_t s) {
+  const int c = pcls<T>(P_RBGS64, P_RBGS32);
+  prof_begin(c, s);
   k_rbgs_zero<T><<<stream_blocks(d.n(), 256), 256, 0, s>>>(x, b, bshift, d.nx, d.ny, d.nz, (T)(1.0 / st.diag));
-  check_launch("rbgs_zero");
+  prof_end(c, s, "rbgs_zero", 1.5 * sizeof(T) * d.n());
 }
 
 template <typename T>
@@ -347,73 +355,88 @@ void launch_residual_restrict(const T* x, const T* b, const double* bshift, T* b
   const int nxc = d.nx / 2, nyc = d.ny / 2, nzc = d.nz / 2;
   dim3 blk(nxc >= 32 ? 32 : nxc, 4, 2);
   dim3 g((nxc + blk.x - 1) / blk.x, (nyc + blk.y - 1) / blk.y, (nzc + blk.z - 1) / blk.z);
+  const int c = pcls<T>(P_RESTRICT64, P_RESTRICT32);
+  prof_begin(c, s);
   k_residual_restrict<T><<<g, blk, 0, s>>>(x, b, bshift, bc, d.nx, d.ny, d.nz, (T)st.diag, (T)st.off);
-  check_launch("residual_restrict");
+  prof_end(c, s, "residual_restrict", 2.125 * sizeof(T) * d.n());
 }
 
 template <typename T>
 void launch_prolong_add(const T* xc, T* x, Dims d, cudaStream_t s) {
   dim3 blk(d.nx >= 64 ? 64 : d.nx, 2, 2);
   dim3 g((d.nx + blk.x - 1) / blk.x, (d.ny + blk.y - 1) / blk.y, (d.nz + blk.z - 1) / blk.z);
+  const int c = pcls<T>(P_PROLONG64, P_PROLONG32);
+  prof_begin(c, s);
   k_prolong_add<T><<<g, blk, 0, s>>>(xc, x, d.nx, d.ny, d.nz);
-  check_launch("prolong_add");
+  prof_end(c, s, "prolong_add", 2.125 * sizeof(T) * d.n());
 }
 
 template <typename T>
 void launch_coarse_solve(const T* table, const T* b, T* x, Dims dc, cudaStream_t s) {
+  prof_begin(P_COARSE, s);
   k_coarse_solve<T><<<1, 256, 0, s>>>(table, b, x, dc.nx, dc.ny, dc.nz);
-  check_launch("coarse_solve");
+  prof_end(P_COARSE, s, "coarse_solve", 3.0 * sizeof(T) * dc.n());
 }
 
 template <typename T>
 void launch_coarse_table(T* table, Dims dc, Stencil st, int singular, cudaStream_t s) {
   const int n = (int)dc.n();
+  prof_begin(P_SETUP, s);
   k_coarse_table<T><<<(n + 127) / 128, 128, 0, s>>>(table, dc.nx, dc.ny, dc.nz, st.diag, st.off, singular);
-  check_launch("coarse_table");
+  prof_end(P_SETUP, s, "coarse_table");
 }
 
 template <typename T>
 void launch_sum(const T* x, size_t n, double* partial, double* out, double scale, cudaStream_t s) {
+  prof_begin(P_DOT, s);
   k_sum_partial<T><<<kRedBlocks, kRedThreads, 0, s>>>(x, n, partial);
-  check_launch("sum_partial");
+  prof_end(P_DOT, s, "sum_partial", 1.0 * sizeof(T) * n);
+  prof_begin(P_REDUCE, s);
   k_finalize<<<1, kRedThreads, 0, s>>>(partial, kRedBlocks, out, scale);
-  check_launch("finalize");
+  prof_end(P_REDUCE, s, "finalize");
 }
 
 void launch_dot(const double* x, const double* y, size_t n, double* partial, double* out, double scale,
                 cudaStream_t s) {
+  prof_begin(P_DOT, s);
   k_dot_partial<<<kRedBlocks, kRedThreads, 0, s>>>(x, y, n, partial);
-  check_launch("dot_partial");
+  prof_end(P_DOT, s, "dot_partial", 16.0 * n);
+  prof_begin(P_REDUCE, s);
   k_finalize<<<1, kRedThreads, 0, s>>>(partial, kRedBlocks, out, scale);
-  check_launch("finalize");
+  prof_end(P_REDUCE, s, "finalize");
 }
 
 template <typename T>
 void launch_sub_scalar(T* x, size_t n, const double* mean, cudaStream_t s) {
+  prof_begin(P_VEC, s);
   k_sub_scalar<T><<<stream_blocks(n, 256), 256, 0, s>>>(x, n, mean);
-  check_launch("sub_scalar");
+  prof_end(P_VEC, s, "sub_scalar", 2.0 * sizeof(T) * n);
 }
 
 template <typename Tx, typename Ty>
 void launch_convert(const Tx* x, Ty* y, size_t n, double a, const double* shift, cudaStream_t s) {
+  prof_begin(P_VEC, s);
   k_convert<Tx, Ty><<<stream_blocks(n, 256), 256, 0, s>>>(x, y, n, a, shift);
-  check_launch("convert");
+  prof_end(P_VEC, s, "convert", (double)(sizeof(Tx) + sizeof(Ty)) * n);
 }
 
 void launch_axpby(double a, const double* x, double b, double* y, size_t n, cudaStream_t s) {
+  prof_begin(P_VEC, s);
   k_axpby<<<stream_blocks(n, 256), 256, 0, s>>>(a, x, b, y, n);
-  check_launch("axpby");
+  prof_end(P_VEC, s, "axpby", (b == 0.0 ? 16.0 : 24.0) * n);
 }
 
 void launch_scale_by_inv(const double* x, double* y, size_t n, const double* den, double num, cudaStream_t s) {
+  prof_begin(P_VEC, s);
   k_scale_by_inv<<<stream_blocks(n, 256), 256, 0, s>>>(x, y, n, den, num);
-  check_launch("scale_by_inv");
+  prof_end(P_VEC, s, "scale_by_inv", 16.0 * n);
 }
 
 template <typename T>
 void launch_nonfinite(const T* x, size_t n, int* flag, cudaStream_t s) {
+  prof_begin(P_SETUP, s);
   k_nonfinite<T><<<stream_blocks(n, 256), 256, 0, s>>>(x, n, flag);
-  check_launch("nonfinite");
+  prof_end(P_SETUP, s, "nonfinite", 1.0 * sizeof(T) * n);
 }
 
 #define IBRD_INST(T)                                                                                   \

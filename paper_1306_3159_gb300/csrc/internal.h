@@ -30,6 +30,23 @@ inline void check_launch(const char* what) {
   if (e != cudaSuccess) throw CudaError{e, what};
 }
 
+// ---------------------------------------------------------------- profiling
+// Kernel classes timed by the launch profiler (names in api.cu).
+enum ProfClass {
+  P_APPLY64, P_APPLY32, P_RBGS64, P_RBGS32, P_RESTRICT64, P_RESTRICT32, P_PROLONG64, P_PROLONG32,
+  P_COARSE, P_SPREAD64, P_SPREAD32, P_INTERP64, P_INTERP32, P_DOT, P_AXPY, P_REDUCE, P_VEC, P_SMALL,
+  P_SETUP, P_NCLASS
+};
+// Every launch in the library is bracketed by prof_begin / prof_end: the
+// pair counts the launch, checks it, and (when the calling handle has
+// profiling on) records CUDA events around it on stream s.
+void prof_begin(int cls, cudaStream_t s);
+// `bytes` is the algorithmic traffic of the launch (each input read once, each
+// output written once), used for achieved-bandwidth reports.
+void prof_end(int cls, cudaStream_t s, const char* what, double bytes = 0.0);
+template <typename T>
+constexpr int pcls(int c64, int c32) { return sizeof(T) == 4 ? c32 : c64; }
+
 // ---------------------------------------------------------------- geometry
 struct Dims {
   int nx, ny, nz;

@@ -230,6 +230,8 @@ __global__ void __launch_bounds__(kSmallThreads) k_small_finish(const double* __
 
 void launch_multidot(const double* V, size_t ldv, int nvec, const double* w, size_t n, double* partial,
                      cudaStream_t s) {
+  if (nvec < 1 || nvec > kDotGroup) return;
+  prof_begin(P_DOT, s);
   switch (nvec) {
 #define IBRD_CASE(k) \
   case k: k_multidot<k><<<kRedBlocks, kRedThreads, 0, s>>>(V, ldv, w, n, partial); break;
@@ -237,17 +239,20 @@ void launch_multidot(const double* V, size_t ldv, int nvec, const double* w, siz
 #undef IBRD_CASE
     default: return;
   }
-  check_launch("multidot");
+  prof_end(P_DOT, s, "multidot", 8.0 * (nvec + 1) * n);
 }
 
 void launch_reduce_partials(const double* partial, int nvec, double* out, cudaStream_t s) {
   if (nvec <= 0) return;
+  prof_begin(P_REDUCE, s);
   k_reduce_partials<<<nvec, kRedThreads, 0, s>>>(partial, out);
-  check_launch("reduce_partials");
+  prof_end(P_REDUCE, s, "reduce_partials");
 }
 
 void launch_multi_axpy(double* w, const double* V, size_t ldv, int nvec, const double* coef, double sign, size_t n,
                        double* partial_sq, cudaStream_t s) {
+  if (nvec < 1 || nvec > kDotGroup) return;
+  prof_begin(P_AXPY, s);
   if (partial_sq) {
     switch (nvec) {
 #define IBRD_CASE(k)                                                                                       \
@@ -267,44 +272,51 @@ void launch_multi_axpy(double* w, const double* V, size_t ldv, int nvec, const d
       default: return;
     }
   }
-  check_launch("multi_axpy");
+  prof_end(P_AXPY, s, "multi_axpy", 8.0 * (nvec + 2) * n);
 }
 
 void launch_givens(double* H, int ldh, int j, double* cs, double* sn, double* gvec, double* res, cudaStream_t s) {
+  prof_begin(P_SMALL, s);
   k_givens<<<1, 32, 0, s>>>(H, ldh, j, cs, sn, gvec, res);
-  check_launch("givens");
+  prof_end(P_SMALL, s, "givens");
 }
 
 void launch_backsolve(const double* H, int ldh, int k, const double* gvec, double* y, cudaStream_t s) {
+  prof_begin(P_SMALL, s);
   k_backsolve<<<1, 32, 0, s>>>(H, ldh, k, gvec, y);
-  check_launch("backsolve");
+  prof_end(P_SMALL, s, "backsolve");
 }
 
 void launch_vec_add_small(double* h, const double* h2, int n, cudaStream_t s) {
+  prof_begin(P_SMALL, s);
   k_vec_add_small<<<1, 64, 0, s>>>(h, h2, n);
-  check_launch("vec_add_small");
+  prof_end(P_SMALL, s, "vec_add_small");
 }
 
 void launch_sqrt_scalar(const double* src, double* dst, cudaStream_t s) {
+  prof_begin(P_SMALL, s);
   k_sqrt_scalar<<<1, 32, 0, s>>>(src, dst);
-  check_launch("sqrt_scalar");
+  prof_end(P_SMALL, s, "sqrt_scalar");
 }
 
 void launch_small_start(const double* r, double* U0, int n, double* gvec, int m, cudaStream_t s) {
+  prof_begin(P_SMALL, s);
   k_small_start<<<1, kSmallThreads, 0, s>>>(r, U0, n, gvec, m);
-  check_launch("small_start");
+  prof_end(P_SMALL, s, "small_start");
 }
 
 void launch_small_arnoldi(double* U, int n, int j, double* Hs, int ldh, double* cs, double* sn, double* gvec,
                           cudaStream_t s) {
+  prof_begin(P_SMALL, s);
   k_small_arnoldi<<<1, kSmallThreads, 0, s>>>(U, n, j, Hs, ldh, cs, sn, gvec);
-  check_launch("small_arnoldi");
+  prof_end(P_SMALL, s, "small_arnoldi");
 }
 
 void launch_small_finish(const double* U, int n, int k, const double* Hs, int ldh, const double* gvec, double* x,
                          int project_mean, cudaStream_t s) {
+  prof_begin(P_SMALL, s);
   k_small_finish<<<1, kSmallThreads, 0, s>>>(U, n, k, Hs, ldh, gvec, x, project_mean);
-  check_launch("small_finish");
+  prof_end(P_SMALL, s, "small_finish");
 }
 
 }  // namespace ibrd

@@ -1,8 +1,12 @@
 """Solve-level parity of the CUDA path with the FP64 oracle's exact solutions.
 
-The GPU solves to a relative true residual of 1e-13 (FP64); the solution error
-is then bounded by the condition number times the residual, and the test
-requires the 1e-11 relative error stated as the FP64 target. The mixed FP32
+The FP64 GPU path solves to a relative true residual of 1e-12. That is near
+the rounding floor of FP64 here: in the steady periodic case c carries a large
+constant cbar (about 1e3 for a unit source at 32^3), and A c is formed from
+values of that size, so its rounding is about 6 eps cbar per cell, i.e. a
+relative residual of a few 1e-13. The error in c and lambda is bounded by the
+condition number on mean-zero fields (about 30 at 32^3) times the residual
+relative to ||c||, far below the 1e-11 relative error the tests require. The mixed FP32
 path solves to 1e-10 and must be within 1e-8 of the exact solution.
 """
 import math
@@ -40,7 +44,7 @@ def _grid(ibrd, w, alpha=0.0, kernel=4):
     return g
 
 
-@pytest.mark.parametrize("precision,tol,err", [(0, 1e-13, 1e-11), (1, 1e-10, 1e-8)])
+@pytest.mark.parametrize("precision,tol,err", [(0, 1e-12, 1e-11), (1, 1e-10, 1e-8)])
 def test_saddle_small(ibrd, small, precision, tol, err):
     w, M = small
     c_ref, lam_ref, _ = direct.solve_saddle(w.q, w.g, w.h, w.chi, 0.0, M=M)
@@ -55,7 +59,7 @@ def test_saddle_small(ibrd, small, precision, tol, err):
     assert abs(info["rate_K"] - K_ref) < err * abs(K_ref)
 
 
-@pytest.mark.parametrize("precision,tol,err", [(0, 1e-13, 1e-11), (1, 1e-10, 1e-8)])
+@pytest.mark.parametrize("precision,tol,err", [(0, 1e-12, 1e-11), (1, 1e-10, 1e-8)])
 @pytest.mark.parametrize("alpha", [0.0, 0.2])
 def test_reaction_small(ibrd, small, precision, tol, err, alpha):
     w, M0 = small
@@ -78,7 +82,7 @@ def test_saddle_alpha_positive_nonunit_scales(ibrd):
     c_ref, lam_ref, _ = direct.solve_saddle(q, gsrc, h, chi, alpha, zeta=zeta, f=f)
     g = ibrd.Grid(*dims, h=h, chi=chi, alpha=alpha)
     g.set_blobs(dev(q))
-    c, lam, info = g.solve_saddle(dev(gsrc), f=dev(f), tol=1e-13, zeta=zeta, max_iter=400)
+    c, lam, info = g.solve_saddle(dev(gsrc), f=dev(f), tol=1e-12, zeta=zeta, max_iter=400)
     assert rel_l2(host(c), c_ref) < 1e-11
     assert rel_l2(host(lam), lam_ref) < 1e-11
 
@@ -88,7 +92,7 @@ def test_saddle_tiny_single_blob(ibrd):
     w = workload("tiny")
     c_ref, lam_ref, _ = direct.solve_saddle(w.q, w.g, w.h, w.chi, 0.0)
     g = _grid(ibrd, w)
-    c, lam, info = g.solve_saddle(dev(w.g), tol=1e-13, max_iter=400)
+    c, lam, info = g.solve_saddle(dev(w.g), tol=1e-12, max_iter=400)
     assert rel_l2(host(c), c_ref) < 1e-11
     assert abs(host(lam)[0] - lam_ref[0]) < 1e-11 * abs(lam_ref[0])
 
@@ -97,7 +101,7 @@ def test_saddle_diagonal_preconditioner(ibrd, small):
     w, M = small
     c_ref, lam_ref, _ = direct.solve_saddle(w.q, w.g, w.h, w.chi, 0.0, M=M)
     g = _grid(ibrd, w)
-    c, lam, info = g.solve_saddle(dev(w.g), tol=1e-13, precond=1, restart=60, max_iter=2000)
+    c, lam, info = g.solve_saddle(dev(w.g), tol=1e-12, precond=1, restart=60, max_iter=2000)
     assert rel_l2(host(lam), lam_ref) < 1e-11
 
 
@@ -108,9 +112,9 @@ def test_single_blob_finite_rate_shift(ibrd):
     gsrc = np.full((L, L, L), 1.0 / L ** 3)
     g = ibrd.Grid(L, L, L)
     g.set_blobs(dev(q))
-    c0, lam, _ = g.solve_saddle(dev(gsrc), tol=1e-13, max_iter=400)
+    c0, lam, _ = g.solve_saddle(dev(gsrc), tol=1e-12, max_iter=400)
     for kappa in (0.5, 7.0):
-        cP, _ = g.solve_reaction(dev(np.array([kappa])), dev(gsrc), tol=1e-13, max_iter=400)
+        cP, _ = g.solve_reaction(dev(np.array([kappa])), dev(gsrc), tol=1e-12, max_iter=400)
         d = host(cP) - host(c0)
         assert np.abs(d - 1.0 / kappa).max() < 1e-9
 
