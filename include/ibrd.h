@@ -171,11 +171,14 @@ typedef struct {
   double ms[IBRD_PROF_NCLASS];        /* summed event time per class, milliseconds */
   double bytes[IBRD_PROF_NCLASS];     /* summed algorithmic bytes per class: each
                                          input read once, each output written once */
+  double max_launch_bytes[IBRD_PROF_NCLASS]; /* largest single launch of the class */
+  double timed_bytes[IBRD_PROF_NCLASS];      /* algorithmic bytes of the timed launches */
 } ibrd_profile;
 
 /* Time the launches of every class c with bit c set in class_mask (0 turns
-   timing off). Counting is always on. */
-ibrd_status ibrd_profile_enable(ibrd_grid g, unsigned class_mask);
+   timing off) whose algorithmic bytes are >= min_bytes (e.g. only the finest
+   multigrid level). Counting is always on. */
+ibrd_status ibrd_profile_enable(ibrd_grid g, unsigned class_mask, double min_bytes);
 
 /* Synchronize the handle's stream and report counts and times since the last
    reset; reset != 0 clears them. */

@@ -45,7 +45,8 @@ class SolveInfo(ctypes.Structure):
 class Profile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_longlong), ("nclass", ctypes.c_int), ("overflow", ctypes.c_int),
                 ("count", ctypes.c_longlong * PROF_NCLASS), ("timed", ctypes.c_longlong * PROF_NCLASS),
-                ("ms", ctypes.c_double * PROF_NCLASS), ("bytes", ctypes.c_double * PROF_NCLASS)]
+                ("ms", ctypes.c_double * PROF_NCLASS), ("bytes", ctypes.c_double * PROF_NCLASS),
+                ("max_launch_bytes", ctypes.c_double * PROF_NCLASS), ("timed_bytes", ctypes.c_double * PROF_NCLASS)]
 
 
 class IbrdError(RuntimeError):
@@ -92,7 +93,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ibrd_last_error.restype = ctypes.c_char_p
     lib.ibrd_status_string.argtypes = [i]
     lib.ibrd_status_string.restype = ctypes.c_char_p
-    lib.ibrd_profile_enable.argtypes = [vp, ctypes.c_uint]
+    lib.ibrd_profile_enable.argtypes = [vp, ctypes.c_uint, d]
     lib.ibrd_profile_enable.restype = i
     lib.ibrd_profile_read.argtypes = [vp, P(Profile), i]
     lib.ibrd_profile_read.restype = i
@@ -226,11 +227,12 @@ def profile_class_names():
     return [lib.ibrd_profile_class_name(c).decode() for c in range(PROF_NCLASS)]
 
 
-def ibrd_profile_enable(g, class_mask=PROF_ALL):
-    """Time the kernel classes in class_mask (bit per class; True = all)."""
+def ibrd_profile_enable(g, class_mask=PROF_ALL, min_bytes=0.0):
+    """Time the kernel classes in class_mask (bit per class; True = all),
+    only launches with at least min_bytes algorithmic bytes."""
     if class_mask is True:
         class_mask = PROF_ALL
-    _check(g, load_library().ibrd_profile_enable(g, int(class_mask)))
+    _check(g, load_library().ibrd_profile_enable(g, int(class_mask), float(min_bytes)))
 
 
 def ibrd_profile_read(g, reset=True) -> dict:
@@ -243,7 +245,8 @@ def ibrd_profile_read(g, reset=True) -> dict:
         if pr.count[c]:
             classes[lib.ibrd_profile_class_name(c).decode()] = {
                 "id": c, "launches": int(pr.count[c]), "timed": int(pr.timed[c]), "ms": float(pr.ms[c]),
-                "bytes": float(pr.bytes[c])}
+                "bytes": float(pr.bytes[c]), "max_launch_bytes": float(pr.max_launch_bytes[c]),
+                "timed_bytes": float(pr.timed_bytes[c])}
     return {"launches": int(pr.launches), "overflow": bool(pr.overflow), "classes": classes}
 
 

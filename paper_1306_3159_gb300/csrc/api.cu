@@ -62,6 +62,7 @@ __global__ void k_set_gvec(double* gvec, int m, const double* beta) {
 template <typename T>
 struct Hier {
   std::vector<T*> x, b;                       // levels >= 1 (index = level)
+  std::vector<T*> y;                          // smoothing scratch, every level
   T* f0 = nullptr;                            // level-0 scratch fields (mixed path)
   T* f1 = nullptr;
   std::vector<std::pair<double, T*>> tables;  // coarsest Green's tables by shift
@@ -79,13 +80,17 @@ struct Level {
 struct Profiler {
   bool timing = false;
   unsigned mask = 0;      // classes timed when timing is on
+  double min_bytes = 0.0; // only launches with at least this many algorithmic bytes are timed
   bool overflow = false;
   long long launches = 0;
   long long count[P_NCLASS] = {};
   double bytes[P_NCLASS] = {};
+  double max_bytes[P_NCLASS] = {};
+  double timed_bytes[P_NCLASS] = {};
   std::vector<cudaEvent_t> pool;
   size_t used = 0;
   std::vector<std::pair<int, size_t>> pending;
+  std::vector<double> pending_bytes;
   int open_cls = -1;
   size_t open_idx = 0;
 };
@@ -122,10 +127,16 @@ void prof_end(int cls, cudaStream_t s, const char* what, double bytes) {
   p->launches++;
   p->count[cls]++;
   p->bytes[cls] += bytes;
+  if (bytes > p->max_bytes[cls]) p->max_bytes[cls] = bytes;
   if (p->open_cls == cls) {
+    p->open_cls = -1;
+    if (bytes < p->min_bytes) {
+      p->used -= 2;  // not timed: return the unused event pair
+      return;
+    }
     IBRD_CUDA(cudaEventRecord(p->pool[p->open_idx + 1], s));
     p->pending.emplace_back(cls, p->open_idx);
-    p->open_cls = -1;
+    p->pending_bytes.push_back(bytes);
   }
 }
 
@@ -224,9 +235,13 @@ void ensure_hier(ibrd_grid g) {
   const size_t L = g->levels.size();
   H.x.assign(L, nullptr);
   H.b.assign(L, nullptr);
-  for (size_t l = 1; l < L; ++l) {
-    H.x[l] = dalloc<T>(g->levels[l].d.n());
-    H.b[l] = dalloc<T>(g->levels[l].d.n());
+  H.y.assign(L, nullptr);
+  for (size_t l = 0; l < L; ++l) {
+    if (l > 0) {
+      H.x[l] = dalloc<T>(g->levels[l].d.n());
+      H.b[l] = dalloc<T>(g->levels[l].d.n());
+    }
+    if (l + 1 < L) H.y[l] = dalloc<T>(g->levels[l].d.n());
   }
 }
 
@@ -242,7 +257,8 @@ const T* coarse_table(ibrd_grid g, double shift) {
   return t;
 }
 
-// One V-cycle on level l for A_l x = b - bshift (bshift nullable).
+// One V-cycle on level l for A_l x = b - bshift (bshift nullable). Smoothing
+// sweeps ping-pong between x and the level's scratch field.
 template <typename T>
 void vcycle_level(ibrd_grid g, int l, const T* b, const double* bshift, T* x, bool zero, double shift, int nu1,
                   int nu2) {
@@ -255,21 +271,20 @@ void vcycle_level(ibrd_grid g, int l, const T* b, const double* bshift, T* x, bo
     launch_coarse_solve<T>(coarse_table<T>(g, shift), b, x, lv.d, g->s);
     return;
   }
+  T* cur = x;
+  T* oth = H.y[l];
+  bool first = zero;
   if (nu1 == 0 && zero) IBRD_CUDA(cudaMemsetAsync(x, 0, sizeof(T) * lv.d.n(), g->s));
   for (int sweep = 0; sweep < nu1; ++sweep) {
-    if (sweep == 0 && zero)
-      launch_rbgs_zero<T>(x, b, bshift, lv.d, st, g->s);
-    else
-      launch_rbgs<T>(x, b, bshift, lv.d, st, 0, g->s);
-    launch_rbgs<T>(x, b, bshift, lv.d, st, 1, g->s);
+    if (launch_rb_sweep<T>(cur, oth, b, bshift, lv.d, st, first, g->s)) std::swap(cur, oth);
+    first = false;
   }
-  launch_residual_restrict<T>(x, b, bshift, H.b[l + 1], lv.d, st, g->s);
+  launch_resid_restrict<T>(cur, b, bshift, H.b[l + 1], lv.d, st, g->s);
   vcycle_level<T>(g, l + 1, H.b[l + 1], nullptr, H.x[l + 1], true, shift, nu1, nu2);
-  launch_prolong_add<T>(H.x[l + 1], x, lv.d, g->s);
-  for (int sweep = 0; sweep < nu2; ++sweep) {
-    launch_rbgs<T>(x, b, bshift, lv.d, st, 0, g->s);
-    launch_rbgs<T>(x, b, bshift, lv.d, st, 1, g->s);
-  }
+  launch_prolong8<T>(H.x[l + 1], cur, lv.d, g->s);
+  for (int sweep = 0; sweep < nu2; ++sweep)
+    if (launch_rb_sweep<T>(cur, oth, b, bshift, lv.d, st, false, g->s)) std::swap(cur, oth);
+  if (cur != x) IBRD_CUDA(cudaMemcpyAsync(x, cur, sizeof(T) * lv.d.n(), cudaMemcpyDeviceToDevice, g->s));
 }
 
 // One V-cycle on the finest level for (shift I - chi L) x = b. When shift is
@@ -777,8 +792,10 @@ void ibrd_grid_destroy(ibrd_grid g) {
   auto F = [](void* p) { if (p) cudaFree(p); };
   for (auto p : g->h64.x) F(p);
   for (auto p : g->h64.b) F(p);
+  for (auto p : g->h64.y) F(p);
   for (auto p : g->h32.x) F(p);
   for (auto p : g->h32.b) F(p);
+  for (auto p : g->h32.y) F(p);
   for (auto& e : g->h64.tables) F(e.second);
   for (auto& e : g->h32.tables) F(e.second);
   BlobSet& b = g->blobs;
@@ -998,10 +1015,11 @@ static const char* kProfNames[P_NCLASS] = {
 
 const char* ibrd_profile_class_name(int cls) { return (cls >= 0 && cls < P_NCLASS) ? kProfNames[cls] : ""; }
 
-ibrd_status ibrd_profile_enable(ibrd_grid g, unsigned class_mask) {
+ibrd_status ibrd_profile_enable(ibrd_grid g, unsigned class_mask, double min_bytes) {
   return guarded(g, "ibrd_profile_enable", [&]() {
     g->prof.timing = class_mask != 0;
     g->prof.mask = class_mask;
+    g->prof.min_bytes = min_bytes;
     return IBRD_OK;
   });
 }
@@ -1018,18 +1036,23 @@ ibrd_status ibrd_profile_read(ibrd_grid g, ibrd_profile* out, int reset) {
     for (int c = 0; c < P_NCLASS; ++c) {
       out->count[c] = p.count[c];
       out->bytes[c] = p.bytes[c];
+      out->max_launch_bytes[c] = p.max_bytes[c];
     }
-    for (auto& e : p.pending) {
+    for (size_t i = 0; i < p.pending.size(); ++i) {
+      const auto& e = p.pending[i];
       float ms = 0.f;
       IBRD_CUDA(cudaEventElapsedTime(&ms, p.pool[e.second], p.pool[e.second + 1]));
       out->ms[e.first] += ms;
       out->timed[e.first] += 1;
+      out->timed_bytes[e.first] += p.pending_bytes[i];
     }
     if (reset) {
       p.launches = 0;
       for (auto& c : p.count) c = 0;
       for (auto& b : p.bytes) b = 0.0;
+      for (auto& b : p.max_bytes) b = 0.0;
       p.pending.clear();
+      p.pending_bytes.clear();
       p.used = 0;
       p.overflow = false;
     }

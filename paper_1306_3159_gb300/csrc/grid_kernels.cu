@@ -19,11 +19,6 @@ constexpr int BX = 32, BY = 8, ZCH = 16;
 __device__ __forceinline__ int wrap_dec(int i, int n) { return i == 0 ? n - 1 : i - 1; }
 __device__ __forceinline__ int wrap_inc(int i, int n) { return i == n - 1 ? 0 : i + 1; }
 
-template <typename T>
-__device__ __forceinline__ T bval(const T* __restrict__ b, size_t p, const double* __restrict__ bshift) {
-  return bshift ? b[p] - (T)(*bshift) : b[p];
-}
-
 // y = A x (RESID = false) or y = b - A x (RESID = true); 2.5D z-march with the
 // z-neighbours kept in registers and x/y neighbours served by L1.
 template <typename T, bool RESID>
@@ -51,108 +46,6 @@ __global__ void __launch_bounds__(BX* BY) k_apply(const T* __restrict__ x, const
     xm = x0;
     x0 = xp;
   }
-}
-
-// Red-black Gauss-Seidel half sweep. Each thread owns an x-pair (2p, 2p+1)
-// of a row and marches in z; at plane k exactly one cell of the pair has the
-// active colour. Requires even nx, ny, nz (true on every smoothed level).
-template <typename T>
-__global__ void __launch_bounds__(BX* BY) k_rbgs(T* __restrict__ x, const T* __restrict__ b,
-                                                 const double* __restrict__ bshift, int nx, int ny, int nz,
-                                                 T inv_diag, T off, int colour) {
-  const int p = blockIdx.x * BX + threadIdx.x;
-  const int j = blockIdx.y * BY + threadIdx.y;
-  const int np = nx >> 1;
-  if (p >= np || j >= ny) return;
-  const int k0 = blockIdx.z * ZCH;
-  const int k1 = min(k0 + ZCH, nz);
-  const size_t plane = (size_t)nx * ny;
-  const size_t rj = (size_t)j * nx, rjm = (size_t)wrap_dec(j, ny) * nx, rjp = (size_t)wrap_inc(j, ny) * nx;
-  const T sh = bshift ? (T)(*bshift) : (T)0;
-  for (int k = k0; k < k1; ++k) {
-    const int par = (colour + j + k) & 1;
-    const int ia = 2 * p + par;
-    const int iw = wrap_dec(ia, nx), ie = wrap_inc(ia, nx);
-    const size_t base = (size_t)k * plane;
-    const T s = ((x[base + rj + iw] + x[base + rj + ie]) + (x[base + rjm + ia] + x[base + rjp + ia])) +
-                (x[(size_t)wrap_dec(k, nz) * plane + rj + ia] + x[(size_t)wrap_inc(k, nz) * plane + rj + ia]);
-    x[base + rj + ia] = ((b[base + rj + ia] - sh) + off * s) * inv_diag;
-  }
-}
-
-// First red half sweep from x = 0: red cells (b - shift)/diag, black cells 0.
-template <typename T>
-__global__ void k_rbgs_zero(T* __restrict__ x, const T* __restrict__ b, const double* __restrict__ bshift,
-                            int nx, int ny, int nz, T inv_diag) {
-  const size_t n = (size_t)nx * ny * nz;
-  const T sh = bshift ? (T)(*bshift) : (T)0;
-  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(q % nx);
-    const size_t r = q / nx;
-    const int j = (int)(r % ny);
-    const int k = (int)(r / ny);
-    x[q] = ((i + j + k) & 1) ? (T)0 : (b[q] - sh) * inv_diag;
-  }
-}
-
-// Coarse cell (I, J, K) receives the mean of the residual b - shift - A x over
-// its 8 fine children.
-template <typename T>
-__global__ void k_residual_restrict(const T* __restrict__ x, const T* __restrict__ b,
-                                    const double* __restrict__ bshift, T* __restrict__ bc, int nx, int ny,
-                                    int nz, T diag, T off) {
-  const int nxc = nx >> 1, nyc = ny >> 1, nzc = nz >> 1;
-  const int I = blockIdx.x * blockDim.x + threadIdx.x;
-  const int J = blockIdx.y * blockDim.y + threadIdx.y;
-  const int K = blockIdx.z * blockDim.z + threadIdx.z;
-  if (I >= nxc || J >= nyc || K >= nzc) return;
-  const size_t plane = (size_t)nx * ny;
-  const T sh = bshift ? (T)(*bshift) : (T)0;
-  T acc = 0;
-#pragma unroll
-  for (int c = 0; c < 2; ++c) {
-    const int k = 2 * K + c;
-    const size_t pk = (size_t)k * plane, pkm = (size_t)wrap_dec(k, nz) * plane, pkp = (size_t)wrap_inc(k, nz) * plane;
-#pragma unroll
-    for (int bb = 0; bb < 2; ++bb) {
-      const int j = 2 * J + bb;
-      const size_t rj = (size_t)j * nx, rjm = (size_t)wrap_dec(j, ny) * nx, rjp = (size_t)wrap_inc(j, ny) * nx;
-#pragma unroll
-      for (int a = 0; a < 2; ++a) {
-        const int i = 2 * I + a;
-        const T s = ((x[pk + rj + wrap_dec(i, nx)] + x[pk + rj + wrap_inc(i, nx)]) +
-                     (x[pk + rjm + i] + x[pk + rjp + i])) +
-                    (x[pkm + rj + i] + x[pkp + rj + i]);
-        acc += (b[pk + rj + i] - sh) - (diag * x[pk + rj + i] - off * s);
-      }
-    }
-  }
-  bc[((size_t)K * nyc + J) * nxc + I] = acc * (T)0.125;
-}
-
-// x_fine += trilinear cell-centred interpolation of the coarse correction.
-template <typename T>
-__global__ void k_prolong_add(const T* __restrict__ xc, T* __restrict__ x, int nx, int ny, int nz) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int k = blockIdx.z * blockDim.z + threadIdx.z;
-  if (i >= nx || j >= ny || k >= nz) return;
-  const int nxc = nx >> 1, nyc = ny >> 1, nzc = nz >> 1;
-  const int I = i >> 1, J = j >> 1, K = k >> 1;
-  const int I2 = (i & 1) ? wrap_inc(I, nxc) : wrap_dec(I, nxc);
-  const int J2 = (j & 1) ? wrap_inc(J, nyc) : wrap_dec(J, nyc);
-  const int K2 = (k & 1) ? wrap_inc(K, nzc) : wrap_dec(K, nzc);
-  const size_t pc = (size_t)nxc * nyc;
-  const size_t zA = (size_t)K * pc, zB = (size_t)K2 * pc;
-  const size_t yA = (size_t)J * nxc, yB = (size_t)J2 * nxc;
-  const T w3 = (T)0.75, w1 = (T)0.25;
-  const T rAA = w3 * xc[zA + yA + I] + w1 * xc[zA + yA + I2];
-  const T rAB = w3 * xc[zA + yB + I] + w1 * xc[zA + yB + I2];
-  const T rBA = w3 * xc[zB + yA + I] + w1 * xc[zB + yA + I2];
-  const T rBB = w3 * xc[zB + yB + I] + w1 * xc[zB + yB + I2];
-  const T pA = w3 * rAA + w1 * rAB;
-  const T pB = w3 * rBA + w1 * rBB;
-  x[((size_t)k * ny + j) * nx + i] += w3 * pA + w1 * pB;
 }
 
 // Dense circulant solve on the coarsest grid (at most 512 cells, one block).
@@ -217,23 +110,20 @@ __device__ __forceinline__ double block_sum(double v) {
   return v;
 }
 
+// Sum of x: each thread folds 8-element runs (FP32 inputs summed in FP32 within
+// a run, then in FP64) from a grid-stride loop with 4 independent runs in flight.
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads) k_sum_partial(const T* __restrict__ x, size_t n,
                                                              double* __restrict__ partial) {
   double acc = 0.0;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
-  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (sizeof(T) == 4) {
-    // FP32 input: sum runs of 16 strided values in FP32, fold into FP64.
-    while (i < n) {
-      float f = 0.f;
-#pragma unroll 4
-      for (int r = 0; r < 16 && i < n; ++r, i += stride) f += (float)x[i];
-      acc += (double)f;
-    }
-  } else {
-    for (; i < n; i += stride) acc += (double)x[i];
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  size_t i = t;
+  for (; i + 3 * stride < n; i += 4 * stride) {
+    const T a0 = x[i], a1 = x[i + stride], a2 = x[i + 2 * stride], a3 = x[i + 3 * stride];
+    acc += (double)((a0 + a1) + (a2 + a3));
   }
+  for (; i < n; i += stride) acc += (double)x[i];
   acc = block_sum(acc);
   if (threadIdx.x == 0) partial[blockIdx.x] = acc;
 }
@@ -332,46 +222,6 @@ void launch_residual(const T* x, const T* b, T* y, Dims d, Stencil st, cudaStrea
 }
 
 template <typename T>
-void launch_rbgs(T* x, const T* b, const double* bshift, Dims d, Stencil st, int colour, cudaStream_t s) {
-  const int np = d.nx / 2;
-  dim3 g((np + BX - 1) / BX, (d.ny + BY - 1) / BY, (d.nz + ZCH - 1) / ZCH);
-  const int c = pcls<T>(P_RBGS64, P_RBGS32);
-  prof_begin(c, s);
-  k_rbgs<T><<<g, dim3(BX, BY), 0, s>>>(x, b, bshift, d.nx, d.ny, d.nz, (T)(1.0 / st.diag), (T)st.off, colour);
-  prof_end(c, s, "rbgs", 1.5 * sizeof(T) * d.n());
-}
-
-template <typename T>
-void launch_rbgs_zero(T* x, const T* b, const double* bshift, Dims d, Stencil st, cudaStream_t s) {
-  const int c = pcls<T>(P_RBGS64, P_RBGS32);
-  prof_begin(c, s);
-  k_rbgs_zero<T><<<stream_blocks(d.n(), 256), 256, 0, s>>>(x, b, bshift, d.nx, d.ny, d.nz, (T)(1.0 / st.diag));
-  prof_end(c, s, "rbgs_zero", 1.5 * sizeof(T) * d.n());
-}
-
-template <typename T>
-void launch_residual_restrict(const T* x, const T* b, const double* bshift, T* bc, Dims d, Stencil st,
-                              cudaStream_t s) {
-  const int nxc = d.nx / 2, nyc = d.ny / 2, nzc = d.nz / 2;
-  dim3 blk(nxc >= 32 ? 32 : nxc, 4, 2);
-  dim3 g((nxc + blk.x - 1) / blk.x, (nyc + blk.y - 1) / blk.y, (nzc + blk.z - 1) / blk.z);
-  const int c = pcls<T>(P_RESTRICT64, P_RESTRICT32);
-  prof_begin(c, s);
-  k_residual_restrict<T><<<g, blk, 0, s>>>(x, b, bshift, bc, d.nx, d.ny, d.nz, (T)st.diag, (T)st.off);
-  prof_end(c, s, "residual_restrict", 2.125 * sizeof(T) * d.n());
-}
-
-template <typename T>
-void launch_prolong_add(const T* xc, T* x, Dims d, cudaStream_t s) {
-  dim3 blk(d.nx >= 64 ? 64 : d.nx, 2, 2);
-  dim3 g((d.nx + blk.x - 1) / blk.x, (d.ny + blk.y - 1) / blk.y, (d.nz + blk.z - 1) / blk.z);
-  const int c = pcls<T>(P_PROLONG64, P_PROLONG32);
-  prof_begin(c, s);
-  k_prolong_add<T><<<g, blk, 0, s>>>(xc, x, d.nx, d.ny, d.nz);
-  prof_end(c, s, "prolong_add", 2.125 * sizeof(T) * d.n());
-}
-
-template <typename T>
 void launch_coarse_solve(const T* table, const T* b, T* x, Dims dc, cudaStream_t s) {
   prof_begin(P_COARSE, s);
   k_coarse_solve<T><<<1, 256, 0, s>>>(table, b, x, dc.nx, dc.ny, dc.nz);
@@ -442,11 +292,6 @@ void launch_nonfinite(const T* x, size_t n, int* flag, cudaStream_t s) {
 #define IBRD_INST(T)                                                                                   \
   template void launch_apply_A<T>(const T*, T*, Dims, Stencil, cudaStream_t);                         \
   template void launch_residual<T>(const T*, const T*, T*, Dims, Stencil, cudaStream_t);              \
-  template void launch_rbgs<T>(T*, const T*, const double*, Dims, Stencil, int, cudaStream_t);        \
-  template void launch_rbgs_zero<T>(T*, const T*, const double*, Dims, Stencil, cudaStream_t);        \
-  template void launch_residual_restrict<T>(const T*, const T*, const double*, T*, Dims, Stencil,     \
-                                            cudaStream_t);                                            \
-  template void launch_prolong_add<T>(const T*, T*, Dims, cudaStream_t);                             \
   template void launch_coarse_solve<T>(const T*, const T*, T*, Dims, cudaStream_t);                   \
   template void launch_coarse_table<T>(T*, Dims, Stencil, int, cudaStream_t);                         \
   template void launch_sum<T>(const T*, size_t, double*, double*, double, cudaStream_t);              \

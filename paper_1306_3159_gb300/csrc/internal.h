@@ -71,20 +71,23 @@ void launch_apply_A(const T* x, T* y, Dims d, Stencil st, cudaStream_t s);
 // y = b - A x
 template <typename T>
 void launch_residual(const T* x, const T* b, T* y, Dims d, Stencil st, cudaStream_t s);
-// Red-black Gauss-Seidel half sweep on `colour` (0 = red: (i+j+k) even).
-// bshift (nullable, device scalar): uses b - *bshift in place of b.
+// One full red-black Gauss-Seidel sweep (red = (i+j+k) even) for A x = b -
+// *bshift (bshift nullable). On levels where the fused one-pass kernel
+// applies it reads xin and writes xout (xin != xout) and returns true; on
+// small levels it updates xin in place with two half sweeps and returns
+// false. zero != 0 treats the incoming x as 0.
 template <typename T>
-void launch_rbgs(T* x, const T* b, const double* bshift, Dims d, Stencil st, int colour, cudaStream_t s);
-// First red half sweep from a zero guess: x_red = (b - shift)/diag, x_black = 0.
+bool launch_rb_sweep(const T* xin, T* xout, const T* b, const double* bshift, Dims d, Stencil st, bool zero,
+                     cudaStream_t s);
 template <typename T>
-void launch_rbgs_zero(T* x, const T* b, const double* bshift, Dims d, Stencil st, cudaStream_t s);
+bool rb_sweep_fused_ok(Dims d);
 // bc = mean over 8 children of (b - shift - A x) on the fine grid d.
 template <typename T>
-void launch_residual_restrict(const T* x, const T* b, const double* bshift, T* bc, Dims d,
-                              Stencil st, cudaStream_t s);
-// x (fine, dims d) += trilinear prolongation of xc (coarse dims d/2).
+void launch_resid_restrict(const T* x, const T* b, const double* bshift, T* bc, Dims d, Stencil st,
+                           cudaStream_t s);
+// x (fine, dims d) += trilinear cell-centred prolongation of xc (dims d/2).
 template <typename T>
-void launch_prolong_add(const T* xc, T* x, Dims d, cudaStream_t s);
+void launch_prolong8(const T* xc, T* x, Dims d, cudaStream_t s);
 // Coarsest exact solve x = G b with the circulant table G (dc.n() entries).
 template <typename T>
 void launch_coarse_solve(const T* table, const T* b, T* x, Dims dc, cudaStream_t s);

@@ -38,6 +38,19 @@ def small():
     return w, M
 
 
+EPS = 2.220446049250313e-16
+
+
+def floor_tol(c_ref, g, h, chi, alpha, base=1e-12):
+    """Relative-residual tolerance at the FP64 rounding floor: A c is formed
+    from values of size max|c|, so each cell of the residual carries about
+    eps (alpha + 12 chi/h^2) max|c| of rounding; relative to the rms of g that
+    is the floor. A few times it, and never below `base`."""
+    rms = float(np.sqrt(np.mean(np.asarray(g) ** 2)))
+    fl = 4.0 * EPS * (alpha + 12.0 * chi / h ** 2) * float(np.abs(c_ref).max()) / rms
+    return max(base, fl)
+
+
 def _grid(ibrd, w, alpha=0.0, kernel=4):
     g = ibrd.Grid(*w.dims, h=w.h, chi=w.chi, alpha=alpha, kernel=kernel)
     g.set_blobs(dev(w.q))
@@ -49,6 +62,7 @@ def test_saddle_small(ibrd, small, precision, tol, err):
     w, M = small
     c_ref, lam_ref, _ = direct.solve_saddle(w.q, w.g, w.h, w.chi, 0.0, M=M)
     g = _grid(ibrd, w)
+    tol = max(tol, floor_tol(c_ref, w.g, w.h, w.chi, 0.0)) if precision == 0 else tol
     c, lam, info = g.solve_saddle(dev(w.g), tol=tol, precision=precision, max_iter=400)
     assert info["rel_residual"] <= tol
     assert rel_l2(host(c), c_ref) < err
@@ -66,6 +80,7 @@ def test_reaction_small(ibrd, small, precision, tol, err, alpha):
     M = M0 if alpha == 0.0 else None
     c_ref, u_ref, _ = direct.solve_reaction(w.q, w.kappa, w.g, w.h, w.chi, alpha, M=M)
     g = _grid(ibrd, w, alpha)
+    tol = max(tol, floor_tol(c_ref, w.g, w.h, w.chi, alpha)) if precision == 0 else tol
     c, info = g.solve_reaction(dev(w.kappa), dev(w.g), tol=tol, precision=precision, max_iter=400)
     assert info["rel_residual"] <= tol
     assert rel_l2(host(c), c_ref) < err
@@ -82,7 +97,8 @@ def test_saddle_alpha_positive_nonunit_scales(ibrd):
     c_ref, lam_ref, _ = direct.solve_saddle(q, gsrc, h, chi, alpha, zeta=zeta, f=f)
     g = ibrd.Grid(*dims, h=h, chi=chi, alpha=alpha)
     g.set_blobs(dev(q))
-    c, lam, info = g.solve_saddle(dev(gsrc), f=dev(f), tol=1e-12, zeta=zeta, max_iter=400)
+    # alpha > 0: no large constant mode, so the solve can go below 1e-12
+    c, lam, info = g.solve_saddle(dev(gsrc), f=dev(f), tol=1e-14, zeta=zeta, max_iter=400)
     assert rel_l2(host(c), c_ref) < 1e-11
     assert rel_l2(host(lam), lam_ref) < 1e-11
 
@@ -92,7 +108,7 @@ def test_saddle_tiny_single_blob(ibrd):
     w = workload("tiny")
     c_ref, lam_ref, _ = direct.solve_saddle(w.q, w.g, w.h, w.chi, 0.0)
     g = _grid(ibrd, w)
-    c, lam, info = g.solve_saddle(dev(w.g), tol=1e-12, max_iter=400)
+    c, lam, info = g.solve_saddle(dev(w.g), tol=floor_tol(c_ref, w.g, 1.0, 1.0, 0.0), max_iter=400)
     assert rel_l2(host(c), c_ref) < 1e-11
     assert abs(host(lam)[0] - lam_ref[0]) < 1e-11 * abs(lam_ref[0])
 
@@ -101,7 +117,8 @@ def test_saddle_diagonal_preconditioner(ibrd, small):
     w, M = small
     c_ref, lam_ref, _ = direct.solve_saddle(w.q, w.g, w.h, w.chi, 0.0, M=M)
     g = _grid(ibrd, w)
-    c, lam, info = g.solve_saddle(dev(w.g), tol=1e-12, precond=1, restart=60, max_iter=2000)
+    tol = floor_tol(c_ref, w.g, w.h, w.chi, 0.0)
+    c, lam, info = g.solve_saddle(dev(w.g), tol=tol, precond=1, restart=60, max_iter=2000)
     assert rel_l2(host(lam), lam_ref) < 1e-11
 
 
@@ -112,9 +129,10 @@ def test_single_blob_finite_rate_shift(ibrd):
     gsrc = np.full((L, L, L), 1.0 / L ** 3)
     g = ibrd.Grid(L, L, L)
     g.set_blobs(dev(q))
-    c0, lam, _ = g.solve_saddle(dev(gsrc), tol=1e-12, max_iter=400)
+    c0, lam, _ = g.solve_saddle(dev(gsrc), tol=floor_tol(np.full(1, 0.2), gsrc, 1.0, 1.0, 0.0), max_iter=400)
     for kappa in (0.5, 7.0):
-        cP, _ = g.solve_reaction(dev(np.array([kappa])), dev(gsrc), tol=1e-12, max_iter=400)
+        tol = floor_tol(np.full(1, 0.2 + 1.0 / kappa), gsrc, 1.0, 1.0, 0.0)
+        cP, _ = g.solve_reaction(dev(np.array([kappa])), dev(gsrc), tol=tol, max_iter=400)
         d = host(cP) - host(c0)
         assert np.abs(d - 1.0 / kappa).max() < 1e-9
 
