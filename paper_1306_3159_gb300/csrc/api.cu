@@ -152,6 +152,7 @@ struct ibrd_grid_s {
   int precision = IBRD_FP64;
   cudaStream_t s = nullptr;
   std::vector<Level> levels;
+  int small_from = 0;           // first level handled by the single-CTA coarse V-cycle
   Hier<double> h64;
   Hier<float> h32;
   BlobSet blobs;
@@ -269,6 +270,26 @@ void vcycle_level(ibrd_grid g, int l, const T* b, const double* bshift, T* x, bo
     // Exact coarsest solve. A constant shift of b only changes the mean, which
     // the singular pseudo-inverse ignores; the nonsingular case never shifts.
     launch_coarse_solve<T>(coarse_table<T>(g, shift), b, x, lv.d, g->s);
+    return;
+  }
+  // the coarse end of the hierarchy runs in one CTA out of shared memory
+  if (l >= g->small_from) {
+    CoarseLevels cl{};
+    cl.n = (int)g->levels.size() - l;
+    int tot = 0;
+    for (int i = 0; i < cl.n; ++i) {
+      const Level& li = g->levels[l + i];
+      const Stencil si = stencil(li.h, g->chi, shift);
+      cl.nx[i] = li.d.nx;
+      cl.ny[i] = li.d.ny;
+      cl.nz[i] = li.d.nz;
+      cl.off[i] = tot;
+      cl.diag[i] = si.diag;
+      cl.offd[i] = si.off;
+      tot += (int)li.d.n();
+    }
+    cl.total = tot;
+    launch_vcycle_small<T>(cl, b, x, bshift, coarse_table<T>(g, shift), zero, nu1, nu2, g->s);
     return;
   }
   T* cur = x;
@@ -841,9 +862,23 @@ ibrd_status ibrd_grid_create(ibrd_grid* out, int nx, int ny, int nz, double h, d
     else
       break;
   }
-  if (g->levels.back().d.n() > 512) {
+  if (g->levels.back().d.n() > 512 || g->levels.size() > 16) {
     delete g;
     return IBRD_ERR_ARG;
+  }
+  // single-CTA coarse V-cycle from the first level whose remaining hierarchy
+  // (x and b, FP64) fits in 160 KB of shared memory and has at most 12 levels
+  {
+    const int L = (int)g->levels.size();
+    g->small_from = L;
+    size_t cells = 0;
+    for (int l = L - 1; l >= 0; --l) {
+      cells += g->levels[l].d.n();
+      if (2 * 8 * cells <= 160 * 1024 && L - l <= kMaxSmallLevels)
+        g->small_from = l;
+      else
+        break;
+    }
   }
   ibrd_status st = guarded(g, "ibrd_grid_create", [&]() {
     g->scal = dalloc<double>(S_COUNT);

@@ -188,19 +188,16 @@ __global__ void __launch_bounds__(512) k_spread(const int* __restrict__ active, 
   for (int p = lo; p < hi; ++p) {
     const int b = list[p];
     const int* ib = idx + b * 12;
-    const W* wb = wt + b * 12;
-    W wx = 0, wy = 0, wz = 0;
-    bool mx = false, my = false, mz = false;
-#pragma unroll
-    for (int s = 0; s < 4; ++s) {
-      if (ib[s] == i) { wx += wb[s]; mx = true; }
-      if (ib[4 + s] == j) { wy += wb[4 + s]; my = true; }
-      if (ib[8 + s] == k) { wz += wb[8 + s]; mz = true; }
-    }
-    if (mx && my && mz) {
+    // offset of this cell from the blob's first support cell, per axis
+    int dx = i - ib[0], dy = j - ib[4], dz = k - ib[8];
+    dx += dx < 0 ? nx : 0;
+    dy += dy < 0 ? ny : 0;
+    dz += dz < 0 ? nz : 0;
+    if ((unsigned)dx < 4u && (unsigned)dy < 4u && (unsigned)dz < 4u) {
+      const W* wb = wt + b * 12;
       const double l = lam ? lam[b] : *cval;
       const W amp = (W)(coef ? coef[b] * l : l);
-      acc += amp * (wx * wy * wz);
+      acc += amp * ((wb[dx] * wb[4 + dy]) * wb[8 + dz]);
       hit = true;
     }
   }

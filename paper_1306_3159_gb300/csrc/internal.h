@@ -81,6 +81,20 @@ bool launch_rb_sweep(const T* xin, T* xout, const T* b, const double* bshift, Di
                      cudaStream_t s);
 template <typename T>
 bool rb_sweep_fused_ok(Dims d);
+// Levels handled by the single-CTA coarse V-cycle (shared-memory resident).
+constexpr int kMaxSmallLevels = 12;
+struct CoarseLevels {
+  int n;                          // number of levels
+  int total;                      // cells over all levels
+  int nx[kMaxSmallLevels], ny[kMaxSmallLevels], nz[kMaxSmallLevels];
+  int off[kMaxSmallLevels];       // first cell of each level in the packed arrays
+  double diag[kMaxSmallLevels], offd[kMaxSmallLevels];
+};
+// Whole V-cycle over the levels in lv (the last one solved exactly with the
+// circulant table) in one CTA: x = V(b - bshift), from zero or from x.
+template <typename T>
+void launch_vcycle_small(const CoarseLevels& lv, const T* b, T* x, const double* bshift, const T* table, bool zero,
+                         int nu1, int nu2, cudaStream_t s);
 // bc = mean over 8 children of (b - shift - A x) on the fine grid d.
 template <typename T>
 void launch_resid_restrict(const T* x, const T* b, const double* bshift, T* bc, Dims d, Stencil st,

@@ -23,6 +23,30 @@ namespace {
 
 __device__ __forceinline__ int wrap(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem, int bytes) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  if (bytes == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Ring depths (planes) of the pipelined sweep: x needs the 4 planes k-2..k+1
+// in use plus D in flight, b the 2 planes k-1, k plus D in flight.
+constexpr int kSweepD = 3, kSweepRX = 8, kSweepRB = 8;
+
+template <typename T, int TX, int TY>
+constexpr size_t sweep_smem() {
+  return sizeof(T) * ((size_t)kSweepRX * (TY + 4) * (TX + 4) + (size_t)kSweepRB * (TY + 2) * (TX + 2));
+}
+
+// Plane copies go global -> shared with cp.async, D plane steps ahead of use;
+// commit group G_j holds x plane j+1 and b plane j, the inputs step j needs.
 template <typename T, int TX, int TY, bool ZERO>
 __global__ void __launch_bounds__(TX / 2 * TY) k_rb_sweep(const T* __restrict__ xin, T* __restrict__ xout,
                                                           const T* __restrict__ b, const double* __restrict__ bshift,
@@ -32,15 +56,16 @@ __global__ void __launch_bounds__(TX / 2 * TY) k_rb_sweep(const T* __restrict__ 
   constexpr int BW = TX + 2, BH = TY + 2;   // b plane with 1-cell halo
   constexpr int NPX = (PW * PH + NT - 1) / NT;
   constexpr int NPB = (BW * BH + NT - 1) / NT;
-  __shared__ T px[4][PH][PW];
-  __shared__ T pb[2][BH][BW];
+  constexpr int D = kSweepD, RX = kSweepRX, RB = kSweepRB;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* pxs = reinterpret_cast<T*>(smem_raw);
+  T* pbs = pxs + RX * PH * PW;
   const int tid = threadIdx.x + threadIdx.y * (TX / 2);
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-  const int k0 = blockIdx.z * zc, k1 = k0 + zc;
+  const int k0 = blockIdx.z * zc, k1 = min(k0 + zc, nz);
   const size_t plane = (size_t)nx * ny;
   const T sh = bshift ? (T)(*bshift) : (T)0;
 
-  // global offsets (within a plane) of this thread's share of the halo tiles
   int offx[NPX], offb[NPB];
 #pragma unroll
   for (int r = 0; r < NPX; ++r) {
@@ -54,94 +79,92 @@ __global__ void __launch_bounds__(TX / 2 * TY) k_rb_sweep(const T* __restrict__ 
     const int ly = e / BW, lx = e - ly * BW;
     offb[r] = (e < BW * BH) ? wrap(y0 - 1 + ly, ny) * nx + wrap(x0 - 1 + lx, nx) : -1;
   }
-  auto load_x = [&](int k, T* reg) {
+  auto issue_x = [&](int k) {
+    T* dst = pxs + ((k + 2 * RX) % RX) * (PH * PW);
     const T* src = xin + (size_t)wrap(k, nz) * plane;
 #pragma unroll
-    for (int r = 0; r < NPX; ++r) reg[r] = (ZERO || offx[r] < 0) ? (T)0 : src[offx[r]];
+    for (int r = 0; r < NPX; ++r) {
+      if (offx[r] < 0) continue;
+      if (ZERO)
+        dst[tid + r * NT] = (T)0;
+      else
+        cp_async(dst + tid + r * NT, src + offx[r], (int)sizeof(T));
+    }
   };
-  auto store_x = [&](int k, const T* reg) {
-    T* dst = &px[k & 3][0][0];
-#pragma unroll
-    for (int r = 0; r < NPX; ++r)
-      if (offx[r] >= 0) dst[tid + r * NT] = reg[r];
-  };
-  auto load_b = [&](int k, T* reg) {
+  auto issue_b = [&](int k) {
+    T* dst = pbs + ((k + 2 * RB) % RB) * (BH * BW);
     const T* src = b + (size_t)wrap(k, nz) * plane;
 #pragma unroll
-    for (int r = 0; r < NPB; ++r) reg[r] = (offb[r] < 0) ? (T)0 : src[offb[r]] - sh;
-  };
-  auto store_b = [&](int k, const T* reg) {
-    T* dst = &pb[k & 1][0][0];
-#pragma unroll
     for (int r = 0; r < NPB; ++r)
-      if (offb[r] >= 0) dst[tid + r * NT] = reg[r];
+      if (offb[r] >= 0) cp_async(dst + tid + r * NT, src + offb[r], (int)sizeof(T));
   };
-  // red update of plane k on the tile plus a 1-cell ring (local rows/cols 1..TX+2)
+  auto xp = [&](int k) { return reinterpret_cast<T(*)[PW]>(pxs + ((k + 2 * RX) % RX) * (PH * PW)); };
+  auto bp = [&](int k) { return reinterpret_cast<T(*)[BW]>(pbs + ((k + 2 * RB) % RB) * (BH * BW)); };
+  // red update of plane k on the tile plus a 1-cell ring (local cols/rows 1..TX+2)
   auto red = [&](int k) {
-    const int par = (x0 + y0 + k) & 1;  // parity offset of local (lx, ly) -> global
-    T(*P)[PW] = px[k & 3];
-    T(*Pm)[PW] = px[(k + 3) & 3];
-    T(*Pp)[PW] = px[(k + 1) & 3];
-    T(*B)[BW] = pb[k & 1];
-    constexpr int RW = (TX + 2) / 2;  // red cells per ring row
+    const int par = (x0 + y0 + k) & 1;
+    T(*P)[PW] = xp(k);
+    T(*Pm)[PW] = xp(k - 1);
+    T(*Pp)[PW] = xp(k + 1);
+    T(*B)[BW] = bp(k);
+    constexpr int RW = (TX + 2) / 2;
     for (int e = tid; e < RW * BH; e += NT) {
       const int ly = 1 + e / RW;
       const int q = e - (ly - 1) * RW;
-      // local lx in [1, TX+2]; red when (lx - 2 + ly - 2 + par) even
       const int lx = 1 + 2 * q + ((1 + ly + par) & 1);
       const T s = ((P[ly][lx - 1] + P[ly][lx + 1]) + (P[ly - 1][lx] + P[ly + 1][lx])) + (Pm[ly][lx] + Pp[ly][lx]);
-      P[ly][lx] = (B[ly - 1][lx - 1] + off * s) * inv_diag;
+      P[ly][lx] = ((B[ly - 1][lx - 1] - sh) + off * s) * inv_diag;
     }
   };
-  // black update of plane k on the tile (local rows/cols 2..TX+1)
-  auto black = [&](int k) {
+  // black update of plane k on the tile, then store the tile of plane k
+  auto black_write = [&](int k) {
     const int par = (x0 + y0 + k) & 1;
-    T(*P)[PW] = px[k & 3];
-    T(*Pm)[PW] = px[(k + 3) & 3];
-    T(*Pp)[PW] = px[(k + 1) & 3];
-    T(*B)[BW] = pb[k & 1];
+    T(*P)[PW] = xp(k);
+    T(*Pm)[PW] = xp(k - 1);
+    T(*Pp)[PW] = xp(k + 1);
+    T(*B)[BW] = bp(k);
     const int ly = 2 + threadIdx.y;
-    const int lx = 2 + 2 * threadIdx.x + ((ly + par) & 1 ? 0 : 1);
-    // black when (lx - 2 + ly - 2 + par) odd
+    const int lxr = 2 + 2 * threadIdx.x;
+    const int lx = lxr + (((ly + par) & 1) ? 0 : 1);
     const T s = ((P[ly][lx - 1] + P[ly][lx + 1]) + (P[ly - 1][lx] + P[ly + 1][lx])) + (Pm[ly][lx] + Pp[ly][lx]);
-    P[ly][lx] = (B[ly - 1][lx - 1] + off * s) * inv_diag;
-  };
-  auto write = [&](int k) {
-    T(*P)[PW] = px[k & 3];
-    const int ly = 2 + threadIdx.y;
-    const int lx = 2 + 2 * threadIdx.x;
+    const T v = ((B[ly - 1][lx - 1] - sh) + off * s) * inv_diag;
+    P[ly][lx] = v;
     T* dst = xout + (size_t)k * plane + (size_t)(y0 + threadIdx.y) * nx + x0 + 2 * threadIdx.x;
-    dst[0] = P[ly][lx];
-    dst[1] = P[ly][lx + 1];
+    if (lx == lxr) {
+      dst[0] = v;
+      dst[1] = P[ly][lxr + 1];
+    } else {
+      dst[0] = P[ly][lxr];
+      dst[1] = v;
+    }
   };
 
-  T rx[NPX], rb[NPB];
-  // prologue: planes k0-2 .. k0+1 of x, b at k0-1 and k0
-  for (int k = k0 - 2; k <= k0 + 1; ++k) {
-    load_x(k, rx);
-    store_x(k, rx);
+  // prologue: group P = x planes k0-2..k0+1, b planes k0-1, k0; then groups
+  // G_j = {x(j+1), b(j)} for j = k0+1 .. k0+D-1
+  for (int k = k0 - 2; k <= k0 + 1; ++k) issue_x(k);
+  issue_b(k0 - 1);
+  issue_b(k0);
+  cp_async_commit();
+  for (int j = k0 + 1; j <= k0 + D - 1; ++j) {
+    if (j <= k1) {
+      issue_x(j + 1);
+      issue_b(j);
+    }
+    cp_async_commit();
   }
-  load_b(k0 - 1, rb);
-  store_b(k0 - 1, rb);
-  load_b(k0, rb);
-  store_b(k0, rb);
-  __syncthreads();
-  red(k0 - 1);
-  __syncthreads();
   for (int k = k0; k <= k1; ++k) {
-    const bool pre_x = (k + 2 <= k1 + 1), pre_b = (k + 1 <= k1);
-    if (pre_x) load_x(k + 2, rx);
-    if (pre_b) load_b(k + 1, rb);
+    const int j = k + D;
+    if (j <= k1) {
+      issue_x(j + 1);
+      issue_b(j);
+    }
+    cp_async_commit();
+    cp_async_wait<D>();
+    __syncthreads();
+    if (k == k0) red(k0 - 1);
     red(k);
     __syncthreads();
-    if (k > k0) {
-      black(k - 1);
-      __syncthreads();
-      write(k - 1);
-    }
-    if (pre_x) store_x(k + 2, rx);
-    if (pre_b) store_b(k + 1, rb);
-    __syncthreads();
+    if (k > k0) black_write(k - 1);
   }
 }
 
@@ -252,11 +275,111 @@ __global__ void __launch_bounds__(256) k_prolong8(const T* __restrict__ xc, T* _
     }
 }
 
-inline int pick_zc(Dims d, int tiles_xy, int target_blocks) {
-  for (int zc : {32, 16, 8, 4, 2}) {
-    if (d.nz % zc == 0 && (long)tiles_xy * (d.nz / zc) >= target_blocks) return zc;
+// The coarse end of a V-cycle in ONE CTA: levels lv.first .. lv.n-1 (at most
+// a few thousand cells) live in shared memory; smoothing, residual
+// restriction, the exact coarsest solve and prolongation run with block-wide
+// barriers between phases. Arithmetic matches the multi-kernel levels.
+template <typename T>
+__global__ void __launch_bounds__(1024) k_vcycle_small(CoarseLevels lv, const T* __restrict__ bg, T* __restrict__ xg,
+                                                       const double* __restrict__ bshift, const T* __restrict__ table,
+                                                       int zero, int nu1, int nu2) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* X = reinterpret_cast<T*>(smem_raw);
+  T* B = X + lv.total;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const T sh = bshift ? (T)(*bshift) : (T)0;
+  {
+    const int n0 = lv.nx[0] * lv.ny[0] * lv.nz[0];
+    for (int c = tid; c < n0; c += nt) {
+      B[c] = bg[c] - sh;
+      X[c] = zero ? (T)0 : xg[c];
+    }
+    for (int c = n0 + tid; c < lv.total; c += nt) X[c] = (T)0;
   }
-  return (d.nz % 2 == 0) ? 2 : 1;
+  __syncthreads();
+  auto sweep = [&](int l) {
+    const int nx = lv.nx[l], ny = lv.ny[l], nz = lv.nz[l], n = nx * ny * nz;
+    T* x = X + lv.off[l];
+    const T* b = B + lv.off[l];
+    const T inv = (T)(1.0 / lv.diag[l]), off = (T)lv.offd[l];
+    for (int colour = 0; colour < 2; ++colour) {
+      for (int c = tid; c < n; c += nt) {
+        const int i = c % nx, j = (c / nx) % ny, k = c / (nx * ny);
+        if (((i + j + k) & 1) != colour) continue;
+        const T s = ((x[c - i + wrap(i - 1, nx)] + x[c - i + wrap(i + 1, nx)]) +
+                     (x[c + (wrap(j - 1, ny) - j) * nx] + x[c + (wrap(j + 1, ny) - j) * nx])) +
+                    (x[c + (wrap(k - 1, nz) - k) * nx * ny] + x[c + (wrap(k + 1, nz) - k) * nx * ny]);
+        x[c] = (b[c] + off * s) * inv;
+      }
+      __syncthreads();
+    }
+  };
+  const int last = lv.n - 1;
+  for (int l = 0; l < last; ++l) {
+    for (int sw = 0; sw < nu1; ++sw) sweep(l);
+    // residual restriction to level l+1
+    const int nx = lv.nx[l], ny = lv.ny[l], nz = lv.nz[l];
+    const int nxc = nx >> 1, nyc = ny >> 1, nc = nxc * nyc * (nz >> 1);
+    const T* x = X + lv.off[l];
+    const T* b = B + lv.off[l];
+    T* bc = B + lv.off[l + 1];
+    const T diag = (T)lv.diag[l], off = (T)lv.offd[l];
+    for (int C = tid; C < nc; C += nt) {
+      const int I = C % nxc, J = (C / nxc) % nyc, K = C / (nxc * nyc);
+      T acc = 0;
+      for (int dz = 0; dz < 2; ++dz)
+        for (int dy = 0; dy < 2; ++dy)
+          for (int dx = 0; dx < 2; ++dx) {
+            const int i = 2 * I + dx, j = 2 * J + dy, k = 2 * K + dz;
+            const int c = (k * ny + j) * nx + i;
+            const T s = ((x[c - i + wrap(i - 1, nx)] + x[c - i + wrap(i + 1, nx)]) +
+                         (x[c + (wrap(j - 1, ny) - j) * nx] + x[c + (wrap(j + 1, ny) - j) * nx])) +
+                        (x[c + (wrap(k - 1, nz) - k) * nx * ny] + x[c + (wrap(k + 1, nz) - k) * nx * ny]);
+            acc += b[c] - (diag * x[c] - off * s);
+          }
+      bc[C] = acc * (T)0.125;
+    }
+    __syncthreads();
+  }
+  {
+    // exact coarsest solve with the circulant table
+    const int nx = lv.nx[last], ny = lv.ny[last], nz = lv.nz[last], n = nx * ny * nz;
+    T* x = X + lv.off[last];
+    const T* b = B + lv.off[last];
+    for (int t = tid; t < n; t += nt) {
+      const int ix = t % nx, iy = (t / nx) % ny, iz = t / (nx * ny);
+      T acc = 0;
+      for (int u = 0; u < n; ++u) {
+        const int jx = u % nx, jy = (u / nx) % ny, jz = u / (nx * ny);
+        const int dx = ix - jx + (ix < jx ? nx : 0), dy = iy - jy + (iy < jy ? ny : 0), dz = iz - jz + (iz < jz ? nz : 0);
+        acc += table[(dz * ny + dy) * nx + dx] * b[u];
+      }
+      x[t] = acc;
+    }
+    __syncthreads();
+  }
+  for (int l = last - 1; l >= 0; --l) {
+    const int nx = lv.nx[l], ny = lv.ny[l], nz = lv.nz[l], n = nx * ny * nz;
+    const int nxc = nx >> 1, nyc = ny >> 1, nzc = nz >> 1;
+    T* x = X + lv.off[l];
+    const T* xc = X + lv.off[l + 1];
+    const T w3 = (T)0.75, w1 = (T)0.25;
+    for (int c = tid; c < n; c += nt) {
+      const int i = c % nx, j = (c / nx) % ny, k = c / (nx * ny);
+      const int I = i >> 1, J = j >> 1, K = k >> 1;
+      const int I2 = (i & 1) ? wrap(I + 1, nxc) : wrap(I - 1, nxc);
+      const int J2 = (j & 1) ? wrap(J + 1, nyc) : wrap(J - 1, nyc);
+      const int K2 = (k & 1) ? wrap(K + 1, nzc) : wrap(K - 1, nzc);
+      auto e = [&](int kk, int jj, int ii) { return xc[(kk * nyc + jj) * nxc + ii]; };
+      const T yA = w3 * (w3 * e(K, J, I) + w1 * e(K, J, I2)) + w1 * (w3 * e(K, J2, I) + w1 * e(K, J2, I2));
+      const T yB = w3 * (w3 * e(K2, J, I) + w1 * e(K2, J, I2)) + w1 * (w3 * e(K2, J2, I) + w1 * e(K2, J2, I2));
+      x[c] += w3 * yA + w1 * yB;
+    }
+    __syncthreads();
+    for (int sw = 0; sw < nu2; ++sw) sweep(l);
+  }
+  const int n0 = lv.nx[0] * lv.ny[0] * lv.nz[0];
+  for (int c = tid; c < n0; c += nt) xg[c] = X[c];
 }
 
 }  // namespace
@@ -264,6 +387,19 @@ inline int pick_zc(Dims d, int tiles_xy, int target_blocks) {
 template <typename T>
 bool rb_sweep_fused_ok(Dims d) {
   return d.nx % 32 == 0 && d.ny % 8 == 0 && d.nz % 2 == 0 && d.nz >= 4;
+}
+
+
+template <typename T, int TX, bool ZERO>
+void sweep_launch(dim3 g, cudaStream_t s, const T* xin, T* xout, const T* b, const double* bshift, Dims d, int zc,
+                  T inv, T off) {
+  constexpr size_t sm = sweep_smem<T, TX, 8>();
+  static bool attr = false;
+  if (!attr) {
+    IBRD_CUDA(cudaFuncSetAttribute(k_rb_sweep<T, TX, 8, ZERO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    attr = true;
+  }
+  k_rb_sweep<T, TX, 8, ZERO><<<g, dim3(TX / 2, 8), sm, s>>>(xin, xout, b, bshift, d.nx, d.ny, d.nz, zc, inv, off);
 }
 
 template <typename T>
@@ -274,20 +410,28 @@ bool launch_rb_sweep(const T* xin, T* xout, const T* b, const double* bshift, Di
   if (rb_sweep_fused_ok<T>(d)) {
     const bool wide = (d.nx % 64 == 0);
     const int TX = wide ? 64 : 32, TY = 8;
-    const int txy = (d.nx / TX) * (d.ny / TY);
-    const int zc = pick_zc(d, txy, 2 * 152 * 4);
-    dim3 g(d.nx / TX, d.ny / TY, d.nz / zc);
+    const int cols = (d.nx / TX) * (d.ny / TY);
+    // about one wave of resident CTAs: chunks per column = resident slots / columns
+    const size_t sm = wide ? sweep_smem<T, 64, 8>() : sweep_smem<T, 32, 8>();
+    int per_sm = (int)(200 * 1024 / sm);
+    per_sm = per_sm < 1 ? 1 : (per_sm > 8 ? 8 : per_sm);
+    const int slots = 152 * per_sm;
+    int chunks = slots / cols;
+    chunks = chunks < 1 ? 1 : chunks;
+    int zc = (d.nz + chunks - 1) / chunks;
+    if (zc < 2) zc = 2;
+    dim3 g(d.nx / TX, d.ny / TY, (d.nz + zc - 1) / zc);
     prof_begin(c, s);
     if (wide) {
       if (zero)
-        k_rb_sweep<T, 64, 8, true><<<g, dim3(32, 8), 0, s>>>(xin, xout, b, bshift, d.nx, d.ny, d.nz, zc, inv, off);
+        sweep_launch<T, 64, true>(g, s, xin, xout, b, bshift, d, zc, inv, off);
       else
-        k_rb_sweep<T, 64, 8, false><<<g, dim3(32, 8), 0, s>>>(xin, xout, b, bshift, d.nx, d.ny, d.nz, zc, inv, off);
+        sweep_launch<T, 64, false>(g, s, xin, xout, b, bshift, d, zc, inv, off);
     } else {
       if (zero)
-        k_rb_sweep<T, 32, 8, true><<<g, dim3(16, 8), 0, s>>>(xin, xout, b, bshift, d.nx, d.ny, d.nz, zc, inv, off);
+        sweep_launch<T, 32, true>(g, s, xin, xout, b, bshift, d, zc, inv, off);
       else
-        k_rb_sweep<T, 32, 8, false><<<g, dim3(16, 8), 0, s>>>(xin, xout, b, bshift, d.nx, d.ny, d.nz, zc, inv, off);
+        sweep_launch<T, 32, false>(g, s, xin, xout, b, bshift, d, zc, inv, off);
     }
     // one read of x (skipped from zero), one read of b, one write of x
     prof_end(c, s, "rb_sweep", (zero ? 2.0 : 3.0) * sizeof(T) * d.n());
@@ -331,7 +475,24 @@ void launch_prolong8(const T* xc, T* x, Dims d, cudaStream_t s) {
   prof_end(c, s, "prolong8", 2.125 * sizeof(T) * d.n());
 }
 
+template <typename T>
+void launch_vcycle_small(const CoarseLevels& lv, const T* b, T* x, const double* bshift, const T* table, bool zero,
+                         int nu1, int nu2, cudaStream_t s) {
+  const size_t sm = 2 * sizeof(T) * (size_t)lv.total;
+  static bool attr = false;
+  if (!attr) {
+    IBRD_CUDA(cudaFuncSetAttribute(k_vcycle_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    attr = true;
+  }
+  const int c = pcls<T>(P_RBGS64, P_RBGS32);
+  prof_begin(c, s);
+  k_vcycle_small<T><<<1, 1024, sm, s>>>(lv, b, x, bshift, table, zero ? 1 : 0, nu1, nu2);
+  prof_end(c, s, "vcycle_small", 2.0 * sizeof(T) * lv.total);
+}
+
 #define IBRD_INST(T)                                                                                         \
+  template void launch_vcycle_small<T>(const CoarseLevels&, const T*, T*, const double*, const T*, bool, int,  \
+                                       int, cudaStream_t);                                                  \
   template bool launch_rb_sweep<T>(const T*, T*, const T*, const double*, Dims, Stencil, bool, cudaStream_t); \
   template void launch_resid_restrict<T>(const T*, const T*, const double*, T*, Dims, Stencil, cudaStream_t); \
   template void launch_prolong8<T>(const T*, T*, Dims, cudaStream_t);                                       \
