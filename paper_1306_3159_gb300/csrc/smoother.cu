@@ -23,12 +23,9 @@ namespace {
 
 __device__ __forceinline__ int wrap(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
-__device__ __forceinline__ void cp_async(void* smem, const void* gmem, int bytes) {
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  if (bytes == 8)
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
-  else
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
@@ -38,109 +35,156 @@ __device__ __forceinline__ void cp_async_wait() {
 
 // Ring depths (planes) of the pipelined sweep: x needs the 4 planes k-2..k+1
 // in use plus D in flight, b the 2 planes k-1, k plus D in flight.
-constexpr int kSweepD = 3, kSweepRX = 8, kSweepRB = 8;
+constexpr int kSweepD = 3, kSweepR = 8;
+
+// 16-byte vectors: V values per vector.
+template <typename T>
+struct Vec;
+template <>
+struct Vec<float> {
+  using type = float4;
+  static constexpr int V = 4;
+};
+template <>
+struct Vec<double> {
+  using type = double2;
+  static constexpr int V = 2;
+};
 
 template <typename T, int TX, int TY>
 constexpr size_t sweep_smem() {
-  return sizeof(T) * ((size_t)kSweepRX * (TY + 4) * (TX + 4) + (size_t)kSweepRB * (TY + 2) * (TX + 2));
+  constexpr int V = Vec<T>::V;
+  return sizeof(T) * (size_t)kSweepR * ((TY + 4) + (TY + 2)) * (TX + 2 * V);
 }
 
-// Plane copies go global -> shared with cp.async, D plane steps ahead of use;
-// commit group G_j holds x plane j+1 and b plane j, the inputs step j needs.
+template <typename T>
+__device__ __forceinline__ T vget(const typename Vec<T>::type& v, int c);
+template <>
+__device__ __forceinline__ float vget<float>(const float4& v, int c) {
+  return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w));
+}
+template <>
+__device__ __forceinline__ double vget<double>(const double2& v, int c) {
+  return c == 0 ? v.x : v.y;
+}
+template <typename T>
+__device__ __forceinline__ void vset(typename Vec<T>::type& v, int c, T x);
+template <>
+__device__ __forceinline__ void vset<float>(float4& v, int c, float x) {
+  if (c == 0) v.x = x;
+  else if (c == 1) v.y = x;
+  else if (c == 2) v.z = x;
+  else v.w = x;
+}
+template <>
+__device__ __forceinline__ void vset<double>(double2& v, int c, double x) {
+  if (c == 0) v.x = x;
+  else v.y = x;
+}
+
+// Plane layout in shared memory: x planes hold rows y0-2 .. y0+TY+1, b planes
+// rows y0-1 .. y0+TY; both hold columns x0-V .. x0+TX+V-1 (local column
+// lx = x - x0 + V), so every row starts on a 16-byte boundary and every copy,
+// including the periodic wrap at the domain edge, is one aligned 16-byte
+// cp.async. Commit group G_j holds x plane j+1 and b plane j; step j uses it.
 template <typename T, int TX, int TY, bool ZERO>
-__global__ void __launch_bounds__(TX / 2 * TY) k_rb_sweep(const T* __restrict__ xin, T* __restrict__ xout,
-                                                          const T* __restrict__ b, const double* __restrict__ bshift,
-                                                          int nx, int ny, int nz, int zc, T inv_diag, T off) {
-  constexpr int NT = TX / 2 * TY;
-  constexpr int PW = TX + 4, PH = TY + 4;   // x plane with 2-cell halo
-  constexpr int BW = TX + 2, BH = TY + 2;   // b plane with 1-cell halo
-  constexpr int NPX = (PW * PH + NT - 1) / NT;
-  constexpr int NPB = (BW * BH + NT - 1) / NT;
-  constexpr int D = kSweepD, RX = kSweepRX, RB = kSweepRB;
+__global__ void __launch_bounds__(256) k_rb_sweep(const T* __restrict__ xin, T* __restrict__ xout,
+                                                  const T* __restrict__ b, const double* __restrict__ bshift, int nx,
+                                                  int ny, int nz, int zc, T inv_diag, T off) {
+  using VT = typename Vec<T>::type;
+  constexpr int V = Vec<T>::V;
+  constexpr int NT = 256;
+  constexpr int W = TX + 2 * V;            // row length (values)
+  constexpr int NV = W / V;                // vectors per row
+  constexpr int XR = TY + 4, BR = TY + 2;  // rows per x / b plane
+  constexpr int D = kSweepD, R = kSweepR;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* pxs = reinterpret_cast<T*>(smem_raw);
-  T* pbs = pxs + RX * PH * PW;
-  const int tid = threadIdx.x + threadIdx.y * (TX / 2);
+  T* pbs = pxs + R * XR * W;
+  const int tid = threadIdx.x;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   const int k0 = blockIdx.z * zc, k1 = min(k0 + zc, nz);
   const size_t plane = (size_t)nx * ny;
   const T sh = bshift ? (T)(*bshift) : (T)0;
 
-  int offx[NPX], offb[NPB];
-#pragma unroll
-  for (int r = 0; r < NPX; ++r) {
-    const int e = tid + r * NT;
-    const int ly = e / PW, lx = e - ly * PW;
-    offx[r] = (e < PW * PH) ? wrap(y0 - 2 + ly, ny) * nx + wrap(x0 - 2 + lx, nx) : -1;
-  }
-#pragma unroll
-  for (int r = 0; r < NPB; ++r) {
-    const int e = tid + r * NT;
-    const int ly = e / BW, lx = e - ly * BW;
-    offb[r] = (e < BW * BH) ? wrap(y0 - 1 + ly, ny) * nx + wrap(x0 - 1 + lx, nx) : -1;
-  }
+  auto slot_x = [&](int k) { return pxs + (k & (R - 1)) * (XR * W); };
+  auto slot_b = [&](int k) { return pbs + (k & (R - 1)) * (BR * W); };
+  // vector copies of one plane: x rows y0-2.., b rows y0-1..
   auto issue_x = [&](int k) {
-    T* dst = pxs + ((k + 2 * RX) % RX) * (PH * PW);
+    T* dst = slot_x(k);
     const T* src = xin + (size_t)wrap(k, nz) * plane;
-#pragma unroll
-    for (int r = 0; r < NPX; ++r) {
-      if (offx[r] < 0) continue;
-      if (ZERO)
-        dst[tid + r * NT] = (T)0;
-      else
-        cp_async(dst + tid + r * NT, src + offx[r], (int)sizeof(T));
+    for (int e = tid; e < XR * NV; e += NT) {
+      const int r = e / NV, v = e - r * NV;
+      T* d = dst + r * W + v * V;
+      if (ZERO) {
+        *reinterpret_cast<VT*>(d) = VT{};
+      } else {
+        const int gy = wrap(y0 - 2 + r, ny), gx = wrap(x0 - V + v * V, nx);
+        cp_async16(d, src + (size_t)gy * nx + gx);
+      }
     }
   };
   auto issue_b = [&](int k) {
-    T* dst = pbs + ((k + 2 * RB) % RB) * (BH * BW);
+    T* dst = slot_b(k);
     const T* src = b + (size_t)wrap(k, nz) * plane;
-#pragma unroll
-    for (int r = 0; r < NPB; ++r)
-      if (offb[r] >= 0) cp_async(dst + tid + r * NT, src + offb[r], (int)sizeof(T));
-  };
-  auto xp = [&](int k) { return reinterpret_cast<T(*)[PW]>(pxs + ((k + 2 * RX) % RX) * (PH * PW)); };
-  auto bp = [&](int k) { return reinterpret_cast<T(*)[BW]>(pbs + ((k + 2 * RB) % RB) * (BH * BW)); };
-  // red update of plane k on the tile plus a 1-cell ring (local cols/rows 1..TX+2)
-  auto red = [&](int k) {
-    const int par = (x0 + y0 + k) & 1;
-    T(*P)[PW] = xp(k);
-    T(*Pm)[PW] = xp(k - 1);
-    T(*Pp)[PW] = xp(k + 1);
-    T(*B)[BW] = bp(k);
-    constexpr int RW = (TX + 2) / 2;
-    for (int e = tid; e < RW * BH; e += NT) {
-      const int ly = 1 + e / RW;
-      const int q = e - (ly - 1) * RW;
-      const int lx = 1 + 2 * q + ((1 + ly + par) & 1);
-      const T s = ((P[ly][lx - 1] + P[ly][lx + 1]) + (P[ly - 1][lx] + P[ly + 1][lx])) + (Pm[ly][lx] + Pp[ly][lx]);
-      P[ly][lx] = ((B[ly - 1][lx - 1] - sh) + off * s) * inv_diag;
+    for (int e = tid; e < BR * NV; e += NT) {
+      const int r = e / NV, v = e - r * NV;
+      const int gy = wrap(y0 - 1 + r, ny), gx = wrap(x0 - V + v * V, nx);
+      cp_async16(dst + r * W + v * V, src + (size_t)gy * nx + gx);
     }
   };
-  // black update of plane k on the tile, then store the tile of plane k
+  // Update the cells of `colour` (0 red, 1 black) of vector group (row ly of
+  // the x plane k, vector v) whose column lies in [lo, hi]; returns the group.
+  auto update = [&](int k, int ly, int v, int colour, int lo, int hi) -> VT {
+    T* P = slot_x(k);
+    const T* Pm = slot_x(k - 1);
+    const T* Pp = slot_x(k + 1);
+    const T* B = slot_b(k);
+    const int o = ly * W + v * V;
+    VT c = *reinterpret_cast<const VT*>(P + o);
+    const VT u = *reinterpret_cast<const VT*>(P + o - W);
+    const VT dn = *reinterpret_cast<const VT*>(P + o + W);
+    const VT zm = *reinterpret_cast<const VT*>(Pm + o);
+    const VT zp = *reinterpret_cast<const VT*>(Pp + o);
+    const VT bb = *reinterpret_cast<const VT*>(B + o - W);
+    const T left = v > 0 ? P[o - 1] : (T)0;
+    const T right = v < NV - 1 ? P[o + V] : (T)0;
+    const int par = (x0 + y0 + k + ly) & 1;
+    VT out = c;
+#pragma unroll
+    for (int q = 0; q < V; ++q) {
+      const int lx = v * V + q;
+      if (((par + q) & 1) != colour || lx < lo || lx > hi) continue;
+      const T xl = q == 0 ? left : vget<T>(c, q - 1);
+      const T xr = q == V - 1 ? right : vget<T>(c, q + 1);
+      const T s = ((xl + xr) + (vget<T>(u, q) + vget<T>(dn, q))) + (vget<T>(zm, q) + vget<T>(zp, q));
+      vset<T>(out, q, ((vget<T>(bb, q) - sh) + off * s) * inv_diag);
+    }
+    return out;
+  };
+  // red cells of plane k on the tile plus a 1-cell ring: rows 1..TY+2,
+  // columns V-1 .. TX+V (all NV vectors of the row)
+  auto red = [&](int k) {
+    T* P = slot_x(k);
+    for (int e = tid; e < (TY + 2) * NV; e += NT) {
+      const int ly = 1 + e / NV, v = e - (ly - 1) * NV;
+      const VT r = update(k, ly, v, 0, V - 1, TX + V);
+      *reinterpret_cast<VT*>(P + ly * W + v * V) = r;
+    }
+  };
+  // black cells of plane k on the tile, then store the tile row of plane k
   auto black_write = [&](int k) {
-    const int par = (x0 + y0 + k) & 1;
-    T(*P)[PW] = xp(k);
-    T(*Pm)[PW] = xp(k - 1);
-    T(*Pp)[PW] = xp(k + 1);
-    T(*B)[BW] = bp(k);
-    const int ly = 2 + threadIdx.y;
-    const int lxr = 2 + 2 * threadIdx.x;
-    const int lx = lxr + (((ly + par) & 1) ? 0 : 1);
-    const T s = ((P[ly][lx - 1] + P[ly][lx + 1]) + (P[ly - 1][lx] + P[ly + 1][lx])) + (Pm[ly][lx] + Pp[ly][lx]);
-    const T v = ((B[ly - 1][lx - 1] - sh) + off * s) * inv_diag;
-    P[ly][lx] = v;
-    T* dst = xout + (size_t)k * plane + (size_t)(y0 + threadIdx.y) * nx + x0 + 2 * threadIdx.x;
-    if (lx == lxr) {
-      dst[0] = v;
-      dst[1] = P[ly][lxr + 1];
-    } else {
-      dst[0] = P[ly][lxr];
-      dst[1] = v;
+    T* P = slot_x(k);
+    constexpr int TV = TX / V;
+    for (int e = tid; e < TY * TV; e += NT) {
+      const int ty = e / TV, v = 1 + (e - ty * TV);
+      const int ly = 2 + ty;
+      const VT r = update(k, ly, v, 1, V, TX + V - 1);
+      *reinterpret_cast<VT*>(P + ly * W + v * V) = r;
+      *reinterpret_cast<VT*>(xout + (size_t)k * plane + (size_t)(y0 + ty) * nx + x0 + (v - 1) * V) = r;
     }
   };
 
-  // prologue: group P = x planes k0-2..k0+1, b planes k0-1, k0; then groups
-  // G_j = {x(j+1), b(j)} for j = k0+1 .. k0+D-1
   for (int k = k0 - 2; k <= k0 + 1; ++k) issue_x(k);
   issue_b(k0 - 1);
   issue_b(k0);
@@ -399,7 +443,7 @@ void sweep_launch(dim3 g, cudaStream_t s, const T* xin, T* xout, const T* b, con
     IBRD_CUDA(cudaFuncSetAttribute(k_rb_sweep<T, TX, 8, ZERO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     attr = true;
   }
-  k_rb_sweep<T, TX, 8, ZERO><<<g, dim3(TX / 2, 8), sm, s>>>(xin, xout, b, bshift, d.nx, d.ny, d.nz, zc, inv, off);
+  k_rb_sweep<T, TX, 8, ZERO><<<g, 256, sm, s>>>(xin, xout, b, bshift, d.nx, d.ny, d.nz, zc, inv, off);
 }
 
 template <typename T>
