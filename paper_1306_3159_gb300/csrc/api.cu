@@ -39,8 +39,17 @@ enum Slot {
   S_TMP,      // scratch
   S_TMP2,
   S_NORM,     // sqrt of S_SQ
-  S_COUNT = 32
+  S_G32SUM,   // sum of the FP32-rounded source (saddle preconditioner)
+  S_BMEAN1,   // mean of g~ (saddle preconditioner)
+  S_XMEAN1,   // mean of c~* (saddle preconditioner)
+  S_UB = 64,  // mean of S U_j for the inner iterations j = 0..m (64 slots)
+  S_UX = 128, // mean of A~^-1 S U_j (64 slots)
+  S_COUNT = 192
 };
+
+__global__ void k_bmean1(double* out, const double* sum32, const double* sum64, double inv_n) {
+  if (threadIdx.x == 0) *out = (*sum32 - *sum64) * inv_n;
+}
 
 __global__ void k_scalar_affine(double* dst, const double* src, double a) {
   if (threadIdx.x == 0) *dst = a * (*src);
@@ -259,10 +268,12 @@ const T* coarse_table(ibrd_grid g, double shift) {
 }
 
 // One V-cycle on level l for A_l x = b - bshift (bshift nullable). Smoothing
-// sweeps ping-pong between x and the level's scratch field.
+// sweeps ping-pong between x and the level's scratch field. If part is
+// non-null (finest level only) the last smoothing sweep also writes per-CTA
+// sums of the new x there; the return value is their count (0: none).
 template <typename T>
-void vcycle_level(ibrd_grid g, int l, const T* b, const double* bshift, T* x, bool zero, double shift, int nu1,
-                  int nu2) {
+int vcycle_level(ibrd_grid g, int l, const T* b, const double* bshift, T* x, bool zero, double shift, int nu1,
+                 int nu2, double* part) {
   Hier<T>& H = hier<T>(g);
   const Level& lv = g->levels[l];
   const Stencil st = stencil(lv.h, g->chi, shift);
@@ -270,7 +281,7 @@ void vcycle_level(ibrd_grid g, int l, const T* b, const double* bshift, T* x, bo
     // Exact coarsest solve. A constant shift of b only changes the mean, which
     // the singular pseudo-inverse ignores; the nonsingular case never shifts.
     launch_coarse_solve<T>(coarse_table<T>(g, shift), b, x, lv.d, g->s);
-    return;
+    return 0;
   }
   // the coarse end of the hierarchy runs in one CTA out of shared memory
   if (l >= g->small_from) {
@@ -284,53 +295,87 @@ void vcycle_level(ibrd_grid g, int l, const T* b, const double* bshift, T* x, bo
       cl.ny[i] = li.d.ny;
       cl.nz[i] = li.d.nz;
       cl.off[i] = tot;
+      auto lg = [](int v) { return (v & (v - 1)) == 0 ? __builtin_ctz((unsigned)v) : -1; };
+      cl.lgx[i] = lg(li.d.nx);
+      cl.lgy[i] = lg(li.d.ny);
       cl.diag[i] = si.diag;
       cl.offd[i] = si.off;
       tot += (int)li.d.n();
     }
     cl.total = tot;
     launch_vcycle_small<T>(cl, b, x, bshift, coarse_table<T>(g, shift), zero, nu1, nu2, g->s);
-    return;
+    return 0;
   }
+  const int part_cap = kRedBlocks * kDotGroup;
   T* cur = x;
   T* oth = H.y[l];
   bool first = zero;
+  int np = 0;
   if (nu1 == 0 && zero) IBRD_CUDA(cudaMemsetAsync(x, 0, sizeof(T) * lv.d.n(), g->s));
   for (int sweep = 0; sweep < nu1; ++sweep) {
-    if (launch_rb_sweep<T>(cur, oth, b, bshift, lv.d, st, first, g->s)) std::swap(cur, oth);
+    if (launch_rb_sweep<T>(cur, oth, b, bshift, lv.d, st, first, nullptr, 0, g->s) >= 0) std::swap(cur, oth);
     first = false;
   }
   launch_resid_restrict<T>(cur, b, bshift, H.b[l + 1], lv.d, st, g->s);
-  vcycle_level<T>(g, l + 1, H.b[l + 1], nullptr, H.x[l + 1], true, shift, nu1, nu2);
+  vcycle_level<T>(g, l + 1, H.b[l + 1], nullptr, H.x[l + 1], true, shift, nu1, nu2, nullptr);
   launch_prolong8<T>(H.x[l + 1], cur, lv.d, g->s);
-  for (int sweep = 0; sweep < nu2; ++sweep)
-    if (launch_rb_sweep<T>(cur, oth, b, bshift, lv.d, st, false, g->s)) std::swap(cur, oth);
+  for (int sweep = 0; sweep < nu2; ++sweep) {
+    const bool last = (sweep == nu2 - 1);
+    const int r = launch_rb_sweep<T>(cur, oth, b, bshift, lv.d, st, false, last ? part : nullptr, part_cap, g->s);
+    if (r >= 0) std::swap(cur, oth);
+    np = last ? (r > 0 ? r : 0) : np;
+  }
   if (cur != x) IBRD_CUDA(cudaMemcpyAsync(x, cur, sizeof(T) * lv.d.n(), cudaMemcpyDeviceToDevice, g->s));
+  return np;
 }
+
+// What a singular (shift = 0) V-cycle does with the mean of its result.
+enum class XMean {
+  Project,  // subtract it: the restricted inverse of Appendix A (mean-zero result)
+  Report,   // write it to *xmean and leave x unprojected
+  Ignore    // leave x unprojected; the caller's use is invariant to a constant
+};
 
 // One V-cycle on the finest level for (shift I - chi L) x = b. When shift is
 // 0 (periodic, singular) the right-hand side is taken with its mean removed
-// and the result is returned with mean zero.
+// (bmean: that mean if the caller knows it, else computed here) and the
+// result's mean is handled as `xm` says.
 template <typename T>
-void vcycle(ibrd_grid g, const T* b, T* x, bool zero, double shift, int nu1, int nu2) {
+void vcycle(ibrd_grid g, const T* b, T* x, bool zero, double shift, int nu1, int nu2, const double* bmean = nullptr,
+            XMean xm = XMean::Project, double* xmean = nullptr) {
   ensure_hier<T>(g);
   const Dims d = g->d;
+  const bool singular = (shift == 0.0);
   const double* bshift = nullptr;
-  if (shift == 0.0) {
-    launch_sum<T>(b, d.n(), g->partial, g->scal + S_MEAN, 1.0 / (double)d.n(), g->s);
-    bshift = g->scal + S_MEAN;
+  if (singular) {
+    if (!bmean) {
+      launch_sum<T>(b, d.n(), g->partial, g->scal + S_MEAN, 1.0 / (double)d.n(), g->s);
+      bmean = g->scal + S_MEAN;
+    }
+    bshift = bmean;
   }
-  vcycle_level<T>(g, 0, b, bshift, x, zero, shift, nu1, nu2);
-  if (shift == 0.0) {
-    launch_sum<T>(x, d.n(), g->partial, g->scal + S_MEANX, 1.0 / (double)d.n(), g->s);
-    launch_sub_scalar<T>(x, d.n(), g->scal + S_MEANX, g->s);
+  const bool want = singular && xm != XMean::Ignore;
+  const int np = vcycle_level<T>(g, 0, b, bshift, x, zero, shift, nu1, nu2, want ? g->partial : nullptr);
+  if (want) {
+    double* mout = (xm == XMean::Report && xmean) ? xmean : g->scal + S_MEANX;
+    if (np > 0)
+      launch_finalize(g->partial, np, mout, 1.0 / (double)d.n(), g->s);
+    else
+      launch_sum<T>(x, d.n(), g->partial, mout, 1.0 / (double)d.n(), g->s);
+    if (xm == XMean::Project) launch_sub_scalar<T>(x, d.n(), mout, g->s);
   }
   g->vcycles++;
 }
 
+// n V-cycles; the mean options apply to every cycle (the last one's report
+// is the result's).
 template <typename T>
-void vcycles(ibrd_grid g, const T* b, T* x, bool zero, double shift, int n, int nu1, int nu2) {
-  for (int i = 0; i < n; ++i) vcycle<T>(g, b, x, zero && i == 0, shift, nu1, nu2);
+void vcycles(ibrd_grid g, const T* b, T* x, bool zero, double shift, int n, int nu1, int nu2,
+             const double* bmean = nullptr, XMean xm = XMean::Project, double* xmean = nullptr) {
+  for (int i = 0; i < n; ++i) {
+    const XMean m = (i + 1 < n && xm == XMean::Report) ? XMean::Ignore : xm;
+    vcycle<T>(g, b, x, zero && i == 0, shift, nu1, nu2, bmean, m, xmean);
+  }
 }
 
 // ---------------------------------------------------------------- Krylov
@@ -607,6 +652,15 @@ struct SaddleOp : LinOp {
   }
   // Appendix A, steps 1-5, with A~_n^-1 = n V-cycles and, for the approximate
   // Schur complement, m GMRES iterations on J A~_1^-1 S.
+  //
+  // When A is singular the restricted inverse needs mean-zero input and gives
+  // mean-zero output. The means involved are known without extra passes over
+  // the grid: spreading preserves sums (h^3 sum S u = sum u), so the mean of
+  // S U_j comes from the N-vector U_j; the source's mean comes out of the
+  // FP64 -> FP32 conversion; and the result means are summed inside the last
+  // smoothing sweep. Where a constant offset of a field cancels (c~ is used
+  // only through c~ + cbar with cbar = <f/xi - J c~> and J 1 = 1) the mean is
+  // not formed at all.
   void precond(const double* v, double* z) override {
     const size_t nc = g->d.n();
     const int N = g->blobs.n;
@@ -618,54 +672,75 @@ struct SaddleOp : LinOp {
     T* cs = pfield<T>(g, 1);   // c~* then c~
     const double volume = (double)nc * g->h * g->h * g->h;
     const double shift = g->alpha;
+    const double ih3 = inv_h3(g);
+    double* sc = g->scal;
     // step 1: g~ = g - alpha V N^-1 S <g>, c~* = A~_n^-1 g~
-    launch_convert<double, T>(vc, gt, nc, 1.0, nullptr, g->s);
+    const double* bmean = nullptr;
+    const double* xshift = nullptr;
     if (singular) {
-      launch_sum<double>(vc, nc, g->partial, g->scal + S_GSUM, 1.0, g->s);
-      // zeta S (lambda-bar 1) = (V / (N N_c)) sum(g) S 1
-      launch_spread_const<T>(g->blobs, g->d, g->scal + S_GSUM, -volume / ((double)N * (double)nc) * inv_h3(g), gt,
-                             g->s);
+      launch_convert_sum<T>(vc, gt, nc, g->partial, sc + S_GSUM, sc + S_G32SUM, g->s);
+      // zeta S (lambda-bar 1) = (V / (N N_c)) sum(g) S 1; its total is sum(g)
+      launch_spread_const<T>(g->blobs, g->d, sc + S_GSUM, -volume / ((double)N * (double)nc) * ih3, gt, g->s);
       prof_begin(P_SMALL, g->s);
-      k_scalar_affine<<<1, 1, 0, g->s>>>(g->scal + S_LBAR, g->scal + S_GSUM, volume / (zeta * N * (double)nc));
+      k_scalar_affine<<<1, 1, 0, g->s>>>(sc + S_LBAR, sc + S_GSUM, volume / (zeta * N * (double)nc));
       prof_end(P_SMALL, g->s, "lbar");
+      prof_begin(P_SMALL, g->s);
+      k_bmean1<<<1, 1, 0, g->s>>>(sc + S_BMEAN1, sc + S_G32SUM, sc + S_GSUM, 1.0 / (double)nc);
+      prof_end(P_SMALL, g->s, "bmean");
+      bmean = sc + S_BMEAN1;
+      xshift = sc + S_XMEAN1;
+      vcycles<T>(g, gt, cs, true, shift, o.mg_cycles, o.nu1, o.nu2, bmean, XMean::Report, sc + S_XMEAN1);
+    } else {
+      launch_convert<double, T>(vc, gt, nc, 1.0, nullptr, g->s);
+      vcycles<T>(g, gt, cs, true, shift, o.mg_cycles, o.nu1, o.nu2);
     }
-    vcycles<T>(g, gt, cs, true, shift, o.mg_cycles, o.nu1, o.nu2);
-    // step 2: rhs = (zeta xi)^-1 (xi J c~* - f)
+    // step 2: rhs = (zeta xi)^-1 (xi J c~* - f), with J applied to the
+    // mean-zero c~* (J 1 = 1, so subtracting the mean of c~* from J c~*)
     double* rhs = g->nv[0];
     double* lam = g->nv[1];
-    launch_interp<T>(g->blobs, g->d, cs, 1.0 / zeta, rhs, g->s);
-    launch_axpby(-1.0 / (zeta * xi), vf, 1.0, rhs, N, g->s);
+    launch_interp<T>(g->blobs, g->d, cs, 1.0, rhs, g->s);
+    launch_nvec_affine(rhs, rhs, N, 1.0 / zeta, xshift, vf, -1.0 / (zeta * xi), g->s);
     if (o.precond == IBRD_PRECOND_DIAG) {
       launch_convert<double, double>(rhs, lam, N, 1.0 / g->gamma_diag, nullptr, g->s);
       if (singular) {
-        launch_sum<double>(lam, N, g->partial, g->scal + S_TMP, 1.0 / N, g->s);
-        launch_sub_scalar<double>(lam, N, g->scal + S_TMP, g->s);
+        launch_sum<double>(lam, N, g->partial, sc + S_TMP, 1.0 / N, g->s);
+        launch_sub_scalar<double>(lam, N, sc + S_TMP, g->s);
       }
     } else {
       const int m = std::max(1, o.schur_inner);
       T* fs = pfield<T>(g, 2);
       T* fx = pfield<T>(g, 3);
-      launch_small_start(rhs, g->U, N, g->sg, m, g->s);
+      // mean of S U_j = h^-3 sum(U_j) / N_c
+      const double ub_scale = ih3 / (double)nc;
+      launch_small_start(rhs, g->U, N, g->sg, m, singular ? sc + S_UB : nullptr, ub_scale, g->s);
       for (int j = 0; j < m; ++j) {
-        launch_spread<T>(g->blobs, g->d, g->U + (size_t)j * N, nullptr, inv_h3(g), fs, 0, g->s);
-        vcycle<T>(g, fs, fx, true, shift, o.nu1, o.nu2);
+        launch_spread<T>(g->blobs, g->d, g->U + (size_t)j * N, nullptr, ih3, fs, 0, g->s);
+        if (singular)
+          vcycle<T>(g, fs, fx, true, shift, o.nu1, o.nu2, sc + S_UB + j, XMean::Report, sc + S_UX + j);
+        else
+          vcycle<T>(g, fs, fx, true, shift, o.nu1, o.nu2);
         launch_interp<T>(g->blobs, g->d, fx, 1.0, g->U + (size_t)(j + 1) * N, g->s);
-        launch_small_arnoldi(g->U, N, j, g->Hs, m + 1, g->scs, g->ssn, g->sg, g->s);
+        launch_small_arnoldi(g->U, N, j, g->Hs, m + 1, g->scs, g->ssn, g->sg, singular ? sc + S_UX + j : nullptr,
+                             singular && j + 1 < m ? sc + S_UB + j + 1 : nullptr, ub_scale, g->s);
         g->inner++;
       }
       launch_small_finish(g->U, N, m, g->Hs, m + 1, g->sg, lam, singular ? 1 : 0, g->s);
     }
-    // step 3: c~ = A~_n^-1 (g~ - zeta S lambda~) from c~*
-    launch_spread<T>(g->blobs, g->d, lam, nullptr, -zeta * inv_h3(g), gt, 1, g->s);
-    vcycles<T>(g, gt, cs, false, shift, o.mg_cycles, o.nu1, o.nu2);
-    // steps 4-5
+    // step 3: c~ = A~_n^-1 (g~ - zeta S lambda~) from c~*; lambda~ has mean
+    // zero, so the right-hand side keeps the mean of g~
+    launch_spread<T>(g->blobs, g->d, lam, nullptr, -zeta * ih3, gt, 1, g->s);
+    if (singular)
+      vcycles<T>(g, gt, cs, false, shift, o.mg_cycles, o.nu1, o.nu2, bmean, XMean::Ignore);
+    else
+      vcycles<T>(g, gt, cs, false, shift, o.mg_cycles, o.nu1, o.nu2);
+    // steps 4-5: cbar = <f/xi - J c~>, c = c~ + cbar, lambda = lambda~ + lambda-bar
     if (singular) {
       double* t = g->nv[2];
       launch_interp<T>(g->blobs, g->d, cs, 1.0, t, g->s);
-      launch_axpby(1.0 / xi, vf, -1.0, t, N, g->s);
-      launch_sum<double>(t, N, g->partial, g->scal + S_CBAR, 1.0 / N, g->s);
-      launch_convert<double, double>(lam, zl, N, 1.0, g->scal + S_LBAR, g->s);
-      launch_convert<T, double>(cs, zc, nc, 1.0, g->scal + S_CBAR, g->s);
+      launch_nvec_affine(t, t, N, -1.0, nullptr, vf, 1.0 / xi, g->s);
+      launch_sum<double>(t, N, g->partial, sc + S_CBAR, 1.0 / N, g->s);
+      launch_convert<double, double>(lam, zl, N, 1.0, sc + S_LBAR, g->s);
+      launch_convert<T, double>(cs, zc, nc, 1.0, sc + S_CBAR, g->s);
     } else {
       IBRD_CUDA(cudaMemcpyAsync(zl, lam, sizeof(double) * N, cudaMemcpyDeviceToDevice, g->s));
       launch_convert<T, double>(cs, zc, nc, 1.0, nullptr, g->s);

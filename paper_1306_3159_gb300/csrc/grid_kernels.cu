@@ -7,6 +7,7 @@
 // FP64 arithmetic on GB300 is bound by the FP64 pipe (about 0.6 T FMA/s), so
 // the FP64 kernels minimise FP64 instructions per cell; the FP32 kernels are
 // bound by HBM and keep one read of each input and one write per output.
+#include <algorithm>
 #include <cmath>
 
 #include "internal.h"
@@ -146,6 +147,35 @@ __global__ void __launch_bounds__(kRedThreads) k_finalize(const double* __restri
   if (threadIdx.x == 0) *out = acc * scale;
 }
 
+// y = (T) x with the FP64 sum of x and the sum of the converted values.
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) k_convert_sum(const double* __restrict__ x, T* __restrict__ y,
+                                                             size_t n, double* __restrict__ pin,
+                                                             double* __restrict__ pout) {
+  double si = 0.0, so = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double v = x[i];
+    const T t = (T)v;
+    y[i] = t;
+    si += v;
+    so += (double)t;
+  }
+  si = block_sum(si);
+  if (threadIdx.x == 0) pin[blockIdx.x] = si;
+  so = block_sum(so);
+  if (threadIdx.x == 0) pout[blockIdx.x] = so;
+}
+
+__global__ void k_nvec_affine(const double* __restrict__ in, double* __restrict__ out, int n, double a,
+                              const double* __restrict__ shift, const double* __restrict__ f, double bcoef) {
+  const double sh = shift ? *shift : 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double v = a * (in[i] - sh);
+    if (f) v = fma(bcoef, f[i], v);
+    out[i] = v;
+  }
+}
+
 template <typename T>
 __global__ void k_sub_scalar(T* __restrict__ x, size_t n, const double* __restrict__ m) {
   const T v = (T)(*m);
@@ -246,6 +276,30 @@ void launch_sum(const T* x, size_t n, double* partial, double* out, double scale
   prof_end(P_REDUCE, s, "finalize");
 }
 
+void launch_finalize(const double* partial, int np, double* out, double scale, cudaStream_t s) {
+  prof_begin(P_REDUCE, s);
+  k_finalize<<<1, kRedThreads, 0, s>>>(partial, np, out, scale);
+  prof_end(P_REDUCE, s, "finalize");
+}
+
+template <typename T>
+void launch_convert_sum(const double* x, T* y, size_t n, double* partial, double* out_in, double* out_out,
+                        cudaStream_t s) {
+  prof_begin(P_VEC, s);
+  k_convert_sum<T><<<kRedBlocks, kRedThreads, 0, s>>>(x, y, n, partial, partial + kRedBlocks);
+  prof_end(P_VEC, s, "convert_sum", (8.0 + sizeof(T)) * n);
+  launch_finalize(partial, kRedBlocks, out_in, 1.0, s);
+  launch_finalize(partial + kRedBlocks, kRedBlocks, out_out, 1.0, s);
+}
+
+void launch_nvec_affine(const double* in, double* out, int n, double a, const double* shift, const double* f,
+                        double bcoef, cudaStream_t s) {
+  if (n <= 0) return;
+  prof_begin(P_VEC, s);
+  k_nvec_affine<<<std::min(64, (n + 255) / 256), 256, 0, s>>>(in, out, n, a, shift, f, bcoef);
+  prof_end(P_VEC, s, "nvec_affine", 24.0 * n);
+}
+
 void launch_dot(const double* x, const double* y, size_t n, double* partial, double* out, double scale,
                 cudaStream_t s) {
   prof_begin(P_DOT, s);
@@ -300,6 +354,8 @@ void launch_nonfinite(const T* x, size_t n, int* flag, cudaStream_t s) {
 IBRD_INST(double)
 IBRD_INST(float)
 #undef IBRD_INST
+template void launch_convert_sum<float>(const double*, float*, size_t, double*, double*, double*, cudaStream_t);
+template void launch_convert_sum<double>(const double*, double*, size_t, double*, double*, double*, cudaStream_t);
 template void launch_convert<double, float>(const double*, float*, size_t, double, const double*, cudaStream_t);
 template void launch_convert<float, double>(const float*, double*, size_t, double, const double*, cudaStream_t);
 template void launch_convert<double, double>(const double*, double*, size_t, double, const double*, cudaStream_t);

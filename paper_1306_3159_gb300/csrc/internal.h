@@ -73,12 +73,14 @@ template <typename T>
 void launch_residual(const T* x, const T* b, T* y, Dims d, Stencil st, cudaStream_t s);
 // One full red-black Gauss-Seidel sweep (red = (i+j+k) even) for A x = b -
 // *bshift (bshift nullable). On levels where the fused one-pass kernel
-// applies it reads xin and writes xout (xin != xout) and returns true; on
-// small levels it updates xin in place with two half sweeps and returns
-// false. zero != 0 treats the incoming x as 0.
+// applies it reads xin and writes xout (xin != xout) and returns the number
+// of per-CTA partial sums of the new x written into part (0 when part is
+// null or holds fewer than the CTA count); on small levels it updates xin in
+// place with two half sweeps and returns -1. zero != 0 treats the incoming x
+// as 0.
 template <typename T>
-bool launch_rb_sweep(const T* xin, T* xout, const T* b, const double* bshift, Dims d, Stencil st, bool zero,
-                     cudaStream_t s);
+int launch_rb_sweep(const T* xin, T* xout, const T* b, const double* bshift, Dims d, Stencil st, bool zero,
+                    double* part, int part_cap, cudaStream_t s);
 template <typename T>
 bool rb_sweep_fused_ok(Dims d);
 // Levels handled by the single-CTA coarse V-cycle (shared-memory resident).
@@ -88,6 +90,7 @@ struct CoarseLevels {
   int total;                      // cells over all levels
   int nx[kMaxSmallLevels], ny[kMaxSmallLevels], nz[kMaxSmallLevels];
   int off[kMaxSmallLevels];       // first cell of each level in the packed arrays
+  int lgx[kMaxSmallLevels], lgy[kMaxSmallLevels];  // log2 of nx, ny, or -1 if not a power of 2
   double diag[kMaxSmallLevels], offd[kMaxSmallLevels];
 };
 // Whole V-cycle over the levels in lv (the last one solved exactly with the
@@ -114,6 +117,16 @@ void launch_coarse_table(T* table, Dims dc, Stencil st, int singular, cudaStream
 // Sum of x[0..n) into partials (kRedBlocks doubles); then finalize into *out.
 template <typename T>
 void launch_sum(const T* x, size_t n, double* partial, double* out, double scale, cudaStream_t s);
+// *out = scale * sum(partial[0..np))
+void launch_finalize(const double* partial, int np, double* out, double scale, cudaStream_t s);
+// y = (T)x with sums: *sum_in += sum(x) (FP64), *sum_out += sum(y); both sums
+// are finalized by the launcher into out_in / out_out.
+template <typename T>
+void launch_convert_sum(const double* x, T* y, size_t n, double* partial, double* out_in, double* out_out,
+                        cudaStream_t s);
+// out[i] = a * (in[i] - *shift) + bcoef * f[i]   (shift, f nullable; N-vectors)
+void launch_nvec_affine(const double* in, double* out, int n, double a, const double* shift, const double* f,
+                        double bcoef, cudaStream_t s);
 // out[0] = scale * sum(x*y)
 void launch_dot(const double* x, const double* y, size_t n, double* partial, double* out, double scale,
                 cudaStream_t s);
@@ -192,10 +205,14 @@ void launch_sqrt_scalar(const double* src, double* dst, cudaStream_t s);
 // block does the Arnoldi step on U (rows of length n, ldu) with small
 // Hessenberg Hs (ldh = m + 1), including Givens rotations.
 // Step j: w (= U[j+1]) orthogonalized against U[0..j] by MGS, normalized.
+// If wshift is non-null, *wshift is first subtracted from every entry of w;
+// if usum is non-null, *usum = usum_scale * sum(U[j+1]) after normalising.
 void launch_small_arnoldi(double* U, int n, int j, double* Hs, int ldh, double* cs, double* sn,
-                          double* gvec, cudaStream_t s);
-// U[0] = r / ||r||, gvec = [||r||, 0, ...] (r may alias U[0])
-void launch_small_start(const double* r, double* U0, int n, double* gvec, int m, cudaStream_t s);
+                          double* gvec, const double* wshift, double* usum, double usum_scale, cudaStream_t s);
+// U[0] = r / ||r||, gvec = [||r||, 0, ...] (r may alias U[0]); *usum =
+// usum_scale * sum(U[0]) if usum is non-null.
+void launch_small_start(const double* r, double* U0, int n, double* gvec, int m, double* usum, double usum_scale,
+                        cudaStream_t s);
 // x = U[0..k) y where y = R^{-1} g (solved inside); subtract mean if project.
 void launch_small_finish(const double* U, int n, int k, const double* Hs, int ldh, const double* gvec,
                          double* x, int project_mean, cudaStream_t s);

@@ -144,13 +144,23 @@ __global__ void k_sqrt_scalar(const double* __restrict__ src, double* __restrict
 constexpr int kSmallThreads = 1024;
 
 __global__ void __launch_bounds__(kSmallThreads) k_small_start(const double* __restrict__ r, double* __restrict__ U0,
-                                                                int n, double* __restrict__ gvec, int m) {
+                                                                int n, double* __restrict__ gvec, int m,
+                                                                double* __restrict__ usum, double usum_scale) {
   double s = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) s = fma(r[i], r[i], s);
   const double nrm = sqrt(block_sum_all(s));
   const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) U0[i] = r[i] * inv;
+  double su = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double u = r[i] * inv;
+    U0[i] = u;
+    su += u;
+  }
   if (threadIdx.x <= m) gvec[threadIdx.x] = (threadIdx.x == 0) ? nrm : 0.0;
+  if (usum) {
+    su = block_sum_all(su);
+    if (threadIdx.x == 0) *usum = usum_scale * su;
+  }
 }
 
 // Arnoldi step j: w = U[j+1] holds (J A~^-1 S) U[j]; modified Gram-Schmidt
@@ -158,9 +168,15 @@ __global__ void __launch_bounds__(kSmallThreads) k_small_start(const double* __r
 __global__ void __launch_bounds__(kSmallThreads) k_small_arnoldi(double* __restrict__ U, int n, int j,
                                                                   double* __restrict__ Hs, int ldh,
                                                                   double* __restrict__ cs, double* __restrict__ sn,
-                                                                  double* __restrict__ gvec) {
+                                                                  double* __restrict__ gvec,
+                                                                  const double* __restrict__ wshift,
+                                                                  double* __restrict__ usum, double usum_scale) {
   double* w = U + (size_t)(j + 1) * n;
   double* h = Hs + (size_t)j * ldh;
+  if (wshift) {
+    const double sh = *wshift;
+    for (int t = threadIdx.x; t < n; t += blockDim.x) w[t] -= sh;
+  }
   for (int i = 0; i <= j; ++i) {
     const double* u = U + (size_t)i * n;
     double s = 0.0;
@@ -174,7 +190,15 @@ __global__ void __launch_bounds__(kSmallThreads) k_small_arnoldi(double* __restr
   for (int t = threadIdx.x; t < n; t += blockDim.x) s = fma(w[t], w[t], s);
   const double nrm = sqrt(block_sum_all(s));
   const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
-  for (int t = threadIdx.x; t < n; t += blockDim.x) w[t] *= inv;
+  double su = 0.0;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    w[t] *= inv;
+    su += w[t];
+  }
+  if (usum) {
+    su = block_sum_all(su);
+    if (threadIdx.x == 0) *usum = usum_scale * su;
+  }
   if (threadIdx.x == 0) {
     h[j + 1] = nrm;
     for (int i = 0; i < j; ++i) {
@@ -299,16 +323,17 @@ void launch_sqrt_scalar(const double* src, double* dst, cudaStream_t s) {
   prof_end(P_SMALL, s, "sqrt_scalar");
 }
 
-void launch_small_start(const double* r, double* U0, int n, double* gvec, int m, cudaStream_t s) {
+void launch_small_start(const double* r, double* U0, int n, double* gvec, int m, double* usum, double usum_scale,
+                        cudaStream_t s) {
   prof_begin(P_SMALL, s);
-  k_small_start<<<1, kSmallThreads, 0, s>>>(r, U0, n, gvec, m);
+  k_small_start<<<1, kSmallThreads, 0, s>>>(r, U0, n, gvec, m, usum, usum_scale);
   prof_end(P_SMALL, s, "small_start");
 }
 
 void launch_small_arnoldi(double* U, int n, int j, double* Hs, int ldh, double* cs, double* sn, double* gvec,
-                          cudaStream_t s) {
+                          const double* wshift, double* usum, double usum_scale, cudaStream_t s) {
   prof_begin(P_SMALL, s);
-  k_small_arnoldi<<<1, kSmallThreads, 0, s>>>(U, n, j, Hs, ldh, cs, sn, gvec);
+  k_small_arnoldi<<<1, kSmallThreads, 0, s>>>(U, n, j, Hs, ldh, cs, sn, gvec, wshift, usum, usum_scale);
   prof_end(P_SMALL, s, "small_arnoldi");
 }
 

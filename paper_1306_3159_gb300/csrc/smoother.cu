@@ -14,6 +14,7 @@
 // and writes plane k-1. The sweep is out of place (x_in -> x_out), so every
 // CTA reads old values only and no CTA waits on another. HBM traffic per
 // sweep: one read of x, one read of b, one write of x.
+#include <climits>
 #include <cmath>
 
 #include "internal.h"
@@ -82,22 +83,69 @@ __device__ __forceinline__ void vset<double>(double2& v, int c, double x) {
   else v.y = x;
 }
 
+// Update of one 16-byte group for colour parity a: the active cells of the
+// group are q = a and q = a + 2 (float4) or q = a (double2); the other cells
+// keep c. left/right are the neighbours beyond the group's ends.
+__device__ __forceinline__ float4 rb_group(int a, float4 c, float left, float right, float4 u, float4 dn, float4 zm,
+                                           float4 zp, float4 bb, float sh, float off, float inv) {
+  const float c0 = a ? c.y : c.x, c1 = a ? c.w : c.z;
+  const float l0 = a ? c.x : left, r0 = a ? c.z : c.y;
+  const float l1 = a ? c.z : c.y, r1 = a ? right : c.w;
+  const float u0 = a ? u.y : u.x, u1 = a ? u.w : u.z;
+  const float d0 = a ? dn.y : dn.x, d1 = a ? dn.w : dn.z;
+  const float m0 = a ? zm.y : zm.x, m1 = a ? zm.w : zm.z;
+  const float p0 = a ? zp.y : zp.x, p1 = a ? zp.w : zp.z;
+  const float b0 = a ? bb.y : bb.x, b1 = a ? bb.w : bb.z;
+  (void)c0;
+  (void)c1;
+  const float n0 = ((b0 - sh) + off * (((l0 + r0) + (u0 + d0)) + (m0 + p0))) * inv;
+  const float n1 = ((b1 - sh) + off * (((l1 + r1) + (u1 + d1)) + (m1 + p1))) * inv;
+  float4 o = c;
+  if (a) {
+    o.y = n0;
+    o.w = n1;
+  } else {
+    o.x = n0;
+    o.z = n1;
+  }
+  return o;
+}
+__device__ __forceinline__ double2 rb_group(int a, double2 c, double left, double right, double2 u, double2 dn,
+                                            double2 zm, double2 zp, double2 bb, double sh, double off, double inv) {
+  const double l0 = a ? c.x : left, r0 = a ? right : c.y;
+  const double u0 = a ? u.y : u.x, d0 = a ? dn.y : dn.x;
+  const double m0 = a ? zm.y : zm.x, p0 = a ? zp.y : zp.x;
+  const double b0 = a ? bb.y : bb.x;
+  const double n0 = ((b0 - sh) + off * (((l0 + r0) + (u0 + d0)) + (m0 + p0))) * inv;
+  double2 o = c;
+  if (a)
+    o.y = n0;
+  else
+    o.x = n0;
+  return o;
+}
+
 // Plane layout in shared memory: x planes hold rows y0-2 .. y0+TY+1, b planes
 // rows y0-1 .. y0+TY; both hold columns x0-V .. x0+TX+V-1 (local column
 // lx = x - x0 + V), so every row starts on a 16-byte boundary and every copy,
 // including the periodic wrap at the domain edge, is one aligned 16-byte
 // cp.async. Commit group G_j holds x plane j+1 and b plane j; step j uses it.
+// Threads have fixed roles: one x-plane copy, one b-plane copy, one red
+// group (tile + ring) and one black group (tile) each at most.
 template <typename T, int TX, int TY, bool ZERO>
 __global__ void __launch_bounds__(256) k_rb_sweep(const T* __restrict__ xin, T* __restrict__ xout,
                                                   const T* __restrict__ b, const double* __restrict__ bshift, int nx,
-                                                  int ny, int nz, int zc, T inv_diag, T off) {
+                                                  int ny, int nz, int zc, T inv_diag, T off,
+                                                  double* __restrict__ part) {
   using VT = typename Vec<T>::type;
   constexpr int V = Vec<T>::V;
   constexpr int NT = 256;
   constexpr int W = TX + 2 * V;            // row length (values)
   constexpr int NV = W / V;                // vectors per row
   constexpr int XR = TY + 4, BR = TY + 2;  // rows per x / b plane
+  constexpr int TV = TX / V;
   constexpr int D = kSweepD, R = kSweepR;
+  static_assert(XR * NV <= NT && BR * NV <= NT && (TY + 2) * NV <= NT, "one item per thread");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* pxs = reinterpret_cast<T*>(smem_raw);
   T* pbs = pxs + R * XR * W;
@@ -107,101 +155,104 @@ __global__ void __launch_bounds__(256) k_rb_sweep(const T* __restrict__ xin, T* 
   const size_t plane = (size_t)nx * ny;
   const T sh = bshift ? (T)(*bshift) : (T)0;
 
+  // fixed per-thread roles
+  int gx_off = -1, sx_off = 0, gb_off = -1, sb_off = 0;
+  if (tid < XR * NV) {
+    const int r = tid / NV, v = tid - r * NV;
+    gx_off = wrap(y0 - 2 + r, ny) * nx + wrap(x0 - V + v * V, nx);
+    sx_off = r * W + v * V;
+  }
+  if (tid < BR * NV) {
+    const int r = tid / NV, v = tid - r * NV;
+    gb_off = wrap(y0 - 1 + r, ny) * nx + wrap(x0 - V + v * V, nx);
+    sb_off = r * W + v * V;
+  }
+  const bool has_red = tid < (TY + 2) * NV;
+  const int rly = 1 + tid / NV, rv = tid - (tid / NV) * NV;
+  const int ro = rly * W + rv * V;
+  const bool red_lo = rv == 0, red_hi = rv == NV - 1;  // ring edges: only one cell active
+  const bool has_black = tid < TY * TV;
+  const int bty = tid / TV, bv = 1 + (tid - (tid / TV) * TV);
+  const int bo = (2 + bty) * W + bv * V;
+  T* gout = xout + (size_t)(y0 + bty) * nx + x0 + (bv - 1) * V;
+
   auto slot_x = [&](int k) { return pxs + (k & (R - 1)) * (XR * W); };
   auto slot_b = [&](int k) { return pbs + (k & (R - 1)) * (BR * W); };
-  // vector copies of one plane: x rows y0-2.., b rows y0-1..
-  auto issue_x = [&](int k) {
-    T* dst = slot_x(k);
-    const T* src = xin + (size_t)wrap(k, nz) * plane;
-    for (int e = tid; e < XR * NV; e += NT) {
-      const int r = e / NV, v = e - r * NV;
-      T* d = dst + r * W + v * V;
-      if (ZERO) {
+  auto issue = [&](int kx, int kb) {
+    if (kx != INT_MIN && gx_off >= 0) {
+      T* d = slot_x(kx) + sx_off;
+      if (ZERO)
         *reinterpret_cast<VT*>(d) = VT{};
-      } else {
-        const int gy = wrap(y0 - 2 + r, ny), gx = wrap(x0 - V + v * V, nx);
-        cp_async16(d, src + (size_t)gy * nx + gx);
-      }
+      else
+        cp_async16(d, xin + (size_t)wrap(kx, nz) * plane + gx_off);
     }
+    if (kb != INT_MIN && gb_off >= 0) cp_async16(slot_b(kb) + sb_off, b + (size_t)wrap(kb, nz) * plane + gb_off);
   };
-  auto issue_b = [&](int k) {
-    T* dst = slot_b(k);
-    const T* src = b + (size_t)wrap(k, nz) * plane;
-    for (int e = tid; e < BR * NV; e += NT) {
-      const int r = e / NV, v = e - r * NV;
-      const int gy = wrap(y0 - 1 + r, ny), gx = wrap(x0 - V + v * V, nx);
-      cp_async16(dst + r * W + v * V, src + (size_t)gy * nx + gx);
-    }
-  };
-  // Update the cells of `colour` (0 red, 1 black) of vector group (row ly of
-  // the x plane k, vector v) whose column lies in [lo, hi]; returns the group.
-  auto update = [&](int k, int ly, int v, int colour, int lo, int hi) -> VT {
-    T* P = slot_x(k);
+  auto group = [&](int k, int o, int ly_par_base, int colour, bool lo_edge, bool hi_edge) -> VT {
+    const T* P = slot_x(k);
     const T* Pm = slot_x(k - 1);
     const T* Pp = slot_x(k + 1);
     const T* B = slot_b(k);
-    const int o = ly * W + v * V;
-    VT c = *reinterpret_cast<const VT*>(P + o);
+    const VT c = *reinterpret_cast<const VT*>(P + o);
     const VT u = *reinterpret_cast<const VT*>(P + o - W);
     const VT dn = *reinterpret_cast<const VT*>(P + o + W);
     const VT zm = *reinterpret_cast<const VT*>(Pm + o);
     const VT zp = *reinterpret_cast<const VT*>(Pp + o);
     const VT bb = *reinterpret_cast<const VT*>(B + o - W);
-    const T left = v > 0 ? P[o - 1] : (T)0;
-    const T right = v < NV - 1 ? P[o + V] : (T)0;
-    const int par = (x0 + y0 + k + ly) & 1;
-    VT out = c;
-#pragma unroll
-    for (int q = 0; q < V; ++q) {
-      const int lx = v * V + q;
-      if (((par + q) & 1) != colour || lx < lo || lx > hi) continue;
-      const T xl = q == 0 ? left : vget<T>(c, q - 1);
-      const T xr = q == V - 1 ? right : vget<T>(c, q + 1);
-      const T s = ((xl + xr) + (vget<T>(u, q) + vget<T>(dn, q))) + (vget<T>(zm, q) + vget<T>(zp, q));
-      vset<T>(out, q, ((vget<T>(bb, q) - sh) + off * s) * inv_diag);
+    const T left = lo_edge ? (T)0 : P[o - 1];
+    const T right = hi_edge ? (T)0 : P[o + V];
+    // active cells: q with (x0 + y0 + k + ly + q) % 2 == colour
+    const int a = (ly_par_base + k + colour) & 1;
+    VT r = rb_group(a, c, left, right, u, dn, zm, zp, bb, sh, off, inv_diag);
+    // ring edge groups of the red region hold one active cell each: lx = V-1
+    // (last of group 0) and lx = TX+V (first of the last group)
+    if (lo_edge) {
+      VT t = c;
+      vset<T>(t, V - 1, vget<T>(r, V - 1));
+      r = t;
     }
-    return out;
+    if (hi_edge) {
+      VT t = c;
+      vset<T>(t, 0, vget<T>(r, 0));
+      r = t;
+    }
+    return r;
   };
-  // red cells of plane k on the tile plus a 1-cell ring: rows 1..TY+2,
-  // columns V-1 .. TX+V (all NV vectors of the row)
+  const int rpar = (x0 + y0 + rly) & 1;
+  const int bpar = (x0 + y0 + 2 + bty) & 1;
   auto red = [&](int k) {
-    T* P = slot_x(k);
-    for (int e = tid; e < (TY + 2) * NV; e += NT) {
-      const int ly = 1 + e / NV, v = e - (ly - 1) * NV;
-      const VT r = update(k, ly, v, 0, V - 1, TX + V);
-      *reinterpret_cast<VT*>(P + ly * W + v * V) = r;
+    if (has_red) {
+      const VT r = group(k, ro, rpar, 0, red_lo, red_hi);
+      *reinterpret_cast<VT*>(slot_x(k) + ro) = r;
     }
   };
-  // black cells of plane k on the tile, then store the tile row of plane k
+  double xsum = 0.0;
   auto black_write = [&](int k) {
-    T* P = slot_x(k);
-    constexpr int TV = TX / V;
-    for (int e = tid; e < TY * TV; e += NT) {
-      const int ty = e / TV, v = 1 + (e - ty * TV);
-      const int ly = 2 + ty;
-      const VT r = update(k, ly, v, 1, V, TX + V - 1);
-      *reinterpret_cast<VT*>(P + ly * W + v * V) = r;
-      *reinterpret_cast<VT*>(xout + (size_t)k * plane + (size_t)(y0 + ty) * nx + x0 + (v - 1) * V) = r;
+    if (has_black) {
+      const VT r = group(k, bo, bpar, 1, false, false);
+      *reinterpret_cast<VT*>(slot_x(k) + bo) = r;
+      *reinterpret_cast<VT*>(gout + (size_t)k * plane) = r;
+      if (part) {
+        T t = vget<T>(r, 0);
+#pragma unroll
+        for (int q = 1; q < V; ++q) t += vget<T>(r, q);
+        xsum += (double)t;
+      }
     }
   };
 
-  for (int k = k0 - 2; k <= k0 + 1; ++k) issue_x(k);
-  issue_b(k0 - 1);
-  issue_b(k0);
+  issue(k0 - 2, k0 - 1);
+  issue(k0 - 1, k0);
+  issue(k0, INT_MIN);
+  issue(k0 + 1, INT_MIN);
   cp_async_commit();
   for (int j = k0 + 1; j <= k0 + D - 1; ++j) {
-    if (j <= k1) {
-      issue_x(j + 1);
-      issue_b(j);
-    }
+    if (j <= k1) issue(j + 1, j);
     cp_async_commit();
   }
   for (int k = k0; k <= k1; ++k) {
     const int j = k + D;
-    if (j <= k1) {
-      issue_x(j + 1);
-      issue_b(j);
-    }
+    if (j <= k1) issue(j + 1, j);
     cp_async_commit();
     cp_async_wait<D>();
     __syncthreads();
@@ -209,6 +260,20 @@ __global__ void __launch_bounds__(256) k_rb_sweep(const T* __restrict__ xin, T* 
     red(k);
     __syncthreads();
     if (k > k0) black_write(k - 1);
+  }
+  if (part) {
+    // deterministic CTA sum (fixed shuffle tree, then warp 0)
+    __shared__ double ws[8];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) xsum += __shfl_down_sync(0xffffffffu, xsum, o);
+    if ((tid & 31) == 0) ws[tid >> 5] = xsum;
+    __syncthreads();
+    if (tid < 32) {
+      double v = tid < NT / 32 ? ws[tid] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (tid == 0) part[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = v;
+    }
   }
 }
 
@@ -341,6 +406,19 @@ __global__ void __launch_bounds__(1024) k_vcycle_small(CoarseLevels lv, const T*
     for (int c = n0 + tid; c < lv.total; c += nt) X[c] = (T)0;
   }
   __syncthreads();
+  // cell index -> (i, j, k); shifts when the level's nx, ny are powers of 2
+  auto decode = [&](int l, int c, int& i, int& j, int& k) {
+    const int lx = lv.lgx[l], ly = lv.lgy[l];
+    if (lx >= 0 && ly >= 0) {
+      i = c & (lv.nx[l] - 1);
+      j = (c >> lx) & (lv.ny[l] - 1);
+      k = c >> (lx + ly);
+    } else {
+      i = c % lv.nx[l];
+      j = (c / lv.nx[l]) % lv.ny[l];
+      k = c / (lv.nx[l] * lv.ny[l]);
+    }
+  };
   auto sweep = [&](int l) {
     const int nx = lv.nx[l], ny = lv.ny[l], nz = lv.nz[l], n = nx * ny * nz;
     T* x = X + lv.off[l];
@@ -348,7 +426,8 @@ __global__ void __launch_bounds__(1024) k_vcycle_small(CoarseLevels lv, const T*
     const T inv = (T)(1.0 / lv.diag[l]), off = (T)lv.offd[l];
     for (int colour = 0; colour < 2; ++colour) {
       for (int c = tid; c < n; c += nt) {
-        const int i = c % nx, j = (c / nx) % ny, k = c / (nx * ny);
+        int i, j, k;
+        decode(l, c, i, j, k);
         if (((i + j + k) & 1) != colour) continue;
         const T s = ((x[c - i + wrap(i - 1, nx)] + x[c - i + wrap(i + 1, nx)]) +
                      (x[c + (wrap(j - 1, ny) - j) * nx] + x[c + (wrap(j + 1, ny) - j) * nx])) +
@@ -369,7 +448,8 @@ __global__ void __launch_bounds__(1024) k_vcycle_small(CoarseLevels lv, const T*
     T* bc = B + lv.off[l + 1];
     const T diag = (T)lv.diag[l], off = (T)lv.offd[l];
     for (int C = tid; C < nc; C += nt) {
-      const int I = C % nxc, J = (C / nxc) % nyc, K = C / (nxc * nyc);
+      int I, J, K;
+      decode(l + 1, C, I, J, K);
       T acc = 0;
       for (int dz = 0; dz < 2; ++dz)
         for (int dy = 0; dy < 2; ++dy)
@@ -409,7 +489,8 @@ __global__ void __launch_bounds__(1024) k_vcycle_small(CoarseLevels lv, const T*
     const T* xc = X + lv.off[l + 1];
     const T w3 = (T)0.75, w1 = (T)0.25;
     for (int c = tid; c < n; c += nt) {
-      const int i = c % nx, j = (c / nx) % ny, k = c / (nx * ny);
+      int i, j, k;
+      decode(l, c, i, j, k);
       const int I = i >> 1, J = j >> 1, K = k >> 1;
       const int I2 = (i & 1) ? wrap(I + 1, nxc) : wrap(I - 1, nxc);
       const int J2 = (j & 1) ? wrap(J + 1, nyc) : wrap(J - 1, nyc);
@@ -436,27 +517,28 @@ bool rb_sweep_fused_ok(Dims d) {
 
 template <typename T, int TX, bool ZERO>
 void sweep_launch(dim3 g, cudaStream_t s, const T* xin, T* xout, const T* b, const double* bshift, Dims d, int zc,
-                  T inv, T off) {
+                  T inv, T off, double* part) {
   constexpr size_t sm = sweep_smem<T, TX, 8>();
   static bool attr = false;
   if (!attr) {
     IBRD_CUDA(cudaFuncSetAttribute(k_rb_sweep<T, TX, 8, ZERO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     attr = true;
   }
-  k_rb_sweep<T, TX, 8, ZERO><<<g, 256, sm, s>>>(xin, xout, b, bshift, d.nx, d.ny, d.nz, zc, inv, off);
+  k_rb_sweep<T, TX, 8, ZERO><<<g, 256, sm, s>>>(xin, xout, b, bshift, d.nx, d.ny, d.nz, zc, inv, off, part);
 }
 
 template <typename T>
-bool launch_rb_sweep(const T* xin, T* xout, const T* b, const double* bshift, Dims d, Stencil st, bool zero,
-                     cudaStream_t s) {
+int launch_rb_sweep(const T* xin, T* xout, const T* b, const double* bshift, Dims d, Stencil st, bool zero,
+                    double* part, int part_cap, cudaStream_t s) {
   const int c = pcls<T>(P_RBGS64, P_RBGS32);
   const T inv = (T)(1.0 / st.diag), off = (T)st.off;
   if (rb_sweep_fused_ok<T>(d)) {
-    const bool wide = (d.nx % 64 == 0);
+    // 64-wide tiles for FP32 (18 vectors per row), 32-wide for FP64
+    const bool wide = (sizeof(T) == 4) && (d.nx % 64 == 0);
     const int TX = wide ? 64 : 32, TY = 8;
     const int cols = (d.nx / TX) * (d.ny / TY);
     // about one wave of resident CTAs: chunks per column = resident slots / columns
-    const size_t sm = wide ? sweep_smem<T, 64, 8>() : sweep_smem<T, 32, 8>();
+    const size_t sm = wide ? sweep_smem<T, (sizeof(T) == 4 ? 64 : 32), 8>() : sweep_smem<T, 32, 8>();
     int per_sm = (int)(200 * 1024 / sm);
     per_sm = per_sm < 1 ? 1 : (per_sm > 8 ? 8 : per_sm);
     const int slots = 152 * per_sm;
@@ -465,21 +547,26 @@ bool launch_rb_sweep(const T* xin, T* xout, const T* b, const double* bshift, Di
     int zc = (d.nz + chunks - 1) / chunks;
     if (zc < 2) zc = 2;
     dim3 g(d.nx / TX, d.ny / TY, (d.nz + zc - 1) / zc);
+    const int nblk = (int)(g.x * g.y * g.z);
+    if (nblk > part_cap) part = nullptr;
     prof_begin(c, s);
-    if (wide) {
+    if constexpr (sizeof(T) == 4) {
+      if (wide) {
+        if (zero)
+          sweep_launch<T, 64, true>(g, s, xin, xout, b, bshift, d, zc, inv, off, part);
+        else
+          sweep_launch<T, 64, false>(g, s, xin, xout, b, bshift, d, zc, inv, off, part);
+      }
+    }
+    if (!wide) {
       if (zero)
-        sweep_launch<T, 64, true>(g, s, xin, xout, b, bshift, d, zc, inv, off);
+        sweep_launch<T, 32, true>(g, s, xin, xout, b, bshift, d, zc, inv, off, part);
       else
-        sweep_launch<T, 64, false>(g, s, xin, xout, b, bshift, d, zc, inv, off);
-    } else {
-      if (zero)
-        sweep_launch<T, 32, true>(g, s, xin, xout, b, bshift, d, zc, inv, off);
-      else
-        sweep_launch<T, 32, false>(g, s, xin, xout, b, bshift, d, zc, inv, off);
+        sweep_launch<T, 32, false>(g, s, xin, xout, b, bshift, d, zc, inv, off, part);
     }
     // one read of x (skipped from zero), one read of b, one write of x
     prof_end(c, s, "rb_sweep", (zero ? 2.0 : 3.0) * sizeof(T) * d.n());
-    return true;
+    return part ? nblk : 0;
   }
   // small levels: two in-place half sweeps
   const int np = d.nx / 2;
@@ -492,9 +579,9 @@ bool launch_rb_sweep(const T* xin, T* xout, const T* b, const double* bshift, Di
     prof_begin(c, s);
     k_rb_half<T><<<g, blk, 0, s>>>(xin, const_cast<T*>(xin), b, bshift, d.nx, d.ny, d.nz, zc, inv, off, colour,
                                    (zero && colour == 0) ? 1 : 0);
-    prof_end(c, s, "rb_half", (zero && colour == 0 ? 1.5 : 1.5) * sizeof(T) * d.n());
+    prof_end(c, s, "rb_half", 1.5 * sizeof(T) * d.n());
   }
-  return false;
+  return -1;
 }
 
 template <typename T>
@@ -537,7 +624,8 @@ void launch_vcycle_small(const CoarseLevels& lv, const T* b, T* x, const double*
 #define IBRD_INST(T)                                                                                         \
   template void launch_vcycle_small<T>(const CoarseLevels&, const T*, T*, const double*, const T*, bool, int,  \
                                        int, cudaStream_t);                                                  \
-  template bool launch_rb_sweep<T>(const T*, T*, const T*, const double*, Dims, Stencil, bool, cudaStream_t); \
+  template int launch_rb_sweep<T>(const T*, T*, const T*, const double*, Dims, Stencil, bool, double*, int,    \
+                                  cudaStream_t);                                                            \
   template void launch_resid_restrict<T>(const T*, const T*, const double*, T*, Dims, Stencil, cudaStream_t); \
   template void launch_prolong8<T>(const T*, T*, Dims, cudaStream_t);                                       \
   template bool rb_sweep_fused_ok<T>(Dims);
