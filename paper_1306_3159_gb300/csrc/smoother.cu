@@ -34,9 +34,8 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// Ring depths (planes) of the pipelined sweep: x needs the 4 planes k-2..k+1
-// in use plus D in flight, b the 2 planes k-1, k plus D in flight.
-constexpr int kSweepD = 3, kSweepR = 8;
+// Ring depth (planes) of the pipelined sweep, for x and for b.
+constexpr int kSweepR = 8;
 
 // 16-byte vectors: V values per vector.
 template <typename T>
@@ -129,23 +128,38 @@ __device__ __forceinline__ double2 rb_group(int a, double2 c, double left, doubl
 // rows y0-1 .. y0+TY; both hold columns x0-V .. x0+TX+V-1 (local column
 // lx = x - x0 + V), so every row starts on a 16-byte boundary and every copy,
 // including the periodic wrap at the domain edge, is one aligned 16-byte
-// cp.async. Commit group G_j holds x plane j+1 and b plane j; step j uses it.
-// Threads have fixed roles: one x-plane copy, one b-plane copy, one red
-// group (tile + ring) and one black group (tile) each at most.
+// cp.async.
+//
+// Schedule: phase p updates the red cells of plane p (tile + ring) AND the
+// black cells of plane p-2 (tile), then stores plane p-2. The two touch
+// disjoint cells: red(p) reads planes p-1..p+1 and writes red cells of p;
+// black(p-2) reads red cells of planes p-3..p-1, all final by phase p-1, and
+// writes black cells of p-2. So one barrier per plane suffices. Warps 0-5
+// own the red groups, warps 6-9 the black groups.
+//
+// Copies: group G_q = {x plane q+1, b plane q} is needed by red(q); it is
+// issued at the start of phase q-2 (prefetch distance 2). With rings of 8
+// planes the target slots are never in use by a thread still in phase p-1.
+constexpr int kSweepThreads = 320;
+
 template <typename T, int TX, int TY, bool ZERO>
-__global__ void __launch_bounds__(256) k_rb_sweep(const T* __restrict__ xin, T* __restrict__ xout,
-                                                  const T* __restrict__ b, const double* __restrict__ bshift, int nx,
-                                                  int ny, int nz, int zc, T inv_diag, T off,
-                                                  double* __restrict__ part) {
+__global__ void __launch_bounds__(kSweepThreads) k_rb_sweep(const T* __restrict__ xin, T* __restrict__ xout,
+                                                            const T* __restrict__ b,
+                                                            const double* __restrict__ bshift, int nx, int ny,
+                                                            int nz, int zc, T inv_diag, T off,
+                                                            double* __restrict__ part) {
   using VT = typename Vec<T>::type;
   constexpr int V = Vec<T>::V;
-  constexpr int NT = 256;
+  constexpr int NT = kSweepThreads;
   constexpr int W = TX + 2 * V;            // row length (values)
   constexpr int NV = W / V;                // vectors per row
   constexpr int XR = TY + 4, BR = TY + 2;  // rows per x / b plane
   constexpr int TV = TX / V;
-  constexpr int D = kSweepD, R = kSweepR;
-  static_assert(XR * NV <= NT && BR * NV <= NT && (TY + 2) * NV <= NT, "one item per thread");
+  constexpr int R = kSweepR;
+  constexpr int NRED = (TY + 2) * NV, NBLK = TY * TV;
+  constexpr int BLK0 = 192;  // first thread of the black role (warp 6)
+  static_assert(NRED <= BLK0 && NBLK <= NT - BLK0, "role sizes");
+  static_assert(XR * NV <= 2 * NT && BR * NV <= NT, "copy roles");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* pxs = reinterpret_cast<T*>(smem_raw);
   T* pbs = pxs + R * XR * W;
@@ -155,44 +169,75 @@ __global__ void __launch_bounds__(256) k_rb_sweep(const T* __restrict__ xin, T* 
   const size_t plane = (size_t)nx * ny;
   const T sh = bshift ? (T)(*bshift) : (T)0;
 
-  // fixed per-thread roles
-  int gx_off = -1, sx_off = 0, gb_off = -1, sb_off = 0;
-  if (tid < XR * NV) {
-    const int r = tid / NV, v = tid - r * NV;
-    gx_off = wrap(y0 - 2 + r, ny) * nx + wrap(x0 - V + v * V, nx);
-    sx_off = r * W + v * V;
+  // copy roles: x-plane vectors e = tid and tid + NT, b-plane vector e = tid
+  int gx0 = -1, sx0 = 0, gx1 = -1, sx1 = 0, gb = -1, sb = 0;
+  {
+    int e = tid;
+    if (e < XR * NV) {
+      const int r = e / NV, v = e - r * NV;
+      gx0 = wrap(y0 - 2 + r, ny) * nx + wrap(x0 - V + v * V, nx);
+      sx0 = r * W + v * V;
+    }
+    e = tid + NT;
+    if (e < XR * NV) {
+      const int r = e / NV, v = e - r * NV;
+      gx1 = wrap(y0 - 2 + r, ny) * nx + wrap(x0 - V + v * V, nx);
+      sx1 = r * W + v * V;
+    }
+    if (tid < BR * NV) {
+      const int r = tid / NV, v = tid - r * NV;
+      gb = wrap(y0 - 1 + r, ny) * nx + wrap(x0 - V + v * V, nx);
+      sb = r * W + v * V;
+    }
   }
-  if (tid < BR * NV) {
-    const int r = tid / NV, v = tid - r * NV;
-    gb_off = wrap(y0 - 1 + r, ny) * nx + wrap(x0 - V + v * V, nx);
-    sb_off = r * W + v * V;
+  // update roles
+  const bool is_red = tid < NRED;
+  const bool is_black = tid >= BLK0 && tid < BLK0 + NBLK;
+  int go, gpar;
+  bool lo_edge = false, hi_edge = false;
+  T* gout = xout;
+  if (tid < BLK0) {
+    const int ly = 1 + tid / NV, v = tid - (tid / NV) * NV;
+    go = ly * W + v * V;
+    gpar = (x0 + y0 + ly) & 1;
+    lo_edge = v == 0;
+    hi_edge = v == NV - 1;
+  } else {
+    const int e = tid - BLK0;
+    const int ty = e / TV, v = 1 + (e - (e / TV) * TV);
+    go = (2 + ty) * W + v * V;
+    gpar = (x0 + y0 + 2 + ty) & 1;
+    gout = xout + (size_t)(y0 + ty) * nx + x0 + (v - 1) * V;
   }
-  const bool has_red = tid < (TY + 2) * NV;
-  const int rly = 1 + tid / NV, rv = tid - (tid / NV) * NV;
-  const int ro = rly * W + rv * V;
-  const bool red_lo = rv == 0, red_hi = rv == NV - 1;  // ring edges: only one cell active
-  const bool has_black = tid < TY * TV;
-  const int bty = tid / TV, bv = 1 + (tid - (tid / TV) * TV);
-  const int bo = (2 + bty) * W + bv * V;
-  T* gout = xout + (size_t)(y0 + bty) * nx + x0 + (bv - 1) * V;
 
   auto slot_x = [&](int k) { return pxs + (k & (R - 1)) * (XR * W); };
   auto slot_b = [&](int k) { return pbs + (k & (R - 1)) * (BR * W); };
-  auto issue = [&](int kx, int kb) {
-    if (kx != INT_MIN && gx_off >= 0) {
-      T* d = slot_x(kx) + sx_off;
+  auto copy_x = [&](int k) {
+    const T* src = xin + (size_t)wrap(k, nz) * plane;
+    T* dst = slot_x(k);
+    if (gx0 >= 0) {
       if (ZERO)
-        *reinterpret_cast<VT*>(d) = VT{};
+        *reinterpret_cast<VT*>(dst + sx0) = VT{};
       else
-        cp_async16(d, xin + (size_t)wrap(kx, nz) * plane + gx_off);
+        cp_async16(dst + sx0, src + gx0);
     }
-    if (kb != INT_MIN && gb_off >= 0) cp_async16(slot_b(kb) + sb_off, b + (size_t)wrap(kb, nz) * plane + gb_off);
+    if (gx1 >= 0) {
+      if (ZERO)
+        *reinterpret_cast<VT*>(dst + sx1) = VT{};
+      else
+        cp_async16(dst + sx1, src + gx1);
+    }
   };
-  auto group = [&](int k, int o, int ly_par_base, int colour, bool lo_edge, bool hi_edge) -> VT {
+  auto copy_b = [&](int k) {
+    if (gb >= 0) cp_async16(slot_b(k) + sb, b + (size_t)wrap(k, nz) * plane + gb);
+  };
+  // colour 0 = red (active lanes of the group follow from the global parity)
+  auto group = [&](int k, int colour) -> VT {
     const T* P = slot_x(k);
     const T* Pm = slot_x(k - 1);
     const T* Pp = slot_x(k + 1);
     const T* B = slot_b(k);
+    const int o = go;
     const VT c = *reinterpret_cast<const VT*>(P + o);
     const VT u = *reinterpret_cast<const VT*>(P + o - W);
     const VT dn = *reinterpret_cast<const VT*>(P + o + W);
@@ -201,8 +246,7 @@ __global__ void __launch_bounds__(256) k_rb_sweep(const T* __restrict__ xin, T* 
     const VT bb = *reinterpret_cast<const VT*>(B + o - W);
     const T left = lo_edge ? (T)0 : P[o - 1];
     const T right = hi_edge ? (T)0 : P[o + V];
-    // active cells: q with (x0 + y0 + k + ly + q) % 2 == colour
-    const int a = (ly_par_base + k + colour) & 1;
+    const int a = (gpar + k + colour) & 1;
     VT r = rb_group(a, c, left, right, u, dn, zm, zp, bb, sh, off, inv_diag);
     // ring edge groups of the red region hold one active cell each: lx = V-1
     // (last of group 0) and lx = TX+V (first of the last group)
@@ -218,54 +262,50 @@ __global__ void __launch_bounds__(256) k_rb_sweep(const T* __restrict__ xin, T* 
     }
     return r;
   };
-  const int rpar = (x0 + y0 + rly) & 1;
-  const int bpar = (x0 + y0 + 2 + bty) & 1;
-  auto red = [&](int k) {
-    if (has_red) {
-      const VT r = group(k, ro, rpar, 0, red_lo, red_hi);
-      *reinterpret_cast<VT*>(slot_x(k) + ro) = r;
-    }
-  };
   double xsum = 0.0;
-  auto black_write = [&](int k) {
-    if (has_black) {
-      const VT r = group(k, bo, bpar, 1, false, false);
-      *reinterpret_cast<VT*>(slot_x(k) + bo) = r;
-      *reinterpret_cast<VT*>(gout + (size_t)k * plane) = r;
-      if (part) {
-        T t = vget<T>(r, 0);
-#pragma unroll
-        for (int q = 1; q < V; ++q) t += vget<T>(r, q);
-        xsum += (double)t;
-      }
-    }
-  };
 
-  issue(k0 - 2, k0 - 1);
-  issue(k0 - 1, k0);
-  issue(k0, INT_MIN);
-  issue(k0 + 1, INT_MIN);
+  constexpr int D = 2;
+  // prologue: x planes k0-2, k0-1 plus G_{k0-1} = {x(k0), b(k0-1)}, then G_{k0}
+  copy_x(k0 - 2);
+  copy_x(k0 - 1);
+  copy_x(k0);
+  copy_b(k0 - 1);
   cp_async_commit();
-  for (int j = k0 + 1; j <= k0 + D - 1; ++j) {
-    if (j <= k1) issue(j + 1, j);
-    cp_async_commit();
-  }
-  for (int k = k0; k <= k1; ++k) {
-    const int j = k + D;
-    if (j <= k1) issue(j + 1, j);
+  copy_x(k0 + 1);
+  copy_b(k0);
+  cp_async_commit();
+  for (int p = k0 - 1; p <= k1 + 1; ++p) {
+    const int q = p + D;
+    if (q <= k1) {
+      copy_x(q + 1);
+      copy_b(q);
+    }
     cp_async_commit();
     cp_async_wait<D>();
     __syncthreads();
-    if (k == k0) red(k0 - 1);
-    red(k);
-    __syncthreads();
-    if (k > k0) black_write(k - 1);
+    if (is_red && p <= k1) {
+      const VT r = group(p, 0);
+      *reinterpret_cast<VT*>(slot_x(p) + go) = r;
+    }
+    const int kb = p - 2;
+    if (is_black && kb >= k0) {
+      const VT r = group(kb, 1);
+      *reinterpret_cast<VT*>(slot_x(kb) + go) = r;
+      *reinterpret_cast<VT*>(gout + (size_t)kb * plane) = r;
+      if (part) {
+        T t = vget<T>(r, 0);
+#pragma unroll
+        for (int qq = 1; qq < V; ++qq) t += vget<T>(r, qq);
+        xsum += (double)t;
+      }
+    }
   }
   if (part) {
     // deterministic CTA sum (fixed shuffle tree, then warp 0)
-    __shared__ double ws[8];
+    __shared__ double ws[NT / 32];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) xsum += __shfl_down_sync(0xffffffffu, xsum, o);
+    __syncthreads();
     if ((tid & 31) == 0) ws[tid >> 5] = xsum;
     __syncthreads();
     if (tid < 32) {
@@ -524,7 +564,8 @@ void sweep_launch(dim3 g, cudaStream_t s, const T* xin, T* xout, const T* b, con
     IBRD_CUDA(cudaFuncSetAttribute(k_rb_sweep<T, TX, 8, ZERO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     attr = true;
   }
-  k_rb_sweep<T, TX, 8, ZERO><<<g, 256, sm, s>>>(xin, xout, b, bshift, d.nx, d.ny, d.nz, zc, inv, off, part);
+  k_rb_sweep<T, TX, 8, ZERO><<<g, kSweepThreads, sm, s>>>(xin, xout, b, bshift, d.nx, d.ny, d.nz, zc, inv, off,
+                                                           part);
 }
 
 template <typename T>
