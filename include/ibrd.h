@@ -69,6 +69,9 @@ typedef struct {
   int nu1, nu2;      /* red-black Gauss-Seidel sweeps before/after (2, 2) */
   int precision;     /* IBRD_FP64 or IBRD_MIXED_FP32; -1 = the handle's */
   int use_guess;     /* 1: c (and lambda) hold an initial guess; 0: start at 0 */
+  int reorth;        /* Gram-Schmidt second pass: 0 never, 1 when the new
+                        vector's norm drops below 1/sqrt(2) of its value
+                        (default), 2 always */
 } ibrd_solve_opts;
 
 /* Solve report. residual_history, if non-NULL, is a caller-owned HOST array
@@ -79,6 +82,7 @@ typedef struct {
   int outer_iters;     /* outer FGMRES iterations */
   int inner_iters;     /* inner Schur Krylov iterations (saddle) */
   int vcycles;         /* V-cycles applied (the paper's cost proxy, Sec. III.E) */
+  int reorths;         /* Gram-Schmidt second passes taken */
   double rel_residual; /* final relative true residual */
   double sum_lambda;   /* sum_i lambda_i (saddle) or sum_i kappa_i (J c)_i */
   double cbar;         /* mean of c over all cells (Sec. IV.A) */

@@ -190,6 +190,7 @@ struct ibrd_grid_s {
   // counters of the current solve
   long vcycles = 0;
   long inner = 0;
+  long reorths = 0;
   Profiler prof;
   std::string err;
 };
@@ -415,7 +416,7 @@ void ensure_krylov(ibrd_grid g, size_t n, int restart) {
 // w (= V[j+1]) <- w - sum_{i<=j} h_i V[i], h written into H[:, j]; returns
 // ||w||^2 after orthogonalisation in S_SQ. Classical Gram-Schmidt with a
 // second pass when the norm drops below 1/sqrt(2) of its value (DGKS test).
-double orthogonalize(ibrd_grid g, int j, size_t n, int ldh, double* ww_out) {
+double orthogonalize(ibrd_grid g, int j, size_t n, int ldh, double* ww_out, int reorth) {
   double* V = g->V;
   double* w = V + (size_t)(j + 1) * n;
   double* hcol = g->H + (size_t)j * ldh;
@@ -439,7 +440,8 @@ double orthogonalize(ibrd_grid g, int j, size_t n, int ldh, double* ww_out) {
   const double ww = g->host[0];
   double sq = g->host[1];
   if (ww_out) *ww_out = ww;
-  if (sq < 0.5 * ww) {
+  if (reorth == 2 || (reorth == 1 && sq < 0.5 * ww)) {
+    g->reorths++;
     // pass 2
     for (int g0 = 0; g0 < nb; g0 += kDotGroup) {
       const int m = std::min(kDotGroup, nb - g0);
@@ -517,7 +519,7 @@ SolveResult fgmres(ibrd_grid g, LinOp& op, const double* b, double* x, size_t n,
       op.precond(V + (size_t)j * n, Z + (size_t)j * n);
       op.apply(Z + (size_t)j * n, V + (size_t)(j + 1) * n);
       double ww = 0;
-      const double sq = orthogonalize(g, j, n, ldh, &ww);
+      const double sq = orthogonalize(g, j, n, ldh, &ww, o.reorth);
       double* hcol = g->H + (size_t)j * ldh;
       launch_sqrt_scalar(g->scal + S_SQ, hcol + j + 1, g->s);
       const bool tiny = !(sq > 1e-28 * ww) || sq <= 0.0;
@@ -805,6 +807,7 @@ ibrd_solve_opts resolve_opts(ibrd_grid g, const ibrd_solve_opts* in) {
   if (o.xi <= 0.0) o.xi = o.zeta / (g->h * g->h * g->h);
   if (!(o.tol > 0.0) || o.restart < 1 || o.restart > 60 || o.max_iter < 0 || o.mg_cycles < 1 ||
       o.schur_inner < 1 || o.schur_inner > 60 || o.nu1 < 0 || o.nu2 < 0 || !(o.zeta != 0.0) ||
+      o.reorth < 0 || o.reorth > 2 ||
       (o.precision != IBRD_FP64 && o.precision != IBRD_MIXED_FP32) ||
       (o.precond != IBRD_PRECOND_SCHUR && o.precond != IBRD_PRECOND_DIAG))
     throw ArgError{IBRD_ERR_ARG, "invalid solver options"};
@@ -817,6 +820,7 @@ void fill_info(ibrd_solve_info* info, const SolveResult& R, ibrd_grid g, double 
   info->outer_iters = R.iters;
   info->inner_iters = (int)g->inner;
   info->vcycles = (int)g->vcycles;
+  info->reorths = (int)g->reorths;
   info->rel_residual = R.rel;
   info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count() - t0;
 }
@@ -863,6 +867,7 @@ void ibrd_default_opts(ibrd_solve_opts* o) {
   o->nu2 = 2;
   o->precision = -1;
   o->use_guess = 0;
+  o->reorth = 1;
 }
 
 const char* ibrd_status_string(int st) {
@@ -896,7 +901,7 @@ void ibrd_grid_destroy(ibrd_grid g) {
   for (auto& e : g->h32.tables) F(e.second);
   BlobSet& b = g->blobs;
   F(b.q); F(b.idx); F(b.w64); F(b.w32); F(b.tile_count); F(b.tile_offset); F(b.tile_cursor); F(b.tile_blobs);
-  F(b.active); F(b.d_meta);
+  F(b.active); F(b.d_meta); F(b.cell_count); F(b.cell_offset); F(b.cells); F(b.cell_tile);
   F(g->scal); F(g->partial); F(g->dflag);
   if (g->host) cudaFreeHost(g->host);
   F(g->V); F(g->Z); F(g->H); F(g->cs); F(g->sn); F(g->gvec); F(g->yv); F(g->hb2); F(g->xs); F(g->bs);
@@ -1036,6 +1041,7 @@ ibrd_status ibrd_solve_reaction(ibrd_grid g, const double* kappa, const double* 
     if (!rhs || !c || (N > 0 && !kappa)) throw ArgError{IBRD_ERR_ARG, "null pointer"};
     g->vcycles = 0;
     g->inner = 0;
+    g->reorths = 0;
     ensure_nvec(g, o.schur_inner);
     double sigma = g->alpha;
     if (N > 0) {
@@ -1076,6 +1082,7 @@ ibrd_status ibrd_solve_saddle(ibrd_grid g, const double* rhs, const double* f, d
     if (!rhs || !c || !lambda) throw ArgError{IBRD_ERR_ARG, "null pointer"};
     g->vcycles = 0;
     g->inner = 0;
+    g->reorths = 0;
     ensure_nvec(g, o.schur_inner);
     const size_t nc = g->d.n();
     const size_t n = nc + N;

@@ -7,6 +7,7 @@
 // support touches, and one CTA per occupied tile gathers, for each of its
 // cells, the contributions of the tile's blobs in increasing blob index, so
 // the result is deterministic and each field cell is written once.
+#include <algorithm>
 #include <cmath>
 
 #include "internal.h"
@@ -171,41 +172,112 @@ __global__ void k_tile_sort(const int* __restrict__ active, int na, const int* _
   }
 }
 
-// One CTA per occupied tile, one thread per tile cell (8x8x8).
+// Is cell (i, j, k) inside the support of blob b? (offsets from the blob's
+// first support cell, per axis, in [0, 4))
+__device__ __forceinline__ bool covers(const int* __restrict__ ib, int i, int j, int k, int nx, int ny, int nz,
+                                       int& dx, int& dy, int& dz) {
+  dx = i - ib[0];
+  dy = j - ib[4];
+  dz = k - ib[8];
+  dx += dx < 0 ? nx : 0;
+  dy += dy < 0 ? ny : 0;
+  dz += dz < 0 ? nz : 0;
+  return (unsigned)dx < 4u && (unsigned)dy < 4u && (unsigned)dz < 4u;
+}
+
+// Pass 1 (count) and pass 2 (fill) of the covered-cell list: one CTA per
+// occupied tile, one thread per tile cell.
+template <bool FILL>
+__global__ void __launch_bounds__(512) k_cover(const int* __restrict__ active, const int* __restrict__ offset,
+                                               const int* __restrict__ list, const int* __restrict__ idx, int nx,
+                                               int ny, int nz, int ntx, int nty, int* __restrict__ count,
+                                               const int* __restrict__ coff, int* __restrict__ cells,
+                                               int* __restrict__ cell_tile) {
+  const int a = blockIdx.x;
+  const int tile = active[a];
+  const int tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
+  const int i = tx * kTile + threadIdx.x, j = ty * kTile + threadIdx.y, k = tz * kTile + threadIdx.z;
+  bool hit = false;
+  if (i < nx && j < ny && k < nz) {
+    for (int p = offset[tile]; p < offset[tile + 1] && !hit; ++p) {
+      int dx, dy, dz;
+      hit = covers(idx + list[p] * 12, i, j, k, nx, ny, nz, dx, dy, dz);
+    }
+  }
+  if (!FILL) {
+    const int c = __syncthreads_count(hit);
+    if (threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0) count[a] = c;
+    return;
+  }
+  // rank of this cell among the block's covered cells, in thread order
+  __shared__ int wsum[16];
+  const int t = threadIdx.x + kTile * (threadIdx.y + kTile * threadIdx.z);
+  const unsigned bal = __ballot_sync(0xffffffffu, hit);
+  const int lane = t & 31, w = t >> 5;
+  if (lane == 0) wsum[w] = __popc(bal);
+  __syncthreads();
+  int base = 0;
+  for (int u = 0; u < w; ++u) base += wsum[u];
+  if (hit) {
+    const int r = coff[a] + base + __popc(bal & ((1u << lane) - 1u));
+    cells[r] = (k * ny + j) * nx + i;
+    cell_tile[r] = tile;
+  }
+}
+
+// Exclusive scan of n ints (single block), total into *total.
+__global__ void __launch_bounds__(1024) k_scan_ints(const int* __restrict__ in, int n, int* __restrict__ out,
+                                                    int* __restrict__ total) {
+  __shared__ int s_sum[1024];
+  const int t = threadIdx.x;
+  const int chunk = (n + blockDim.x - 1) / blockDim.x;
+  const int lo = min(n, t * chunk), hi = min(n, lo + chunk);
+  int sum = 0;
+  for (int i = lo; i < hi; ++i) sum += in[i];
+  s_sum[t] = sum;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    const int v = t >= o ? s_sum[t - o] : 0;
+    __syncthreads();
+    s_sum[t] += v;
+    __syncthreads();
+  }
+  int run = s_sum[t] - sum;
+  for (int i = lo; i < hi; ++i) {
+    out[i] = run;
+    run += in[i];
+  }
+  if (t == blockDim.x - 1) {
+    out[n] = s_sum[t];
+    *total = s_sum[t];
+  }
+}
+
+// One thread per covered cell: gathers the contributions of its tile's blobs
+// in increasing blob index.
 template <typename T, typename W>
-__global__ void __launch_bounds__(512) k_spread(const int* __restrict__ active, const int* __restrict__ offset,
+__global__ void __launch_bounds__(256) k_spread(const int* __restrict__ cells, const int* __restrict__ cell_tile,
+                                                int n_cells, const int* __restrict__ offset,
                                                 const int* __restrict__ list, const int* __restrict__ idx,
                                                 const W* __restrict__ wt, const double* __restrict__ lam,
                                                 const double* __restrict__ cval, const double* __restrict__ coef,
-                                                double scale, T* __restrict__ out, int accumulate, int nx, int ny,
-                                                int nz, int ntx, int nty) {
-  const int tile = active[blockIdx.x];
-  const int tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
-  const int i = tx * kTile + threadIdx.x, j = ty * kTile + threadIdx.y, k = tz * kTile + threadIdx.z;
-  const int lo = offset[tile], hi = offset[tile + 1];
+                                                double scale, T* __restrict__ out, int nx, int ny, int nz) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_cells) return;
+  const int cell = cells[t], tile = cell_tile[t];
+  const int i = cell % nx, j = (cell / nx) % ny, k = cell / (nx * ny);
   W acc = 0;
-  bool hit = false;
-  for (int p = lo; p < hi; ++p) {
+  for (int p = offset[tile]; p < offset[tile + 1]; ++p) {
     const int b = list[p];
-    const int* ib = idx + b * 12;
-    // offset of this cell from the blob's first support cell, per axis
-    int dx = i - ib[0], dy = j - ib[4], dz = k - ib[8];
-    dx += dx < 0 ? nx : 0;
-    dy += dy < 0 ? ny : 0;
-    dz += dz < 0 ? nz : 0;
-    if ((unsigned)dx < 4u && (unsigned)dy < 4u && (unsigned)dz < 4u) {
+    int dx, dy, dz;
+    if (covers(idx + b * 12, i, j, k, nx, ny, nz, dx, dy, dz)) {
       const W* wb = wt + b * 12;
       const double l = lam ? lam[b] : *cval;
       const W amp = (W)(coef ? coef[b] * l : l);
       acc += amp * ((wb[dx] * wb[4 + dy]) * wb[8 + dz]);
-      hit = true;
     }
   }
-  if (hit && i < nx && j < ny && k < nz) {
-    const size_t p = ((size_t)k * ny + j) * nx + i;
-    const T v = (T)scale * (T)acc;
-    out[p] = accumulate ? out[p] + v : v;
-  }
+  out[cell] += (T)scale * (T)acc;
 }
 
 // One warp per blob: lanes cover the 4x4x4 support, two cells each.
@@ -247,9 +319,14 @@ void blobs_setup(BlobSet& b, Dims d, double h, const double* q_in, int n, cudaSt
     IBRD_CUDA(cudaMalloc(&b.tile_offset, sizeof(int) * (nt + 1)));
     IBRD_CUDA(cudaMalloc(&b.tile_cursor, sizeof(int) * nt));
     IBRD_CUDA(cudaMalloc(&b.active, sizeof(int) * nt));
+    cudaFree(b.cell_count);
+    cudaFree(b.cell_offset);
+    b.cell_count = b.cell_offset = nullptr;
+    IBRD_CUDA(cudaMalloc(&b.cell_count, sizeof(int) * (nt + 1)));
+    IBRD_CUDA(cudaMalloc(&b.cell_offset, sizeof(int) * (nt + 1)));
     b.ntiles = nt;
   }
-  if (!b.d_meta) IBRD_CUDA(cudaMalloc(&b.d_meta, sizeof(int) * 2));
+  if (!b.d_meta) IBRD_CUDA(cudaMalloc(&b.d_meta, sizeof(int) * 4));
   if (n > b.cap) {
     cudaFree(b.q);
     cudaFree(b.idx);
@@ -301,40 +378,67 @@ void blobs_setup(BlobSet& b, Dims d, double h, const double* q_in, int n, cudaSt
       prof_end(P_SETUP, s, "tile_sort");
     }
   }
+  // covered-cell list (count per occupied tile, scan, ordered fill)
+  b.n_cells = 0;
+  if (n > 0 && b.n_active > 0) {
+    const dim3 tb(kTile, kTile, kTile);
+    prof_begin(P_SETUP, s);
+    k_cover<false><<<b.n_active, tb, 0, s>>>(b.active, b.tile_offset, b.tile_blobs, b.idx, d.nx, d.ny, d.nz, b.ntx,
+                                             b.nty, b.cell_count, nullptr, nullptr, nullptr);
+    prof_end(P_SETUP, s, "cover_count");
+    prof_begin(P_SETUP, s);
+    k_scan_ints<<<1, 1024, 0, s>>>(b.cell_count, b.n_active, b.cell_offset, b.d_meta + 2);
+    prof_end(P_SETUP, s, "cover_scan");
+    int nc = 0;
+    IBRD_CUDA(cudaMemcpyAsync(&nc, b.d_meta + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
+    IBRD_CUDA(cudaStreamSynchronize(s));
+    if (nc > b.cell_cap || !b.cells) {
+      cudaFree(b.cells);
+      cudaFree(b.cell_tile);
+      b.cells = b.cell_tile = nullptr;
+      const int cap = std::max(nc, 1);
+      IBRD_CUDA(cudaMalloc(&b.cells, sizeof(int) * cap));
+      IBRD_CUDA(cudaMalloc(&b.cell_tile, sizeof(int) * cap));
+      b.cell_cap = cap;
+    }
+    prof_begin(P_SETUP, s);
+    k_cover<true><<<b.n_active, tb, 0, s>>>(b.active, b.tile_offset, b.tile_blobs, b.idx, d.nx, d.ny, d.nz, b.ntx,
+                                            b.nty, nullptr, b.cell_offset, b.cells, b.cell_tile);
+    prof_end(P_SETUP, s, "cover_fill");
+    b.n_cells = nc;
+  }
 }
 
 template <typename T>
 void launch_spread(const BlobSet& b, Dims d, const double* lam, const double* coef, double scale, T* out,
                    int accumulate, cudaStream_t s) {
   if (!accumulate) IBRD_CUDA(cudaMemsetAsync(out, 0, sizeof(T) * d.n(), s));
-  if (b.n == 0 || b.n_active == 0) return;
+  if (b.n == 0 || b.n_cells == 0) return;
   const int c = pcls<T>(P_SPREAD64, P_SPREAD32);
+  const int blocks = (b.n_cells + 255) / 256;
   prof_begin(c, s);
   if (sizeof(T) == 8)
-    k_spread<T, double><<<b.n_active, dim3(kTile, kTile, kTile), 0, s>>>(
-        b.active, b.tile_offset, b.tile_blobs, b.idx, b.w64, lam, nullptr, coef, scale, out, 1, d.nx, d.ny, d.nz,
-        b.ntx, b.nty);
+    k_spread<T, double><<<blocks, 256, 0, s>>>(b.cells, b.cell_tile, b.n_cells, b.tile_offset, b.tile_blobs, b.idx,
+                                               b.w64, lam, nullptr, coef, scale, out, d.nx, d.ny, d.nz);
   else
-    k_spread<T, float><<<b.n_active, dim3(kTile, kTile, kTile), 0, s>>>(
-        b.active, b.tile_offset, b.tile_blobs, b.idx, b.w32, lam, nullptr, coef, scale, out, 1, d.nx, d.ny, d.nz,
-        b.ntx, b.nty);
-  prof_end(c, s, "spread", (double)b.n * (64.0 * 2.0 * sizeof(T) + 48.0 + 12.0 * sizeof(T) + 16.0));
+    k_spread<T, float><<<blocks, 256, 0, s>>>(b.cells, b.cell_tile, b.n_cells, b.tile_offset, b.tile_blobs, b.idx,
+                                              b.w32, lam, nullptr, coef, scale, out, d.nx, d.ny, d.nz);
+  prof_end(c, s, "spread", (double)b.n_cells * (2.0 * sizeof(T) + 8.0) + (double)b.n * (48.0 + 12.0 * sizeof(T) + 16.0));
 }
 
 template <typename T>
 void launch_spread_const(const BlobSet& b, Dims d, const double* cval, double scale, T* out, cudaStream_t s) {
-  if (b.n == 0 || b.n_active == 0) return;
+  if (b.n == 0 || b.n_cells == 0) return;
   const int c = pcls<T>(P_SPREAD64, P_SPREAD32);
+  const int blocks = (b.n_cells + 255) / 256;
   prof_begin(c, s);
   if (sizeof(T) == 8)
-    k_spread<T, double><<<b.n_active, dim3(kTile, kTile, kTile), 0, s>>>(
-        b.active, b.tile_offset, b.tile_blobs, b.idx, b.w64, nullptr, cval, nullptr, scale, out, 1, d.nx, d.ny,
-        d.nz, b.ntx, b.nty);
+    k_spread<T, double><<<blocks, 256, 0, s>>>(b.cells, b.cell_tile, b.n_cells, b.tile_offset, b.tile_blobs, b.idx,
+                                               b.w64, nullptr, cval, nullptr, scale, out, d.nx, d.ny, d.nz);
   else
-    k_spread<T, float><<<b.n_active, dim3(kTile, kTile, kTile), 0, s>>>(
-        b.active, b.tile_offset, b.tile_blobs, b.idx, b.w32, nullptr, cval, nullptr, scale, out, 1, d.nx, d.ny,
-        d.nz, b.ntx, b.nty);
-  prof_end(c, s, "spread_const", (double)b.n * (64.0 * 2.0 * sizeof(T) + 48.0 + 12.0 * sizeof(T)));
+    k_spread<T, float><<<blocks, 256, 0, s>>>(b.cells, b.cell_tile, b.n_cells, b.tile_offset, b.tile_blobs, b.idx,
+                                              b.w32, nullptr, cval, nullptr, scale, out, d.nx, d.ny, d.nz);
+  prof_end(c, s, "spread_const", (double)b.n_cells * (2.0 * sizeof(T) + 8.0) + (double)b.n * (48.0 + 12.0 * sizeof(T)));
 }
 
 template <typename T>

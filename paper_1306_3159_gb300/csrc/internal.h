@@ -164,7 +164,14 @@ struct BlobSet {
   int pair_cap = 0;
   int* active = nullptr;       // active tile ids (ntiles capacity)
   int n_active = 0;
-  int* d_meta = nullptr;       // [0] = pairs, [1] = active tiles
+  int* d_meta = nullptr;       // [0] = pairs, [1] = active tiles, [2] = covered cells
+  // cells covered by at least one blob support, in (tile, cell) order
+  int* cell_count = nullptr;   // per active tile
+  int* cell_offset = nullptr;  // per active tile + 1
+  int* cells = nullptr;        // linear cell index
+  int* cell_tile = nullptr;    // tile id of each covered cell
+  int cell_cap = 0;
+  int n_cells = 0;
 };
 
 void blobs_setup(BlobSet& b, Dims d, double h, const double* q_in, int n, cudaStream_t s);
