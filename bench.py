@@ -32,6 +32,11 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "solve time at rel. residual 1e-8, 256³+4096 blobs: plain vs chosen; % HBM peak"
+# Chosen solver settings for this workload (FP32 multigrid in FP64 FGMRES):
+# second Gram-Schmidt pass only under severe cancellation (||w'|| < 1e-3 ||w||),
+# and the V-cycle counts / sweeps that minimised time to 1e-8 on GB300.
+CHOSEN_REACTION = dict(mg_cycles=1, nu1=1, nu2=2, reorth_eta=1e-3)
+CHOSEN_SADDLE = dict(schur_inner=4, mg_cycles=1, nu1=1, nu2=1, reorth_eta=1e-3)
 UNIT = "s"
 WORKLOAD = "scale"
 
@@ -170,11 +175,18 @@ def run_ours(args):
     out_l = torch.empty(N, dtype=torch.float64).pin_memory()
     tol = 1e-8
     infos = {}
+    chosen = p.IBRD_MIXED_FP32
+    plain = p.IBRD_FP64
+    # solver settings: the plain path keeps the library defaults (the paper's
+    # m = 5, n = 1, nu = 2/2 and a DGKS second Gram-Schmidt pass); the chosen
+    # path uses the settings tuned for this workload on GB300
+    settings = {plain: ({}, {}), chosen: (CHOSEN_REACTION, CHOSEN_SADDLE)}
 
     def step(precision, qd=q_d, kd=k_d, gd=g_d):
+        kr, ks = settings[precision]
         grid.set_blobs(qd)
-        _, ir = grid.solve_reaction(kd, gd, c_r, tol=tol, precision=precision, max_iter=3000)
-        _, _, isd = grid.solve_saddle(gd, c=c_s, lam=lam, tol=tol, precision=precision, max_iter=3000)
+        _, ir = grid.solve_reaction(kd, gd, c_r, tol=tol, precision=precision, max_iter=3000, **kr)
+        _, _, isd = grid.solve_saddle(gd, c=c_s, lam=lam, tol=tol, precision=precision, max_iter=3000, **ks)
         infos[precision] = (ir, isd)
 
     def step_e2e(precision):
@@ -213,8 +225,6 @@ def run_ours(args):
         barrier()
         return max_over_ranks(e0.elapsed_time(e1) / 1e3 / k)
 
-    chosen = p.IBRD_MIXED_FP32
-    plain = p.IBRD_FP64
     if args.ncu_step:
         # profiler range around one chosen step (ncu --profile-from-start off)
         for _ in range(args.warmup):
@@ -275,7 +285,7 @@ def run_ours(args):
 
     def solve_summary(i):
         return {"outer_iters": i["outer_iters"], "inner_iters": i["inner_iters"], "vcycles": i["vcycles"],
-                "rel_residual": i["rel_residual"], "rate_K": i["rate_K"], "cbar": i["cbar"]}
+                "reorths": i["reorths"], "rel_residual": i["rel_residual"], "rate_K": i["rate_K"], "cbar": i["cbar"]}
 
     h2d = (q_h.numel() + k_h.numel() + g_h.numel()) * 8
     d2h = (out_cr.numel() + out_cs.numel() + out_l.numel()) * 8
@@ -287,7 +297,9 @@ def run_ours(args):
         "config": {"workload": "256^3 periodic grid, 4096 RSA blobs (spacing 4h), uniform source, steady; "
                                "reaction (kappa log-uniform [0.1,10]) + saddle solves to rel. residual 1e-8",
                    "grid": [nx, ny, nz], "blobs": N, "tol": tol, "precision": "FP32 multigrid + spread/interp "
-                   "in FP64 FGMRES(30)", "preconditioner": "approximate Schur m=5, n=1 (saddle); 1 V-cycle (reaction)",
+                   "in FP64 FGMRES(30)", "reaction_opts": CHOSEN_REACTION, "saddle_opts": CHOSEN_SADDLE,
+                   "preconditioner": "approximate Schur (saddle, Appendix A); V-cycles of (sigma I - chi L) "
+                                     "(reaction)",
                    "parallelism": f"replicas x{world}",
                    "l2": "no flush: working set > L2 (one FP64 field is 134 MB, a step streams hundreds of fields)"},
         "gpu_launches": prof_timed["launches"] // max(1, args.steps) * args.steps,

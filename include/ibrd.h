@@ -69,9 +69,10 @@ typedef struct {
   int nu1, nu2;      /* red-black Gauss-Seidel sweeps before/after (2, 2) */
   int precision;     /* IBRD_FP64 or IBRD_MIXED_FP32; -1 = the handle's */
   int use_guess;     /* 1: c (and lambda) hold an initial guess; 0: start at 0 */
-  int reorth;        /* Gram-Schmidt second pass: 0 never, 1 when the new
-                        vector's norm drops below 1/sqrt(2) of its value
-                        (default), 2 always */
+  double reorth_eta; /* classical Gram-Schmidt takes a second pass when the
+                        orthogonalised vector's norm falls below reorth_eta
+                        times its norm before (DGKS test): 1/sqrt(2) (default),
+                        0 never, >= 1 always */
 } ibrd_solve_opts;
 
 /* Solve report. residual_history, if non-NULL, is a caller-owned HOST array

@@ -31,7 +31,8 @@ class SolveOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("restart", ctypes.c_int),
                 ("mg_cycles", ctypes.c_int), ("schur_inner", ctypes.c_int), ("precond", ctypes.c_int),
                 ("zeta", ctypes.c_double), ("xi", ctypes.c_double), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
-                ("precision", ctypes.c_int), ("use_guess", ctypes.c_int), ("reorth", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("use_guess", ctypes.c_int),
+                ("reorth_eta", ctypes.c_double)]
 
 
 class SolveInfo(ctypes.Structure):

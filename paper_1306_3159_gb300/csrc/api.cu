@@ -416,7 +416,7 @@ void ensure_krylov(ibrd_grid g, size_t n, int restart) {
 // w (= V[j+1]) <- w - sum_{i<=j} h_i V[i], h written into H[:, j]; returns
 // ||w||^2 after orthogonalisation in S_SQ. Classical Gram-Schmidt with a
 // second pass when the norm drops below 1/sqrt(2) of its value (DGKS test).
-double orthogonalize(ibrd_grid g, int j, size_t n, int ldh, double* ww_out, int reorth) {
+double orthogonalize(ibrd_grid g, int j, size_t n, int ldh, double* ww_out, double eta) {
   double* V = g->V;
   double* w = V + (size_t)(j + 1) * n;
   double* hcol = g->H + (size_t)j * ldh;
@@ -440,7 +440,7 @@ double orthogonalize(ibrd_grid g, int j, size_t n, int ldh, double* ww_out, int 
   const double ww = g->host[0];
   double sq = g->host[1];
   if (ww_out) *ww_out = ww;
-  if (reorth == 2 || (reorth == 1 && sq < 0.5 * ww)) {
+  if (eta >= 1.0 || sq < eta * eta * ww) {
     g->reorths++;
     // pass 2
     for (int g0 = 0; g0 < nb; g0 += kDotGroup) {
@@ -519,7 +519,7 @@ SolveResult fgmres(ibrd_grid g, LinOp& op, const double* b, double* x, size_t n,
       op.precond(V + (size_t)j * n, Z + (size_t)j * n);
       op.apply(Z + (size_t)j * n, V + (size_t)(j + 1) * n);
       double ww = 0;
-      const double sq = orthogonalize(g, j, n, ldh, &ww, o.reorth);
+      const double sq = orthogonalize(g, j, n, ldh, &ww, o.reorth_eta);
       double* hcol = g->H + (size_t)j * ldh;
       launch_sqrt_scalar(g->scal + S_SQ, hcol + j + 1, g->s);
       const bool tiny = !(sq > 1e-28 * ww) || sq <= 0.0;
@@ -807,7 +807,7 @@ ibrd_solve_opts resolve_opts(ibrd_grid g, const ibrd_solve_opts* in) {
   if (o.xi <= 0.0) o.xi = o.zeta / (g->h * g->h * g->h);
   if (!(o.tol > 0.0) || o.restart < 1 || o.restart > 60 || o.max_iter < 0 || o.mg_cycles < 1 ||
       o.schur_inner < 1 || o.schur_inner > 60 || o.nu1 < 0 || o.nu2 < 0 || !(o.zeta != 0.0) ||
-      o.reorth < 0 || o.reorth > 2 ||
+      !(o.reorth_eta >= 0.0) ||
       (o.precision != IBRD_FP64 && o.precision != IBRD_MIXED_FP32) ||
       (o.precond != IBRD_PRECOND_SCHUR && o.precond != IBRD_PRECOND_DIAG))
     throw ArgError{IBRD_ERR_ARG, "invalid solver options"};
@@ -867,7 +867,7 @@ void ibrd_default_opts(ibrd_solve_opts* o) {
   o->nu2 = 2;
   o->precision = -1;
   o->use_guess = 0;
-  o->reorth = 1;
+  o->reorth_eta = 0.70710678118654752;
 }
 
 const char* ibrd_status_string(int st) {
