@@ -42,6 +42,8 @@ enum Slot {
   S_G32SUM,   // sum of the FP32-rounded source (saddle preconditioner)
   S_BMEAN1,   // mean of g~ (saddle preconditioner)
   S_XMEAN1,   // mean of c~* (saddle preconditioner)
+  S_RFLAG,    // Gram-Schmidt second pass taken in this iteration (0/1)
+  S_RCOUNT,   // second passes taken in this solve
   S_UB = 64,  // mean of S U_j for the inner iterations j = 0..m (64 slots)
   S_UX = 128, // mean of A~^-1 S U_j (64 slots)
   S_COUNT = 192
@@ -416,7 +418,12 @@ void ensure_krylov(ibrd_grid g, size_t n, int restart) {
 // w (= V[j+1]) <- w - sum_{i<=j} h_i V[i], h written into H[:, j]; returns
 // ||w||^2 after orthogonalisation in S_SQ. Classical Gram-Schmidt with a
 // second pass when the norm drops below 1/sqrt(2) of its value (DGKS test).
-double orthogonalize(ibrd_grid g, int j, size_t n, int ldh, double* ww_out, double eta) {
+// w (= V[j+1]) <- w - sum_{i<=j} h_i V[i], h written into H[:, j]; ||w||^2
+// after orthogonalisation lands in S_SQ, ||w||^2 before in S_TMP. Classical
+// Gram-Schmidt; the second pass (DGKS test with threshold eta) is decided on
+// the device and its kernels return at once when it is not needed, so the
+// host does not wait here.
+void orthogonalize(ibrd_grid g, int j, size_t n, int ldh, double eta) {
   double* V = g->V;
   double* w = V + (size_t)(j + 1) * n;
   double* hcol = g->H + (size_t)j * ldh;
@@ -434,30 +441,21 @@ double orthogonalize(ibrd_grid g, int j, size_t n, int ldh, double* ww_out, doub
     launch_multi_axpy(w, V + (size_t)g0 * n, n, m, hcol + g0, -1.0, n, last ? g->partial : nullptr, g->s);
   }
   launch_reduce_partials(g->partial, 1, g->scal + S_SQ, g->s);
-  IBRD_CUDA(cudaMemcpyAsync(g->host, g->scal + S_TMP, sizeof(double) * 1, cudaMemcpyDeviceToHost, g->s));
-  IBRD_CUDA(cudaMemcpyAsync(g->host + 1, g->scal + S_SQ, sizeof(double) * 1, cudaMemcpyDeviceToHost, g->s));
-  IBRD_CUDA(cudaStreamSynchronize(g->s));
-  const double ww = g->host[0];
-  double sq = g->host[1];
-  if (ww_out) *ww_out = ww;
-  if (eta >= 1.0 || sq < eta * eta * ww) {
-    g->reorths++;
-    // pass 2
-    for (int g0 = 0; g0 < nb; g0 += kDotGroup) {
-      const int m = std::min(kDotGroup, nb - g0);
-      launch_multidot(V + (size_t)g0 * n, n, m, w, n, g->partial, g->s);
-      launch_reduce_partials(g->partial, m, g->hb2 + g0, g->s);
-    }
-    for (int g0 = 0; g0 < nb; g0 += kDotGroup) {
-      const int m = std::min(kDotGroup, nb - g0);
-      const bool last = g0 + m >= nb;
-      launch_multi_axpy(w, V + (size_t)g0 * n, n, m, g->hb2 + g0, -1.0, n, last ? g->partial : nullptr, g->s);
-    }
-    launch_reduce_partials(g->partial, 1, g->scal + S_SQ, g->s);
-    launch_vec_add_small(hcol, g->hb2, nb, g->s);
-    sq = host_scalar(g, S_SQ);
+  if (eta <= 0.0) return;
+  const double* gate = g->scal + S_RFLAG;
+  launch_reorth_flag(g->scal + S_TMP, g->scal + S_SQ, eta, g->scal + S_RFLAG, g->scal + S_RCOUNT, g->s);
+  for (int g0 = 0; g0 < nb; g0 += kDotGroup) {
+    const int m = std::min(kDotGroup, nb - g0);
+    launch_multidot(V + (size_t)g0 * n, n, m, w, n, g->partial, g->s, gate);
+    launch_reduce_partials(g->partial, m, g->hb2 + g0, g->s, gate);
   }
-  return sq;
+  for (int g0 = 0; g0 < nb; g0 += kDotGroup) {
+    const int m = std::min(kDotGroup, nb - g0);
+    const bool last = g0 + m >= nb;
+    launch_multi_axpy(w, V + (size_t)g0 * n, n, m, g->hb2 + g0, -1.0, n, last ? g->partial : nullptr, g->s, gate);
+  }
+  launch_reduce_partials(g->partial, 1, g->scal + S_SQ, g->s, gate);
+  launch_vec_add_small(hcol, g->hb2, nb, g->s, gate);
 }
 
 struct SolveResult {
@@ -472,6 +470,7 @@ SolveResult fgmres(ibrd_grid g, LinOp& op, const double* b, double* x, size_t n,
   SolveResult R;
   const int m = std::max(1, o.restart);
   ensure_krylov(g, n, m);
+  IBRD_CUDA(cudaMemsetAsync(g->scal + S_RCOUNT, 0, sizeof(double), g->s));
   const int ldh = m + 1;
   double* V = g->V;
   double* Z = g->Z;
@@ -518,14 +517,18 @@ SolveResult fgmres(ibrd_grid g, LinOp& op, const double* b, double* x, size_t n,
     for (int j = 0; j < m; ++j) {
       op.precond(V + (size_t)j * n, Z + (size_t)j * n);
       op.apply(Z + (size_t)j * n, V + (size_t)(j + 1) * n);
-      double ww = 0;
-      const double sq = orthogonalize(g, j, n, ldh, &ww, o.reorth_eta);
+      orthogonalize(g, j, n, ldh, o.reorth_eta);
       double* hcol = g->H + (size_t)j * ldh;
       launch_sqrt_scalar(g->scal + S_SQ, hcol + j + 1, g->s);
-      const bool tiny = !(sq > 1e-28 * ww) || sq <= 0.0;
-      if (!tiny) launch_scale_by_inv(V + (size_t)(j + 1) * n, V + (size_t)(j + 1) * n, n, hcol + j + 1, 1.0, g->s);
+      launch_scale_by_inv(V + (size_t)(j + 1) * n, V + (size_t)(j + 1) * n, n, hcol + j + 1, 1.0, g->s);
       launch_givens(g->H, ldh, j, g->cs, g->sn, g->gvec, g->scal + S_RES, g->s);
-      const double res = host_scalar(g, S_RES);
+      // one host read per iteration: residual estimate and the norms
+      IBRD_CUDA(cudaMemcpyAsync(g->host, g->scal, sizeof(double) * 16, cudaMemcpyDeviceToHost, g->s));
+      IBRD_CUDA(cudaStreamSynchronize(g->s));
+      const double res = g->host[S_RES], sq = g->host[S_SQ], ww = g->host[S_TMP];
+      // breakdown: w lies in the span of V (a zero or negligible new column);
+      // V[j+1] is then not used again
+      const bool tiny = !(sq > 1e-28 * ww) || sq <= 0.0;
       k = j + 1;
       R.iters++;
       if (info && info->residual_history && hist < info->history_cap) info->residual_history[hist++] = res / bnorm;
@@ -563,6 +566,7 @@ SolveResult fgmres(ibrd_grid g, LinOp& op, const double* b, double* x, size_t n,
     }
   }
   if (info) info->history_len = hist;
+  g->reorths = (long)host_scalar(g, S_RCOUNT);
   return R;
 }
 

@@ -152,13 +152,22 @@ template <typename T>
 __global__ void __launch_bounds__(kRedThreads) k_convert_sum(const double* __restrict__ x, T* __restrict__ y,
                                                              size_t n, double* __restrict__ pin,
                                                              double* __restrict__ pout) {
+  // the input sum needs one FP64 add per value; the converted values are
+  // summed in T over runs of 8 and folded into FP64
   double si = 0.0, so = 0.0;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const double v = x[i];
-    const T t = (T)v;
-    y[i] = t;
-    si += v;
-    so += (double)t;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  while (i < n) {
+    T run = 0;
+#pragma unroll 4
+    for (int r = 0; r < 8 && i < n; ++r, i += stride) {
+      const double v = x[i];
+      const T t = (T)v;
+      y[i] = t;
+      si += v;
+      run += t;
+    }
+    so += (double)run;
   }
   si = block_sum(si);
   if (threadIdx.x == 0) pin[blockIdx.x] = si;

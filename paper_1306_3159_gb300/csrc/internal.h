@@ -190,13 +190,15 @@ void launch_interp(const BlobSet& b, Dims d, const T* x, double scale, double* o
 // ---------------------------------------------------------------- Krylov kernels
 constexpr int kDotGroup = 8;
 // partial[g * kRedBlocks + blk] for g < nvec (nvec <= kDotGroup)
+// gate (nullable device scalar): the kernel does nothing when *gate == 0.
 void launch_multidot(const double* V, size_t ldv, int nvec, const double* w, size_t n, double* partial,
-                     cudaStream_t s);
+                     cudaStream_t s, const double* gate = nullptr);
 // out[g] = sum_blk partial[g*kRedBlocks + blk]   (g < nvec)
-void launch_reduce_partials(const double* partial, int nvec, double* out, cudaStream_t s);
+void launch_reduce_partials(const double* partial, int nvec, double* out, cudaStream_t s,
+                            const double* gate = nullptr);
 // w += sign * sum_g coef[g] V[g]; optional partial sums of squares of new w.
 void launch_multi_axpy(double* w, const double* V, size_t ldv, int nvec, const double* coef, double sign,
-                       size_t n, double* partial_sq, cudaStream_t s);
+                       size_t n, double* partial_sq, cudaStream_t s, const double* gate = nullptr);
 // Givens step j on column H[:, j] (ldh = restart + 1): rotations cs/sn,
 // residual vector gvec; writes |gvec[j+1]| to *res.
 void launch_givens(double* H, int ldh, int j, double* cs, double* sn, double* gvec, double* res,
@@ -204,7 +206,9 @@ void launch_givens(double* H, int ldh, int j, double* cs, double* sn, double* gv
 // Back substitution y = R^{-1} g for the leading k x k block.
 void launch_backsolve(const double* H, int ldh, int k, const double* gvec, double* y, cudaStream_t s);
 // Combine two dot results: h[i] += h2[i] for i < n (device).
-void launch_vec_add_small(double* h, const double* h2, int n, cudaStream_t s);
+void launch_vec_add_small(double* h, const double* h2, int n, cudaStream_t s, const double* gate = nullptr);
+// *flag = (eta >= 1 || *sq < eta^2 *ww); *count += *flag
+void launch_reorth_flag(const double* ww, const double* sq, double eta, double* flag, double* count, cudaStream_t s);
 // *dst = sqrt(*src)
 void launch_sqrt_scalar(const double* src, double* dst, cudaStream_t s);
 

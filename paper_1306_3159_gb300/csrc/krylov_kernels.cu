@@ -48,7 +48,8 @@ __device__ __forceinline__ double block_sum_all(double v) {
 template <int NV>
 __global__ void __launch_bounds__(kRedThreads) k_multidot(const double* __restrict__ V, size_t ldv,
                                                           const double* __restrict__ w, size_t n,
-                                                          double* __restrict__ partial) {
+                                                          double* __restrict__ partial, const double* __restrict__ gate) {
+  if (gate && *gate == 0.0) return;
   double acc[NV];
 #pragma unroll
   for (int g = 0; g < NV; ++g) acc[g] = 0.0;
@@ -65,7 +66,9 @@ __global__ void __launch_bounds__(kRedThreads) k_multidot(const double* __restri
 }
 
 __global__ void __launch_bounds__(kRedThreads) k_reduce_partials(const double* __restrict__ partial,
-                                                                 double* __restrict__ out) {
+                                                                 double* __restrict__ out,
+                                                                 const double* __restrict__ gate) {
+  if (gate && *gate == 0.0) return;
   // blockIdx.x = vector g
   double acc = 0.0;
   for (int i = threadIdx.x; i < kRedBlocks; i += blockDim.x) acc += partial[blockIdx.x * kRedBlocks + i];
@@ -76,7 +79,9 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_partials(const double* _
 template <int NV, bool SQ>
 __global__ void __launch_bounds__(kRedThreads) k_multi_axpy(double* __restrict__ w, const double* __restrict__ V,
                                                             size_t ldv, const double* __restrict__ coef,
-                                                            double sign, size_t n, double* __restrict__ partial_sq) {
+                                                            double sign, size_t n, double* __restrict__ partial_sq,
+                                                            const double* __restrict__ gate) {
+  if (gate && *gate == 0.0) return;
   double c[NV];
 #pragma unroll
   for (int g = 0; g < NV; ++g) c[g] = sign * coef[g];
@@ -131,9 +136,21 @@ __global__ void k_backsolve(const double* __restrict__ H, int ldh, int k, const 
   }
 }
 
-__global__ void k_vec_add_small(double* __restrict__ h, const double* __restrict__ h2, int n) {
+__global__ void k_vec_add_small(double* __restrict__ h, const double* __restrict__ h2, int n,
+                                const double* __restrict__ gate) {
+  if (gate && *gate == 0.0) return;
   const int i = threadIdx.x;
   if (i < n) h[i] += h2[i];
+}
+
+// flag = 1 when the Gram-Schmidt second pass is needed: ||w'||^2 < eta^2 ||w||^2
+// (or eta >= 1); counts the passes in *count.
+__global__ void k_reorth_flag(const double* __restrict__ ww, const double* __restrict__ sq, double eta,
+                              double* __restrict__ flag, double* __restrict__ count) {
+  if (threadIdx.x != 0) return;
+  const double f = (eta >= 1.0 || *sq < eta * eta * *ww) ? 1.0 : 0.0;
+  *flag = f;
+  *count += f;
 }
 
 __global__ void k_sqrt_scalar(const double* __restrict__ src, double* __restrict__ dst) {
@@ -253,12 +270,12 @@ __global__ void __launch_bounds__(kSmallThreads) k_small_finish(const double* __
 }  // namespace
 
 void launch_multidot(const double* V, size_t ldv, int nvec, const double* w, size_t n, double* partial,
-                     cudaStream_t s) {
+                     cudaStream_t s, const double* gate) {
   if (nvec < 1 || nvec > kDotGroup) return;
   prof_begin(P_DOT, s);
   switch (nvec) {
 #define IBRD_CASE(k) \
-  case k: k_multidot<k><<<kRedBlocks, kRedThreads, 0, s>>>(V, ldv, w, n, partial); break;
+  case k: k_multidot<k><<<kRedBlocks, kRedThreads, 0, s>>>(V, ldv, w, n, partial, gate); break;
     IBRD_CASE(1) IBRD_CASE(2) IBRD_CASE(3) IBRD_CASE(4) IBRD_CASE(5) IBRD_CASE(6) IBRD_CASE(7) IBRD_CASE(8)
 #undef IBRD_CASE
     default: return;
@@ -266,22 +283,22 @@ void launch_multidot(const double* V, size_t ldv, int nvec, const double* w, siz
   prof_end(P_DOT, s, "multidot", 8.0 * (nvec + 1) * n);
 }
 
-void launch_reduce_partials(const double* partial, int nvec, double* out, cudaStream_t s) {
+void launch_reduce_partials(const double* partial, int nvec, double* out, cudaStream_t s, const double* gate) {
   if (nvec <= 0) return;
   prof_begin(P_REDUCE, s);
-  k_reduce_partials<<<nvec, kRedThreads, 0, s>>>(partial, out);
+  k_reduce_partials<<<nvec, kRedThreads, 0, s>>>(partial, out, gate);
   prof_end(P_REDUCE, s, "reduce_partials");
 }
 
 void launch_multi_axpy(double* w, const double* V, size_t ldv, int nvec, const double* coef, double sign, size_t n,
-                       double* partial_sq, cudaStream_t s) {
+                       double* partial_sq, cudaStream_t s, const double* gate) {
   if (nvec < 1 || nvec > kDotGroup) return;
   prof_begin(P_AXPY, s);
   if (partial_sq) {
     switch (nvec) {
 #define IBRD_CASE(k)                                                                                       \
   case k:                                                                                                  \
-    k_multi_axpy<k, true><<<kRedBlocks, kRedThreads, 0, s>>>(w, V, ldv, coef, sign, n, partial_sq); break;
+    k_multi_axpy<k, true><<<kRedBlocks, kRedThreads, 0, s>>>(w, V, ldv, coef, sign, n, partial_sq, gate); break;
       IBRD_CASE(1) IBRD_CASE(2) IBRD_CASE(3) IBRD_CASE(4) IBRD_CASE(5) IBRD_CASE(6) IBRD_CASE(7) IBRD_CASE(8)
 #undef IBRD_CASE
       default: return;
@@ -290,7 +307,7 @@ void launch_multi_axpy(double* w, const double* V, size_t ldv, int nvec, const d
     switch (nvec) {
 #define IBRD_CASE(k)                                                                                        \
   case k:                                                                                                   \
-    k_multi_axpy<k, false><<<kRedBlocks, kRedThreads, 0, s>>>(w, V, ldv, coef, sign, n, nullptr); break;
+    k_multi_axpy<k, false><<<kRedBlocks, kRedThreads, 0, s>>>(w, V, ldv, coef, sign, n, nullptr, gate); break;
       IBRD_CASE(1) IBRD_CASE(2) IBRD_CASE(3) IBRD_CASE(4) IBRD_CASE(5) IBRD_CASE(6) IBRD_CASE(7) IBRD_CASE(8)
 #undef IBRD_CASE
       default: return;
@@ -311,10 +328,16 @@ void launch_backsolve(const double* H, int ldh, int k, const double* gvec, doubl
   prof_end(P_SMALL, s, "backsolve");
 }
 
-void launch_vec_add_small(double* h, const double* h2, int n, cudaStream_t s) {
+void launch_vec_add_small(double* h, const double* h2, int n, cudaStream_t s, const double* gate) {
   prof_begin(P_SMALL, s);
-  k_vec_add_small<<<1, 64, 0, s>>>(h, h2, n);
+  k_vec_add_small<<<1, 64, 0, s>>>(h, h2, n, gate);
   prof_end(P_SMALL, s, "vec_add_small");
+}
+
+void launch_reorth_flag(const double* ww, const double* sq, double eta, double* flag, double* count, cudaStream_t s) {
+  prof_begin(P_SMALL, s);
+  k_reorth_flag<<<1, 32, 0, s>>>(ww, sq, eta, flag, count);
+  prof_end(P_SMALL, s, "reorth_flag");
 }
 
 void launch_sqrt_scalar(const double* src, double* dst, cudaStream_t s) {
