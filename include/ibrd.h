@@ -73,6 +73,9 @@ typedef struct {
                         orthogonalised vector's norm falls below reorth_eta
                         times its norm before (DGKS test): 1/sqrt(2) (default),
                         0 never, >= 1 always */
+  int graphs;        /* 1 (default): replay each preconditioner application
+                        from a captured CUDA graph after its first use; 0: launch
+                        every kernel directly */
 } ibrd_solve_opts;
 
 /* Solve report. residual_history, if non-NULL, is a caller-owned HOST array

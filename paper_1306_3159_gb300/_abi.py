@@ -32,7 +32,7 @@ class SolveOpts(ctypes.Structure):
                 ("mg_cycles", ctypes.c_int), ("schur_inner", ctypes.c_int), ("precond", ctypes.c_int),
                 ("zeta", ctypes.c_double), ("xi", ctypes.c_double), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
                 ("precision", ctypes.c_int), ("use_guess", ctypes.c_int),
-                ("reorth_eta", ctypes.c_double)]
+                ("reorth_eta", ctypes.c_double), ("graphs", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):

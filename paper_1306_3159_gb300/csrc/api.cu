@@ -194,6 +194,19 @@ struct ibrd_grid_s {
   long inner = 0;
   long reorths = 0;
   Profiler prof;
+  // CUDA graphs of preconditioner applications, one per Krylov index j
+  struct GraphEntry {
+    cudaGraphExec_t exec = nullptr;
+    long long launches = 0;
+    long long count[P_NCLASS] = {};
+    double bytes[P_NCLASS] = {};
+    long vcycles = 0, inner = 0;  // solver counters one application adds
+    int seen = 0;
+  };
+  std::string graph_key;
+  std::vector<GraphEntry> graphs;
+  cudaStream_t cap_stream = nullptr;
+  long blob_version = 0;
   std::string err;
 };
 
@@ -386,10 +399,104 @@ struct LinOp {
   virtual ~LinOp() = default;
   virtual void apply(const double* x, double* y) = 0;
   virtual void precond(const double* v, double* z) = 0;
+  // everything a preconditioner application depends on besides v and z
+  virtual std::string key() const = 0;
 };
+
+void free_graphs(ibrd_grid g) {
+  for (auto& e : g->graphs)
+    if (e.exec) cudaGraphExecDestroy(e.exec);
+  g->graphs.clear();
+  g->graph_key.clear();
+}
+
+// Apply the preconditioner z = P(v) for Krylov index j. The launch sequence
+// of one application is fixed for a given configuration and j (all buffers
+// and device scalars have fixed addresses), so from the second encounter on
+// it is captured once into a CUDA graph and replayed with one launch. The
+// first encounter runs directly, which also performs any lazy allocation.
+// Capture happens on a private stream (the legacy default stream cannot be
+// captured); the graph is launched on the handle's stream. While per-launch
+// timing is on the sequence always runs directly.
+void run_precond(ibrd_grid g, LinOp& op, int j, const double* v, double* z, bool use_graphs) {
+  Profiler& p = g->prof;
+  if (!use_graphs || p.timing) {
+    op.precond(v, z);
+    return;
+  }
+  const std::string key = op.key() + "|" + std::to_string(g->blob_version) + "|" +
+                          std::to_string((unsigned long long)(uintptr_t)g->V) + "|" +
+                          std::to_string((unsigned long long)(uintptr_t)g->Z) + "|" + std::to_string(g->vlen);
+  if (key != g->graph_key) {
+    free_graphs(g);
+    g->graph_key = key;
+  }
+  if ((int)g->graphs.size() <= j) g->graphs.resize(j + 1);
+  auto& e = g->graphs[j];
+  if (!e.exec) {
+    if (e.seen == 0) {
+      e.seen = 1;
+      op.precond(v, z);
+      return;
+    }
+    if (!g->cap_stream) IBRD_CUDA(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
+    const long long l0 = p.launches;
+    long long c0[P_NCLASS];
+    double b0[P_NCLASS];
+    for (int c = 0; c < P_NCLASS; ++c) {
+      c0[c] = p.count[c];
+      b0[c] = p.bytes[c];
+    }
+    const long v0 = g->vcycles, i0 = g->inner;
+    cudaStream_t user = g->s;
+    g->s = g->cap_stream;
+    cudaGraph_t graph = nullptr;
+    IBRD_CUDA(cudaStreamBeginCapture(g->s, cudaStreamCaptureModeRelaxed));
+    try {
+      op.precond(v, z);
+    } catch (...) {
+      cudaStreamEndCapture(g->s, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      g->s = user;
+      throw;
+    }
+    const cudaError_t ec = cudaStreamEndCapture(g->s, &graph);
+    g->s = user;
+    if (ec != cudaSuccess) throw CudaError{ec, "cudaStreamEndCapture"};
+    const cudaError_t ei = cudaGraphInstantiate(&e.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+      e.exec = nullptr;
+      throw CudaError{ei, "cudaGraphInstantiate"};
+    }
+    // the capture counted launches (and V-cycles) that did not run; keep
+    // them per graph and add them at each replay
+    e.vcycles = g->vcycles - v0;
+    e.inner = g->inner - i0;
+    g->vcycles = v0;
+    g->inner = i0;
+    e.launches = p.launches - l0;
+    p.launches = l0;
+    for (int c = 0; c < P_NCLASS; ++c) {
+      e.count[c] = p.count[c] - c0[c];
+      e.bytes[c] = p.bytes[c] - b0[c];
+      p.count[c] = c0[c];
+      p.bytes[c] = b0[c];
+    }
+  }
+  IBRD_CUDA(cudaGraphLaunch(e.exec, g->s));
+  g->vcycles += e.vcycles;
+  g->inner += e.inner;
+  p.launches += e.launches;
+  for (int c = 0; c < P_NCLASS; ++c) {
+    p.count[c] += e.count[c];
+    p.bytes[c] += e.bytes[c];
+  }
+}
 
 void ensure_krylov(ibrd_grid g, size_t n, int restart) {
   if (g->vlen != n || g->vcap < restart) {
+    free_graphs(g);
     cudaFree(g->V);
     cudaFree(g->Z);
     g->V = g->Z = nullptr;
@@ -515,7 +622,7 @@ SolveResult fgmres(ibrd_grid g, LinOp& op, const double* b, double* x, size_t n,
     int k = 0;
     bool breakdown = false;
     for (int j = 0; j < m; ++j) {
-      op.precond(V + (size_t)j * n, Z + (size_t)j * n);
+      run_precond(g, op, j, V + (size_t)j * n, Z + (size_t)j * n, o.graphs != 0);
       op.apply(Z + (size_t)j * n, V + (size_t)(j + 1) * n);
       orthogonalize(g, j, n, ldh, o.reorth_eta);
       double* hcol = g->H + (size_t)j * ldh;
@@ -621,6 +728,11 @@ struct ReactionOp : LinOp {
   double sigma;
   ibrd_solve_opts o;
   ReactionOp(ibrd_grid g_, const double* k_, double sg, const ibrd_solve_opts& o_) : g(g_), kappa(k_), sigma(sg), o(o_) {}
+  std::string key() const override {
+    char buf[160];
+    std::snprintf(buf, sizeof buf, "reaction|%zu|%d|%d|%d|%.17g", sizeof(T), o.mg_cycles, o.nu1, o.nu2, sigma);
+    return buf;
+  }
   void apply(const double* x, double* y) override {
     launch_interp<double>(g->blobs, g->d, x, 1.0, g->nv[0], g->s);
     launch_apply_A<double>(x, y, g->d, stencil(g->h, g->chi, g->alpha), g->s);
@@ -649,6 +761,12 @@ struct SaddleOp : LinOp {
   bool singular;
   SaddleOp(ibrd_grid g_, const ibrd_solve_opts& o_, double z, double x) : g(g_), o(o_), zeta(z), xi(x) {
     singular = (g->alpha == 0.0);
+  }
+  std::string key() const override {
+    char buf[200];
+    std::snprintf(buf, sizeof buf, "saddle|%zu|%d|%d|%d|%d|%d|%.17g|%.17g|%.17g|%.17g", sizeof(T), o.mg_cycles,
+                  o.nu1, o.nu2, o.schur_inner, o.precond, zeta, xi, g->alpha, g->gamma_diag);
+    return buf;
   }
   void apply(const double* x, double* y) override {
     const size_t nc = g->d.n();
@@ -872,6 +990,7 @@ void ibrd_default_opts(ibrd_solve_opts* o) {
   o->precision = -1;
   o->use_guess = 0;
   o->reorth_eta = 0.70710678118654752;
+  o->graphs = 1;
 }
 
 const char* ibrd_status_string(int st) {
@@ -914,6 +1033,8 @@ void ibrd_grid_destroy(ibrd_grid g) {
   for (auto p : g->nv) F(p);
   F(g->U); F(g->Hs); F(g->scs); F(g->ssn); F(g->sg);
   for (auto e : g->prof.pool) cudaEventDestroy(e);
+  free_graphs(g);
+  if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
   delete g;
 }
 
@@ -991,6 +1112,7 @@ ibrd_status ibrd_set_blobs(ibrd_grid g, const double* q, int n) {
     IBRD_CUDA(cudaStreamSynchronize(g->s));
     if (flag) throw ArgError{IBRD_ERR_NONFINITE, "non-finite blob position"};
     blobs_setup(g->blobs, g->d, g->h, q, n, g->s);
+    g->blob_version++;
     g->gamma_valid = false;
     return IBRD_OK;
   });

@@ -190,3 +190,23 @@ def test_full_size_properties(ibrd):
     assert abs(lh.sum() - w.g.sum()) < 1e-6 * w.g.sum()
     c2, info2 = g.solve_reaction(dev(w.kappa), dev(w.g), tol=1e-8, precision=1, max_iter=2000)
     assert _residual_oracle(w.q, w.kappa, w.g, host(c2), None, 1.0, 1.0, 0.0) < 2e-8
+
+
+def test_graph_replay_matches_direct_launches(ibrd, small):
+    """Preconditioner applications replayed from captured CUDA graphs give
+    the same iterates, bit for bit, as direct launches (every kernel is
+    deterministic), for both solves and both precisions."""
+    import torch
+    w, _ = small
+    g = _grid(ibrd, w)
+    for precision in (0, 1):
+        outs = []
+        for graphs in (0, 1, 1, 1):  # direct, first encounter, capture, replay
+            c, lam, info = g.solve_saddle(dev(w.g), tol=1e-9, precision=precision, graphs=graphs)
+            c2, info2 = g.solve_reaction(dev(w.kappa), dev(w.g), tol=1e-9, precision=precision, graphs=graphs)
+            outs.append((host(c), host(lam), host(c2), info["outer_iters"], info["vcycles"], info2["vcycles"]))
+        for o in outs[1:]:
+            assert np.array_equal(o[0], outs[0][0]) and np.array_equal(o[1], outs[0][1])
+            assert np.array_equal(o[2], outs[0][2])
+            assert o[3:] == outs[0][3:]
+    torch.cuda.synchronize()
