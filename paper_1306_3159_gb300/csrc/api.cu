@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <new>
 #include <string>
 #include <utility>
@@ -174,8 +175,8 @@ struct ibrd_grid_s {
   // Krylov workspace
   double* V = nullptr;
   double* Z = nullptr;
-  size_t vlen = 0;
-  int vcap = 0;
+  size_t vlen = 0;        // length of the current solve's vectors
+  size_t vcap_elems = 0;  // capacity of V and Z (doubles each)
   double *H = nullptr, *cs = nullptr, *sn = nullptr, *gvec = nullptr, *yv = nullptr, *hb2 = nullptr;
   int hcap = 0;
   double *xs = nullptr, *bs = nullptr;  // saddle [c; lambda] solution and rhs
@@ -203,10 +204,8 @@ struct ibrd_grid_s {
     long vcycles = 0, inner = 0;  // solver counters one application adds
     int seen = 0;
   };
-  std::string graph_key;
-  std::vector<GraphEntry> graphs;
+  std::map<std::string, std::vector<GraphEntry>> graphs;  // by configuration key
   cudaStream_t cap_stream = nullptr;
-  long blob_version = 0;
   std::string err;
 };
 
@@ -404,10 +403,10 @@ struct LinOp {
 };
 
 void free_graphs(ibrd_grid g) {
-  for (auto& e : g->graphs)
-    if (e.exec) cudaGraphExecDestroy(e.exec);
+  for (auto& kv : g->graphs)
+    for (auto& e : kv.second)
+      if (e.exec) cudaGraphExecDestroy(e.exec);
   g->graphs.clear();
-  g->graph_key.clear();
 }
 
 // Apply the preconditioner z = P(v) for Krylov index j. The launch sequence
@@ -424,15 +423,19 @@ void run_precond(ibrd_grid g, LinOp& op, int j, const double* v, double* z, bool
     op.precond(v, z);
     return;
   }
-  const std::string key = op.key() + "|" + std::to_string(g->blob_version) + "|" +
-                          std::to_string((unsigned long long)(uintptr_t)g->V) + "|" +
-                          std::to_string((unsigned long long)(uintptr_t)g->Z) + "|" + std::to_string(g->vlen);
-  if (key != g->graph_key) {
-    free_graphs(g);
-    g->graph_key = key;
-  }
-  if ((int)g->graphs.size() <= j) g->graphs.resize(j + 1);
-  auto& e = g->graphs[j];
+  // blob data enters the graphs through device arrays (whose contents may
+  // change between solves) and through the blob and covered-cell counts and
+  // array addresses (which may not)
+  const BlobSet& bl = g->blobs;
+  char sig[256];
+  std::snprintf(sig, sizeof sig, "|%d|%d|%p|%p|%p|%p|%p|%p|%p|%p|%zu", bl.n, bl.n_cells, (void*)g->V, (void*)g->Z,
+                (void*)bl.idx, (void*)bl.w32, (void*)bl.w64, (void*)bl.cells, (void*)bl.cell_tile,
+                (void*)bl.tile_blobs, g->vlen);
+  const std::string key = op.key() + sig;
+  if (g->graphs.size() > 16 && !g->graphs.count(key)) free_graphs(g);
+  auto& list = g->graphs[key];
+  if ((int)list.size() <= j) list.resize(j + 1);
+  auto& e = list[j];
   if (!e.exec) {
     if (e.seen == 0) {
       e.seen = 1;
@@ -494,17 +497,21 @@ void run_precond(ibrd_grid g, LinOp& op, int j, const double* v, double* z, bool
   }
 }
 
+// The Krylov bases V ((restart+1) vectors) and Z (restart vectors) of length
+// n live in two blocks that are only ever grown, so the reaction (n = N_c) and
+// saddle (n = N_c + N) solves of one handle share them without reallocating.
 void ensure_krylov(ibrd_grid g, size_t n, int restart) {
-  if (g->vlen != n || g->vcap < restart) {
+  const size_t need = n * (size_t)(restart + 1);
+  if (need > g->vcap_elems) {
     free_graphs(g);
     cudaFree(g->V);
     cudaFree(g->Z);
     g->V = g->Z = nullptr;
-    g->V = dalloc<double>(n * (restart + 1));
-    g->Z = dalloc<double>(n * restart);
-    g->vlen = n;
-    g->vcap = restart;
+    g->V = dalloc<double>(need);
+    g->Z = dalloc<double>(need);
+    g->vcap_elems = need;
   }
+  g->vlen = n;
   if (g->hcap < restart) {
     cudaFree(g->H);
     cudaFree(g->cs);
@@ -1112,7 +1119,6 @@ ibrd_status ibrd_set_blobs(ibrd_grid g, const double* q, int n) {
     IBRD_CUDA(cudaStreamSynchronize(g->s));
     if (flag) throw ArgError{IBRD_ERR_NONFINITE, "non-finite blob position"};
     blobs_setup(g->blobs, g->d, g->h, q, n, g->s);
-    g->blob_version++;
     g->gamma_valid = false;
     return IBRD_OK;
   });
