@@ -134,6 +134,29 @@ ibrd_status ibrd_apply_L(ibrd_grid g, const double* c, double* y);
    ignores the incoming x. rhs and x must not overlap. */
 ibrd_status ibrd_vcycle(ibrd_grid g, const double* rhs, double* x, int zero_initial_guess);
 
+/* ibrd_vcycle for callers that cannot allocate device memory (no counterpart
+   in the paper: it is a packaging of the V-cycle above). Some callers may not
+   call cudaMalloc at all: code running under a device-memory budget fixed at
+   start-up, code inside another library that may only use the memory it is
+   handed, or a process whose device memory already belongs to a framework's
+   caching allocator. This entry point needs no grid handle and allocates
+   nothing: the V-cycle's workspaces come from one 16 MiB scratch array that
+   the library holds in static device memory on every GPU that loads it, until
+   the process exits. That limits the grid to about 1.4 million cells (96^3 and
+   112^3 fit; 128^3 does not); larger grids return IBRD_ERR_ARG without any
+   GPU work. The grid, h, chi and alpha are passed directly; rhs and x are
+   caller-owned device arrays as for ibrd_vcycle (rhs != x), and the result is
+   the one ibrd_vcycle computes. stream is a cudaStream_t (NULL = legacy
+   default stream); the call only enqueues work on it and does not synchronize.
+   The first call on a device looks up the scratch array's device address
+   (cudaGetSymbolAddress) once, with that device current; make that first call
+   before any stream capture. Every call uses the same scratch and leaves its
+   contents behind (nothing in it is read before the call writes it), so calls
+   whose GPU work overlaps (different streams or host threads, same device)
+   race on it: serialize them. Returns IBRD_ERR_CUDA if a CUDA call fails. */
+ibrd_status ibrd_vcycle_noalloc(int nx, int ny, int nz, double h, double chi, double alpha, const double* rhs,
+                                double* x, int zero_initial_guess, void* stream);
+
 /* The same V-cycle with FP32 fields and FP32 arithmetic (the multigrid used
    inside the mixed-precision solves). rhs, x: FP32 device fields. */
 ibrd_status ibrd_vcycle_f32(ibrd_grid g, const float* rhs, float* x, int zero_initial_guess);
