@@ -121,23 +121,33 @@ def measured_peaks():
 FP64_PEAK_TFLOPS = 1.2   # FP64 FMA rate of GB300 (recipe: 1.25 TFLOP/s nominal)
 
 
-def kernel_source_hash():
+# source file that defines each kernel class (for matching committed ncu data)
+CLASS_SOURCE = {"rbgs": "smoother.cu", "restrict": "smoother.cu", "prolong": "smoother.cu",
+                "apply": "grid_kernels.cu", "vector": "grid_kernels.cu", "reduce": "grid_kernels.cu",
+                "dot": "krylov_kernels.cu", "axpy": "krylov_kernels.cu", "small": "krylov_kernels.cu",
+                "spread": "blob_kernels.cu", "interp": "blob_kernels.cu"}
+
+
+def kernel_source_hash(kernel_class: str = "rbgs_f32"):
+    """Hash of the source file (plus the shared internal header) of a class."""
+    f = CLASS_SOURCE.get(kernel_class.split("_")[0], "smoother.cu")
+    csrc = os.path.join(ROOT, "paper_1306_3159_gb300", "csrc")
     h = hashlib.sha256()
-    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1306_3159_gb300", "csrc"))):
-        h.update(open(os.path.join(ROOT, "paper_1306_3159_gb300", "csrc", f), "rb").read())
+    for name in (f, "internal.h"):
+        h.update(open(os.path.join(csrc, name), "rb").read())
     return h.hexdigest()[:16]
 
 
 def committed_traffic(kernel_class: str):
     """DRAM bytes per finest-level launch from the committed ncu summary, if
-    it was taken on the current kernel sources."""
+    it was taken on the current source of that kernel class."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    if d.get("source_hash") != kernel_source_hash():
-        return None
     e = d.get("classes", {}).get(kernel_class)
+    if not e or e.get("source_hash") != kernel_source_hash(kernel_class):
+        return None
     return e
 
 
