@@ -82,45 +82,31 @@ __device__ __forceinline__ void vset<double>(double2& v, int c, double x) {
   else v.y = x;
 }
 
-// Update of one 16-byte group for colour parity a: the active cells of the
-// group are q = a and q = a + 2 (float4) or q = a (double2); the other cells
-// keep c. left/right are the neighbours beyond the group's ends.
-__device__ __forceinline__ float4 rb_group(int a, float4 c, float left, float right, float4 u, float4 dn, float4 zm,
-                                           float4 zp, float4 bb, float sh, float off, float inv) {
-  const float c0 = a ? c.y : c.x, c1 = a ? c.w : c.z;
-  const float l0 = a ? c.x : left, r0 = a ? c.z : c.y;
-  const float l1 = a ? c.z : c.y, r1 = a ? right : c.w;
-  const float u0 = a ? u.y : u.x, u1 = a ? u.w : u.z;
-  const float d0 = a ? dn.y : dn.x, d1 = a ? dn.w : dn.z;
-  const float m0 = a ? zm.y : zm.x, m1 = a ? zm.w : zm.z;
-  const float p0 = a ? zp.y : zp.x, p1 = a ? zp.w : zp.z;
-  const float b0 = a ? bb.y : bb.x, b1 = a ? bb.w : bb.z;
-  (void)c0;
-  (void)c1;
-  const float n0 = ((b0 - sh) + off * (((l0 + r0) + (u0 + d0)) + (m0 + p0))) * inv;
-  const float n1 = ((b1 - sh) + off * (((l1 + r1) + (u1 + d1)) + (m1 + p1))) * inv;
+// Update of one 16-byte group whose active cells (those of the colour being
+// updated) are q = A and q = A + 2 (float4) or q = A (double2); the other
+// cells keep c. xo is the neighbour beyond the group's end on the side the
+// active cells need: the left one when A = 0, the right one when A = 1.
+template <int A>
+__device__ __forceinline__ float4 rb_group(float4 c, float xo, float4 u, float4 dn, float4 zm, float4 zp, float4 bb,
+                                           float sh, float off, float inv) {
   float4 o = c;
-  if (a) {
-    o.y = n0;
-    o.w = n1;
+  if (A == 0) {
+    o.x = ((bb.x - sh) + off * (((xo + c.y) + (u.x + dn.x)) + (zm.x + zp.x))) * inv;
+    o.z = ((bb.z - sh) + off * (((c.y + c.w) + (u.z + dn.z)) + (zm.z + zp.z))) * inv;
   } else {
-    o.x = n0;
-    o.z = n1;
+    o.y = ((bb.y - sh) + off * (((c.x + c.z) + (u.y + dn.y)) + (zm.y + zp.y))) * inv;
+    o.w = ((bb.w - sh) + off * (((c.z + xo) + (u.w + dn.w)) + (zm.w + zp.w))) * inv;
   }
   return o;
 }
-__device__ __forceinline__ double2 rb_group(int a, double2 c, double left, double right, double2 u, double2 dn,
-                                            double2 zm, double2 zp, double2 bb, double sh, double off, double inv) {
-  const double l0 = a ? c.x : left, r0 = a ? right : c.y;
-  const double u0 = a ? u.y : u.x, d0 = a ? dn.y : dn.x;
-  const double m0 = a ? zm.y : zm.x, p0 = a ? zp.y : zp.x;
-  const double b0 = a ? bb.y : bb.x;
-  const double n0 = ((b0 - sh) + off * (((l0 + r0) + (u0 + d0)) + (m0 + p0))) * inv;
+template <int A>
+__device__ __forceinline__ double2 rb_group(double2 c, double xo, double2 u, double2 dn, double2 zm, double2 zp,
+                                            double2 bb, double sh, double off, double inv) {
   double2 o = c;
-  if (a)
-    o.y = n0;
+  if (A == 0)
+    o.x = ((bb.x - sh) + off * (((xo + c.y) + (u.x + dn.x)) + (zm.x + zp.x))) * inv;
   else
-    o.x = n0;
+    o.y = ((bb.y - sh) + off * (((c.x + xo) + (u.y + dn.y)) + (zm.y + zp.y))) * inv;
   return o;
 }
 
@@ -156,9 +142,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_rb_sweep(const T* __restrict_
   constexpr int XR = TY + 4, BR = TY + 2;  // rows per x / b plane
   constexpr int TV = TX / V;
   constexpr int R = kSweepR;
-  constexpr int NRED = (TY + 2) * NV, NBLK = TY * TV;
   constexpr int BLK0 = 192;  // first thread of the black role (warp 6)
-  static_assert(NRED <= BLK0 && NBLK <= NT - BLK0, "role sizes");
   static_assert(XR * NV <= 2 * NT && BR * NV <= NT, "copy roles");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* pxs = reinterpret_cast<T*>(smem_raw);
@@ -190,21 +174,29 @@ __global__ void __launch_bounds__(kSweepThreads) k_rb_sweep(const T* __restrict_
       sb = r * W + v * V;
     }
   }
-  // update roles
-  const bool is_red = tid < NRED;
-  const bool is_black = tid >= BLK0 && tid < BLK0 + NBLK;
-  int go, gpar;
+  // update roles. Each warp takes rows of one parity only, so the pattern of
+  // active cells in a group is the same for all its lanes: warps 0-2 the red
+  // groups of rows 1, 3, .., warps 3-5 those of rows 2, 4, ..; warps 6-7 the
+  // black groups of rows 2, 4, .., warps 8-9 those of rows 3, 5, ...
+  static_assert(TY % 2 == 0 && (TY + 2) / 2 * NV <= 96 && TY / 2 * TV <= 64, "row-parity roles");
+  bool is_red = false, is_black = false;
+  int go = 0, gpar = 0;
   bool lo_edge = false, hi_edge = false;
   T* gout = xout;
   if (tid < BLK0) {
-    const int ly = 1 + tid / NV, v = tid - (tid / NV) * NV;
+    const int h = tid / 96, e = tid - h * 96;
+    const int r = 2 * (e / NV) + h, v = e - (e / NV) * NV;
+    is_red = e < (TY + 2) / 2 * NV;
+    const int ly = 1 + r;
     go = ly * W + v * V;
     gpar = (x0 + y0 + ly) & 1;
     lo_edge = v == 0;
     hi_edge = v == NV - 1;
   } else {
     const int e = tid - BLK0;
-    const int ty = e / TV, v = 1 + (e - (e / TV) * TV);
+    const int h = e / 64, f = e - h * 64;
+    const int ty = 2 * (f / TV) + h, v = 1 + (f - (f / TV) * TV);
+    is_black = f < TY / 2 * TV;
     go = (2 + ty) * W + v * V;
     gpar = (x0 + y0 + 2 + ty) & 1;
     gout = xout + (size_t)(y0 + ty) * nx + x0 + (v - 1) * V;
@@ -244,10 +236,13 @@ __global__ void __launch_bounds__(kSweepThreads) k_rb_sweep(const T* __restrict_
     const VT zm = *reinterpret_cast<const VT*>(Pm + o);
     const VT zp = *reinterpret_cast<const VT*>(Pp + o);
     const VT bb = *reinterpret_cast<const VT*>(B + o - W);
-    const T left = lo_edge ? (T)0 : P[o - 1];
-    const T right = hi_edge ? (T)0 : P[o + V];
+    // warp-uniform: all lanes of a warp share the row parity
     const int a = (gpar + k + colour) & 1;
-    VT r = rb_group(a, c, left, right, u, dn, zm, zp, bb, sh, off, inv_diag);
+    VT r;
+    if (a == 0)
+      r = rb_group<0>(c, lo_edge ? (T)0 : P[o - 1], u, dn, zm, zp, bb, sh, off, inv_diag);
+    else
+      r = rb_group<1>(c, hi_edge ? (T)0 : P[o + V], u, dn, zm, zp, bb, sh, off, inv_diag);
     // ring edge groups of the red region hold one active cell each: lx = V-1
     // (last of group 0) and lx = TX+V (first of the last group)
     if (lo_edge) {
