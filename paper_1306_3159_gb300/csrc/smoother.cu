@@ -124,8 +124,8 @@ __device__ __forceinline__ double2 rb_group(double2 c, double xo, double2 u, dou
 // own the red groups, warps 6-9 the black groups.
 //
 // Copies: group G_q = {x plane q+1, b plane q} is needed by red(q); it is
-// issued at the start of phase q-2 (prefetch distance 2). With rings of 8
-// planes the target slots are never in use by a thread still in phase p-1.
+// issued right after the barrier of phase q-3 (prefetch distance 3). With
+// rings of 8 planes its target slots are not read during that phase.
 constexpr int kSweepThreads = 320;
 
 template <typename T, int TX, int TY, bool ZERO>
@@ -259,25 +259,33 @@ __global__ void __launch_bounds__(kSweepThreads) k_rb_sweep(const T* __restrict_
   };
   double xsum = 0.0;
 
-  constexpr int D = 2;
-  // prologue: x planes k0-2, k0-1 plus G_{k0-1} = {x(k0), b(k0-1)}, then G_{k0}
+  constexpr int D = 3;
+  // prologue: x planes k0-2, k0-1 plus G_{k0-1} = {x(k0), b(k0-1)}, then
+  // G_{k0} .. G_{k0+D-2}
   copy_x(k0 - 2);
   copy_x(k0 - 1);
   copy_x(k0);
   copy_b(k0 - 1);
   cp_async_commit();
-  copy_x(k0 + 1);
-  copy_b(k0);
-  cp_async_commit();
+  for (int q = k0; q <= k0 + D - 2; ++q) {
+    if (q <= k1) {
+      copy_x(q + 1);
+      copy_b(q);
+    }
+    cp_async_commit();
+  }
   for (int p = k0 - 1; p <= k1 + 1; ++p) {
+    cp_async_wait<D - 1>();
+    __syncthreads();
+    // G_{p+D} is issued after the barrier: its slots (x plane p+D+1, b plane
+    // p+D) are not among the planes any warp reads in phase p (x p-3..p+1,
+    // b p-2 and p)
     const int q = p + D;
     if (q <= k1) {
       copy_x(q + 1);
       copy_b(q);
     }
     cp_async_commit();
-    cp_async_wait<D>();
-    __syncthreads();
     if (is_red && p <= k1) {
       const VT r = group(p, 0);
       *reinterpret_cast<VT*>(slot_x(p) + go) = r;
