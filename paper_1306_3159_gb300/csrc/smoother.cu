@@ -223,18 +223,26 @@ __global__ void __launch_bounds__(kSweepThreads) k_rb_sweep(const T* __restrict_
   auto copy_b = [&](int k) {
     if (gb >= 0) cp_async16(slot_b(k) + sb, b + (size_t)wrap(k, nz) * plane + gb);
   };
-  // colour 0 = red (active lanes of the group follow from the global parity)
-  auto group = [&](int k, int colour) -> VT {
+  // Group update for plane k (colour 0 = red). zm, c, zp are this thread's
+  // group in planes k-1, k, k+1: a role thread keeps the same (row, group)
+  // in every phase, and the cells it needs there (the other colour) do not
+  // change between the phase that read them and the phase that uses them,
+  // so they rotate through registers and only plane k+1 is read anew.
+  VT zm{}, c{}, zp{};
+  auto group = [&](int k, int colour, bool first) -> VT {
     const T* P = slot_x(k);
-    const T* Pm = slot_x(k - 1);
-    const T* Pp = slot_x(k + 1);
     const T* B = slot_b(k);
     const int o = go;
-    const VT c = *reinterpret_cast<const VT*>(P + o);
+    if (first) {
+      zm = *reinterpret_cast<const VT*>(slot_x(k - 1) + o);
+      c = *reinterpret_cast<const VT*>(P + o);
+    } else {
+      zm = c;
+      c = zp;
+    }
+    zp = *reinterpret_cast<const VT*>(slot_x(k + 1) + o);
     const VT u = *reinterpret_cast<const VT*>(P + o - W);
     const VT dn = *reinterpret_cast<const VT*>(P + o + W);
-    const VT zm = *reinterpret_cast<const VT*>(Pm + o);
-    const VT zp = *reinterpret_cast<const VT*>(Pp + o);
     const VT bb = *reinterpret_cast<const VT*>(B + o - W);
     // warp-uniform: all lanes of a warp share the row parity
     const int a = (gpar + k + colour) & 1;
@@ -287,12 +295,12 @@ __global__ void __launch_bounds__(kSweepThreads) k_rb_sweep(const T* __restrict_
     }
     cp_async_commit();
     if (is_red && p <= k1) {
-      const VT r = group(p, 0);
+      const VT r = group(p, 0, p == k0 - 1);
       *reinterpret_cast<VT*>(slot_x(p) + go) = r;
     }
     const int kb = p - 2;
     if (is_black && kb >= k0) {
-      const VT r = group(kb, 1);
+      const VT r = group(kb, 1, kb == k0);
       *reinterpret_cast<VT*>(slot_x(kb) + go) = r;
       *reinterpret_cast<VT*>(gout + (size_t)kb * plane) = r;
       if (part) {
