@@ -109,6 +109,32 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ---------------------------------------------------------------- ranks
+# One process per GPU; every rank solves its own replica of the workload (the
+# solve does not shard), so the only cross-rank steps are the barriers around
+# the timed region and the maximum of the per-step times.
+def rank_barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(seconds_per_step: float, world: int, solves_per_step: int = 2) -> float:
+    """Solves per second of the whole job: every rank completes one step of
+    `solves_per_step` solves in at most `seconds_per_step`."""
+    return world * solves_per_step / seconds_per_step
+
+
 # ---------------------------------------------------------------- peaks
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -211,17 +237,7 @@ def run_ours(args):
         torch.cuda.current_stream().synchronize()
 
     def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
-
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        rank_barrier(world)
 
     def timed(fn, k):
         barrier()
@@ -234,7 +250,7 @@ def run_ours(args):
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        return max_over_ranks(e0.elapsed_time(e1) / 1e3 / k)
+        return max_over_ranks(e0.elapsed_time(e1) / 1e3 / k, world, "cuda")
 
     if args.ncu_step:
         # profiler range around one chosen step (ncu --profile-from-start off)
@@ -323,6 +339,7 @@ def run_ours(args):
         "gpu_launches": prof_counts["launches"],
         "gpu_launches_per_step": prof_counts["launches"] / max(1, args.steps),
         "solves": {"reaction": solve_summary(ir), "saddle": solve_summary(isd)},
+        "solves_per_s_all_ranks": round(replica_throughput(t_step, world), 3),
         "plain_fp64": {"s_per_step": round(t_plain, 6), "steps": k_plain,
                        "reaction": solve_summary(ir64), "saddle": solve_summary(is64),
                        "chosen_speedup": round(t_plain / t_step, 3)},

@@ -1,0 +1,79 @@
+"""Physics checks of the CUDA path against numbers the paper prints
+(Sec. IV.A and IV.B), at sizes the paper used."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import outputs
+from synthetic import lattice_positions
+from tests.gpu_util import dev, host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ibrd():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_1306_3159_gb300 import build
+    build.build()
+    import paper_1306_3159_gb300 as p
+    return p
+
+
+def _radius(ibrd, L, q, w=4):
+    g = ibrd.Grid(L, L, L, kernel=w)
+    g.set_blobs(dev(np.asarray(q, dtype=np.float64)))
+    src = np.full((L, L, L), 1.0 / L ** 3)
+    c, lam, info = g.solve_saddle(dev(src), tol=1e-10, max_iter=500)
+    aL = info["sum_lambda"] / (4 * math.pi * 1.0 * info["cbar"])
+    a = aL
+    for _ in range(200):
+        x = 2.84 * a / L
+        a = aL / (1 + x + x * x)
+    return aL, a
+
+
+def test_reaction_radius_at_node_L128(ibrd):
+    """A blob at a grid node in a periodic 128^3 box: Eq. a_phi's series gives
+    a = 1.27h (4-point) within 1.5%."""
+    L = 128
+    aL, a = _radius(ibrd, L, [[L / 2, L / 2, L / 2]])
+    assert abs(a - 1.27) < 0.015 * 1.27
+    assert aL > a
+
+
+def test_translational_variation_L128(ibrd):
+    """Sec. IV.A at L = 128: the 4-point radius varies by about 1.5% as the
+    blob moves relative to the grid, the 3-point one by about 5%."""
+    L = 128
+    offsets = [(0, 0, 0), (0.5, 0, 0), (0.5, 0.5, 0), (0.5, 0.5, 0.5), (0.25, 0.25, 0.25)]
+    var = {}
+    for w in (4, 3):
+        a = np.array([_radius(ibrd, L, [[L / 2 + 0.5 + d[0], L / 2 + 0.5 + d[1], L / 2 + 0.5 + d[2]]], w)[1]
+                      for d in offsets])
+        var[w] = (a.max() - a.min()) / a.mean()
+        if w == 4:
+            assert abs(a.mean() - 1.255) < 0.01 * 1.255
+    assert var[4] < 0.03 and 0.02 < var[3] < 0.075 and var[4] < var[3]
+
+
+def test_cubic_lattice_rate_L64(ibrd):
+    """Sec. IV.B: 512 blobs on a cubic lattice of spacing 8h in 64^3 follow
+    Eq. beta_cubic within 1%."""
+    L, sp = 64, 8
+    q = lattice_positions((L, L, L), 1.0, sp)
+    g = ibrd.Grid(L, L, L)
+    g.set_blobs(dev(q))
+    V = L ** 3
+    src = np.full((L, L, L), 1.0 / V)
+    c, lam, info = g.solve_saddle(dev(src), tol=1e-10, max_iter=500)
+    a = 1.27
+    phi = len(q) * (4 * math.pi * a ** 3 / 3) / V
+    b0 = outputs.beta0(info["cbar"], 1.0 / V, a, 1.0, len(q), V)
+    fit = outputs.beta0_cubic_fit(phi)
+    assert abs(b0 - fit) < 0.01 * fit
+    # every blob of the lattice sees the same environment: equal rates
+    lh = host(lam)
+    assert np.abs(lh - lh.mean()).max() < 1e-7 * abs(lh.mean())

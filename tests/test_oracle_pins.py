@@ -307,3 +307,52 @@ def test_outputs_formulae():
     b = outputs.beta0(cbar, 1.0 / V, a, chi, 1, V)
     assert abs(b - 1.0) < 1e-6
     assert abs(outputs.beta0_cubic_fit(0.0) - 1.0) < 1e-15
+
+
+def _extrapolated_radius(aL, L, k=2.84):
+    a = aL
+    for _ in range(200):
+        x = k * a / L
+        a = aL / (1 + x + x * x)
+    return a
+
+
+def test_translational_invariance_of_radius():
+    """Sec. IV.A: moving the blob relative to the grid changes the reaction
+    radius by about 1.5% (4-point) and 5% (3-point); the 4-point average is
+    about 1.255h (caption of Fig. FarFieldDecay). L = 64, blob displaced from a
+    cell centre along several directions."""
+    L = 64
+    offsets = [(0, 0, 0), (0.5, 0, 0), (0.5, 0.5, 0), (0.5, 0.5, 0.5)]
+    res = {}
+    for w in (4, 3):
+        vals = []
+        for d in offsets:
+            q = np.array([[L / 2 + 0.5 + d[0], L / 2 + 0.5 + d[1], L / 2 + 0.5 + d[2]]])
+            g = np.full((L, L, L), 1.0 / L ** 3)
+            c, lam, _ = direct.solve_saddle(q, g, 1.0, 1.0, 0.0, w=w)
+            vals.append(_extrapolated_radius(outputs.reaction_radius(lam, c, 1.0), L))
+        res[w] = np.array(vals)
+    v4, v3 = res[4], res[3]
+    assert (v4.max() - v4.min()) / v4.mean() < 2 * GOLD["translational_variation_4pt"]["value"]
+    assert abs(v4.mean() - GOLD["reaction_radius_4pt_average"]["value"]) < 0.01 * GOLD["reaction_radius_4pt_average"]["value"]
+    var3 = (v3.max() - v3.min()) / v3.mean()
+    assert 0.4 * GOLD["translational_variation_3pt"]["value"] < var3 < 1.5 * GOLD["translational_variation_3pt"]["value"]
+    assert (v4.max() - v4.min()) / v4.mean() < var3   # the 4-point kernel is the more invariant one
+
+
+@pytest.mark.parametrize("L,spacing", [(32, 8), (48, 12)])
+def test_cubic_lattice_rate_matches_fit(L, spacing):
+    """Sec. IV.B: a cubic array of blobs (at grid nodes, a = 1.27h) follows
+    the paper's cubic-lattice fit Eq. beta_cubic (with its b = -0.92,
+    c = 17.4) at low packing fraction."""
+    from synthetic import lattice_positions
+    q = lattice_positions((L, L, L), 1.0, spacing)
+    V = L ** 3
+    g = np.full((L, L, L), 1.0 / V)
+    c, lam, _ = direct.solve_saddle(q, g, 1.0, 1.0, 0.0)
+    a = GOLD["reaction_radius_4pt_node"]["value"]
+    phi = len(q) * (4 * math.pi * a ** 3 / 3) / V
+    b0 = outputs.beta0(c.mean(), 1.0 / V, a, 1.0, len(q), V)
+    fit = outputs.beta0_cubic_fit(phi, GOLD["cubic_fit_b"]["value"], GOLD["cubic_fit_c"]["value"])
+    assert abs(b0 - fit) < 0.01 * fit
