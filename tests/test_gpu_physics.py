@@ -26,7 +26,10 @@ def _radius(ibrd, L, q, w=4):
     g = ibrd.Grid(L, L, L, kernel=w)
     g.set_blobs(dev(np.asarray(q, dtype=np.float64)))
     src = np.full((L, L, L), 1.0 / L ** 3)
-    c, lam, info = g.solve_saddle(dev(src), tol=1e-10, max_iter=500)
+    # relative residual 1e-8: the source is 1/L^3, so the FP64 floor of the
+    # relative residual is near 1e-9 here, and c-bar (hence a) is fixed to
+    # far more digits than the percent-level checks below need
+    c, lam, info = g.solve_saddle(dev(src), tol=1e-8, max_iter=500)
     aL = info["sum_lambda"] / (4 * math.pi * 1.0 * info["cbar"])
     a = aL
     for _ in range(200):
@@ -68,7 +71,7 @@ def test_cubic_lattice_rate_L64(ibrd):
     g.set_blobs(dev(q))
     V = L ** 3
     src = np.full((L, L, L), 1.0 / V)
-    c, lam, info = g.solve_saddle(dev(src), tol=1e-10, max_iter=500)
+    c, lam, info = g.solve_saddle(dev(src), tol=1e-8, max_iter=500)
     a = 1.27
     phi = len(q) * (4 * math.pi * a ** 3 / 3) / V
     b0 = outputs.beta0(info["cbar"], 1.0 / V, a, 1.0, len(q), V)
@@ -76,4 +79,4 @@ def test_cubic_lattice_rate_L64(ibrd):
     assert abs(b0 - fit) < 0.01 * fit
     # every blob of the lattice sees the same environment: equal rates
     lh = host(lam)
-    assert np.abs(lh - lh.mean()).max() < 1e-7 * abs(lh.mean())
+    assert np.abs(lh - lh.mean()).max() < 1e-6 * abs(lh.mean())
