@@ -30,6 +30,10 @@ inline void check_launch(const char* what) {
   if (e != cudaSuccess) throw CudaError{e, what};
 }
 
+// 16-byte copies and vector accesses need 16-byte aligned fields; a caller's
+// pointer into the middle of an allocation may not be.
+inline bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
 // ---------------------------------------------------------------- profiling
 // Kernel classes timed by the launch profiler (names in api.cu).
 enum ProfClass {

@@ -435,6 +435,129 @@ __global__ void __launch_bounds__(256) k_prolong8(const T* __restrict__ xc, T* _
     }
 }
 
+// Two coarse cells (I, I+1) per thread: the fine x range 2I-1 .. 2I+4 of each
+// row is one aligned 4-vector plus two scalars. Needs nx % 4 == 0.
+template <typename T>
+__global__ void __launch_bounds__(256) k_resid_restrict2(const T* __restrict__ x, const T* __restrict__ b,
+                                                         const double* __restrict__ bshift, T* __restrict__ bc,
+                                                         int nx, int ny, int nz, T diag, T off) {
+  const int nxc = nx >> 1, nyc = ny >> 1, nzc = nz >> 1;
+  const int I2 = blockIdx.x * blockDim.x + threadIdx.x;  // pair index
+  const int J = blockIdx.y * blockDim.y + threadIdx.y;
+  const int K = blockIdx.z * blockDim.z + threadIdx.z;
+  if (2 * I2 >= nxc || J >= nyc || K >= nzc) return;
+  const int plane = nx * ny;
+  const T sh = bshift ? (T)(*bshift) : (T)0;
+  const int i0 = 4 * I2, iw = wrap(i0 - 1, nx), ie = wrap(i0 + 4, nx);
+  T acc0 = 0, acc1 = 0;
+  auto ld4 = [&](int o, T* v) {
+    if constexpr (sizeof(T) == 4) {
+      const float4 t = *reinterpret_cast<const float4*>(x + o);
+      v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    } else {
+      const double2 t0 = *reinterpret_cast<const double2*>(x + o);
+      const double2 t1 = *reinterpret_cast<const double2*>(x + o + 2);
+      v[0] = t0.x; v[1] = t0.y; v[2] = t1.x; v[3] = t1.y;
+    }
+  };
+  auto ldb4 = [&](int o, T* v) {
+    if constexpr (sizeof(T) == 4) {
+      const float4 t = *reinterpret_cast<const float4*>(b + o);
+      v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    } else {
+      const double2 t0 = *reinterpret_cast<const double2*>(b + o);
+      const double2 t1 = *reinterpret_cast<const double2*>(b + o + 2);
+      v[0] = t0.x; v[1] = t0.y; v[2] = t1.x; v[3] = t1.y;
+    }
+  };
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const int k = 2 * K + c;
+    const int pk = k * plane, pkm = wrap(k - 1, nz) * plane, pkp = wrap(k + 1, nz) * plane;
+#pragma unroll
+    for (int bb = 0; bb < 2; ++bb) {
+      const int j = 2 * J + bb;
+      const int rj = j * nx, rjm = wrap(j - 1, ny) * nx, rjp = wrap(j + 1, ny) * nx;
+      T m[4], yn[4], ys[4], zd[4], zu[4], bv[4];
+      ld4(pk + rj + i0, m);
+      ld4(pk + rjm + i0, ys);
+      ld4(pk + rjp + i0, yn);
+      ld4(pkm + rj + i0, zd);
+      ld4(pkp + rj + i0, zu);
+      ldb4(pk + rj + i0, bv);
+      const T xw = x[pk + rj + iw], xe = x[pk + rj + ie];
+      T r[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const T l = q == 0 ? xw : m[q - 1];
+        const T rr = q == 3 ? xe : m[q + 1];
+        const T s = ((l + rr) + (ys[q] + yn[q])) + (zd[q] + zu[q]);
+        r[q] = (bv[q] - sh) - (diag * m[q] - off * s);
+      }
+      acc0 += r[0] + r[1];
+      acc1 += r[2] + r[3];
+    }
+  }
+  const int o = (K * nyc + J) * nxc + 2 * I2;
+  bc[o] = acc0 * (T)0.125;
+  bc[o + 1] = acc1 * (T)0.125;
+}
+
+// Two coarse cells (I, I+1) per thread; writes the 4 x 2 x 2 fine children
+// with aligned 4-vector read-modify-writes. Needs nx % 4 == 0.
+template <typename T>
+__global__ void __launch_bounds__(256) k_prolong8x2(const T* __restrict__ xc, T* __restrict__ x, int nx, int ny,
+                                                    int nz) {
+  const int nxc = nx >> 1, nyc = ny >> 1, nzc = nz >> 1;
+  const int I2 = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y * blockDim.y + threadIdx.y;
+  const int K = blockIdx.z * blockDim.z + threadIdx.z;
+  if (2 * I2 >= nxc || J >= nyc || K >= nzc) return;
+  const int I = 2 * I2;
+  const T w3 = (T)0.75, w1 = (T)0.25;
+  const int Ix[4] = {wrap(I - 1, nxc), I, I + 1, wrap(I + 2, nxc)};
+  const int Jy[3] = {wrap(J - 1, nyc), J, wrap(J + 1, nyc)};
+  const int Kz[3] = {wrap(K - 1, nzc), K, wrap(K + 1, nzc)};
+  // x interpolation on the 3 x 3 coarse rows: fine cells 2I .. 2I+3
+  T ex[3][3][4];
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const T* row = xc + (Kz[c] * nyc + Jy[r]) * nxc;
+      const T a0 = row[Ix[0]], a1 = row[Ix[1]], a2 = row[Ix[2]], a3 = row[Ix[3]];
+      ex[c][r][0] = w3 * a1 + w1 * a0;
+      ex[c][r][1] = w3 * a1 + w1 * a2;
+      ex[c][r][2] = w3 * a2 + w1 * a1;
+      ex[c][r][3] = w3 * a2 + w1 * a3;
+    }
+#pragma unroll
+  for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy) {
+      const int k = 2 * K + dz, j = 2 * J + dy;
+      T* dst = x + ((size_t)k * ny + j) * nx + 4 * I2;
+      T v[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const T yA = w3 * ex[1][1][q] + w1 * ex[1][dy ? 2 : 0][q];
+        const T yB = w3 * ex[dz ? 2 : 0][1][q] + w1 * ex[dz ? 2 : 0][dy ? 2 : 0][q];
+        v[q] = w3 * yA + w1 * yB;
+      }
+      if constexpr (sizeof(T) == 4) {
+        float4 t = *reinterpret_cast<float4*>(dst);
+        t.x += v[0]; t.y += v[1]; t.z += v[2]; t.w += v[3];
+        *reinterpret_cast<float4*>(dst) = t;
+      } else {
+        double2 t0 = *reinterpret_cast<double2*>(dst);
+        double2 t1 = *reinterpret_cast<double2*>(dst + 2);
+        t0.x += v[0]; t0.y += v[1]; t1.x += v[2]; t1.y += v[3];
+        *reinterpret_cast<double2*>(dst) = t0;
+        *reinterpret_cast<double2*>(dst + 2) = t1;
+      }
+    }
+}
+
 // The coarse end of a V-cycle in ONE CTA: levels lv.first .. lv.n-1 (at most
 // a few thousand cells) live in shared memory; smoothing, residual
 // restriction, the exact coarsest solve and prolongation run with block-wide
@@ -584,7 +707,7 @@ int launch_rb_sweep(const T* xin, T* xout, const T* b, const double* bshift, Dim
                     double* part, int part_cap, cudaStream_t s) {
   const int c = pcls<T>(P_RBGS64, P_RBGS32);
   const T inv = (T)(1.0 / st.diag), off = (T)st.off;
-  if (rb_sweep_fused_ok<T>(d)) {
+  if (rb_sweep_fused_ok<T>(d) && aligned16(xin) && aligned16(xout) && aligned16(b)) {
     // 64-wide tiles for FP32 (18 vectors per row), 32-wide for FP64
     const bool wide = (sizeof(T) == 4) && (d.nx % 64 == 0);
     const int TX = wide ? 64 : 32, TY = 8;
@@ -639,6 +762,16 @@ int launch_rb_sweep(const T* xin, T* xout, const T* b, const double* bshift, Dim
 template <typename T>
 void launch_resid_restrict(const T* x, const T* b, const double* bshift, T* bc, Dims d, Stencil st, cudaStream_t s) {
   const int nxc = d.nx / 2, nyc = d.ny / 2, nzc = d.nz / 2;
+  if (d.nx % 4 == 0 && d.nx >= 8 && aligned16(x) && aligned16(b)) {
+    const int np = nxc / 2;
+    dim3 blk(np >= 32 ? 32 : np, 4, 2);
+    dim3 g((np + blk.x - 1) / blk.x, (nyc + blk.y - 1) / blk.y, (nzc + blk.z - 1) / blk.z);
+    const int c = pcls<T>(P_RESTRICT64, P_RESTRICT32);
+    prof_begin(c, s);
+    k_resid_restrict2<T><<<g, blk, 0, s>>>(x, b, bshift, bc, d.nx, d.ny, d.nz, (T)st.diag, (T)st.off);
+    prof_end(c, s, "resid_restrict", 2.125 * sizeof(T) * d.n());
+    return;
+  }
   dim3 blk(nxc >= 32 ? 32 : nxc, 4, 2);
   dim3 g((nxc + blk.x - 1) / blk.x, (nyc + blk.y - 1) / blk.y, (nzc + blk.z - 1) / blk.z);
   const int c = pcls<T>(P_RESTRICT64, P_RESTRICT32);
@@ -650,6 +783,16 @@ void launch_resid_restrict(const T* x, const T* b, const double* bshift, T* bc, 
 template <typename T>
 void launch_prolong8(const T* xc, T* x, Dims d, cudaStream_t s) {
   const int nxc = d.nx / 2, nyc = d.ny / 2, nzc = d.nz / 2;
+  if (d.nx % 4 == 0 && d.nx >= 8 && aligned16(x)) {
+    const int np = nxc / 2;
+    dim3 blk(np >= 32 ? 32 : np, 4, 2);
+    dim3 g((np + blk.x - 1) / blk.x, (nyc + blk.y - 1) / blk.y, (nzc + blk.z - 1) / blk.z);
+    const int c = pcls<T>(P_PROLONG64, P_PROLONG32);
+    prof_begin(c, s);
+    k_prolong8x2<T><<<g, blk, 0, s>>>(xc, x, d.nx, d.ny, d.nz);
+    prof_end(c, s, "prolong8", 2.125 * sizeof(T) * d.n());
+    return;
+  }
   dim3 blk(nxc >= 32 ? 32 : nxc, 4, 2);
   dim3 g((nxc + blk.x - 1) / blk.x, (nyc + blk.y - 1) / blk.y, (nzc + blk.z - 1) / blk.z);
   const int c = pcls<T>(P_PROLONG64, P_PROLONG32);
