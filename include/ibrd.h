@@ -58,7 +58,8 @@ enum { IBRD_PRECOND_SCHUR = 0, IBRD_PRECOND_DIAG = 1 }; /* saddle preconditioner
 /* Solver options. ibrd_default_opts fills the defaults noted here. */
 typedef struct {
   double tol;        /* relative true residual ||b - K x||_2 / ||b||_2 (1e-8) */
-  int max_iter;      /* total outer FGMRES iterations (1000) */
+  int max_iter;      /* total FGMRES iterations, over all refinement steps of
+                        a mixed-precision solve (1000) */
   int restart;       /* FGMRES restart length (30, Sec. III.E Figs. 3, 5) */
   int mg_cycles;     /* n: V-cycles per approximate Helmholtz solve (1) */
   int schur_inner;   /* m: inner Krylov iterations of the approximate Schur
@@ -67,7 +68,12 @@ typedef struct {
   double zeta;       /* scaling zeta of Eq. saddle_point (1) */
   double xi;         /* scaling xi; <= 0 selects zeta / h^3 (Eq. saddle_point) */
   int nu1, nu2;      /* red-black Gauss-Seidel sweeps before/after (2, 2) */
-  int precision;     /* IBRD_FP64 or IBRD_MIXED_FP32; -1 = the handle's */
+  int precision;     /* IBRD_FP64: FGMRES on FP64 vectors with FP64 V-cycles.
+                        IBRD_MIXED_FP32: iterative refinement, each step an
+                        FP32 FGMRES solve (FP32 vectors, V-cycles, spreading)
+                        of K d = r for the FP64 residual r = b - K x, then
+                        x += d in FP64; tol applies to the FP64 residual.
+                        -1 = the handle's */
   int use_guess;     /* 1: c (and lambda) hold an initial guess; 0: start at 0 */
   double reorth_eta; /* classical Gram-Schmidt takes a second pass when the
                         orthogonalised vector's norm falls below reorth_eta
@@ -76,14 +82,20 @@ typedef struct {
   int graphs;        /* 1 (default): replay each preconditioner application
                         from a captured CUDA graph after its first use; 0: launch
                         every kernel directly */
+  double inner_tol;  /* IBRD_MIXED_FP32: relative residual each FP32 FGMRES
+                        solve aims for, unless less is needed to reach tol
+                        (1e-4; the FP32 rounding floor of the operator is
+                        near 1e-6 on the grids of Sec. IV) */
 } ibrd_solve_opts;
 
 /* Solve report. residual_history, if non-NULL, is a caller-owned HOST array
    of history_cap doubles that receives the relative residual estimate after
-   each outer iteration (history_len entries are written). */
+   each FGMRES iteration (history_len entries are written); in a
+   mixed-precision solve an entry is the FP32 solve's estimate times the FP64
+   relative residual its refinement step started from. */
 typedef struct {
   int status;          /* same value the solve returned */
-  int outer_iters;     /* outer FGMRES iterations */
+  int outer_iters;     /* FGMRES iterations (all refinement steps) */
   int inner_iters;     /* inner Schur Krylov iterations (saddle) */
   int vcycles;         /* V-cycles applied (the paper's cost proxy, Sec. III.E) */
   int reorths;         /* Gram-Schmidt second passes taken */
@@ -95,6 +107,7 @@ typedef struct {
   double* residual_history;
   int history_len;
   int history_cap;
+  int refinements;     /* IBRD_MIXED_FP32: refinement steps (FP32 solves) */
 } ibrd_solve_info;
 
 /* Fill *opts with the defaults listed in ibrd_solve_opts. */

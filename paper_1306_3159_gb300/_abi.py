@@ -32,7 +32,7 @@ class SolveOpts(ctypes.Structure):
                 ("mg_cycles", ctypes.c_int), ("schur_inner", ctypes.c_int), ("precond", ctypes.c_int),
                 ("zeta", ctypes.c_double), ("xi", ctypes.c_double), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
                 ("precision", ctypes.c_int), ("use_guess", ctypes.c_int),
-                ("reorth_eta", ctypes.c_double), ("graphs", ctypes.c_int)]
+                ("reorth_eta", ctypes.c_double), ("graphs", ctypes.c_int), ("inner_tol", ctypes.c_double)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -40,7 +40,7 @@ class SolveInfo(ctypes.Structure):
                 ("vcycles", ctypes.c_int), ("reorths", ctypes.c_int), ("rel_residual", ctypes.c_double), ("sum_lambda", ctypes.c_double),
                 ("cbar", ctypes.c_double), ("rate_K", ctypes.c_double), ("seconds", ctypes.c_double),
                 ("residual_history", ctypes.POINTER(ctypes.c_double)), ("history_len", ctypes.c_int),
-                ("history_cap", ctypes.c_int)]
+                ("history_cap", ctypes.c_int), ("refinements", ctypes.c_int)]
 
 
 class Profile(ctypes.Structure):
@@ -194,7 +194,7 @@ def _info(history_cap):
 def _info_dict(info, hist):
     return {"status": info.status, "outer_iters": info.outer_iters, "inner_iters": info.inner_iters,
             "vcycles": info.vcycles, "reorths": info.reorths, "rel_residual": info.rel_residual, "sum_lambda": info.sum_lambda,
-            "cbar": info.cbar, "rate_K": info.rate_K, "seconds": info.seconds,
+            "cbar": info.cbar, "rate_K": info.rate_K, "seconds": info.seconds, "refinements": info.refinements,
             "history": hist[:info.history_len].copy()}
 
 

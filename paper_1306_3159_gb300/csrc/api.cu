@@ -181,6 +181,10 @@ struct ibrd_grid_s {
   int hcap = 0;
   double *xs = nullptr, *bs = nullptr;  // saddle [c; lambda] solution and rhs
   size_t xs_cap = 0;
+  // iterative refinement: FP64 residual, its FP32 copy and the FP32 correction
+  double* ir_r = nullptr;
+  float *ir_r32 = nullptr, *ir_d32 = nullptr;
+  size_t ir_cap = 0;
   // preconditioner workspaces (FP64 and FP32 fields)
   double *p64[4] = {nullptr, nullptr, nullptr, nullptr};
   float *p32[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -194,6 +198,7 @@ struct ibrd_grid_s {
   long vcycles = 0;
   long inner = 0;
   long reorths = 0;
+  long refinements = 0;
   Profiler prof;
   // CUDA graphs of preconditioner applications, one per Krylov index j
   struct GraphEntry {
@@ -394,10 +399,13 @@ void vcycles(ibrd_grid g, const T* b, T* x, bool zero, double shift, int n, int 
 }
 
 // ---------------------------------------------------------------- Krylov
+// A linear operator with its preconditioner on vectors of type E (FP64 or
+// FP32 Krylov vectors).
+template <typename E>
 struct LinOp {
   virtual ~LinOp() = default;
-  virtual void apply(const double* x, double* y) = 0;
-  virtual void precond(const double* v, double* z) = 0;
+  virtual void apply(const E* x, E* y) = 0;
+  virtual void precond(const E* v, E* z) = 0;
   // everything a preconditioner application depends on besides v and z
   virtual std::string key() const = 0;
 };
@@ -417,7 +425,8 @@ void free_graphs(ibrd_grid g) {
 // Capture happens on a private stream (the legacy default stream cannot be
 // captured); the graph is launched on the handle's stream. While per-launch
 // timing is on the sequence always runs directly.
-void run_precond(ibrd_grid g, LinOp& op, int j, const double* v, double* z, bool use_graphs) {
+template <typename E>
+void run_precond(ibrd_grid g, LinOp<E>& op, int j, const E* v, E* z, bool use_graphs) {
   Profiler& p = g->prof;
   if (!use_graphs || p.timing) {
     op.precond(v, z);
@@ -499,9 +508,14 @@ void run_precond(ibrd_grid g, LinOp& op, int j, const double* v, double* z, bool
 
 // The Krylov bases V ((restart+1) vectors) and Z (restart vectors) of length
 // n live in two blocks that are only ever grown, so the reaction (n = N_c) and
-// saddle (n = N_c + N) solves of one handle share them without reallocating.
-void ensure_krylov(ibrd_grid g, size_t n, int restart) {
-  const size_t need = n * (size_t)(restart + 1);
+// saddle (n = N_c + N) solves of one handle, in either precision, share them
+// without reallocating. Vectors start every ld elements, ld = n rounded up to
+// 32 elements (128-byte aligned vectors for the 16-byte copies of the
+// smoother and the 4-vector Krylov kernels). Returns ld.
+template <typename E>
+size_t ensure_krylov(ibrd_grid g, size_t n, int restart) {
+  const size_t ld = (n + 31) & ~size_t(31);
+  const size_t need = (ld * (size_t)(restart + 1) * sizeof(E) + 7) / 8;  // in doubles
   if (need > g->vcap_elems) {
     free_graphs(g);
     cudaFree(g->V);
@@ -511,7 +525,7 @@ void ensure_krylov(ibrd_grid g, size_t n, int restart) {
     g->Z = dalloc<double>(need);
     g->vcap_elems = need;
   }
-  g->vlen = n;
+  g->vlen = ld * sizeof(E);
   if (g->hcap < restart) {
     cudaFree(g->H);
     cudaFree(g->cs);
@@ -527,32 +541,31 @@ void ensure_krylov(ibrd_grid g, size_t n, int restart) {
     g->hb2 = dalloc<double>(restart + 1);
     g->hcap = restart;
   }
+  return ld;
 }
 
-// w (= V[j+1]) <- w - sum_{i<=j} h_i V[i], h written into H[:, j]; returns
-// ||w||^2 after orthogonalisation in S_SQ. Classical Gram-Schmidt with a
-// second pass when the norm drops below 1/sqrt(2) of its value (DGKS test).
 // w (= V[j+1]) <- w - sum_{i<=j} h_i V[i], h written into H[:, j]; ||w||^2
 // after orthogonalisation lands in S_SQ, ||w||^2 before in S_TMP. Classical
 // Gram-Schmidt; the second pass (DGKS test with threshold eta) is decided on
 // the device and its kernels return at once when it is not needed, so the
-// host does not wait here.
-void orthogonalize(ibrd_grid g, int j, size_t n, int ldh, double eta) {
-  double* V = g->V;
-  double* w = V + (size_t)(j + 1) * n;
+// host does not wait here. Vectors of length n, stride ld.
+template <typename E>
+void orthogonalize(ibrd_grid g, int j, size_t n, size_t ld, int ldh, double eta) {
+  E* V = reinterpret_cast<E*>(g->V);
+  E* w = V + (size_t)(j + 1) * ld;
   double* hcol = g->H + (size_t)j * ldh;
   const int nb = j + 1;  // basis vectors V[0..j]
   // pass 1: dots of V[0..j+1] (the last is <w, w>)
   for (int g0 = 0; g0 < nb + 1; g0 += kDotGroup) {
     const int m = std::min(kDotGroup, nb + 1 - g0);
-    launch_multidot(V + (size_t)g0 * n, n, m, w, n, g->partial, g->s);
+    launch_multidot(V + (size_t)g0 * ld, ld, m, w, n, g->partial, g->s);
     launch_reduce_partials(g->partial, m, hcol + g0, g->s);
   }
   IBRD_CUDA(cudaMemcpyAsync(g->scal + S_TMP, hcol + nb, sizeof(double), cudaMemcpyDeviceToDevice, g->s));
   for (int g0 = 0; g0 < nb; g0 += kDotGroup) {
     const int m = std::min(kDotGroup, nb - g0);
     const bool last = g0 + m >= nb;
-    launch_multi_axpy(w, V + (size_t)g0 * n, n, m, hcol + g0, -1.0, n, last ? g->partial : nullptr, g->s);
+    launch_multi_axpy(w, V + (size_t)g0 * ld, ld, m, hcol + g0, -1.0, n, last ? g->partial : nullptr, g->s);
   }
   launch_reduce_partials(g->partial, 1, g->scal + S_SQ, g->s);
   if (eta <= 0.0) return;
@@ -560,13 +573,14 @@ void orthogonalize(ibrd_grid g, int j, size_t n, int ldh, double eta) {
   launch_reorth_flag(g->scal + S_TMP, g->scal + S_SQ, eta, g->scal + S_RFLAG, g->scal + S_RCOUNT, g->s);
   for (int g0 = 0; g0 < nb; g0 += kDotGroup) {
     const int m = std::min(kDotGroup, nb - g0);
-    launch_multidot(V + (size_t)g0 * n, n, m, w, n, g->partial, g->s, gate);
+    launch_multidot(V + (size_t)g0 * ld, ld, m, w, n, g->partial, g->s, gate);
     launch_reduce_partials(g->partial, m, g->hb2 + g0, g->s, gate);
   }
   for (int g0 = 0; g0 < nb; g0 += kDotGroup) {
     const int m = std::min(kDotGroup, nb - g0);
     const bool last = g0 + m >= nb;
-    launch_multi_axpy(w, V + (size_t)g0 * n, n, m, g->hb2 + g0, -1.0, n, last ? g->partial : nullptr, g->s, gate);
+    launch_multi_axpy(w, V + (size_t)g0 * ld, ld, m, g->hb2 + g0, -1.0, n, last ? g->partial : nullptr, g->s,
+                      gate);
   }
   launch_reduce_partials(g->partial, 1, g->scal + S_SQ, g->s, gate);
   launch_vec_add_small(hcol, g->hb2, nb, g->s, gate);
@@ -578,17 +592,164 @@ struct SolveResult {
   double rel = 0;
 };
 
-// Right-preconditioned flexible GMRES (Saad 1993) with true-residual restarts.
-SolveResult fgmres(ibrd_grid g, LinOp& op, const double* b, double* x, size_t n, const ibrd_solve_opts& o,
-                   bool zero_guess, ibrd_solve_info* info) {
+// Where the per-iteration residual estimates go: entry = scale * |g_{j+1}| / ||b||.
+struct History {
+  double* buf = nullptr;
+  int cap = 0;
+  int len = 0;
+  double scale = 1.0;
+  void add(double v) {
+    if (buf && len < cap) buf[len++] = scale * v;
+  }
+};
+
+// Right-preconditioned flexible GMRES (Saad 1993) with true-residual restarts,
+// on vectors of type E, to relative residual tol in at most max_iter
+// iterations. With trust_estimate the solve ends as soon as the Givens
+// residual estimate meets tol (no true residual is formed then): used for the
+// inner solves of iterative refinement, whose caller forms the true residual
+// itself.
+template <typename E>
+SolveResult fgmres(ibrd_grid g, LinOp<E>& op, const E* b, E* x, size_t n, const ibrd_solve_opts& o, double tol,
+                   int max_iter, bool zero_guess, History& hist, bool trust_estimate = false) {
   SolveResult R;
   const int m = std::max(1, o.restart);
-  ensure_krylov(g, n, m);
+  const size_t ld = ensure_krylov<E>(g, n, m);
   IBRD_CUDA(cudaMemsetAsync(g->scal + S_RCOUNT, 0, sizeof(double), g->s));
   const int ldh = m + 1;
-  double* V = g->V;
-  double* Z = g->Z;
-  launch_dot(b, b, n, g->partial, g->scal + S_BB, 1.0, g->s);
+  E* V = reinterpret_cast<E*>(g->V);
+  E* Z = reinterpret_cast<E*>(g->Z);
+  launch_dot<E>(b, b, n, g->partial, g->scal + S_BB, 1.0, g->s);
+  const double bnorm = std::sqrt(host_scalar(g, S_BB));
+  if (!std::isfinite(bnorm)) {
+    R.st = IBRD_ERR_NONFINITE;
+    return R;
+  }
+  if (bnorm == 0.0) {
+    IBRD_CUDA(cudaMemsetAsync(x, 0, sizeof(E) * n, g->s));
+    return R;
+  }
+  // r0 = b - K x0
+  if (zero_guess) {
+    IBRD_CUDA(cudaMemsetAsync(x, 0, sizeof(E) * n, g->s));
+    IBRD_CUDA(cudaMemcpyAsync(V, b, sizeof(E) * n, cudaMemcpyDeviceToDevice, g->s));
+  } else {
+    op.apply(x, V);
+    launch_axpby<E>(1.0, b, -1.0, V, n, g->s);
+  }
+  launch_dot<E>(V, V, n, g->partial, g->scal + S_TMP2, 1.0, g->s);
+  launch_sqrt_scalar(g->scal + S_TMP2, g->scal + S_NORM, g->s);
+  double beta = std::sqrt(host_scalar(g, S_TMP2));
+  while (true) {
+    R.rel = beta / bnorm;
+    if (!std::isfinite(R.rel)) {
+      R.st = IBRD_ERR_NONFINITE;
+      break;
+    }
+    if (R.rel <= tol) break;
+    if (R.iters >= max_iter) {
+      R.st = IBRD_ERR_NOT_CONVERGED;
+      break;
+    }
+    // V[0] = r / beta, gvec = [beta, 0, ...]
+    launch_scale_by_inv<E>(V, V, n, g->scal + S_NORM, 1.0, g->s);
+    prof_begin(P_SMALL, g->s);
+    k_set_gvec<<<1, 64, 0, g->s>>>(g->gvec, m, g->scal + S_NORM);
+    prof_end(P_SMALL, g->s, "set_gvec");
+    int k = 0;
+    bool breakdown = false, estimate_met = false;
+    double res_last = 0.0;
+    for (int j = 0; j < m; ++j) {
+      E* vj = V + (size_t)j * ld;
+      E* zj = Z + (size_t)j * ld;
+      E* w = V + (size_t)(j + 1) * ld;
+      run_precond<E>(g, op, j, vj, zj, o.graphs != 0);
+      op.apply(zj, w);
+      orthogonalize<E>(g, j, n, ld, ldh, o.reorth_eta);
+      double* hcol = g->H + (size_t)j * ldh;
+      launch_sqrt_scalar(g->scal + S_SQ, hcol + j + 1, g->s);
+      launch_scale_by_inv<E>(w, w, n, hcol + j + 1, 1.0, g->s);
+      launch_givens(g->H, ldh, j, g->cs, g->sn, g->gvec, g->scal + S_RES, g->s);
+      // one host read per iteration: residual estimate and the norms
+      IBRD_CUDA(cudaMemcpyAsync(g->host, g->scal, sizeof(double) * 16, cudaMemcpyDeviceToHost, g->s));
+      IBRD_CUDA(cudaStreamSynchronize(g->s));
+      const double res = g->host[S_RES], sq = g->host[S_SQ], ww = g->host[S_TMP];
+      // breakdown: w lies in the span of V (a zero or negligible new column,
+      // relative to the rounding of E); V[j+1] is then not used again
+      const double floor_sq = sizeof(E) == 4 ? 1e-12 : 1e-28;
+      const bool tiny = !(sq > floor_sq * ww) || sq <= 0.0;
+      k = j + 1;
+      R.iters++;
+      res_last = res;
+      hist.add(res / bnorm);
+      if (!std::isfinite(res) || !std::isfinite(sq)) {
+        R.st = IBRD_ERR_NONFINITE;
+        break;
+      }
+      if (tiny) {
+        breakdown = true;
+        break;
+      }
+      if (res / bnorm <= tol) {
+        estimate_met = true;
+        break;
+      }
+      if (R.iters >= max_iter) break;
+    }
+    if (R.st == IBRD_ERR_NONFINITE) break;
+    // x += Z y
+    launch_backsolve(g->H, ldh, k, g->gvec, g->yv, g->s);
+    for (int g0 = 0; g0 < k; g0 += kDotGroup) {
+      const int mm = std::min(kDotGroup, k - g0);
+      launch_multi_axpy(x, Z + (size_t)g0 * ld, ld, mm, g->yv + g0, 1.0, n, nullptr, g->s);
+    }
+    if (trust_estimate && (estimate_met || breakdown)) {
+      R.rel = res_last / bnorm;
+      break;
+    }
+    // true residual
+    op.apply(x, V);
+    launch_axpby<E>(1.0, b, -1.0, V, n, g->s);
+    launch_dot<E>(V, V, n, g->partial, g->scal + S_TMP2, 1.0, g->s);
+    launch_sqrt_scalar(g->scal + S_TMP2, g->scal + S_NORM, g->s);
+    beta = std::sqrt(host_scalar(g, S_TMP2));
+    if (breakdown && beta / bnorm > tol) {
+      R.rel = beta / bnorm;
+      // an invariant subspace was found but the true residual disagrees:
+      // restart once more unless nothing changes
+      if (R.iters >= max_iter) {
+        R.st = IBRD_ERR_BREAKDOWN;
+        break;
+      }
+    }
+  }
+  g->reorths += (long)host_scalar(g, S_RCOUNT);
+  return R;
+}
+
+// FP64 solve of K x = b through FP32 Krylov iterations (iterative refinement):
+// the residual r = b - K x is formed in FP64 (op64), the correction solves
+// K d = r / ||r|| by FP32 FGMRES (op32, FP32 preconditioner) to relative
+// residual max(inner_tol, tol ||b|| / (2 ||r||)), and x += ||r|| d in FP64.
+// Each refinement step multiplies the FP64 residual by about the inner
+// tolerance until the FP64 rounding floor, so the stopping test below is on
+// the true FP64 residual, as for the FP64 solver.
+SolveResult refine(ibrd_grid g, LinOp<double>& op64, LinOp<float>& op32, const double* b, double* x, size_t n,
+                   const ibrd_solve_opts& o, bool zero_guess, History& hist) {
+  SolveResult R;
+  if (g->ir_cap < n) {
+    cudaFree(g->ir_r);
+    cudaFree(g->ir_r32);
+    cudaFree(g->ir_d32);
+    g->ir_r = nullptr;
+    g->ir_r32 = g->ir_d32 = nullptr;
+    g->ir_r = dalloc<double>(n);
+    g->ir_r32 = dalloc<float>(n);
+    g->ir_d32 = dalloc<float>(n);
+    g->ir_cap = n;
+  }
+  double* r = g->ir_r;
+  launch_dot<double>(b, b, n, g->partial, g->scal + S_BB, 1.0, g->s);
   const double bnorm = std::sqrt(host_scalar(g, S_BB));
   if (!std::isfinite(bnorm)) {
     R.st = IBRD_ERR_NONFINITE;
@@ -598,20 +759,23 @@ SolveResult fgmres(ibrd_grid g, LinOp& op, const double* b, double* x, size_t n,
     IBRD_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, g->s));
     return R;
   }
-  // r0 = b - K x0
+  auto residual = [&]() {
+    op64.apply(x, r);
+    launch_axpby<double>(1.0, b, -1.0, r, n, g->s);
+    launch_dot<double>(r, r, n, g->partial, g->scal + S_TMP2, 1.0, g->s);
+    return std::sqrt(host_scalar(g, S_TMP2));
+  };
+  double rnorm;
   if (zero_guess) {
     IBRD_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, g->s));
-    IBRD_CUDA(cudaMemcpyAsync(V, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, g->s));
+    IBRD_CUDA(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, g->s));
+    rnorm = bnorm;
   } else {
-    op.apply(x, V);
-    launch_axpby(1.0, b, -1.0, V, n, g->s);
+    rnorm = residual();
   }
-  launch_dot(V, V, n, g->partial, g->scal + S_TMP2, 1.0, g->s);
-  launch_sqrt_scalar(g->scal + S_TMP2, g->scal + S_NORM, g->s);
-  double beta = std::sqrt(host_scalar(g, S_TMP2));
-  int hist = 0;
+  int stalled = 0;
   while (true) {
-    R.rel = beta / bnorm;
+    R.rel = rnorm / bnorm;
     if (!std::isfinite(R.rel)) {
       R.st = IBRD_ERR_NONFINITE;
       break;
@@ -621,66 +785,28 @@ SolveResult fgmres(ibrd_grid g, LinOp& op, const double* b, double* x, size_t n,
       R.st = IBRD_ERR_NOT_CONVERGED;
       break;
     }
-    // V[0] = r / beta, gvec = [beta, 0, ...]
-    launch_scale_by_inv(V, V, n, g->scal + S_NORM, 1.0, g->s);
-    prof_begin(P_SMALL, g->s);
-    k_set_gvec<<<1, 64, 0, g->s>>>(g->gvec, m, g->scal + S_NORM);
-    prof_end(P_SMALL, g->s, "set_gvec");
-    int k = 0;
-    bool breakdown = false;
-    for (int j = 0; j < m; ++j) {
-      run_precond(g, op, j, V + (size_t)j * n, Z + (size_t)j * n, o.graphs != 0);
-      op.apply(Z + (size_t)j * n, V + (size_t)(j + 1) * n);
-      orthogonalize(g, j, n, ldh, o.reorth_eta);
-      double* hcol = g->H + (size_t)j * ldh;
-      launch_sqrt_scalar(g->scal + S_SQ, hcol + j + 1, g->s);
-      launch_scale_by_inv(V + (size_t)(j + 1) * n, V + (size_t)(j + 1) * n, n, hcol + j + 1, 1.0, g->s);
-      launch_givens(g->H, ldh, j, g->cs, g->sn, g->gvec, g->scal + S_RES, g->s);
-      // one host read per iteration: residual estimate and the norms
-      IBRD_CUDA(cudaMemcpyAsync(g->host, g->scal, sizeof(double) * 16, cudaMemcpyDeviceToHost, g->s));
-      IBRD_CUDA(cudaStreamSynchronize(g->s));
-      const double res = g->host[S_RES], sq = g->host[S_SQ], ww = g->host[S_TMP];
-      // breakdown: w lies in the span of V (a zero or negligible new column);
-      // V[j+1] is then not used again
-      const bool tiny = !(sq > 1e-28 * ww) || sq <= 0.0;
-      k = j + 1;
-      R.iters++;
-      if (info && info->residual_history && hist < info->history_cap) info->residual_history[hist++] = res / bnorm;
-      if (!std::isfinite(res) || !std::isfinite(sq)) {
-        R.st = IBRD_ERR_NONFINITE;
-        break;
-      }
-      if (tiny) {
-        breakdown = true;
-        break;
-      }
-      if (res / bnorm <= o.tol || R.iters >= o.max_iter) break;
+    // three refinement steps in a row that do not halve the residual: the
+    // FP32 corrections no longer improve the FP64 iterate
+    if (stalled >= 3) {
+      R.st = IBRD_ERR_NOT_CONVERGED;
+      break;
     }
-    if (R.st == IBRD_ERR_NONFINITE) break;
-    // x += Z y
-    launch_backsolve(g->H, ldh, k, g->gvec, g->yv, g->s);
-    for (int g0 = 0; g0 < k; g0 += kDotGroup) {
-      const int mm = std::min(kDotGroup, k - g0);
-      launch_multi_axpy(x, Z + (size_t)g0 * n, n, mm, g->yv + g0, 1.0, n, nullptr, g->s);
+    launch_convert<double, float>(r, g->ir_r32, n, 1.0 / rnorm, nullptr, g->s);
+    const double tol_in = std::max(o.inner_tol, 0.5 * o.tol / R.rel);
+    hist.scale = R.rel;
+    const SolveResult I =
+        fgmres<float>(g, op32, g->ir_r32, g->ir_d32, n, o, tol_in, o.max_iter - R.iters, true, hist, true);
+    R.iters += I.iters;
+    g->refinements++;
+    if (I.st == IBRD_ERR_NONFINITE) {
+      R.st = IBRD_ERR_NONFINITE;
+      break;
     }
-    // true residual
-    op.apply(x, V);
-    launch_axpby(1.0, b, -1.0, V, n, g->s);
-    launch_dot(V, V, n, g->partial, g->scal + S_TMP2, 1.0, g->s);
-    launch_sqrt_scalar(g->scal + S_TMP2, g->scal + S_NORM, g->s);
-    beta = std::sqrt(host_scalar(g, S_TMP2));
-    if (breakdown && beta / bnorm > o.tol) {
-      R.rel = beta / bnorm;
-      // an invariant subspace was found but the true residual disagrees:
-      // restart once more unless nothing changes
-      if (R.iters >= o.max_iter) {
-        R.st = IBRD_ERR_BREAKDOWN;
-        break;
-      }
-    }
+    launch_add_scaled(rnorm, g->ir_d32, x, n, g->s);
+    const double rn = residual();
+    stalled = (rn > 0.5 * rnorm) ? stalled + 1 : 0;
+    rnorm = rn;
   }
-  if (info) info->history_len = hist;
-  g->reorths = (long)host_scalar(g, S_RCOUNT);
   return R;
 }
 
@@ -728,8 +854,9 @@ void ensure_nvec(ibrd_grid g, int m) {
 
 // ---------------------------------------------------------------- operators
 // B c = alpha c - chi L c + S (kappa * J c)  (Eq. unsteady_system / steady_state)
+// on fields of type T; the preconditioner is V-cycles in T.
 template <typename T>
-struct ReactionOp : LinOp {
+struct ReactionOp : LinOp<T> {
   ibrd_grid g;
   const double* kappa;
   double sigma;
@@ -740,28 +867,19 @@ struct ReactionOp : LinOp {
     std::snprintf(buf, sizeof buf, "reaction|%zu|%d|%d|%d|%.17g", sizeof(T), o.mg_cycles, o.nu1, o.nu2, sigma);
     return buf;
   }
-  void apply(const double* x, double* y) override {
-    launch_interp<double>(g->blobs, g->d, x, 1.0, g->nv[0], g->s);
-    launch_apply_A<double>(x, y, g->d, stencil(g->h, g->chi, g->alpha), g->s);
-    launch_spread<double>(g->blobs, g->d, g->nv[0], kappa, inv_h3(g), y, 1, g->s);
+  void apply(const T* x, T* y) override {
+    launch_interp<T>(g->blobs, g->d, x, 1.0, g->nv[0], g->s);
+    launch_apply_A<T>(x, y, g->d, stencil(g->h, g->chi, g->alpha), g->s);
+    launch_spread<T>(g->blobs, g->d, g->nv[0], kappa, inv_h3(g), y, 1, g->s);
   }
   // n V-cycles of (sigma I - chi L) (Eq. Pinv_Poisson)
-  void precond(const double* v, double* z) override {
-    if (sizeof(T) == 8) {
-      vcycles<double>(g, v, z, true, sigma, o.mg_cycles, o.nu1, o.nu2);
-    } else {
-      float* b32 = pfield<float>(g, 0);
-      float* x32 = pfield<float>(g, 1);
-      launch_convert<double, float>(v, b32, g->d.n(), 1.0, nullptr, g->s);
-      vcycles<float>(g, b32, x32, true, sigma, o.mg_cycles, o.nu1, o.nu2);
-      launch_convert<float, double>(x32, z, g->d.n(), 1.0, nullptr, g->s);
-    }
-  }
+  void precond(const T* v, T* z) override { vcycles<T>(g, v, z, true, sigma, o.mg_cycles, o.nu1, o.nu2); }
 };
 
-// K [c; lambda] = [A c + zeta S lambda; xi J c]  (Eq. saddle_point)
+// K [c; lambda] = [A c + zeta S lambda; xi J c]  (Eq. saddle_point) on
+// vectors [c; lambda] of type T; the preconditioner works in T.
 template <typename T>
-struct SaddleOp : LinOp {
+struct SaddleOp : LinOp<T> {
   ibrd_grid g;
   ibrd_solve_opts o;
   double zeta, xi;
@@ -775,11 +893,11 @@ struct SaddleOp : LinOp {
                   o.nu1, o.nu2, o.schur_inner, o.precond, zeta, xi, g->alpha, g->gamma_diag);
     return buf;
   }
-  void apply(const double* x, double* y) override {
+  void apply(const T* x, T* y) override {
     const size_t nc = g->d.n();
-    launch_apply_A<double>(x, y, g->d, stencil(g->h, g->chi, g->alpha), g->s);
-    launch_spread<double>(g->blobs, g->d, x + nc, nullptr, zeta * inv_h3(g), y, 1, g->s);
-    launch_interp<double>(g->blobs, g->d, x, xi, y + nc, g->s);
+    launch_apply_A<T>(x, y, g->d, stencil(g->h, g->chi, g->alpha), g->s);
+    launch_spread<T, T>(g->blobs, g->d, x + nc, nullptr, zeta * inv_h3(g), y, 1, g->s);
+    launch_interp<T, T>(g->blobs, g->d, x, xi, y + nc, g->s);
   }
   // Appendix A, steps 1-5, with A~_n^-1 = n V-cycles and, for the approximate
   // Schur complement, m GMRES iterations on J A~_1^-1 S.
@@ -792,13 +910,13 @@ struct SaddleOp : LinOp {
   // smoothing sweep. Where a constant offset of a field cancels (c~ is used
   // only through c~ + cbar with cbar = <f/xi - J c~> and J 1 = 1) the mean is
   // not formed at all.
-  void precond(const double* v, double* z) override {
+  void precond(const T* v, T* z) override {
     const size_t nc = g->d.n();
     const int N = g->blobs.n;
-    const double* vc = v;
-    const double* vf = v + nc;
-    double* zc = z;
-    double* zl = z + nc;
+    const T* vc = v;
+    const T* vf = v + nc;
+    T* zc = z;
+    T* zl = z + nc;
     T* gt = pfield<T>(g, 0);   // g~
     T* cs = pfield<T>(g, 1);   // c~* then c~
     const double volume = (double)nc * g->h * g->h * g->h;
@@ -809,7 +927,7 @@ struct SaddleOp : LinOp {
     const double* bmean = nullptr;
     const double* xshift = nullptr;
     if (singular) {
-      launch_convert_sum<T>(vc, gt, nc, g->partial, sc + S_GSUM, sc + S_G32SUM, g->s);
+      launch_convert_sum<T, T>(vc, gt, nc, g->partial, sc + S_GSUM, sc + S_G32SUM, g->s);
       // zeta S (lambda-bar 1) = (V / (N N_c)) sum(g) S 1; its total is sum(g)
       launch_spread_const<T>(g->blobs, g->d, sc + S_GSUM, -volume / ((double)N * (double)nc) * ih3, gt, g->s);
       prof_begin(P_SMALL, g->s);
@@ -822,7 +940,7 @@ struct SaddleOp : LinOp {
       xshift = sc + S_XMEAN1;
       vcycles<T>(g, gt, cs, true, shift, o.mg_cycles, o.nu1, o.nu2, bmean, XMean::Report, sc + S_XMEAN1);
     } else {
-      launch_convert<double, T>(vc, gt, nc, 1.0, nullptr, g->s);
+      launch_convert<T, T>(vc, gt, nc, 1.0, nullptr, g->s);
       vcycles<T>(g, gt, cs, true, shift, o.mg_cycles, o.nu1, o.nu2);
     }
     // step 2: rhs = (zeta xi)^-1 (xi J c~* - f), with J applied to the
@@ -870,11 +988,11 @@ struct SaddleOp : LinOp {
       launch_interp<T>(g->blobs, g->d, cs, 1.0, t, g->s);
       launch_nvec_affine(t, t, N, -1.0, nullptr, vf, 1.0 / xi, g->s);
       launch_sum<double>(t, N, g->partial, sc + S_CBAR, 1.0 / N, g->s);
-      launch_convert<double, double>(lam, zl, N, 1.0, sc + S_LBAR, g->s);
-      launch_convert<T, double>(cs, zc, nc, 1.0, sc + S_CBAR, g->s);
+      launch_convert<double, T>(lam, zl, N, 1.0, sc + S_LBAR, g->s);
+      launch_convert<T, T>(cs, zc, nc, 1.0, sc + S_CBAR, g->s);
     } else {
-      IBRD_CUDA(cudaMemcpyAsync(zl, lam, sizeof(double) * N, cudaMemcpyDeviceToDevice, g->s));
-      launch_convert<T, double>(cs, zc, nc, 1.0, nullptr, g->s);
+      launch_convert<double, T>(lam, zl, N, 1.0, nullptr, g->s);
+      IBRD_CUDA(cudaMemcpyAsync(zc, cs, sizeof(T) * nc, cudaMemcpyDeviceToDevice, g->s));
     }
   }
 };
@@ -936,7 +1054,7 @@ ibrd_solve_opts resolve_opts(ibrd_grid g, const ibrd_solve_opts* in) {
   if (o.xi <= 0.0) o.xi = o.zeta / (g->h * g->h * g->h);
   if (!(o.tol > 0.0) || o.restart < 1 || o.restart > 60 || o.max_iter < 0 || o.mg_cycles < 1 ||
       o.schur_inner < 1 || o.schur_inner > 60 || o.nu1 < 0 || o.nu2 < 0 || !(o.zeta != 0.0) ||
-      !(o.reorth_eta >= 0.0) ||
+      !(o.reorth_eta >= 0.0) || !(o.inner_tol > 0.0 && o.inner_tol < 1.0) ||
       (o.precision != IBRD_FP64 && o.precision != IBRD_MIXED_FP32) ||
       (o.precond != IBRD_PRECOND_SCHUR && o.precond != IBRD_PRECOND_DIAG))
     throw ArgError{IBRD_ERR_ARG, "invalid solver options"};
@@ -950,6 +1068,7 @@ void fill_info(ibrd_solve_info* info, const SolveResult& R, ibrd_grid g, double 
   info->inner_iters = (int)g->inner;
   info->vcycles = (int)g->vcycles;
   info->reorths = (int)g->reorths;
+  info->refinements = (int)g->refinements;
   info->rel_residual = R.rel;
   info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count() - t0;
 }
@@ -998,6 +1117,7 @@ void ibrd_default_opts(ibrd_solve_opts* o) {
   o->use_guess = 0;
   o->reorth_eta = 0.70710678118654752;
   o->graphs = 1;
+  o->inner_tol = 1e-4;
 }
 
 const char* ibrd_status_string(int st) {
@@ -1035,6 +1155,7 @@ void ibrd_grid_destroy(ibrd_grid g) {
   F(g->scal); F(g->partial); F(g->dflag);
   if (g->host) cudaFreeHost(g->host);
   F(g->V); F(g->Z); F(g->H); F(g->cs); F(g->sn); F(g->gvec); F(g->yv); F(g->hb2); F(g->xs); F(g->bs);
+  F(g->ir_r); F(g->ir_r32); F(g->ir_d32);
   for (auto p : g->p64) F(p);
   for (auto p : g->p32) F(p);
   for (auto p : g->nv) F(p);
@@ -1174,6 +1295,7 @@ ibrd_status ibrd_solve_reaction(ibrd_grid g, const double* kappa, const double* 
     g->vcycles = 0;
     g->inner = 0;
     g->reorths = 0;
+    g->refinements = 0;
     ensure_nvec(g, o.schur_inner);
     double sigma = g->alpha;
     if (N > 0) {
@@ -1190,13 +1312,19 @@ ibrd_status ibrd_solve_reaction(ibrd_grid g, const double* kappa, const double* 
     }
     if (!(sigma > 0.0)) throw ArgError{IBRD_ERR_ARG, "steady reaction system needs some kappa > 0"};
     SolveResult R;
-    if (o.precision == IBRD_FP64) {
-      ReactionOp<double> op(g, kappa, sigma, o);
-      R = fgmres(g, op, rhs, c, g->d.n(), o, !o.use_guess, info);
-    } else {
-      ReactionOp<float> op(g, kappa, sigma, o);
-      R = fgmres(g, op, rhs, c, g->d.n(), o, !o.use_guess, info);
+    History hist;
+    if (info) {
+      hist.buf = info->residual_history;
+      hist.cap = info->history_cap;
     }
+    ReactionOp<double> op(g, kappa, sigma, o);
+    if (o.precision == IBRD_FP64) {
+      R = fgmres<double>(g, op, rhs, c, g->d.n(), o, o.tol, o.max_iter, !o.use_guess, hist);
+    } else {
+      ReactionOp<float> op32(g, kappa, sigma, o);
+      R = refine(g, op, op32, rhs, c, g->d.n(), o, !o.use_guess, hist);
+    }
+    if (info) info->history_len = hist.len;
     report(g, c, nullptr, kappa, info);
     fill_info(info, R, g, t0);
     if (R.st != IBRD_OK) g->err = std::string("ibrd_solve_reaction: ") + ibrd_status_string(R.st);
@@ -1215,6 +1343,7 @@ ibrd_status ibrd_solve_saddle(ibrd_grid g, const double* rhs, const double* f, d
     g->vcycles = 0;
     g->inner = 0;
     g->reorths = 0;
+    g->refinements = 0;
     ensure_nvec(g, o.schur_inner);
     const size_t nc = g->d.n();
     const size_t n = nc + N;
@@ -1241,13 +1370,19 @@ ibrd_status ibrd_solve_saddle(ibrd_grid g, const double* rhs, const double* f, d
       g->vcycles = 0;
     }
     SolveResult R;
-    if (o.precision == IBRD_FP64) {
-      SaddleOp<double> op(g, o, o.zeta, o.xi);
-      R = fgmres(g, op, g->bs, g->xs, n, o, !o.use_guess, info);
-    } else {
-      SaddleOp<float> op(g, o, o.zeta, o.xi);
-      R = fgmres(g, op, g->bs, g->xs, n, o, !o.use_guess, info);
+    History hist;
+    if (info) {
+      hist.buf = info->residual_history;
+      hist.cap = info->history_cap;
     }
+    SaddleOp<double> op(g, o, o.zeta, o.xi);
+    if (o.precision == IBRD_FP64) {
+      R = fgmres<double>(g, op, g->bs, g->xs, n, o, o.tol, o.max_iter, !o.use_guess, hist);
+    } else {
+      SaddleOp<float> op32(g, o, o.zeta, o.xi);
+      R = refine(g, op, op32, g->bs, g->xs, n, o, !o.use_guess, hist);
+    }
+    if (info) info->history_len = hist.len;
     IBRD_CUDA(cudaMemcpyAsync(c, g->xs, sizeof(double) * nc, cudaMemcpyDeviceToDevice, g->s));
     IBRD_CUDA(cudaMemcpyAsync(lambda, g->xs + nc, sizeof(double) * N, cudaMemcpyDeviceToDevice, g->s));
     report(g, c, lambda, nullptr, info);

@@ -255,11 +255,11 @@ __global__ void __launch_bounds__(1024) k_scan_ints(const int* __restrict__ in, 
 
 // One thread per covered cell: gathers the contributions of its tile's blobs
 // in increasing blob index.
-template <typename T, typename W>
+template <typename T, typename W, typename L>
 __global__ void __launch_bounds__(256) k_spread(const int* __restrict__ cells, const int* __restrict__ cell_tile,
                                                 int n_cells, const int* __restrict__ offset,
                                                 const int* __restrict__ list, const int* __restrict__ idx,
-                                                const W* __restrict__ wt, const double* __restrict__ lam,
+                                                const W* __restrict__ wt, const L* __restrict__ lam,
                                                 const double* __restrict__ cval, const double* __restrict__ coef,
                                                 double scale, T* __restrict__ out, int nx, int ny, int nz) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(256) k_spread(const int* __restrict__ cells, c
     int dx, dy, dz;
     if (covers(idx + b * 12, i, j, k, nx, ny, nz, dx, dy, dz)) {
       const W* wb = wt + b * 12;
-      const double l = lam ? lam[b] : *cval;
+      const double l = lam ? (double)lam[b] : *cval;
       const W amp = (W)(coef ? coef[b] * l : l);
       acc += amp * ((wb[dx] * wb[4 + dy]) * wb[8 + dz]);
     }
@@ -281,9 +281,9 @@ __global__ void __launch_bounds__(256) k_spread(const int* __restrict__ cells, c
 }
 
 // One warp per blob: lanes cover the 4x4x4 support, two cells each.
-template <typename T, typename W>
+template <typename T, typename W, typename O>
 __global__ void k_interp(const int* __restrict__ idx, const W* __restrict__ wt, const T* __restrict__ x,
-                         double scale, double* __restrict__ out, int n, int nx, int ny) {
+                         double scale, O* __restrict__ out, int n, int nx, int ny) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= n) return;
@@ -299,7 +299,7 @@ __global__ void k_interp(const int* __restrict__ idx, const W* __restrict__ wt, 
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if (lane == 0) out[warp] = scale * (double)v;
+  if (lane == 0) out[warp] = (O)(scale * (double)v);
 }
 
 }  // namespace
@@ -409,8 +409,8 @@ void blobs_setup(BlobSet& b, Dims d, double h, const double* q_in, int n, cudaSt
   }
 }
 
-template <typename T>
-void launch_spread(const BlobSet& b, Dims d, const double* lam, const double* coef, double scale, T* out,
+template <typename T, typename L>
+void launch_spread(const BlobSet& b, Dims d, const L* lam, const double* coef, double scale, T* out,
                    int accumulate, cudaStream_t s) {
   if (!accumulate) IBRD_CUDA(cudaMemsetAsync(out, 0, sizeof(T) * d.n(), s));
   if (b.n == 0 || b.n_cells == 0) return;
@@ -418,11 +418,11 @@ void launch_spread(const BlobSet& b, Dims d, const double* lam, const double* co
   const int blocks = (b.n_cells + 255) / 256;
   prof_begin(c, s);
   if (sizeof(T) == 8)
-    k_spread<T, double><<<blocks, 256, 0, s>>>(b.cells, b.cell_tile, b.n_cells, b.tile_offset, b.tile_blobs, b.idx,
-                                               b.w64, lam, nullptr, coef, scale, out, d.nx, d.ny, d.nz);
+    k_spread<T, double, L><<<blocks, 256, 0, s>>>(b.cells, b.cell_tile, b.n_cells, b.tile_offset, b.tile_blobs,
+                                                  b.idx, b.w64, lam, nullptr, coef, scale, out, d.nx, d.ny, d.nz);
   else
-    k_spread<T, float><<<blocks, 256, 0, s>>>(b.cells, b.cell_tile, b.n_cells, b.tile_offset, b.tile_blobs, b.idx,
-                                              b.w32, lam, nullptr, coef, scale, out, d.nx, d.ny, d.nz);
+    k_spread<T, float, L><<<blocks, 256, 0, s>>>(b.cells, b.cell_tile, b.n_cells, b.tile_offset, b.tile_blobs,
+                                                 b.idx, b.w32, lam, nullptr, coef, scale, out, d.nx, d.ny, d.nz);
   prof_end(c, s, "spread", (double)b.n_cells * (2.0 * sizeof(T) + 8.0) + (double)b.n * (48.0 + 12.0 * sizeof(T) + 16.0));
 }
 
@@ -433,35 +433,40 @@ void launch_spread_const(const BlobSet& b, Dims d, const double* cval, double sc
   const int blocks = (b.n_cells + 255) / 256;
   prof_begin(c, s);
   if (sizeof(T) == 8)
-    k_spread<T, double><<<blocks, 256, 0, s>>>(b.cells, b.cell_tile, b.n_cells, b.tile_offset, b.tile_blobs, b.idx,
-                                               b.w64, nullptr, cval, nullptr, scale, out, d.nx, d.ny, d.nz);
+    k_spread<T, double, double><<<blocks, 256, 0, s>>>(b.cells, b.cell_tile, b.n_cells, b.tile_offset,
+                                                       b.tile_blobs, b.idx, b.w64, nullptr, cval, nullptr, scale,
+                                                       out, d.nx, d.ny, d.nz);
   else
-    k_spread<T, float><<<blocks, 256, 0, s>>>(b.cells, b.cell_tile, b.n_cells, b.tile_offset, b.tile_blobs, b.idx,
-                                              b.w32, nullptr, cval, nullptr, scale, out, d.nx, d.ny, d.nz);
+    k_spread<T, float, double><<<blocks, 256, 0, s>>>(b.cells, b.cell_tile, b.n_cells, b.tile_offset,
+                                                      b.tile_blobs, b.idx, b.w32, nullptr, cval, nullptr, scale,
+                                                      out, d.nx, d.ny, d.nz);
   prof_end(c, s, "spread_const", (double)b.n_cells * (2.0 * sizeof(T) + 8.0) + (double)b.n * (48.0 + 12.0 * sizeof(T)));
 }
 
-template <typename T>
-void launch_interp(const BlobSet& b, Dims d, const T* x, double scale, double* out, cudaStream_t s) {
+template <typename T, typename O>
+void launch_interp(const BlobSet& b, Dims d, const T* x, double scale, O* out, cudaStream_t s) {
   if (b.n == 0) return;
   const int threads = 256;
   const int blocks = (int)(((size_t)b.n * 32 + threads - 1) / threads);
   const int c = pcls<T>(P_INTERP64, P_INTERP32);
   prof_begin(c, s);
   if (sizeof(T) == 8)
-    k_interp<T, double><<<blocks, threads, 0, s>>>(b.idx, b.w64, x, scale, out, b.n, d.nx, d.ny);
+    k_interp<T, double, O><<<blocks, threads, 0, s>>>(b.idx, b.w64, x, scale, out, b.n, d.nx, d.ny);
   else
-    k_interp<T, float><<<blocks, threads, 0, s>>>(b.idx, b.w32, x, scale, out, b.n, d.nx, d.ny);
+    k_interp<T, float, O><<<blocks, threads, 0, s>>>(b.idx, b.w32, x, scale, out, b.n, d.nx, d.ny);
   prof_end(c, s, "interp", (double)b.n * (64.0 * sizeof(T) + 48.0 + 12.0 * sizeof(T) + 8.0));
 }
 
-template void launch_spread<double>(const BlobSet&, Dims, const double*, const double*, double, double*, int,
-                                    cudaStream_t);
-template void launch_spread<float>(const BlobSet&, Dims, const double*, const double*, double, float*, int,
-                                   cudaStream_t);
+template void launch_spread<double, double>(const BlobSet&, Dims, const double*, const double*, double, double*,
+                                            int, cudaStream_t);
+template void launch_spread<float, double>(const BlobSet&, Dims, const double*, const double*, double, float*, int,
+                                           cudaStream_t);
+template void launch_spread<float, float>(const BlobSet&, Dims, const float*, const double*, double, float*, int,
+                                          cudaStream_t);
 template void launch_spread_const<double>(const BlobSet&, Dims, const double*, double, double*, cudaStream_t);
 template void launch_spread_const<float>(const BlobSet&, Dims, const double*, double, float*, cudaStream_t);
-template void launch_interp<double>(const BlobSet&, Dims, const double*, double, double*, cudaStream_t);
-template void launch_interp<float>(const BlobSet&, Dims, const float*, double, double*, cudaStream_t);
+template void launch_interp<double, double>(const BlobSet&, Dims, const double*, double, double*, cudaStream_t);
+template void launch_interp<float, double>(const BlobSet&, Dims, const float*, double, double*, cudaStream_t);
+template void launch_interp<float, float>(const BlobSet&, Dims, const float*, double, float*, cudaStream_t);
 
 }  // namespace ibrd

@@ -129,12 +129,25 @@ __global__ void __launch_bounds__(kRedThreads) k_sum_partial(const T* __restrict
   if (threadIdx.x == 0) partial[blockIdx.x] = acc;
 }
 
-__global__ void __launch_bounds__(kRedThreads) k_dot_partial(const double* __restrict__ x,
-                                                             const double* __restrict__ y, size_t n,
-                                                             double* __restrict__ partial) {
+// FP64: one FMA per element; FP32: products summed in FP32 over runs of 4
+// (stride apart) and the runs in FP64.
+template <typename E>
+__global__ void __launch_bounds__(kRedThreads) k_dot_partial(const E* __restrict__ x, const E* __restrict__ y,
+                                                             size_t n, double* __restrict__ partial) {
   double acc = 0.0;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    acc = fma(x[i], y[i], acc);
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if constexpr (sizeof(E) == 4) {
+    for (; i + 3 * stride < n; i += 4 * stride) {
+      const float r = fmaf(x[i], y[i], fmaf(x[i + stride], y[i + stride],
+                                            fmaf(x[i + 2 * stride], y[i + 2 * stride],
+                                                 x[i + 3 * stride] * y[i + 3 * stride])));
+      acc += (double)r;
+    }
+    for (; i < n; i += stride) acc += (double)(x[i] * y[i]);
+  } else {
+    for (; i < n; i += stride) acc = fma(x[i], y[i], acc);
+  }
   acc = block_sum(acc);
   if (threadIdx.x == 0) partial[blockIdx.x] = acc;
 }
@@ -147,26 +160,31 @@ __global__ void __launch_bounds__(kRedThreads) k_finalize(const double* __restri
   if (threadIdx.x == 0) *out = acc * scale;
 }
 
-// y = (T) x with the FP64 sum of x and the sum of the converted values.
-template <typename T>
-__global__ void __launch_bounds__(kRedThreads) k_convert_sum(const double* __restrict__ x, T* __restrict__ y,
+// y = (T) x with the sum of x and the sum of the converted values.
+template <typename X, typename T>
+__global__ void __launch_bounds__(kRedThreads) k_convert_sum(const X* __restrict__ x, T* __restrict__ y,
                                                              size_t n, double* __restrict__ pin,
                                                              double* __restrict__ pout) {
-  // the input sum needs one FP64 add per value; the converted values are
-  // summed in T over runs of 8 and folded into FP64
+  // FP64 input is summed with one FP64 add per value; FP32 values (input or
+  // converted) are summed in FP32 over runs of 8 and the runs in FP64
   double si = 0.0, so = 0.0;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   while (i < n) {
     T run = 0;
+    X run_in = 0;
 #pragma unroll 4
     for (int r = 0; r < 8 && i < n; ++r, i += stride) {
-      const double v = x[i];
+      const X v = x[i];
       const T t = (T)v;
       y[i] = t;
-      si += v;
+      if constexpr (sizeof(X) == 8)
+        si += v;
+      else
+        run_in += v;
       run += t;
     }
+    if constexpr (sizeof(X) == 4) si += (double)run_in;
     so += (double)run;
   }
   si = block_sum(si);
@@ -175,12 +193,13 @@ __global__ void __launch_bounds__(kRedThreads) k_convert_sum(const double* __res
   if (threadIdx.x == 0) pout[blockIdx.x] = so;
 }
 
+template <typename F>
 __global__ void k_nvec_affine(const double* __restrict__ in, double* __restrict__ out, int n, double a,
-                              const double* __restrict__ shift, const double* __restrict__ f, double bcoef) {
+                              const double* __restrict__ shift, const F* __restrict__ f, double bcoef) {
   const double sh = shift ? *shift : 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     double v = a * (in[i] - sh);
-    if (f) v = fma(bcoef, f[i], v);
+    if (f) v = fma(bcoef, (double)f[i], v);
     out[i] = v;
   }
 }
@@ -209,19 +228,27 @@ __global__ void k_convert(const Tx* __restrict__ x, Ty* __restrict__ y, size_t n
   }
 }
 
-__global__ void k_axpby(double a, const double* __restrict__ x, double b, double* __restrict__ y, size_t n) {
+template <typename E>
+__global__ void k_axpby(E a, const E* __restrict__ x, E b, E* __restrict__ y, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    y[i] = (b == 0.0) ? a * x[i] : fma(a, x[i], b * y[i]);
+    y[i] = (b == (E)0) ? a * x[i] : fma(a, x[i], b * y[i]);
 }
 
-__global__ void k_scale_by_inv(const double* __restrict__ x, double* __restrict__ y, size_t n,
-                               const double* __restrict__ den, double num) {
-  __shared__ double f;
-  if (threadIdx.x == 0) f = num / *den;
+template <typename E>
+__global__ void k_scale_by_inv(const E* __restrict__ x, E* __restrict__ y, size_t n, const double* __restrict__ den,
+                               double num) {
+  __shared__ E f;
+  if (threadIdx.x == 0) f = (E)(num / *den);
   __syncthreads();
-  const double ff = f;
+  const E ff = f;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     y[i] = x[i] * ff;
+}
+
+// x += a * (double) d: FP32 correction added to an FP64 field
+__global__ void k_add_scaled(double a, const float* __restrict__ d, double* __restrict__ x, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    x[i] = fma(a, (double)d[i], x[i]);
 }
 
 template <typename T>
@@ -291,29 +318,30 @@ void launch_finalize(const double* partial, int np, double* out, double scale, c
   prof_end(P_REDUCE, s, "finalize");
 }
 
-template <typename T>
-void launch_convert_sum(const double* x, T* y, size_t n, double* partial, double* out_in, double* out_out,
+template <typename X, typename T>
+void launch_convert_sum(const X* x, T* y, size_t n, double* partial, double* out_in, double* out_out,
                         cudaStream_t s) {
   prof_begin(P_VEC, s);
-  k_convert_sum<T><<<kRedBlocks, kRedThreads, 0, s>>>(x, y, n, partial, partial + kRedBlocks);
-  prof_end(P_VEC, s, "convert_sum", (8.0 + sizeof(T)) * n);
+  k_convert_sum<X, T><<<kRedBlocks, kRedThreads, 0, s>>>(x, y, n, partial, partial + kRedBlocks);
+  prof_end(P_VEC, s, "convert_sum", (double)(sizeof(X) + sizeof(T)) * n);
   launch_finalize(partial, kRedBlocks, out_in, 1.0, s);
   launch_finalize(partial + kRedBlocks, kRedBlocks, out_out, 1.0, s);
 }
 
-void launch_nvec_affine(const double* in, double* out, int n, double a, const double* shift, const double* f,
+template <typename F>
+void launch_nvec_affine(const double* in, double* out, int n, double a, const double* shift, const F* f,
                         double bcoef, cudaStream_t s) {
   if (n <= 0) return;
   prof_begin(P_VEC, s);
-  k_nvec_affine<<<std::min(64, (n + 255) / 256), 256, 0, s>>>(in, out, n, a, shift, f, bcoef);
+  k_nvec_affine<F><<<std::min(64, (n + 255) / 256), 256, 0, s>>>(in, out, n, a, shift, f, bcoef);
   prof_end(P_VEC, s, "nvec_affine", 24.0 * n);
 }
 
-void launch_dot(const double* x, const double* y, size_t n, double* partial, double* out, double scale,
-                cudaStream_t s) {
+template <typename E>
+void launch_dot(const E* x, const E* y, size_t n, double* partial, double* out, double scale, cudaStream_t s) {
   prof_begin(P_DOT, s);
-  k_dot_partial<<<kRedBlocks, kRedThreads, 0, s>>>(x, y, n, partial);
-  prof_end(P_DOT, s, "dot_partial", 16.0 * n);
+  k_dot_partial<E><<<kRedBlocks, kRedThreads, 0, s>>>(x, y, n, partial);
+  prof_end(P_DOT, s, "dot_partial", 2.0 * sizeof(E) * n);
   prof_begin(P_REDUCE, s);
   k_finalize<<<1, kRedThreads, 0, s>>>(partial, kRedBlocks, out, scale);
   prof_end(P_REDUCE, s, "finalize");
@@ -333,16 +361,24 @@ void launch_convert(const Tx* x, Ty* y, size_t n, double a, const double* shift,
   prof_end(P_VEC, s, "convert", (double)(sizeof(Tx) + sizeof(Ty)) * n);
 }
 
-void launch_axpby(double a, const double* x, double b, double* y, size_t n, cudaStream_t s) {
+template <typename E>
+void launch_axpby(double a, const E* x, double b, E* y, size_t n, cudaStream_t s) {
   prof_begin(P_VEC, s);
-  k_axpby<<<stream_blocks(n, 256), 256, 0, s>>>(a, x, b, y, n);
-  prof_end(P_VEC, s, "axpby", (b == 0.0 ? 16.0 : 24.0) * n);
+  k_axpby<E><<<stream_blocks(n, 256), 256, 0, s>>>((E)a, x, (E)b, y, n);
+  prof_end(P_VEC, s, "axpby", (b == 0.0 ? 2.0 : 3.0) * sizeof(E) * n);
 }
 
-void launch_scale_by_inv(const double* x, double* y, size_t n, const double* den, double num, cudaStream_t s) {
+template <typename E>
+void launch_scale_by_inv(const E* x, E* y, size_t n, const double* den, double num, cudaStream_t s) {
   prof_begin(P_VEC, s);
-  k_scale_by_inv<<<stream_blocks(n, 256), 256, 0, s>>>(x, y, n, den, num);
-  prof_end(P_VEC, s, "scale_by_inv", 16.0 * n);
+  k_scale_by_inv<E><<<stream_blocks(n, 256), 256, 0, s>>>(x, y, n, den, num);
+  prof_end(P_VEC, s, "scale_by_inv", 2.0 * sizeof(E) * n);
+}
+
+void launch_add_scaled(double a, const float* d, double* x, size_t n, cudaStream_t s) {
+  prof_begin(P_VEC, s);
+  k_add_scaled<<<stream_blocks(n, 256), 256, 0, s>>>(a, d, x, n);
+  prof_end(P_VEC, s, "add_scaled", 20.0 * n);
 }
 
 template <typename T>
@@ -363,8 +399,22 @@ void launch_nonfinite(const T* x, size_t n, int* flag, cudaStream_t s) {
 IBRD_INST(double)
 IBRD_INST(float)
 #undef IBRD_INST
-template void launch_convert_sum<float>(const double*, float*, size_t, double*, double*, double*, cudaStream_t);
-template void launch_convert_sum<double>(const double*, double*, size_t, double*, double*, double*, cudaStream_t);
+template void launch_convert_sum<double, float>(const double*, float*, size_t, double*, double*, double*,
+                                                cudaStream_t);
+template void launch_convert_sum<double, double>(const double*, double*, size_t, double*, double*, double*,
+                                                 cudaStream_t);
+template void launch_convert_sum<float, float>(const float*, float*, size_t, double*, double*, double*,
+                                               cudaStream_t);
+template void launch_nvec_affine<double>(const double*, double*, int, double, const double*, const double*, double,
+                                         cudaStream_t);
+template void launch_nvec_affine<float>(const double*, double*, int, double, const double*, const float*, double,
+                                        cudaStream_t);
+template void launch_dot<double>(const double*, const double*, size_t, double*, double*, double, cudaStream_t);
+template void launch_dot<float>(const float*, const float*, size_t, double*, double*, double, cudaStream_t);
+template void launch_axpby<double>(double, const double*, double, double*, size_t, cudaStream_t);
+template void launch_axpby<float>(double, const float*, double, float*, size_t, cudaStream_t);
+template void launch_scale_by_inv<double>(const double*, double*, size_t, const double*, double, cudaStream_t);
+template void launch_scale_by_inv<float>(const float*, float*, size_t, const double*, double, cudaStream_t);
 template void launch_convert<double, float>(const double*, float*, size_t, double, const double*, cudaStream_t);
 template void launch_convert<float, double>(const float*, double*, size_t, double, const double*, cudaStream_t);
 template void launch_convert<double, double>(const double*, double*, size_t, double, const double*, cudaStream_t);

@@ -123,27 +123,32 @@ template <typename T>
 void launch_sum(const T* x, size_t n, double* partial, double* out, double scale, cudaStream_t s);
 // *out = scale * sum(partial[0..np))
 void launch_finalize(const double* partial, int np, double* out, double scale, cudaStream_t s);
-// y = (T)x with sums: *sum_in += sum(x) (FP64), *sum_out += sum(y); both sums
-// are finalized by the launcher into out_in / out_out.
-template <typename T>
-void launch_convert_sum(const double* x, T* y, size_t n, double* partial, double* out_in, double* out_out,
+// y = (T)x with sums: *out_in = sum(x), *out_out = sum(y), both in FP64
+// (partial uses 2 * kRedBlocks doubles).
+template <typename X, typename T>
+void launch_convert_sum(const X* x, T* y, size_t n, double* partial, double* out_in, double* out_out,
                         cudaStream_t s);
 // out[i] = a * (in[i] - *shift) + bcoef * f[i]   (shift, f nullable; N-vectors)
-void launch_nvec_affine(const double* in, double* out, int n, double a, const double* shift, const double* f,
+template <typename F>
+void launch_nvec_affine(const double* in, double* out, int n, double a, const double* shift, const F* f,
                         double bcoef, cudaStream_t s);
-// out[0] = scale * sum(x*y)
-void launch_dot(const double* x, const double* y, size_t n, double* partial, double* out, double scale,
-                cudaStream_t s);
+// out[0] = scale * sum(x*y)  (FP32 vectors: FP32 products, FP64 sums of runs)
+template <typename E>
+void launch_dot(const E* x, const E* y, size_t n, double* partial, double* out, double scale, cudaStream_t s);
 // x[i] -= *mean (device scalar)
 template <typename T>
 void launch_sub_scalar(T* x, size_t n, const double* mean, cudaStream_t s);
 // y = (Ty)(a * x + shift), shift from device scalar (nullable)
 template <typename Tx, typename Ty>
 void launch_convert(const Tx* x, Ty* y, size_t n, double a, const double* shift, cudaStream_t s);
-// y = a x + b y (host scalars)
-void launch_axpby(double a, const double* x, double b, double* y, size_t n, cudaStream_t s);
+// y = a x + b y (host scalars, applied in E)
+template <typename E>
+void launch_axpby(double a, const E* x, double b, E* y, size_t n, cudaStream_t s);
 // y = x * (num / *den)  (device scalar den, host num)
-void launch_scale_by_inv(const double* x, double* y, size_t n, const double* den, double num, cudaStream_t s);
+template <typename E>
+void launch_scale_by_inv(const E* x, E* y, size_t n, const double* den, double num, cudaStream_t s);
+// x += a * d  (FP32 d added to FP64 x)
+void launch_add_scaled(double a, const float* d, double* x, size_t n, cudaStream_t s);
 // flag = any non-finite in x (writes 1 into *flag if so; *flag must start 0)
 template <typename T>
 void launch_nonfinite(const T* x, size_t n, int* flag, cudaStream_t s);
@@ -180,16 +185,16 @@ struct BlobSet {
 
 void blobs_setup(BlobSet& b, Dims d, double h, const double* q_in, int n, cudaStream_t s);
 // out (+)= scale * sum_b coef_b lam_b phi_b  (coef nullable = 1);
-// lam, coef FP64 device N-vectors; out field of type T.
-template <typename T>
-void launch_spread(const BlobSet& b, Dims d, const double* lam, const double* coef, double scale, T* out,
+// lam (type L) and coef (FP64) device N-vectors; out field of type T.
+template <typename T, typename L = double>
+void launch_spread(const BlobSet& b, Dims d, const L* lam, const double* coef, double scale, T* out,
                    int accumulate, cudaStream_t s);
 // Spread a constant *cval (device scalar) times scale to all blobs.
 template <typename T>
 void launch_spread_const(const BlobSet& b, Dims d, const double* cval, double scale, T* out, cudaStream_t s);
-// out[b] = scale * (J x)_b  (FP64 output)
-template <typename T>
-void launch_interp(const BlobSet& b, Dims d, const T* x, double scale, double* out, cudaStream_t s);
+// out[b] = scale * (J x)_b  (output N-vector of type O)
+template <typename T, typename O = double>
+void launch_interp(const BlobSet& b, Dims d, const T* x, double scale, O* out, cudaStream_t s);
 
 // ---------------------------------------------------------------- Krylov kernels
 constexpr int kDotGroup = 8;
@@ -197,12 +202,18 @@ constexpr int kDotGroup = 8;
 // gate (nullable device scalar): the kernel does nothing when *gate == 0.
 void launch_multidot(const double* V, size_t ldv, int nvec, const double* w, size_t n, double* partial,
                      cudaStream_t s, const double* gate = nullptr);
+// FP32 basis: V and w 16-byte aligned, ldv % 4 == 0.
+void launch_multidot(const float* V, size_t ldv, int nvec, const float* w, size_t n, double* partial,
+                     cudaStream_t s, const double* gate = nullptr);
 // out[g] = sum_blk partial[g*kRedBlocks + blk]   (g < nvec)
 void launch_reduce_partials(const double* partial, int nvec, double* out, cudaStream_t s,
                             const double* gate = nullptr);
 // w += sign * sum_g coef[g] V[g]; optional partial sums of squares of new w.
 void launch_multi_axpy(double* w, const double* V, size_t ldv, int nvec, const double* coef, double sign,
                        size_t n, double* partial_sq, cudaStream_t s, const double* gate = nullptr);
+// FP32 basis: V and w 16-byte aligned, ldv % 4 == 0.
+void launch_multi_axpy(float* w, const float* V, size_t ldv, int nvec, const double* coef, double sign, size_t n,
+                       double* partial_sq, cudaStream_t s, const double* gate = nullptr);
 // Givens step j on column H[:, j] (ldh = restart + 1): rotations cs/sn,
 // residual vector gvec; writes |gvec[j+1]| to *res.
 void launch_givens(double* H, int ldh, int j, double* cs, double* sn, double* gvec, double* res,

@@ -45,6 +45,7 @@ __device__ __forceinline__ double block_sum_all(double v) {
   return r;
 }
 
+// FP64 vectors: one FMA per element and vector.
 template <int NV>
 __global__ void __launch_bounds__(kRedThreads) k_multidot(const double* __restrict__ V, size_t ldv,
                                                           const double* __restrict__ w, size_t n,
@@ -61,6 +62,40 @@ __global__ void __launch_bounds__(kRedThreads) k_multidot(const double* __restri
 #pragma unroll
   for (int g = 0; g < NV; ++g) {
     const double s = block_sum(acc[g]);
+    if (threadIdx.x == 0) partial[g * kRedBlocks + blockIdx.x] = s;
+  }
+}
+
+// FP32 vectors (16-byte aligned, ldv % 4 == 0): 4-vectors, FP32 products
+// summed per thread in FP32 and across threads in FP64.
+template <int NV>
+__global__ void __launch_bounds__(kRedThreads) k_multidot_f32(const float* __restrict__ V, size_t ldv,
+                                                              const float* __restrict__ w, size_t n,
+                                                              double* __restrict__ partial,
+                                                              const double* __restrict__ gate) {
+  if (gate && *gate == 0.0) return;
+  float acc[NV];
+#pragma unroll
+  for (int g = 0; g < NV; ++g) acc[g] = 0.f;
+  const size_t n4 = n >> 2, stride = (size_t)gridDim.x * blockDim.x;
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  for (size_t i = t; i < n4; i += stride) {
+    const float4 wi = reinterpret_cast<const float4*>(w)[i];
+#pragma unroll
+    for (int g = 0; g < NV; ++g) {
+      const float4 v = reinterpret_cast<const float4*>(V + g * ldv)[i];
+      acc[g] = fmaf(v.x, wi.x, fmaf(v.y, wi.y, fmaf(v.z, wi.z, fmaf(v.w, wi.w, acc[g]))));
+    }
+  }
+  const size_t i = 4 * n4 + t;  // at most 3 tail elements
+  if (i < n) {
+    const float wi = w[i];
+#pragma unroll
+    for (int g = 0; g < NV; ++g) acc[g] = fmaf(V[g * ldv + i], wi, acc[g]);
+  }
+#pragma unroll
+  for (int g = 0; g < NV; ++g) {
+    const double s = block_sum((double)acc[g]);
     if (threadIdx.x == 0) partial[g * kRedBlocks + blockIdx.x] = s;
   }
 }
@@ -96,6 +131,48 @@ __global__ void __launch_bounds__(kRedThreads) k_multi_axpy(double* __restrict__
   if (SQ) {
     sq = block_sum(sq);
     if (threadIdx.x == 0) partial_sq[blockIdx.x] = sq;
+  }
+}
+
+// FP32 vectors (16-byte aligned, ldv % 4 == 0), 4-vectors; the sum of squares
+// is taken per thread in FP32 and across threads in FP64.
+template <int NV, bool SQ>
+__global__ void __launch_bounds__(kRedThreads) k_multi_axpy_f32(float* __restrict__ w, const float* __restrict__ V,
+                                                                size_t ldv, const double* __restrict__ coef,
+                                                                double sign, size_t n,
+                                                                double* __restrict__ partial_sq,
+                                                                const double* __restrict__ gate) {
+  if (gate && *gate == 0.0) return;
+  float c[NV];
+#pragma unroll
+  for (int g = 0; g < NV; ++g) c[g] = (float)(sign * coef[g]);
+  float sq = 0.f;
+  const size_t n4 = n >> 2, stride = (size_t)gridDim.x * blockDim.x;
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  for (size_t i = t; i < n4; i += stride) {
+    float4 wi = reinterpret_cast<const float4*>(w)[i];
+#pragma unroll
+    for (int g = 0; g < NV; ++g) {
+      const float4 v = reinterpret_cast<const float4*>(V + g * ldv)[i];
+      wi.x = fmaf(c[g], v.x, wi.x);
+      wi.y = fmaf(c[g], v.y, wi.y);
+      wi.z = fmaf(c[g], v.z, wi.z);
+      wi.w = fmaf(c[g], v.w, wi.w);
+    }
+    reinterpret_cast<float4*>(w)[i] = wi;
+    if (SQ) sq = fmaf(wi.x, wi.x, fmaf(wi.y, wi.y, fmaf(wi.z, wi.z, fmaf(wi.w, wi.w, sq))));
+  }
+  const size_t i = 4 * n4 + t;
+  if (i < n) {
+    float wi = w[i];
+#pragma unroll
+    for (int g = 0; g < NV; ++g) wi = fmaf(c[g], V[g * ldv + i], wi);
+    w[i] = wi;
+    if (SQ) sq = fmaf(wi, wi, sq);
+  }
+  if (SQ) {
+    const double b = block_sum((double)sq);
+    if (threadIdx.x == 0) partial_sq[blockIdx.x] = b;
   }
 }
 
@@ -283,6 +360,21 @@ void launch_multidot(const double* V, size_t ldv, int nvec, const double* w, siz
   prof_end(P_DOT, s, "multidot", 8.0 * (nvec + 1) * n);
 }
 
+void launch_multidot(const float* V, size_t ldv, int nvec, const float* w, size_t n, double* partial,
+                     cudaStream_t s, const double* gate) {
+  if (nvec < 1 || nvec > kDotGroup) return;
+  if (ldv % 4 != 0 || !aligned16(V) || !aligned16(w)) throw CudaError{cudaErrorMisalignedAddress, "multidot_f32"};
+  prof_begin(P_DOT, s);
+  switch (nvec) {
+#define IBRD_CASE(k) \
+  case k: k_multidot_f32<k><<<kRedBlocks, kRedThreads, 0, s>>>(V, ldv, w, n, partial, gate); break;
+    IBRD_CASE(1) IBRD_CASE(2) IBRD_CASE(3) IBRD_CASE(4) IBRD_CASE(5) IBRD_CASE(6) IBRD_CASE(7) IBRD_CASE(8)
+#undef IBRD_CASE
+    default: return;
+  }
+  prof_end(P_DOT, s, "multidot_f32", 4.0 * (nvec + 1) * n);
+}
+
 void launch_reduce_partials(const double* partial, int nvec, double* out, cudaStream_t s, const double* gate) {
   if (nvec <= 0) return;
   prof_begin(P_REDUCE, s);
@@ -314,6 +406,35 @@ void launch_multi_axpy(double* w, const double* V, size_t ldv, int nvec, const d
     }
   }
   prof_end(P_AXPY, s, "multi_axpy", 8.0 * (nvec + 2) * n);
+}
+
+void launch_multi_axpy(float* w, const float* V, size_t ldv, int nvec, const double* coef, double sign, size_t n,
+                       double* partial_sq, cudaStream_t s, const double* gate) {
+  if (nvec < 1 || nvec > kDotGroup) return;
+  if (ldv % 4 != 0 || !aligned16(V) || !aligned16(w)) throw CudaError{cudaErrorMisalignedAddress, "multi_axpy_f32"};
+  prof_begin(P_AXPY, s);
+  if (partial_sq) {
+    switch (nvec) {
+#define IBRD_CASE(k)                                                                                           \
+  case k:                                                                                                      \
+    k_multi_axpy_f32<k, true><<<kRedBlocks, kRedThreads, 0, s>>>(w, V, ldv, coef, sign, n, partial_sq, gate); \
+    break;
+      IBRD_CASE(1) IBRD_CASE(2) IBRD_CASE(3) IBRD_CASE(4) IBRD_CASE(5) IBRD_CASE(6) IBRD_CASE(7) IBRD_CASE(8)
+#undef IBRD_CASE
+      default: return;
+    }
+  } else {
+    switch (nvec) {
+#define IBRD_CASE(k)                                                                                            \
+  case k:                                                                                                       \
+    k_multi_axpy_f32<k, false><<<kRedBlocks, kRedThreads, 0, s>>>(w, V, ldv, coef, sign, n, nullptr, gate); \
+    break;
+      IBRD_CASE(1) IBRD_CASE(2) IBRD_CASE(3) IBRD_CASE(4) IBRD_CASE(5) IBRD_CASE(6) IBRD_CASE(7) IBRD_CASE(8)
+#undef IBRD_CASE
+      default: return;
+    }
+  }
+  prof_end(P_AXPY, s, "multi_axpy_f32", 4.0 * (nvec + 2) * n);
 }
 
 void launch_givens(double* H, int ldh, int j, double* cs, double* sn, double* gvec, double* res, cudaStream_t s) {
