@@ -287,6 +287,29 @@ const T* coarse_table(ibrd_grid g, double shift) {
   return t;
 }
 
+// Levels l .. L-1 of the hierarchy as the single-CTA coarse V-cycle sees them.
+CoarseLevels small_levels(ibrd_grid g, int l, double shift) {
+  CoarseLevels cl{};
+  cl.n = (int)g->levels.size() - l;
+  int tot = 0;
+  for (int i = 0; i < cl.n; ++i) {
+    const Level& li = g->levels[l + i];
+    const Stencil si = stencil(li.h, g->chi, shift);
+    cl.nx[i] = li.d.nx;
+    cl.ny[i] = li.d.ny;
+    cl.nz[i] = li.d.nz;
+    cl.off[i] = tot;
+    auto lg = [](int v) { return (v & (v - 1)) == 0 ? __builtin_ctz((unsigned)v) : -1; };
+    cl.lgx[i] = lg(li.d.nx);
+    cl.lgy[i] = lg(li.d.ny);
+    cl.diag[i] = si.diag;
+    cl.offd[i] = si.off;
+    tot += (int)li.d.n();
+  }
+  cl.total = tot;
+  return cl;
+}
+
 // One V-cycle on level l for A_l x = b - bshift (bshift nullable). Smoothing
 // sweeps ping-pong between x and the level's scratch field. If part is
 // non-null (finest level only) the last smoothing sweep also writes per-CTA
@@ -305,24 +328,7 @@ int vcycle_level(ibrd_grid g, int l, const T* b, const double* bshift, T* x, boo
   }
   // the coarse end of the hierarchy runs in one CTA out of shared memory
   if (l >= g->small_from) {
-    CoarseLevels cl{};
-    cl.n = (int)g->levels.size() - l;
-    int tot = 0;
-    for (int i = 0; i < cl.n; ++i) {
-      const Level& li = g->levels[l + i];
-      const Stencil si = stencil(li.h, g->chi, shift);
-      cl.nx[i] = li.d.nx;
-      cl.ny[i] = li.d.ny;
-      cl.nz[i] = li.d.nz;
-      cl.off[i] = tot;
-      auto lg = [](int v) { return (v & (v - 1)) == 0 ? __builtin_ctz((unsigned)v) : -1; };
-      cl.lgx[i] = lg(li.d.nx);
-      cl.lgy[i] = lg(li.d.ny);
-      cl.diag[i] = si.diag;
-      cl.offd[i] = si.off;
-      tot += (int)li.d.n();
-    }
-    cl.total = tot;
+    const CoarseLevels cl = small_levels(g, l, shift);
     launch_vcycle_small<T>(cl, b, x, bshift, coarse_table<T>(g, shift), zero, nu1, nu2, g->s);
     return 0;
   }

@@ -394,6 +394,58 @@ __global__ void __launch_bounds__(256) k_resid_restrict(const T* __restrict__ x,
   bc[(K * nyc + J) * nxc + I] = acc * (T)0.125;
 }
 
+// The first red-black sweep from x = 0, FP32, as one 7-point stencil on b:
+// a red cell gets r = (b - shift) / diag (its neighbours are still 0), a black
+// cell ((b - shift) + off * (sum of the r of its 6 red neighbours)) / diag.
+// Same arithmetic as the fused sweep; reads b once and writes x once. Four
+// cells per thread (16-byte rows; nx % 4 == 0, aligned fields), z-march over
+// zc planes with the neighbour planes' r in registers.
+__global__ void __launch_bounds__(256) k_rb_zero_f32v(const float* __restrict__ b, float* __restrict__ x,
+                                                      const double* __restrict__ bshift, int nx, int ny, int nz,
+                                                      int zc, float inv, float off) {
+  const int i4 = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i4 >= (nx >> 2) || j >= ny) return;
+  const int k0 = blockIdx.z * zc;
+  const int k1 = min(k0 + zc, nz);
+  if (k0 >= k1) return;
+  const float sh = bshift ? (float)(*bshift) : 0.f;
+  const int i = 4 * i4;
+  const int im = i == 0 ? nx - 1 : i - 1, ip = i + 4 == nx ? 0 : i + 4;
+  const size_t plane = (size_t)nx * ny;
+  const size_t rj = (size_t)j * nx, rjm = (size_t)(j == 0 ? ny - 1 : j - 1) * nx,
+               rjp = (size_t)(j == ny - 1 ? 0 : j + 1) * nx;
+  auto ldb = [&](size_t o) { return *reinterpret_cast<const float4*>(b + o); };
+  auto red = [&](float4 t) {
+    return make_float4((t.x - sh) * inv, (t.y - sh) * inv, (t.z - sh) * inv, (t.w - sh) * inv);
+  };
+  float4 rm = red(ldb((size_t)(k0 == 0 ? nz - 1 : k0 - 1) * plane + rj + i));
+  float4 b0 = ldb((size_t)k0 * plane + rj + i);
+  float4 r0 = red(b0);
+  for (int k = k0; k < k1; ++k) {
+    const size_t base = (size_t)k * plane;
+    const float4 bp = ldb((size_t)(k == nz - 1 ? 0 : k + 1) * plane + rj + i);
+    const float4 rp = red(bp);
+    const float4 ys = red(ldb(base + rjm + i)), yn = red(ldb(base + rjp + i));
+    const float rl = (b[base + rj + im] - sh) * inv, rr = (b[base + rj + ip] - sh) * inv;
+    const float bc[4] = {b0.x, b0.y, b0.z, b0.w}, rc[4] = {r0.x, r0.y, r0.z, r0.w};
+    const float us[4] = {ys.x, ys.y, ys.z, ys.w}, un[4] = {yn.x, yn.y, yn.z, yn.w};
+    const float zm[4] = {rm.x, rm.y, rm.z, rm.w}, zp[4] = {rp.x, rp.y, rp.z, rp.w};
+    float o[4];
+    const int par = (j + k) & 1;  // parity of element 0 (i is a multiple of 4)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float L = q == 0 ? rl : rc[q - 1], R = q == 3 ? rr : rc[q + 1];
+      const float blk = ((bc[q] - sh) + off * (((L + R) + (us[q] + un[q])) + (zm[q] + zp[q]))) * inv;
+      o[q] = ((q + par) & 1) ? blk : rc[q];
+    }
+    *reinterpret_cast<float4*>(x + base + rj + i) = make_float4(o[0], o[1], o[2], o[3]);
+    rm = r0;
+    b0 = bp;
+    r0 = rp;
+  }
+}
+
 // Thread per coarse cell: adds the trilinear cell-centred interpolation of
 // the coarse correction to its 8 fine children (weights 3/4, 1/4 per axis).
 template <typename T>
@@ -559,14 +611,14 @@ __global__ void __launch_bounds__(256) k_prolong8x2(const T* __restrict__ xc, T*
 }
 
 // The coarse end of a V-cycle in ONE CTA: levels lv.first .. lv.n-1 (at most
-// a few thousand cells) live in shared memory; smoothing, residual
-// restriction, the exact coarsest solve and prolongation run with block-wide
-// barriers between phases. Arithmetic matches the multi-kernel levels.
+// a few thousand cells) live in shared memory (smem_raw, 2 lv.total values);
+// smoothing, residual restriction, the exact coarsest solve and prolongation
+// run with block-wide barriers between phases. Arithmetic matches the
+// multi-kernel levels.
 template <typename T>
-__global__ void __launch_bounds__(1024) k_vcycle_small(CoarseLevels lv, const T* __restrict__ bg, T* __restrict__ xg,
-                                                       const double* __restrict__ bshift, const T* __restrict__ table,
-                                                       int zero, int nu1, int nu2) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ void vcycle_small_body(const CoarseLevels& lv, const T* __restrict__ bg, T* __restrict__ xg,
+                                  const double* __restrict__ bshift, const T* __restrict__ table, int zero, int nu1,
+                                  int nu2, unsigned char* smem_raw) {
   T* X = reinterpret_cast<T*>(smem_raw);
   T* B = X + lv.total;
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -593,20 +645,36 @@ __global__ void __launch_bounds__(1024) k_vcycle_small(CoarseLevels lv, const T*
       k = c / (lv.nx[l] * lv.ny[l]);
     }
   };
+  // one red-black sweep on level l (all sides even): each half-sweep visits
+  // only the cells of its colour, enumerated as (i/2, j, k)
   auto sweep = [&](int l) {
-    const int nx = lv.nx[l], ny = lv.ny[l], nz = lv.nz[l], n = nx * ny * nz;
+    const int nx = lv.nx[l], ny = lv.ny[l], nz = lv.nz[l];
+    const int hx = nx >> 1, nh = hx * ny * nz, plane = nx * ny;
     T* x = X + lv.off[l];
     const T* b = B + lv.off[l];
     const T inv = (T)(1.0 / lv.diag[l]), off = (T)lv.offd[l];
+    const int lx = lv.lgx[l], ly = lv.lgy[l];
+    const bool pow2 = lx >= 1 && ly >= 0;
     for (int colour = 0; colour < 2; ++colour) {
-      for (int c = tid; c < n; c += nt) {
-        int i, j, k;
-        decode(l, c, i, j, k);
-        if (((i + j + k) & 1) != colour) continue;
-        const T s = ((x[c - i + wrap(i - 1, nx)] + x[c - i + wrap(i + 1, nx)]) +
-                     (x[c + (wrap(j - 1, ny) - j) * nx] + x[c + (wrap(j + 1, ny) - j) * nx])) +
-                    (x[c + (wrap(k - 1, nz) - k) * nx * ny] + x[c + (wrap(k + 1, nz) - k) * nx * ny]);
-        x[c] = (b[c] + off * s) * inv;
+      for (int p = tid; p < nh; p += nt) {
+        int ih, j, k;
+        if (pow2) {
+          ih = p & (hx - 1);
+          j = (p >> (lx - 1)) & (ny - 1);
+          k = p >> (lx - 1 + ly);
+        } else {
+          ih = p % hx;
+          j = (p / hx) % ny;
+          k = p / (hx * ny);
+        }
+        const int i = 2 * ih + ((j + k + colour) & 1);
+        const int rowc = k * plane + j * nx;
+        const int c = rowc + i;
+        const int xw = rowc + (i == 0 ? nx - 1 : i - 1), xe = rowc + (i == nx - 1 ? 0 : i + 1);
+        const int ys = c + (j == 0 ? plane - nx : -nx), yn = c + (j == ny - 1 ? nx - plane : nx);
+        const int zd = c + (k == 0 ? plane * (nz - 1) : -plane), zu = c + (k == nz - 1 ? -plane * (nz - 1) : plane);
+        const T sum = ((x[xw] + x[xe]) + (x[ys] + x[yn])) + (x[zd] + x[zu]);
+        x[c] = (b[c] + off * sum) * inv;
       }
       __syncthreads();
     }
@@ -681,6 +749,14 @@ __global__ void __launch_bounds__(1024) k_vcycle_small(CoarseLevels lv, const T*
   for (int c = tid; c < n0; c += nt) xg[c] = X[c];
 }
 
+template <typename T>
+__global__ void __launch_bounds__(1024) k_vcycle_small(CoarseLevels lv, const T* __restrict__ bg, T* __restrict__ xg,
+                                                       const double* __restrict__ bshift, const T* __restrict__ table,
+                                                       int zero, int nu1, int nu2) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  vcycle_small_body<T>(lv, bg, xg, bshift, table, zero, nu1, nu2, smem_raw);
+}
+
 }  // namespace
 
 template <typename T>
@@ -707,6 +783,23 @@ int launch_rb_sweep(const T* xin, T* xout, const T* b, const double* bshift, Dim
                     double* part, int part_cap, cudaStream_t s) {
   const int c = pcls<T>(P_RBGS64, P_RBGS32);
   const T inv = (T)(1.0 / st.diag), off = (T)st.off;
+  if constexpr (sizeof(T) == 4) {
+    // from zero: one stencil pass over b (no partial sums are asked of a first sweep)
+    if (zero && !part && d.nx % 4 == 0 && aligned16(xout) && aligned16(b)) {
+      const int nx4 = d.nx / 4;
+      const int tx = nx4 >= 32 ? 32 : nx4, ty = 256 / tx;
+      const int bx = (nx4 + tx - 1) / tx, by = (d.ny + ty - 1) / ty;
+      int chunks = (152 * 8) / (bx * by);
+      chunks = chunks < 1 ? 1 : chunks;
+      int zc = (d.nz + chunks - 1) / chunks;
+      zc = zc < 2 ? 2 : zc;
+      dim3 g(bx, by, (d.nz + zc - 1) / zc);
+      prof_begin(c, s);
+      k_rb_zero_f32v<<<g, dim3(tx, ty), 0, s>>>(b, xout, bshift, d.nx, d.ny, d.nz, zc, inv, off);
+      prof_end(c, s, "rb_sweep_zero", 8.0 * d.n());
+      return 0;
+    }
+  }
   if (rb_sweep_fused_ok<T>(d) && aligned16(xin) && aligned16(xout) && aligned16(b)) {
     // 64-wide tiles for FP32 (18 vectors per row), 32-wide for FP64
     const bool wide = (sizeof(T) == 4) && (d.nx % 64 == 0);
