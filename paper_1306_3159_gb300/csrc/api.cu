@@ -967,19 +967,21 @@ struct SaddleOp : LinOp<T> {
       T* fx = pfield<T>(g, 3);
       // mean of S U_j = h^-3 sum(U_j) / N_c
       const double ub_scale = ih3 / (double)nc;
-      launch_small_start(rhs, g->U, N, g->sg, m, singular ? sc + S_UB : nullptr, ub_scale, g->s);
+      // the inner basis has the preconditioner's precision T
+      T* U = reinterpret_cast<T*>(g->U);
+      launch_small_start<T>(rhs, U, N, g->sg, m, singular ? sc + S_UB : nullptr, ub_scale, g->s);
       for (int j = 0; j < m; ++j) {
-        launch_spread<T>(g->blobs, g->d, g->U + (size_t)j * N, nullptr, ih3, fs, 0, g->s);
+        launch_spread<T, T>(g->blobs, g->d, U + (size_t)j * N, nullptr, ih3, fs, 0, g->s);
         if (singular)
           vcycle<T>(g, fs, fx, true, shift, o.nu1, o.nu2, sc + S_UB + j, XMean::Report, sc + S_UX + j);
         else
           vcycle<T>(g, fs, fx, true, shift, o.nu1, o.nu2);
-        launch_interp<T>(g->blobs, g->d, fx, 1.0, g->U + (size_t)(j + 1) * N, g->s);
-        launch_small_arnoldi(g->U, N, j, g->Hs, m + 1, g->scs, g->ssn, g->sg, singular ? sc + S_UX + j : nullptr,
+        launch_interp<T, T>(g->blobs, g->d, fx, 1.0, U + (size_t)(j + 1) * N, g->s);
+        launch_small_arnoldi<T>(U, N, j, g->Hs, m + 1, g->scs, g->ssn, g->sg, singular ? sc + S_UX + j : nullptr,
                              singular && j + 1 < m ? sc + S_UB + j + 1 : nullptr, ub_scale, g->s);
         g->inner++;
       }
-      launch_small_finish(g->U, N, m, g->Hs, m + 1, g->sg, lam, singular ? 1 : 0, g->s);
+      launch_small_finish<T>(U, N, m, g->Hs, m + 1, g->sg, lam, singular ? 1 : 0, g->s);
     }
     // step 3: c~ = A~_n^-1 (g~ - zeta S lambda~) from c~*; lambda~ has mean
     // zero, so the right-hand side keeps the mean of g~

@@ -66,11 +66,15 @@ __global__ void __launch_bounds__(256) k_apply_f32v(const float* __restrict__ x,
   const size_t plane = (size_t)nx * ny;
   const size_t rj = (size_t)j * nx, rjm = (size_t)wrap_dec(j, ny) * nx, rjp = (size_t)wrap_inc(j, ny) * nx;
   auto ld4 = [&](size_t o) { return *reinterpret_cast<const float4*>(x + o); };
+  auto kw = [&](int k) { return (size_t)(k >= nz ? k - nz : k) * plane + rj + i; };
   float4 xm = ld4((size_t)wrap_dec(k0, nz) * plane + rj + i);
-  float4 x0 = ld4((size_t)k0 * plane + rj + i);
+  float4 x0 = ld4(kw(k0));
+  // the next plane's centre row is loaded one iteration ahead (two rows in flight)
+  float4 x1 = ld4(kw(k0 + 1));
   for (int k = k0; k < k1; ++k) {
     const size_t base = (size_t)k * plane;
-    const float4 xp = ld4((size_t)wrap_inc(k, nz) * plane + rj + i);
+    const float4 xp = x1;
+    if (k + 1 < k1) x1 = ld4(kw(k + 2));
     const float4 ys = ld4(base + rjm + i), yn = ld4(base + rjp + i);
     const float xl = x[base + rj + im], xr = x[base + rj + ip];
     float4 v;

@@ -228,19 +228,23 @@ void launch_reorth_flag(const double* ww, const double* sq, double eta, double* 
 void launch_sqrt_scalar(const double* src, double* dst, cudaStream_t s);
 
 // Small-vector (length N) GMRES for the approximate Schur complement: one
-// block does the Arnoldi step on U (rows of length n, ldu) with small
-// Hessenberg Hs (ldh = m + 1), including Givens rotations.
-// Step j: w (= U[j+1]) orthogonalized against U[0..j] by MGS, normalized.
+// block does the Arnoldi step on U (rows of length n, type S) with small
+// Hessenberg Hs (FP64, ldh = m + 1), including Givens rotations.
+// Step j: w (= U[j+1]) orthogonalized against U[0..j] by classical
+// Gram-Schmidt with a DGKS second pass, normalized.
 // If wshift is non-null, *wshift is first subtracted from every entry of w;
 // if usum is non-null, *usum = usum_scale * sum(U[j+1]) after normalising.
-void launch_small_arnoldi(double* U, int n, int j, double* Hs, int ldh, double* cs, double* sn,
-                          double* gvec, const double* wshift, double* usum, double usum_scale, cudaStream_t s);
-// U[0] = r / ||r||, gvec = [||r||, 0, ...] (r may alias U[0]); *usum =
-// usum_scale * sum(U[0]) if usum is non-null.
-void launch_small_start(const double* r, double* U0, int n, double* gvec, int m, double* usum, double usum_scale,
+template <typename S>
+void launch_small_arnoldi(S* U, int n, int j, double* Hs, int ldh, double* cs, double* sn, double* gvec,
+                          const double* wshift, double* usum, double usum_scale, cudaStream_t s);
+// U[0] = r / ||r||, gvec = [||r||, 0, ...]; *usum = usum_scale * sum(U[0]) if
+// usum is non-null.
+template <typename S>
+void launch_small_start(const double* r, S* U0, int n, double* gvec, int m, double* usum, double usum_scale,
                         cudaStream_t s);
 // x = U[0..k) y where y = R^{-1} g (solved inside); subtract mean if project.
-void launch_small_finish(const double* U, int n, int k, const double* Hs, int ldh, const double* gvec,
-                         double* x, int project_mean, cudaStream_t s);
+template <typename S>
+void launch_small_finish(const S* U, int n, int k, const double* Hs, int ldh, const double* gvec, double* x,
+                         int project_mean, cudaStream_t s);
 
 }  // namespace ibrd

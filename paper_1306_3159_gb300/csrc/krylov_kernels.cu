@@ -34,17 +34,6 @@ __device__ __forceinline__ double block_sum(double v) {
   return v;
 }
 
-// Block sum broadcast to all threads.
-__device__ __forceinline__ double block_sum_all(double v) {
-  __shared__ double s_res;
-  v = block_sum(v);
-  if (threadIdx.x == 0) s_res = v;
-  __syncthreads();
-  const double r = s_res;
-  __syncthreads();
-  return r;
-}
-
 // FP64 vectors: one FMA per element and vector.
 template <int NV>
 __global__ void __launch_bounds__(kRedThreads) k_multidot(const double* __restrict__ V, size_t ldv,
@@ -235,112 +224,240 @@ __global__ void k_sqrt_scalar(const double* __restrict__ src, double* __restrict
 }
 
 // ---------------------------------------------------------------- small GMRES
+// One CTA; vectors and arithmetic of type S (FP32 in the mixed-precision
+// solves). On GB300 one SM runs FP64 at about 2 FMA per clock with long
+// dependent latencies, so these kernels avoid serial FP64 chains: every
+// reduction is a tree over lanes and warps, and with S = float the small
+// least-squares problem (Givens rotations, back substitution) runs in FP32
+// too; the Hessenberg matrix and residual vector are stored in FP64.
 constexpr int kSmallThreads = 1024;
+constexpr int kSmallMaxBasis = 64;  // m + 1 <= 61 basis vectors
+constexpr int kSmallRegBasis = 8;   // bases up to this size are read with independent loads
 
-__global__ void __launch_bounds__(kSmallThreads) k_small_start(const double* __restrict__ r, double* __restrict__ U0,
-                                                                int n, double* __restrict__ gvec, int m,
+template <typename S>
+__device__ __forceinline__ S warp_sum_t(S v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sums over the block of per-warp partials red[w][v] (v < cnt): warp v adds
+// the 32 partials of value v. Every thread sees out[] afterwards.
+template <typename S>
+__device__ __forceinline__ void finish_sums(int cnt, S (*red)[kSmallMaxBasis + 1], S* out) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  for (int v = wid; v < cnt; v += nw) {
+    S x = lane < nw ? red[lane][v] : (S)0;
+    x = warp_sum_t<S>(x);
+    if (lane == 0) out[v] = x;
+  }
+  __syncthreads();
+}
+
+template <typename S>
+__global__ void __launch_bounds__(kSmallThreads) k_small_start(const double* __restrict__ r, S* __restrict__ U0, int n,
+                                                                double* __restrict__ gvec, int m,
                                                                 double* __restrict__ usum, double usum_scale) {
-  double s = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) s = fma(r[i], r[i], s);
-  const double nrm = sqrt(block_sum_all(s));
-  const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
-  double su = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const double u = r[i] * inv;
+  __shared__ S red[32][kSmallMaxBasis + 1];
+  __shared__ S out[2];
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
+  S ss = 0;
+#pragma unroll 4
+  for (int i = tid; i < n; i += nt) {
+    const S v = (S)r[i];
+    ss += v * v;
+  }
+  ss = warp_sum_t<S>(ss);
+  if (lane == 0) red[wid][0] = ss;
+  finish_sums<S>(1, red, out);
+  const S nrm = sqrt(out[0]);
+  const S inv = nrm > (S)0 ? (S)1 / nrm : (S)0;
+  S su = 0;
+#pragma unroll 4
+  for (int i = tid; i < n; i += nt) {
+    const S u = (S)r[i] * inv;
     U0[i] = u;
     su += u;
   }
-  if (threadIdx.x <= m) gvec[threadIdx.x] = (threadIdx.x == 0) ? nrm : 0.0;
+  if (tid <= m) gvec[tid] = (tid == 0) ? (double)nrm : 0.0;
   if (usum) {
-    su = block_sum_all(su);
-    if (threadIdx.x == 0) *usum = usum_scale * su;
+    su = warp_sum_t<S>(su);
+    if (lane == 0) red[wid][0] = su;
+    finish_sums<S>(1, red, out + 1);
+    if (tid == 0) *usum = usum_scale * (double)out[1];
   }
 }
 
-// Arnoldi step j: w = U[j+1] holds (J A~^-1 S) U[j]; modified Gram-Schmidt
-// against U[0..j], normalise, then one Givens rotation.
-__global__ void __launch_bounds__(kSmallThreads) k_small_arnoldi(double* __restrict__ U, int n, int j,
+// Arnoldi step j: w = U[j+1] holds (J A~^-1 S) U[j]. Classical Gram-Schmidt
+// against U[0..j] (all projections in one pass and one block reduction),
+// repeated once when the norm falls below 1/sqrt(2) of its value before
+// (DGKS test); normalise, then one Givens rotation. Up to kSmallRegBasis
+// basis vectors are read with independent loads, larger bases in a loop.
+template <typename S>
+__global__ void __launch_bounds__(kSmallThreads) k_small_arnoldi(S* __restrict__ U, int n, int j,
                                                                   double* __restrict__ Hs, int ldh,
                                                                   double* __restrict__ cs, double* __restrict__ sn,
                                                                   double* __restrict__ gvec,
                                                                   const double* __restrict__ wshift,
                                                                   double* __restrict__ usum, double usum_scale) {
-  double* w = U + (size_t)(j + 1) * n;
-  double* h = Hs + (size_t)j * ldh;
-  if (wshift) {
-    const double sh = *wshift;
-    for (int t = threadIdx.x; t < n; t += blockDim.x) w[t] -= sh;
+  __shared__ S red[32][kSmallMaxBasis + 1];
+  __shared__ S hv[kSmallMaxBasis + 1], hacc[kSmallMaxBasis + 1], nv[2];
+  S* w = U + (size_t)(j + 1) * n;
+  const int nb = j + 1;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, wid = tid >> 5;
+  const bool reg = nb <= kSmallRegBasis - 1;  // the nb projections and <w, w> fit the register path
+  const S sh = wshift ? (S)*wshift : (S)0;
+  if (wshift)
+    for (int t = tid; t < n; t += nt) w[t] -= sh;
+  for (int v = tid; v < nb; v += nt) hacc[v] = 0;
+  // hv[i] = <U_i, w> for i < nb and, with ww, hv[nb] = <w, w>
+  auto dots = [&](bool ww) {
+    const int cnt = nb + (ww ? 1 : 0);
+    if (reg) {
+      S acc[kSmallRegBasis];
+#pragma unroll
+      for (int v = 0; v < kSmallRegBasis; ++v) acc[v] = 0;
+#pragma unroll 4
+      for (int t = tid; t < n; t += nt) {
+        const S wt = w[t];
+        S u[kSmallRegBasis];
+#pragma unroll
+        for (int v = 0; v < kSmallRegBasis; ++v) u[v] = v < nb ? U[(size_t)v * n + t] : (S)0;
+#pragma unroll
+        for (int v = 0; v < kSmallRegBasis; ++v) acc[v] += (v < nb ? u[v] : (v == nb ? wt : (S)0)) * wt;
+      }
+#pragma unroll
+      for (int v = 0; v < kSmallRegBasis; ++v) {
+        const S sv = warp_sum_t<S>(acc[v]);
+        if (lane == 0 && v < cnt) red[wid][v] = sv;
+      }
+    } else {
+      for (int v = 0; v < cnt; ++v) {
+        S a = 0;
+        const S* u = v < nb ? U + (size_t)v * n : w;
+        for (int t = tid; t < n; t += nt) a += u[t] * w[t];
+        a = warp_sum_t<S>(a);
+        if (lane == 0) red[wid][v] = a;
+      }
+    }
+    finish_sums<S>(cnt, red, hv);
+  };
+  // w -= sum_i hv[i] U_i; nv[0] = <w, w> after
+  auto update = [&]() {
+    S sq = 0;
+#pragma unroll 4
+    for (int t = tid; t < n; t += nt) {
+      S x = w[t];
+      if (reg) {
+        S u[kSmallRegBasis];
+#pragma unroll
+        for (int v = 0; v < kSmallRegBasis; ++v) u[v] = v < nb ? U[(size_t)v * n + t] : (S)0;
+#pragma unroll
+        for (int v = 0; v < kSmallRegBasis; ++v)
+          if (v < nb) x -= hv[v] * u[v];
+      } else {
+        for (int v = 0; v < nb; ++v) x -= hv[v] * U[(size_t)v * n + t];
+      }
+      w[t] = x;
+      sq += x * x;
+    }
+    for (int v = tid; v < nb; v += nt) hacc[v] += hv[v];
+    sq = warp_sum_t<S>(sq);
+    if (lane == 0) red[wid][0] = sq;
+    finish_sums<S>(1, red, nv);
+  };
+  dots(true);
+  const S before = hv[nb];
+  update();
+  if (nv[0] < (S)0.5 * before) {
+    dots(false);
+    update();
   }
-  for (int i = 0; i <= j; ++i) {
-    const double* u = U + (size_t)i * n;
-    double s = 0.0;
-    for (int t = threadIdx.x; t < n; t += blockDim.x) s = fma(u[t], w[t], s);
-    const double hij = block_sum_all(s);
-    for (int t = threadIdx.x; t < n; t += blockDim.x) w[t] -= hij * u[t];
-    if (threadIdx.x == 0) h[i] = hij;
-    __syncthreads();
-  }
-  double s = 0.0;
-  for (int t = threadIdx.x; t < n; t += blockDim.x) s = fma(w[t], w[t], s);
-  const double nrm = sqrt(block_sum_all(s));
-  const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
-  double su = 0.0;
-  for (int t = threadIdx.x; t < n; t += blockDim.x) {
-    w[t] *= inv;
-    su += w[t];
+  const S nrm = sqrt(nv[0]);
+  const S inv = nrm > (S)0 ? (S)1 / nrm : (S)0;
+  S su = 0;
+#pragma unroll 4
+  for (int t = tid; t < n; t += nt) {
+    const S x = w[t] * inv;
+    w[t] = x;
+    su += x;
   }
   if (usum) {
-    su = block_sum_all(su);
-    if (threadIdx.x == 0) *usum = usum_scale * su;
+    su = warp_sum_t<S>(su);
+    if (lane == 0) red[wid][0] = su;
+    finish_sums<S>(1, red, nv + 1);
+    if (tid == 0) *usum = usum_scale * (double)nv[1];
   }
-  if (threadIdx.x == 0) {
-    h[j + 1] = nrm;
+  if (tid == 0) {
+    double* h = Hs + (size_t)j * ldh;
+    S hc[kSmallMaxBasis + 1];
+    for (int i = 0; i < nb; ++i) hc[i] = hacc[i];
+    hc[j + 1] = nrm;
     for (int i = 0; i < j; ++i) {
-      const double tt = cs[i] * h[i] + sn[i] * h[i + 1];
-      h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
-      h[i] = tt;
+      const S c = (S)cs[i], sg = (S)sn[i];
+      const S tt = c * hc[i] + sg * hc[i + 1];
+      hc[i + 1] = -sg * hc[i] + c * hc[i + 1];
+      hc[i] = tt;
     }
-    const double a = h[j], b = h[j + 1];
-    const double r = hypot(a, b);
-    double c = 1.0, sg = 0.0;
-    if (r > 0.0) {
+    const S a = hc[j], b = hc[j + 1];
+    const S r = hypot(a, b);
+    S c = 1, sg = 0;
+    if (r > (S)0) {
       c = a / r;
       sg = b / r;
     }
-    h[j] = r;
-    h[j + 1] = 0.0;
-    cs[j] = c;
-    sn[j] = sg;
-    const double gj = gvec[j];
-    gvec[j + 1] = -sg * gj;
-    gvec[j] = c * gj;
+    hc[j] = r;
+    hc[j + 1] = 0;
+    for (int i = 0; i <= j + 1; ++i) h[i] = (double)hc[i];
+    cs[j] = (double)c;
+    sn[j] = (double)sg;
+    const S gj = (S)gvec[j];
+    gvec[j + 1] = (double)(-sg * gj);
+    gvec[j] = (double)(c * gj);
   }
 }
 
-__global__ void __launch_bounds__(kSmallThreads) k_small_finish(const double* __restrict__ U, int n, int k,
+template <typename S>
+__global__ void __launch_bounds__(kSmallThreads) k_small_finish(const S* __restrict__ U, int n, int k,
                                                                  const double* __restrict__ Hs, int ldh,
                                                                  const double* __restrict__ gvec,
                                                                  double* __restrict__ x, int project_mean) {
-  __shared__ double y[64];
-  if (threadIdx.x == 0) {
+  __shared__ S red[32][kSmallMaxBasis + 1];
+  __shared__ S y[kSmallMaxBasis], out[1];
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
+  if (tid == 0) {
     for (int i = k - 1; i >= 0; --i) {
-      double t = gvec[i];
-      for (int l = i + 1; l < k; ++l) t -= Hs[(size_t)l * ldh + i] * y[l];
-      const double d = Hs[(size_t)i * ldh + i];
-      y[i] = d != 0.0 ? t / d : 0.0;
+      S t = (S)gvec[i];
+      for (int l = i + 1; l < k; ++l) t -= (S)Hs[(size_t)l * ldh + i] * y[l];
+      const S d = (S)Hs[(size_t)i * ldh + i];
+      y[i] = d != (S)0 ? t / d : (S)0;
     }
   }
   __syncthreads();
-  double s = 0.0;
-  for (int t = threadIdx.x; t < n; t += blockDim.x) {
-    double v = 0.0;
-    for (int l = 0; l < k; ++l) v = fma(y[l], U[(size_t)l * n + t], v);
-    x[t] = v;
+  S s = 0;
+  for (int t = tid; t < n; t += nt) {
+    S v = 0;
+    if (k <= kSmallRegBasis) {
+      S u[kSmallRegBasis];
+#pragma unroll
+      for (int l = 0; l < kSmallRegBasis; ++l) u[l] = l < k ? U[(size_t)l * n + t] : (S)0;
+#pragma unroll
+      for (int l = 0; l < kSmallRegBasis; ++l)
+        if (l < k) v += y[l] * u[l];
+    } else {
+      for (int l = 0; l < k; ++l) v += y[l] * U[(size_t)l * n + t];
+    }
+    x[t] = (double)v;
     s += v;
   }
   if (project_mean) {
-    const double mean = block_sum_all(s) / n;
-    for (int t = threadIdx.x; t < n; t += blockDim.x) x[t] -= mean;
+    s = warp_sum_t<S>(s);
+    if (lane == 0) red[wid][0] = s;
+    finish_sums<S>(1, red, out);
+    const double mean = (double)out[0] / n;
+    for (int t = tid; t < n; t += nt) x[t] -= mean;
   }
 }
 
@@ -467,25 +584,40 @@ void launch_sqrt_scalar(const double* src, double* dst, cudaStream_t s) {
   prof_end(P_SMALL, s, "sqrt_scalar");
 }
 
-void launch_small_start(const double* r, double* U0, int n, double* gvec, int m, double* usum, double usum_scale,
+template <typename S>
+void launch_small_start(const double* r, S* U0, int n, double* gvec, int m, double* usum, double usum_scale,
                         cudaStream_t s) {
   prof_begin(P_SMALL, s);
-  k_small_start<<<1, kSmallThreads, 0, s>>>(r, U0, n, gvec, m, usum, usum_scale);
+  k_small_start<S><<<1, kSmallThreads, 0, s>>>(r, U0, n, gvec, m, usum, usum_scale);
   prof_end(P_SMALL, s, "small_start");
 }
 
-void launch_small_arnoldi(double* U, int n, int j, double* Hs, int ldh, double* cs, double* sn, double* gvec,
+template <typename S>
+void launch_small_arnoldi(S* U, int n, int j, double* Hs, int ldh, double* cs, double* sn, double* gvec,
                           const double* wshift, double* usum, double usum_scale, cudaStream_t s) {
+  if (j + 2 > kSmallMaxBasis) throw CudaError{cudaErrorInvalidValue, "small_arnoldi: basis too large"};
   prof_begin(P_SMALL, s);
-  k_small_arnoldi<<<1, kSmallThreads, 0, s>>>(U, n, j, Hs, ldh, cs, sn, gvec, wshift, usum, usum_scale);
+  k_small_arnoldi<S><<<1, kSmallThreads, 0, s>>>(U, n, j, Hs, ldh, cs, sn, gvec, wshift, usum, usum_scale);
   prof_end(P_SMALL, s, "small_arnoldi");
 }
 
-void launch_small_finish(const double* U, int n, int k, const double* Hs, int ldh, const double* gvec, double* x,
+template <typename S>
+void launch_small_finish(const S* U, int n, int k, const double* Hs, int ldh, const double* gvec, double* x,
                          int project_mean, cudaStream_t s) {
+  if (k > kSmallMaxBasis) throw CudaError{cudaErrorInvalidValue, "small_finish: basis too large"};
   prof_begin(P_SMALL, s);
-  k_small_finish<<<1, kSmallThreads, 0, s>>>(U, n, k, Hs, ldh, gvec, x, project_mean);
+  k_small_finish<S><<<1, kSmallThreads, 0, s>>>(U, n, k, Hs, ldh, gvec, x, project_mean);
   prof_end(P_SMALL, s, "small_finish");
 }
+
+#define IBRD_INST(S)                                                                                          \
+  template void launch_small_start<S>(const double*, S*, int, double*, int, double*, double, cudaStream_t);   \
+  template void launch_small_arnoldi<S>(S*, int, int, double*, int, double*, double*, double*, const double*, \
+                                        double*, double, cudaStream_t);                                       \
+  template void launch_small_finish<S>(const S*, int, int, const double*, int, const double*, double*, int,   \
+                                       cudaStream_t);
+IBRD_INST(double)
+IBRD_INST(float)
+#undef IBRD_INST
 
 }  // namespace ibrd

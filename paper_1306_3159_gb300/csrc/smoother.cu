@@ -419,12 +419,16 @@ __global__ void __launch_bounds__(256) k_rb_zero_f32v(const float* __restrict__ 
   auto red = [&](float4 t) {
     return make_float4((t.x - sh) * inv, (t.y - sh) * inv, (t.z - sh) * inv, (t.w - sh) * inv);
   };
+  auto kw = [&](int k) { return (size_t)(k >= nz ? k - nz : k) * plane + rj + i; };
   float4 rm = red(ldb((size_t)(k0 == 0 ? nz - 1 : k0 - 1) * plane + rj + i));
-  float4 b0 = ldb((size_t)k0 * plane + rj + i);
+  float4 b0 = ldb(kw(k0));
   float4 r0 = red(b0);
+  // the next plane's centre row is loaded one iteration ahead (two rows in flight)
+  float4 b1 = ldb(kw(k0 + 1));
   for (int k = k0; k < k1; ++k) {
     const size_t base = (size_t)k * plane;
-    const float4 bp = ldb((size_t)(k == nz - 1 ? 0 : k + 1) * plane + rj + i);
+    const float4 bp = b1;
+    if (k + 1 < k1) b1 = ldb(kw(k + 2));
     const float4 rp = red(bp);
     const float4 ys = red(ldb(base + rjm + i)), yn = red(ldb(base + rjp + i));
     const float rl = (b[base + rj + im] - sh) * inv, rr = (b[base + rj + ip] - sh) * inv;
