@@ -337,12 +337,20 @@ int vcycle_level(ibrd_grid g, int l, const T* b, const double* bshift, T* x, boo
   T* oth = H.y[l];
   bool first = zero;
   int np = 0;
-  if (nu1 == 0 && zero) IBRD_CUDA(cudaMemsetAsync(x, 0, sizeof(T) * lv.d.n(), g->s));
-  for (int sweep = 0; sweep < nu1; ++sweep) {
-    if (launch_rb_sweep<T>(cur, oth, b, bshift, lv.d, st, first, nullptr, 0, g->s) >= 0) std::swap(cur, oth);
-    first = false;
+  if (sizeof(T) == 4 && nu1 == 1 && zero && zero_restrict_ok(lv.d) && lv.d.n() <= (size_t(1) << 18)) {
+    // the single pre-smoothing sweep from zero and the restriction in one
+    // pass (levels up to 64^3 cells: launch latency dominates there; larger
+    // levels run faster as the two streaming kernels)
+    launch_zero_restrict(reinterpret_cast<const float*>(b), bshift, reinterpret_cast<float*>(cur),
+                         reinterpret_cast<float*>(H.b[l + 1]), lv.d, st, g->s);
+  } else {
+    if (nu1 == 0 && zero) IBRD_CUDA(cudaMemsetAsync(x, 0, sizeof(T) * lv.d.n(), g->s));
+    for (int sweep = 0; sweep < nu1; ++sweep) {
+      if (launch_rb_sweep<T>(cur, oth, b, bshift, lv.d, st, first, nullptr, 0, g->s) >= 0) std::swap(cur, oth);
+      first = false;
+    }
+    launch_resid_restrict<T>(cur, b, bshift, H.b[l + 1], lv.d, st, g->s);
   }
-  launch_resid_restrict<T>(cur, b, bshift, H.b[l + 1], lv.d, st, g->s);
   vcycle_level<T>(g, l + 1, H.b[l + 1], nullptr, H.x[l + 1], true, shift, nu1, nu2, nullptr);
   launch_prolong8<T>(H.x[l + 1], cur, lv.d, g->s);
   for (int sweep = 0; sweep < nu2; ++sweep) {
@@ -411,6 +419,8 @@ template <typename E>
 struct LinOp {
   virtual ~LinOp() = default;
   virtual void apply(const E* x, E* y) = 0;
+  // r = b - K x
+  virtual void residual(const E* b, const E* x, E* r) = 0;
   virtual void precond(const E* v, E* z) = 0;
   // everything a preconditioner application depends on besides v and z
   virtual std::string key() const = 0;
@@ -640,8 +650,7 @@ SolveResult fgmres(ibrd_grid g, LinOp<E>& op, const E* b, E* x, size_t n, const 
     IBRD_CUDA(cudaMemsetAsync(x, 0, sizeof(E) * n, g->s));
     IBRD_CUDA(cudaMemcpyAsync(V, b, sizeof(E) * n, cudaMemcpyDeviceToDevice, g->s));
   } else {
-    op.apply(x, V);
-    launch_axpby<E>(1.0, b, -1.0, V, n, g->s);
+    op.residual(b, x, V);
   }
   launch_dot<E>(V, V, n, g->partial, g->scal + S_TMP2, 1.0, g->s);
   launch_sqrt_scalar(g->scal + S_TMP2, g->scal + S_NORM, g->s);
@@ -714,8 +723,7 @@ SolveResult fgmres(ibrd_grid g, LinOp<E>& op, const E* b, E* x, size_t n, const 
       break;
     }
     // true residual
-    op.apply(x, V);
-    launch_axpby<E>(1.0, b, -1.0, V, n, g->s);
+    op.residual(b, x, V);
     launch_dot<E>(V, V, n, g->partial, g->scal + S_TMP2, 1.0, g->s);
     launch_sqrt_scalar(g->scal + S_TMP2, g->scal + S_NORM, g->s);
     beta = std::sqrt(host_scalar(g, S_TMP2));
@@ -765,19 +773,24 @@ SolveResult refine(ibrd_grid g, LinOp<double>& op64, LinOp<float>& op32, const d
     IBRD_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, g->s));
     return R;
   }
-  auto residual = [&]() {
-    op64.apply(x, r);
-    launch_axpby<double>(1.0, b, -1.0, r, n, g->s);
-    launch_dot<double>(r, r, n, g->partial, g->scal + S_TMP2, 1.0, g->s);
-    return std::sqrt(host_scalar(g, S_TMP2));
+  // The FP32 right-hand side of a refinement step is sigma r, sigma a power
+  // of two that brings the expected norm of r near 1 (FP32 squares stay in
+  // range); the step's correction is then divided by sigma.
+  double sigma = 1.0;
+  auto set_sigma = [&](double expect) { sigma = std::ldexp(1.0, -std::ilogb(std::max(expect, 1e-300))); };
+  auto to_f32 = [&](const double* v) {
+    launch_convert_sq(v, g->ir_r32, n, sigma, g->partial, g->scal + S_TMP2, g->s);
+    return std::sqrt(host_scalar(g, S_TMP2)) / sigma;
   };
   double rnorm;
+  set_sigma(bnorm);
   if (zero_guess) {
     IBRD_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, g->s));
-    IBRD_CUDA(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, g->s));
+    to_f32(b);
     rnorm = bnorm;
   } else {
-    rnorm = residual();
+    op64.residual(b, x, r);
+    rnorm = to_f32(r);
   }
   int stalled = 0;
   while (true) {
@@ -797,7 +810,6 @@ SolveResult refine(ibrd_grid g, LinOp<double>& op64, LinOp<float>& op32, const d
       R.st = IBRD_ERR_NOT_CONVERGED;
       break;
     }
-    launch_convert<double, float>(r, g->ir_r32, n, 1.0 / rnorm, nullptr, g->s);
     const double tol_in = std::max(o.inner_tol, 0.5 * o.tol / R.rel);
     hist.scale = R.rel;
     const SolveResult I =
@@ -808,8 +820,10 @@ SolveResult refine(ibrd_grid g, LinOp<double>& op64, LinOp<float>& op32, const d
       R.st = IBRD_ERR_NONFINITE;
       break;
     }
-    launch_add_scaled(rnorm, g->ir_d32, x, n, g->s);
-    const double rn = residual();
+    launch_add_scaled(1.0 / sigma, g->ir_d32, x, n, g->s);
+    op64.residual(b, x, r);
+    set_sigma(rnorm * std::max(I.rel, 1e-7));
+    const double rn = to_f32(r);
     stalled = (rn > 0.5 * rnorm) ? stalled + 1 : 0;
     rnorm = rn;
   }
@@ -878,6 +892,11 @@ struct ReactionOp : LinOp<T> {
     launch_apply_A<T>(x, y, g->d, stencil(g->h, g->chi, g->alpha), g->s);
     launch_spread<T>(g->blobs, g->d, g->nv[0], kappa, inv_h3(g), y, 1, g->s);
   }
+  void residual(const T* b, const T* x, T* r) override {
+    launch_interp<T>(g->blobs, g->d, x, 1.0, g->nv[0], g->s);
+    launch_residual<T>(x, b, r, g->d, stencil(g->h, g->chi, g->alpha), g->s);
+    launch_spread<T>(g->blobs, g->d, g->nv[0], kappa, -inv_h3(g), r, 1, g->s);
+  }
   // n V-cycles of (sigma I - chi L) (Eq. Pinv_Poisson)
   void precond(const T* v, T* z) override { vcycles<T>(g, v, z, true, sigma, o.mg_cycles, o.nu1, o.nu2); }
 };
@@ -904,6 +923,13 @@ struct SaddleOp : LinOp<T> {
     launch_apply_A<T>(x, y, g->d, stencil(g->h, g->chi, g->alpha), g->s);
     launch_spread<T, T>(g->blobs, g->d, x + nc, nullptr, zeta * inv_h3(g), y, 1, g->s);
     launch_interp<T, T>(g->blobs, g->d, x, xi, y + nc, g->s);
+  }
+  void residual(const T* b, const T* x, T* r) override {
+    const size_t nc = g->d.n();
+    launch_residual<T>(x, b, r, g->d, stencil(g->h, g->chi, g->alpha), g->s);
+    launch_spread<T, T>(g->blobs, g->d, x + nc, nullptr, -zeta * inv_h3(g), r, 1, g->s);
+    launch_interp<T, T>(g->blobs, g->d, x, -xi, r + nc, g->s);
+    launch_axpby<T>(1.0, b + nc, 1.0, r + nc, g->blobs.n, g->s);
   }
   // Appendix A, steps 1-5, with A~_n^-1 = n V-cycles and, for the approximate
   // Schur complement, m GMRES iterations on J A~_1^-1 S.

@@ -284,6 +284,27 @@ __global__ void k_scale_by_inv(const E* __restrict__ x, E* __restrict__ y, size_
     y[i] = x[i] * ff;
 }
 
+// y = (float) x * sigma, with the sum of squares of y: FP32 over runs of 8
+// (stride apart), the runs in FP64.
+__global__ void __launch_bounds__(kRedThreads) k_convert_sq(const double* __restrict__ x, float* __restrict__ y,
+                                                            size_t n, float sigma, double* __restrict__ partial) {
+  double acc = 0.0;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  while (i < n) {
+    float run = 0.f;
+#pragma unroll 4
+    for (int r = 0; r < 8 && i < n; ++r, i += stride) {
+      const float v = (float)x[i] * sigma;
+      y[i] = v;
+      run = fmaf(v, v, run);
+    }
+    acc += (double)run;
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
 // x += a * (double) d: FP32 correction added to an FP64 field
 __global__ void k_add_scaled(double a, const float* __restrict__ d, double* __restrict__ x, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
@@ -429,6 +450,14 @@ void launch_scale_by_inv(const E* x, E* y, size_t n, const double* den, double n
   prof_begin(P_VEC, s);
   k_scale_by_inv<E><<<stream_blocks(n, 256), 256, 0, s>>>(x, y, n, den, num);
   prof_end(P_VEC, s, "scale_by_inv", 2.0 * sizeof(E) * n);
+}
+
+void launch_convert_sq(const double* x, float* y, size_t n, double sigma, double* partial, double* out,
+                       cudaStream_t s) {
+  prof_begin(P_VEC, s);
+  k_convert_sq<<<kRedBlocks, kRedThreads, 0, s>>>(x, y, n, (float)sigma, partial);
+  prof_end(P_VEC, s, "convert_sq", 12.0 * n);
+  launch_finalize(partial, kRedBlocks, out, 1.0, s);
 }
 
 void launch_add_scaled(double a, const float* d, double* x, size_t n, cudaStream_t s) {

@@ -106,6 +106,11 @@ void launch_vcycle_small(const CoarseLevels& lv, const T* b, T* x, const double*
 template <typename T>
 void launch_resid_restrict(const T* x, const T* b, const double* bshift, T* bc, Dims d, Stencil st,
                            cudaStream_t s);
+// FP32 pre-smoothing of one sweep from x = 0 fused with the residual
+// restriction: x = sweep(0), bc = mean over 8 children of (b - shift - A x).
+bool zero_restrict_ok(Dims d);
+void launch_zero_restrict(const float* b, const double* bshift, float* x, float* bc, Dims d, Stencil st,
+                          cudaStream_t s);
 // x (fine, dims d) += trilinear cell-centred prolongation of xc (dims d/2).
 template <typename T>
 void launch_prolong8(const T* xc, T* x, Dims d, cudaStream_t s);
@@ -147,6 +152,9 @@ void launch_axpby(double a, const E* x, double b, E* y, size_t n, cudaStream_t s
 // y = x * (num / *den)  (device scalar den, host num)
 template <typename E>
 void launch_scale_by_inv(const E* x, E* y, size_t n, const double* den, double num, cudaStream_t s);
+// y = (float) x * sigma and *out = sum of y^2 (partial: kRedBlocks doubles)
+void launch_convert_sq(const double* x, float* y, size_t n, double sigma, double* partial, double* out,
+                       cudaStream_t s);
 // x += a * d  (FP32 d added to FP64 x)
 void launch_add_scaled(double a, const float* d, double* x, size_t n, cudaStream_t s);
 // flag = any non-finite in x (writes 1 into *flag if so; *flag must start 0)

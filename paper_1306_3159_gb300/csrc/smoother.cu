@@ -450,6 +450,144 @@ __global__ void __launch_bounds__(256) k_rb_zero_f32v(const float* __restrict__ 
   }
 }
 
+// One pre-smoothing sweep from x = 0 followed by the residual restriction,
+// FP32, in one pass: x = first red-black sweep of A x = b - shift (the
+// stencil of k_rb_zero_f32v) and bc = mean over the 8 children of
+// b - shift - A x. A CTA owns a 32 x 8 tile of cells and marches in z over zc
+// planes (zc even, chunks start on even planes). Shared-memory rings hold
+// b - shift and r = (b - shift) / diag on the tile plus a 2-cell halo (4
+// planes) and x on the tile plus a 1-cell halo (3 planes). Step k loads b
+// plane k+2, forms x on plane k+1, then the residual on plane k, writes x and,
+// on odd k, the coarse cells of planes (k-1, k). Needs nx % 32 == 0,
+// ny % 8 == 0, nz even.
+constexpr int kZR_TX = 32, kZR_TY = 8;
+constexpr int kZR_BW = kZR_TX + 4, kZR_BH = kZR_TY + 4;  // b tile with 2-cell halo
+constexpr int kZR_XW = kZR_TX + 2, kZR_XH = kZR_TY + 2;  // x tile with 1-cell halo
+
+__global__ void __launch_bounds__(kZR_TX* kZR_TY) k_zero_restrict_f32(const float* __restrict__ b,
+                                                                      const double* __restrict__ bshift,
+                                                                      float* __restrict__ x, float* __restrict__ bc,
+                                                                      int nx, int ny, int nz, int zc, float inv,
+                                                                      float off, float diag) {
+  constexpr int NT = kZR_TX * kZR_TY;
+  constexpr int NB = kZR_BH * kZR_BW, NX = kZR_XH * kZR_XW;  // 432 and 340: at most 2 per thread
+  static_assert(NB <= 2 * NT && NX <= 2 * NT, "two ring entries per thread");
+  __shared__ float BS[4][NB];
+  __shared__ float RB[4][NB];
+  __shared__ float XS[3][NX];
+  __shared__ float RS[kZR_TY][kZR_TX];
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kZR_TX + tx;
+  const int x0 = blockIdx.x * kZR_TX, y0 = blockIdx.y * kZR_TY;
+  const int k0 = blockIdx.z * zc;
+  const int k1 = min(k0 + zc, nz);
+  if (k0 >= k1) return;
+  const float sh = bshift ? (float)(*bshift) : 0.f;
+  const size_t plane = (size_t)nx * ny;
+  auto wz = [&](int p) { return p < 0 ? p + nz : (p >= nz ? p - nz : p); };
+  // ring slots follow the unwrapped plane index (k0 - 2 <= p <= k1 + 1), so
+  // consecutive planes never share a slot at the periodic seam
+  auto xslot = [](int p) {
+    const int m = p % 3;
+    return m < 0 ? m + 3 : m;
+  };
+  // this thread's b ring entries (tile + 2-cell halo, periodic): in-plane offsets
+  int boff[2];
+  bool bval[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int e = tid + q * NT;
+    bval[q] = e < NB;
+    const int row = e / kZR_BW, col = e - row * kZR_BW;
+    boff[q] = bval[q] ? wrap(y0 - 2 + row, ny) * nx + wrap(x0 - 2 + col, nx) : 0;
+  }
+  // this thread's x ring entries (tile + 1-cell halo): ring index of the
+  // cell in the b tile, and the in-plane parity
+  int xr[2], xpar[2];
+  bool xval[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int e = tid + q * NT;
+    xval[q] = e < NX;
+    const int row = e / kZR_XW, col = e - row * kZR_XW;
+    xr[q] = (row + 1) * kZR_BW + col + 1;
+    xpar[q] = ((x0 - 1 + col) + (y0 - 1 + row)) & 1;  // the even-period wrap keeps parity
+  }
+  float pre[2];
+  auto fetch_b = [&](int p) {
+    const float* bp = b + (size_t)wz(p) * plane;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) pre[q] = bval[q] ? bp[boff[q]] : 0.f;
+  };
+  auto store_b = [&](int p) {
+    const int sl = p & 3;
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+      if (bval[q]) {
+        const float v = pre[q] - sh;
+        BS[sl][tid + q * NT] = v;
+        RB[sl][tid + q * NT] = v * inv;
+      }
+  };
+  // x on plane p: red cells r, black cells one update from their red
+  // neighbours (same expression as the other sweep kernels)
+  auto comp_x = [&](int p) {
+    const int sl = p & 3, slm = (p + 3) & 3, slp = (p + 1) & 3, xs = xslot(p);
+    const int pp = wz(p) & 1;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      if (!xval[q]) continue;
+      const int o = xr[q];
+      float v;
+      if (((xpar[q] + pp) & 1) == 0) {
+        v = RB[sl][o];
+      } else {
+        const float sum = ((RB[sl][o - 1] + RB[sl][o + 1]) + (RB[sl][o - kZR_BW] + RB[sl][o + kZR_BW])) +
+                          (RB[slm][o] + RB[slp][o]);
+        v = (BS[sl][o] + off * sum) * inv;
+      }
+      XS[xs][tid + q * NT] = v;
+    }
+  };
+  // prologue: b planes k0 - 2 .. k0 + 1 and x planes k0 - 1, k0
+  for (int p = k0 - 2; p <= k0 + 1; ++p) {
+    fetch_b(p);
+    store_b(p);
+  }
+  fetch_b(k0 + 2);  // in flight during the prologue's x planes
+  __syncthreads();
+  comp_x(k0 - 1);
+  comp_x(k0);
+  __syncthreads();  // b plane k0 - 2 (read above) shares its slot with plane k0 + 2
+  float acc = 0.f;  // coarse-cell sum over the even plane (threads with even tx, ty)
+  const int c = (ty + 1) * kZR_XW + tx + 1;  // this thread's tile cell in the x ring
+  for (int k = k0; k < k1; ++k) {
+    store_b(k + 2);
+    if (k + 3 <= k1 + 1) fetch_b(k + 3);  // next plane's b in flight during this step
+    __syncthreads();
+    comp_x(k + 1);
+    __syncthreads();
+    const int sm = xslot(k - 1), s0 = xslot(k), sp = xslot(k + 1);
+    const float xc = XS[s0][c];
+    const float sum = ((XS[s0][c - 1] + XS[s0][c + 1]) + (XS[s0][c - kZR_XW] + XS[s0][c + kZR_XW])) +
+                      (XS[sm][c] + XS[sp][c]);
+    const float res = BS[k & 3][(ty + 2) * kZR_BW + tx + 2] - (diag * xc - off * sum);
+    x[(size_t)k * plane + (size_t)(y0 + ty) * nx + x0 + tx] = xc;
+    // 2 x 2 in-plane sum: x pairs are neighbouring lanes, y pairs neighbouring warps
+    const float px = res + __shfl_xor_sync(0xffffffffu, res, 1);
+    RS[ty][tx] = px;
+    __syncthreads();
+    if (((tx | ty) & 1) == 0) {
+      const float q = RS[ty][tx] + RS[ty + 1][tx];
+      if ((k & 1) == 0) {
+        acc = q;
+      } else {
+        const int nxc = nx >> 1, nyc = ny >> 1;
+        bc[((size_t)(k >> 1) * nyc + ((y0 + ty) >> 1)) * nxc + ((x0 + tx) >> 1)] = (acc + q) * 0.125f;
+      }
+    }
+  }
+}
+
 // Thread per coarse cell: adds the trilinear cell-centred interpolation of
 // the coarse correction to its 8 fine children (weights 3/4, 1/4 per axis).
 template <typename T>
@@ -875,6 +1013,25 @@ void launch_resid_restrict(const T* x, const T* b, const double* bshift, T* bc, 
   prof_begin(c, s);
   k_resid_restrict<T><<<g, blk, 0, s>>>(x, b, bshift, bc, d.nx, d.ny, d.nz, (T)st.diag, (T)st.off);
   prof_end(c, s, "resid_restrict", 2.125 * sizeof(T) * d.n());
+}
+
+bool zero_restrict_ok(Dims d) { return d.nx % kZR_TX == 0 && d.ny % kZR_TY == 0 && d.nz % 2 == 0 && d.nz >= 4; }
+
+void launch_zero_restrict(const float* b, const double* bshift, float* x, float* bc, Dims d, Stencil st,
+                          cudaStream_t s) {
+  const int bx = d.nx / kZR_TX, by = d.ny / kZR_TY;
+  // about one wave of 8 resident CTAs per SM; chunks of an even number of planes
+  int chunks = (152 * 8) / (bx * by);
+  chunks = chunks < 1 ? 1 : chunks;
+  int zc = (d.nz + chunks - 1) / chunks;
+  zc += zc & 1;
+  zc = zc < 2 ? 2 : zc;
+  dim3 g(bx, by, (d.nz + zc - 1) / zc);
+  prof_begin(P_RBGS32, s);
+  k_zero_restrict_f32<<<g, dim3(kZR_TX, kZR_TY), 0, s>>>(b, bshift, x, bc, d.nx, d.ny, d.nz, zc,
+                                                          (float)(1.0 / st.diag), (float)st.off, (float)st.diag);
+  // one read of b, one write of x and of the coarse right-hand side
+  prof_end(P_RBGS32, s, "zero_restrict", 8.0 * d.n() + 0.5 * d.n());
 }
 
 template <typename T>
