@@ -172,11 +172,20 @@ __global__ void __launch_bounds__(kRedThreads) k_sum_partial(const T* __restrict
 // (stride apart) and the runs in FP64.
 template <typename E>
 __global__ void __launch_bounds__(kRedThreads) k_dot_partial(const E* __restrict__ x, const E* __restrict__ y,
-                                                             size_t n, double* __restrict__ partial) {
+                                                             size_t n, double* __restrict__ partial, int vec) {
   double acc = 0.0;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if constexpr (sizeof(E) == 4) {
+    if (vec) {
+      // 16-byte aligned: 4-vectors, FP32 sums of one vector each
+      const size_t n4 = n >> 2, t = i;
+      for (size_t v = t; v < n4; v += stride) {
+        const float4 a = reinterpret_cast<const float4*>(x)[v], b = reinterpret_cast<const float4*>(y)[v];
+        acc += (double)fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, a.w * b.w)));
+      }
+      i = 4 * n4 + t;
+    }
     for (; i + 3 * stride < n; i += 4 * stride) {
       const float r = fmaf(x[i], y[i], fmaf(x[i + stride], y[i + stride],
                                             fmaf(x[i + 2 * stride], y[i + 2 * stride],
@@ -250,6 +259,55 @@ __global__ void k_sub_scalar(T* __restrict__ x, size_t n, const double* __restri
     x[i] -= v;
 }
 
+// FP32 to FP32 with 16-byte aligned fields: 4-vectors.
+__global__ void k_convert_f32v(const float* __restrict__ x, float* __restrict__ y, size_t n, float a,
+                               const double* __restrict__ shift) {
+  const float sh = shift ? (float)*shift : 0.f;
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
+  const size_t n4 = n >> 2;
+  for (size_t i = t; i < n4; i += stride) {
+    float4 v = reinterpret_cast<const float4*>(x)[i];
+    v.x = a * v.x + sh;
+    v.y = a * v.y + sh;
+    v.z = a * v.z + sh;
+    v.w = a * v.w + sh;
+    reinterpret_cast<float4*>(y)[i] = v;
+  }
+  for (size_t i = 4 * n4 + t; i < n; i += stride) y[i] = a * x[i] + sh;
+}
+
+// FP32 copy with sums (both equal to the sum of x), 16-byte aligned fields:
+// 4-vectors summed in FP32 over runs of 2 vectors, the runs in FP64.
+__global__ void __launch_bounds__(kRedThreads) k_copy_sum_f32v(const float* __restrict__ x, float* __restrict__ y,
+                                                               size_t n, double* __restrict__ pin,
+                                                               double* __restrict__ pout) {
+  double acc = 0.0;
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
+  const size_t n4 = n >> 2;
+  size_t i = t;
+  for (; i + stride < n4; i += 2 * stride) {
+    const float4 a = reinterpret_cast<const float4*>(x)[i];
+    const float4 b = reinterpret_cast<const float4*>(x)[i + stride];
+    reinterpret_cast<float4*>(y)[i] = a;
+    reinterpret_cast<float4*>(y)[i + stride] = b;
+    acc += (double)(((a.x + a.y) + (a.z + a.w)) + ((b.x + b.y) + (b.z + b.w)));
+  }
+  for (; i < n4; i += stride) {
+    const float4 a = reinterpret_cast<const float4*>(x)[i];
+    reinterpret_cast<float4*>(y)[i] = a;
+    acc += (double)((a.x + a.y) + (a.z + a.w));
+  }
+  for (size_t k = 4 * n4 + t; k < n; k += stride) {
+    y[k] = x[k];
+    acc += (double)x[k];
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) {
+    pin[blockIdx.x] = acc;
+    pout[blockIdx.x] = acc;
+  }
+}
+
 template <typename Tx, typename Ty>
 __global__ void k_convert(const Tx* __restrict__ x, Ty* __restrict__ y, size_t n, double a,
                           const double* __restrict__ shift) {
@@ -267,21 +325,54 @@ __global__ void k_convert(const Tx* __restrict__ x, Ty* __restrict__ y, size_t n
   }
 }
 
+// FP32 fields in 4-vectors when both are 16-byte aligned (vec), the last
+// n % 4 entries one by one.
 template <typename E>
-__global__ void k_axpby(E a, const E* __restrict__ x, E b, E* __restrict__ y, size_t n) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    y[i] = (b == (E)0) ? a * x[i] : fma(a, x[i], b * y[i]);
+__global__ void k_axpby(E a, const E* __restrict__ x, E b, E* __restrict__ y, size_t n, int vec) {
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
+  size_t i0 = 0;
+  if constexpr (sizeof(E) == 4) {
+    if (vec) {
+      const size_t n4 = n >> 2;
+      for (size_t i = t; i < n4; i += stride) {
+        const float4 xv = reinterpret_cast<const float4*>(x)[i];
+        float4 yv = b == 0.f ? make_float4(0.f, 0.f, 0.f, 0.f) : reinterpret_cast<const float4*>(y)[i];
+        yv.x = b == 0.f ? a * xv.x : fmaf(a, xv.x, b * yv.x);
+        yv.y = b == 0.f ? a * xv.y : fmaf(a, xv.y, b * yv.y);
+        yv.z = b == 0.f ? a * xv.z : fmaf(a, xv.z, b * yv.z);
+        yv.w = b == 0.f ? a * xv.w : fmaf(a, xv.w, b * yv.w);
+        reinterpret_cast<float4*>(y)[i] = yv;
+      }
+      i0 = 4 * n4;
+    }
+  }
+  for (size_t i = i0 + t; i < n; i += stride) y[i] = (b == (E)0) ? a * x[i] : fma(a, x[i], b * y[i]);
 }
 
 template <typename E>
 __global__ void k_scale_by_inv(const E* __restrict__ x, E* __restrict__ y, size_t n, const double* __restrict__ den,
-                               double num) {
+                               double num, int vec) {
   __shared__ E f;
   if (threadIdx.x == 0) f = (E)(num / *den);
   __syncthreads();
   const E ff = f;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    y[i] = x[i] * ff;
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
+  size_t i0 = 0;
+  if constexpr (sizeof(E) == 4) {
+    if (vec) {
+      const size_t n4 = n >> 2;
+      for (size_t i = t; i < n4; i += stride) {
+        float4 v = reinterpret_cast<const float4*>(x)[i];
+        v.x *= ff;
+        v.y *= ff;
+        v.z *= ff;
+        v.w *= ff;
+        reinterpret_cast<float4*>(y)[i] = v;
+      }
+      i0 = 4 * n4;
+    }
+  }
+  for (size_t i = i0 + t; i < n; i += stride) y[i] = x[i] * ff;
 }
 
 // y = (float) x * sigma, with the sum of squares of y: FP32 over runs of 8
@@ -399,7 +490,14 @@ template <typename X, typename T>
 void launch_convert_sum(const X* x, T* y, size_t n, double* partial, double* out_in, double* out_out,
                         cudaStream_t s) {
   prof_begin(P_VEC, s);
-  k_convert_sum<X, T><<<kRedBlocks, kRedThreads, 0, s>>>(x, y, n, partial, partial + kRedBlocks);
+  if constexpr (sizeof(X) == 4 && sizeof(T) == 4) {
+    if (aligned16(x) && aligned16(y))
+      k_copy_sum_f32v<<<kRedBlocks, kRedThreads, 0, s>>>(x, y, n, partial, partial + kRedBlocks);
+    else
+      k_convert_sum<X, T><<<kRedBlocks, kRedThreads, 0, s>>>(x, y, n, partial, partial + kRedBlocks);
+  } else {
+    k_convert_sum<X, T><<<kRedBlocks, kRedThreads, 0, s>>>(x, y, n, partial, partial + kRedBlocks);
+  }
   prof_end(P_VEC, s, "convert_sum", (double)(sizeof(X) + sizeof(T)) * n);
   launch_finalize(partial, kRedBlocks, out_in, 1.0, s);
   launch_finalize(partial + kRedBlocks, kRedBlocks, out_out, 1.0, s);
@@ -417,7 +515,7 @@ void launch_nvec_affine(const double* in, double* out, int n, double a, const do
 template <typename E>
 void launch_dot(const E* x, const E* y, size_t n, double* partial, double* out, double scale, cudaStream_t s) {
   prof_begin(P_DOT, s);
-  k_dot_partial<E><<<kRedBlocks, kRedThreads, 0, s>>>(x, y, n, partial);
+  k_dot_partial<E><<<kRedBlocks, kRedThreads, 0, s>>>(x, y, n, partial, aligned16(x) && aligned16(y));
   prof_end(P_DOT, s, "dot_partial", 2.0 * sizeof(E) * n);
   prof_begin(P_REDUCE, s);
   k_finalize<<<1, kRedThreads, 0, s>>>(partial, kRedBlocks, out, scale);
@@ -434,21 +532,31 @@ void launch_sub_scalar(T* x, size_t n, const double* mean, cudaStream_t s) {
 template <typename Tx, typename Ty>
 void launch_convert(const Tx* x, Ty* y, size_t n, double a, const double* shift, cudaStream_t s) {
   prof_begin(P_VEC, s);
-  k_convert<Tx, Ty><<<stream_blocks(n, 256), 256, 0, s>>>(x, y, n, a, shift);
+  bool done = false;
+  if constexpr (sizeof(Tx) == 4 && sizeof(Ty) == 4) {
+    if (aligned16(x) && aligned16(y)) {
+      k_convert_f32v<<<stream_blocks(n / 4 + 1, 256), 256, 0, s>>>(x, y, n, (float)a, shift);
+      done = true;
+    }
+  }
+  if (!done) k_convert<Tx, Ty><<<stream_blocks(n, 256), 256, 0, s>>>(x, y, n, a, shift);
   prof_end(P_VEC, s, "convert", (double)(sizeof(Tx) + sizeof(Ty)) * n);
 }
 
 template <typename E>
 void launch_axpby(double a, const E* x, double b, E* y, size_t n, cudaStream_t s) {
   prof_begin(P_VEC, s);
-  k_axpby<E><<<stream_blocks(n, 256), 256, 0, s>>>((E)a, x, (E)b, y, n);
+  const int vec = aligned16(x) && aligned16(y);
+  k_axpby<E><<<stream_blocks(vec && sizeof(E) == 4 ? n / 4 + 1 : n, 256), 256, 0, s>>>((E)a, x, (E)b, y, n, vec);
   prof_end(P_VEC, s, "axpby", (b == 0.0 ? 2.0 : 3.0) * sizeof(E) * n);
 }
 
 template <typename E>
 void launch_scale_by_inv(const E* x, E* y, size_t n, const double* den, double num, cudaStream_t s) {
   prof_begin(P_VEC, s);
-  k_scale_by_inv<E><<<stream_blocks(n, 256), 256, 0, s>>>(x, y, n, den, num);
+  const int vec = aligned16(x) && aligned16(y);
+  k_scale_by_inv<E><<<stream_blocks(vec && sizeof(E) == 4 ? n / 4 + 1 : n, 256), 256, 0, s>>>(x, y, n, den, num,
+                                                                                               vec);
   prof_end(P_VEC, s, "scale_by_inv", 2.0 * sizeof(E) * n);
 }
 

@@ -632,7 +632,7 @@ __global__ void __launch_bounds__(256) k_prolong8(const T* __restrict__ xc, T* _
 // Two coarse cells (I, I+1) per thread: the fine x range 2I-1 .. 2I+4 of each
 // row is one aligned 4-vector plus two scalars. Needs nx % 4 == 0.
 template <typename T>
-__global__ void __launch_bounds__(256) k_resid_restrict2(const T* __restrict__ x, const T* __restrict__ b,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 3) k_resid_restrict2(const T* __restrict__ x, const T* __restrict__ b,
                                                          const double* __restrict__ bshift, T* __restrict__ bc,
                                                          int nx, int ny, int nz, T diag, T off) {
   const int nxc = nx >> 1, nyc = ny >> 1, nzc = nz >> 1;
@@ -831,21 +831,26 @@ __device__ void vcycle_small_body(const CoarseLevels& lv, const T* __restrict__ 
     const T* b = B + lv.off[l];
     T* bc = B + lv.off[l + 1];
     const T diag = (T)lv.diag[l], off = (T)lv.offd[l];
-    for (int C = tid; C < nc; C += nt) {
-      int I, J, K;
-      decode(l + 1, C, I, J, K);
-      T acc = 0;
-      for (int dz = 0; dz < 2; ++dz)
-        for (int dy = 0; dy < 2; ++dy)
-          for (int dx = 0; dx < 2; ++dx) {
-            const int i = 2 * I + dx, j = 2 * J + dy, k = 2 * K + dz;
-            const int c = (k * ny + j) * nx + i;
-            const T s = ((x[c - i + wrap(i - 1, nx)] + x[c - i + wrap(i + 1, nx)]) +
-                         (x[c + (wrap(j - 1, ny) - j) * nx] + x[c + (wrap(j + 1, ny) - j) * nx])) +
-                        (x[c + (wrap(k - 1, nz) - k) * nx * ny] + x[c + (wrap(k + 1, nz) - k) * nx * ny]);
-            acc += b[c] - (diag * x[c] - off * s);
-          }
-      bc[C] = acc * (T)0.125;
+    // one child per thread: entry e = 8 C + (dz, dy, dx) bits, so the 8
+    // children of a coarse cell sit in 8 neighbouring lanes and are summed
+    // by shuffles (the loop bound is a multiple of 32 so warps stay whole)
+    const int nf = 8 * nc, nround = (nf + 31) & ~31;
+    for (int e = tid; e < nround; e += nt) {
+      T r = 0;
+      if (e < nf) {
+        int I, J, K;
+        decode(l + 1, e >> 3, I, J, K);
+        const int i = 2 * I + (e & 1), j = 2 * J + ((e >> 1) & 1), k = 2 * K + (e >> 2 & 1);
+        const int c = (k * ny + j) * nx + i;
+        const T s = ((x[c - i + wrap(i - 1, nx)] + x[c - i + wrap(i + 1, nx)]) +
+                     (x[c + (wrap(j - 1, ny) - j) * nx] + x[c + (wrap(j + 1, ny) - j) * nx])) +
+                    (x[c + (wrap(k - 1, nz) - k) * nx * ny] + x[c + (wrap(k + 1, nz) - k) * nx * ny]);
+        r = b[c] - (diag * x[c] - off * s);
+      }
+      r += __shfl_xor_sync(0xffffffffu, r, 1);
+      r += __shfl_xor_sync(0xffffffffu, r, 2);
+      r += __shfl_xor_sync(0xffffffffu, r, 4);
+      if (e < nf && (e & 7) == 0) bc[e >> 3] = r * (T)0.125;
     }
     __syncthreads();
   }
