@@ -52,7 +52,7 @@ typedef enum {
 } ibrd_status;
 
 enum { IBRD_PESKIN4 = 4, IBRD_PESKIN3 = 3 };          /* kernel width w */
-enum { IBRD_FP64 = 0, IBRD_MIXED_FP32 = 1 };          /* precision */
+enum { IBRD_FP64 = 0, IBRD_MIXED_FP32 = 1, IBRD_MIXED_REFINE = 2 };  /* precision */
 enum { IBRD_PRECOND_SCHUR = 0, IBRD_PRECOND_DIAG = 1 }; /* saddle preconditioner */
 
 /* Solver options. ibrd_default_opts fills the defaults noted here. */
@@ -69,10 +69,15 @@ typedef struct {
   double xi;         /* scaling xi; <= 0 selects zeta / h^3 (Eq. saddle_point) */
   int nu1, nu2;      /* red-black Gauss-Seidel sweeps before/after (2, 2) */
   int precision;     /* IBRD_FP64: FGMRES on FP64 vectors with FP64 V-cycles.
-                        IBRD_MIXED_FP32: iterative refinement, each step an
-                        FP32 FGMRES solve (FP32 vectors, V-cycles, spreading)
-                        of K d = r for the FP64 residual r = b - K x, then
-                        x += d in FP64; tol applies to the FP64 residual.
+                        IBRD_MIXED_FP32: FGMRES on FP64 vectors (FP64
+                        operator, residual, Arnoldi, dot products and the
+                        inner Schur update) preconditioned by FP32 V-cycles
+                        and FP32 spreading/interpolation.
+                        IBRD_MIXED_REFINE: iterative refinement, each step an
+                        FP32 FGMRES solve (FP32 vectors, operator, V-cycles,
+                        spreading, inner Schur GMRES) of K d = r for the FP64
+                        residual r = b - K x, then x += d in FP64.
+                        Every mode stops on the FP64 true residual.
                         -1 = the handle's */
   int use_guess;     /* 1: c (and lambda) hold an initial guess; 0: start at 0 */
   double reorth_eta; /* classical Gram-Schmidt takes a second pass when the
@@ -82,7 +87,7 @@ typedef struct {
   int graphs;        /* 1 (default): replay each preconditioner application
                         from a captured CUDA graph after its first use; 0: launch
                         every kernel directly */
-  double inner_tol;  /* IBRD_MIXED_FP32: relative residual each FP32 FGMRES
+  double inner_tol;  /* IBRD_MIXED_REFINE: relative residual each FP32 FGMRES
                         solve aims for, unless less is needed to reach tol
                         (1e-4; the FP32 rounding floor of the operator is
                         near 1e-6 on the grids of Sec. IV) */
@@ -107,7 +112,7 @@ typedef struct {
   double* residual_history;
   int history_len;
   int history_cap;
-  int refinements;     /* IBRD_MIXED_FP32: refinement steps (FP32 solves) */
+  int refinements;     /* IBRD_MIXED_REFINE: refinement steps (FP32 solves) */
 } ibrd_solve_info;
 
 /* Fill *opts with the defaults listed in ibrd_solve_opts. */

@@ -12,7 +12,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libibrd.so")
 
 IBRD_PESKIN4, IBRD_PESKIN3 = 4, 3
-IBRD_FP64, IBRD_MIXED_FP32 = 0, 1
+IBRD_FP64, IBRD_MIXED_FP32, IBRD_MIXED_REFINE = 0, 1, 2
 IBRD_PRECOND_SCHUR, IBRD_PRECOND_DIAG = 0, 1
 
 STATUS = {0: "IBRD_OK", 1: "IBRD_ERR_ARG", 2: "IBRD_ERR_CUDA", 3: "IBRD_ERR_OOM", 4: "IBRD_ERR_NOT_CONVERGED",

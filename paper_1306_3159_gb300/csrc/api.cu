@@ -13,6 +13,7 @@
 #include <map>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <utility>
 #include <vector>
 
@@ -874,9 +875,10 @@ void ensure_nvec(ibrd_grid g, int m) {
 
 // ---------------------------------------------------------------- operators
 // B c = alpha c - chi L c + S (kappa * J c)  (Eq. unsteady_system / steady_state)
-// on fields of type T; the preconditioner is V-cycles in T.
-template <typename T>
-struct ReactionOp : LinOp<T> {
+// on Krylov vectors of type E; the preconditioner is V-cycles in T (FP32
+// V-cycles inside FP64 FGMRES convert on the way in and out).
+template <typename T, typename E = T>
+struct ReactionOp : LinOp<E> {
   ibrd_grid g;
   const double* kappa;
   double sigma;
@@ -884,27 +886,39 @@ struct ReactionOp : LinOp<T> {
   ReactionOp(ibrd_grid g_, const double* k_, double sg, const ibrd_solve_opts& o_) : g(g_), kappa(k_), sigma(sg), o(o_) {}
   std::string key() const override {
     char buf[160];
-    std::snprintf(buf, sizeof buf, "reaction|%zu|%d|%d|%d|%.17g", sizeof(T), o.mg_cycles, o.nu1, o.nu2, sigma);
+    std::snprintf(buf, sizeof buf, "reaction|%zu|%zu|%d|%d|%d|%.17g", sizeof(T), sizeof(E), o.mg_cycles, o.nu1,
+                  o.nu2, sigma);
     return buf;
   }
-  void apply(const T* x, T* y) override {
-    launch_interp<T>(g->blobs, g->d, x, 1.0, g->nv[0], g->s);
-    launch_apply_A<T>(x, y, g->d, stencil(g->h, g->chi, g->alpha), g->s);
-    launch_spread<T>(g->blobs, g->d, g->nv[0], kappa, inv_h3(g), y, 1, g->s);
+  void apply(const E* x, E* y) override {
+    launch_interp<E>(g->blobs, g->d, x, 1.0, g->nv[0], g->s);
+    launch_apply_A<E>(x, y, g->d, stencil(g->h, g->chi, g->alpha), g->s);
+    launch_spread<E>(g->blobs, g->d, g->nv[0], kappa, inv_h3(g), y, 1, g->s);
   }
-  void residual(const T* b, const T* x, T* r) override {
-    launch_interp<T>(g->blobs, g->d, x, 1.0, g->nv[0], g->s);
-    launch_residual<T>(x, b, r, g->d, stencil(g->h, g->chi, g->alpha), g->s);
-    launch_spread<T>(g->blobs, g->d, g->nv[0], kappa, -inv_h3(g), r, 1, g->s);
+  void residual(const E* b, const E* x, E* r) override {
+    launch_interp<E>(g->blobs, g->d, x, 1.0, g->nv[0], g->s);
+    launch_residual<E>(x, b, r, g->d, stencil(g->h, g->chi, g->alpha), g->s);
+    launch_spread<E>(g->blobs, g->d, g->nv[0], kappa, -inv_h3(g), r, 1, g->s);
   }
   // n V-cycles of (sigma I - chi L) (Eq. Pinv_Poisson)
-  void precond(const T* v, T* z) override { vcycles<T>(g, v, z, true, sigma, o.mg_cycles, o.nu1, o.nu2); }
+  void precond(const E* v, E* z) override {
+    if constexpr (std::is_same<T, E>::value) {
+      vcycles<T>(g, v, z, true, sigma, o.mg_cycles, o.nu1, o.nu2);
+    } else {
+      T* bt = pfield<T>(g, 0);
+      T* xt = pfield<T>(g, 1);
+      launch_convert<E, T>(v, bt, g->d.n(), 1.0, nullptr, g->s);
+      vcycles<T>(g, bt, xt, true, sigma, o.mg_cycles, o.nu1, o.nu2);
+      launch_convert<T, E>(xt, z, g->d.n(), 1.0, nullptr, g->s);
+    }
+  }
 };
 
 // K [c; lambda] = [A c + zeta S lambda; xi J c]  (Eq. saddle_point) on
-// vectors [c; lambda] of type T; the preconditioner works in T.
-template <typename T>
-struct SaddleOp : LinOp<T> {
+// vectors [c; lambda] of type E. The preconditioner's V-cycles, spreading and
+// interpolation run in T; its inner Schur GMRES basis has the vectors' type E.
+template <typename T, typename E = T>
+struct SaddleOp : LinOp<E> {
   ibrd_grid g;
   ibrd_solve_opts o;
   double zeta, xi;
@@ -914,22 +928,22 @@ struct SaddleOp : LinOp<T> {
   }
   std::string key() const override {
     char buf[200];
-    std::snprintf(buf, sizeof buf, "saddle|%zu|%d|%d|%d|%d|%d|%.17g|%.17g|%.17g|%.17g", sizeof(T), o.mg_cycles,
-                  o.nu1, o.nu2, o.schur_inner, o.precond, zeta, xi, g->alpha, g->gamma_diag);
+    std::snprintf(buf, sizeof buf, "saddle|%zu|%zu|%d|%d|%d|%d|%d|%.17g|%.17g|%.17g|%.17g", sizeof(T), sizeof(E),
+                  o.mg_cycles, o.nu1, o.nu2, o.schur_inner, o.precond, zeta, xi, g->alpha, g->gamma_diag);
     return buf;
   }
-  void apply(const T* x, T* y) override {
+  void apply(const E* x, E* y) override {
     const size_t nc = g->d.n();
-    launch_apply_A<T>(x, y, g->d, stencil(g->h, g->chi, g->alpha), g->s);
-    launch_spread<T, T>(g->blobs, g->d, x + nc, nullptr, zeta * inv_h3(g), y, 1, g->s);
-    launch_interp<T, T>(g->blobs, g->d, x, xi, y + nc, g->s);
+    launch_apply_A<E>(x, y, g->d, stencil(g->h, g->chi, g->alpha), g->s);
+    launch_spread<E, E>(g->blobs, g->d, x + nc, nullptr, zeta * inv_h3(g), y, 1, g->s);
+    launch_interp<E, E>(g->blobs, g->d, x, xi, y + nc, g->s);
   }
-  void residual(const T* b, const T* x, T* r) override {
+  void residual(const E* b, const E* x, E* r) override {
     const size_t nc = g->d.n();
-    launch_residual<T>(x, b, r, g->d, stencil(g->h, g->chi, g->alpha), g->s);
-    launch_spread<T, T>(g->blobs, g->d, x + nc, nullptr, -zeta * inv_h3(g), r, 1, g->s);
-    launch_interp<T, T>(g->blobs, g->d, x, -xi, r + nc, g->s);
-    launch_axpby<T>(1.0, b + nc, 1.0, r + nc, g->blobs.n, g->s);
+    launch_residual<E>(x, b, r, g->d, stencil(g->h, g->chi, g->alpha), g->s);
+    launch_spread<E, E>(g->blobs, g->d, x + nc, nullptr, -zeta * inv_h3(g), r, 1, g->s);
+    launch_interp<E, E>(g->blobs, g->d, x, -xi, r + nc, g->s);
+    launch_axpby<E>(1.0, b + nc, 1.0, r + nc, g->blobs.n, g->s);
   }
   // Appendix A, steps 1-5, with A~_n^-1 = n V-cycles and, for the approximate
   // Schur complement, m GMRES iterations on J A~_1^-1 S.
@@ -942,13 +956,13 @@ struct SaddleOp : LinOp<T> {
   // smoothing sweep. Where a constant offset of a field cancels (c~ is used
   // only through c~ + cbar with cbar = <f/xi - J c~> and J 1 = 1) the mean is
   // not formed at all.
-  void precond(const T* v, T* z) override {
+  void precond(const E* v, E* z) override {
     const size_t nc = g->d.n();
     const int N = g->blobs.n;
-    const T* vc = v;
-    const T* vf = v + nc;
-    T* zc = z;
-    T* zl = z + nc;
+    const E* vc = v;
+    const E* vf = v + nc;
+    E* zc = z;
+    E* zl = z + nc;
     T* gt = pfield<T>(g, 0);   // g~
     T* cs = pfield<T>(g, 1);   // c~* then c~
     const double volume = (double)nc * g->h * g->h * g->h;
@@ -959,7 +973,7 @@ struct SaddleOp : LinOp<T> {
     const double* bmean = nullptr;
     const double* xshift = nullptr;
     if (singular) {
-      launch_convert_sum<T, T>(vc, gt, nc, g->partial, sc + S_GSUM, sc + S_G32SUM, g->s);
+      launch_convert_sum<E, T>(vc, gt, nc, g->partial, sc + S_GSUM, sc + S_G32SUM, g->s);
       // zeta S (lambda-bar 1) = (V / (N N_c)) sum(g) S 1; its total is sum(g)
       launch_spread_const<T>(g->blobs, g->d, sc + S_GSUM, -volume / ((double)N * (double)nc) * ih3, gt, g->s);
       prof_begin(P_SMALL, g->s);
@@ -972,7 +986,7 @@ struct SaddleOp : LinOp<T> {
       xshift = sc + S_XMEAN1;
       vcycles<T>(g, gt, cs, true, shift, o.mg_cycles, o.nu1, o.nu2, bmean, XMean::Report, sc + S_XMEAN1);
     } else {
-      launch_convert<T, T>(vc, gt, nc, 1.0, nullptr, g->s);
+      launch_convert<E, T>(vc, gt, nc, 1.0, nullptr, g->s);
       vcycles<T>(g, gt, cs, true, shift, o.mg_cycles, o.nu1, o.nu2);
     }
     // step 2: rhs = (zeta xi)^-1 (xi J c~* - f), with J applied to the
@@ -993,21 +1007,21 @@ struct SaddleOp : LinOp<T> {
       T* fx = pfield<T>(g, 3);
       // mean of S U_j = h^-3 sum(U_j) / N_c
       const double ub_scale = ih3 / (double)nc;
-      // the inner basis has the preconditioner's precision T
-      T* U = reinterpret_cast<T*>(g->U);
-      launch_small_start<T>(rhs, U, N, g->sg, m, singular ? sc + S_UB : nullptr, ub_scale, g->s);
+      // the inner basis has the Krylov vectors' precision E
+      E* U = reinterpret_cast<E*>(g->U);
+      launch_small_start<E>(rhs, U, N, g->sg, m, singular ? sc + S_UB : nullptr, ub_scale, g->s);
       for (int j = 0; j < m; ++j) {
-        launch_spread<T, T>(g->blobs, g->d, U + (size_t)j * N, nullptr, ih3, fs, 0, g->s);
+        launch_spread<T, E>(g->blobs, g->d, U + (size_t)j * N, nullptr, ih3, fs, 0, g->s);
         if (singular)
           vcycle<T>(g, fs, fx, true, shift, o.nu1, o.nu2, sc + S_UB + j, XMean::Report, sc + S_UX + j);
         else
           vcycle<T>(g, fs, fx, true, shift, o.nu1, o.nu2);
-        launch_interp<T, T>(g->blobs, g->d, fx, 1.0, U + (size_t)(j + 1) * N, g->s);
-        launch_small_arnoldi<T>(U, N, j, g->Hs, m + 1, g->scs, g->ssn, g->sg, singular ? sc + S_UX + j : nullptr,
+        launch_interp<T, E>(g->blobs, g->d, fx, 1.0, U + (size_t)(j + 1) * N, g->s);
+        launch_small_arnoldi<E>(U, N, j, g->Hs, m + 1, g->scs, g->ssn, g->sg, singular ? sc + S_UX + j : nullptr,
                              singular && j + 1 < m ? sc + S_UB + j + 1 : nullptr, ub_scale, g->s);
         g->inner++;
       }
-      launch_small_finish<T>(U, N, m, g->Hs, m + 1, g->sg, lam, singular ? 1 : 0, g->s);
+      launch_small_finish<E>(U, N, m, g->Hs, m + 1, g->sg, lam, singular ? 1 : 0, g->s);
     }
     // step 3: c~ = A~_n^-1 (g~ - zeta S lambda~) from c~*; lambda~ has mean
     // zero, so the right-hand side keeps the mean of g~
@@ -1022,11 +1036,11 @@ struct SaddleOp : LinOp<T> {
       launch_interp<T>(g->blobs, g->d, cs, 1.0, t, g->s);
       launch_nvec_affine(t, t, N, -1.0, nullptr, vf, 1.0 / xi, g->s);
       launch_sum<double>(t, N, g->partial, sc + S_CBAR, 1.0 / N, g->s);
-      launch_convert<double, T>(lam, zl, N, 1.0, sc + S_LBAR, g->s);
-      launch_convert<T, T>(cs, zc, nc, 1.0, sc + S_CBAR, g->s);
+      launch_convert<double, E>(lam, zl, N, 1.0, sc + S_LBAR, g->s);
+      launch_convert<T, E>(cs, zc, nc, 1.0, sc + S_CBAR, g->s);
     } else {
-      launch_convert<double, T>(lam, zl, N, 1.0, nullptr, g->s);
-      IBRD_CUDA(cudaMemcpyAsync(zc, cs, sizeof(T) * nc, cudaMemcpyDeviceToDevice, g->s));
+      launch_convert<double, E>(lam, zl, N, 1.0, nullptr, g->s);
+      launch_convert<T, E>(cs, zc, nc, 1.0, nullptr, g->s);
     }
   }
 };
@@ -1089,7 +1103,7 @@ ibrd_solve_opts resolve_opts(ibrd_grid g, const ibrd_solve_opts* in) {
   if (!(o.tol > 0.0) || o.restart < 1 || o.restart > 60 || o.max_iter < 0 || o.mg_cycles < 1 ||
       o.schur_inner < 1 || o.schur_inner > 60 || o.nu1 < 0 || o.nu2 < 0 || !(o.zeta != 0.0) ||
       !(o.reorth_eta >= 0.0) || !(o.inner_tol > 0.0 && o.inner_tol < 1.0) ||
-      (o.precision != IBRD_FP64 && o.precision != IBRD_MIXED_FP32) ||
+      (o.precision != IBRD_FP64 && o.precision != IBRD_MIXED_FP32 && o.precision != IBRD_MIXED_REFINE) ||
       (o.precond != IBRD_PRECOND_SCHUR && o.precond != IBRD_PRECOND_DIAG))
     throw ArgError{IBRD_ERR_ARG, "invalid solver options"};
   return o;
@@ -1206,7 +1220,7 @@ ibrd_status ibrd_grid_create(ibrd_grid* out, int nx, int ny, int nz, double h, d
   *out = nullptr;
   if (nx < 4 || ny < 4 || nz < 4 || !(h > 0.0) || !(chi > 0.0) || !(alpha >= 0.0) || !std::isfinite(h) ||
       !std::isfinite(chi) || !std::isfinite(alpha) || (kernel != IBRD_PESKIN4 && kernel != IBRD_PESKIN3) ||
-      (precision != IBRD_FP64 && precision != IBRD_MIXED_FP32))
+      (precision != IBRD_FP64 && precision != IBRD_MIXED_FP32 && precision != IBRD_MIXED_REFINE))
     return IBRD_ERR_ARG;
   if ((double)nx * ny * nz > 4.0e9) return IBRD_ERR_ARG;
   ibrd_grid g = new (std::nothrow) ibrd_grid_s();
@@ -1351,10 +1365,14 @@ ibrd_status ibrd_solve_reaction(ibrd_grid g, const double* kappa, const double* 
       hist.buf = info->residual_history;
       hist.cap = info->history_cap;
     }
-    ReactionOp<double> op(g, kappa, sigma, o);
     if (o.precision == IBRD_FP64) {
+      ReactionOp<double> op(g, kappa, sigma, o);
+      R = fgmres<double>(g, op, rhs, c, g->d.n(), o, o.tol, o.max_iter, !o.use_guess, hist);
+    } else if (o.precision == IBRD_MIXED_FP32) {
+      ReactionOp<float, double> op(g, kappa, sigma, o);
       R = fgmres<double>(g, op, rhs, c, g->d.n(), o, o.tol, o.max_iter, !o.use_guess, hist);
     } else {
+      ReactionOp<double> op(g, kappa, sigma, o);
       ReactionOp<float> op32(g, kappa, sigma, o);
       R = refine(g, op, op32, rhs, c, g->d.n(), o, !o.use_guess, hist);
     }
@@ -1409,10 +1427,14 @@ ibrd_status ibrd_solve_saddle(ibrd_grid g, const double* rhs, const double* f, d
       hist.buf = info->residual_history;
       hist.cap = info->history_cap;
     }
-    SaddleOp<double> op(g, o, o.zeta, o.xi);
     if (o.precision == IBRD_FP64) {
+      SaddleOp<double> op(g, o, o.zeta, o.xi);
+      R = fgmres<double>(g, op, g->bs, g->xs, n, o, o.tol, o.max_iter, !o.use_guess, hist);
+    } else if (o.precision == IBRD_MIXED_FP32) {
+      SaddleOp<float, double> op(g, o, o.zeta, o.xi);
       R = fgmres<double>(g, op, g->bs, g->xs, n, o, o.tol, o.max_iter, !o.use_guess, hist);
     } else {
+      SaddleOp<double> op(g, o, o.zeta, o.xi);
       SaddleOp<float> op32(g, o, o.zeta, o.xi);
       R = refine(g, op, op32, g->bs, g->xs, n, o, !o.use_guess, hist);
     }
