@@ -16,6 +16,10 @@ GPU library fixes these readings, and this module states them plainly:
   axis from the two nearest coarse centres).
 * Coarsest level: solved exactly; when alpha = 0 with the pseudo-inverse, which
   is the restricted inverse of Appendix A (mean-zero in, mean-zero out).
+  The FP32 V-cycle of the GPU library stops coarsening earlier, at the first
+  level with at most 4096 cells and no side above 64, and solves that level
+  exactly (``exact_cells`` / ``exact_side`` below); the FP64 V-cycle coarsens
+  to the end.
 * When alpha = 0 the right-hand side is first projected to mean zero and the
   returned field is projected to mean zero (Appendix A's restricted inverse).
 """
@@ -26,9 +30,17 @@ import numpy as np
 from . import operators as op
 
 
-def level_shapes(dims, h):
-    """List of ((nx, ny, nz), h_l) from finest to coarsest."""
+def level_shapes(dims, h, exact_cells=None, exact_side=None):
+    """List of ((nx, ny, nz), h_l) from finest to coarsest. With exact_cells
+    (and exact_side), the list ends at the first level with at most
+    exact_cells cells and no side above exact_side, if one exists."""
     out = [(tuple(int(v) for v in dims), float(h))]
+    if exact_cells is not None:
+        full = level_shapes(dims, h)
+        for i, (d, _) in enumerate(full):
+            if d[0] * d[1] * d[2] <= exact_cells and max(d) <= exact_side:
+                return full[:i + 1]
+        return full
     while True:
         d, hl = out[-1]
         if all(v % 2 == 0 and v >= 4 for v in d):
@@ -90,17 +102,22 @@ def prolong(e):
 
 
 def coarse_solve(b, h, chi, alpha):
-    """Exact coarsest solve from the assembled dense matrix (pseudo-inverse when
-    alpha = 0)."""
+    """Exact coarsest solve (pseudo-inverse when alpha = 0): from the assembled
+    dense matrix up to 512 cells, by the FFT Green's function above."""
     nz, ny, nx = b.shape
     n = b.size
+    if n > 512:
+        return op.green_apply(b, h, chi, alpha)
     A = np.zeros((n, n))
     for k in range(n):
         e = np.zeros(n)
         e[k] = 1.0
         A[:, k] = op.apply_A(e.reshape(b.shape), h, chi, alpha).ravel()
     if alpha == 0.0:
-        x = np.linalg.pinv(A) @ b.ravel()
+        # the minimum-norm least-squares solution: the pseudo-inverse applied
+        # to b, computed directly (an explicit pinv loses accuracy on some
+        # non-cubic singular operators)
+        x = np.linalg.lstsq(A, b.ravel(), rcond=None)[0]
     else:
         x = np.linalg.solve(A, b.ravel())
     return x.reshape(b.shape)
@@ -121,10 +138,11 @@ def _vcycle(levels, l, b, x, chi, alpha, nu1, nu2):
     return x
 
 
-def vcycle(b, h, chi, alpha, x0=None, nu1=2, nu2=2):
-    """One V-cycle for A x = b from x0 (zero if None); returns the new x."""
+def vcycle(b, h, chi, alpha, x0=None, nu1=2, nu2=2, exact_cells=None, exact_side=None):
+    """One V-cycle for A x = b from x0 (zero if None); returns the new x. The
+    hierarchy follows level_shapes (exact_cells / exact_side as there)."""
     nz, ny, nx = b.shape
-    levels = level_shapes((nx, ny, nz), h)
+    levels = level_shapes((nx, ny, nz), h, exact_cells, exact_side)
     b = np.array(b, dtype=np.float64)
     if alpha == 0.0:
         b = b - b.mean()

@@ -270,25 +270,54 @@ def test_level_shapes():
     assert [d for d, _ in mg.level_shapes((32, 32, 32), 1.0)] == [(32,) * 3, (16,) * 3, (8,) * 3, (4,) * 3, (2,) * 3]
     assert [d[0] for d, _ in mg.level_shapes((160, 160, 160), 1.0)] == [160, 80, 40, 20, 10, 5]
     assert [d[0] for d, _ in mg.level_shapes((96, 96, 96), 1.0)] == [96, 48, 24, 12, 6, 3]
+    # the FP32 V-cycle's hierarchy: it ends at the first level of <= 4096 cells with no side above 64
+    ex = dict(exact_cells=4096, exact_side=64)
+    assert [d[0] for d, _ in mg.level_shapes((256,) * 3, 1.0, **ex)] == [256, 128, 64, 32, 16]
+    assert [d[0] for d, _ in mg.level_shapes((160,) * 3, 1.0, **ex)] == [160, 80, 40, 20, 10]
+    assert [d for d, _ in mg.level_shapes((16, 16, 16), 1.0, **ex)] == [(16,) * 3]
+    # no level qualifies (a side stays above 64): the full hierarchy
+    assert [d for d, _ in mg.level_shapes((256, 8, 2), 1.0, **ex)] == [(256, 8, 2)]
 
 
+@pytest.mark.parametrize("exact", [{}, dict(exact_cells=4096, exact_side=64)])
 @pytest.mark.parametrize("alpha", [0.0, 0.05])
-def test_vcycle_fixed_point_and_reduction(alpha):
+def test_vcycle_fixed_point_and_reduction(alpha, exact):
     """A V-cycle started from the exact solution returns it; from zero it
-    reduces the residual by at least the 5x the paper quotes (Sec. III.E)."""
+    reduces the residual by at least the 5x the paper quotes (Sec. III.E);
+    both for the full hierarchy and the one ending in an exact 16^3 level."""
     n, h, chi = 32, 1.0, 1.0
     rng = np.random.default_rng(51)
     x = rng.standard_normal((n, n, n))
     if alpha == 0.0:
         x -= x.mean()
     b = op.apply_A(x, h, chi, alpha)
-    np.testing.assert_allclose(mg.vcycle(b, h, chi, alpha, x0=x), x, atol=1e-11)
+    np.testing.assert_allclose(mg.vcycle(b, h, chi, alpha, x0=x, **exact), x, atol=1e-11)
     b2 = rng.standard_normal((n, n, n))
     if alpha == 0.0:
         b2 -= b2.mean()
-    y = mg.vcycle(b2, h, chi, alpha)
+    y = mg.vcycle(b2, h, chi, alpha, **exact)
     red = np.linalg.norm(b2) / np.linalg.norm(b2 - op.apply_A(y, h, chi, alpha))
     assert red >= GOLD["vcycle_residual_reduction"]["min"]
+
+
+@pytest.mark.parametrize("alpha", [0.0, 0.3])
+def test_coarse_solve_large_level_by_brute_force(alpha):
+    """Levels above 512 cells are solved through the FFT Green's function:
+    checked against the assembled dense operator at 10 x 10 x 8 (800 cells)."""
+    rng = np.random.default_rng(62)
+    shape = (8, 10, 10)
+    b = rng.standard_normal(shape)
+    if alpha == 0.0:
+        b -= b.mean()
+    h, chi = 2.0, 1.3
+    n = b.size
+    A = np.zeros((n, n))
+    for k in range(n):
+        e = np.zeros(n)
+        e[k] = 1.0
+        A[:, k] = op.apply_A(e.reshape(shape), h, chi, alpha).ravel()
+    want = np.linalg.lstsq(A, b.ravel(), rcond=None)[0]  # minimum-norm solution when singular
+    np.testing.assert_allclose(mg.coarse_solve(b, h, chi, alpha).ravel(), want, atol=1e-12)
 
 
 def test_coarse_solve_vs_fft_green():
@@ -298,6 +327,10 @@ def test_coarse_solve_vs_fft_green():
     np.testing.assert_allclose(mg.coarse_solve(b, 16.0, 1.0, 0.0), op.green_apply(b, 16.0, 1.0, 0.0), atol=1e-13)
     b3 = rng.standard_normal((3, 3, 3))
     np.testing.assert_allclose(mg.coarse_solve(b3, 4.0, 1.0, 0.2), op.green_apply(b3, 4.0, 1.0, 0.2), atol=1e-13)
+    # a non-cubic singular coarsest level (the (64, 48, 40) hierarchy ends at 8 x 6 x 5)
+    b4 = rng.standard_normal((5, 6, 8))
+    b4 -= b4.mean()
+    np.testing.assert_allclose(mg.coarse_solve(b4, 8.0, 2.0, 0.0), op.green_apply(b4, 8.0, 2.0, 0.0), atol=1e-12)
 
 
 def test_outputs_formulae():
