@@ -79,6 +79,7 @@ struct Hier {
   T* f0 = nullptr;                            // level-0 scratch fields (mixed path)
   T* f1 = nullptr;
   std::vector<std::pair<double, T*>> tables;  // coarsest Green's tables by shift
+  std::vector<std::pair<double, T*>> hartley; // exact-level transform tables by shift (FP32)
 };
 
 struct Level {
@@ -166,6 +167,7 @@ struct ibrd_grid_s {
   cudaStream_t s = nullptr;
   std::vector<Level> levels;
   int small_from = 0;           // first level handled by the single-CTA coarse V-cycle
+  int exact32 = -1;             // FP32 V-cycles: level solved exactly by the Hartley transform (-1: none)
   Hier<double> h64;
   Hier<float> h32;
   BlobSet blobs;
@@ -276,6 +278,18 @@ void ensure_hier(ibrd_grid g) {
   }
 }
 
+// Hartley tables of the FP32 exact level for a shift.
+const float* hartley_table(ibrd_grid g, double shift) {
+  Hier<float>& H = g->h32;
+  for (auto& e : H.hartley)
+    if (e.first == shift) return e.second;
+  const Level& le = g->levels[g->exact32];
+  float* t = dalloc<float>(hartley_table_size(le.d));
+  launch_hartley_tables(t, le.d, stencil(le.h, g->chi, shift), shift == 0.0 ? 1 : 0, g->s);
+  H.hartley.emplace_back(shift, t);
+  return t;
+}
+
 template <typename T>
 const T* coarse_table(ibrd_grid g, double shift) {
   Hier<T>& H = hier<T>(g);
@@ -321,6 +335,12 @@ int vcycle_level(ibrd_grid g, int l, const T* b, const double* bshift, T* x, boo
   Hier<T>& H = hier<T>(g);
   const Level& lv = g->levels[l];
   const Stencil st = stencil(lv.h, g->chi, shift);
+  if (sizeof(T) == 4 && l == g->exact32) {
+    // FP32 hierarchy: this level is solved exactly
+    launch_hartley_solve(hartley_table(g, shift), reinterpret_cast<const float*>(b), bshift,
+                         reinterpret_cast<float*>(x), lv.d, g->s);
+    return 0;
+  }
   if (l == (int)g->levels.size() - 1) {
     // Exact coarsest solve. A constant shift of b only changes the mean, which
     // the singular pseudo-inverse ignores; the nonsingular case never shifts.
@@ -328,7 +348,8 @@ int vcycle_level(ibrd_grid g, int l, const T* b, const double* bshift, T* x, boo
     return 0;
   }
   // the coarse end of the hierarchy runs in one CTA out of shared memory
-  if (l >= g->small_from) {
+  // (FP64 V-cycles, and FP32 ones on grids without an exact level)
+  if (l >= g->small_from && !(sizeof(T) == 4 && g->exact32 >= 0)) {
     const CoarseLevels cl = small_levels(g, l, shift);
     launch_vcycle_small<T>(cl, b, x, bshift, coarse_table<T>(g, shift), zero, nu1, nu2, g->s);
     return 0;
@@ -1197,6 +1218,7 @@ void ibrd_grid_destroy(ibrd_grid g) {
   for (auto p : g->h32.y) F(p);
   for (auto& e : g->h64.tables) F(e.second);
   for (auto& e : g->h32.tables) F(e.second);
+  for (auto& e : g->h32.hartley) F(e.second);
   BlobSet& b = g->blobs;
   F(b.q); F(b.idx); F(b.w64); F(b.w32); F(b.tile_count); F(b.tile_offset); F(b.tile_cursor); F(b.tile_blobs);
   F(b.active); F(b.d_meta); F(b.cell_count); F(b.cell_offset); F(b.cells); F(b.cell_tile);
@@ -1261,6 +1283,13 @@ ibrd_status ibrd_grid_create(ibrd_grid* out, int nx, int ny, int nz, double h, d
         break;
     }
   }
+  // FP32 V-cycles end at the first level of at most 4096 cells with no side
+  // above 64, solved exactly (the FP64 V-cycles coarsen to the end)
+  for (int l = 0; l < (int)g->levels.size(); ++l)
+    if (hartley_ok(g->levels[l].d)) {
+      g->exact32 = l;
+      break;
+    }
   ibrd_status st = guarded(g, "ibrd_grid_create", [&]() {
     g->scal = dalloc<double>(S_COUNT);
     g->partial = dalloc<double>((size_t)kRedBlocks * kDotGroup);

@@ -130,6 +130,131 @@ __global__ void k_coarse_table(T* __restrict__ table, int nx, int ny, int nz, do
   table[t] = (T)(acc / n);
 }
 
+// Exact solve on a small periodic level through the separable Hartley
+// transform. With cas(t) = cos t + sin t, the matrix H_n[k][j] =
+// cas(2 pi k j / n) is symmetric, H_n^2 = n I, and its columns are
+// eigenvectors of every symmetric circulant of order n (cos and sin of the
+// same frequency share an eigenvalue). So T = H_nz (x) H_ny (x) H_nx is
+// symmetric with T^2 = N I and diagonalises A = diag I - off * (sum of the 6
+// shifts) with eigenvalues lambda_k = diag - 2 off (cos(2 pi kx / nx) +
+// cos(2 pi ky / ny) + cos(2 pi kz / nz)); hence A^-1 = T diag(w) T with
+// w_k = 1 / (N lambda_k), and w_0 = 0 when singular (the pseudo-inverse:
+// mean-zero in, mean-zero out).
+//
+// Table layout (FP32): cas_x (nx^2), cas_y (ny^2), cas_z (nz^2), w (N).
+__global__ void k_hartley_tables(float* __restrict__ tab, int nx, int ny, int nz, double diag, double off,
+                                 int singular) {
+  const int n = nx * ny * nz;
+  const int ox = 0, oy = nx * nx, oz = oy + ny * ny, ow = oz + nz * nz;
+  const double twopi = 6.283185307179586476925286766559;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  auto cas = [&](int k, int j, int m) {
+    const double a = twopi * (double)((k * j) % m) / m;
+    return (float)(cos(a) + sin(a));
+  };
+  if (t < nx * nx) tab[ox + t] = cas(t / nx, t % nx, nx);
+  if (t < ny * ny) tab[oy + t] = cas(t / ny, t % ny, ny);
+  if (t < nz * nz) tab[oz + t] = cas(t / nz, t % nz, nz);
+  if (t < n) {
+    const int kx = t % nx, ky = (t / nx) % ny, kz = t / (nx * ny);
+    const double lam =
+        diag - 2.0 * off * (cos(twopi * kx / nx) + cos(twopi * ky / ny) + cos(twopi * kz / nz));
+    tab[ow + t] = (singular && t == 0) ? 0.f : (float)(1.0 / ((double)n * lam));
+  }
+}
+
+// One CTA: loads b - shift, applies T, scales by w, applies T, stores x. In
+// shared memory the field is padded (strides 1, nx + 1, (nx + 1)(ny + 1)) and
+// the rows of H are padded to m + 1, so that a pass, one thread per output
+// (line, k) with consecutive threads on consecutive k, reads H rows and
+// writes outputs without bank conflicts and reads each input as a broadcast.
+// CUBE = 16 fixes a 16^3 level at compile time: each thread then computes 4
+// outputs (k0 .. k0 + 3) of one line, holding the line's 16 inputs in
+// registers and reading H (symmetric, unpadded) as 4-vectors, a quarter of
+// the shared-memory loads per output. CUBE = 0 takes the sides at run time.
+template <int CUBE>
+__global__ void __launch_bounds__(1024) k_hartley_solve(const float* __restrict__ tab, const float* __restrict__ b,
+                                                        const double* __restrict__ bshift, float* __restrict__ x,
+                                                        int nx_, int ny_, int nz_) {
+  extern __shared__ __align__(16) float hs[];
+  const int nx = CUBE ? CUBE : nx_, ny = CUBE ? CUBE : ny_, nz = CUBE ? CUBE : nz_;
+  const int n = nx * ny * nz;
+  const int px = nx + 1, pxy = (nx + 1) * (ny + 1), pn = pxy * nz;
+  float* Hp[3];
+  Hp[0] = hs;
+  Hp[1] = Hp[0] + nx * (nx + 1);  // (CUBE = 16: 272 floats, a multiple of 4, so the unpadded tables stay aligned)
+  Hp[2] = Hp[1] + ny * (ny + 1);
+  float* D0 = Hp[2] + nz * (nz + 1);
+  float* D1 = D0 + pn;
+  const float* W = tab + nx * nx + ny * ny + nz * nz;  // read from global (once per cell)
+  const int len[3] = {nx, ny, nz}, pstr[3] = {1, px, pxy};
+  const float* src[3] = {tab, tab + nx * nx, tab + nx * nx + ny * ny};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int m = len[a];
+    if constexpr (CUBE == 16)
+      for (int i = threadIdx.x; i < m * m; i += blockDim.x) Hp[a][i] = src[a][i];  // unpadded
+    else
+      for (int i = threadIdx.x; i < m * m; i += blockDim.x) Hp[a][(i / m) * (m + 1) + i % m] = src[a][i];
+  }
+  const float sh = bshift ? (float)(*bshift) : 0.f;
+  auto pidx = [&](int c) {  // padded index of cell c
+    const int i = c % nx, j = (c / nx) % ny, k = c / (nx * ny);
+    return k * pxy + j * px + i;
+  };
+  for (int c = threadIdx.x; c < n; c += blockDim.x) D0[pidx(c)] = b[c] - sh;
+  __syncthreads();
+  // out = transform of in along axis a
+  auto pass = [&](const float* in, float* out, int a) {
+    const int m = len[a], st = pstr[a];
+    const float* h = Hp[a];
+    const int o1 = a == 0 ? ny : nx;  // the two other coordinates of a line
+    if constexpr (CUBE == 16) {
+      // blockDim.x == 1024 == 4096 outputs / 4: one item per thread
+      const int line = threadIdx.x >> 2, k0 = (threadIdx.x & 3) * 4;
+      const int u = line & 15, v = line >> 4;
+      const int base = a == 0 ? u * px + v * pxy : (a == 1 ? u + v * pxy : u + v * px);
+      float xin[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) xin[j] = in[base + j * st];
+      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const float4 hv = *reinterpret_cast<const float4*>(h + j * 16 + k0);  // H[k0..k0+3][j] (symmetric)
+        acc.x = fmaf(hv.x, xin[j], acc.x);
+        acc.y = fmaf(hv.y, xin[j], acc.y);
+        acc.z = fmaf(hv.z, xin[j], acc.z);
+        acc.w = fmaf(hv.w, xin[j], acc.w);
+      }
+      out[base + (k0 + 0) * st] = acc.x;
+      out[base + (k0 + 1) * st] = acc.y;
+      out[base + (k0 + 2) * st] = acc.z;
+      out[base + (k0 + 3) * st] = acc.w;
+    } else {
+    for (int it = threadIdx.x; it < n; it += blockDim.x) {
+      const int line = it / m, k = it - line * m;
+      const int u = line % o1, v = line / o1;
+      const int base = a == 0 ? u * px + v * pxy : (a == 1 ? u + v * pxy : u + v * px);
+      const float* hk = h + k * (m + 1);
+      const float* ip = in + base;
+      float acc = 0.f;
+      for (int j = 0; j < m; ++j) acc = fmaf(hk[j], ip[j * st], acc);
+      out[base + k * st] = acc;
+    }
+    }
+    __syncthreads();
+  };
+  pass(D0, D1, 0);
+  pass(D1, D0, 1);
+  pass(D0, D1, 2);
+  for (int c = threadIdx.x; c < n; c += blockDim.x) D1[pidx(c)] *= W[c];
+  __syncthreads();
+  pass(D1, D0, 0);
+  pass(D0, D1, 1);
+  pass(D1, D0, 2);
+  for (int c = threadIdx.x; c < n; c += blockDim.x) x[c] = D0[pidx(c)];
+}
+
 // ---------------------------------------------------------------- reductions
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -468,6 +593,35 @@ void launch_coarse_table(T* table, Dims dc, Stencil st, int singular, cudaStream
   prof_begin(P_SETUP, s);
   k_coarse_table<T><<<(n + 127) / 128, 128, 0, s>>>(table, dc.nx, dc.ny, dc.nz, st.diag, st.off, singular);
   prof_end(P_SETUP, s, "coarse_table");
+}
+
+size_t hartley_table_size(Dims d) { return (size_t)d.nx * d.nx + (size_t)d.ny * d.ny + (size_t)d.nz * d.nz + d.n(); }
+
+bool hartley_ok(Dims d) { return d.n() <= 4096 && d.nx <= 64 && d.ny <= 64 && d.nz <= 64; }
+
+void launch_hartley_tables(float* tab, Dims d, Stencil st, int singular, cudaStream_t s) {
+  const int m = (int)std::max<size_t>(d.n(), std::max(d.nx * d.nx, std::max(d.ny * d.ny, d.nz * d.nz)));
+  prof_begin(P_SETUP, s);
+  k_hartley_tables<<<(m + 127) / 128, 128, 0, s>>>(tab, d.nx, d.ny, d.nz, st.diag, st.off, singular);
+  prof_end(P_SETUP, s, "hartley_tables");
+}
+
+void launch_hartley_solve(const float* tab, const float* b, const double* bshift, float* x, Dims d, cudaStream_t s) {
+  const size_t pn = (size_t)(d.nx + 1) * (d.ny + 1) * d.nz;
+  const size_t sm = sizeof(float) * ((size_t)d.nx * (d.nx + 1) + (size_t)d.ny * (d.ny + 1) +
+                                     (size_t)d.nz * (d.nz + 1) + 2 * pn);
+  static bool attr = false;
+  if (!attr) {
+    IBRD_CUDA(cudaFuncSetAttribute(k_hartley_solve<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    IBRD_CUDA(cudaFuncSetAttribute(k_hartley_solve<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    attr = true;
+  }
+  prof_begin(P_COARSE, s);
+  if (d.nx == 16 && d.ny == 16 && d.nz == 16)
+    k_hartley_solve<16><<<1, 1024, sm, s>>>(tab, b, bshift, x, d.nx, d.ny, d.nz);
+  else
+    k_hartley_solve<0><<<1, 1024, sm, s>>>(tab, b, bshift, x, d.nx, d.ny, d.nz);
+  prof_end(P_COARSE, s, "hartley_solve", 8.0 * d.n());
 }
 
 template <typename T>

@@ -122,6 +122,15 @@ void launch_coarse_solve(const T* table, const T* b, T* x, Dims dc, cudaStream_t
 template <typename T>
 void launch_coarse_table(T* table, Dims dc, Stencil st, int singular, cudaStream_t s);
 
+// Exact FP32 solve of A x = b - shift on a small periodic level (at most 4096
+// cells, no side above 64) by the separable Hartley transform; tab holds
+// hartley_table_size(d) floats written by launch_hartley_tables (singular:
+// pseudo-inverse, mean-zero result).
+bool hartley_ok(Dims d);
+size_t hartley_table_size(Dims d);
+void launch_hartley_tables(float* tab, Dims d, Stencil st, int singular, cudaStream_t s);
+void launch_hartley_solve(const float* tab, const float* b, const double* bshift, float* x, Dims d, cudaStream_t s);
+
 // ---------------------------------------------------------------- vector kernels
 // Sum of x[0..n) into partials (kRedBlocks doubles); then finalize into *out.
 template <typename T>

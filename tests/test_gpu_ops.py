@@ -133,8 +133,30 @@ def test_vcycle_f32(ibrd, dims, alpha):
     b = rng.standard_normal((nz, ny, nx)).astype(np.float32)
     g = ibrd.Grid(*dims, alpha=alpha)
     x = g.vcycle_f32(torch.from_numpy(b).cuda())
-    want = mg.vcycle(b.astype(np.float64), 1.0, 1.0, alpha)
+    # the FP32 hierarchy ends at an exact level of at most 4096 cells
+    want = mg.vcycle(b.astype(np.float64), 1.0, 1.0, alpha, exact_cells=4096, exact_side=64)
     assert rel_max(x.cpu().numpy().astype(np.float64), want) < 2e-5
+
+
+@pytest.mark.parametrize("dims,alpha", [((16, 16, 16), 0.0), ((12, 8, 20), 0.3), ((40, 40, 40), 0.0)])
+def test_vcycle_f32_exact_level(ibrd, dims, alpha):
+    """FP32 V-cycles whose hierarchy ends in the exact Hartley-transform solve:
+    at 16^3 and 12 x 8 x 20 the finest level itself is exact (the result is
+    the FFT Green's function solution); at 40^3 the exact level is 10^3 below
+    two smoothed levels."""
+    import torch
+    nx, ny, nz = dims
+    rng = np.random.default_rng(17)
+    b = rng.standard_normal((nz, ny, nx)).astype(np.float32)
+    g = ibrd.Grid(*dims, alpha=alpha)
+    x = g.vcycle_f32(torch.from_numpy(b).cuda()).cpu().numpy().astype(np.float64)
+    want = mg.vcycle(b.astype(np.float64), 1.0, 1.0, alpha, exact_cells=4096, exact_side=64)
+    assert rel_max(x, want) < 2e-5
+    if nx * ny * nz <= 4096:
+        bb = b.astype(np.float64)
+        if alpha == 0.0:
+            bb = bb - bb.mean()
+        assert rel_max(x, op.green_apply(bb, 1.0, 1.0, alpha)) < 2e-5
 
 
 def test_vcycle_smoother_variants_agree(ibrd):
