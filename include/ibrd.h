@@ -177,7 +177,7 @@ ibrd_status ibrd_vcycle_noalloc(int nx, int ny, int nz, double h, double chi, do
 
 /* The V-cycle with FP32 fields and FP32 arithmetic (the multigrid used inside
    the mixed-precision solves). Its hierarchy ends at the first level with at
-   most 4096 cells and no side above 64, which is solved exactly by the
+   most 32768 cells and no side above 64, which is solved exactly by the
    separable Hartley transform (pseudo-inverse when alpha = 0); without such a
    level it coarsens like the FP64 V-cycle. rhs, x: FP32 device fields. */
 ibrd_status ibrd_vcycle_f32(ibrd_grid g, const float* rhs, float* x, int zero_initial_guess);

@@ -17,7 +17,7 @@ GPU library fixes these readings, and this module states them plainly:
 * Coarsest level: solved exactly; when alpha = 0 with the pseudo-inverse, which
   is the restricted inverse of Appendix A (mean-zero in, mean-zero out).
   The FP32 V-cycle of the GPU library stops coarsening earlier, at the first
-  level with at most 4096 cells and no side above 64, and solves that level
+  level with at most 32768 cells and no side above 64, and solves that level
   exactly (``exact_cells`` / ``exact_side`` below); the FP64 V-cycle coarsens
   to the end.
 * When alpha = 0 the right-hand side is first projected to mean zero and the

@@ -1283,7 +1283,7 @@ ibrd_status ibrd_grid_create(ibrd_grid* out, int nx, int ny, int nz, double h, d
         break;
     }
   }
-  // FP32 V-cycles end at the first level of at most 4096 cells with no side
+  // FP32 V-cycles end at the first level of at most 32768 cells with no side
   // above 64, solved exactly (the FP64 V-cycles coarsen to the end)
   for (int l = 0; l < (int)g->levels.size(); ++l)
     if (hartley_ok(g->levels[l].d)) {

@@ -255,6 +255,77 @@ __global__ void __launch_bounds__(1024) k_hartley_solve(const float* __restrict_
   for (int c = threadIdx.x; c < n; c += blockDim.x) x[c] = D0[pidx(c)];
 }
 
+// Larger exact levels (4096 < N <= 32768 cells, sides <= 64): the same
+// transform T = H_z H_y H_x in three launches through a scratch field:
+// planes (H_y H_x per z-plane, one CTA each), columns (H_z, scale by w, H_z,
+// one CTA per y-row), planes again (H_y H_x). In shared memory a 2-D slice is
+// padded to a row stride of cols + 1, H rows to m + 1 (conflict-free).
+// Transform along one axis of a padded 2-D slice: `lines` lines of m values,
+// element j of line l at base(l) + j * st.
+__device__ void hartley_pass2d(const float* __restrict__ in, float* __restrict__ out, const float* __restrict__ h,
+                               int m, int lines, int st, int lstride) {
+  for (int it = threadIdx.x; it < lines * m; it += blockDim.x) {
+    const int line = it / m, k = it - line * m;
+    const int base = line * lstride;
+    const float* hk = h + k * (m + 1);
+    float acc = 0.f;
+    for (int j = 0; j < m; ++j) acc = fmaf(hk[j], in[base + j * st], acc);
+    out[base + k * st] = acc;
+  }
+  __syncthreads();
+}
+
+// H_y H_x on z-plane blockIdx.x of src (minus *bshift when given) into dst.
+__global__ void __launch_bounds__(1024) k_hartley_planes(const float* __restrict__ src,
+                                                         const double* __restrict__ bshift, float* __restrict__ dst,
+                                                         const float* __restrict__ tab, int nx, int ny) {
+  extern __shared__ __align__(16) float hs[];
+  const int px = nx + 1, pn = px * ny;
+  float* hx = hs;
+  float* hy = hx + nx * (nx + 1);
+  float* A = hy + ny * (ny + 1);
+  float* Bf = A + pn;
+  for (int i = threadIdx.x; i < nx * nx; i += blockDim.x) hx[(i / nx) * (nx + 1) + i % nx] = tab[i];
+  for (int i = threadIdx.x; i < ny * ny; i += blockDim.x) hy[(i / ny) * (ny + 1) + i % ny] = tab[nx * nx + i];
+  const float sh = bshift ? (float)(*bshift) : 0.f;
+  const float* sp = src + (size_t)blockIdx.x * nx * ny;
+  for (int c = threadIdx.x; c < nx * ny; c += blockDim.x) A[(c / nx) * px + c % nx] = sp[c] - sh;
+  __syncthreads();
+  hartley_pass2d(A, Bf, hx, nx, ny, 1, px);   // along x: ny lines (rows)
+  hartley_pass2d(Bf, A, hy, ny, nx, px, 1);   // along y: nx lines (columns)
+  float* dp = dst + (size_t)blockIdx.x * nx * ny;
+  for (int c = threadIdx.x; c < nx * ny; c += blockDim.x) dp[c] = A[(c / nx) * px + c % nx];
+}
+
+// H_z, scale by w, H_z on the (x, z) slice of y-row blockIdx.x, in place.
+__global__ void __launch_bounds__(1024) k_hartley_columns(float* __restrict__ f, const float* __restrict__ tab, int nx,
+                                                          int ny, int nz) {
+  extern __shared__ __align__(16) float hs[];
+  const int px = nx + 1, pn = px * nz, j = blockIdx.x;
+  float* hz = hs;
+  float* A = hz + nz * (nz + 1);
+  float* Bf = A + pn;
+  const float* tz = tab + nx * nx + ny * ny;
+  const float* W = tz + nz * nz;
+  for (int i = threadIdx.x; i < nz * nz; i += blockDim.x) hz[(i / nz) * (nz + 1) + i % nz] = tz[i];
+  for (int c = threadIdx.x; c < nx * nz; c += blockDim.x) {
+    const int i = c % nx, k = c / nx;
+    A[k * px + i] = f[((size_t)k * ny + j) * nx + i];
+  }
+  __syncthreads();
+  hartley_pass2d(A, Bf, hz, nz, nx, px, 1);  // along z: nx lines
+  for (int c = threadIdx.x; c < nx * nz; c += blockDim.x) {
+    const int i = c % nx, k = c / nx;
+    Bf[k * px + i] *= W[((size_t)k * ny + j) * nx + i];
+  }
+  __syncthreads();
+  hartley_pass2d(Bf, A, hz, nz, nx, px, 1);
+  for (int c = threadIdx.x; c < nx * nz; c += blockDim.x) {
+    const int i = c % nx, k = c / nx;
+    f[((size_t)k * ny + j) * nx + i] = A[k * px + i];
+  }
+}
+
 // ---------------------------------------------------------------- reductions
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -595,9 +666,13 @@ void launch_coarse_table(T* table, Dims dc, Stencil st, int singular, cudaStream
   prof_end(P_SETUP, s, "coarse_table");
 }
 
-size_t hartley_table_size(Dims d) { return (size_t)d.nx * d.nx + (size_t)d.ny * d.ny + (size_t)d.nz * d.nz + d.n(); }
+// tables, then (levels above 4096 cells) a scratch field of N floats
+size_t hartley_table_size(Dims d) {
+  const size_t t = (size_t)d.nx * d.nx + (size_t)d.ny * d.ny + (size_t)d.nz * d.nz + d.n();
+  return d.n() > 4096 ? t + d.n() : t;
+}
 
-bool hartley_ok(Dims d) { return d.n() <= 4096 && d.nx <= 64 && d.ny <= 64 && d.nz <= 64; }
+bool hartley_ok(Dims d) { return d.n() <= 32768 && d.nx <= 64 && d.ny <= 64 && d.nz <= 64; }
 
 void launch_hartley_tables(float* tab, Dims d, Stencil st, int singular, cudaStream_t s) {
   const int m = (int)std::max<size_t>(d.n(), std::max(d.nx * d.nx, std::max(d.ny * d.ny, d.nz * d.nz)));
@@ -607,6 +682,22 @@ void launch_hartley_tables(float* tab, Dims d, Stencil st, int singular, cudaStr
 }
 
 void launch_hartley_solve(const float* tab, const float* b, const double* bshift, float* x, Dims d, cudaStream_t s) {
+  if (d.n() > 4096) {
+    // three launches through the scratch field behind the tables
+    float* tmp = const_cast<float*>(tab) + ((size_t)d.nx * d.nx + (size_t)d.ny * d.ny + (size_t)d.nz * d.nz + d.n());
+    const size_t smp = sizeof(float) * ((size_t)d.nx * (d.nx + 1) + (size_t)d.ny * (d.ny + 1) + 2 * (size_t)(d.nx + 1) * d.ny);
+    const size_t smc = sizeof(float) * ((size_t)d.nz * (d.nz + 1) + 2 * (size_t)(d.nx + 1) * d.nz);
+    prof_begin(P_COARSE, s);
+    k_hartley_planes<<<d.nz, 1024, smp, s>>>(b, bshift, tmp, tab, d.nx, d.ny);
+    prof_end(P_COARSE, s, "hartley_planes", 8.0 * d.n());
+    prof_begin(P_COARSE, s);
+    k_hartley_columns<<<d.ny, 1024, smc, s>>>(tmp, tab, d.nx, d.ny, d.nz);
+    prof_end(P_COARSE, s, "hartley_columns", 12.0 * d.n());
+    prof_begin(P_COARSE, s);
+    k_hartley_planes<<<d.nz, 1024, smp, s>>>(tmp, nullptr, x, tab, d.nx, d.ny);
+    prof_end(P_COARSE, s, "hartley_planes", 8.0 * d.n());
+    return;
+  }
   const size_t pn = (size_t)(d.nx + 1) * (d.ny + 1) * d.nz;
   const size_t sm = sizeof(float) * ((size_t)d.nx * (d.nx + 1) + (size_t)d.ny * (d.ny + 1) +
                                      (size_t)d.nz * (d.nz + 1) + 2 * pn);

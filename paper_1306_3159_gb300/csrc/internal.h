@@ -122,10 +122,10 @@ void launch_coarse_solve(const T* table, const T* b, T* x, Dims dc, cudaStream_t
 template <typename T>
 void launch_coarse_table(T* table, Dims dc, Stencil st, int singular, cudaStream_t s);
 
-// Exact FP32 solve of A x = b - shift on a small periodic level (at most 4096
+// Exact FP32 solve of A x = b - shift on a small periodic level (at most 32768
 // cells, no side above 64) by the separable Hartley transform; tab holds
-// hartley_table_size(d) floats written by launch_hartley_tables (singular:
-// pseudo-inverse, mean-zero result).
+// hartley_table_size(d) floats, the first part written by
+// launch_hartley_tables (singular: pseudo-inverse, mean-zero result).
 bool hartley_ok(Dims d);
 size_t hartley_table_size(Dims d);
 void launch_hartley_tables(float* tab, Dims d, Stencil st, int singular, cudaStream_t s);

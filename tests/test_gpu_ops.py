@@ -133,8 +133,8 @@ def test_vcycle_f32(ibrd, dims, alpha):
     b = rng.standard_normal((nz, ny, nx)).astype(np.float32)
     g = ibrd.Grid(*dims, alpha=alpha)
     x = g.vcycle_f32(torch.from_numpy(b).cuda())
-    # the FP32 hierarchy ends at an exact level of at most 4096 cells
-    want = mg.vcycle(b.astype(np.float64), 1.0, 1.0, alpha, exact_cells=4096, exact_side=64)
+    # the FP32 hierarchy ends at an exact level of at most 32768 cells
+    want = mg.vcycle(b.astype(np.float64), 1.0, 1.0, alpha, exact_cells=32768, exact_side=64)
     assert rel_max(x.cpu().numpy().astype(np.float64), want) < 2e-5
 
 
@@ -150,9 +150,9 @@ def test_vcycle_f32_exact_level(ibrd, dims, alpha):
     b = rng.standard_normal((nz, ny, nx)).astype(np.float32)
     g = ibrd.Grid(*dims, alpha=alpha)
     x = g.vcycle_f32(torch.from_numpy(b).cuda()).cpu().numpy().astype(np.float64)
-    want = mg.vcycle(b.astype(np.float64), 1.0, 1.0, alpha, exact_cells=4096, exact_side=64)
+    want = mg.vcycle(b.astype(np.float64), 1.0, 1.0, alpha, exact_cells=32768, exact_side=64)
     assert rel_max(x, want) < 2e-5
-    if nx * ny * nz <= 4096:
+    if nx * ny * nz <= 32768:
         bb = b.astype(np.float64)
         if alpha == 0.0:
             bb = bb - bb.mean()

@@ -270,16 +270,16 @@ def test_level_shapes():
     assert [d for d, _ in mg.level_shapes((32, 32, 32), 1.0)] == [(32,) * 3, (16,) * 3, (8,) * 3, (4,) * 3, (2,) * 3]
     assert [d[0] for d, _ in mg.level_shapes((160, 160, 160), 1.0)] == [160, 80, 40, 20, 10, 5]
     assert [d[0] for d, _ in mg.level_shapes((96, 96, 96), 1.0)] == [96, 48, 24, 12, 6, 3]
-    # the FP32 V-cycle's hierarchy: it ends at the first level of <= 4096 cells with no side above 64
-    ex = dict(exact_cells=4096, exact_side=64)
-    assert [d[0] for d, _ in mg.level_shapes((256,) * 3, 1.0, **ex)] == [256, 128, 64, 32, 16]
-    assert [d[0] for d, _ in mg.level_shapes((160,) * 3, 1.0, **ex)] == [160, 80, 40, 20, 10]
-    assert [d for d, _ in mg.level_shapes((16, 16, 16), 1.0, **ex)] == [(16,) * 3]
+    # the FP32 V-cycle's hierarchy: it ends at the first level of <= 32768 cells with no side above 64
+    ex = dict(exact_cells=32768, exact_side=64)
+    assert [d[0] for d, _ in mg.level_shapes((256,) * 3, 1.0, **ex)] == [256, 128, 64, 32]
+    assert [d[0] for d, _ in mg.level_shapes((160,) * 3, 1.0, **ex)] == [160, 80, 40, 20]
+    assert [d for d, _ in mg.level_shapes((32, 32, 32), 1.0, **ex)] == [(32,) * 3]
     # no level qualifies (a side stays above 64): the full hierarchy
     assert [d for d, _ in mg.level_shapes((256, 8, 2), 1.0, **ex)] == [(256, 8, 2)]
 
 
-@pytest.mark.parametrize("exact", [{}, dict(exact_cells=4096, exact_side=64)])
+@pytest.mark.parametrize("exact", [{}, dict(exact_cells=32768, exact_side=64)])
 @pytest.mark.parametrize("alpha", [0.0, 0.05])
 def test_vcycle_fixed_point_and_reduction(alpha, exact):
     """A V-cycle started from the exact solution returns it; from zero it
