@@ -359,10 +359,11 @@ int vcycle_level(ibrd_grid g, int l, const T* b, const double* bshift, T* x, boo
   T* oth = H.y[l];
   bool first = zero;
   int np = 0;
-  if (sizeof(T) == 4 && nu1 == 1 && zero && zero_restrict_ok(lv.d) && lv.d.n() <= (size_t(1) << 18)) {
-    // the single pre-smoothing sweep from zero and the restriction in one
-    // pass (levels up to 64^3 cells: launch latency dominates there; larger
-    // levels run faster as the two streaming kernels)
+  if (sizeof(T) == 4 && nu1 == 1 && zero && zero_restrict_ok(lv.d) && aligned16(b) && aligned16(cur) &&
+      lv.d.n() <= (size_t(1) << 21)) {
+    // the single pre-smoothing sweep from zero and the restriction in one pass
+    // (levels up to 128^3 cells; on larger ones the kernel is bound by its
+    // shared-memory traffic and the two streaming kernels are faster)
     launch_zero_restrict(reinterpret_cast<const float*>(b), bshift, reinterpret_cast<float*>(cur),
                          reinterpret_cast<float*>(H.b[l + 1]), lv.d, st, g->s);
   } else {

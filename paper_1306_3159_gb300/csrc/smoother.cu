@@ -453,139 +453,157 @@ __global__ void __launch_bounds__(256) k_rb_zero_f32v(const float* __restrict__ 
 // One pre-smoothing sweep from x = 0 followed by the residual restriction,
 // FP32, in one pass: x = first red-black sweep of A x = b - shift (the
 // stencil of k_rb_zero_f32v) and bc = mean over the 8 children of
-// b - shift - A x. A CTA owns a 32 x 8 tile of cells and marches in z over zc
-// planes (zc even, chunks start on even planes). Shared-memory rings hold
-// b - shift and r = (b - shift) / diag on the tile plus a 2-cell halo (4
-// planes) and x on the tile plus a 1-cell halo (3 planes). Step k loads b
-// plane k+2, forms x on plane k+1, then the residual on plane k, writes x and,
-// on odd k, the coarse cells of planes (k-1, k). Needs nx % 32 == 0,
-// ny % 8 == 0, nz even.
-constexpr int kZR_TX = 32, kZR_TY = 8;
-constexpr int kZR_BW = kZR_TX + 4, kZR_BH = kZR_TY + 4;  // b tile with 2-cell halo
-constexpr int kZR_XW = kZR_TX + 2, kZR_XH = kZR_TY + 2;  // x tile with 1-cell halo
+// b - shift - A x. A CTA of 8 x TX4 threads owns a tile of 8 rows x 4 TX4
+// cells (one 4-vector per thread) and marches in z over zc planes (zc even,
+// chunks start on even planes). b planes (the tile with a halo of 2 vectors
+// in x and 2 rows in y) arrive in a ring of 8 by 16-byte cp.async, kZR_D
+// planes ahead of use; x (tile with a halo of 1 vector and 1 row) is formed in
+// a ring of 4. Phase p forms x on plane p+1 and, in the same phase, the
+// residual on plane p-1 (it reads x planes p-2 .. p, formed in earlier
+// phases), so one barrier per plane suffices; it writes x of plane p-1 and,
+// when p-1 is odd, the coarse cells of planes (p-2, p-1): x pairs within a
+// thread, y pairs across lanes TX4 apart, z pairs in registers.
+// Needs nx % (4 TX4) == 0, ny % 8 == 0, nz even.
+constexpr int kZR_D = 4;
 
-__global__ void __launch_bounds__(kZR_TX* kZR_TY) k_zero_restrict_f32(const float* __restrict__ b,
-                                                                      const double* __restrict__ bshift,
-                                                                      float* __restrict__ x, float* __restrict__ bc,
-                                                                      int nx, int ny, int nz, int zc, float inv,
-                                                                      float off, float diag) {
-  constexpr int NT = kZR_TX * kZR_TY;
-  constexpr int NB = kZR_BH * kZR_BW, NX = kZR_XH * kZR_XW;  // 432 and 340: at most 2 per thread
-  static_assert(NB <= 2 * NT && NX <= 2 * NT, "two ring entries per thread");
-  __shared__ float BS[4][NB];
-  __shared__ float RB[4][NB];
-  __shared__ float XS[3][NX];
-  __shared__ float RS[kZR_TY][kZR_TX];
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kZR_TX + tx;
-  const int x0 = blockIdx.x * kZR_TX, y0 = blockIdx.y * kZR_TY;
+template <int TX4>
+__global__ void __launch_bounds__(TX4 * 8) k_zero_restrict_f32(const float* __restrict__ b,
+                                                               const double* __restrict__ bshift,
+                                                               float* __restrict__ x, float* __restrict__ bc, int nx,
+                                                               int ny, int nz, int zc, float inv, float off,
+                                                               float diag) {
+  constexpr int TY = 8, NT = TX4 * TY, RB = 8, D = kZR_D;
+  constexpr int BW4 = TX4 + 4, BH = TY + 4;  // b tile (4-vectors), halo 2 vectors / 2 rows
+  constexpr int XW4 = TX4 + 2, XH = TY + 2;  // x tile, halo 1 vector / 1 row
+  constexpr int NB = BH * BW4, NX = XH * XW4;
+  constexpr int QB = (NB + NT - 1) / NT, QX = (NX + NT - 1) / NT;
+  static_assert(QB <= 3 && QX <= 2 && 32 % TX4 == 0 && D + 3 <= RB, "roles");
+  extern __shared__ __align__(16) float4 zr_smem[];
+  float4* BSM = zr_smem;           // RB planes of NB raw b values
+  float4* XSM = zr_smem + RB * NB;  // 4 planes of NX x values
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX4 + tx;
+  const int x0 = blockIdx.x * 4 * TX4, y0 = blockIdx.y * TY;
   const int k0 = blockIdx.z * zc;
   const int k1 = min(k0 + zc, nz);
   if (k0 >= k1) return;
   const float sh = bshift ? (float)(*bshift) : 0.f;
   const size_t plane = (size_t)nx * ny;
   auto wz = [&](int p) { return p < 0 ? p + nz : (p >= nz ? p - nz : p); };
-  // ring slots follow the unwrapped plane index (k0 - 2 <= p <= k1 + 1), so
+  // x ring slots follow the unwrapped plane index (k0 - 1 <= p <= k1), so
   // consecutive planes never share a slot at the periodic seam
-  auto xslot = [](int p) {
-    const int m = p % 3;
-    return m < 0 ? m + 3 : m;
-  };
-  // this thread's b ring entries (tile + 2-cell halo, periodic): in-plane offsets
-  int boff[2];
-  bool bval[2];
+  auto xslot = [](int p) { return p & 3; };
+  auto bslot = [&](int p) { return BSM + (p & (RB - 1)) * NB; };
+  // this thread's b copies: in-plane offsets (periodic)
+  int boff[QB];
+  bool bval[QB];
 #pragma unroll
-  for (int q = 0; q < 2; ++q) {
+  for (int q = 0; q < QB; ++q) {
     const int e = tid + q * NT;
     bval[q] = e < NB;
-    const int row = e / kZR_BW, col = e - row * kZR_BW;
-    boff[q] = bval[q] ? wrap(y0 - 2 + row, ny) * nx + wrap(x0 - 2 + col, nx) : 0;
+    const int row = e / BW4, c4 = e - row * BW4;
+    boff[q] = bval[q] ? wrap(y0 - 2 + row, ny) * nx + wrap(x0 - 8 + 4 * c4, nx) : 0;
   }
-  // this thread's x ring entries (tile + 1-cell halo): ring index of the
-  // cell in the b tile, and the in-plane parity
-  int xr[2], xpar[2];
-  bool xval[2];
+  // this thread's x entries: position in the b tile and parity of element 0
+  int xob[QX], xpar[QX];
+  bool xval[QX];
 #pragma unroll
-  for (int q = 0; q < 2; ++q) {
+  for (int q = 0; q < QX; ++q) {
     const int e = tid + q * NT;
     xval[q] = e < NX;
-    const int row = e / kZR_XW, col = e - row * kZR_XW;
-    xr[q] = (row + 1) * kZR_BW + col + 1;
-    xpar[q] = ((x0 - 1 + col) + (y0 - 1 + row)) & 1;  // the even-period wrap keeps parity
+    const int row = e / XW4, c4 = e - row * XW4;
+    xob[q] = (row + 1) * BW4 + c4 + 1;
+    xpar[q] = ((x0 - 4 + 4 * c4) + (y0 - 1 + row)) & 1;  // the even-period wrap keeps parity
   }
-  float pre[2];
-  auto fetch_b = [&](int p) {
+  // b plane p into its ring slot (one commit group per plane)
+  auto copy_b = [&](int p) {
     const float* bp = b + (size_t)wz(p) * plane;
+    float4* dst = bslot(p);
 #pragma unroll
-    for (int q = 0; q < 2; ++q) pre[q] = bval[q] ? bp[boff[q]] : 0.f;
+    for (int q = 0; q < QB; ++q)
+      if (bval[q]) cp_async16(dst + tid + q * NT, bp + boff[q]);
+    cp_async_commit();
   };
-  auto store_b = [&](int p) {
-    const int sl = p & 3;
-#pragma unroll
-    for (int q = 0; q < 2; ++q)
-      if (bval[q]) {
-        const float v = pre[q] - sh;
-        BS[sl][tid + q * NT] = v;
-        RB[sl][tid + q * NT] = v * inv;
-      }
-  };
-  // x on plane p: red cells r, black cells one update from their red
-  // neighbours (same expression as the other sweep kernels)
+  auto el = [](const float4& v, int e) { return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w)); };
+  // x on plane p: red cells r = (b - shift) / diag, black cells one update
+  // from their red neighbours (same expression as the other sweep kernels)
   auto comp_x = [&](int p) {
-    const int sl = p & 3, slm = (p + 3) & 3, slp = (p + 1) & 3, xs = xslot(p);
+    const float4 *Bc = bslot(p), *Bm = bslot(p - 1), *Bp = bslot(p + 1);
+    float4* xs = XSM + xslot(p) * NX;
     const int pp = wz(p) & 1;
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
+    for (int q = 0; q < QX; ++q) {
       if (!xval[q]) continue;
-      const int o = xr[q];
-      float v;
-      if (((xpar[q] + pp) & 1) == 0) {
-        v = RB[sl][o];
-      } else {
-        const float sum = ((RB[sl][o - 1] + RB[sl][o + 1]) + (RB[sl][o - kZR_BW] + RB[sl][o + kZR_BW])) +
-                          (RB[slm][o] + RB[slp][o]);
-        v = (BS[sl][o] + off * sum) * inv;
+      const int o = xob[q];
+      const float4 c = Bc[o], u = Bc[o - BW4], dn = Bc[o + BW4], zm = Bm[o], zp = Bp[o];
+      const float lw = Bc[o - 1].w, rx = Bc[o + 1].x;
+      auto r = [&](float v) { return (v - sh) * inv; };
+      float out[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float ce = el(c, e) - sh;
+        if (((xpar[q] + e + pp) & 1) == 0) {
+          out[e] = ce * inv;
+        } else {
+          const float L = r(e == 0 ? lw : el(c, e - 1)), R = r(e == 3 ? rx : el(c, e + 1));
+          const float sum = ((L + R) + (r(el(u, e)) + r(el(dn, e)))) + (r(el(zm, e)) + r(el(zp, e)));
+          out[e] = (ce + off * sum) * inv;
+        }
       }
-      XS[xs][tid + q * NT] = v;
+      xs[tid + q * NT] = make_float4(out[0], out[1], out[2], out[3]);
     }
   };
-  // prologue: b planes k0 - 2 .. k0 + 1 and x planes k0 - 1, k0
-  for (int p = k0 - 2; p <= k0 + 1; ++p) {
-    fetch_b(p);
-    store_b(p);
-  }
-  fetch_b(k0 + 2);  // in flight during the prologue's x planes
+  // prologue: b planes k0 - 2 .. k0 + D + 1 in flight; x planes k0 - 1, k0
+  for (int p = k0 - 2; p <= k0 + D + 1; ++p) copy_b(p);
+  cp_async_wait<D>();  // planes up to k0 + 1 landed
   __syncthreads();
   comp_x(k0 - 1);
   comp_x(k0);
-  __syncthreads();  // b plane k0 - 2 (read above) shares its slot with plane k0 + 2
-  float acc = 0.f;  // coarse-cell sum over the even plane (threads with even tx, ty)
-  const int c = (ty + 1) * kZR_XW + tx + 1;  // this thread's tile cell in the x ring
-  for (int k = k0; k < k1; ++k) {
-    store_b(k + 2);
-    if (k + 3 <= k1 + 1) fetch_b(k + 3);  // next plane's b in flight during this step
+  float acc0 = 0.f, acc1 = 0.f;  // coarse sums over the even plane (threads with even ty)
+  const int ox = (ty + 1) * XW4 + tx + 1;  // this thread's tile group in the x ring
+  const int ob = (ty + 2) * BW4 + tx + 2;  // and in the b ring
+  const int nxc = nx >> 1, nyc = ny >> 1;
+  for (int p = k0; p <= k1; ++p) {
+    // b plane p + 2 landed; planes p + 3 .. p + D + 1 may still be in flight
+    cp_async_wait<D - 1>();
     __syncthreads();
-    comp_x(k + 1);
-    __syncthreads();
-    const int sm = xslot(k - 1), s0 = xslot(k), sp = xslot(k + 1);
-    const float xc = XS[s0][c];
-    const float sum = ((XS[s0][c - 1] + XS[s0][c + 1]) + (XS[s0][c - kZR_XW] + XS[s0][c + kZR_XW])) +
-                      (XS[sm][c] + XS[sp][c]);
-    const float res = BS[k & 3][(ty + 2) * kZR_BW + tx + 2] - (diag * xc - off * sum);
-    x[(size_t)k * plane + (size_t)(y0 + ty) * nx + x0 + tx] = xc;
-    // 2 x 2 in-plane sum: x pairs are neighbouring lanes, y pairs neighbouring warps
-    const float px = res + __shfl_xor_sync(0xffffffffu, res, 1);
-    RS[ty][tx] = px;
-    __syncthreads();
-    if (((tx | ty) & 1) == 0) {
-      const float q = RS[ty][tx] + RS[ty + 1][tx];
+    // plane p + D + 2 takes the slot of plane p + D - 6, last read in phase
+    // p - 1 (ring planes in use: p - 1 .. p + D + 2)
+    if (p + D + 2 <= k1 + 1)
+      copy_b(p + D + 2);
+    else
+      cp_async_commit();  // keep one group per phase
+    if (p + 1 <= k1) comp_x(p + 1);
+    const int k = p - 1;
+    if (k < k0) continue;
+    const float4* xm = XSM + xslot(k - 1) * NX;
+    const float4* xc = XSM + xslot(k) * NX;
+    const float4* xp = XSM + xslot(k + 1) * NX;
+    const float4 c = xc[ox], u = xc[ox - XW4], dn = xc[ox + XW4], zm = xm[ox], zp = xp[ox];
+    const float lw = xc[ox - 1].w, rx = xc[ox + 1].x;
+    const float4 bb = bslot(k)[ob];
+    float res[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float L = e == 0 ? lw : el(c, e - 1), R = e == 3 ? rx : el(c, e + 1);
+      const float sum = ((L + R) + (el(u, e) + el(dn, e))) + (el(zm, e) + el(zp, e));
+      res[e] = (el(bb, e) - sh) - (diag * el(c, e) - off * sum);
+    }
+    *reinterpret_cast<float4*>(x + (size_t)k * plane + (size_t)(y0 + ty) * nx + x0 + 4 * tx) = c;
+    // x pairs in the thread, y pairs across lanes TX4 apart (same warp)
+    float p0 = res[0] + res[1], p1 = res[2] + res[3];
+    p0 += __shfl_down_sync(0xffffffffu, p0, TX4);
+    p1 += __shfl_down_sync(0xffffffffu, p1, TX4);
+    if ((ty & 1) == 0) {
       if ((k & 1) == 0) {
-        acc = q;
+        acc0 = p0;
+        acc1 = p1;
       } else {
-        const int nxc = nx >> 1, nyc = ny >> 1;
-        bc[((size_t)(k >> 1) * nyc + ((y0 + ty) >> 1)) * nxc + ((x0 + tx) >> 1)] = (acc + q) * 0.125f;
+        float* dst = bc + ((size_t)(k >> 1) * nyc + ((y0 + ty) >> 1)) * nxc + (x0 >> 1) + 2 * tx;
+        *reinterpret_cast<float2*>(dst) = make_float2((acc0 + p0) * 0.125f, (acc1 + p1) * 0.125f);
       }
     }
   }
+  cp_async_wait<0>();
 }
 
 // Thread per coarse cell: adds the trilinear cell-centred interpolation of
@@ -1020,21 +1038,37 @@ void launch_resid_restrict(const T* x, const T* b, const double* bshift, T* bc, 
   prof_end(c, s, "resid_restrict", 2.125 * sizeof(T) * d.n());
 }
 
-bool zero_restrict_ok(Dims d) { return d.nx % kZR_TX == 0 && d.ny % kZR_TY == 0 && d.nz % 2 == 0 && d.nz >= 4; }
+bool zero_restrict_ok(Dims d) { return d.nx % 32 == 0 && d.ny % 8 == 0 && d.nz % 2 == 0 && d.nz >= 4; }
 
-void launch_zero_restrict(const float* b, const double* bshift, float* x, float* bc, Dims d, Stencil st,
+template <int TX4>
+void zero_restrict_launch(const float* b, const double* bshift, float* x, float* bc, Dims d, Stencil st,
                           cudaStream_t s) {
-  const int bx = d.nx / kZR_TX, by = d.ny / kZR_TY;
-  // about one wave of 8 resident CTAs per SM; chunks of an even number of planes
-  int chunks = (152 * 8) / (bx * by);
+  const int bx = d.nx / (4 * TX4), by = d.ny / 8;
+  // about one wave of 5 resident CTAs per SM (shared-memory rings); chunks of
+  // an even number of planes
+  int chunks = (152 * 5) / (bx * by);
   chunks = chunks < 1 ? 1 : chunks;
   int zc = (d.nz + chunks - 1) / chunks;
   zc += zc & 1;
   zc = zc < 2 ? 2 : zc;
   dim3 g(bx, by, (d.nz + zc - 1) / zc);
+  constexpr size_t sm = sizeof(float4) * (8 * (8 + 4) * (TX4 + 4) + 4 * (8 + 2) * (TX4 + 2));
+  static bool attr = false;
+  if (!attr) {
+    IBRD_CUDA(cudaFuncSetAttribute(k_zero_restrict_f32<TX4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    attr = true;
+  }
+  k_zero_restrict_f32<TX4><<<g, dim3(TX4, 8), sm, s>>>(b, bshift, x, bc, d.nx, d.ny, d.nz, zc, (float)(1.0 / st.diag),
+                                                        (float)st.off, (float)st.diag);
+}
+
+void launch_zero_restrict(const float* b, const double* bshift, float* x, float* bc, Dims d, Stencil st,
+                          cudaStream_t s) {
   prof_begin(P_RBGS32, s);
-  k_zero_restrict_f32<<<g, dim3(kZR_TX, kZR_TY), 0, s>>>(b, bshift, x, bc, d.nx, d.ny, d.nz, zc,
-                                                          (float)(1.0 / st.diag), (float)st.off, (float)st.diag);
+  if (d.nx % 64 == 0)
+    zero_restrict_launch<16>(b, bshift, x, bc, d, st, s);
+  else
+    zero_restrict_launch<8>(b, bshift, x, bc, d, st, s);
   // one read of b, one write of x and of the coarse right-hand side
   prof_end(P_RBGS32, s, "zero_restrict", 8.0 * d.n() + 0.5 * d.n());
 }
