@@ -21,3 +21,16 @@ def rel_l2(a, b):
     a = np.asarray(a).ravel()
     b = np.asarray(b).ravel()
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+EPS = 2.220446049250313e-16
+
+
+def floor_tol(c_ref, g, h, chi, alpha, base=1e-12):
+    """Relative-residual tolerance at the FP64 rounding floor: A c is formed
+    from values of size max|c|, so each cell of the residual carries about
+    eps (alpha + 12 chi/h^2) max|c| of rounding; relative to the rms of g that
+    is the floor. A few times it, and never below `base`."""
+    rms = float(np.sqrt(np.mean(np.asarray(g) ** 2)))
+    fl = 4.0 * EPS * (alpha + 12.0 * chi / h ** 2) * float(np.abs(c_ref).max()) / rms
+    return max(base, fl)
