@@ -209,6 +209,31 @@ ibrd_status ibrd_solve_reaction(ibrd_grid g, const double* kappa, const double* 
 ibrd_status ibrd_solve_saddle(ibrd_grid g, const double* rhs, const double* f, double* c,
                               double* lambda, const ibrd_solve_opts* opts, ibrd_solve_info* info);
 
+/* Batched solves: count independent problems, problem i on handle grids[i]
+   with its own grid size, blobs and stream (e.g. the disordered suspensions of
+   Sec. IV.B, one realisation per handle). Each problem is solved exactly as
+   the single-problem call would solve it, with the same result. The library
+   runs the solves on `threads` host threads of its own (<= 0: 16; never more
+   than count or 64), taking the problems with the most cells and blobs first;
+   solves on handles whose streams differ (give each handle its own
+   non-blocking stream) overlap on the GPU. Handles must be distinct and
+   non-NULL (else IBRD_ERR_ARG before any work). kappa, rhs, f, c and lambda
+   are HOST arrays of count device pointers, entry i meaning what the
+   single-problem argument means for problem i; f may be NULL (all f = 0), as
+   may any f[i]. opts (shared by all problems) may be NULL. infos, if non-NULL,
+   is an array of count reports; infos[i].status is set for every problem,
+   also when its solve fails. Returns the first non-OK status in index order
+   (every problem is still attempted); the message is on that problem's
+   handle. Returns after every solve has finished and synchronized its
+   stream. */
+ibrd_status ibrd_solve_reaction_batch(int count, const ibrd_grid* grids, const double* const* kappa,
+                                      const double* const* rhs, double* const* c,
+                                      const ibrd_solve_opts* opts, ibrd_solve_info* infos, int threads);
+
+ibrd_status ibrd_solve_saddle_batch(int count, const ibrd_grid* grids, const double* const* rhs,
+                                    const double* const* f, double* const* c, double* const* lambda,
+                                    const ibrd_solve_opts* opts, ibrd_solve_info* infos, int threads);
+
 /* Launch profiler (not in the paper: instrumentation of this library).
    Every kernel the library launches is counted per kernel class; with timing
    enabled each launch is also bracketed by CUDA events on the handle's stream,

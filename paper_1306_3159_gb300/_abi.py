@@ -21,6 +21,7 @@ STATUS = {0: "IBRD_OK", 1: "IBRD_ERR_ARG", 2: "IBRD_ERR_CUDA", 3: "IBRD_ERR_OOM"
 # Every entry point declared in include/ibrd.h.
 EXPORTED = ["ibrd_default_opts", "ibrd_grid_create", "ibrd_grid_destroy", "ibrd_set_blobs", "ibrd_apply_L",
             "ibrd_vcycle", "ibrd_vcycle_f32", "ibrd_vcycle_noalloc", "ibrd_spread", "ibrd_interp", "ibrd_solve_reaction", "ibrd_solve_saddle",
+            "ibrd_solve_reaction_batch", "ibrd_solve_saddle_batch",
             "ibrd_last_error", "ibrd_status_string", "ibrd_profile_enable", "ibrd_profile_read",
             "ibrd_profile_class_name"]
 
@@ -90,6 +91,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ibrd_solve_reaction.restype = i
     lib.ibrd_solve_saddle.argtypes = [vp, vp, vp, vp, vp, P(SolveOpts), P(SolveInfo)]
     lib.ibrd_solve_saddle.restype = i
+    lib.ibrd_solve_reaction_batch.argtypes = [i, P(vp), P(vp), P(vp), P(vp), P(SolveOpts), P(SolveInfo), i]
+    lib.ibrd_solve_reaction_batch.restype = i
+    lib.ibrd_solve_saddle_batch.argtypes = [i, P(vp), P(vp), P(vp), P(vp), P(vp), P(SolveOpts), P(SolveInfo), i]
+    lib.ibrd_solve_saddle_batch.restype = i
     lib.ibrd_last_error.argtypes = [vp]
     lib.ibrd_last_error.restype = ctypes.c_char_p
     lib.ibrd_status_string.argtypes = [i]
@@ -218,6 +223,68 @@ def ibrd_solve_saddle(g, rhs, f, c, lam, opts: SolveOpts | None = None, history_
     out = _info_dict(info, hist)
     out["status"] = st
     return out
+
+
+def _ptr_array(items, dtype="float64"):
+    arr = (ctypes.c_void_p * max(1, len(items)))()
+    for k, t in enumerate(items):
+        p = _ptr(t, dtype)
+        arr[k] = p.value if p is not None else None
+    return arr
+
+
+def _handles(grids):
+    vals = [g.value if isinstance(g, ctypes.c_void_p) else g for g in grids]
+    return (ctypes.c_void_p * max(1, len(vals)))(*vals)
+
+
+def _batch_infos(count, history_cap):
+    import numpy as np
+    infos = (SolveInfo * max(1, count))()
+    hists = []
+    for k in range(count):
+        h = np.zeros(max(1, history_cap), dtype=np.float64)
+        infos[k].residual_history = h.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        infos[k].history_cap = history_cap
+        hists.append(h)
+    return infos, hists
+
+
+def _batch_result(grids, st, infos, hists, raise_on_error):
+    out = [_info_dict(infos[k], hists[k]) for k in range(len(grids))]
+    if raise_on_error and st != 0:
+        bad = next((k for k, r in enumerate(out) if r["status"] != 0), None)
+        raise IbrdError(st, f"problem {bad}: " + (ibrd_last_error(grids[bad]) if bad is not None else ""))
+    return out
+
+
+def ibrd_solve_reaction_batch(grids, kappa, rhs, c, opts: SolveOpts | None = None, threads=0, history_cap=0,
+                              raise_on_error=True):
+    """Solve len(grids) reaction problems concurrently; lists of per-problem tensors."""
+    n = len(grids)
+    if not (len(kappa) == len(rhs) == len(c) == n):
+        raise ValueError("one kappa, rhs and c per handle")
+    infos, hists = _batch_infos(n, history_cap)
+    hs = _handles(grids)
+    st = load_library().ibrd_solve_reaction_batch(n, hs, _ptr_array(kappa), _ptr_array(rhs), _ptr_array(c),
+                                                  ctypes.byref(opts) if opts is not None else None, infos,
+                                                  int(threads))
+    return _batch_result(grids, st, infos, hists, raise_on_error)
+
+
+def ibrd_solve_saddle_batch(grids, rhs, f, c, lam, opts: SolveOpts | None = None, threads=0, history_cap=0,
+                            raise_on_error=True):
+    """Solve len(grids) saddle-point problems concurrently; f may be None."""
+    n = len(grids)
+    if not (len(rhs) == len(c) == len(lam) == n) or (f is not None and len(f) != n):
+        raise ValueError("one rhs, c and lambda (and f) per handle")
+    infos, hists = _batch_infos(n, history_cap)
+    hs = _handles(grids)
+    st = load_library().ibrd_solve_saddle_batch(n, hs, _ptr_array(rhs), _ptr_array(f) if f is not None else None,
+                                                _ptr_array(c), _ptr_array(lam),
+                                                ctypes.byref(opts) if opts is not None else None, infos,
+                                                int(threads))
+    return _batch_result(grids, st, infos, hists, raise_on_error)
 
 
 PROF_ALL = (1 << PROF_NCLASS) - 1

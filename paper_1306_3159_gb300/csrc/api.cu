@@ -6,6 +6,7 @@
 // blob_kernels.cu and krylov_kernels.cu; the host only sequences launches and
 // reads back scalars (norms, residual estimates) to steer the iteration.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -13,6 +14,7 @@
 #include <map>
 #include <new>
 #include <string>
+#include <thread>
 #include <type_traits>
 #include <utility>
 #include <vector>
@@ -1143,6 +1145,47 @@ void fill_info(ibrd_solve_info* info, const SolveResult& R, ibrd_grid g, double 
   info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count() - t0;
 }
 
+// Runs solve(i) for every i in [0, count) on `threads` host threads, largest
+// estimated work (cells plus a blob term) first so that the longest solves do
+// not start last. Each solve orders its GPU work on its own handle's stream, so
+// solves whose handles have distinct streams overlap on the device. Returns the
+// first non-OK status in index order.
+template <typename F>
+ibrd_status run_batch(int count, const ibrd_grid* grids, int threads, F&& solve) {
+  if (count < 0 || (count > 0 && !grids)) return IBRD_ERR_ARG;
+  if (count == 0) return IBRD_OK;
+  std::vector<ibrd_grid> seen(grids, grids + count);
+  std::sort(seen.begin(), seen.end());
+  for (int i = 0; i < count; ++i)
+    if (!seen[i] || (i > 0 && seen[i] == seen[i - 1])) return IBRD_ERR_ARG;  // null or shared handle
+  if (threads <= 0) threads = 16;
+  threads = std::max(1, std::min(std::min(threads, 64), count));
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  auto cost = [&](int i) { return (double)grids[i]->d.n() + 512.0 * grids[i]->blobs.n; };
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
+  std::vector<ibrd_status> st(count, IBRD_OK);
+  std::atomic<int> next{0};
+  auto worker = [&]() {
+    for (;;) {
+      const int k = next.fetch_add(1, std::memory_order_relaxed);
+      if (k >= count) return;
+      st[order[k]] = solve(order[k]);
+    }
+  };
+  std::vector<std::thread> pool;
+  try {
+    for (int t = 1; t < threads; ++t) pool.emplace_back(worker);
+  } catch (...) {
+    // fewer threads than asked: the calling thread and those started share the queue
+  }
+  worker();
+  for (auto& th : pool) th.join();
+  for (int i = 0; i < count; ++i)
+    if (st[i] != IBRD_OK) return st[i];
+  return IBRD_OK;
+}
+
 double now_s() { return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count(); }
 
 // sum over all cells and N-vector reductions for the report
@@ -1475,6 +1518,30 @@ ibrd_status ibrd_solve_saddle(ibrd_grid g, const double* rhs, const double* f, d
     fill_info(info, R, g, t0);
     if (R.st != IBRD_OK) g->err = std::string("ibrd_solve_saddle: ") + ibrd_status_string(R.st);
     return R.st;
+  });
+}
+
+ibrd_status ibrd_solve_reaction_batch(int count, const ibrd_grid* grids, const double* const* kappa,
+                                      const double* const* rhs, double* const* c, const ibrd_solve_opts* opts,
+                                      ibrd_solve_info* infos, int threads) {
+  if (count > 0 && (!kappa || !rhs || !c)) return IBRD_ERR_ARG;
+  return run_batch(count, grids, threads, [&](int i) {
+    ibrd_solve_info* info = infos ? infos + i : nullptr;
+    const ibrd_status st = ibrd_solve_reaction(grids[i], kappa[i], rhs[i], c[i], opts, info);
+    if (info) info->status = st;
+    return st;
+  });
+}
+
+ibrd_status ibrd_solve_saddle_batch(int count, const ibrd_grid* grids, const double* const* rhs,
+                                    const double* const* f, double* const* c, double* const* lambda,
+                                    const ibrd_solve_opts* opts, ibrd_solve_info* infos, int threads) {
+  if (count > 0 && (!rhs || !c || !lambda)) return IBRD_ERR_ARG;
+  return run_batch(count, grids, threads, [&](int i) {
+    ibrd_solve_info* info = infos ? infos + i : nullptr;
+    const ibrd_status st = ibrd_solve_saddle(grids[i], rhs[i], f ? f[i] : nullptr, c[i], lambda[i], opts, info);
+    if (info) info->status = st;
+    return st;
   });
 }
 

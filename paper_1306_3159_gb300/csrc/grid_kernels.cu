@@ -701,12 +701,9 @@ void launch_hartley_solve(const float* tab, const float* b, const double* bshift
   const size_t pn = (size_t)(d.nx + 1) * (d.ny + 1) * d.nz;
   const size_t sm = sizeof(float) * ((size_t)d.nx * (d.nx + 1) + (size_t)d.ny * (d.ny + 1) +
                                      (size_t)d.nz * (d.nz + 1) + 2 * pn);
-  static bool attr = false;
-  if (!attr) {
-    IBRD_CUDA(cudaFuncSetAttribute(k_hartley_solve<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    IBRD_CUDA(cudaFuncSetAttribute(k_hartley_solve<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    attr = true;
-  }
+  static std::atomic<unsigned long long> attr0{0}, attr16{0};
+  ensure_smem_attr((const void*)k_hartley_solve<0>, 200 * 1024, attr0);
+  ensure_smem_attr((const void*)k_hartley_solve<16>, 200 * 1024, attr16);
   prof_begin(P_COARSE, s);
   if (d.nx == 16 && d.ny == 16 && d.nz == 16)
     k_hartley_solve<16><<<1, 1024, sm, s>>>(tab, b, bshift, x, d.nx, d.ny, d.nz);

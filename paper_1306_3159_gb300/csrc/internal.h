@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 #include <string>
@@ -28,6 +29,17 @@ struct CudaError {
 inline void check_launch(const char* what) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) throw CudaError{e, what};
+}
+
+// Raises the dynamic shared-memory limit of kernel f to `bytes` on the current
+// device, once per device (thread-safe; concurrent first calls both set it).
+inline void ensure_smem_attr(const void* f, int bytes, std::atomic<unsigned long long>& done) {
+  int dev = 0;
+  IBRD_CUDA(cudaGetDevice(&dev));
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (done.load(std::memory_order_acquire) & bit) return;
+  IBRD_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  done.fetch_or(bit, std::memory_order_release);
 }
 
 // 16-byte copies and vector accesses need 16-byte aligned fields; a caller's

@@ -934,11 +934,8 @@ template <typename T, int TX, bool ZERO>
 void sweep_launch(dim3 g, cudaStream_t s, const T* xin, T* xout, const T* b, const double* bshift, Dims d, int zc,
                   T inv, T off, double* part) {
   constexpr size_t sm = sweep_smem<T, TX, 8>();
-  static bool attr = false;
-  if (!attr) {
-    IBRD_CUDA(cudaFuncSetAttribute(k_rb_sweep<T, TX, 8, ZERO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    attr = true;
-  }
+  static std::atomic<unsigned long long> attr{0};
+  ensure_smem_attr((const void*)k_rb_sweep<T, TX, 8, ZERO>, (int)sm, attr);
   k_rb_sweep<T, TX, 8, ZERO><<<g, kSweepThreads, sm, s>>>(xin, xout, b, bshift, d.nx, d.ny, d.nz, zc, inv, off,
                                                            part);
 }
@@ -1053,11 +1050,8 @@ void zero_restrict_launch(const float* b, const double* bshift, float* x, float*
   zc = zc < 2 ? 2 : zc;
   dim3 g(bx, by, (d.nz + zc - 1) / zc);
   constexpr size_t sm = sizeof(float4) * (8 * (8 + 4) * (TX4 + 4) + 4 * (8 + 2) * (TX4 + 2));
-  static bool attr = false;
-  if (!attr) {
-    IBRD_CUDA(cudaFuncSetAttribute(k_zero_restrict_f32<TX4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    attr = true;
-  }
+  static std::atomic<unsigned long long> attr{0};
+  ensure_smem_attr((const void*)k_zero_restrict_f32<TX4>, (int)sm, attr);
   k_zero_restrict_f32<TX4><<<g, dim3(TX4, 8), sm, s>>>(b, bshift, x, bc, d.nx, d.ny, d.nz, zc, (float)(1.0 / st.diag),
                                                         (float)st.off, (float)st.diag);
 }
@@ -1098,11 +1092,8 @@ template <typename T>
 void launch_vcycle_small(const CoarseLevels& lv, const T* b, T* x, const double* bshift, const T* table, bool zero,
                          int nu1, int nu2, cudaStream_t s) {
   const size_t sm = 2 * sizeof(T) * (size_t)lv.total;
-  static bool attr = false;
-  if (!attr) {
-    IBRD_CUDA(cudaFuncSetAttribute(k_vcycle_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    attr = true;
-  }
+  static std::atomic<unsigned long long> attr{0};
+  ensure_smem_attr((const void*)k_vcycle_small<T>, 200 * 1024, attr);
   const int c = pcls<T>(P_RBGS64, P_RBGS32);
   prof_begin(c, s);
   k_vcycle_small<T><<<1, 1024, sm, s>>>(lv, b, x, bshift, table, zero ? 1 : 0, nu1, nu2);

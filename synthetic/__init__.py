@@ -12,7 +12,7 @@ placed by random sequential addition in place of the external hard-sphere
 packings of Sec. IV.C.
 """
 from .placement import (rsa_positions, lattice_positions, single_blob_position,
-                        loguniform_rates, uniform_source, Workload, workload)
+                        loguniform_rates, uniform_source, Workload, workload, batch_workloads)
 
 __all__ = ["rsa_positions", "lattice_positions", "single_blob_position",
-           "loguniform_rates", "uniform_source", "Workload", "workload"]
+           "loguniform_rates", "uniform_source", "Workload", "workload", "batch_workloads"]

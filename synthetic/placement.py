@@ -147,3 +147,21 @@ def workload(name: str) -> Workload:
     else:
         raise KeyError(name)
     return Workload(name, d, h, chi, q, kappa, uniform_source(d, 1.0))
+
+
+def batch_workloads(count: int, sides=(64, 96, 128, 160), n_lo: int = 16, n_hi: int = 2000,
+                    spacing: float = 3.0, seed: int = 11) -> list:
+    """Independent disordered-suspension realisations of uneven size: realisation
+    i has a cubic grid whose side is drawn uniformly from ``sides``, a blob count
+    drawn log-uniformly in [n_lo, n_hi] (rounded), RSA placement with minimum
+    centre spacing ``spacing`` h, rates log-uniform in [0.1, 10] and g = 1."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        side = int(sides[int(rng.integers(len(sides)))])
+        n = int(round(float(np.exp(rng.uniform(np.log(n_lo), np.log(n_hi))))))
+        d = (side, side, side)
+        q = rsa_positions(n, d, 1.0, spacing, seed * 1000 + 2 * i)
+        kappa = loguniform_rates(n, 0.1, 10.0, seed * 1000 + 2 * i + 1)
+        out.append(Workload(f"batch{i}", d, 1.0, 1.0, q, kappa, uniform_source(d, 1.0)))
+    return out

@@ -67,3 +67,17 @@ def test_no_oracle_import_in_product():
             if f.endswith((".py", ".cu", ".h", ".cuh")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
+
+
+def test_batch_rejects_bad_handles_without_touching_gpu(lib):
+    # The batch entry points check count and handles (null, shared) before any
+    # handle is dereferenced; the fake addresses below are never followed.
+    vp = ctypes.c_void_p
+    lib.ibrd_solve_reaction_batch.restype = ctypes.c_int
+    ptrs = (vp * 2)(vp(0x1000).value, vp(0x2000).value)
+    assert lib.ibrd_solve_reaction_batch(0, None, None, None, None, None, None, 0) == 0
+    assert lib.ibrd_solve_reaction_batch(-1, None, None, None, None, None, None, 0) == 1
+    for grids in [(vp * 2)(vp(0x1000).value, None), (vp * 2)(vp(0x1000).value, vp(0x1000).value)]:
+        assert lib.ibrd_solve_reaction_batch(2, grids, ptrs, ptrs, ptrs, None, None, 4) == 1
+        assert lib.ibrd_solve_saddle_batch(2, grids, ptrs, None, ptrs, ptrs, None, None, 4) == 1
+    assert lib.ibrd_solve_reaction_batch(2, ptrs, None, ptrs, ptrs, None, None, 0) == 1

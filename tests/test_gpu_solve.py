@@ -218,3 +218,43 @@ def test_graph_replay_matches_direct_launches(ibrd, small):
             assert np.array_equal(o[2], outs[0][2])
             assert o[3:] == outs[0][3:]
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("precision", [0, 2])
+def test_batch_matches_single_solves(ibrd, precision):
+    """Batched solves of uneven realisations (grid sides 32-64, 4-200 blobs),
+    each handle on its own stream and run concurrently from the library's host
+    threads, give bit for bit the iterates of the same solves run one at a
+    time; the smallest reaction problem also matches the oracle's exact
+    solution."""
+    import torch
+    from synthetic import batch_workloads
+    ws = batch_workloads(6, sides=(32, 40, 48, 64), n_lo=4, n_hi=200, seed=12)
+    streams = [torch.cuda.Stream() for _ in ws]
+    grids = [ibrd.Grid(*w.dims, h=w.h, chi=w.chi, stream=s.cuda_stream) for w, s in zip(ws, streams)]
+    qs, ks, gs = [dev(w.q) for w in ws], [dev(w.kappa) for w in ws], [dev(w.g) for w in ws]
+    cb = [torch.zeros_like(x) for x in gs]
+    cs = [torch.zeros_like(x) for x in gs]
+    lb = [torch.zeros(len(w.q), dtype=torch.float64, device="cuda") for w in ws]
+    c1s, c2s, l2s = [torch.zeros_like(x) for x in gs], [torch.zeros_like(x) for x in gs], [torch.zeros_like(x) for x in lb]
+    torch.cuda.synchronize()  # the handles' streams do not wait for torch's
+    for g, q in zip(grids, qs):
+        g.set_blobs(q)
+    opts = ibrd.ibrd_default_opts(tol=1e-10, precision=precision, max_iter=400)
+    hs = [g.handle for g in grids]
+    rb = ibrd.ibrd_solve_reaction_batch(hs, ks, gs, cb, opts, threads=4)
+    sb = ibrd.ibrd_solve_saddle_batch(hs, gs, None, cs, lb, opts, threads=3)
+    for i, g in enumerate(grids):
+        c1, c2, l2 = c1s[i], c2s[i], l2s[i]
+        r1 = ibrd.ibrd_solve_reaction(g.handle, ks[i], gs[i], c1, opts)
+        s1 = ibrd.ibrd_solve_saddle(g.handle, gs[i], None, c2, l2, opts)
+        assert torch.equal(c1, cb[i]) and torch.equal(c2, cs[i]) and torch.equal(l2, lb[i])
+        for a, b in ((r1, rb[i]), (s1, sb[i])):
+            assert a["status"] == b["status"] == 0
+            assert (a["outer_iters"], a["vcycles"], a["rel_residual"]) == (b["outer_iters"], b["vcycles"],
+                                                                            b["rel_residual"])
+    k = min(range(len(ws)), key=lambda i: ws[i].dims[0] ** 3 + len(ws[i].q))
+    w = ws[k]
+    c_ref, _, _ = direct.solve_reaction(w.q, w.kappa, w.g, w.h, w.chi, 0.0)
+    assert rel_l2(host(cb[k]), c_ref) < 1e-8
+    torch.cuda.synchronize()
