@@ -257,6 +257,9 @@ def run_ours(args):
         barrier()
         return max_over_ranks(e0.elapsed_time(e1) / 1e3 / k, world, "cuda")
 
+    # launch shapes of the sweep kernels chosen by the library's autotuner
+    # (setup, like graph capture: outside the timed region)
+    tune = [] if args.no_autotune else p.ibrd_autotune(grid.handle, p.IBRD_MIXED_REFINE)
     if args.ncu_step:
         # profiler range around one chosen step (ncu --profile-from-start off)
         for _ in range(args.warmup):
@@ -359,11 +362,14 @@ def run_ours(args):
                                      "speedup_vs_plain": round(t_plain / t_fk, 3)},
         "e2e": {"value": round(t_e2e, 6), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "roofline": roofline, "kernel_breakdown": breakdown, "clocks": clocks,
+        "autotune": [{"level": [r["nx"], r["ny"], r["nz"]], "kernel": ["sweep", "sweep_from_zero"][r["kind"]],
+                      "tx": r["tx"], "zc": r["zc"], "us_builtin": round(r["us_default"], 2),
+                      "us_kept": round(r["us_tuned"], 2)} for r in tune],
     }
     if not args.no_batched:
         grid.close()
         torch.cuda.empty_cache()
-        result["batched"] = run_batched(p, torch, world, args)
+        result["batched"] = run_batched(p, torch, world, args, tune=not args.no_autotune)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline_sample(columns=args.cpu_columns)
     if rank == 0:
@@ -376,7 +382,7 @@ def run_ours(args):
 BATCH_COUNT = 64
 
 
-def run_batched(p, torch, world, args):
+def run_batched(p, torch, world, args, tune=True):
     """Aggregate throughput of independent reaction solves: 64 realisations with
     grid sides drawn from {64, 96, 128, 160}, 16-2000 RSA blobs (spacing 3h),
     rates log-uniform in [0.1, 10], each on its own handle and stream, solved
@@ -395,6 +401,11 @@ def run_batched(p, torch, world, args):
     for g, q in zip(grids, qs):
         g.set_blobs(q)
     hs = [g.handle for g in grids]
+    t0 = time.perf_counter()
+    if tune:
+        for h in hs:
+            p.ibrd_autotune(h, p.IBRD_MIXED_REFINE)
+    t_tune = time.perf_counter() - t0
     opts = p.ibrd_default_opts(tol=1e-8, precision=p.IBRD_MIXED_REFINE, max_iter=3000, **CHOSEN_REACTION)
 
     def run(threads):
@@ -426,7 +437,8 @@ def run_batched(p, torch, world, args):
            "serial_ms_per_batch": round(t_serial * 1e3, 3), "concurrency_speedup": round(t_serial / t_conc, 3),
            "outer_iters_mean": round(sum(i["outer_iters"] for i in infos) / len(infos), 2),
            "outer_iters_max": max(i["outer_iters"] for i in infos),
-           "max_rel_residual": max(i["rel_residual"] for i in infos), "timing": "host wall clock around the "
+           "max_rel_residual": max(i["rel_residual"] for i in infos), "autotuned": tune,
+           "autotune_s": round(t_tune, 3), "timing": "host wall clock around the "
            "synchronous batch call (all streams finished), max over ranks"}
     for g in grids:
         g.close()
@@ -546,6 +558,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-realisations leg")
+    ap.add_argument("--no-autotune", action="store_true", help="built-in launch shapes only")
     ap.add_argument("--cpu-columns", type=int, default=3)
     ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--ncu-step", action="store_true", help="profiler range around one step, then exit")

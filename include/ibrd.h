@@ -234,6 +234,45 @@ ibrd_status ibrd_solve_saddle_batch(int count, const ibrd_grid* grids, const dou
                                     const double* const* f, double* const* c, double* const* lambda,
                                     const ibrd_solve_opts* opts, ibrd_solve_info* infos, int threads);
 
+/* Autotuner (not in the paper: launch-shape selection for this library's
+   kernels). For every multigrid level whose red-black sweeps (Sec. III.E) run
+   as the fused sweep kernel, times candidate launch shapes of that kernel --
+   tile width (32 or 64 cells in x, FP32) and z-march depth (planes per CTA,
+   1 to 512) -- and the z-march depth of the stencil pass that forms the first
+   sweep from a zero guess (FP32), on scratch fields of the level's size with
+   CUDA events, and keeps a shape only when it is at least 3 % faster than the
+   built-in one. Shapes tuned before in this process for the same device and
+   grid are reused without timing unless retune != 0. Every later call on the
+   handle launches the kept shapes; results can change in the last bits only
+   (per-CTA partial sums group differently). Drops the handle's captured CUDA
+   graphs. precision: IBRD_FP64 tunes the FP64 kernels, either mixed mode the
+   FP32 ones, -1 both. out (may be NULL if cap = 0) receives up to cap
+   records; *n_out (may be NULL) the number of records. Allocates three
+   scratch fields of the finest grid for the duration of the call.
+   Synchronizes the stream. */
+typedef struct {
+  int nx, ny, nz;    /* level grid */
+  int elem_bytes;    /* 4 (FP32) or 8 (FP64) */
+  int kind;          /* 0: fused sweep; 1: stencil pass of a sweep from zero */
+  int tx, zc;        /* kept tile width (0: built-in) and z-march depth (0: built-in) */
+  double us_default; /* average launch time of the built-in shape, microseconds */
+  double us_tuned;   /* average launch time of the kept shape */
+  int cached;        /* 1: reused from an earlier tuning in this process */
+} ibrd_tune_entry;
+
+ibrd_status ibrd_autotune(ibrd_grid g, int precision, int retune, ibrd_tune_entry* out, int cap, int* n_out);
+
+/* Set one launch shape by hand (as ibrd_autotune would keep it): elem_bytes
+   4 or 8, kind 0 or 1 as in ibrd_tune_entry, (nx, ny, nz) a level of the
+   handle's hierarchy, tx in {0, 32, 64} (0 for kind 1; 64 only for FP32 and
+   when 64 divides nx, else ignored), zc >= 0 (0 = built-in; clamped to the
+   level's nz). Drops the handle's captured CUDA graphs. */
+ibrd_status ibrd_tune_set(ibrd_grid g, int elem_bytes, int kind, int nx, int ny, int nz, int tx, int zc);
+
+/* Forget the handle's tuned shapes (back to the built-in ones); drops its
+   captured CUDA graphs. */
+ibrd_status ibrd_tune_clear(ibrd_grid g);
+
 /* Launch profiler (not in the paper: instrumentation of this library).
    Every kernel the library launches is counted per kernel class; with timing
    enabled each launch is also bracketed by CUDA events on the handle's stream,

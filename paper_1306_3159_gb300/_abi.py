@@ -21,7 +21,8 @@ STATUS = {0: "IBRD_OK", 1: "IBRD_ERR_ARG", 2: "IBRD_ERR_CUDA", 3: "IBRD_ERR_OOM"
 # Every entry point declared in include/ibrd.h.
 EXPORTED = ["ibrd_default_opts", "ibrd_grid_create", "ibrd_grid_destroy", "ibrd_set_blobs", "ibrd_apply_L",
             "ibrd_vcycle", "ibrd_vcycle_f32", "ibrd_vcycle_noalloc", "ibrd_spread", "ibrd_interp", "ibrd_solve_reaction", "ibrd_solve_saddle",
-            "ibrd_solve_reaction_batch", "ibrd_solve_saddle_batch",
+            "ibrd_solve_reaction_batch", "ibrd_solve_saddle_batch", "ibrd_autotune", "ibrd_tune_set",
+            "ibrd_tune_clear",
             "ibrd_last_error", "ibrd_status_string", "ibrd_profile_enable", "ibrd_profile_read",
             "ibrd_profile_class_name"]
 
@@ -49,6 +50,12 @@ class Profile(ctypes.Structure):
                 ("count", ctypes.c_longlong * PROF_NCLASS), ("timed", ctypes.c_longlong * PROF_NCLASS),
                 ("ms", ctypes.c_double * PROF_NCLASS), ("bytes", ctypes.c_double * PROF_NCLASS),
                 ("max_launch_bytes", ctypes.c_double * PROF_NCLASS), ("timed_bytes", ctypes.c_double * PROF_NCLASS)]
+
+
+class TuneEntry(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("elem_bytes", ctypes.c_int),
+                ("kind", ctypes.c_int), ("tx", ctypes.c_int), ("zc", ctypes.c_int), ("us_default", ctypes.c_double),
+                ("us_tuned", ctypes.c_double), ("cached", ctypes.c_int)]
 
 
 class IbrdError(RuntimeError):
@@ -95,6 +102,12 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ibrd_solve_reaction_batch.restype = i
     lib.ibrd_solve_saddle_batch.argtypes = [i, P(vp), P(vp), P(vp), P(vp), P(vp), P(SolveOpts), P(SolveInfo), i]
     lib.ibrd_solve_saddle_batch.restype = i
+    lib.ibrd_autotune.argtypes = [vp, i, i, P(TuneEntry), i, P(i)]
+    lib.ibrd_autotune.restype = i
+    lib.ibrd_tune_set.argtypes = [vp, i, i, i, i, i, i, i]
+    lib.ibrd_tune_set.restype = i
+    lib.ibrd_tune_clear.argtypes = [vp]
+    lib.ibrd_tune_clear.restype = i
     lib.ibrd_last_error.argtypes = [vp]
     lib.ibrd_last_error.restype = ctypes.c_char_p
     lib.ibrd_status_string.argtypes = [i]
@@ -285,6 +298,24 @@ def ibrd_solve_saddle_batch(grids, rhs, f, c, lam, opts: SolveOpts | None = None
                                                 ctypes.byref(opts) if opts is not None else None, infos,
                                                 int(threads))
     return _batch_result(grids, st, infos, hists, raise_on_error)
+
+
+def ibrd_autotune(g, precision=-1, retune=False, cap=64) -> list:
+    """Tune the sweep kernels' launch shapes for handle g; one dict per
+    (level, precision, kernel) tuned."""
+    arr = (TuneEntry * cap)()
+    n = ctypes.c_int(0)
+    _check(g, load_library().ibrd_autotune(g, int(precision), int(bool(retune)), arr, cap, ctypes.byref(n)))
+    return [{f: getattr(arr[k], f) for f, _ in TuneEntry._fields_} for k in range(min(n.value, cap))]
+
+
+def ibrd_tune_set(g, elem_bytes, kind, nx, ny, nz, tx, zc):
+    _check(g, load_library().ibrd_tune_set(g, int(elem_bytes), int(kind), int(nx), int(ny), int(nz), int(tx),
+                                           int(zc)))
+
+
+def ibrd_tune_clear(g):
+    _check(g, load_library().ibrd_tune_clear(g))
 
 
 PROF_ALL = (1 << PROF_NCLASS) - 1

@@ -12,9 +12,11 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <thread>
+#include <tuple>
 #include <type_traits>
 #include <utility>
 #include <vector>
@@ -111,10 +113,34 @@ struct Profiler {
   size_t open_idx = 0;
 };
 
+// Launch shapes the autotuner chose for one handle, by element size, kernel
+// and level grid.
+struct Tuning {
+  struct Entry {
+    int elem, kind;
+    Dims d;
+    SweepShape s;
+  };
+  std::vector<Entry> e;
+  SweepShape* find(int elem, int kind, Dims d) {
+    for (auto& x : e)
+      if (x.elem == elem && x.kind == kind && x.d.nx == d.nx && x.d.ny == d.ny && x.d.nz == d.nz) return &x.s;
+    return nullptr;
+  }
+};
+
 namespace {
 thread_local Profiler* t_prof = nullptr;
+thread_local Tuning* t_tune = nullptr;
 constexpr size_t kMaxEvents = 1 << 20;
 }  // namespace
+
+const SweepShape* tuned_sweep(int elem, int kind, Dims d) {
+  Tuning* t = t_tune;
+  if (!t || t->e.empty()) return nullptr;
+  const SweepShape* x = t->find(elem, kind, d);
+  return (x && (x->tx || x->zc)) ? x : nullptr;
+}
 
 void prof_begin(int cls, cudaStream_t s) {
   Profiler* p = t_prof;
@@ -205,6 +231,7 @@ struct ibrd_grid_s {
   long reorths = 0;
   long refinements = 0;
   Profiler prof;
+  Tuning tune;  // launch shapes from ibrd_autotune
   // CUDA graphs of preconditioner applications, one per Krylov index j
   struct GraphEntry {
     cudaGraphExec_t exec = nullptr;
@@ -1095,15 +1122,22 @@ ibrd_status fail(ibrd_grid g, ibrd_status st, const std::string& msg) {
 
 struct ProfScope {
   Profiler* prev;
-  explicit ProfScope(Profiler* p) : prev(t_prof) { t_prof = p; }
-  ~ProfScope() { t_prof = prev; }
+  Tuning* prev_tune;
+  ProfScope(Profiler* p, Tuning* t) : prev(t_prof), prev_tune(t_tune) {
+    t_prof = p;
+    t_tune = t;
+  }
+  ~ProfScope() {
+    t_prof = prev;
+    t_tune = prev_tune;
+  }
 };
 
 template <typename F>
 ibrd_status guarded(ibrd_grid g, const char* name, F&& f) {
   if (!g) return IBRD_ERR_ARG;
   DeviceGuard dg(g->dev);
-  ProfScope ps(&g->prof);
+  ProfScope ps(&g->prof, &g->tune);
   try {
     g->err.clear();
     return f();
@@ -1184,6 +1218,138 @@ ibrd_status run_batch(int count, const ibrd_grid* grids, int threads, F&& solve)
   for (int i = 0; i < count; ++i)
     if (st[i] != IBRD_OK) return st[i];
   return IBRD_OK;
+}
+
+// ---------------------------------------------------------------- autotuner
+// Shapes tuned in this process, by device, element size, kernel and grid.
+struct TuneKey {
+  int dev, elem, kind, nx, ny, nz;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(dev, elem, kind, nx, ny, nz) < std::tie(o.dev, o.elem, o.kind, o.nx, o.ny, o.nz);
+  }
+};
+struct TuneResult {
+  SweepShape s;
+  double us_default, us_tuned;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneResult> g_tune_cache;
+
+// Average duration (us) of `reps` back-to-back sweeps with the handle's current
+// shape for (elem, kind, d); the best of two timed runs after one warm-up.
+template <typename T>
+double time_sweep(ibrd_grid g, int kind, Dims d, Stencil st, T* x0, T* x1, T* b, cudaEvent_t e0, cudaEvent_t e1,
+                  int reps) {
+  auto one = [&]() { launch_rb_sweep<T>(x0, x1, b, nullptr, d, st, kind == TUNE_ZERO, nullptr, 0, g->s); };
+  one();
+  double best = 1e30;
+  for (int r = 0; r < 2; ++r) {
+    IBRD_CUDA(cudaEventRecord(e0, g->s));
+    for (int i = 0; i < reps; ++i) one();
+    IBRD_CUDA(cudaEventRecord(e1, g->s));
+    IBRD_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    IBRD_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    best = std::min(best, 1e3 * (double)ms / reps);
+  }
+  return best;
+}
+
+// Tunes the sweep kernels of element type T on the levels that run them.
+template <typename T>
+void autotune_levels(ibrd_grid g, bool retune, std::vector<ibrd_tune_entry>& rep) {
+  const int elem = (int)sizeof(T);
+  int end = g->small_from;
+  if (elem == 4 && g->exact32 >= 0) end = g->exact32;
+  end = std::min(end, (int)g->levels.size() - 1);
+  if (end <= 0) return;
+  const size_t n = g->d.n();
+  T* x0 = dalloc<T>(n);
+  T* x1 = dalloc<T>(n);
+  T* b = dalloc<T>(n);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto cleanup = [&]() {
+    cudaFree(x0);
+    cudaFree(x1);
+    cudaFree(b);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  };
+  try {
+    IBRD_CUDA(cudaEventCreate(&e0));
+    IBRD_CUDA(cudaEventCreate(&e1));
+    IBRD_CUDA(cudaMemsetAsync(x0, 0, sizeof(T) * n, g->s));
+    IBRD_CUDA(cudaMemsetAsync(x1, 0, sizeof(T) * n, g->s));
+    IBRD_CUDA(cudaMemsetAsync(b, 0, sizeof(T) * n, g->s));
+    for (int l = 0; l < end; ++l) {
+      const Dims d = g->levels[l].d;
+      const Stencil st = stencil(g->levels[l].h, g->chi, g->alpha > 0.0 ? g->alpha : 1.0);
+      const int reps = (int)std::max(3.0, std::min(200.0, 2e8 / (3.0 * elem * (double)d.n())));
+      for (int kind = TUNE_SWEEP; kind <= TUNE_ZERO; ++kind) {
+        if (kind == TUNE_SWEEP && !rb_sweep_fused_ok<T>(d)) continue;
+        if (kind == TUNE_ZERO && (elem != 4 || d.nx % 4 != 0)) continue;
+        const TuneKey key{g->dev, elem, kind, d.nx, d.ny, d.nz};
+        TuneResult res{};
+        bool cached = false;
+        if (!retune) {
+          std::lock_guard<std::mutex> lk(g_tune_mu);
+          auto it = g_tune_cache.find(key);
+          if (it != g_tune_cache.end()) {
+            res = it->second;
+            cached = true;
+          }
+        }
+        SweepShape* slot = g->tune.find(elem, kind, d);
+        if (!slot) {
+          g->tune.e.push_back(Tuning::Entry{elem, kind, d, SweepShape{}});
+          slot = &g->tune.e.back().s;
+        }
+        if (!cached) {
+          *slot = SweepShape{};
+          res.us_default = time_sweep<T>(g, kind, d, st, x0, x1, b, e0, e1, reps);
+          res.us_tuned = res.us_default;
+          res.s = SweepShape{};
+          std::vector<int> txs = {0};
+          if (kind == TUNE_SWEEP) {
+            txs = {32};
+            if (elem == 4 && d.nx % 64 == 0) txs.push_back(64);
+          }
+          static const int zcs[] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512};
+          for (int tx : txs)
+            for (int zc : zcs) {
+              if (zc > d.nz || (kind == TUNE_SWEEP && zc < 2)) continue;
+              *slot = SweepShape{tx, zc};
+              const double us = time_sweep<T>(g, kind, d, st, x0, x1, b, e0, e1, reps);
+              // a shape replaces the built-in one only when clearly faster
+              if (us < res.us_tuned && us < 0.97 * res.us_default) {
+                res.us_tuned = us;
+                res.s = *slot;
+              }
+            }
+          std::lock_guard<std::mutex> lk(g_tune_mu);
+          g_tune_cache[key] = res;
+        }
+        // re-find: push_back above may have moved the entries
+        *g->tune.find(elem, kind, d) = res.s;
+        ibrd_tune_entry r{};
+        r.nx = d.nx;
+        r.ny = d.ny;
+        r.nz = d.nz;
+        r.elem_bytes = elem;
+        r.kind = kind;
+        r.tx = res.s.tx;
+        r.zc = res.s.zc;
+        r.us_default = res.us_default;
+        r.us_tuned = res.us_tuned;
+        r.cached = cached ? 1 : 0;
+        rep.push_back(r);
+      }
+    }
+  } catch (...) {
+    cleanup();
+    throw;
+  }
+  cleanup();
 }
 
 double now_s() { return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count(); }
@@ -1542,6 +1708,51 @@ ibrd_status ibrd_solve_saddle_batch(int count, const ibrd_grid* grids, const dou
     const ibrd_status st = ibrd_solve_saddle(grids[i], rhs[i], f ? f[i] : nullptr, c[i], lambda[i], opts, info);
     if (info) info->status = st;
     return st;
+  });
+}
+
+ibrd_status ibrd_autotune(ibrd_grid g, int precision, int retune, ibrd_tune_entry* out, int cap, int* n_out) {
+  return guarded(g, "ibrd_autotune", [&]() {
+    if (precision != -1 && precision != IBRD_FP64 && precision != IBRD_MIXED_FP32 &&
+        precision != IBRD_MIXED_REFINE)
+      throw ArgError{IBRD_ERR_ARG, "bad precision"};
+    if (cap < 0 || (cap > 0 && !out)) throw ArgError{IBRD_ERR_ARG, "bad report array"};
+    std::vector<ibrd_tune_entry> rep;
+    free_graphs(g);  // captured launches would keep the old shapes
+    if (precision != IBRD_FP64) autotune_levels<float>(g, retune != 0, rep);
+    if (precision == IBRD_FP64 || precision == -1) autotune_levels<double>(g, retune != 0, rep);
+    IBRD_CUDA(cudaStreamSynchronize(g->s));
+    for (int i = 0; i < (int)rep.size() && i < cap; ++i) out[i] = rep[i];
+    if (n_out) *n_out = (int)rep.size();
+    return IBRD_OK;
+  });
+}
+
+ibrd_status ibrd_tune_set(ibrd_grid g, int elem_bytes, int kind, int nx, int ny, int nz, int tx, int zc) {
+  return guarded(g, "ibrd_tune_set", [&]() {
+    if ((elem_bytes != 4 && elem_bytes != 8) || (kind != TUNE_SWEEP && kind != TUNE_ZERO) || zc < 0 ||
+        (tx != 0 && tx != 32 && tx != 64) || (kind == TUNE_ZERO && tx != 0) || (elem_bytes == 8 && tx == 64))
+      throw ArgError{IBRD_ERR_ARG, "bad launch shape"};
+    bool level = false;
+    for (const Level& l : g->levels) level |= (l.d.nx == nx && l.d.ny == ny && l.d.nz == nz);
+    if (!level) throw ArgError{IBRD_ERR_ARG, "no multigrid level of that size"};
+    const Dims d{nx, ny, nz};
+    free_graphs(g);
+    SweepShape* slot = g->tune.find(elem_bytes, kind, d);
+    if (!slot) {
+      g->tune.e.push_back(Tuning::Entry{elem_bytes, kind, d, SweepShape{}});
+      slot = &g->tune.e.back().s;
+    }
+    *slot = SweepShape{tx, zc};
+    return IBRD_OK;
+  });
+}
+
+ibrd_status ibrd_tune_clear(ibrd_grid g) {
+  return guarded(g, "ibrd_tune_clear", [&]() {
+    free_graphs(g);
+    g->tune.e.clear();
+    return IBRD_OK;
   });
 }
 

@@ -99,6 +99,18 @@ int launch_rb_sweep(const T* xin, T* xout, const T* b, const double* bshift, Dim
                     double* part, int part_cap, cudaStream_t s);
 template <typename T>
 bool rb_sweep_fused_ok(Dims d);
+// Launch shape of a red-black sweep kernel picked by the autotuner: tile width
+// tx (cells, fused sweep only) and z-march depth zc (planes per CTA); 0 keeps
+// the built-in rule.
+struct SweepShape {
+  int tx = 0;
+  int zc = 0;
+};
+// Sweep kernels: the fused sweep and the stencil pass of a sweep from zero.
+enum { TUNE_SWEEP = 0, TUNE_ZERO = 1 };
+// The tuned shape for kernel `kind` on elements of `elem` bytes and grid d in
+// the handle the calling thread is working for, or null.
+const SweepShape* tuned_sweep(int elem, int kind, Dims d);
 // Levels handled by the single-CTA coarse V-cycle (shared-memory resident).
 constexpr int kMaxSmallLevels = 12;
 struct CoarseLevels {

@@ -955,6 +955,8 @@ int launch_rb_sweep(const T* xin, T* xout, const T* b, const double* bshift, Dim
       chunks = chunks < 1 ? 1 : chunks;
       int zc = (d.nz + chunks - 1) / chunks;
       zc = zc < 2 ? 2 : zc;
+      const SweepShape* tn = tuned_sweep(4, TUNE_ZERO, d);
+      if (tn && tn->zc >= 1) zc = tn->zc < d.nz ? tn->zc : d.nz;
       dim3 g(bx, by, (d.nz + zc - 1) / zc);
       prof_begin(c, s);
       k_rb_zero_f32v<<<g, dim3(tx, ty), 0, s>>>(b, xout, bshift, d.nx, d.ny, d.nz, zc, inv, off);
@@ -964,7 +966,8 @@ int launch_rb_sweep(const T* xin, T* xout, const T* b, const double* bshift, Dim
   }
   if (rb_sweep_fused_ok<T>(d) && aligned16(xin) && aligned16(xout) && aligned16(b)) {
     // 64-wide tiles for FP32 (18 vectors per row), 32-wide for FP64
-    const bool wide = (sizeof(T) == 4) && (d.nx % 64 == 0);
+    const SweepShape* tn = tuned_sweep((int)sizeof(T), TUNE_SWEEP, d);
+    const bool wide = (sizeof(T) == 4) && (d.nx % 64 == 0) && !(tn && tn->tx == 32);
     const int TX = wide ? 64 : 32, TY = 8;
     const int cols = (d.nx / TX) * (d.ny / TY);
     // about one wave of resident CTAs: chunks per column = resident slots / columns
@@ -976,6 +979,7 @@ int launch_rb_sweep(const T* xin, T* xout, const T* b, const double* bshift, Dim
     chunks = chunks < 1 ? 1 : chunks;
     int zc = (d.nz + chunks - 1) / chunks;
     if (zc < 2) zc = 2;
+    if (tn && tn->zc >= 2) zc = tn->zc < d.nz ? tn->zc : d.nz;
     dim3 g(d.nx / TX, d.ny / TY, (d.nz + zc - 1) / zc);
     const int nblk = (int)(g.x * g.y * g.z);
     if (nblk > part_cap) part = nullptr;

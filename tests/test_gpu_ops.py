@@ -168,3 +168,54 @@ def test_vcycle_smoother_variants_agree(ibrd):
         b = np.random.default_rng(8).standard_normal((nz, ny, nx))
         g = ibrd.Grid(*dims)
         assert rel_max(host(g.vcycle(dev(b))), mg.vcycle(b, 1.0, 1.0, 0.0)) < 1e-12
+
+
+TUNE_DIMS = (128, 64, 80)  # levels 128x64x80, 64x32x40 (FP32 exact level 32x16x20); FP64 coarsens to 8x4x5
+TUNE_LEVELS = [(128, 64, 80), (64, 32, 40), (32, 16, 20)]
+
+
+def _vcycle_both(ibrd, g, seed):
+    import torch
+    nx, ny, nz = TUNE_DIMS
+    b = np.random.default_rng(seed).standard_normal((nz, ny, nx))
+    x64 = host(g.vcycle(dev(b)))
+    x32 = g.vcycle_f32(torch.from_numpy(b.astype(np.float32)).cuda()).cpu().numpy().astype(np.float64)
+    assert rel_max(x64, mg.vcycle(b, 1.0, 1.0, 0.0)) < 1e-12
+    b32 = b.astype(np.float32).astype(np.float64)
+    assert rel_max(x32, mg.vcycle(b32, 1.0, 1.0, 0.0, exact_cells=32768, exact_side=64)) < 2e-5
+
+
+@pytest.mark.parametrize("tx,zc", [(32, 2), (32, 3), (64, 7), (64, 80), (0, 12)])
+def test_vcycle_tuned_shapes(ibrd, tx, zc):
+    """Launch shapes the autotuner may keep (tile width 32 or 64, z-march depths
+    with a ragged last chunk, down to one CTA per column) give the V-cycle of
+    the oracle definition, FP64 and FP32, on every level that runs the sweep
+    kernels."""
+    g = ibrd.Grid(*TUNE_DIMS)
+    for (nx, ny, nz) in TUNE_LEVELS:
+        t32 = tx if (tx != 64 or nx % 64 == 0) else 32
+        ibrd.ibrd_tune_set(g.handle, 4, 0, nx, ny, nz, t32, zc)
+        ibrd.ibrd_tune_set(g.handle, 4, 1, nx, ny, nz, 0, max(1, zc // 2))
+        ibrd.ibrd_tune_set(g.handle, 8, 0, nx, ny, nz, 32 if tx else 0, zc)
+    _vcycle_both(ibrd, g, 21)
+
+
+def test_autotune_report_and_parity(ibrd):
+    """The autotuner times every level that runs the sweep kernels, keeps a
+    shape only when it is faster than the built-in one, reuses its results for
+    a second handle of the same grid, and leaves the V-cycle's definition
+    unchanged."""
+    g = ibrd.Grid(*TUNE_DIMS)
+    rep = ibrd.ibrd_autotune(g.handle, -1, retune=True)
+    seen = {(r["elem_bytes"], r["kind"], (r["nx"], r["ny"], r["nz"])) for r in rep}
+    assert (4, 0, TUNE_LEVELS[0]) in seen and (4, 0, TUNE_LEVELS[1]) in seen and (4, 1, TUNE_LEVELS[0]) in seen
+    assert (8, 0, TUNE_LEVELS[2]) in seen and (4, 0, TUNE_LEVELS[2]) not in seen  # FP32 exact level
+    for r in rep:
+        assert 0 < r["us_tuned"] <= r["us_default"] and r["cached"] == 0
+        assert (r["zc"] == 0) == (r["us_tuned"] == r["us_default"])
+    _vcycle_both(ibrd, g, 22)
+    g2 = ibrd.Grid(*TUNE_DIMS)
+    rep2 = ibrd.ibrd_autotune(g2.handle, -1)
+    assert all(r["cached"] == 1 for r in rep2) and len(rep2) == len(rep)
+    ibrd.ibrd_tune_clear(g.handle)
+    _vcycle_both(ibrd, g, 23)
