@@ -167,15 +167,18 @@ def kernel_source_hash(kernel_class: str = "rbgs_f32"):
     return h.hexdigest()[:16]
 
 
-def committed_traffic(kernel_class: str):
+def committed_traffic(kernel_class: str, shape: dict | None = None):
     """DRAM bytes per finest-level launch from the committed ncu summary, if
-    it was taken on the current source of that kernel class."""
+    it was taken on the current source of that kernel class and with the
+    launch shape the bench runs."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
     e = d.get("classes", {}).get(kernel_class)
     if not e or e.get("source_hash") != kernel_source_hash(kernel_class):
+        return None
+    if shape is not None and e.get("shape") != shape:
         return None
     return e
 
@@ -312,11 +315,14 @@ def run_ours(args):
     peaks = measured_peaks()
     fp32_or_bytes = dom_name.endswith("f32") or dom_name in ("dot", "axpy", "vector")
     achieved_gbs = dc["timed_bytes"] / (dc["ms"] * 1e-3) / 1e9 if dc["ms"] > 0 else 0.0
-    traffic = committed_traffic(dom_name)
+    fine = next((r for r in tune if r["kind"] == 0 and (r["nx"], r["ny"], r["nz"]) == (nx, ny, nz)), None)
+    fine_shape = {"tx": fine["tx"], "zc": fine["zc"]} if fine else {"tx": 0, "zc": 0}
+    traffic = committed_traffic(dom_name, fine_shape if dom_name == "rbgs_f32" else None)
     roofline = {"bound": "hbm", "kernel_class": dom_name, "achieved": round(achieved_gbs, 1),
                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(achieved_gbs / peaks["hbm_gbs"], 4),
                 "peak_source": f"{peaks['source']} hbm_gbs (copy)",
                 "traffic": traffic["dram_bytes_per_launch"] if traffic else None,
+                "launch_shape": fine_shape if dom_name == "rbgs_f32" else None,
                 "algorithmic_bytes_per_launch": dc["timed_bytes"] / max(1, dc["timed"]),
                 "launch_scope": "finest-level launches of the class, CUDA events on the solver stream over a "
                                 "second timed region of the same K steps (per-launch events turn graph replay off; "
@@ -457,6 +463,9 @@ def run_kernel_case(args):
     import paper_1306_3159_gb300 as p
     n = 256
     grid = p.Grid(n, n, n, stream=torch.cuda.current_stream().cuda_stream)
+    # the launch shapes the bench runs (its autotuner, FP32 kernels)
+    for r in p.ibrd_autotune(grid.handle, p.IBRD_MIXED_REFINE):
+        log(f"[bench] tuned {r['nx']}x{r['ny']}x{r['nz']} kind {r['kind']}: tx {r['tx']} zc {r['zc']}")
     b = torch.randn((n, n, n), dtype=torch.float32, device="cuda", generator=torch.Generator("cuda").manual_seed(1))
     b -= b.mean()
     x = torch.zeros_like(b)
