@@ -36,7 +36,8 @@ METRIC = "solve time at rel. residual 1e-8, 256³+4096 blobs: plain vs chosen; %
 # second Gram-Schmidt pass only under severe cancellation (||w'|| < 1e-3 ||w||),
 # and the V-cycle counts / sweeps that minimised time to 1e-8 on GB300.
 CHOSEN_REACTION = dict(mg_cycles=1, nu1=1, nu2=1, reorth_eta=0.0, inner_tol=1e-3)
-CHOSEN_SADDLE = dict(schur_inner=4, mg_cycles=1, nu1=1, nu2=1, reorth_eta=0.0, inner_tol=1e-4)
+CHOSEN_SADDLE = dict(schur_inner=3, mg_cycles=1, nu1=1, nu2=1, reorth_eta=0.0, inner_tol=1e-4, lambda_guess=1,
+                     warm_cycles=1)
 # FP64 FGMRES with the FP32 preconditioner (FP64 Arnoldi, dots and Schur update)
 FP64_KRYLOV_REACTION = dict(mg_cycles=1, nu1=1, nu2=2, reorth_eta=1e-3)
 FP64_KRYLOV_SADDLE = dict(schur_inner=4, mg_cycles=1, nu1=1, nu2=1, reorth_eta=1e-3)

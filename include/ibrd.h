@@ -54,6 +54,7 @@ typedef enum {
 enum { IBRD_PESKIN4 = 4, IBRD_PESKIN3 = 3 };          /* kernel width w */
 enum { IBRD_FP64 = 0, IBRD_MIXED_FP32 = 1, IBRD_MIXED_REFINE = 2 };  /* precision */
 enum { IBRD_PRECOND_SCHUR = 0, IBRD_PRECOND_DIAG = 1 }; /* saddle preconditioner */
+enum { IBRD_GUESS_NONE = 0, IBRD_GUESS_UNIFORM = 1, IBRD_GUESS_GIVEN = 2 }; /* saddle warm start */
 
 /* Solver options. ibrd_default_opts fills the defaults noted here. */
 typedef struct {
@@ -91,6 +92,21 @@ typedef struct {
                         solve aims for, unless less is needed to reach tol
                         (1e-4; the FP32 rounding floor of the operator is
                         near 1e-6 on the grids of Sec. IV) */
+  int lambda_guess;  /* saddle solves with use_guess = 0: start from a guess
+                        lambda0 of the multipliers instead of zero.
+                        IBRD_GUESS_NONE (default): start at 0.
+                        IBRD_GUESS_UNIFORM: lambda0_i = h^3 sum(g) / (zeta N).
+                        IBRD_GUESS_GIVEN: lambda0 = the incoming lambda (c is
+                        ignored), scaled when alpha = 0 so that
+                        zeta sum(lambda0) = h^3 sum(g) (the solvability
+                        condition of Appendix A; the uniform share if its sum
+                        is 0). The grid part of the start is
+                        c0 = A~^-1 (g - zeta S lambda0) by warm_cycles V-cycles
+                        in the preconditioner's precision plus, when
+                        alpha = 0, the constant <f/xi - J c~> (Appendix A
+                        steps 3-5 with lambda0 for the Schur solution). The
+                        solve then runs to tol as from any other start. */
+  int warm_cycles;   /* V-cycles forming c0 of a warm start (2) */
 } ibrd_solve_opts;
 
 /* Solve report. residual_history, if non-NULL, is a caller-owned HOST array

@@ -1096,6 +1096,56 @@ struct SaddleOp : LinOp<E> {
   }
 };
 
+__global__ void k_fill_or_scale(double* x, int n, double c, int scale) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] = scale ? x[i] * c : c;
+}
+
+// Warm start of a saddle solve from a guess lambda0 of the multipliers (mode 1:
+// the uniform share lambda0_i = h^3 sum(g) / (zeta N); mode 2: the caller's
+// lambda, in x + N_c, scaled when A is singular to the solvability condition
+// zeta sum(lambda) = h^3 sum(g), Appendix A). The grid part follows Appendix A
+// steps 3-5 with lambda0 in place of the Schur solution: c~ = A~^-1 (g - zeta S
+// lambda0) by `cycles` V-cycles in precision T and, when A is singular,
+// c0 = c~ + cbar0 with cbar0 = <f/xi - J c~>. b = [g; f]; writes [c0; lambda0]
+// into x.
+template <typename T>
+void saddle_warm_start(ibrd_grid g, const ibrd_solve_opts& o, const double* b, double* x, int mode, int cycles) {
+  const size_t nc = g->d.n();
+  const int N = g->blobs.n;
+  const bool singular = (g->alpha == 0.0);
+  const double h3 = g->h * g->h * g->h;
+  double* sc = g->scal;
+  double* lam = x + nc;
+  launch_sum<double>(b, nc, g->partial, sc + S_TMP, h3 / o.zeta, g->s);
+  if (mode == 2) launch_sum<double>(lam, N, g->partial, sc + S_TMP2, 1.0, g->s);
+  IBRD_CUDA(cudaMemcpyAsync(g->host, sc + S_TMP, sizeof(double) * 2, cudaMemcpyDeviceToHost, g->s));
+  IBRD_CUDA(cudaStreamSynchronize(g->s));
+  const double total = g->host[0], lsum = mode == 2 ? g->host[1] : 0.0;
+  const int nb = std::min(1024, (N + 255) / 256);
+  prof_begin(P_SMALL, g->s);
+  if (mode == 1 || (singular && !(std::isfinite(lsum) && lsum != 0.0)))
+    k_fill_or_scale<<<nb, 256, 0, g->s>>>(lam, N, total / N, 0);
+  else if (singular)
+    k_fill_or_scale<<<nb, 256, 0, g->s>>>(lam, N, total / lsum, 1);
+  prof_end(P_SMALL, g->s, "lambda0");
+  // g - zeta S lambda0 (has mean zero when A is singular)
+  T* rt = pfield<T>(g, 0);
+  T* ct = pfield<T>(g, 1);
+  IBRD_CUDA(cudaMemcpyAsync(x, b, sizeof(double) * nc, cudaMemcpyDeviceToDevice, g->s));
+  launch_spread<double>(g->blobs, g->d, lam, nullptr, -o.zeta * inv_h3(g), x, 1, g->s);
+  launch_convert<double, T>(x, rt, nc, 1.0, nullptr, g->s);
+  vcycles<T>(g, rt, ct, true, g->alpha, std::max(1, cycles), o.nu1, o.nu2);
+  if (singular) {
+    double* t = g->nv[2];
+    launch_interp<T>(g->blobs, g->d, ct, 1.0, t, g->s);
+    launch_nvec_affine(t, t, N, -1.0, nullptr, b + nc, 1.0 / o.xi, g->s);
+    launch_sum<double>(t, N, g->partial, sc + S_CBAR, 1.0 / N, g->s);
+    launch_convert<T, double>(ct, x, nc, 1.0, sc + S_CBAR, g->s);
+  } else {
+    launch_convert<T, double>(ct, x, nc, 1.0, nullptr, g->s);
+  }
+}
+
 // M_11 = (J A^-1 S)_11 of blob 0 by V-cycle iteration to convergence (used by
 // the diagonal preconditioner, Eq. Schur_diagonal).
 double compute_gamma(ibrd_grid g, const ibrd_solve_opts& o) {
@@ -1162,7 +1212,9 @@ ibrd_solve_opts resolve_opts(ibrd_grid g, const ibrd_solve_opts* in) {
       o.schur_inner < 1 || o.schur_inner > 60 || o.nu1 < 0 || o.nu2 < 0 || !(o.zeta != 0.0) ||
       !(o.reorth_eta >= 0.0) || !(o.inner_tol > 0.0 && o.inner_tol < 1.0) ||
       (o.precision != IBRD_FP64 && o.precision != IBRD_MIXED_FP32 && o.precision != IBRD_MIXED_REFINE) ||
-      (o.precond != IBRD_PRECOND_SCHUR && o.precond != IBRD_PRECOND_DIAG))
+      (o.precond != IBRD_PRECOND_SCHUR && o.precond != IBRD_PRECOND_DIAG) ||
+      (o.lambda_guess != IBRD_GUESS_NONE && o.lambda_guess != IBRD_GUESS_UNIFORM &&
+       o.lambda_guess != IBRD_GUESS_GIVEN) || o.warm_cycles < 1 || o.warm_cycles > 64)
     throw ArgError{IBRD_ERR_ARG, "invalid solver options"};
   return o;
 }
@@ -1397,6 +1449,8 @@ void ibrd_default_opts(ibrd_solve_opts* o) {
   o->reorth_eta = 0.70710678118654752;
   o->graphs = 1;
   o->inner_tol = 1e-4;
+  o->lambda_guess = IBRD_GUESS_NONE;
+  o->warm_cycles = 2;
 }
 
 const char* ibrd_status_string(int st) {
@@ -1655,6 +1709,16 @@ ibrd_status ibrd_solve_saddle(ibrd_grid g, const double* rhs, const double* f, d
       IBRD_CUDA(cudaMemcpyAsync(g->xs, c, sizeof(double) * nc, cudaMemcpyDeviceToDevice, g->s));
       IBRD_CUDA(cudaMemcpyAsync(g->xs + nc, lambda, sizeof(double) * N, cudaMemcpyDeviceToDevice, g->s));
     }
+    const bool warm = !o.use_guess && o.lambda_guess != IBRD_GUESS_NONE;
+    if (warm) {
+      if (o.lambda_guess == IBRD_GUESS_GIVEN)
+        IBRD_CUDA(cudaMemcpyAsync(g->xs + nc, lambda, sizeof(double) * N, cudaMemcpyDeviceToDevice, g->s));
+      if (o.precision == IBRD_FP64)
+        saddle_warm_start<double>(g, o, g->bs, g->xs, o.lambda_guess, o.warm_cycles);
+      else
+        saddle_warm_start<float>(g, o, g->bs, g->xs, o.lambda_guess, o.warm_cycles);
+    }
+    const bool zero_start = !o.use_guess && !warm;
     if (o.precond == IBRD_PRECOND_DIAG && !g->gamma_valid) {
       g->gamma_diag = compute_gamma(g, o);
       g->gamma_valid = true;
@@ -1668,14 +1732,14 @@ ibrd_status ibrd_solve_saddle(ibrd_grid g, const double* rhs, const double* f, d
     }
     if (o.precision == IBRD_FP64) {
       SaddleOp<double> op(g, o, o.zeta, o.xi);
-      R = fgmres<double>(g, op, g->bs, g->xs, n, o, o.tol, o.max_iter, !o.use_guess, hist);
+      R = fgmres<double>(g, op, g->bs, g->xs, n, o, o.tol, o.max_iter, zero_start, hist);
     } else if (o.precision == IBRD_MIXED_FP32) {
       SaddleOp<float, double> op(g, o, o.zeta, o.xi);
-      R = fgmres<double>(g, op, g->bs, g->xs, n, o, o.tol, o.max_iter, !o.use_guess, hist);
+      R = fgmres<double>(g, op, g->bs, g->xs, n, o, o.tol, o.max_iter, zero_start, hist);
     } else {
       SaddleOp<double> op(g, o, o.zeta, o.xi);
       SaddleOp<float> op32(g, o, o.zeta, o.xi);
-      R = refine(g, op, op32, g->bs, g->xs, n, o, !o.use_guess, hist);
+      R = refine(g, op, op32, g->bs, g->xs, n, o, zero_start, hist);
     }
     if (info) info->history_len = hist.len;
     IBRD_CUDA(cudaMemcpyAsync(c, g->xs, sizeof(double) * nc, cudaMemcpyDeviceToDevice, g->s));

@@ -258,3 +258,29 @@ def test_batch_matches_single_solves(ibrd, precision):
     c_ref, _, _ = direct.solve_reaction(w.q, w.kappa, w.g, w.h, w.chi, 0.0)
     assert rel_l2(host(cb[k]), c_ref) < 1e-8
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("precision", [0, 2])
+def test_saddle_warm_start(ibrd, small, precision):
+    """Saddle solves started from a guess of lambda (uniform share, the exact
+    multipliers with 1 % noise, and an all-zero guess, which falls back to the
+    uniform share) and the grid field built from it by Appendix A steps 3-5
+    reach the tolerance and the oracle's solution; the exact multipliers never
+    cost more iterations than a zero start."""
+    import torch
+    w, M = small
+    c_ref, lam_ref, _ = direct.solve_saddle(w.q, w.g, w.h, w.chi, 0.0, M=M)
+    g = _grid(ibrd, w)
+    tol = max(1e-12, floor_tol(c_ref, w.g, w.h, w.chi, 0.0))
+    err = 1e-11
+    noise = np.random.default_rng(3).standard_normal(len(lam_ref))
+    _, _, cold = g.solve_saddle(dev(w.g), tol=tol, precision=precision, max_iter=400)
+    for guess, lam0 in [(1, None), (2, lam_ref * (1 + 0.01 * noise)), (2, np.zeros_like(lam_ref)), (2, lam_ref)]:
+        lam = dev(lam0) if lam0 is not None else None
+        c, lam, info = g.solve_saddle(dev(w.g), lam=lam, tol=tol, precision=precision, max_iter=400,
+                                      lambda_guess=guess, warm_cycles=3)
+        assert info["rel_residual"] <= tol
+        assert rel_l2(host(c), c_ref) < err and rel_l2(host(lam), lam_ref) < err
+        if lam0 is not None and np.array_equal(lam0, lam_ref):
+            assert info["outer_iters"] <= cold["outer_iters"]
+    torch.cuda.synchronize()
