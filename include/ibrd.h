@@ -289,6 +289,73 @@ ibrd_status ibrd_tune_set(ibrd_grid g, int elem_bytes, int kind, int nx, int ny,
    captured CUDA graphs. */
 ibrd_status ibrd_tune_clear(ibrd_grid g);
 
+/* ---------------------------------------------------------------------
+   Learned multiplier predictor (not in the paper). The paper leaves a good
+   treatment of the Schur complement J A^-1 S of the saddle point for many
+   blobs open (Sec. III.E, Sec. V). This is a small graph network over each
+   blob's neighbours (minimum-image distance below the cutoff in the periodic
+   box) that predicts the relative sink strengths lambda_i / <lambda>, used as
+   the initial guess of the multipliers (ibrd_solve_opts.lambda_guess =
+   IBRD_GUESS_GIVEN). Definition, with s = r / R, f_c = (1 - s)^2 and K = 16
+   radial bases b_k = f_c exp(-((s - k/15) / 0.1)^2), width 64:
+     x_i = sum_j b(r_ij);  h1_i = relu(W1 x_i + c1);
+     m_i = sum_j f_c(r_ij) relu(E b(r_ij) + e) * h1_j (elementwise);
+     h2_i = h1_i + relu(W2 m_i + V2 h1_i + c2);  y_i = o . h2_i + o0;
+     lambda0_i = total exp(y_i) / sum_k exp(y_k).
+   Training minimises <((y - <y>) - (t - <t>))^2>, t_i = log lambda_i, over
+   (configuration, lambda) pairs from saddle solves, by Adam (beta 0.9,
+   0.999, eps 1e-8). Parameters are FP32, in the order W1 (64 x 16, row
+   major), c1 (64), E (64 x 16), e (64), W2 (64 x 64), V2 (64 x 64), c2 (64),
+   o (64), o0 (1). Positions q are DEVICE arrays of n x 3 FP64 values (as for
+   ibrd_set_blobs) in a periodic box lx x ly x lz; the cutoff must not exceed
+   half the shortest side. A blob with more than max_neighbours neighbours
+   makes the call fail with IBRD_ERR_ARG. Multipliers lam must be > 0. Every
+   call orders its work on the handle's stream and synchronizes it. */
+typedef struct ibrd_gnn_s* ibrd_gnn;
+
+/* Number of parameters (10497). */
+int ibrd_gnn_num_params(void);
+
+/* New model with all parameters 0 (set them with ibrd_gnn_set_params).
+   cutoff > 0 (same length unit as positions), 1 <= max_neighbours <= 1024. */
+ibrd_status ibrd_gnn_create(ibrd_gnn* out, double cutoff, int max_neighbours, void* stream);
+void ibrd_gnn_destroy(ibrd_gnn m);
+const char* ibrd_gnn_last_error(ibrd_gnn m);
+
+/* theta: HOST array of ibrd_gnn_num_params() FP32 values. reset_optimizer != 0
+   also zeroes Adam's moments and step count. */
+ibrd_status ibrd_gnn_set_params(ibrd_gnn m, const float* theta, int reset_optimizer);
+ibrd_status ibrd_gnn_get_params(ibrd_gnn m, float* theta);
+
+/* Neighbour lists of a configuration (DEVICE outputs): count[n], index[n x
+   max_neighbours] (increasing j, then unused), dist[n x max_neighbours] (FP32
+   distances). */
+ibrd_status ibrd_gnn_neighbours(ibrd_gnn m, const double* q, int n, double lx, double ly, double lz, int* count,
+                                int* index, float* dist);
+
+/* y (DEVICE, n FP32 values): the network's outputs. */
+ibrd_status ibrd_gnn_forward(ibrd_gnn m, const double* q, int n, double lx, double ly, double lz, float* y);
+
+/* lambda0 (DEVICE, n FP64 values) = total * softmax(y). */
+ibrd_status ibrd_gnn_predict(ibrd_gnn m, const double* q, int n, double lx, double ly, double lz, double total,
+                             double* lambda0);
+
+/* Loss of one configuration with multipliers lam (DEVICE, n FP64 values) into
+   *loss (host, may be NULL) and its gradient into grad (DEVICE, num_params FP32
+   values, may be NULL). Parameters unchanged. */
+ibrd_status ibrd_gnn_loss_grad(ibrd_gnn m, const double* q, int n, double lx, double ly, double lz,
+                               const double* lam, double* loss, float* grad);
+
+/* One Adam step with gradient grad (DEVICE) and learning rate lr > 0. */
+ibrd_status ibrd_gnn_adam_step(ibrd_gnn m, const float* grad, double lr);
+
+/* epochs passes over count configurations in index order, one Adam step per
+   configuration. q[c], lam[c]: DEVICE arrays; n[c]: blob counts (HOST);
+   boxes: HOST array of 3 count box sides; epoch_loss (HOST, may be NULL):
+   mean loss of each epoch (losses before each step). */
+ibrd_status ibrd_gnn_train(ibrd_gnn m, int count, const double* const* q, const int* n, const double* boxes,
+                           const double* const* lam, int epochs, double lr, double* epoch_loss);
+
 /* Launch profiler (not in the paper: instrumentation of this library).
    Every kernel the library launches is counted per kernel class; with timing
    enabled each launch is also bracketed by CUDA events on the handle's stream,

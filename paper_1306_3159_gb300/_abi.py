@@ -23,7 +23,9 @@ STATUS = {0: "IBRD_OK", 1: "IBRD_ERR_ARG", 2: "IBRD_ERR_CUDA", 3: "IBRD_ERR_OOM"
 EXPORTED = ["ibrd_default_opts", "ibrd_grid_create", "ibrd_grid_destroy", "ibrd_set_blobs", "ibrd_apply_L",
             "ibrd_vcycle", "ibrd_vcycle_f32", "ibrd_vcycle_noalloc", "ibrd_spread", "ibrd_interp", "ibrd_solve_reaction", "ibrd_solve_saddle",
             "ibrd_solve_reaction_batch", "ibrd_solve_saddle_batch", "ibrd_autotune", "ibrd_tune_set",
-            "ibrd_tune_clear",
+            "ibrd_tune_clear", "ibrd_gnn_num_params", "ibrd_gnn_create", "ibrd_gnn_destroy", "ibrd_gnn_last_error",
+            "ibrd_gnn_set_params", "ibrd_gnn_get_params", "ibrd_gnn_neighbours", "ibrd_gnn_forward",
+            "ibrd_gnn_predict", "ibrd_gnn_loss_grad", "ibrd_gnn_adam_step", "ibrd_gnn_train",
             "ibrd_last_error", "ibrd_status_string", "ibrd_profile_enable", "ibrd_profile_read",
             "ibrd_profile_class_name"]
 
@@ -110,6 +112,30 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ibrd_tune_set.restype = i
     lib.ibrd_tune_clear.argtypes = [vp]
     lib.ibrd_tune_clear.restype = i
+    lib.ibrd_gnn_num_params.argtypes = []
+    lib.ibrd_gnn_num_params.restype = i
+    lib.ibrd_gnn_create.argtypes = [P(vp), d, i, vp]
+    lib.ibrd_gnn_create.restype = i
+    lib.ibrd_gnn_destroy.argtypes = [vp]
+    lib.ibrd_gnn_destroy.restype = None
+    lib.ibrd_gnn_last_error.argtypes = [vp]
+    lib.ibrd_gnn_last_error.restype = ctypes.c_char_p
+    lib.ibrd_gnn_set_params.argtypes = [vp, vp, i]
+    lib.ibrd_gnn_set_params.restype = i
+    lib.ibrd_gnn_get_params.argtypes = [vp, vp]
+    lib.ibrd_gnn_get_params.restype = i
+    lib.ibrd_gnn_neighbours.argtypes = [vp, vp, i, d, d, d, vp, vp, vp]
+    lib.ibrd_gnn_neighbours.restype = i
+    lib.ibrd_gnn_forward.argtypes = [vp, vp, i, d, d, d, vp]
+    lib.ibrd_gnn_forward.restype = i
+    lib.ibrd_gnn_predict.argtypes = [vp, vp, i, d, d, d, d, vp]
+    lib.ibrd_gnn_predict.restype = i
+    lib.ibrd_gnn_loss_grad.argtypes = [vp, vp, i, d, d, d, vp, P(d), vp]
+    lib.ibrd_gnn_loss_grad.restype = i
+    lib.ibrd_gnn_adam_step.argtypes = [vp, vp, d]
+    lib.ibrd_gnn_adam_step.restype = i
+    lib.ibrd_gnn_train.argtypes = [vp, i, P(vp), P(i), P(d), P(vp), i, d, P(d)]
+    lib.ibrd_gnn_train.restype = i
     lib.ibrd_last_error.argtypes = [vp]
     lib.ibrd_last_error.restype = ctypes.c_char_p
     lib.ibrd_status_string.argtypes = [i]
@@ -419,3 +445,102 @@ class Grid:
         lam = torch.zeros(self.n_blobs, dtype=torch.float64, device="cuda") if lam is None else lam
         info = ibrd_solve_saddle(self.handle, rhs, f, c, lam, ibrd_default_opts(**kw))
         return c, lam, info
+
+
+# ---------------------------------------------------------------- learned multiplier predictor
+def ibrd_gnn_num_params() -> int:
+    return int(load_library().ibrd_gnn_num_params())
+
+
+def _gnn_check(m, st):
+    if st != 0:
+        raise IbrdError(st, load_library().ibrd_gnn_last_error(m).decode() if m else "")
+
+
+class GNN:
+    """Owning wrapper of an ``ibrd_gnn`` model (positions: CUDA FP64 (n, 3))."""
+
+    def __init__(self, cutoff, max_neighbours=64, stream=None):
+        lib = load_library()
+        self.handle = ctypes.c_void_p()
+        st = lib.ibrd_gnn_create(ctypes.byref(self.handle), float(cutoff), int(max_neighbours), _stream(stream))
+        if st != 0:
+            raise IbrdError(st, "ibrd_gnn_create rejected its arguments")
+        self.cutoff, self.kmax = float(cutoff), int(max_neighbours)
+
+    def close(self):
+        if self.handle is not None:
+            load_library().ibrd_gnn_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, theta, reset_optimizer=True):
+        import numpy as np
+        t = np.ascontiguousarray(theta, dtype=np.float32)
+        if t.size != ibrd_gnn_num_params():
+            raise ValueError("wrong parameter count")
+        _gnn_check(self.handle, load_library().ibrd_gnn_set_params(self.handle, t.ctypes.data_as(ctypes.c_void_p),
+                                                                    int(bool(reset_optimizer))))
+
+    def get_params(self):
+        import numpy as np
+        t = np.zeros(ibrd_gnn_num_params(), dtype=np.float32)
+        _gnn_check(self.handle, load_library().ibrd_gnn_get_params(self.handle, t.ctypes.data_as(ctypes.c_void_p)))
+        return t
+
+    def neighbours(self, q, box):
+        import torch
+        n = int(q.shape[0])
+        cnt = torch.zeros(n, dtype=torch.int32, device="cuda")
+        idx = torch.zeros((n, self.kmax), dtype=torch.int32, device="cuda")
+        dist = torch.zeros((n, self.kmax), dtype=torch.float32, device="cuda")
+        _gnn_check(self.handle, load_library().ibrd_gnn_neighbours(
+            self.handle, _ptr(q), n, *map(float, box), _ptr(cnt, "int32"), _ptr(idx, "int32"),
+            _ptr(dist, "float32")))
+        return cnt, idx, dist
+
+    def forward(self, q, box):
+        import torch
+        n = int(q.shape[0])
+        y = torch.zeros(n, dtype=torch.float32, device="cuda")
+        _gnn_check(self.handle, load_library().ibrd_gnn_forward(self.handle, _ptr(q), n, *map(float, box),
+                                                                _ptr(y, "float32")))
+        return y
+
+    def predict(self, q, box, total, out=None):
+        import torch
+        n = int(q.shape[0])
+        out = torch.zeros(n, dtype=torch.float64, device="cuda") if out is None else out
+        _gnn_check(self.handle, load_library().ibrd_gnn_predict(self.handle, _ptr(q), n, *map(float, box),
+                                                                float(total), _ptr(out)))
+        return out
+
+    def loss_grad(self, q, box, lam):
+        import torch
+        g = torch.zeros(ibrd_gnn_num_params(), dtype=torch.float32, device="cuda")
+        loss = ctypes.c_double(0.0)
+        _gnn_check(self.handle, load_library().ibrd_gnn_loss_grad(self.handle, _ptr(q), int(q.shape[0]),
+                                                                  *map(float, box), _ptr(lam), ctypes.byref(loss),
+                                                                  _ptr(g, "float32")))
+        return loss.value, g
+
+    def adam_step(self, grad, lr):
+        _gnn_check(self.handle, load_library().ibrd_gnn_adam_step(self.handle, _ptr(grad, "float32"), float(lr)))
+
+    def train(self, qs, boxes, lams, epochs, lr):
+        """epochs passes over the configurations (lists of CUDA tensors); returns
+        the mean loss of each epoch."""
+        import numpy as np
+        c = len(qs)
+        qa, la = _ptr_array(qs), _ptr_array(lams)
+        ns = (ctypes.c_int * c)(*[int(q.shape[0]) for q in qs])
+        bx = (ctypes.c_double * (3 * c))(*[float(v) for b in boxes for v in b])
+        out = (ctypes.c_double * epochs)()
+        _gnn_check(self.handle, load_library().ibrd_gnn_train(self.handle, c, qa, ns, bx, la, int(epochs),
+                                                              float(lr), out))
+        return np.array(out[:])

@@ -1,6 +1,6 @@
 """Build libibrd.so in-tree with nvcc for sm_103a (GB300).
 
-The four CUDA translation units compile in parallel into ``_build/`` at the
+The CUDA translation units compile in parallel into ``_build/`` at the
 repository root and link into ``paper_1306_3159_gb300/libibrd.so``. A stamp
 file records the host architecture, so a tree copied between an x86 host and
 an aarch64 host is rebuilt.
@@ -20,7 +20,8 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libibrd.so")
 STAMP = os.path.join(BUILD, "stamp.txt")
-SOURCES = ["grid_kernels.cu", "smoother.cu", "blob_kernels.cu", "krylov_kernels.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["grid_kernels.cu", "smoother.cu", "blob_kernels.cu", "krylov_kernels.cu", "api.cu", "noalloc.cu",
+           "gnn.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fno-strict-aliasing",
          "-Wno-deprecated-declarations"]

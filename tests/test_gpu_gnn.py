@@ -1,0 +1,146 @@
+"""The learned multiplier predictor's CUDA kernels against its FP64 definition
+(oracle/gnn.py), through the C ABI: neighbour lists bit for bit, the forward
+pass, loss and gradient within FP32 rounding, Adam's update, the softmax
+prediction, training, and its use as the warm start of a saddle solve."""
+import numpy as np
+import pytest
+
+from oracle import direct, gnn
+from synthetic import rsa_positions, workload
+from tests.gpu_util import dev, floor_tol, host, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ibrd():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_1306_3159_gb300 import build
+    build.build()
+    import paper_1306_3159_gb300 as p
+    return p
+
+
+def _theta(seed):
+    th = gnn.init_params(seed)
+    p = gnn.unpack(th)
+    rng = np.random.default_rng(seed + 100)
+    for k in ("c1", "e", "c2"):
+        p[k] = rng.uniform(-0.3, 0.3, size=p[k].shape)
+    p["o0"] = np.array([0.2])
+    # the FP32 model holds FP32 weights: give the reference the same values
+    return gnn.pack(p).astype(np.float32).astype(np.float64)
+
+
+def _config(n, side, seed, spacing=2.0):
+    q = rsa_positions(n, (side, side, side), 1.0, spacing, seed)
+    return q, np.array([side, side, side], dtype=np.float64)
+
+
+@pytest.mark.parametrize("n,side,R", [(200, 40, 8.0), (37, 20, 9.5), (1, 24, 6.0)])
+def test_neighbours_exact(ibrd, n, side, R):
+    q, box = _config(n, side, 3)
+    m = ibrd.GNN(R, 64)
+    cnt, idx, dist = m.neighbours(dev(q), box)
+    cnt, idx, dist = host(cnt), host(idx), host(dist)
+    nb, rr = gnn.neighbours(q, box, R)
+    for i in range(n):
+        assert cnt[i] == len(nb[i])
+        assert list(idx[i, :cnt[i]]) == list(nb[i])
+        assert np.array_equal(dist[i, :cnt[i]], rr[i].astype(np.float32))
+
+
+def test_forward_loss_gradient_and_adam(ibrd):
+    import torch
+    q, box = _config(300, 48, 5)
+    R = 10.0
+    th = _theta(7)
+    lam = np.exp(np.random.default_rng(2).normal(0.0, 0.15, size=len(q)))
+    m = ibrd.GNN(R, 64)
+    m.set_params(th)
+    qd, ld = dev(q), dev(lam)
+    y = host(m.forward(qd, box)).astype(np.float64)
+    y_ref, _ = gnn.forward(th, q, box, R)
+    assert np.abs(y - y_ref).max() < 2e-5 * max(1.0, np.abs(y_ref).max())
+    L, g = m.loss_grad(qd, box, ld)
+    L_ref, g_ref = gnn.loss_and_grad(th, q, box, R, lam)
+    assert abs(L - L_ref) < 1e-4 * L_ref
+    g = host(g).astype(np.float64)
+    off = 0
+    for name, shape in gnn.LAYOUT:
+        k = int(np.prod(shape))
+        a, b = g[off:off + k], g_ref[off:off + k]
+        # FP32 sums over blobs and edges: 1e-4 of the block, or 1e-6 of the
+        # whole gradient for blocks that are sums of nearly cancelling terms
+        assert np.linalg.norm(a - b) <= 1e-4 * np.linalg.norm(b) + 1e-6 * np.linalg.norm(g_ref), name
+        off += k
+    # one Adam step from zero moments against the reference update
+    m.adam_step(torch.from_numpy(g.astype(np.float32)).cuda(), 1e-3)
+    th1 = m.get_params().astype(np.float64)
+    z = np.zeros_like(th)
+    want, _, _ = gnn.adam_step(th, g.astype(np.float32).astype(np.float64), z, z, 1, 1e-3)
+    assert np.abs(th1 - want).max() < 1e-6
+    # prediction: softmax of y scaled to the total
+    lam0 = host(m.predict(qd, box, 123.0))
+    assert abs(lam0.sum() - 123.0) < 1e-9 * 123.0
+    assert rel_l2(lam0, gnn.predict(gnn.pack(gnn.unpack(th1)), q, box, R, 123.0)) < 1e-5
+
+
+def test_too_many_neighbours_is_an_argument_error(ibrd):
+    q, box = _config(60, 20, 9, spacing=1.0)
+    m = ibrd.GNN(9.9, 4)
+    with pytest.raises(ibrd.IbrdError) as e:
+        m.forward(dev(q), box)
+    assert e.value.status == 1
+
+
+def test_training_reduces_the_loss(ibrd):
+    """Targets made by a teacher network of the same form: training a fresh
+    model on 12 configurations lowers the loss several-fold."""
+    R = 10.0
+    teacher = _theta(11)
+    qs, boxes, lams = [], [], []
+    for s in range(12):
+        q, box = _config(120, 40, 40 + s)
+        y, _ = gnn.forward(teacher, q, box, R)
+        qs.append(dev(q))
+        boxes.append(box)
+        lams.append(dev(np.exp(y - y.mean())))
+    m = ibrd.GNN(R, 64)
+    m.set_params(gnn.init_params(3).astype(np.float32))
+    losses = m.train(qs, boxes, lams, epochs=30, lr=3e-3)
+    assert np.all(np.isfinite(losses)) and losses[-1] < 0.25 * losses[0]
+
+
+def test_learned_warm_start_saddle(ibrd):
+    """Multipliers from GPU saddle solves train the model; its prediction on a
+    new configuration starts a saddle solve that reaches the oracle's exact
+    solution within 1e-11."""
+    import torch
+    d, h = (32, 32, 32), 1.0
+    box = np.array([32.0, 32.0, 32.0])
+    R = 12.0
+    qs, lams = [], []
+    for s in range(6):
+        q = rsa_positions(40, d, h, 4.0, 60 + s)
+        g = ibrd.Grid(*d)
+        g.set_blobs(dev(q))
+        _, lam, info = g.solve_saddle(dev(np.ones((32, 32, 32))), tol=1e-10, precision=0)
+        assert info["status"] == 0
+        qs.append(dev(q))
+        lams.append(lam)
+    m = ibrd.GNN(R, 64)
+    m.set_params(gnn.init_params(5).astype(np.float32))
+    losses = m.train(qs, [box] * len(qs), lams, epochs=20, lr=2e-3)
+    assert losses[-1] < losses[0]
+    w = workload("small")
+    c_ref, lam_ref, _ = direct.solve_saddle(w.q, w.g, w.h, w.chi, 0.0)
+    lam0 = m.predict(dev(w.q), box, float(w.g.sum()))
+    g = ibrd.Grid(*w.dims)
+    g.set_blobs(dev(w.q))
+    tol = floor_tol(c_ref, w.g, w.h, w.chi, 0.0)
+    c, lam, info = g.solve_saddle(dev(w.g), lam=lam0, tol=tol, precision=2, lambda_guess=2, max_iter=400)
+    assert info["rel_residual"] <= tol
+    assert rel_l2(host(c), c_ref) < 1e-11 and rel_l2(host(lam), lam_ref) < 1e-11
+    torch.cuda.synchronize()
