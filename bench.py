@@ -377,6 +377,8 @@ def run_ours(args):
         grid.close()
         torch.cuda.empty_cache()
         result["batched"] = run_batched(p, torch, world, args, tune=not args.no_autotune)
+    if not args.no_learned:
+        result["learned"] = run_learned(p, torch, world, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline_sample(columns=args.cpu_columns)
     if rank == 0:
@@ -451,6 +453,113 @@ def run_batched(p, torch, world, args, tune=True):
         g.close()
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
+    return out
+
+
+LEARNED_CUTOFF = 24.0
+
+
+def run_learned(p, torch, world, args):
+    """The learned multiplier predictor as the warm start of the saddle solve.
+    Training data: 64 saddle solves at 128^3 (blob density 1.2e-4 to 2e-3 per
+    h^3, RSA spacing 3h-4h, unit source) from the batched entry point in the
+    chosen mode; 56 train the network (80 epochs of Adam), 8 are held out.
+    Evaluation: time to 1e-8 of the chosen saddle solve from a zero start, the
+    uniform share and the learned prediction (its inference inside the timed
+    region) on the 256^3 workloads with 4096 blobs (spacing 4h) and 16384 blobs
+    (spacing 3h)."""
+    import time
+    import numpy as np
+    from synthetic import rsa_positions, workload
+    side = 128
+    rng = np.random.default_rng(5)
+    cfgs = []
+    for s in range(64):
+        n = int(round(np.exp(rng.uniform(np.log(side ** 3 * 1.2e-4), np.log(side ** 3 * 2e-3)))))
+        cfgs.append(rsa_positions(n, (side,) * 3, 1.0, float(rng.uniform(3.0, 4.0)), 1000 + s))
+    streams = [torch.cuda.Stream() for _ in cfgs]
+    grids = [p.Grid(side, side, side, precision=p.IBRD_MIXED_REFINE, stream=st.cuda_stream) for st in streams]
+    qs = [torch.from_numpy(q).cuda() for q in cfgs]
+    gs = [torch.ones((side,) * 3, dtype=torch.float64, device="cuda") for _ in cfgs]
+    cs = [torch.zeros_like(x) for x in gs]
+    ls = [torch.zeros(len(q), dtype=torch.float64, device="cuda") for q in cfgs]
+    torch.cuda.synchronize()
+    for g, q in zip(grids, qs):
+        g.set_blobs(q)
+    opts = p.ibrd_default_opts(tol=1e-8, precision=p.IBRD_MIXED_REFINE, max_iter=3000, **CHOSEN_SADDLE)
+    t0 = time.perf_counter()
+    p.ibrd_solve_saddle_batch([g.handle for g in grids], gs, None, cs, ls, opts)
+    t_data = time.perf_counter() - t0
+    for g in grids:
+        g.close()
+    del gs, cs
+    torch.cuda.empty_cache()
+    box = np.array([float(side)] * 3)
+    m = p.GNN(LEARNED_CUTOFF, 256)
+    m.init_params(1)
+    t0 = time.perf_counter()
+    losses = m.train(qs[:56], [box] * 56, ls[:56], epochs=80, lr=2e-3)
+    t_train = time.perf_counter() - t0
+
+    def err(a, b):
+        return float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+
+    held = {"learned": float(np.mean([err(m.predict(qs[i], box, float(ls[i].sum())), ls[i]) for i in range(56, 64)])),
+            "uniform": float(np.mean([err(torch.full_like(ls[i], float(ls[i].mean())), ls[i])
+                                      for i in range(56, 64)]))}
+    out = {"model": f"radial-basis graph network, width 64, cutoff {LEARNED_CUTOFF:g}h, {p.ibrd_gnn_num_params()} "
+                    "FP32 parameters; hand-written CUDA training and inference",
+           "training": {"configs": 56, "held_out": 8, "grid": [side] * 3, "data_s": round(t_data, 3),
+                        "train_s": round(t_train, 3), "epochs": 80, "loss_first": float(losses[0]),
+                        "loss_last": float(losses[-1])},
+           "held_out_rel_error": {k: round(v, 4) for k, v in held.items()}, "eval": {}}
+    for name, nblob, spacing in [("256^3, 4096 blobs, spacing 4h", 4096, 4.0),
+                                 ("256^3, 16384 blobs, spacing 3h", 16384, 3.0)]:
+        if nblob == 4096:
+            w = workload("scale")
+            q, gsrc = w.q, w.g
+        else:
+            q, gsrc = rsa_positions(nblob, (256,) * 3, 1.0, spacing, 77), np.ones((256,) * 3)
+        G = p.Grid(256, 256, 256, precision=p.IBRD_MIXED_REFINE)
+        p.ibrd_autotune(G.handle, p.IBRD_MIXED_REFINE)
+        qd = torch.from_numpy(q).cuda()
+        G.set_blobs(qd)
+        gd = torch.from_numpy(gsrc).cuda()
+        total = float(gsrc.sum())
+        N = len(q)
+        c_ex = torch.zeros_like(gd)
+        l_ex = torch.zeros(N, dtype=torch.float64, device="cuda")
+        G.solve_saddle(gd, c=c_ex, lam=l_ex, tol=1e-11, max_iter=3000, precision=p.IBRD_FP64)
+        wbox = np.array([256.0] * 3)
+        lam0 = m.predict(qd, wbox, total)
+        row = {"blobs": N, "rel_error": {"learned": round(err(lam0, l_ex), 4),
+                                         "uniform": round(err(torch.full_like(l_ex, total / N), l_ex), 4)}}
+        for label, guess in [("zero", p.IBRD_GUESS_NONE), ("uniform", p.IBRD_GUESS_UNIFORM),
+                             ("learned", p.IBRD_GUESS_GIVEN)]:
+            ts = []
+            for rep in range(4):
+                c = torch.zeros_like(gd)
+                lam = torch.zeros(N, dtype=torch.float64, device="cuda")
+                rank_barrier(world)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                if guess == p.IBRD_GUESS_GIVEN:
+                    m.predict(qd, wbox, total, out=lam)
+                _, _, info = G.solve_saddle(gd, c=c, lam=lam, tol=1e-8, max_iter=3000,
+                                            precision=p.IBRD_MIXED_REFINE, **dict(CHOSEN_SADDLE, lambda_guess=guess))
+                torch.cuda.synchronize()
+                ts.append(time.perf_counter() - t0)
+            row[label] = {"ms": round(1e3 * min(ts[1:]), 3), "outer_iters": info["outer_iters"],
+                          "vcycles": info["vcycles"], "rel_residual": info["rel_residual"]}
+        t0 = time.perf_counter()
+        for _ in range(5):
+            m.predict(qd, wbox, total, out=lam0)
+        torch.cuda.synchronize()
+        row["predict_ms"] = round(1e3 * (time.perf_counter() - t0) / 5, 3)
+        out["eval"][name] = row
+        G.close()
+        torch.cuda.empty_cache()
+    out["timing"] = "host wall clock per solve (best of 3 after one warm-up), learned includes its inference"
     return out
 
 
@@ -569,6 +678,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-realisations leg")
     ap.add_argument("--no-autotune", action="store_true", help="built-in launch shapes only")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned warm-start leg")
     ap.add_argument("--cpu-columns", type=int, default=3)
     ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--ncu-step", action="store_true", help="profiler range around one step, then exit")

@@ -307,8 +307,8 @@ ibrd_status ibrd_tune_clear(ibrd_grid g);
    0.999, eps 1e-8). Parameters are FP32, in the order W1 (64 x 16, row
    major), c1 (64), E (64 x 16), e (64), W2 (64 x 64), V2 (64 x 64), c2 (64),
    o (64), o0 (1). Positions q are DEVICE arrays of n x 3 FP64 values (as for
-   ibrd_set_blobs) in a periodic box lx x ly x lz; the cutoff must not exceed
-   half the shortest side. A blob with more than max_neighbours neighbours
+   ibrd_set_blobs) in a periodic box lx x ly x lz, within 100 box lengths of
+   the origin; the cutoff must not exceed half the shortest side. A blob with more than max_neighbours neighbours
    makes the call fail with IBRD_ERR_ARG. Multipliers lam must be > 0. Every
    call orders its work on the handle's stream and synchronizes it. */
 typedef struct ibrd_gnn_s* ibrd_gnn;
@@ -326,6 +326,11 @@ const char* ibrd_gnn_last_error(ibrd_gnn m);
    also zeroes Adam's moments and step count. */
 ibrd_status ibrd_gnn_set_params(ibrd_gnn m, const float* theta, int reset_optimizer);
 ibrd_status ibrd_gnn_get_params(ibrd_gnn m, float* theta);
+
+/* Seeded initial parameters: every weight matrix (and o) uniform in
+   +-1/sqrt(fan in) from a splitmix64 stream started at seed, biases 0; zeroes
+   Adam's state. */
+ibrd_status ibrd_gnn_init_params(ibrd_gnn m, unsigned long long seed);
 
 /* Neighbour lists of a configuration (DEVICE outputs): count[n], index[n x
    max_neighbours] (increasing j, then unused), dist[n x max_neighbours] (FP32

@@ -24,7 +24,7 @@ EXPORTED = ["ibrd_default_opts", "ibrd_grid_create", "ibrd_grid_destroy", "ibrd_
             "ibrd_vcycle", "ibrd_vcycle_f32", "ibrd_vcycle_noalloc", "ibrd_spread", "ibrd_interp", "ibrd_solve_reaction", "ibrd_solve_saddle",
             "ibrd_solve_reaction_batch", "ibrd_solve_saddle_batch", "ibrd_autotune", "ibrd_tune_set",
             "ibrd_tune_clear", "ibrd_gnn_num_params", "ibrd_gnn_create", "ibrd_gnn_destroy", "ibrd_gnn_last_error",
-            "ibrd_gnn_set_params", "ibrd_gnn_get_params", "ibrd_gnn_neighbours", "ibrd_gnn_forward",
+            "ibrd_gnn_set_params", "ibrd_gnn_get_params", "ibrd_gnn_init_params", "ibrd_gnn_neighbours", "ibrd_gnn_forward",
             "ibrd_gnn_predict", "ibrd_gnn_loss_grad", "ibrd_gnn_adam_step", "ibrd_gnn_train",
             "ibrd_last_error", "ibrd_status_string", "ibrd_profile_enable", "ibrd_profile_read",
             "ibrd_profile_class_name"]
@@ -122,6 +122,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ibrd_gnn_last_error.restype = ctypes.c_char_p
     lib.ibrd_gnn_set_params.argtypes = [vp, vp, i]
     lib.ibrd_gnn_set_params.restype = i
+    lib.ibrd_gnn_init_params.argtypes = [vp, ctypes.c_ulonglong]
+    lib.ibrd_gnn_init_params.restype = i
     lib.ibrd_gnn_get_params.argtypes = [vp, vp]
     lib.ibrd_gnn_get_params.restype = i
     lib.ibrd_gnn_neighbours.argtypes = [vp, vp, i, d, d, d, vp, vp, vp]
@@ -486,6 +488,9 @@ class GNN:
             raise ValueError("wrong parameter count")
         _gnn_check(self.handle, load_library().ibrd_gnn_set_params(self.handle, t.ctypes.data_as(ctypes.c_void_p),
                                                                     int(bool(reset_optimizer))))
+
+    def init_params(self, seed):
+        _gnn_check(self.handle, load_library().ibrd_gnn_init_params(self.handle, int(seed)))
 
     def get_params(self):
         import numpy as np

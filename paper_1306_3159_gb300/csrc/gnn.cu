@@ -68,32 +68,67 @@ __device__ __forceinline__ double min_image_dist(const double* q, int i, int j, 
   return sqrt(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
 }
 
+// FP32 copies of the positions (x, y, z, 0) for the neighbour screen.
+__global__ void k_gnn_pos32(const double* __restrict__ q, int n, float4* __restrict__ p) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) p[j] = make_float4((float)q[3 * j], (float)q[3 * j + 1], (float)q[3 * j + 2], 0.f);
+}
+
+constexpr int kNbTile = 1024;  // positions staged in shared memory per pass
+
 // Neighbours j != i with r_ij < R, in increasing j; count clipped to kmax,
-// *overflow set when a list was clipped.
-__global__ void k_gnn_neighbours(const double* __restrict__ q, int n, double lx, double ly, double lz, double R,
-                                 int kmax, int* __restrict__ cnt, int* __restrict__ nidx, float* __restrict__ nr,
-                                 int* __restrict__ overflow) {
+// *overflow set when a list was clipped. FP64 is slow on this GPU, so every
+// pair is first screened in FP32 against R + margin (margin far above the
+// FP32 rounding of the coordinates) and only the candidates take the exact
+// FP64 test. The CTA's 8 blobs scan tiles of FP32 positions staged in shared
+// memory.
+__global__ void __launch_bounds__(kWarps * 32) k_gnn_neighbours(const double* __restrict__ q,
+                                                                const float4* __restrict__ p32, int n, double lx,
+                                                                double ly, double lz, double R, float margin,
+                                                                int kmax, int* __restrict__ cnt,
+                                                                int* __restrict__ nidx, float* __restrict__ nr,
+                                                                int* __restrict__ overflow) {
+  __shared__ float4 tile[kNbTile];
   const int lane = threadIdx.x & 31;
   const int i = blockIdx.x * kWarps + (threadIdx.x >> 5);
-  if (i >= n) return;
+  const bool active = i < n;
+  const float4 pi = active ? p32[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float flx = (float)lx, fly = (float)ly, flz = (float)lz;
+  const float ilx = 1.f / flx, ily = 1.f / fly, ilz = 1.f / flz;
+  const float rs = (float)R + margin, rs2 = rs * rs;
   int c = 0;
-  for (int j0 = 0; j0 < n; j0 += 32) {
-    const int j = j0 + lane;
-    double r = 0.0;
-    bool in = false;
-    if (j < n && j != i) {
-      r = min_image_dist(q, i, j, lx, ly, lz);
-      in = r < R;
+  for (int t0 = 0; t0 < n; t0 += kNbTile) {
+    const int tn = min(kNbTile, n - t0);
+    __syncthreads();
+    for (int t = threadIdx.x; t < tn; t += blockDim.x) tile[t] = p32[t0 + t];
+    __syncthreads();
+    if (!active) continue;
+    for (int j0 = 0; j0 < tn; j0 += 32) {
+      const int jl = j0 + lane;
+      const int j = t0 + jl;
+      double r = 0.0;
+      bool in = false;
+      if (jl < tn && j != i) {
+        const float4 pj = tile[jl];
+        float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
+        dx -= flx * rintf(dx * ilx);
+        dy -= fly * rintf(dy * ily);
+        dz -= flz * rintf(dz * ilz);
+        if (dx * dx + dy * dy + dz * dz < rs2) {
+          r = min_image_dist(q, i, j, lx, ly, lz);
+          in = r < R;
+        }
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, in);
+      const int slot = c + __popc(bal & ((1u << lane) - 1u));
+      if (in && slot < kmax) {
+        nidx[(size_t)i * kmax + slot] = j;
+        nr[(size_t)i * kmax + slot] = (float)r;
+      }
+      c += __popc(bal);
     }
-    const unsigned bal = __ballot_sync(0xffffffffu, in);
-    const int slot = c + __popc(bal & ((1u << lane) - 1u));
-    if (in && slot < kmax) {
-      nidx[(size_t)i * kmax + slot] = j;
-      nr[(size_t)i * kmax + slot] = (float)r;
-    }
-    c += __popc(bal);
   }
-  if (lane == 0) {
+  if (active && lane == 0) {
     cnt[i] = c < kmax ? c : kmax;
     if (c > kmax) atomicOr(overflow, 1);
   }
@@ -420,6 +455,7 @@ struct ibrd_gnn_s {
   // per-configuration workspaces (grow only)
   int cap = 0;
   int *cnt = nullptr, *nidx = nullptr, *oflow = nullptr;
+  float4* p32 = nullptr;
   float *nr = nullptr, *x = nullptr, *a1 = nullptr, *h1 = nullptr, *m = nullptr, *a2 = nullptr, *y = nullptr;
   float *dy = nullptr, *da1 = nullptr, *da2 = nullptr, *dm = nullptr, *dh1 = nullptr, *part = nullptr;
   double* loss = nullptr;  // device scalar
@@ -471,6 +507,7 @@ void ensure_cap(ibrd_gnn m, int n) {
   if (n <= m->cap) return;
   const size_t N = (size_t)n, nb = (N + kWarps - 1) / kWarps;
   galloc(&m->cnt, N);
+  galloc(&m->p32, N);
   galloc(&m->nidx, N * m->kmax);
   galloc(&m->nr, N * m->kmax);
   galloc(&m->x, N * K);
@@ -503,8 +540,14 @@ void forward(ibrd_gnn m, const double* q, int n, double lx, double ly, double lz
   const float invR = (float)(1.0 / m->cutoff);
   IBRD_CUDA(cudaMemsetAsync(m->oflow, 0, sizeof(int), m->s));
   prof_begin(P_SETUP, m->s);
-  k_gnn_neighbours<<<nb, kWarps * 32, 0, m->s>>>(q, n, lx, ly, lz, m->cutoff, m->kmax, m->cnt, m->nidx, m->nr,
-                                                 m->oflow);
+  // FP32 screen margin: well above the FP32 error of a minimum-image distance
+  // (a few ulps of the box side)
+  const float margin = (float)(1e-3 * m->cutoff + 1e-5 * std::max(lx, std::max(ly, lz)));
+  k_gnn_pos32<<<(n + 255) / 256, 256, 0, m->s>>>(q, n, m->p32);
+  prof_end(P_SETUP, m->s, "gnn_pos32");
+  prof_begin(P_SETUP, m->s);
+  k_gnn_neighbours<<<nb, kWarps * 32, 0, m->s>>>(q, m->p32, n, lx, ly, lz, m->cutoff, margin, m->kmax, m->cnt,
+                                                 m->nidx, m->nr, m->oflow);
   prof_end(P_SETUP, m->s, "gnn_neighbours");
   prof_begin(P_SETUP, m->s);
   k_gnn_layer1<<<nb, kWarps * 32, 0, m->s>>>(m->th, n, invR, m->kmax, m->cnt, m->nr, m->x, m->a1, m->h1);
@@ -607,7 +650,7 @@ void ibrd_gnn_destroy(ibrd_gnn m) {
   for (void* p : {(void*)m->th, (void*)m->g, (void*)m->m1, (void*)m->m2, (void*)m->cnt, (void*)m->nidx,
                   (void*)m->oflow, (void*)m->nr, (void*)m->x, (void*)m->a1, (void*)m->h1, (void*)m->m,
                   (void*)m->a2, (void*)m->y, (void*)m->dy, (void*)m->da1, (void*)m->da2, (void*)m->dm,
-                  (void*)m->dh1, (void*)m->part, (void*)m->loss})
+                  (void*)m->dh1, (void*)m->part, (void*)m->loss, (void*)m->p32})
     if (p) cudaFree(p);
   if (m->host) cudaFreeHost(m->host);
   if (prev >= 0 && prev != m->dev) cudaSetDevice(prev);
@@ -625,6 +668,35 @@ ibrd_status ibrd_gnn_set_params(ibrd_gnn m, const float* theta, int reset_optimi
       IBRD_CUDA(cudaMemsetAsync(m->m2, 0, sizeof(float) * NPARAM, m->s));
       m->step = 0;
     }
+    IBRD_CUDA(cudaStreamSynchronize(m->s));
+    return IBRD_OK;
+  });
+}
+
+ibrd_status ibrd_gnn_init_params(ibrd_gnn m, unsigned long long seed) {
+  return gnn_guarded(m, "ibrd_gnn_init_params", [&]() {
+    // splitmix64 stream -> uniform in [-1, 1) (53-bit mantissa)
+    unsigned long long st = seed;
+    auto next = [&st]() {
+      unsigned long long z = (st += 0x9E3779B97F4A7C15ull);
+      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+      z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+      z ^= z >> 31;
+      return (double)(z >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+    };
+    std::vector<float> th(NPARAM, 0.f);
+    auto fill = [&](int off, int count, double lim) {
+      for (int k = 0; k < count; ++k) th[off + k] = (float)(lim * next());
+    };
+    fill(OFF_W1, H * K, 1.0 / std::sqrt((double)K));
+    fill(OFF_E, H * K, 1.0 / std::sqrt((double)K));
+    fill(OFF_W2, H * H, 1.0 / std::sqrt((double)H));
+    fill(OFF_V2, H * H, 1.0 / std::sqrt((double)H));
+    fill(OFF_O, H, 1.0 / std::sqrt((double)H));
+    IBRD_CUDA(cudaMemcpyAsync(m->th, th.data(), sizeof(float) * NPARAM, cudaMemcpyHostToDevice, m->s));
+    IBRD_CUDA(cudaMemsetAsync(m->m1, 0, sizeof(float) * NPARAM, m->s));
+    IBRD_CUDA(cudaMemsetAsync(m->m2, 0, sizeof(float) * NPARAM, m->s));
+    m->step = 0;
     IBRD_CUDA(cudaStreamSynchronize(m->s));
     return IBRD_OK;
   });

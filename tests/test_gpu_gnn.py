@@ -144,3 +144,21 @@ def test_learned_warm_start_saddle(ibrd):
     assert info["rel_residual"] <= tol
     assert rel_l2(host(c), c_ref) < 1e-11 and rel_l2(host(lam), lam_ref) < 1e-11
     torch.cuda.synchronize()
+
+
+def test_seeded_init(ibrd):
+    """The library's seeded initial parameters: reproducible, seed-dependent,
+    within +-1/sqrt(fan in), biases zero."""
+    m = ibrd.GNN(8.0, 16)
+    m.init_params(9)
+    a = m.get_params()
+    m.init_params(9)
+    b = m.get_params()
+    m.init_params(10)
+    c = m.get_params()
+    assert np.array_equal(a, b) and not np.array_equal(a, c)
+    p = gnn.unpack(a.astype(np.float64))
+    for name, lim in [("W1", 0.25), ("E", 0.25), ("W2", 0.125), ("V2", 0.125), ("o", 0.125)]:
+        assert np.abs(p[name]).max() <= lim and np.abs(p[name]).max() > 0.9 * lim
+    for name in ("c1", "e", "c2", "o0"):
+        assert not p[name].any()
