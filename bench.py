@@ -460,13 +460,15 @@ LEARNED_CUTOFF = 24.0
 
 
 def run_learned(p, torch, world, args):
-    """The learned multiplier predictor as the warm start of the saddle solve.
+    """The learned multiplier predictor (and the penalty form) as the start of
+    the saddle solve.
     Training data: 64 saddle solves at 128^3 (blob density 1.2e-4 to 2e-3 per
     h^3, RSA spacing 3h-4h, unit source) from the batched entry point in the
     chosen mode; 56 train the network (80 epochs of Adam), 8 are held out.
     Evaluation: time to 1e-8 of the chosen saddle solve from a zero start, the
-    uniform share and the learned prediction (its inference inside the timed
-    region) on the 256^3 workloads with 4096 blobs (spacing 4h) and 16384 blobs
+    uniform share, the learned prediction (its inference inside the timed
+    region) and the penalty form (a reaction-limited solve with the uniform
+    rate 1000 to 1e-2, inside the timed region) on the 256^3 workloads with 4096 blobs (spacing 4h) and 16384 blobs
     (spacing 3h)."""
     import time
     import numpy as np
@@ -535,7 +537,7 @@ def run_learned(p, torch, world, args):
         row = {"blobs": N, "rel_error": {"learned": round(err(lam0, l_ex), 4),
                                          "uniform": round(err(torch.full_like(l_ex, total / N), l_ex), 4)}}
         for label, guess in [("zero", p.IBRD_GUESS_NONE), ("uniform", p.IBRD_GUESS_UNIFORM),
-                             ("learned", p.IBRD_GUESS_GIVEN)]:
+                             ("learned", p.IBRD_GUESS_GIVEN), ("penalty_kappa_1000", p.IBRD_GUESS_PENALTY)]:
             ts = []
             for rep in range(4):
                 c = torch.zeros_like(gd)
@@ -559,7 +561,8 @@ def run_learned(p, torch, world, args):
         out["eval"][name] = row
         G.close()
         torch.cuda.empty_cache()
-    out["timing"] = "host wall clock per solve (best of 3 after one warm-up), learned includes its inference"
+    out["timing"] = ("host wall clock per solve (best of 3 after one warm-up); learned includes its inference, "
+                     "penalty its reaction-limited solve")
     return out
 
 

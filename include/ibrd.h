@@ -54,7 +54,7 @@ typedef enum {
 enum { IBRD_PESKIN4 = 4, IBRD_PESKIN3 = 3 };          /* kernel width w */
 enum { IBRD_FP64 = 0, IBRD_MIXED_FP32 = 1, IBRD_MIXED_REFINE = 2 };  /* precision */
 enum { IBRD_PRECOND_SCHUR = 0, IBRD_PRECOND_DIAG = 1 }; /* saddle preconditioner */
-enum { IBRD_GUESS_NONE = 0, IBRD_GUESS_UNIFORM = 1, IBRD_GUESS_GIVEN = 2 }; /* saddle warm start */
+enum { IBRD_GUESS_NONE = 0, IBRD_GUESS_UNIFORM = 1, IBRD_GUESS_GIVEN = 2, IBRD_GUESS_PENALTY = 3 }; /* saddle start */
 
 /* Solver options. ibrd_default_opts fills the defaults noted here. */
 typedef struct {
@@ -105,8 +105,18 @@ typedef struct {
                         in the preconditioner's precision plus, when
                         alpha = 0, the constant <f/xi - J c~> (Appendix A
                         steps 3-5 with lambda0 for the Schur solution). The
-                        solve then runs to tol as from any other start. */
+                        solve then runs to tol as from any other start.
+                        IBRD_GUESS_PENALTY: [c0; lambda0] from the penalty
+                        form (Sec. II.B: the reaction-limited system with a
+                        large rate): c0 solves
+                        (A + zeta kappa_p S J) c0 = g + (zeta kappa_p / xi) S f
+                        to relative residual penalty_tol (a reaction-limited
+                        solve with uniform rate zeta kappa_p, in this solve's
+                        precision mode, its V-cycles counted in vcycles), and
+                        lambda0 = kappa_p (J c0 - f / xi). */
   int warm_cycles;   /* V-cycles forming c0 of a warm start (2) */
+  double penalty_kappa; /* kappa_p of IBRD_GUESS_PENALTY (1000) */
+  double penalty_tol;   /* relative residual of its reaction solve (1e-2) */
 } ibrd_solve_opts;
 
 /* Solve report. residual_history, if non-NULL, is a caller-owned HOST array
@@ -334,7 +344,8 @@ ibrd_status ibrd_gnn_init_params(ibrd_gnn m, unsigned long long seed);
 
 /* Neighbour lists of a configuration (DEVICE outputs): count[n], index[n x
    max_neighbours] (increasing j, then unused), dist[n x max_neighbours] (FP32
-   distances). */
+   distances; the neighbour sets follow the FP64 minimum-image distance, a
+   stored distance may be the FP32 one, within a few ulps of the box side). */
 ibrd_status ibrd_gnn_neighbours(ibrd_gnn m, const double* q, int n, double lx, double ly, double lz, int* count,
                                 int* index, float* dist);
 

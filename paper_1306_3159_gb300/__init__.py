@@ -8,14 +8,14 @@ Importing this package does not need a GPU; calling into it does, and a
 missing or unloadable library raises ``ImportError``/``RuntimeError``: there is
 no CPU fallback.
 """
-from ._abi import (IBRD_GUESS_NONE, IBRD_GUESS_UNIFORM, IBRD_GUESS_GIVEN, IBRD_FP64, IBRD_MIXED_FP32, IBRD_MIXED_REFINE, IBRD_PESKIN3, IBRD_PESKIN4, IBRD_PRECOND_DIAG,
+from ._abi import (IBRD_GUESS_NONE, IBRD_GUESS_UNIFORM, IBRD_GUESS_GIVEN, IBRD_GUESS_PENALTY, IBRD_FP64, IBRD_MIXED_FP32, IBRD_MIXED_REFINE, IBRD_PESKIN3, IBRD_PESKIN4, IBRD_PRECOND_DIAG,
                    IBRD_PRECOND_SCHUR, IbrdError, Grid, SolveOpts, load_library, EXPORTED,
                    ibrd_apply_L, ibrd_grid_create, ibrd_grid_destroy, ibrd_interp, ibrd_set_blobs,
                    ibrd_solve_reaction, ibrd_solve_saddle, ibrd_solve_reaction_batch, ibrd_solve_saddle_batch,
                    ibrd_autotune, ibrd_tune_set, ibrd_tune_clear, GNN, ibrd_gnn_num_params, ibrd_spread, ibrd_vcycle, ibrd_vcycle_f32, ibrd_last_error,
                    ibrd_default_opts, ibrd_profile_enable, ibrd_profile_read)
 
-__all__ = ["IBRD_GUESS_NONE", "IBRD_GUESS_UNIFORM", "IBRD_GUESS_GIVEN", "IBRD_FP64", "IBRD_MIXED_FP32", "IBRD_MIXED_REFINE", "IBRD_PESKIN3", "IBRD_PESKIN4", "IBRD_PRECOND_DIAG",
+__all__ = ["IBRD_GUESS_NONE", "IBRD_GUESS_UNIFORM", "IBRD_GUESS_GIVEN", "IBRD_GUESS_PENALTY", "IBRD_FP64", "IBRD_MIXED_FP32", "IBRD_MIXED_REFINE", "IBRD_PESKIN3", "IBRD_PESKIN4", "IBRD_PRECOND_DIAG",
            "IBRD_PRECOND_SCHUR", "IbrdError", "Grid", "SolveOpts", "load_library", "EXPORTED",
            "ibrd_apply_L", "ibrd_grid_create", "ibrd_grid_destroy", "ibrd_interp", "ibrd_set_blobs",
            "ibrd_solve_reaction", "ibrd_solve_saddle", "ibrd_solve_reaction_batch", "ibrd_solve_saddle_batch",

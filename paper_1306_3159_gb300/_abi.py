@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(PKG, "libibrd.so")
 IBRD_PESKIN4, IBRD_PESKIN3 = 4, 3
 IBRD_FP64, IBRD_MIXED_FP32, IBRD_MIXED_REFINE = 0, 1, 2
 IBRD_PRECOND_SCHUR, IBRD_PRECOND_DIAG = 0, 1
-IBRD_GUESS_NONE, IBRD_GUESS_UNIFORM, IBRD_GUESS_GIVEN = 0, 1, 2
+IBRD_GUESS_NONE, IBRD_GUESS_UNIFORM, IBRD_GUESS_GIVEN, IBRD_GUESS_PENALTY = 0, 1, 2, 3
 
 STATUS = {0: "IBRD_OK", 1: "IBRD_ERR_ARG", 2: "IBRD_ERR_CUDA", 3: "IBRD_ERR_OOM", 4: "IBRD_ERR_NOT_CONVERGED",
           5: "IBRD_ERR_BREAKDOWN", 6: "IBRD_ERR_NONFINITE", 7: "IBRD_ERR_TIMEOUT", 8: "IBRD_ERR_STATE"}
@@ -38,7 +38,8 @@ class SolveOpts(ctypes.Structure):
                 ("zeta", ctypes.c_double), ("xi", ctypes.c_double), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
                 ("precision", ctypes.c_int), ("use_guess", ctypes.c_int),
                 ("reorth_eta", ctypes.c_double), ("graphs", ctypes.c_int), ("inner_tol", ctypes.c_double),
-                ("lambda_guess", ctypes.c_int), ("warm_cycles", ctypes.c_int)]
+                ("lambda_guess", ctypes.c_int), ("warm_cycles", ctypes.c_int),
+                ("penalty_kappa", ctypes.c_double), ("penalty_tol", ctypes.c_double)]
 
 
 class SolveInfo(ctypes.Structure):

@@ -1146,6 +1146,49 @@ void saddle_warm_start(ibrd_grid g, const ibrd_solve_opts& o, const double* b, d
   }
 }
 
+// Warm start from the penalty form of the saddle point (Sec. II.B: the
+// reaction-limited system with a large rate is a penalty method for the
+// constrained one): relaxing xi J c = f to xi J c - (xi / kappa_p) lambda = f
+// gives (A + zeta kappa_p S J) c = g + (zeta kappa_p / xi) S f and
+// lambda = kappa_p (J c - f / xi). The first is a reaction-limited solve with
+// the uniform rate zeta kappa_p (to relative residual o.penalty_tol, in the
+// solve's precision mode); the pair starts the saddle solve. b = [g; f];
+// writes [c; lambda] into x.
+void saddle_penalty_start(ibrd_grid g, const ibrd_solve_opts& o, const double* b, double* x) {
+  const size_t nc = g->d.n();
+  const int N = g->blobs.n;
+  const double kp = o.penalty_kappa;
+  const double rate = o.zeta * kp;
+  double* kappa = g->nv[3];
+  const int nb = std::min(1024, (N + 255) / 256);
+  prof_begin(P_SMALL, g->s);
+  k_fill_or_scale<<<nb, 256, 0, g->s>>>(kappa, N, rate, 0);
+  prof_end(P_SMALL, g->s, "penalty_kappa");
+  double* bp = pfield<double>(g, 2);
+  IBRD_CUDA(cudaMemcpyAsync(bp, b, sizeof(double) * nc, cudaMemcpyDeviceToDevice, g->s));
+  launch_spread<double>(g->blobs, g->d, b + nc, nullptr, (o.zeta * kp / o.xi) * inv_h3(g), bp, 1, g->s);
+  const double sigma = g->alpha > 0.0 ? g->alpha : rate * N / ((double)nc * g->h * g->h * g->h);
+  ibrd_solve_opts op = o;
+  op.tol = o.penalty_tol;
+  History none;
+  SolveResult R;
+  if (o.precision == IBRD_FP64) {
+    ReactionOp<double> r64(g, kappa, sigma, op);
+    R = fgmres<double>(g, r64, bp, x, nc, op, op.tol, op.max_iter, true, none);
+  } else if (o.precision == IBRD_MIXED_FP32) {
+    ReactionOp<float, double> r(g, kappa, sigma, op);
+    R = fgmres<double>(g, r, bp, x, nc, op, op.tol, op.max_iter, true, none);
+  } else {
+    ReactionOp<double> r64(g, kappa, sigma, op);
+    ReactionOp<float> r32(g, kappa, sigma, op);
+    R = refine(g, r64, r32, bp, x, nc, op, true, none);
+  }
+  if (R.st == IBRD_ERR_NONFINITE) throw ArgError{IBRD_ERR_NONFINITE, "penalty start: non-finite residual"};
+  // lambda = kappa_p J c - (kappa_p / xi) f
+  launch_interp<double>(g->blobs, g->d, x, kp, x + nc, g->s);
+  launch_nvec_affine(x + nc, x + nc, N, 1.0, nullptr, b + nc, -kp / o.xi, g->s);
+}
+
 // M_11 = (J A^-1 S)_11 of blob 0 by V-cycle iteration to convergence (used by
 // the diagonal preconditioner, Eq. Schur_diagonal).
 double compute_gamma(ibrd_grid g, const ibrd_solve_opts& o) {
@@ -1214,7 +1257,9 @@ ibrd_solve_opts resolve_opts(ibrd_grid g, const ibrd_solve_opts* in) {
       (o.precision != IBRD_FP64 && o.precision != IBRD_MIXED_FP32 && o.precision != IBRD_MIXED_REFINE) ||
       (o.precond != IBRD_PRECOND_SCHUR && o.precond != IBRD_PRECOND_DIAG) ||
       (o.lambda_guess != IBRD_GUESS_NONE && o.lambda_guess != IBRD_GUESS_UNIFORM &&
-       o.lambda_guess != IBRD_GUESS_GIVEN) || o.warm_cycles < 1 || o.warm_cycles > 64)
+       o.lambda_guess != IBRD_GUESS_GIVEN && o.lambda_guess != IBRD_GUESS_PENALTY) || o.warm_cycles < 1 ||
+      o.warm_cycles > 64 || !(o.penalty_kappa > 0.0) || !std::isfinite(o.penalty_kappa) ||
+      !(o.penalty_tol > 0.0 && o.penalty_tol < 1.0))
     throw ArgError{IBRD_ERR_ARG, "invalid solver options"};
   return o;
 }
@@ -1451,6 +1496,8 @@ void ibrd_default_opts(ibrd_solve_opts* o) {
   o->inner_tol = 1e-4;
   o->lambda_guess = IBRD_GUESS_NONE;
   o->warm_cycles = 2;
+  o->penalty_kappa = 1000.0;
+  o->penalty_tol = 1e-2;
 }
 
 const char* ibrd_status_string(int st) {
@@ -1713,7 +1760,9 @@ ibrd_status ibrd_solve_saddle(ibrd_grid g, const double* rhs, const double* f, d
     if (warm) {
       if (o.lambda_guess == IBRD_GUESS_GIVEN)
         IBRD_CUDA(cudaMemcpyAsync(g->xs + nc, lambda, sizeof(double) * N, cudaMemcpyDeviceToDevice, g->s));
-      if (o.precision == IBRD_FP64)
+      if (o.lambda_guess == IBRD_GUESS_PENALTY)
+        saddle_penalty_start(g, o, g->bs, g->xs);
+      else if (o.precision == IBRD_FP64)
         saddle_warm_start<double>(g, o, g->bs, g->xs, o.lambda_guess, o.warm_cycles);
       else
         saddle_warm_start<float>(g, o, g->bs, g->xs, o.lambda_guess, o.warm_cycles);

@@ -78,10 +78,11 @@ constexpr int kNbTile = 1024;  // positions staged in shared memory per pass
 
 // Neighbours j != i with r_ij < R, in increasing j; count clipped to kmax,
 // *overflow set when a list was clipped. FP64 is slow on this GPU, so every
-// pair is first screened in FP32 against R + margin (margin far above the
-// FP32 rounding of the coordinates) and only the candidates take the exact
-// FP64 test. The CTA's 8 blobs scan tiles of FP32 positions staged in shared
-// memory.
+// pair is measured in FP32 and only pairs within a margin of R (the margin far
+// above the FP32 rounding of the coordinates) take the exact FP64 test: the
+// neighbour sets are the FP64 definition's; a stored distance is the FP32 one
+// (within a few ulps of the box side) away from the boundary. The CTA's 8 blobs
+// scan tiles of FP32 positions staged in shared memory.
 __global__ void __launch_bounds__(kWarps * 32) k_gnn_neighbours(const double* __restrict__ q,
                                                                 const float4* __restrict__ p32, int n, double lx,
                                                                 double ly, double lz, double R, float margin,
@@ -96,6 +97,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_gnn_neighbours(const double* __
   const float flx = (float)lx, fly = (float)ly, flz = (float)lz;
   const float ilx = 1.f / flx, ily = 1.f / fly, ilz = 1.f / flz;
   const float rs = (float)R + margin, rs2 = rs * rs;
+  const float ri = (float)R - margin, ri2 = ri > 0.f ? ri * ri : 0.f;
   int c = 0;
   for (int t0 = 0; t0 < n; t0 += kNbTile) {
     const int tn = min(kNbTile, n - t0);
@@ -114,9 +116,17 @@ __global__ void __launch_bounds__(kWarps * 32) k_gnn_neighbours(const double* __
         dx -= flx * rintf(dx * ilx);
         dy -= fly * rintf(dy * ily);
         dz -= flz * rintf(dz * ilz);
-        if (dx * dx + dy * dy + dz * dz < rs2) {
-          r = min_image_dist(q, i, j, lx, ly, lz);
-          in = r < R;
+        const float d2 = dx * dx + dy * dy + dz * dz;
+        if (d2 < rs2) {
+          if (d2 < ri2) {
+            // clearly inside: the FP32 distance is kept
+            r = (double)sqrtf(d2);
+            in = true;
+          } else {
+            // within the margin of R: the exact FP64 test decides
+            r = min_image_dist(q, i, j, lx, ly, lz);
+            in = r < R;
+          }
         }
       }
       const unsigned bal = __ballot_sync(0xffffffffu, in);

@@ -1,5 +1,5 @@
 """The learned multiplier predictor's CUDA kernels against its FP64 definition
-(oracle/gnn.py), through the C ABI: neighbour lists bit for bit, the forward
+(oracle/gnn.py), through the C ABI: neighbour sets exactly, the forward
 pass, loss and gradient within FP32 rounding, Adam's update, the softmax
 prediction, training, and its use as the warm start of a saddle solve."""
 import numpy as np
@@ -48,7 +48,8 @@ def test_neighbours_exact(ibrd, n, side, R):
     for i in range(n):
         assert cnt[i] == len(nb[i])
         assert list(idx[i, :cnt[i]]) == list(nb[i])
-        assert np.array_equal(dist[i, :cnt[i]], rr[i].astype(np.float32))
+        # distances from FP32 coordinates: within a few ulps of the box side
+        assert np.abs(dist[i, :cnt[i]] - rr[i]).max(initial=0.0) < 4e-6 * side
 
 
 def test_forward_loss_gradient_and_adam(ibrd):

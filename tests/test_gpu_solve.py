@@ -264,7 +264,8 @@ def test_batch_matches_single_solves(ibrd, precision):
 def test_saddle_warm_start(ibrd, small, precision):
     """Saddle solves started from a guess of lambda (uniform share, the exact
     multipliers with 1 % noise, and an all-zero guess, which falls back to the
-    uniform share) and the grid field built from it by Appendix A steps 3-5
+    uniform share) and the grid field built from it by Appendix A steps 3-5,
+    or from the penalty form (a reaction-limited solve with a large rate),
     reach the tolerance and the oracle's solution; the exact multipliers never
     cost more iterations than a zero start."""
     import torch
@@ -275,7 +276,8 @@ def test_saddle_warm_start(ibrd, small, precision):
     err = 1e-11
     noise = np.random.default_rng(3).standard_normal(len(lam_ref))
     _, _, cold = g.solve_saddle(dev(w.g), tol=tol, precision=precision, max_iter=400)
-    for guess, lam0 in [(1, None), (2, lam_ref * (1 + 0.01 * noise)), (2, np.zeros_like(lam_ref)), (2, lam_ref)]:
+    for guess, lam0 in [(1, None), (2, lam_ref * (1 + 0.01 * noise)), (2, np.zeros_like(lam_ref)), (2, lam_ref),
+                        (3, None)]:
         lam = dev(lam0) if lam0 is not None else None
         c, lam, info = g.solve_saddle(dev(w.g), lam=lam, tol=tol, precision=precision, max_iter=400,
                                       lambda_guess=guess, warm_cycles=3)

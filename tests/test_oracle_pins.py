@@ -389,3 +389,21 @@ def test_cubic_lattice_rate_matches_fit(L, spacing):
     b0 = outputs.beta0(c.mean(), 1.0 / V, a, 1.0, len(q), V)
     fit = outputs.beta0_cubic_fit(phi, GOLD["cubic_fit_b"]["value"], GOLD["cubic_fit_c"]["value"])
     assert abs(b0 - fit) < 0.01 * fit
+
+
+def test_penalty_form_converges_to_saddle_point():
+    """Sec. II.B: the reaction-limited system with a uniform rate kappa is a
+    penalty form of the diffusion-limited saddle point; lambda = kappa J c of
+    the reaction solution approaches the saddle point's multipliers as kappa
+    grows, with an error that falls like 1/kappa."""
+    from oracle import direct
+    from synthetic import rsa_positions
+    q = rsa_positions(5, (16, 16, 16), 1.0, 4.0, 8)
+    g = np.ones((16, 16, 16))
+    _, lam, _ = direct.solve_saddle(q, g, 1.0, 1.0, 0.0)
+    errs = []
+    for kappa in (1e2, 1e3, 1e4):
+        _, u, _ = direct.solve_reaction(q, np.full(len(q), kappa), g, 1.0, 1.0, 0.0)
+        errs.append(np.linalg.norm(u - lam) / np.linalg.norm(lam))
+    assert errs[0] < 0.2
+    assert 7.0 < errs[0] / errs[1] < 13.0 and 7.0 < errs[1] / errs[2] < 13.0
