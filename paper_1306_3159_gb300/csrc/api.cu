@@ -679,7 +679,8 @@ struct History {
 // itself.
 template <typename E>
 SolveResult fgmres(ibrd_grid g, LinOp<E>& op, const E* b, E* x, size_t n, const ibrd_solve_opts& o, double tol,
-                   int max_iter, bool zero_guess, History& hist, bool trust_estimate = false) {
+                   int max_iter, bool zero_guess, History& hist, bool trust_estimate = false,
+                   const double* b_sq = nullptr, double b_norm = -1.0) {
   SolveResult R;
   const int m = std::max(1, o.restart);
   const size_t ld = ensure_krylov<E>(g, n, m);
@@ -687,8 +688,14 @@ SolveResult fgmres(ibrd_grid g, LinOp<E>& op, const E* b, E* x, size_t n, const 
   const int ldh = m + 1;
   E* V = reinterpret_cast<E*>(g->V);
   E* Z = reinterpret_cast<E*>(g->Z);
-  launch_dot<E>(b, b, n, g->partial, g->scal + S_BB, 1.0, g->s);
-  const double bnorm = std::sqrt(host_scalar(g, S_BB));
+  // ||b||: from the caller when it already holds it (b_sq: ||b||^2 on the
+  // device, b_norm: ||b|| on the host), else one reduction
+  const bool known = b_sq && b_norm >= 0.0;
+  double bnorm = b_norm;
+  if (!known) {
+    launch_dot<E>(b, b, n, g->partial, g->scal + S_BB, 1.0, g->s);
+    bnorm = std::sqrt(host_scalar(g, S_BB));
+  }
   if (!std::isfinite(bnorm)) {
     R.st = IBRD_ERR_NONFINITE;
     return R;
@@ -697,16 +704,26 @@ SolveResult fgmres(ibrd_grid g, LinOp<E>& op, const E* b, E* x, size_t n, const 
     IBRD_CUDA(cudaMemsetAsync(x, 0, sizeof(E) * n, g->s));
     return R;
   }
-  // r0 = b - K x0
-  if (zero_guess) {
+  // r0 = b - K x0; from a zero guess with ||b|| known, V[0] is scaled
+  // straight from b
+  bool first_from_b = false;
+  double beta;
+  if (zero_guess && known) {
     IBRD_CUDA(cudaMemsetAsync(x, 0, sizeof(E) * n, g->s));
-    IBRD_CUDA(cudaMemcpyAsync(V, b, sizeof(E) * n, cudaMemcpyDeviceToDevice, g->s));
+    launch_sqrt_scalar(b_sq, g->scal + S_NORM, g->s);
+    beta = bnorm;
+    first_from_b = true;
   } else {
-    op.residual(b, x, V);
+    if (zero_guess) {
+      IBRD_CUDA(cudaMemsetAsync(x, 0, sizeof(E) * n, g->s));
+      IBRD_CUDA(cudaMemcpyAsync(V, b, sizeof(E) * n, cudaMemcpyDeviceToDevice, g->s));
+    } else {
+      op.residual(b, x, V);
+    }
+    launch_dot<E>(V, V, n, g->partial, g->scal + S_TMP2, 1.0, g->s);
+    launch_sqrt_scalar(g->scal + S_TMP2, g->scal + S_NORM, g->s);
+    beta = std::sqrt(host_scalar(g, S_TMP2));
   }
-  launch_dot<E>(V, V, n, g->partial, g->scal + S_TMP2, 1.0, g->s);
-  launch_sqrt_scalar(g->scal + S_TMP2, g->scal + S_NORM, g->s);
-  double beta = std::sqrt(host_scalar(g, S_TMP2));
   while (true) {
     R.rel = beta / bnorm;
     if (!std::isfinite(R.rel)) {
@@ -719,7 +736,8 @@ SolveResult fgmres(ibrd_grid g, LinOp<E>& op, const E* b, E* x, size_t n, const 
       break;
     }
     // V[0] = r / beta, gvec = [beta, 0, ...]
-    launch_scale_by_inv<E>(V, V, n, g->scal + S_NORM, 1.0, g->s);
+    launch_scale_by_inv<E>(first_from_b ? b : V, V, n, g->scal + S_NORM, 1.0, g->s);
+    first_from_b = false;
     prof_begin(P_SMALL, g->s);
     k_set_gvec<<<1, 64, 0, g->s>>>(g->gvec, m, g->scal + S_NORM);
     prof_end(P_SMALL, g->s, "set_gvec");
@@ -830,9 +848,11 @@ SolveResult refine(ibrd_grid g, LinOp<double>& op64, LinOp<float>& op32, const d
   // range); the step's correction is then divided by sigma.
   double sigma = 1.0;
   auto set_sigma = [&](double expect) { sigma = std::ldexp(1.0, -std::ilogb(std::max(expect, 1e-300))); };
+  double r32norm = 0.0;  // ||sigma r|| of the FP32 right-hand side, ||.||^2 kept in S_TMP2
   auto to_f32 = [&](const double* v) {
     launch_convert_sq(v, g->ir_r32, n, sigma, g->partial, g->scal + S_TMP2, g->s);
-    return std::sqrt(host_scalar(g, S_TMP2)) / sigma;
+    r32norm = std::sqrt(host_scalar(g, S_TMP2));
+    return r32norm / sigma;
   };
   double rnorm;
   set_sigma(bnorm);
@@ -865,7 +885,8 @@ SolveResult refine(ibrd_grid g, LinOp<double>& op64, LinOp<float>& op32, const d
     const double tol_in = std::max(o.inner_tol, 0.5 * o.tol / R.rel);
     hist.scale = R.rel;
     const SolveResult I =
-        fgmres<float>(g, op32, g->ir_r32, g->ir_d32, n, o, tol_in, o.max_iter - R.iters, true, hist, true);
+        fgmres<float>(g, op32, g->ir_r32, g->ir_d32, n, o, tol_in, o.max_iter - R.iters, true, hist, true,
+                      g->scal + S_TMP2, r32norm);
     R.iters += I.iters;
     g->refinements++;
     if (I.st == IBRD_ERR_NONFINITE) {
