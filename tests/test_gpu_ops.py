@@ -138,12 +138,15 @@ def test_vcycle_f32(ibrd, dims, alpha):
     assert rel_max(x.cpu().numpy().astype(np.float64), want) < 2e-5
 
 
-@pytest.mark.parametrize("dims,alpha", [((16, 16, 16), 0.0), ((12, 8, 20), 0.3), ((40, 40, 40), 0.0)])
+@pytest.mark.parametrize("dims,alpha", [((16, 16, 16), 0.0), ((12, 8, 20), 0.3), ((40, 40, 40), 0.0),
+                                        ((24, 24, 24), 0.0), ((40, 40, 20), 0.2), ((64, 64, 8), 0.0)])
 def test_vcycle_f32_exact_level(ibrd, dims, alpha):
     """FP32 V-cycles whose hierarchy ends in the exact Hartley-transform solve:
-    at 16^3 and 12 x 8 x 20 the finest level itself is exact (the result is
-    the FFT Green's function solution); at 40^3 the exact level is 10^3 below
-    two smoothed levels."""
+    at 16^3 and 12 x 8 x 20 the finest level itself is exact (one CTA; the
+    result is the FFT Green's function solution); at 40^3 the exact level is
+    10^3 below two smoothed levels; 24^3, 40 x 40 x 20 and 64 x 64 x 8 are
+    exact levels above 4096 cells (three launches: plane transforms, column
+    transforms with the scaling, plane transforms)."""
     import torch
     nx, ny, nz = dims
     rng = np.random.default_rng(17)
