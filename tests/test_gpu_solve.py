@@ -286,3 +286,35 @@ def test_saddle_warm_start(ibrd, small, precision):
         if lam0 is not None and np.array_equal(lam0, lam_ref):
             assert info["outer_iters"] <= cold["outer_iters"]
     torch.cuda.synchronize()
+
+
+def test_batch_reports_each_problem(ibrd):
+    """A failing problem does not stop the others: a NaN source gives
+    IBRD_ERR_NONFINITE for its problem only, a handle without blobs gives
+    IBRD_ERR_STATE for a saddle solve, and the batch returns the first failure
+    in index order while the other problems are solved."""
+    import torch
+    from synthetic import batch_workloads
+    ws = batch_workloads(3, sides=(32,), n_lo=8, n_hi=20, seed=21)
+    streams = [torch.cuda.Stream() for _ in ws]
+    grids = [ibrd.Grid(*w.dims, stream=s.cuda_stream) for w, s in zip(ws, streams)]
+    gs = [dev(w.g) for w in ws]
+    gs[1][0, 0, 0] = float("nan")
+    ks = [dev(w.kappa) for w in ws]
+    cs = [torch.zeros_like(x) for x in gs]
+    ls = [torch.zeros(len(w.q), dtype=torch.float64, device="cuda") for w in ws]
+    qs = [dev(w.q) for w in ws]
+    torch.cuda.synchronize()
+    for i in (0, 1):
+        grids[i].set_blobs(qs[i])
+    opts = ibrd.ibrd_default_opts(tol=1e-10)
+    hs = [g.handle for g in grids]
+    out = ibrd.ibrd_solve_reaction_batch(hs[:2], ks[:2], gs[:2], cs[:2], opts, threads=2, raise_on_error=False)
+    assert [o["status"] for o in out] == [0, 6] and out[0]["rel_residual"] <= 1e-10
+    with pytest.raises(ibrd.IbrdError) as e:
+        ibrd.ibrd_solve_saddle_batch(hs, [gs[0], gs[2], gs[2]], None, cs, ls, opts, threads=3)
+    assert e.value.status == 8  # problem 2 has no blobs; problems 0 and 1 are solved
+    out = ibrd.ibrd_solve_saddle_batch(hs, [gs[0], gs[2], gs[2]], None, cs, ls, opts, threads=3,
+                                       raise_on_error=False)
+    assert [o["status"] for o in out] == [0, 0, 8]
+    torch.cuda.synchronize()
