@@ -687,6 +687,10 @@ void launch_hartley_solve(const float* tab, const float* b, const double* bshift
     float* tmp = const_cast<float*>(tab) + ((size_t)d.nx * d.nx + (size_t)d.ny * d.ny + (size_t)d.nz * d.nz + d.n());
     const size_t smp = sizeof(float) * ((size_t)d.nx * (d.nx + 1) + (size_t)d.ny * (d.ny + 1) + 2 * (size_t)(d.nx + 1) * d.ny);
     const size_t smc = sizeof(float) * ((size_t)d.nz * (d.nz + 1) + 2 * (size_t)(d.nx + 1) * d.nz);
+    // sides up to 64 need more than the default 48 KB (at most 67 KB)
+    static std::atomic<unsigned long long> attrp{0}, attrc{0};
+    ensure_smem_attr((const void*)k_hartley_planes, 200 * 1024, attrp);
+    ensure_smem_attr((const void*)k_hartley_columns, 200 * 1024, attrc);
     prof_begin(P_COARSE, s);
     k_hartley_planes<<<d.nz, 1024, smp, s>>>(b, bshift, tmp, tab, d.nx, d.ny);
     prof_end(P_COARSE, s, "hartley_planes", 8.0 * d.n());
