@@ -273,8 +273,10 @@ ibrd_status ibrd_solve_saddle_batch(int count, const ibrd_grid* grids, const dou
    (per-CTA partial sums group differently). Drops the handle's captured CUDA
    graphs. precision: IBRD_FP64 tunes the FP64 kernels, either mixed mode the
    FP32 ones, -1 both. out (may be NULL if cap = 0) receives up to cap
-   records; *n_out (may be NULL) the number of records. Allocates three
-   scratch fields of the finest grid for the duration of the call.
+   records; *n_out (may be NULL) the number of records. Allocates six
+   scratch fields of the finest grid for the duration of the call (two sets
+   of x in, x out and b that consecutive timed sweeps alternate between, so
+   that levels larger than half the L2 stream from DRAM as in a V-cycle).
    Synchronizes the stream. */
 typedef struct {
   int nx, ny, nz;    /* level grid */

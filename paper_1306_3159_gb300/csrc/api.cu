@@ -1355,15 +1355,23 @@ std::map<TuneKey, TuneResult> g_tune_cache;
 
 // Average duration (us) of `reps` back-to-back sweeps with the handle's current
 // shape for (elem, kind, d); the best of two timed runs after one warm-up.
+// Consecutive sweeps alternate between two sets of fields (x in, x out, b),
+// so that on levels larger than half the L2 each launch streams from DRAM as
+// it does inside a V-cycle, while small levels stay L2-resident as they are
+// there too.
 template <typename T>
-double time_sweep(ibrd_grid g, int kind, Dims d, Stencil st, T* x0, T* x1, T* b, cudaEvent_t e0, cudaEvent_t e1,
+double time_sweep(ibrd_grid g, int kind, Dims d, Stencil st, T* const set[2][3], cudaEvent_t e0, cudaEvent_t e1,
                   int reps) {
-  auto one = [&]() { launch_rb_sweep<T>(x0, x1, b, nullptr, d, st, kind == TUNE_ZERO, nullptr, 0, g->s); };
-  one();
+  auto one = [&](int i) {
+    T* const* f = set[i & 1];
+    launch_rb_sweep<T>(f[0], f[1], f[2], nullptr, d, st, kind == TUNE_ZERO, nullptr, 0, g->s);
+  };
+  one(0);
+  one(1);
   double best = 1e30;
   for (int r = 0; r < 2; ++r) {
     IBRD_CUDA(cudaEventRecord(e0, g->s));
-    for (int i = 0; i < reps; ++i) one();
+    for (int i = 0; i < reps; ++i) one(i);
     IBRD_CUDA(cudaEventRecord(e1, g->s));
     IBRD_CUDA(cudaEventSynchronize(e1));
     float ms = 0.f;
@@ -1382,27 +1390,24 @@ void autotune_levels(ibrd_grid g, bool retune, std::vector<ibrd_tune_entry>& rep
   end = std::min(end, (int)g->levels.size() - 1);
   if (end <= 0) return;
   const size_t n = g->d.n();
-  T* x0 = dalloc<T>(n);
-  T* x1 = dalloc<T>(n);
-  T* b = dalloc<T>(n);
+  // two sets of (x in, x out, b), each field n values (256-byte aligned)
+  const size_t ld = (n + 63) / 64 * 64;
+  T* buf = dalloc<T>(6 * ld);
+  T* const set[2][3] = {{buf, buf + ld, buf + 2 * ld}, {buf + 3 * ld, buf + 4 * ld, buf + 5 * ld}};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   auto cleanup = [&]() {
-    cudaFree(x0);
-    cudaFree(x1);
-    cudaFree(b);
+    cudaFree(buf);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
   };
   try {
     IBRD_CUDA(cudaEventCreate(&e0));
     IBRD_CUDA(cudaEventCreate(&e1));
-    IBRD_CUDA(cudaMemsetAsync(x0, 0, sizeof(T) * n, g->s));
-    IBRD_CUDA(cudaMemsetAsync(x1, 0, sizeof(T) * n, g->s));
-    IBRD_CUDA(cudaMemsetAsync(b, 0, sizeof(T) * n, g->s));
+    IBRD_CUDA(cudaMemsetAsync(buf, 0, sizeof(T) * 6 * ld, g->s));
     for (int l = 0; l < end; ++l) {
       const Dims d = g->levels[l].d;
       const Stencil st = stencil(g->levels[l].h, g->chi, g->alpha > 0.0 ? g->alpha : 1.0);
-      const int reps = (int)std::max(3.0, std::min(200.0, 2e8 / (3.0 * elem * (double)d.n())));
+      const int reps = 2 * (int)std::max(2.0, std::min(100.0, 1e8 / (3.0 * elem * (double)d.n())));
       for (int kind = TUNE_SWEEP; kind <= TUNE_ZERO; ++kind) {
         if (kind == TUNE_SWEEP && !rb_sweep_fused_ok<T>(d)) continue;
         if (kind == TUNE_ZERO && (elem != 4 || d.nx % 4 != 0)) continue;
@@ -1424,7 +1429,7 @@ void autotune_levels(ibrd_grid g, bool retune, std::vector<ibrd_tune_entry>& rep
         }
         if (!cached) {
           *slot = SweepShape{};
-          res.us_default = time_sweep<T>(g, kind, d, st, x0, x1, b, e0, e1, reps);
+          res.us_default = time_sweep<T>(g, kind, d, st, set, e0, e1, reps);
           res.us_tuned = res.us_default;
           res.s = SweepShape{};
           std::vector<int> txs = {0};
@@ -1437,7 +1442,7 @@ void autotune_levels(ibrd_grid g, bool retune, std::vector<ibrd_tune_entry>& rep
             for (int zc : zcs) {
               if (zc > d.nz || (kind == TUNE_SWEEP && zc < 2)) continue;
               *slot = SweepShape{tx, zc};
-              const double us = time_sweep<T>(g, kind, d, st, x0, x1, b, e0, e1, reps);
+              const double us = time_sweep<T>(g, kind, d, st, set, e0, e1, reps);
               // a shape replaces the built-in one only when clearly faster
               if (us < res.us_tuned && us < 0.97 * res.us_default) {
                 res.us_tuned = us;
