@@ -332,6 +332,14 @@ def run_ours(args):
     t_e2e = timed(lambda: step_e2e(chosen), max(1, args.steps // 2))
 
     dc = prof_timed["classes"].get(dom_name, dom)
+    # finest-level red-black Gauss-Seidel cell updates: per second inside the
+    # sweep kernel, and per second of the whole step (sweeps per step x cells)
+    n_cells = nx * ny * nz
+    sweeps_per_step = dc["timed"] / max(1, args.steps) if dom_name == "rbgs_f32" else 0.0
+    cell_updates = {"finest_sweep_kernel": round(n_cells / (dc["ms"] * 1e-3 / max(1, dc["timed"])), 1)
+                    if dom_name == "rbgs_f32" and dc["ms"] > 0 else None,
+                    "whole_step": round(world * sweeps_per_step * n_cells / t_step, 1),
+                    "finest_sweeps_per_step": sweeps_per_step}
     peaks = measured_peaks()
     fp32_or_bytes = dom_name.endswith("f32") or dom_name in ("dot", "axpy", "vector")
     achieved_gbs = dc["timed_bytes"] / (dc["ms"] * 1e-3) / 1e9 if dc["ms"] > 0 else 0.0
@@ -379,6 +387,7 @@ def run_ours(args):
         "gpu_launches_per_step": prof_counts["launches"] / max(1, args.steps),
         "solves": {"reaction": solve_summary(ir), "saddle": solve_summary(isd)},
         "solves_per_s_all_ranks": round(replica_throughput(t_step, world), 3),
+        "cell_updates_per_s": cell_updates,
         "plain_fp64": {"s_per_step": round(t_plain, 6), "steps": k_plain,
                        "reaction": solve_summary(ir64), "saddle": solve_summary(is64),
                        "chosen_speedup": round(t_plain / t_step, 3)},

@@ -139,6 +139,7 @@ typedef struct {
   int history_len;
   int history_cap;
   int refinements;     /* IBRD_MIXED_REFINE: refinement steps (FP32 solves) */
+  double a_L;          /* reaction radius a_L = K / (4 pi chi) (Sec. IV.A) */
 } ibrd_solve_info;
 
 /* Fill *opts with the defaults listed in ibrd_solve_opts. */

@@ -47,7 +47,7 @@ class SolveInfo(ctypes.Structure):
                 ("vcycles", ctypes.c_int), ("reorths", ctypes.c_int), ("rel_residual", ctypes.c_double), ("sum_lambda", ctypes.c_double),
                 ("cbar", ctypes.c_double), ("rate_K", ctypes.c_double), ("seconds", ctypes.c_double),
                 ("residual_history", ctypes.POINTER(ctypes.c_double)), ("history_len", ctypes.c_int),
-                ("history_cap", ctypes.c_int), ("refinements", ctypes.c_int)]
+                ("history_cap", ctypes.c_int), ("refinements", ctypes.c_int), ("a_L", ctypes.c_double)]
 
 
 class Profile(ctypes.Structure):
@@ -243,7 +243,8 @@ def _info(history_cap):
 def _info_dict(info, hist):
     return {"status": info.status, "outer_iters": info.outer_iters, "inner_iters": info.inner_iters,
             "vcycles": info.vcycles, "reorths": info.reorths, "rel_residual": info.rel_residual, "sum_lambda": info.sum_lambda,
-            "cbar": info.cbar, "rate_K": info.rate_K, "seconds": info.seconds, "refinements": info.refinements,
+            "cbar": info.cbar, "rate_K": info.rate_K, "a_L": info.a_L, "seconds": info.seconds,
+            "refinements": info.refinements,
             "history": hist[:info.history_len].copy()}
 
 

@@ -1494,6 +1494,7 @@ void report(ibrd_grid g, const double* c, const double* lam_or_null, const doubl
   info->cbar = g->host[0];
   info->sum_lambda = N > 0 ? g->host[1] : 0.0;
   info->rate_K = (N > 0 && info->cbar != 0.0) ? info->sum_lambda / (N * info->cbar) : 0.0;
+  info->a_L = info->rate_K / (4.0 * 3.14159265358979323846 * g->chi);
 }
 
 }  // namespace

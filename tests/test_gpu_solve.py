@@ -78,6 +78,8 @@ def test_saddle_small(ibrd, small, precision, tol, err):
     assert abs(info["sum_lambda"] - w.g.sum()) < 1e-9 * w.g.sum()
     K_ref = outputs.overall_rate(lam_ref, c_ref)
     assert abs(info["rate_K"] - K_ref) < err * abs(K_ref)
+    a_ref = outputs.reaction_radius(lam_ref, c_ref, w.chi)
+    assert abs(info["a_L"] - a_ref) < err * abs(a_ref)
 
 
 @pytest.mark.parametrize("precision,tol,err", SOLVE_CASES)
