@@ -339,7 +339,7 @@ def run_ours(args):
     cell_updates = {"finest_sweep_kernel": round(n_cells / (dc["ms"] * 1e-3 / max(1, dc["timed"])), 1)
                     if dom_name == "rbgs_f32" and dc["ms"] > 0 else None,
                     "whole_step": round(world * sweeps_per_step * n_cells / t_step, 1),
-                    "finest_sweeps_per_step": sweeps_per_step}
+                    "finest_fused_sweeps_per_step": sweeps_per_step}
     peaks = measured_peaks()
     fp32_or_bytes = dom_name.endswith("f32") or dom_name in ("dot", "axpy", "vector")
     achieved_gbs = dc["timed_bytes"] / (dc["ms"] * 1e-3) / 1e9 if dc["ms"] > 0 else 0.0
