@@ -581,6 +581,18 @@ def run_learned(p, torch, world, args):
                 ts.append(time.perf_counter() - t0)
             row[label] = {"ms": round(1e3 * min(ts[1:]), 3), "outer_iters": info["outer_iters"],
                           "vcycles": info["vcycles"], "rel_residual": info["rel_residual"]}
+        # the plain method for reference: FP64 from zero with the library defaults
+        ts = []
+        for rep in range(2):
+            c = torch.zeros_like(gd)
+            lam = torch.zeros(N, dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, _, info = G.solve_saddle(gd, c=c, lam=lam, tol=1e-8, max_iter=3000, precision=p.IBRD_FP64)
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        row["plain_fp64_zero"] = {"ms": round(1e3 * ts[-1], 3), "outer_iters": info["outer_iters"],
+                                  "vcycles": info["vcycles"], "rel_residual": info["rel_residual"]}
         t0 = time.perf_counter()
         for _ in range(5):
             m.predict(qd, wbox, total, out=lam0)
