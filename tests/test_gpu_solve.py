@@ -320,3 +320,50 @@ def test_batch_reports_each_problem(ibrd):
                                        raise_on_error=False)
     assert [o["status"] for o in out] == [0, 0, 8]
     torch.cuda.synchronize()
+
+
+def test_degenerate_inputs(ibrd):
+    """No blobs: the reaction-limited solve with alpha > 0 is the Helmholtz
+    solve (the oracle's FFT Green's function), with alpha = 0 it has no
+    solution and is refused (IBRD_ERR_ARG), and a saddle solve needs blobs
+    (IBRD_ERR_STATE). Two coincident blobs make J rank-deficient: the field
+    c is still unique and matches the oracle's solution for the merged blob,
+    and the two multipliers share the merged one's."""
+    import torch
+    dims = (24, 16, 20)
+    rng = np.random.default_rng(31)
+    gsrc = 1.0 + 0.3 * rng.standard_normal((20, 16, 24))
+    g = ibrd.Grid(*dims, alpha=0.5)
+    kappa = torch.zeros(0, dtype=torch.float64, device="cuda")
+    c, info = g.solve_reaction(kappa, dev(gsrc), tol=1e-13, max_iter=200)
+    assert rel_l2(host(c), op.green_apply(gsrc, 1.0, 1.0, 0.5)) < 1e-11
+    g0 = ibrd.Grid(*dims)
+    with pytest.raises(ibrd.IbrdError) as e:
+        g0.solve_reaction(kappa, dev(gsrc), tol=1e-10)
+    assert e.value.status == 1
+    with pytest.raises(ibrd.IbrdError) as e:
+        g0.solve_saddle(dev(gsrc), tol=1e-10)
+    assert e.value.status == 8
+    # coincident blobs
+    w = workload("small")
+    q3 = w.q[:3]
+    q4 = np.vstack([q3, q3[:1]])
+    c_ref, lam_ref, _ = direct.solve_saddle(q3, w.g, w.h, w.chi, 0.0)
+    gc = ibrd.Grid(*w.dims)
+    gc.set_blobs(dev(q4))
+    c, lam, info = _saddle_status(ibrd, gc, w.g, 1e-11)
+    assert info["status"] == 0, info["status"]
+    lam = host(lam)
+    assert rel_l2(host(c), c_ref) < 1e-9
+    assert abs(lam[0] + lam[3] - lam_ref[0]) < 1e-9 * abs(lam_ref).max()
+    assert np.abs(lam[1:3] - lam_ref[1:3]).max() < 1e-9 * abs(lam_ref).max()
+    torch.cuda.synchronize()
+
+
+def _saddle_status(ibrd, grid, gsrc, tol):
+    import torch
+    c = grid.field()
+    lam = torch.zeros(grid.n_blobs, dtype=torch.float64, device="cuda")
+    info = ibrd.ibrd_solve_saddle(grid.handle, dev(gsrc), None, c, lam, ibrd.ibrd_default_opts(tol=tol, max_iter=400),
+                                  raise_on_error=False)
+    return c, lam, info
