@@ -261,6 +261,30 @@ ibrd_status ibrd_solve_saddle_batch(int count, const ibrd_grid* grids, const dou
                                     const double* const* f, double* const* c, double* const* lambda,
                                     const ibrd_solve_opts* opts, ibrd_solve_info* infos, int threads);
 
+/* Independent solves of either kind at once: item i is a reaction-limited
+   (kind IBRD_SOLVE_REACTION: kappa, rhs, c) or saddle-point (kind
+   IBRD_SOLVE_SADDLE: rhs, f (may be NULL), c, lambda) solve on its own handle
+   with its own options (opts may be NULL) and report (info may be NULL; its
+   status is set for every item). The pointers mean what they mean in
+   ibrd_solve_reaction / ibrd_solve_saddle. Scheduling, handle rules and the
+   return value are those of the batched calls above; e.g. the two solves of
+   one configuration (Sec. III.C and III.D) on two handles with their own
+   streams overlap on the GPU. items is a HOST array. */
+enum { IBRD_SOLVE_REACTION = 0, IBRD_SOLVE_SADDLE = 1 };
+typedef struct {
+  int kind;
+  ibrd_grid grid;
+  const double* kappa;
+  const double* rhs;
+  const double* f;
+  double* c;
+  double* lambda;
+  const ibrd_solve_opts* opts;
+  ibrd_solve_info* info;
+} ibrd_solve_item;
+
+ibrd_status ibrd_solve_many(int count, const ibrd_solve_item* items, int threads);
+
 /* Autotuner (not in the paper: launch-shape selection for this library's
    kernels). For every multigrid level whose red-black sweeps (Sec. III.E) run
    as the fused sweep kernel, times candidate launch shapes of that kernel --

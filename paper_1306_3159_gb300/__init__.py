@@ -12,6 +12,7 @@ from ._abi import (IBRD_GUESS_NONE, IBRD_GUESS_UNIFORM, IBRD_GUESS_GIVEN, IBRD_G
                    IBRD_PRECOND_SCHUR, IbrdError, Grid, SolveOpts, load_library, EXPORTED,
                    ibrd_apply_L, ibrd_grid_create, ibrd_grid_destroy, ibrd_interp, ibrd_set_blobs,
                    ibrd_solve_reaction, ibrd_solve_saddle, ibrd_solve_reaction_batch, ibrd_solve_saddle_batch,
+                   ibrd_solve_many,
                    ibrd_autotune, ibrd_tune_set, ibrd_tune_clear, GNN, ibrd_gnn_num_params, ibrd_spread, ibrd_vcycle, ibrd_vcycle_f32, ibrd_last_error,
                    ibrd_default_opts, ibrd_profile_enable, ibrd_profile_read)
 
@@ -19,6 +20,7 @@ __all__ = ["IBRD_GUESS_NONE", "IBRD_GUESS_UNIFORM", "IBRD_GUESS_GIVEN", "IBRD_GU
            "IBRD_PRECOND_SCHUR", "IbrdError", "Grid", "SolveOpts", "load_library", "EXPORTED",
            "ibrd_apply_L", "ibrd_grid_create", "ibrd_grid_destroy", "ibrd_interp", "ibrd_set_blobs",
            "ibrd_solve_reaction", "ibrd_solve_saddle", "ibrd_solve_reaction_batch", "ibrd_solve_saddle_batch",
+           "ibrd_solve_many",
            "ibrd_autotune", "ibrd_tune_set", "ibrd_tune_clear", "GNN", "ibrd_gnn_num_params", "ibrd_spread", "ibrd_vcycle", "ibrd_vcycle_f32",
            "ibrd_last_error",
            "ibrd_default_opts", "ibrd_profile_enable", "ibrd_profile_read"]

@@ -22,7 +22,7 @@ STATUS = {0: "IBRD_OK", 1: "IBRD_ERR_ARG", 2: "IBRD_ERR_CUDA", 3: "IBRD_ERR_OOM"
 # Every entry point declared in include/ibrd.h.
 EXPORTED = ["ibrd_default_opts", "ibrd_grid_create", "ibrd_grid_destroy", "ibrd_set_blobs", "ibrd_apply_L",
             "ibrd_vcycle", "ibrd_vcycle_f32", "ibrd_vcycle_noalloc", "ibrd_spread", "ibrd_interp", "ibrd_solve_reaction", "ibrd_solve_saddle",
-            "ibrd_solve_reaction_batch", "ibrd_solve_saddle_batch", "ibrd_autotune", "ibrd_tune_set",
+            "ibrd_solve_reaction_batch", "ibrd_solve_saddle_batch", "ibrd_solve_many", "ibrd_autotune", "ibrd_tune_set",
             "ibrd_tune_clear", "ibrd_gnn_num_params", "ibrd_gnn_create", "ibrd_gnn_destroy", "ibrd_gnn_last_error",
             "ibrd_gnn_set_params", "ibrd_gnn_get_params", "ibrd_gnn_init_params", "ibrd_gnn_neighbours", "ibrd_gnn_forward",
             "ibrd_gnn_predict", "ibrd_gnn_loss_grad", "ibrd_gnn_adam_step", "ibrd_gnn_train",
@@ -55,6 +55,15 @@ class Profile(ctypes.Structure):
                 ("count", ctypes.c_longlong * PROF_NCLASS), ("timed", ctypes.c_longlong * PROF_NCLASS),
                 ("ms", ctypes.c_double * PROF_NCLASS), ("bytes", ctypes.c_double * PROF_NCLASS),
                 ("max_launch_bytes", ctypes.c_double * PROF_NCLASS), ("timed_bytes", ctypes.c_double * PROF_NCLASS)]
+
+
+class SolveItem(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("grid", ctypes.c_void_p), ("kappa", ctypes.c_void_p),
+                ("rhs", ctypes.c_void_p), ("f", ctypes.c_void_p), ("c", ctypes.c_void_p),
+                ("lam", ctypes.c_void_p), ("opts", ctypes.POINTER(SolveOpts)), ("info", ctypes.POINTER(SolveInfo))]
+
+
+IBRD_SOLVE_REACTION, IBRD_SOLVE_SADDLE = 0, 1
 
 
 class TuneEntry(ctypes.Structure):
@@ -107,6 +116,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ibrd_solve_reaction_batch.restype = i
     lib.ibrd_solve_saddle_batch.argtypes = [i, P(vp), P(vp), P(vp), P(vp), P(vp), P(SolveOpts), P(SolveInfo), i]
     lib.ibrd_solve_saddle_batch.restype = i
+    lib.ibrd_solve_many.argtypes = [i, P(SolveItem), i]
+    lib.ibrd_solve_many.restype = i
     lib.ibrd_autotune.argtypes = [vp, i, i, P(TuneEntry), i, P(i)]
     lib.ibrd_autotune.restype = i
     lib.ibrd_tune_set.argtypes = [vp, i, i, i, i, i, i, i]
@@ -330,6 +341,31 @@ def ibrd_solve_saddle_batch(grids, rhs, f, c, lam, opts: SolveOpts | None = None
                                                 ctypes.byref(opts) if opts is not None else None, infos,
                                                 int(threads))
     return _batch_result(grids, st, infos, hists, raise_on_error)
+
+
+def ibrd_solve_many(items, threads=0, history_cap=0, raise_on_error=True) -> list:
+    """Independent solves of either kind at once. items: dicts with "kind"
+    ("reaction" or "saddle"), "grid" (handle), "rhs", "c", and "kappa"
+    (reaction) or "lam" and optionally "f" (saddle), optionally "opts"."""
+    n = len(items)
+    arr = (SolveItem * max(1, n))()
+    infos, hists = _batch_infos(n, history_cap)
+    keep = []
+    for k, it in enumerate(items):
+        kind = {"reaction": IBRD_SOLVE_REACTION, "saddle": IBRD_SOLVE_SADDLE}[it["kind"]]
+        g = it["grid"]
+        arr[k].kind = kind
+        arr[k].grid = g.value if isinstance(g, ctypes.c_void_p) else g
+        for name, key in (("kappa", "kappa"), ("rhs", "rhs"), ("f", "f"), ("c", "c"), ("lam", "lam")):
+            ptr = _ptr(it.get(key))
+            setattr(arr[k], name, ptr.value if ptr is not None else None)
+        o = it.get("opts")
+        if o is not None:
+            keep.append(o)
+            arr[k].opts = ctypes.pointer(o)
+        arr[k].info = ctypes.pointer(infos[k])
+    st = load_library().ibrd_solve_many(n, arr, int(threads))
+    return _batch_result([it["grid"] for it in items], st, infos, hists, raise_on_error)
 
 
 def ibrd_autotune(g, precision=-1, retune=False, cap=64) -> list:

@@ -1851,6 +1851,24 @@ ibrd_status ibrd_solve_saddle_batch(int count, const ibrd_grid* grids, const dou
   });
 }
 
+ibrd_status ibrd_solve_many(int count, const ibrd_solve_item* items, int threads) {
+  if (count < 0 || (count > 0 && !items)) return IBRD_ERR_ARG;
+  std::vector<ibrd_grid> grids((size_t)count);
+  for (int i = 0; i < count; ++i) {
+    if (items[i].kind != IBRD_SOLVE_REACTION && items[i].kind != IBRD_SOLVE_SADDLE) return IBRD_ERR_ARG;
+    grids[i] = items[i].grid;
+  }
+  return run_batch(count, grids.data(), threads, [&](int i) {
+    const ibrd_solve_item& it = items[i];
+    const ibrd_status st =
+        it.kind == IBRD_SOLVE_REACTION
+            ? ibrd_solve_reaction(it.grid, it.kappa, it.rhs, it.c, it.opts, it.info)
+            : ibrd_solve_saddle(it.grid, it.rhs, it.f, it.c, it.lambda, it.opts, it.info);
+    if (it.info) it.info->status = st;
+    return st;
+  });
+}
+
 ibrd_status ibrd_autotune(ibrd_grid g, int precision, int retune, ibrd_tune_entry* out, int cap, int* n_out) {
   return guarded(g, "ibrd_autotune", [&]() {
     if (precision != -1 && precision != IBRD_FP64 && precision != IBRD_MIXED_FP32 &&

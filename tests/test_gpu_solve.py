@@ -367,3 +367,34 @@ def _saddle_status(ibrd, grid, gsrc, tol):
     info = ibrd.ibrd_solve_saddle(grid.handle, dev(gsrc), None, c, lam, ibrd.ibrd_default_opts(tol=tol, max_iter=400),
                                   raise_on_error=False)
     return c, lam, info
+
+
+def test_solve_many_mixed_kinds(ibrd, small):
+    """The two solves of one configuration (reaction-limited and saddle point),
+    each on its own handle and stream with its own options, run together by
+    ibrd_solve_many: bit for bit the results of the separate calls, and the
+    oracle's solutions."""
+    import torch
+    w, M = small
+    sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
+    ga = ibrd.Grid(*w.dims, stream=sa.cuda_stream)
+    gb = ibrd.Grid(*w.dims, stream=sb.cuda_stream)
+    q, k, src = dev(w.q), dev(w.kappa), dev(w.g)
+    c1, c2, c3, c4 = (torch.zeros_like(src) for _ in range(4))
+    l2, l4 = torch.zeros(len(w.q), dtype=torch.float64, device="cuda"), \
+        torch.zeros(len(w.q), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    ga.set_blobs(q)
+    gb.set_blobs(q)
+    ro = ibrd.ibrd_default_opts(tol=1e-10, precision=2, max_iter=400, mg_cycles=1, nu1=1, nu2=1)
+    so = ibrd.ibrd_default_opts(tol=1e-10, precision=2, max_iter=400, schur_inner=3, lambda_guess=1)
+    out = ibrd.ibrd_solve_many([dict(kind="reaction", grid=ga.handle, kappa=k, rhs=src, c=c1, opts=ro),
+                                dict(kind="saddle", grid=gb.handle, rhs=src, c=c2, lam=l2, opts=so)], threads=2)
+    r = ibrd.ibrd_solve_reaction(ga.handle, k, src, c3, ro)
+    s_ = ibrd.ibrd_solve_saddle(gb.handle, src, None, c4, l4, so)
+    assert torch.equal(c1, c3) and torch.equal(c2, c4) and torch.equal(l2, l4)
+    assert out[0]["outer_iters"] == r["outer_iters"] and out[1]["outer_iters"] == s_["outer_iters"]
+    c_ref, u_ref, _ = direct.solve_reaction(w.q, w.kappa, w.g, w.h, w.chi, 0.0, M=M)
+    cs_ref, lam_ref, _ = direct.solve_saddle(w.q, w.g, w.h, w.chi, 0.0, M=M)
+    assert rel_l2(host(c1), c_ref) < 1e-8 and rel_l2(host(c2), cs_ref) < 1e-8 and rel_l2(host(l2), lam_ref) < 1e-8
+    torch.cuda.synchronize()
