@@ -81,3 +81,18 @@ def test_batch_rejects_bad_handles_without_touching_gpu(lib):
         assert lib.ibrd_solve_reaction_batch(2, grids, ptrs, ptrs, ptrs, None, None, 4) == 1
         assert lib.ibrd_solve_saddle_batch(2, grids, ptrs, None, ptrs, ptrs, None, None, 4) == 1
     assert lib.ibrd_solve_reaction_batch(2, ptrs, None, ptrs, ptrs, None, None, 0) == 1
+
+
+def test_solve_many_rejects_bad_items_without_touching_gpu(lib):
+    # an unknown kind, a null handle or a shared handle is refused before any
+    # handle is dereferenced (the fake addresses are never followed)
+    import paper_1306_3159_gb300 as p
+    from paper_1306_3159_gb300._abi import SolveItem
+    fn = p.load_library().ibrd_solve_many
+    assert fn(0, None, 0) == 0 and fn(-1, None, 0) == 1
+    for kinds, grids in [((0, 7), (0x1000, 0x2000)), ((0, 1), (0x1000, 0)), ((0, 1), (0x1000, 0x1000))]:
+        items = (SolveItem * 2)()
+        for k in range(2):
+            items[k].kind = kinds[k]
+            items[k].grid = grids[k] or None
+        assert fn(2, items, 2) == 1
