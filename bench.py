@@ -297,12 +297,14 @@ def run_ours(args):
     if not args.no_autotune:
         p.ibrd_autotune(grid_s.handle, p.IBRD_MIXED_REFINE)  # same shapes, from the process cache
     if args.ncu_step:
-        # profiler range around one chosen step (ncu --profile-from-start off)
+        # profiler range around one chosen step (ncu --profile-from-start off);
+        # the profiler serialises kernels anyway, so the two solves run one
+        # after the other from this thread
         for _ in range(args.warmup):
-            step(chosen)
+            step(chosen, concurrent=False)
         torch.cuda.synchronize()
         torch.cuda.profiler.start()
-        step(chosen)
+        step(chosen, concurrent=False)
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
         log("[bench] ncu step done")
