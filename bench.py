@@ -238,26 +238,26 @@ def run_ours(args):
                  p.ibrd_default_opts(tol=tol, precision=pr, max_iter=3000, **ks))
             for pr, (kr, ks) in settings.items()}
 
-    def solve_both(precision, concurrent=True):
+    def step(precision, concurrent=True, download=False):
+        # each item sets its handle's blobs, solves and (end to end) downloads
+        # its solution, so that one solve's download overlaps the other solve
         o_r, o_s = opts[precision]
-        items = [dict(kind="reaction", grid=grid_r.handle, kappa=k_d, rhs=g_d, c=c_r, opts=o_r),
-                 dict(kind="saddle", grid=grid_s.handle, rhs=g_d, c=c_s, lam=lam, opts=o_s)]
+        items = [dict(kind="reaction", grid=grid_r.handle, kappa=k_d, rhs=g_d, c=c_r, opts=o_r, q=q_d),
+                 dict(kind="saddle", grid=grid_s.handle, rhs=g_d, c=c_s, lam=lam, opts=o_s, q=q_d)]
+        if download:
+            items[0]["c_host"] = out_cr
+            items[1]["c_host"], items[1]["lam_host"] = out_cs, out_l
         if concurrent:
             out = p.ibrd_solve_many(items, threads=2)
         else:
             out = [p.ibrd_solve_many([it], threads=1)[0] for it in items]
         infos[precision] = (out[0], out[1])
 
-    def step(precision, concurrent=True):
-        grid_r.set_blobs(q_d)
-        grid_s.set_blobs(q_d)
-        solve_both(precision, concurrent)
-
     copy_stream = torch.cuda.Stream()
 
     def step_e2e(precision):
-        # host -> device on a copy stream; both solver streams wait for it;
-        # device -> host of each solution on its own solver stream
+        # host -> device on a copy stream that both solver streams wait for;
+        # each solution comes down on its solver stream inside its item
         with torch.cuda.stream(copy_stream):
             q_d.copy_(q_h, non_blocking=True)
             k_d.copy_(k_h, non_blocking=True)
@@ -266,14 +266,7 @@ def run_ours(args):
         ev_in.record(copy_stream)
         stream_r.wait_event(ev_in)
         stream_s.wait_event(ev_in)
-        step(precision)
-        with torch.cuda.stream(stream_r):
-            out_cr.copy_(c_r, non_blocking=True)
-        with torch.cuda.stream(stream_s):
-            out_cs.copy_(c_s, non_blocking=True)
-            out_l.copy_(lam, non_blocking=True)
-        stream_r.synchronize()
-        stream_s.synchronize()
+        step(precision, download=True)
 
     def barrier():
         rank_barrier(world)

@@ -266,10 +266,15 @@ ibrd_status ibrd_solve_saddle_batch(int count, const ibrd_grid* grids, const dou
    IBRD_SOLVE_SADDLE: rhs, f (may be NULL), c, lambda) solve on its own handle
    with its own options (opts may be NULL) and report (info may be NULL; its
    status is set for every item). The pointers mean what they mean in
-   ibrd_solve_reaction / ibrd_solve_saddle. Scheduling, handle rules and the
-   return value are those of the batched calls above; e.g. the two solves of
-   one configuration (Sec. III.C and III.D) on two handles with their own
-   streams overlap on the GPU. items is a HOST array. */
+   ibrd_solve_reaction / ibrd_solve_saddle. If q is non-NULL the item first
+   sets the handle's blobs (ibrd_set_blobs(grid, q, n_blobs)). If c_host
+   (lambda_host) is non-NULL, a HOST buffer of N_c (N) doubles (pinned for an
+   asynchronous copy), the solution is copied there on the handle's stream
+   after the solve, before the item ends, so that one item's download
+   overlaps the others' solves. Scheduling, handle rules and the return value
+   are those of the batched calls above; e.g. the two solves of one
+   configuration (Sec. III.C and III.D) on two handles with their own streams
+   overlap on the GPU. items is a HOST array. */
 enum { IBRD_SOLVE_REACTION = 0, IBRD_SOLVE_SADDLE = 1 };
 typedef struct {
   int kind;
@@ -281,6 +286,10 @@ typedef struct {
   double* lambda;
   const ibrd_solve_opts* opts;
   ibrd_solve_info* info;
+  const double* q;     /* blob positions to set first (device, n_blobs x 3), or NULL */
+  int n_blobs;
+  double* c_host;      /* host destination of c after the solve, or NULL */
+  double* lambda_host; /* host destination of lambda (saddle), or NULL */
 } ibrd_solve_item;
 
 ibrd_status ibrd_solve_many(int count, const ibrd_solve_item* items, int threads);

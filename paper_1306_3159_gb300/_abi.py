@@ -60,7 +60,9 @@ class Profile(ctypes.Structure):
 class SolveItem(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("grid", ctypes.c_void_p), ("kappa", ctypes.c_void_p),
                 ("rhs", ctypes.c_void_p), ("f", ctypes.c_void_p), ("c", ctypes.c_void_p),
-                ("lam", ctypes.c_void_p), ("opts", ctypes.POINTER(SolveOpts)), ("info", ctypes.POINTER(SolveInfo))]
+                ("lam", ctypes.c_void_p), ("opts", ctypes.POINTER(SolveOpts)), ("info", ctypes.POINTER(SolveInfo)),
+                ("q", ctypes.c_void_p), ("n_blobs", ctypes.c_int), ("c_host", ctypes.c_void_p),
+                ("lambda_host", ctypes.c_void_p)]
 
 
 IBRD_SOLVE_REACTION, IBRD_SOLVE_SADDLE = 0, 1
@@ -346,7 +348,9 @@ def ibrd_solve_saddle_batch(grids, rhs, f, c, lam, opts: SolveOpts | None = None
 def ibrd_solve_many(items, threads=0, history_cap=0, raise_on_error=True) -> list:
     """Independent solves of either kind at once. items: dicts with "kind"
     ("reaction" or "saddle"), "grid" (handle), "rhs", "c", and "kappa"
-    (reaction) or "lam" and optionally "f" (saddle), optionally "opts"."""
+    (reaction) or "lam" and optionally "f" (saddle); optionally "opts", "q"
+    (blob positions to set first) and "c_host" / "lam_host" (CPU float64
+    tensors, pinned, that receive the solution after the solve)."""
     n = len(items)
     arr = (SolveItem * max(1, n))()
     infos, hists = _batch_infos(n, history_cap)
@@ -359,6 +363,15 @@ def ibrd_solve_many(items, threads=0, history_cap=0, raise_on_error=True) -> lis
         for name, key in (("kappa", "kappa"), ("rhs", "rhs"), ("f", "f"), ("c", "c"), ("lam", "lam")):
             ptr = _ptr(it.get(key))
             setattr(arr[k], name, ptr.value if ptr is not None else None)
+        if it.get("q") is not None:
+            arr[k].q = _ptr(it["q"]).value
+            arr[k].n_blobs = int(it["q"].shape[0])
+        for name, key in (("c_host", "c_host"), ("lambda_host", "lam_host")):
+            t = it.get(key)
+            if t is not None:
+                if t.is_cuda or not t.is_contiguous() or str(t.dtype) != "torch.float64":
+                    raise ValueError("host outputs are contiguous CPU float64 tensors (pinned for overlap)")
+                setattr(arr[k], name, t.data_ptr())
         o = it.get("opts")
         if o is not None:
             keep.append(o)

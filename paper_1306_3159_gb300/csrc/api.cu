@@ -1860,10 +1860,23 @@ ibrd_status ibrd_solve_many(int count, const ibrd_solve_item* items, int threads
   }
   return run_batch(count, grids.data(), threads, [&](int i) {
     const ibrd_solve_item& it = items[i];
-    const ibrd_status st =
-        it.kind == IBRD_SOLVE_REACTION
-            ? ibrd_solve_reaction(it.grid, it.kappa, it.rhs, it.c, it.opts, it.info)
-            : ibrd_solve_saddle(it.grid, it.rhs, it.f, it.c, it.lambda, it.opts, it.info);
+    ibrd_status st = it.q ? ibrd_set_blobs(it.grid, it.q, it.n_blobs) : IBRD_OK;
+    if (st == IBRD_OK)
+      st = it.kind == IBRD_SOLVE_REACTION
+               ? ibrd_solve_reaction(it.grid, it.kappa, it.rhs, it.c, it.opts, it.info)
+               : ibrd_solve_saddle(it.grid, it.rhs, it.f, it.c, it.lambda, it.opts, it.info);
+    if (st == IBRD_OK && (it.c_host || it.lambda_host)) {
+      st = guarded(it.grid, "ibrd_solve_many", [&]() {
+        ibrd_grid g = it.grid;
+        if (it.c_host)
+          IBRD_CUDA(cudaMemcpyAsync(it.c_host, it.c, sizeof(double) * g->d.n(), cudaMemcpyDeviceToHost, g->s));
+        if (it.lambda_host && it.kind == IBRD_SOLVE_SADDLE && g->blobs.n > 0)
+          IBRD_CUDA(cudaMemcpyAsync(it.lambda_host, it.lambda, sizeof(double) * g->blobs.n,
+                                    cudaMemcpyDeviceToHost, g->s));
+        IBRD_CUDA(cudaStreamSynchronize(g->s));
+        return IBRD_OK;
+      });
+    }
     if (it.info) it.info->status = st;
     return st;
   });

@@ -372,8 +372,9 @@ def _saddle_status(ibrd, grid, gsrc, tol):
 def test_solve_many_mixed_kinds(ibrd, small):
     """The two solves of one configuration (reaction-limited and saddle point),
     each on its own handle and stream with its own options, run together by
-    ibrd_solve_many: bit for bit the results of the separate calls, and the
-    oracle's solutions."""
+    ibrd_solve_many (each item setting its blobs and downloading its solution
+    to pinned host memory): bit for bit the results of the separate calls, and
+    the oracle's solutions."""
     import torch
     w, M = small
     sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
@@ -383,13 +384,19 @@ def test_solve_many_mixed_kinds(ibrd, small):
     c1, c2, c3, c4 = (torch.zeros_like(src) for _ in range(4))
     l2, l4 = torch.zeros(len(w.q), dtype=torch.float64, device="cuda"), \
         torch.zeros(len(w.q), dtype=torch.float64, device="cuda")
+    h1 = torch.zeros(src.shape, dtype=torch.float64).pin_memory()
+    h2 = torch.zeros(src.shape, dtype=torch.float64).pin_memory()
+    hl = torch.zeros(len(w.q), dtype=torch.float64).pin_memory()
     torch.cuda.synchronize()
-    ga.set_blobs(q)
-    gb.set_blobs(q)
     ro = ibrd.ibrd_default_opts(tol=1e-10, precision=2, max_iter=400, mg_cycles=1, nu1=1, nu2=1)
     so = ibrd.ibrd_default_opts(tol=1e-10, precision=2, max_iter=400, schur_inner=3, lambda_guess=1)
-    out = ibrd.ibrd_solve_many([dict(kind="reaction", grid=ga.handle, kappa=k, rhs=src, c=c1, opts=ro),
-                                dict(kind="saddle", grid=gb.handle, rhs=src, c=c2, lam=l2, opts=so)], threads=2)
+    # the items set the blobs themselves and download their solutions
+    out = ibrd.ibrd_solve_many([dict(kind="reaction", grid=ga.handle, kappa=k, rhs=src, c=c1, opts=ro, q=q,
+                                     c_host=h1),
+                                dict(kind="saddle", grid=gb.handle, rhs=src, c=c2, lam=l2, opts=so, q=q,
+                                     c_host=h2, lam_host=hl)], threads=2)
+    gb.n_blobs = ga.n_blobs = len(w.q)
+    assert torch.equal(h1, c1.cpu()) and torch.equal(h2, c2.cpu()) and torch.equal(hl, l2.cpu())
     r = ibrd.ibrd_solve_reaction(ga.handle, k, src, c3, ro)
     s_ = ibrd.ibrd_solve_saddle(gb.handle, src, None, c4, l4, so)
     assert torch.equal(c1, c3) and torch.equal(c2, c4) and torch.equal(l2, l4)
