@@ -405,3 +405,38 @@ def test_solve_many_mixed_kinds(ibrd, small):
     cs_ref, lam_ref, _ = direct.solve_saddle(w.q, w.g, w.h, w.chi, 0.0, M=M)
     assert rel_l2(host(c1), c_ref) < 1e-8 and rel_l2(host(c2), cs_ref) < 1e-8 and rel_l2(host(l2), lam_ref) < 1e-8
     torch.cuda.synchronize()
+
+
+RANDOM_SHAPES = [(16, 24, 32), (40, 24, 16), (48, 48, 16), (32, 64, 16), (24, 24, 24), (20, 40, 12)]
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_configurations(ibrd, seed):
+    """Seeded random configurations: grid shape, blob count (RSA, spacing 3h),
+    kernel width, shift alpha and precision mode drawn per case; both solves
+    against the oracle's exact solutions."""
+    import torch
+    rng = np.random.default_rng(1000 + seed)
+    dims = RANDOM_SHAPES[seed]
+    n = int(rng.integers(1, 40))
+    w_k = int(rng.choice([3, 4]))
+    alpha = float(rng.choice([0.0, 0.3]))
+    precision = int(rng.integers(0, 3))
+    q = rsa_positions(n, dims, 1.0, 3.0, 2000 + seed)
+    n = len(q)
+    kappa = loguniform_rates(n, 0.1, 10.0, 3000 + seed)
+    nx, ny, nz = dims
+    gsrc = 1.0 + 0.5 * rng.random((nz, ny, nx))
+    g = ibrd.Grid(*dims, alpha=alpha, kernel=w_k)
+    g.set_blobs(dev(q))
+    c_ref, lam_ref, _ = direct.solve_saddle(q, gsrc, 1.0, 1.0, alpha, w=w_k)
+    tol = max(1e-12, floor_tol(c_ref, gsrc, 1.0, 1.0, alpha))
+    c, lam, info = g.solve_saddle(dev(gsrc), tol=tol, precision=precision, max_iter=600)
+    assert info["rel_residual"] <= tol
+    assert rel_l2(host(c), c_ref) < 1e-10 and rel_l2(host(lam), lam_ref) < 1e-10, (dims, n, w_k, alpha, precision)
+    cr_ref, u_ref, _ = direct.solve_reaction(q, kappa, gsrc, 1.0, 1.0, alpha, w=w_k)
+    tol = max(1e-12, floor_tol(cr_ref, gsrc, 1.0, 1.0, alpha))
+    cr, info = g.solve_reaction(dev(kappa), dev(gsrc), tol=tol, precision=precision, max_iter=600)
+    assert info["rel_residual"] <= tol
+    assert rel_l2(host(cr), cr_ref) < 1e-10, (dims, n, w_k, alpha, precision)
+    torch.cuda.synchronize()
