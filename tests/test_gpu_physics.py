@@ -80,3 +80,20 @@ def test_cubic_lattice_rate_L64(ibrd):
     # every blob of the lattice sees the same environment: equal rates
     lh = host(lam)
     assert np.abs(lh - lh.mean()).max() < 1e-6 * abs(lh.mean())
+
+
+def test_reaction_radius_sweep_over_box_size(ibrd):
+    """Sec. IV.A: a single blob at a node in periodic boxes of side L = 16,
+    32, 64, 128. The measured a_L falls with L toward the isolated blob's
+    radius (Eq. a_phi: a_L = a (1 + x + x^2 + ...), x = 2.84 a / L), and the
+    series removes the box-size dependence: the corrected radii agree within
+    1 % of each other and lie in 1.24h-1.30h."""
+    rows = []
+    for L in (16, 32, 64, 128):
+        aL, a = _radius(ibrd, L, [[L / 2, L / 2, L / 2]])
+        rows.append((L, aL, a))
+    aLs = [r[1] for r in rows]
+    corr = np.array([r[2] for r in rows])
+    assert all(x > y for x, y in zip(aLs, aLs[1:])) and all(r[1] > r[2] for r in rows), rows
+    assert np.all((corr > 1.24) & (corr < 1.30)), rows
+    assert (corr.max() - corr.min()) / corr.mean() < 0.01, rows
