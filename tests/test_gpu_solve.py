@@ -440,3 +440,24 @@ def test_random_configurations(ibrd, seed):
     assert info["rel_residual"] <= tol
     assert rel_l2(host(cr), cr_ref) < 1e-10, (dims, n, w_k, alpha, precision)
     torch.cuda.synchronize()
+
+
+def test_backward_euler_steps(ibrd, small):
+    """Eq. unsteady_system as time stepping: three backward-Euler steps
+    (alpha = 1/dt, right-hand side c^n / dt + s) of the reaction-limited
+    system from c = 0, each against the oracle's exact step."""
+    import torch
+    w, _ = small
+    dt = 2.0
+    alpha = 1.0 / dt
+    g = _grid(ibrd, w, alpha)
+    c_ref = np.zeros_like(w.g)
+    c = torch.zeros_like(dev(w.g))
+    for _ in range(3):
+        rhs_ref = c_ref / dt + w.g
+        c_ref, _, _ = direct.solve_reaction(w.q, w.kappa, rhs_ref, w.h, w.chi, alpha)
+        rhs = c / dt + dev(w.g)
+        c, info = g.solve_reaction(dev(w.kappa), rhs, tol=max(1e-12, floor_tol(c_ref, rhs_ref, w.h, w.chi, alpha)),
+                                   max_iter=400)
+        assert rel_l2(host(c), c_ref) < 1e-11
+    torch.cuda.synchronize()
