@@ -23,12 +23,15 @@
  * - Blob arrays are contiguous FP64 arrays of N values, in the order the blobs
  *   were given to ibrd_set_blobs.
  * - Every pointer argument is a DEVICE pointer on the device that was current
- *   when the handle was created, caller-owned; the library never frees it.
+ *   when the handle was created, caller-owned, unless its description says
+ *   HOST; the library never frees it.
  *   All work is ordered on the stream given to ibrd_grid_create. Entry points
  *   that return a status synchronize that stream only where stated.
  * - No exception crosses the ABI. On failure a call returns a non-zero status;
  *   ibrd_last_error(handle) then returns a message owned by the handle.
- * - A handle is not thread-safe: calls on one handle must not overlap.
+ * - A handle is not thread-safe: calls on one handle must not overlap. Calls
+ *   on different handles may run at the same time from different host
+ *   threads (the batched entry points do so).
  */
 #ifndef IBRD_H
 #define IBRD_H
