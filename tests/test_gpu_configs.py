@@ -42,6 +42,26 @@ def test_mixed64_against_oracle(ibrd, precision):
     assert abs(info["rate_K"] - K_ref) < 1e-11 * abs(K_ref)
 
 
+@pytest.mark.parametrize("precision", [0, 2])
+def test_mixed64_with_forced_launch_shapes(ibrd, precision):
+    """The same solve with non-default sweep launch shapes on every smoothed
+    level (tile width 32, z-march depth 3 with a ragged last chunk; the
+    stencil pass of the sweep from zero with depth 5): the solution is the
+    oracle's, as with the built-in shapes."""
+    w = workload("mixed64")
+    c_ref, lam_ref, _ = direct.solve_saddle(w.q, w.g, w.h, w.chi, 0.0)
+    g = ibrd.Grid(*w.dims, h=w.h, chi=w.chi)
+    g.set_blobs(dev(w.q))
+    for side in (64, 32, 16):
+        for elem in (4, 8):
+            ibrd.ibrd_tune_set(g.handle, elem, 0, side, side, side, 32, 3)
+        ibrd.ibrd_tune_set(g.handle, 4, 1, side, side, side, 0, 5)
+    tol = floor_tol(c_ref, w.g, w.h, w.chi, 0.0)
+    c, lam, info = g.solve_saddle(dev(w.g), tol=tol, precision=precision, max_iter=2000)
+    assert info["status"] == 0 and info["rel_residual"] <= tol
+    assert rel_l2(host(c), c_ref) < 1e-11 and rel_l2(host(lam), lam_ref) < 1e-11
+
+
 def test_mixed512_modes_against_fp64(ibrd):
     w = workload("mixed")
     g = ibrd.Grid(*w.dims, h=w.h, chi=w.chi)
