@@ -641,6 +641,28 @@ def run_learned(p, torch, world, args):
     return out
 
 
+def run_kernel_case_fp64(args):
+    """FP64 operator applications y = A c on a 256^3 field (about 0.27 GB on
+    the device) with a profiler range around one of them: the small case for
+    ncu captures of the FP64 stencil (the kernel of the refinement residual)."""
+    import torch
+    from paper_1306_3159_gb300 import build as pbuild
+    pbuild.build()
+    import paper_1306_3159_gb300 as p
+    n = 256
+    grid = p.Grid(n, n, n, stream=torch.cuda.current_stream().cuda_stream)
+    c = torch.randn((n, n, n), dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(2))
+    y = torch.zeros_like(c)
+    for _ in range(3):
+        grid.apply_L(c, y)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    grid.apply_L(c, y)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    log("[bench] FP64 kernel case done")
+
+
 def run_kernel_case(args):
     """FP32 V-cycles on a 256^3 field (about 0.3 GB on the device) with a
     profiler range around one V-cycle: the small case for full ncu captures of
@@ -761,6 +783,7 @@ def main():
     ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--ncu-step", action="store_true", help="profiler range around one step, then exit")
     ap.add_argument("--kernel-case", action="store_true", help="FP32 V-cycles at 256^3 for ncu, then exit")
+    ap.add_argument("--kernel-case-fp64", action="store_true", help="FP64 A c at 256^3 for ncu, then exit")
     args = ap.parse_args()
     if args.oracle_sample:
         print(json.dumps(_oracle_sample(args.oracle_sample)), flush=True)
@@ -770,6 +793,8 @@ def main():
         args.warmup = 3
     if args.kernel_case:
         run_kernel_case(args)
+    elif args.kernel_case_fp64:
+        run_kernel_case_fp64(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
