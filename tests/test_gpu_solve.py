@@ -412,9 +412,10 @@ RANDOM_SHAPES = [(16, 24, 32), (40, 24, 16), (48, 48, 16), (32, 64, 16), (24, 24
 
 @pytest.mark.parametrize("seed", range(6))
 def test_random_configurations(ibrd, seed):
-    """Seeded random configurations: grid shape, blob count (RSA, spacing 3h),
-    kernel width, shift alpha and precision mode drawn per case; both solves
-    against the oracle's exact solutions."""
+    """Seeded random configurations: grid shape, spacing h, diffusion
+    coefficient chi, blob count (RSA, spacing 3h), kernel width, shift alpha
+    and precision mode drawn per case; both solves against the oracle's exact
+    solutions."""
     import torch
     rng = np.random.default_rng(1000 + seed)
     dims = RANDOM_SHAPES[seed]
@@ -422,23 +423,26 @@ def test_random_configurations(ibrd, seed):
     w_k = int(rng.choice([3, 4]))
     alpha = float(rng.choice([0.0, 0.3]))
     precision = int(rng.integers(0, 3))
-    q = rsa_positions(n, dims, 1.0, 3.0, 2000 + seed)
+    h = float(rng.choice([0.5, 1.0, 2.0]))
+    chi = float(rng.choice([0.7, 1.0, 1.3]))
+    q = rsa_positions(n, dims, h, 3.0 * h, 2000 + seed)
     n = len(q)
     kappa = loguniform_rates(n, 0.1, 10.0, 3000 + seed)
     nx, ny, nz = dims
     gsrc = 1.0 + 0.5 * rng.random((nz, ny, nx))
-    g = ibrd.Grid(*dims, alpha=alpha, kernel=w_k)
+    g = ibrd.Grid(*dims, h=h, chi=chi, alpha=alpha, kernel=w_k)
     g.set_blobs(dev(q))
-    c_ref, lam_ref, _ = direct.solve_saddle(q, gsrc, 1.0, 1.0, alpha, w=w_k)
-    tol = max(1e-12, floor_tol(c_ref, gsrc, 1.0, 1.0, alpha))
+    case = (dims, h, chi, n, w_k, alpha, precision)
+    c_ref, lam_ref, _ = direct.solve_saddle(q, gsrc, h, chi, alpha, w=w_k)
+    tol = max(1e-12, floor_tol(c_ref, gsrc, h, chi, alpha))
     c, lam, info = g.solve_saddle(dev(gsrc), tol=tol, precision=precision, max_iter=600)
-    assert info["rel_residual"] <= tol
-    assert rel_l2(host(c), c_ref) < 1e-10 and rel_l2(host(lam), lam_ref) < 1e-10, (dims, n, w_k, alpha, precision)
-    cr_ref, u_ref, _ = direct.solve_reaction(q, kappa, gsrc, 1.0, 1.0, alpha, w=w_k)
-    tol = max(1e-12, floor_tol(cr_ref, gsrc, 1.0, 1.0, alpha))
+    assert info["rel_residual"] <= tol, case
+    assert rel_l2(host(c), c_ref) < 1e-10 and rel_l2(host(lam), lam_ref) < 1e-10, case
+    cr_ref, u_ref, _ = direct.solve_reaction(q, kappa, gsrc, h, chi, alpha, w=w_k)
+    tol = max(1e-12, floor_tol(cr_ref, gsrc, h, chi, alpha))
     cr, info = g.solve_reaction(dev(kappa), dev(gsrc), tol=tol, precision=precision, max_iter=600)
-    assert info["rel_residual"] <= tol
-    assert rel_l2(host(cr), cr_ref) < 1e-10, (dims, n, w_k, alpha, precision)
+    assert info["rel_residual"] <= tol, case
+    assert rel_l2(host(cr), cr_ref) < 1e-10, case
     torch.cuda.synchronize()
 
 
