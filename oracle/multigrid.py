@@ -56,16 +56,25 @@ def _colour_masks(shape):
     return red, ~red
 
 
-def rbgs_sweep(x, b, h, chi, alpha):
-    """One red-then-black Gauss-Seidel sweep on A x = b (in place)."""
-    red, black = _colour_masks(x.shape)
+def rbgs_half_sweep(x, b, h, chi, alpha, colour):
+    """Gauss-Seidel update of every cell of one colour (0 = red, 1 = black) of
+    A x = b, in place: each such cell solves its own row of A x = b with its
+    six neighbours (all of the other colour) held at their current values."""
+    mask = _colour_masks(x.shape)[colour]
     diag = alpha + 6.0 * chi / (h * h)
     off = chi / (h * h)
-    for mask in (red, black):
-        nb = np.zeros_like(x)
-        for ax in range(3):
-            nb += np.roll(x, 1, axis=ax) + np.roll(x, -1, axis=ax)
-        x[mask] = ((b + off * nb) / diag)[mask]
+    nb = np.zeros_like(x)
+    for ax in range(3):
+        nb += np.roll(x, 1, axis=ax) + np.roll(x, -1, axis=ax)
+    x[mask] = ((b + off * nb) / diag)[mask]
+    return x
+
+
+def rbgs_sweep(x, b, h, chi, alpha):
+    """One red-black Gauss-Seidel sweep on A x = b (in place): the red half
+    from the old black values, then the black half from the new red values."""
+    rbgs_half_sweep(x, b, h, chi, alpha, 0)
+    rbgs_half_sweep(x, b, h, chi, alpha, 1)
     return x
 
 

@@ -22,9 +22,25 @@ def reaction_radius(lam: np.ndarray, c: np.ndarray, chi: float) -> float:
     return overall_rate(lam, c) / (4.0 * math.pi * chi)
 
 
-def extrapolated_radius(a_L: float, L: int, h: float) -> float:
-    """a ~ a_L - 2.84 a_L^2 / (L h), the leading correction of Eq. a_phi."""
-    return a_L - 2.84 * a_L * a_L / (L * h)
+RADIUS_SERIES_COEFFICIENT = 2.84  # Eq. a_phi
+
+
+def extrapolated_radius(a_L: float, L: int, h: float, k: float = RADIUS_SERIES_COEFFICIENT) -> float:
+    """a ~ a_L - k a_L^2 / (L h): the first-order inversion of Eq. a_phi that
+    Sec. IV.A uses for the translational-invariance study at L = 128. Its
+    error against the exact inverse of the series is second order in a / L."""
+    return a_L - k * a_L * a_L / (L * h)
+
+
+def radius_from_series(a_L: float, L: int, h: float, k: float = RADIUS_SERIES_COEFFICIENT) -> float:
+    """The a that solves Eq. a_phi truncated after its quadratic term,
+    a_L = a [1 + k a/(L h) + (k a/(L h))^2], by fixed-point iteration from
+    a = a_L (a contraction while k a_L / (L h) < 1/2)."""
+    a = a_L
+    for _ in range(200):
+        x = k * a / (L * h)
+        a = a_L / (1.0 + x + x * x)
+    return a
 
 
 def beta0(cbar: float, s: float, a: float, chi: float, n_blobs: int, volume: float) -> float:

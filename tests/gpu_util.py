@@ -23,6 +23,12 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
+def rel_err(a, b):
+    """The larger of the element-wise error (max |a - b| over max |b|) and
+    the relative L2 error: a parity bound on it bounds every element."""
+    return max(rel_max(a, b), rel_l2(a, b))
+
+
 EPS = 2.220446049250313e-16
 
 

@@ -7,7 +7,7 @@ import pytest
 
 from oracle import direct, gnn
 from synthetic import rsa_positions, workload
-from tests.gpu_util import dev, floor_tol, host, rel_l2
+from tests.gpu_util import dev, floor_tol, host, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -85,7 +85,7 @@ def test_forward_loss_gradient_and_adam(ibrd):
     # prediction: softmax of y scaled to the total
     lam0 = host(m.predict(qd, box, 123.0))
     assert abs(lam0.sum() - 123.0) < 1e-9 * 123.0
-    assert rel_l2(lam0, gnn.predict(gnn.pack(gnn.unpack(th1)), q, box, R, 123.0)) < 1e-5
+    assert rel_err(lam0, gnn.predict(gnn.pack(gnn.unpack(th1)), q, box, R, 123.0)) < 1e-5
 
 
 def test_too_many_neighbours_is_an_argument_error(ibrd):
@@ -143,7 +143,7 @@ def test_learned_warm_start_saddle(ibrd):
     tol = floor_tol(c_ref, w.g, w.h, w.chi, 0.0)
     c, lam, info = g.solve_saddle(dev(w.g), lam=lam0, tol=tol, precision=2, lambda_guess=2, max_iter=400)
     assert info["rel_residual"] <= tol
-    assert rel_l2(host(c), c_ref) < 1e-11 and rel_l2(host(lam), lam_ref) < 1e-11
+    assert rel_err(host(c), c_ref) < 1e-11 and rel_err(host(lam), lam_ref) < 1e-11
     torch.cuda.synchronize()
 
 

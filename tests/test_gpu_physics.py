@@ -31,11 +31,7 @@ def _radius(ibrd, L, q, w=4):
     # far more digits than the percent-level checks below need
     c, lam, info = g.solve_saddle(dev(src), tol=1e-8, max_iter=500)
     aL = info["sum_lambda"] / (4 * math.pi * 1.0 * info["cbar"])
-    a = aL
-    for _ in range(200):
-        x = 2.84 * a / L
-        a = aL / (1 + x + x * x)
-    return aL, a
+    return aL, outputs.radius_from_series(aL, L, 1.0)
 
 
 def test_reaction_radius_at_node_L128(ibrd):

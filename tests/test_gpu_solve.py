@@ -16,7 +16,7 @@ import pytest
 
 from oracle import direct, operators as op, outputs
 from synthetic import workload, loguniform_rates, lattice_positions, rsa_positions
-from tests.gpu_util import dev, host, rel_l2, rel_max
+from tests.gpu_util import dev, host, rel_err, rel_max
 
 pytestmark = pytest.mark.gpu
 
@@ -72,8 +72,8 @@ def test_saddle_small(ibrd, small, precision, tol, err):
     c, lam, info = g.solve_saddle(dev(w.g), tol=tol, precision=precision, max_iter=400)
     assert info["rel_residual"] <= tol
     assert (info["refinements"] >= 1) == (precision == 2)
-    assert rel_l2(host(c), c_ref) < err
-    assert rel_l2(host(lam), lam_ref) < err
+    assert rel_err(host(c), c_ref) < err
+    assert rel_err(host(lam), lam_ref) < err
     # Appendix A solvability: sum lambda = h^3 sum g / zeta
     assert abs(info["sum_lambda"] - w.g.sum()) < 1e-9 * w.g.sum()
     K_ref = outputs.overall_rate(lam_ref, c_ref)
@@ -92,7 +92,7 @@ def test_reaction_small(ibrd, small, precision, tol, err, alpha):
     tol = max(tol, floor_tol(c_ref, w.g, w.h, w.chi, alpha))
     c, info = g.solve_reaction(dev(w.kappa), dev(w.g), tol=tol, precision=precision, max_iter=400)
     assert info["rel_residual"] <= tol
-    assert rel_l2(host(c), c_ref) < err
+    assert rel_err(host(c), c_ref) < err
     assert abs(info["sum_lambda"] - u_ref.sum()) < err * abs(u_ref.sum())
 
 
@@ -108,8 +108,8 @@ def test_saddle_alpha_positive_nonunit_scales(ibrd):
     g.set_blobs(dev(q))
     # alpha > 0: no large constant mode, so the solve can go below 1e-12
     c, lam, info = g.solve_saddle(dev(gsrc), f=dev(f), tol=1e-14, zeta=zeta, max_iter=400)
-    assert rel_l2(host(c), c_ref) < 1e-11
-    assert rel_l2(host(lam), lam_ref) < 1e-11
+    assert rel_err(host(c), c_ref) < 1e-11
+    assert rel_err(host(lam), lam_ref) < 1e-11
 
 
 def test_saddle_tiny_single_blob(ibrd):
@@ -118,7 +118,7 @@ def test_saddle_tiny_single_blob(ibrd):
     c_ref, lam_ref, _ = direct.solve_saddle(w.q, w.g, w.h, w.chi, 0.0)
     g = _grid(ibrd, w)
     c, lam, info = g.solve_saddle(dev(w.g), tol=floor_tol(c_ref, w.g, 1.0, 1.0, 0.0), max_iter=400)
-    assert rel_l2(host(c), c_ref) < 1e-11
+    assert rel_err(host(c), c_ref) < 1e-11
     assert abs(host(lam)[0] - lam_ref[0]) < 1e-11 * abs(lam_ref[0])
 
 
@@ -128,7 +128,7 @@ def test_saddle_diagonal_preconditioner(ibrd, small):
     g = _grid(ibrd, w)
     tol = floor_tol(c_ref, w.g, w.h, w.chi, 0.0)
     c, lam, info = g.solve_saddle(dev(w.g), tol=tol, precond=1, restart=60, max_iter=2000)
-    assert rel_l2(host(lam), lam_ref) < 1e-11
+    assert rel_err(host(lam), lam_ref) < 1e-11
 
 
 def test_single_blob_finite_rate_shift(ibrd):
@@ -258,7 +258,7 @@ def test_batch_matches_single_solves(ibrd, precision):
     k = min(range(len(ws)), key=lambda i: ws[i].dims[0] ** 3 + len(ws[i].q))
     w = ws[k]
     c_ref, _, _ = direct.solve_reaction(w.q, w.kappa, w.g, w.h, w.chi, 0.0)
-    assert rel_l2(host(cb[k]), c_ref) < 1e-8
+    assert rel_err(host(cb[k]), c_ref) < 1e-8
     torch.cuda.synchronize()
 
 
@@ -284,7 +284,7 @@ def test_saddle_warm_start(ibrd, small, precision):
         c, lam, info = g.solve_saddle(dev(w.g), lam=lam, tol=tol, precision=precision, max_iter=400,
                                       lambda_guess=guess, warm_cycles=3)
         assert info["rel_residual"] <= tol
-        assert rel_l2(host(c), c_ref) < err and rel_l2(host(lam), lam_ref) < err
+        assert rel_err(host(c), c_ref) < err and rel_err(host(lam), lam_ref) < err
         if lam0 is not None and np.array_equal(lam0, lam_ref):
             assert info["outer_iters"] <= cold["outer_iters"]
     torch.cuda.synchronize()
@@ -336,7 +336,7 @@ def test_degenerate_inputs(ibrd):
     g = ibrd.Grid(*dims, alpha=0.5)
     kappa = torch.zeros(0, dtype=torch.float64, device="cuda")
     c, info = g.solve_reaction(kappa, dev(gsrc), tol=1e-13, max_iter=200)
-    assert rel_l2(host(c), op.green_apply(gsrc, 1.0, 1.0, 0.5)) < 1e-11
+    assert rel_err(host(c), op.green_apply(gsrc, 1.0, 1.0, 0.5)) < 1e-11
     g0 = ibrd.Grid(*dims)
     with pytest.raises(ibrd.IbrdError) as e:
         g0.solve_reaction(kappa, dev(gsrc), tol=1e-10)
@@ -354,7 +354,7 @@ def test_degenerate_inputs(ibrd):
     c, lam, info = _saddle_status(ibrd, gc, w.g, 1e-11)
     assert info["status"] == 0, info["status"]
     lam = host(lam)
-    assert rel_l2(host(c), c_ref) < 1e-9
+    assert rel_err(host(c), c_ref) < 1e-9
     assert abs(lam[0] + lam[3] - lam_ref[0]) < 1e-9 * abs(lam_ref).max()
     assert np.abs(lam[1:3] - lam_ref[1:3]).max() < 1e-9 * abs(lam_ref).max()
     torch.cuda.synchronize()
@@ -403,7 +403,7 @@ def test_solve_many_mixed_kinds(ibrd, small):
     assert out[0]["outer_iters"] == r["outer_iters"] and out[1]["outer_iters"] == s_["outer_iters"]
     c_ref, u_ref, _ = direct.solve_reaction(w.q, w.kappa, w.g, w.h, w.chi, 0.0, M=M)
     cs_ref, lam_ref, _ = direct.solve_saddle(w.q, w.g, w.h, w.chi, 0.0, M=M)
-    assert rel_l2(host(c1), c_ref) < 1e-8 and rel_l2(host(c2), cs_ref) < 1e-8 and rel_l2(host(l2), lam_ref) < 1e-8
+    assert rel_err(host(c1), c_ref) < 1e-8 and rel_err(host(c2), cs_ref) < 1e-8 and rel_err(host(l2), lam_ref) < 1e-8
     torch.cuda.synchronize()
 
 
@@ -415,7 +415,7 @@ def test_random_configurations(ibrd, seed):
     """Seeded random configurations: grid shape, spacing h, diffusion
     coefficient chi, blob count (RSA, spacing 3h), kernel width, shift alpha
     and precision mode drawn per case; both solves against the oracle's exact
-    solutions."""
+    solutions within 1e-11 (element-wise and in L2)."""
     import torch
     rng = np.random.default_rng(1000 + seed)
     dims = RANDOM_SHAPES[seed]
@@ -437,12 +437,14 @@ def test_random_configurations(ibrd, seed):
     tol = max(1e-12, floor_tol(c_ref, gsrc, h, chi, alpha))
     c, lam, info = g.solve_saddle(dev(gsrc), tol=tol, precision=precision, max_iter=600)
     assert info["rel_residual"] <= tol, case
-    assert rel_l2(host(c), c_ref) < 1e-10 and rel_l2(host(lam), lam_ref) < 1e-10, case
+    # every precision mode forms its stopping residual in FP64 and is solved
+    # here to the FP64 rounding floor, so all of them meet the FP64 bar
+    assert rel_err(host(c), c_ref) < 1e-11 and rel_err(host(lam), lam_ref) < 1e-11, case
     cr_ref, u_ref, _ = direct.solve_reaction(q, kappa, gsrc, h, chi, alpha, w=w_k)
     tol = max(1e-12, floor_tol(cr_ref, gsrc, h, chi, alpha))
     cr, info = g.solve_reaction(dev(kappa), dev(gsrc), tol=tol, precision=precision, max_iter=600)
     assert info["rel_residual"] <= tol, case
-    assert rel_l2(host(cr), cr_ref) < 1e-10, case
+    assert rel_err(host(cr), cr_ref) < 1e-11, case
     torch.cuda.synchronize()
 
 
@@ -463,5 +465,5 @@ def test_backward_euler_steps(ibrd, small):
         rhs = c / dt + dev(w.g)
         c, info = g.solve_reaction(dev(w.kappa), rhs, tol=max(1e-12, floor_tol(c_ref, rhs_ref, w.h, w.chi, alpha)),
                                    max_iter=400)
-        assert rel_l2(host(c), c_ref) < 1e-11
+        assert rel_err(host(c), c_ref) < 1e-11
     torch.cuda.synchronize()

@@ -240,10 +240,7 @@ def test_smoluchowski_reaction_radius(w, key, tol):
     c, lam, _ = direct.solve_saddle(q, g, 1.0, 1.0, 0.0, w=w)
     aL = outputs.reaction_radius(lam, c, 1.0)
     k = GOLD["radius_series_coefficient"]["value"]
-    a = aL
-    for _ in range(200):
-        x = k * a / L
-        a = aL / (1 + x + x * x)
+    a = outputs.radius_from_series(aL, L, 1.0, k)
     assert abs(a - GOLD[key]["value"]) < tol * GOLD[key]["value"]
     # a_L decreases towards a as L grows (Eq. a_phi, positive correction)
     assert aL > a
@@ -264,6 +261,64 @@ def test_transfer_operators_exact_on_linear():
     np.testing.assert_allclose(fine[inner], lin_f[inner], atol=1e-13)
     np.testing.assert_allclose(mg.restrict(lin_f), lin_c, atol=1e-13)
     np.testing.assert_allclose(mg.prolong(np.full((4, 4, 4), 3.0)), 3.0, atol=0)
+
+
+def _rbgs_loop(x, b, h, chi, alpha):
+    """One red-black Gauss-Seidel sweep written cell by cell: every red cell
+    (i + j + k even) from its neighbours' current values, then every black
+    cell, which then sees the red cells' new values."""
+    nz, ny, nx = x.shape
+    diag = alpha + 6.0 * chi / (h * h)
+    off = chi / (h * h)
+    for colour in (0, 1):
+        for k in range(nz):
+            for j in range(ny):
+                for i in range(nx):
+                    if (i + j + k) % 2 != colour:
+                        continue
+                    s = (x[k, j, (i - 1) % nx] + x[k, j, (i + 1) % nx] + x[k, (j - 1) % ny, i]
+                         + x[k, (j + 1) % ny, i] + x[(k - 1) % nz, j, i] + x[(k + 1) % nz, j, i])
+                    x[k, j, i] = (b[k, j, i] + off * s) / diag
+    return x
+
+
+@pytest.mark.parametrize("alpha", [0.0, 0.35])
+def test_rbgs_sweep_red_then_black_per_cell(alpha):
+    """Sec. III.E smoother reading: the oracle's red-black sweep equals a
+    per-cell loop that updates red cells, then black cells from the new red
+    values (a Jacobi-ordered or colour-swapped sweep differs from it), on a
+    non-cubic periodic grid; after the red half every red row of A x = b holds
+    to rounding, and after the black half every black row does."""
+    rng = np.random.default_rng(71)
+    shape = (6, 4, 8)  # (nz, ny, nx)
+    h, chi = 0.8, 1.3
+    x0 = rng.standard_normal(shape)
+    b = rng.standard_normal(shape)
+    want = _rbgs_loop(x0.copy(), b, h, chi, alpha)
+    got = mg.rbgs_sweep(x0.copy(), b, h, chi, alpha)
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-14)
+    k, j, i = np.meshgrid(np.arange(6), np.arange(4), np.arange(8), indexing="ij")
+    red = (i + j + k) % 2 == 0
+    x = x0.copy()
+    mg.rbgs_half_sweep(x, b, h, chi, alpha, 0)
+    r = b - op.apply_A(x, h, chi, alpha)
+    assert np.abs(r[red]).max() < 1e-13 and np.abs(r[~red]).max() > 1e-3
+    np.testing.assert_array_equal(x[~red], x0[~red])
+    mg.rbgs_half_sweep(x, b, h, chi, alpha, 1)
+    np.testing.assert_array_equal(x, got)
+    r = b - op.apply_A(x, h, chi, alpha)
+    assert np.abs(r[~red]).max() < 1e-13
+    # the two plausible mistakes differ from the definition
+    jac = x0.copy()
+    nb = sum(np.roll(x0, s, axis=a) for a in range(3) for s in (1, -1))
+    upd = (b + chi / h ** 2 * nb) / (alpha + 6 * chi / h ** 2)
+    jac[red] = upd[red]
+    jac[~red] = upd[~red]
+    assert np.abs(jac - got).max() > 1e-3
+    swapped = x0.copy()
+    mg.rbgs_half_sweep(swapped, b, h, chi, alpha, 1)
+    mg.rbgs_half_sweep(swapped, b, h, chi, alpha, 0)
+    assert np.abs(swapped - got).max() > 1e-3
 
 
 def test_level_shapes():
@@ -333,6 +388,48 @@ def test_coarse_solve_vs_fft_green():
     np.testing.assert_allclose(mg.coarse_solve(b4, 8.0, 2.0, 0.0), op.green_apply(b4, 8.0, 2.0, 0.0), atol=1e-12)
 
 
+def test_radius_series_inversion():
+    """outputs.radius_from_series inverts Eq. a_phi (through its quadratic
+    term): checked against the positive real root of the cubic
+    a + k a^2 / (L h) + k^2 a^3 / (L h)^2 - a_L = 0 found by numpy.roots, for
+    several box sizes, spacings and radii. The printed coefficient is the one
+    in tests/golden."""
+    k = GOLD["radius_series_coefficient"]["value"]
+    assert outputs.RADIUS_SERIES_COEFFICIENT == k
+    for aL, L, h in [(1.62, 16, 1.0), (1.43, 32, 1.0), (1.30, 128, 1.0), (0.74, 20, 0.5), (2.9, 16, 2.0)]:
+        s = 1.0 / (L * h)
+        roots = np.roots([k * k * s * s, k * s, 1.0, -aL])
+        real = [r.real for r in roots if abs(r.imag) < 1e-12 and r.real > 0]
+        assert len(real) == 1
+        a = outputs.radius_from_series(aL, L, h)
+        assert abs(a - real[0]) < 1e-13 * aL
+        x = k * a * s
+        assert abs(a * (1 + x + x * x) - aL) < 1e-13 * aL
+
+
+def test_extrapolated_radius_is_first_order():
+    """outputs.extrapolated_radius (Sec. IV.A: a ~ a_L - 2.84 a_L^2 / (L h))
+    is the exact inverse of Eq. a_phi up to terms of second order in a/(L h):
+    with a_L built from the series for a known a, its error divided by
+    a (k a / (L h))^2 tends to a constant (-1 from the expansion
+    a_L - k a_L^2/(L h) = a (1 - x^2 - 3 x^3 + ...), x = k a / (L h)), so doubling
+    L quarters the error."""
+    k = GOLD["radius_series_coefficient"]["value"]
+    a = 1.27
+    errs = []
+    for L in (64, 128, 256, 512, 1024):
+        x = k * a / L
+        aL = a * (1 + x + x * x)
+        e = outputs.extrapolated_radius(aL, L, 1.0) - a
+        errs.append(e)
+        assert abs(e / (a * x * x) + 1.0) < 4.0 * x  # next term: -3 x
+    for e1, e2 in zip(errs, errs[1:]):
+        assert 3.5 < e1 / e2 < 4.5
+    # the paper's L = 128 study: the first-order form is within 0.1 % of the series inverse
+    aL = a * (1 + k * a / 128 + (k * a / 128) ** 2)
+    assert abs(outputs.extrapolated_radius(aL, 128, 1.0) - outputs.radius_from_series(aL, 128, 1.0)) < 1e-3 * a
+
+
 def test_outputs_formulae():
     # Eq. beta_P_disc at phi -> 0 with s = 1/V: beta0 -> (4 pi a chi cbar)^-1 (Eq. beta0_low_phi)
     a, chi, V = 1.27, 1.0, 1e9
@@ -340,14 +437,6 @@ def test_outputs_formulae():
     b = outputs.beta0(cbar, 1.0 / V, a, chi, 1, V)
     assert abs(b - 1.0) < 1e-6
     assert abs(outputs.beta0_cubic_fit(0.0) - 1.0) < 1e-15
-
-
-def _extrapolated_radius(aL, L, k=2.84):
-    a = aL
-    for _ in range(200):
-        x = k * a / L
-        a = aL / (1 + x + x * x)
-    return a
 
 
 def test_translational_invariance_of_radius():
@@ -364,7 +453,7 @@ def test_translational_invariance_of_radius():
             q = np.array([[L / 2 + 0.5 + d[0], L / 2 + 0.5 + d[1], L / 2 + 0.5 + d[2]]])
             g = np.full((L, L, L), 1.0 / L ** 3)
             c, lam, _ = direct.solve_saddle(q, g, 1.0, 1.0, 0.0, w=w)
-            vals.append(_extrapolated_radius(outputs.reaction_radius(lam, c, 1.0), L))
+            vals.append(outputs.radius_from_series(outputs.reaction_radius(lam, c, 1.0), L, 1.0))
         res[w] = np.array(vals)
     v4, v3 = res[4], res[3]
     assert (v4.max() - v4.min()) / v4.mean() < 2 * GOLD["translational_variation_4pt"]["value"]
