@@ -11,8 +11,8 @@ spreading/averaging inside FP64 flexible GMRES; the plain FP64 path is timed
 beside it.
 
 Prints one JSON line (rank 0). `value` is seconds per step (lower is better).
-`--impl reference` times the FP64 CPU oracle (direct Schur-complement solve)
-on a bounded sample of the same workload instead.
+`--impl reference` times the oracle's iterative FP64 CPU solver on the same
+workload instead (full solves on all host cores).
 """
 from __future__ import annotations
 
@@ -338,12 +338,14 @@ def run_ours(args):
     # launch shares the GPU with the other solve) with every launch timed
     # (events disable graph replay) picks the dominant class ...
     prof_enable(True)
+    prof_read()  # counts of the regions above are not part of the breakdown
     step(chosen, concurrent=False)
     prof_all = prof_read()
     dom_name, dom = max(prof_all["classes"].items(), key=lambda kv: kv[1]["ms"])
     # ... and a second timed region of the same K steps times that class's
     # largest (finest-level) launches with CUDA events on the solver streams
     prof_enable(1 << dom["id"], 0.99 * dom["max_launch_bytes"])
+    prof_read()
     t_step_instr = timed(lambda: step(chosen, concurrent=False), args.steps)
     prof_timed = prof_read()
     prof_enable(0)
@@ -443,7 +445,7 @@ def run_ours(args):
     if not args.no_learned:
         result["learned"] = run_learned(p, torch, world, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        result["cpu_baseline"] = cpu_baseline_sample(columns=args.cpu_columns)
+        result["cpu_baseline"] = cpu_baseline_run()
     if rank == 0:
         print(json.dumps(result), flush=True)
     if world > 1:
@@ -689,84 +691,99 @@ def run_kernel_case(args):
     log("[bench] kernel case done")
 
 
-# ---------------------------------------------------------------- oracle arm
-def _oracle_sample(columns: int):
-    """Time the FP64 oracle on a bounded sample of the workload and scale it
-    to one full step. The oracle solves each system directly: N Green's
-    function (FFT) solves build the Schur matrix M = J G S (shared by both
-    solves), then one dense (N+1) LU per solve and one final Green's solve per
-    solve. The sample times `columns` of the N columns and one dense LU."""
-    import numpy as np
-    from oracle import operators as op
+# ---------------------------------------------------------------- CPU arm
+# The timed CPU baseline is the oracle's iterative FP64 solver (oracle/cpu_solver.c:
+# FGMRES(30) with modified Gram-Schmidt, multigrid V-cycles with nu = 2/2, the
+# Appendix A preconditioner with m = 5, n = 1), run to completion on the same
+# workload and tolerance with all host cores.
+CPU_SETTINGS = dict(tol=1e-8, restart=30, max_iter=3000, mg_cycles=1, nu1=2, nu2=2)
+CPU_SAMPLE = ("reaction + saddle solves of the 256^3 / 4096-blob workload to rel. residual 1e-8 by "
+              "the oracle's iterative FP64 CPU solver (FGMRES(30) with MGS, V-cycles nu = 2/2, Appendix A "
+              "approximate Schur m = 5, n = 1; OpenMP over the grid loops)")
+
+
+def cpu_step(w, threads):
+    """One step of the workload on the host cores; returns timings and the
+    solver reports."""
+    from oracle import cpu_solver as cs
+    t0 = time.perf_counter()
+    _, ir = cs.solve_reaction(w.q, w.kappa, w.g, w.h, w.chi, 0.0, threads=threads, **CPU_SETTINGS)
+    t1 = time.perf_counter()
+    _, _, isd = cs.solve_saddle(w.q, w.g, w.h, w.chi, 0.0, threads=threads, schur_inner=5, **CPU_SETTINGS)
+    t2 = time.perf_counter()
+    if ir["status"] != 0 or isd["status"] != 0:
+        raise RuntimeError(f"CPU solve did not converge: {ir} {isd}")
+    return {"step_s": t2 - t0, "reaction_s": t1 - t0, "saddle_s": t2 - t1, "reaction": ir, "saddle": isd}
+
+
+def cpu_host():
+    model = ""
+    try:
+        for ln in subprocess.run(["lscpu"], capture_output=True, text=True).stdout.splitlines():
+            if ln.startswith("Model name:"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return model
+
+
+def run_cpu_steps(warmup, steps):
+    """Child-process body: `warmup` untimed and `steps` timed CPU steps."""
+    from oracle import cpu_solver as cs
     from synthetic import workload
-
+    cs.build()
     w = workload(WORKLOAD)
-    q = w.q
-    dims = w.dims
-    N = len(q)
+    threads = cs.host_threads()
+    for _ in range(warmup):
+        cpu_step(w, threads)
     t0 = time.perf_counter()
-    for j in range(columns):
-        e = np.zeros(N)
-        e[j] = 1.0
-        col = op.green_apply(op.spread(e, q, dims, w.h), w.h, w.chi, 0.0)
-        op.interp(col, q, w.h)
-    t_col = (time.perf_counter() - t0) / columns
-    rng = np.random.default_rng(0)
-    A = rng.standard_normal((N + 1, N + 1)) + (N + 1) * np.eye(N + 1)
-    t0 = time.perf_counter()
-    np.linalg.solve(A, rng.standard_normal(N + 1))
-    t_lu = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    op.green_apply(w.g - op.spread(np.ones(N), q, dims, w.h), w.h, w.chi, 0.0)
-    t_final = time.perf_counter() - t0
-    total = N * t_col + 2 * t_lu + 2 * t_final
-    return {"value": total, "t_col": t_col, "t_lu": t_lu, "t_final": t_final, "columns": columns, "N": N}
+    outs = [cpu_step(w, threads) for _ in range(steps)]
+    total = time.perf_counter() - t0
+    last = outs[-1]
+    return {"s_per_step": total / max(1, steps), "steps": steps, "threads": last["reaction"]["threads"],
+            "reaction_s": last["reaction_s"], "saddle_s": last["saddle_s"],
+            "reaction": last["reaction"], "saddle": last["saddle"], "host": cpu_host()}
 
 
-def cpu_baseline_sample(columns=3):
-    """Run the oracle sample in a child process pinned to one BLAS/FFT thread."""
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
-               CUDA_VISIBLE_DEVICES="")
-    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", str(columns)],
+def cpu_baseline_run():
+    """The CPU baseline of our arm: one untimed and one timed full step in a
+    child process (no CUDA context, all host cores)."""
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-steps", "1", "--cpu-warmup", "1"],
                        capture_output=True, text=True, env=env)
     if r.returncode != 0:
-        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": r.stderr[-400:]}
+        return {"value": None, "unit": UNIT, "cores": None, "kind": "oracle", "error": r.stderr[-400:]}
     d = json.loads(r.stdout.strip().splitlines()[-1])
-    return {"value": round(d["value"], 3), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{d['columns']} of {d['N']} Schur-complement columns (FFT Green's solves at 256^3), one "
-                      f"dense (N+1) LU and one final Green's solve, scaled to a full step (M once, 2 LU, 2 final "
-                      f"solves): t_col={d['t_col']:.3f}s t_lu={d['t_lu']:.3f}s t_final={d['t_final']:.3f}s"}
+    return {"value": round(d["s_per_step"], 3), "unit": UNIT, "cores": d["threads"], "kind": "oracle",
+            "host": d["host"], "sample": "one full step (" + CPU_SAMPLE + ") after one untimed warm-up step",
+            "reaction_s": round(d["reaction_s"], 3), "saddle_s": round(d["saddle_s"], 3),
+            "outer_iters": {"reaction": d["reaction"]["outer_iters"], "saddle": d["saddle"]["outer_iters"]},
+            "vcycles": {"reaction": d["reaction"]["vcycles"], "saddle": d["saddle"]["vcycles"]}}
 
 
 def run_reference(args):
+    """Reference arm: the oracle's iterative CPU solver on the same workload,
+    metric and tolerance as our arm; W untimed and K timed full steps on rank
+    0 (host wall clock), the other ranks exit without work."""
     rank, world, local = dist_env()
     if rank != 0:
         return
-    # each step: a bounded sample (one Schur column) scaled to a full step
-    vals = []
-    for i in range(args.warmup + args.steps):
-        d = json.loads(_oracle_sample_json(1))
-        if i >= args.warmup:
-            vals.append(d["value"])
-    v = statistics.median(vals)
-    res = {"metric": METRIC, "value": round(v, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+    d = run_cpu_steps(args.warmup, args.steps)
+    v = d["s_per_step"]
+    res = {"metric": METRIC, "value": round(v, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(v * 1e3, 1), "higher_is_better": False, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
            "config": {"workload": "256^3 periodic grid, 4096 RSA blobs (spacing 4h), uniform source, steady; "
-                                  "reaction + saddle solves (exact, direct Schur elimination)"},
-           "cpu_baseline": {"value": round(v, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
-                            "sample": "per step: 1 of 4096 Schur columns + one dense (N+1) LU + one final "
-                                      "Green's solve, scaled to the full step"},
-           "e2e": {"value": round(v, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+                                  "reaction (kappa log-uniform [0.1,10]) + saddle solves to rel. residual 1e-8",
+                      "grid": [256, 256, 256], "blobs": 4096, "tol": 1e-8,
+                      "solver": "oracle/cpu_solver.c: FP64 FGMRES(30) + multigrid + Appendix A, all host cores"},
+           "cpu_baseline": {"value": round(v, 4), "unit": UNIT, "cores": d["threads"], "kind": "oracle",
+                            "host": d["host"], "sample": "full steps (" + CPU_SAMPLE + f"); {args.warmup} untimed + "
+                                                                          f"{args.steps} timed steps"},
+           "solves": {"reaction": d["reaction"], "saddle": d["saddle"]},
+           "e2e": {"value": round(v, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(res), flush=True)
-
-
-def _oracle_sample_json(columns):
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
-               CUDA_VISIBLE_DEVICES="")
-    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", str(columns)],
-                       capture_output=True, text=True, env=env, check=True)
-    return r.stdout.strip().splitlines()[-1]
 
 
 def main():
@@ -779,14 +796,14 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-realisations leg")
     ap.add_argument("--no-autotune", action="store_true", help="built-in launch shapes only")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned warm-start leg")
-    ap.add_argument("--cpu-columns", type=int, default=3)
-    ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-steps", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-warmup", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--ncu-step", action="store_true", help="profiler range around one step, then exit")
     ap.add_argument("--kernel-case", action="store_true", help="FP32 V-cycles at 256^3 for ncu, then exit")
     ap.add_argument("--kernel-case-fp64", action="store_true", help="FP64 A c at 256^3 for ncu, then exit")
     args = ap.parse_args()
-    if args.oracle_sample:
-        print(json.dumps(_oracle_sample(args.oracle_sample)), flush=True)
+    if args.cpu_steps:
+        print(json.dumps(run_cpu_steps(args.cpu_warmup, args.cpu_steps)), flush=True)
         return
     if args.warmup < 3:
         log("[bench] warmup raised to 3 (minimum)")

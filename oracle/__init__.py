@@ -29,6 +29,11 @@ Contents (every function cites the passage it follows):
                     cell-centred prolongation, exact coarsest solve).
 * ``outputs``    -- mean concentration, overall rate K, reaction radius a_L,
                     beta_0 (Sec. I.A, Sec. IV.A, Eqs. beta_P_disc, a_phi).
+* ``cpu_solver`` -- the paper's iterative method (FGMRES with modified
+                    Gram-Schmidt, multigrid V-cycles, Appendix A) written
+                    plainly in C + OpenMP (``cpu_solver.c``): the CPU baseline
+                    that solves the full benchmark workload on the host cores.
+                    Loaded on demand (it needs gcc), not by this package.
 
 Parity status: every function above is pinned by tests in ``tests/`` against
 closed forms, exact invariants, brute-force dense solves or printed constants.
