@@ -31,7 +31,7 @@ def _worker(rank, world, port, out):
 def test_two_gloo_ranks_agree_on_max_time():
     world = 2
     port = _free_port()
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()  # no fork of a process that holds OpenMP threads
     out = mgr.dict()
     mp.start_processes(_worker, args=(world, port, out), nprocs=world, join=True, start_method="spawn")
     for rank in range(world):
