@@ -50,7 +50,7 @@ typedef enum {
   IBRD_ERR_NOT_CONVERGED = 4,  /* max_iter reached; best iterate written */
   IBRD_ERR_BREAKDOWN = 5,      /* Krylov breakdown before convergence */
   IBRD_ERR_NONFINITE = 6,      /* NaN/Inf in an input or a residual */
-  IBRD_ERR_TIMEOUT = 7,        /* reserved: bounded device wait expired */
+  IBRD_ERR_TIMEOUT = 7,        /* a bounded device wait gave up (see ibrd_set_wait_limit) */
   IBRD_ERR_STATE = 8           /* call needs state not set (e.g. no blobs) */
 } ibrd_status;
 
@@ -299,9 +299,11 @@ ibrd_status ibrd_solve_many(int count, const ibrd_solve_item* items, int threads
 
 /* Autotuner (not in the paper: launch-shape selection for this library's
    kernels). For every multigrid level whose red-black sweeps (Sec. III.E) run
-   as the fused sweep kernel, times candidate launch shapes of that kernel --
-   tile width (32 or 64 cells in x, FP32) and z-march depth (planes per CTA,
-   1 to 512) -- and the z-march depth of the stencil pass that forms the first
+   as a fused one-pass sweep kernel, times candidate launch shapes of the
+   sweep -- the row-resident FP32 kernel (levels whose rows are 128 or 256
+   cells; tx = nx) or the tiled kernel with tile width 32 or 64 cells (FP32)
+   or 32 (FP64), each with z-march depths (planes per CTA, 2 to 512) -- and
+   the z-march depth of the stencil pass that forms the first
    sweep from a zero guess (FP32), on scratch fields of the level's size with
    CUDA events, and keeps a shape only when it is at least 3 % faster than the
    built-in one. Shapes tuned before in this process for the same device and
@@ -319,7 +321,7 @@ typedef struct {
   int nx, ny, nz;    /* level grid */
   int elem_bytes;    /* 4 (FP32) or 8 (FP64) */
   int kind;          /* 0: fused sweep; 1: stencil pass of a sweep from zero */
-  int tx, zc;        /* kept tile width (0: built-in) and z-march depth (0: built-in) */
+  int tx, zc;        /* kept tile width (0: built-in; nx: row-resident kernel) and z-march depth (0: built-in) */
   double us_default; /* average launch time of the built-in shape, microseconds */
   double us_tuned;   /* average launch time of the kept shape */
   int cached;        /* 1: reused from an earlier tuning in this process */
@@ -329,10 +331,25 @@ ibrd_status ibrd_autotune(ibrd_grid g, int precision, int retune, ibrd_tune_entr
 
 /* Set one launch shape by hand (as ibrd_autotune would keep it): elem_bytes
    4 or 8, kind 0 or 1 as in ibrd_tune_entry, (nx, ny, nz) a level of the
-   handle's hierarchy, tx in {0, 32, 64} (0 for kind 1; 64 only for FP32 and
-   when 64 divides nx, else ignored), zc >= 0 (0 = built-in; clamped to the
-   level's nz). Drops the handle's captured CUDA graphs. */
+   handle's hierarchy, tx in {0, 32, 64} or tx = nx (0 for kind 1; 64 only
+   for FP32 and when 64 divides nx, else ignored; nx selects the row-resident
+   FP32 sweep on levels whose rows are 128 or 256 cells, ny a multiple of 8
+   and nz even), zc >= 0 (0 = built-in; clamped to the level's nz). Drops the
+   handle's captured CUDA graphs. */
 ibrd_status ibrd_tune_set(ibrd_grid g, int elem_bytes, int kind, int nx, int ny, int nz, int tx, int zc);
+
+/* Bound on the device waits of this handle's kernels (not in the paper). The
+   row-resident FP32 sweep waits in every plane step for its TMA copies on an
+   mbarrier; each wait makes at most `tries` polls (mbarrier try_wait, each of
+   which may suspend the thread for a short hardware-defined time) before it
+   gives up. A wait that gives up makes its CTA wait (with a fixed larger
+   bound) for its copies still in flight and stop; the launch's output is then
+   incomplete, and the solve that ran it returns IBRD_ERR_TIMEOUT (its
+   iterate is not a solution), as does ibrd_vcycle / ibrd_vcycle_f32 when the
+   stream is not being captured. Default 2^24 polls, far beyond any copy's
+   latency; 0 makes every such wait give up at once (for testing the error
+   path; no wait ever spins without bound). */
+ibrd_status ibrd_set_wait_limit(ibrd_grid g, unsigned tries);
 
 /* Forget the handle's tuned shapes (back to the built-in ones); drops its
    captured CUDA graphs. */

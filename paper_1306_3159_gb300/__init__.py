@@ -20,7 +20,8 @@ from ._abi import (
     Grid, IbrdError, SolveOpts, ibrd_apply_L, ibrd_autotune, ibrd_default_opts, ibrd_gnn_num_params,
     ibrd_grid_create, ibrd_grid_destroy, ibrd_interp, ibrd_last_error, ibrd_profile_enable, ibrd_profile_read,
     ibrd_set_blobs, ibrd_solve_many, ibrd_solve_reaction, ibrd_solve_reaction_batch, ibrd_solve_saddle,
-    ibrd_solve_saddle_batch, ibrd_spread, ibrd_tune_clear, ibrd_tune_set, ibrd_vcycle, ibrd_vcycle_f32,
+    ibrd_solve_saddle_batch, ibrd_spread, ibrd_set_wait_limit, ibrd_tune_clear, ibrd_tune_set, ibrd_vcycle,
+    ibrd_vcycle_f32,
     load_library)
 
 __all__ = [
@@ -30,6 +31,6 @@ __all__ = [
     "ibrd_autotune", "ibrd_default_opts", "ibrd_gnn_num_params", "ibrd_grid_create", "ibrd_grid_destroy",
     "ibrd_interp", "ibrd_last_error", "ibrd_profile_enable", "ibrd_profile_read", "ibrd_set_blobs",
     "ibrd_solve_many", "ibrd_solve_reaction", "ibrd_solve_reaction_batch", "ibrd_solve_saddle",
-    "ibrd_solve_saddle_batch", "ibrd_spread", "ibrd_tune_clear", "ibrd_tune_set", "ibrd_vcycle",
+    "ibrd_solve_saddle_batch", "ibrd_spread", "ibrd_set_wait_limit", "ibrd_tune_clear", "ibrd_tune_set", "ibrd_vcycle",
     "ibrd_vcycle_f32", "load_library",
 ]

@@ -23,7 +23,7 @@ STATUS = {0: "IBRD_OK", 1: "IBRD_ERR_ARG", 2: "IBRD_ERR_CUDA", 3: "IBRD_ERR_OOM"
 EXPORTED = ["ibrd_default_opts", "ibrd_grid_create", "ibrd_grid_destroy", "ibrd_set_blobs", "ibrd_apply_L",
             "ibrd_vcycle", "ibrd_vcycle_f32", "ibrd_vcycle_noalloc", "ibrd_spread", "ibrd_interp", "ibrd_solve_reaction", "ibrd_solve_saddle",
             "ibrd_solve_reaction_batch", "ibrd_solve_saddle_batch", "ibrd_solve_many", "ibrd_autotune", "ibrd_tune_set",
-            "ibrd_tune_clear", "ibrd_gnn_num_params", "ibrd_gnn_create", "ibrd_gnn_destroy", "ibrd_gnn_last_error",
+            "ibrd_tune_clear", "ibrd_set_wait_limit", "ibrd_gnn_num_params", "ibrd_gnn_create", "ibrd_gnn_destroy", "ibrd_gnn_last_error",
             "ibrd_gnn_set_params", "ibrd_gnn_get_params", "ibrd_gnn_init_params", "ibrd_gnn_neighbours", "ibrd_gnn_forward",
             "ibrd_gnn_predict", "ibrd_gnn_loss_grad", "ibrd_gnn_adam_step", "ibrd_gnn_train",
             "ibrd_last_error", "ibrd_status_string", "ibrd_profile_enable", "ibrd_profile_read",
@@ -126,6 +126,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ibrd_tune_set.restype = i
     lib.ibrd_tune_clear.argtypes = [vp]
     lib.ibrd_tune_clear.restype = i
+    lib.ibrd_set_wait_limit.argtypes = [vp, ctypes.c_uint]
+    lib.ibrd_set_wait_limit.restype = i
     lib.ibrd_gnn_num_params.argtypes = []
     lib.ibrd_gnn_num_params.restype = i
     lib.ibrd_gnn_create.argtypes = [P(vp), d, i, vp]
@@ -397,6 +399,11 @@ def ibrd_tune_set(g, elem_bytes, kind, nx, ny, nz, tx, zc):
 
 def ibrd_tune_clear(g):
     _check(g, load_library().ibrd_tune_clear(g))
+
+
+def ibrd_set_wait_limit(g, tries):
+    """Polls each bounded device wait of handle g makes before it gives up."""
+    _check(g, load_library().ibrd_set_wait_limit(g, int(tries)))
 
 
 PROF_ALL = (1 << PROF_NCLASS) - 1

@@ -20,8 +20,8 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libibrd.so")
 STAMP = os.path.join(BUILD, "stamp.txt")
-SOURCES = ["grid_kernels.cu", "smoother.cu", "blob_kernels.cu", "krylov_kernels.cu", "api.cu", "noalloc.cu",
-           "gnn.cu"]
+SOURCES = ["grid_kernels.cu", "smoother.cu", "sweep_rows.cu", "blob_kernels.cu", "krylov_kernels.cu", "api.cu",
+           "noalloc.cu", "gnn.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fno-strict-aliasing",
          "-Wno-deprecated-declarations"]

@@ -50,6 +50,7 @@ enum Slot {
   S_XMEAN1,   // mean of c~* (saddle preconditioner)
   S_RFLAG,    // Gram-Schmidt second pass taken in this iteration (0/1)
   S_RCOUNT,   // second passes taken in this solve
+  S_WAIT,     // nonzero bits: a bounded device wait gave up (written as an int)
   S_UB = 64,  // mean of S U_j for the inner iterations j = 0..m (64 slots)
   S_UX = 128, // mean of A~^-1 S U_j (64 slots)
   S_COUNT = 192
@@ -122,6 +123,9 @@ struct Tuning {
     SweepShape s;
   };
   std::vector<Entry> e;
+  // context of kernels with bounded device waits
+  int* wait_err = nullptr;              // device flag set when a wait gives up
+  unsigned wait_limit = kDefaultWaitLimit;  // tries per wait
   SweepShape* find(int elem, int kind, Dims d) {
     for (auto& x : e)
       if (x.elem == elem && x.kind == kind && x.d.nx == d.nx && x.d.ny == d.ny && x.d.nz == d.nz) return &x.s;
@@ -141,6 +145,9 @@ const SweepShape* tuned_sweep(int elem, int kind, Dims d) {
   const SweepShape* x = t->find(elem, kind, d);
   return (x && (x->tx || x->zc)) ? x : nullptr;
 }
+
+int* wait_error_flag() { return t_tune ? t_tune->wait_err : nullptr; }
+unsigned wait_limit() { return t_tune ? t_tune->wait_limit : kDefaultWaitLimit; }
 
 void prof_begin(int cls, cudaStream_t s) {
   Profiler* p = t_prof;
@@ -267,6 +274,13 @@ T* dalloc(size_t n) {
   T* p = nullptr;
   IBRD_CUDA(cudaMalloc(&p, sizeof(T) * (n ? n : 1)));
   return p;
+}
+
+// The wait flag is an int written into the low bytes of a zeroed double slot.
+bool wait_bits(double v) {
+  unsigned long long u;
+  std::memcpy(&u, &v, sizeof(u));
+  return u != 0;
 }
 
 double host_scalar(ibrd_grid g, int slot) {
@@ -756,9 +770,13 @@ SolveResult fgmres(ibrd_grid g, LinOp<E>& op, const E* b, E* x, size_t n, const 
       launch_scale_by_inv<E>(w, w, n, hcol + j + 1, 1.0, g->s);
       launch_givens(g->H, ldh, j, g->cs, g->sn, g->gvec, g->scal + S_RES, g->s);
       // one host read per iteration: residual estimate and the norms
-      IBRD_CUDA(cudaMemcpyAsync(g->host, g->scal, sizeof(double) * 16, cudaMemcpyDeviceToHost, g->s));
+      IBRD_CUDA(cudaMemcpyAsync(g->host, g->scal, sizeof(double) * (S_WAIT + 1), cudaMemcpyDeviceToHost, g->s));
       IBRD_CUDA(cudaStreamSynchronize(g->s));
       const double res = g->host[S_RES], sq = g->host[S_SQ], ww = g->host[S_TMP];
+      if (wait_bits(g->host[S_WAIT])) {
+        R.st = IBRD_ERR_TIMEOUT;
+        break;
+      }
       // breakdown: w lies in the span of V (a zero or negligible new column,
       // relative to the rounding of E); V[j+1] is then not used again
       const double floor_sq = sizeof(E) == 4 ? 1e-12 : 1e-28;
@@ -781,7 +799,7 @@ SolveResult fgmres(ibrd_grid g, LinOp<E>& op, const E* b, E* x, size_t n, const 
       }
       if (R.iters >= max_iter) break;
     }
-    if (R.st == IBRD_ERR_NONFINITE) break;
+    if (R.st == IBRD_ERR_NONFINITE || R.st == IBRD_ERR_TIMEOUT) break;
     // x += Z y
     launch_backsolve(g->H, ldh, k, g->gvec, g->yv, g->s);
     for (int g0 = 0; g0 < k; g0 += kDotGroup) {
@@ -889,8 +907,8 @@ SolveResult refine(ibrd_grid g, LinOp<double>& op64, LinOp<float>& op32, const d
                       g->scal + S_TMP2, r32norm);
     R.iters += I.iters;
     g->refinements++;
-    if (I.st == IBRD_ERR_NONFINITE) {
-      R.st = IBRD_ERR_NONFINITE;
+    if (I.st == IBRD_ERR_NONFINITE || I.st == IBRD_ERR_TIMEOUT) {
+      R.st = I.st;
       break;
     }
     launch_add_scaled(1.0 / sigma, g->ir_d32, x, n, g->s);
@@ -1229,6 +1247,23 @@ double compute_gamma(ibrd_grid g, const ibrd_solve_opts& o) {
   return g->host[0];
 }
 
+// Whether a bounded device wait of this handle's kernels gave up since the
+// last check (then the flag is cleared). Waits for the handle's stream.
+bool take_wait_flag(ibrd_grid g) {
+  const bool flag = wait_bits(host_scalar(g, S_WAIT));
+  if (flag) IBRD_CUDA(cudaMemsetAsync(g->scal + S_WAIT, 0, sizeof(double), g->s));
+  return flag;
+}
+
+// Entry points that only enqueue work check the flag when the stream is not
+// being captured into a graph (a capture cannot synchronize).
+void check_waits_if_not_capturing(ibrd_grid g, const char* name) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  IBRD_CUDA(cudaStreamIsCapturing(g->s, &cs));
+  if (cs == cudaStreamCaptureStatusNone && take_wait_flag(g))
+    throw ArgError{IBRD_ERR_TIMEOUT, std::string(name) + ": a bounded device wait gave up"};
+}
+
 ibrd_status fail(ibrd_grid g, ibrd_status st, const std::string& msg) {
   if (g) g->err = msg;
   return st;
@@ -1436,6 +1471,7 @@ void autotune_levels(ibrd_grid g, bool retune, std::vector<ibrd_tune_entry>& rep
           if (kind == TUNE_SWEEP) {
             txs = {32};
             if (elem == 4 && d.nx % 64 == 0) txs.push_back(64);
+            if (elem == 4 && rows_sweep_ok(d)) txs.push_back(d.nx);
           }
           static const int zcs[] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512};
           for (int tx : txs)
@@ -1632,6 +1668,8 @@ ibrd_status ibrd_grid_create(ibrd_grid* out, int nx, int ny, int nz, double h, d
     g->scal = dalloc<double>(S_COUNT);
     g->partial = dalloc<double>((size_t)kRedBlocks * kDotGroup);
     g->dflag = dalloc<int>(4);
+    IBRD_CUDA(cudaMemsetAsync(g->dflag, 0, sizeof(int) * 4, g->s));
+    g->tune.wait_err = reinterpret_cast<int*>(g->scal + S_WAIT);
     IBRD_CUDA(cudaMallocHost(&g->host, sizeof(double) * 64));
     IBRD_CUDA(cudaMemsetAsync(g->scal, 0, sizeof(double) * S_COUNT, g->s));
     blobs_setup(g->blobs, g->d, g->h, nullptr, 0, g->s);
@@ -1672,6 +1710,7 @@ ibrd_status ibrd_vcycle(ibrd_grid g, const double* rhs, double* x, int zero) {
   return guarded(g, "ibrd_vcycle", [&]() {
     if (!rhs || !x || rhs == x) throw ArgError{IBRD_ERR_ARG, "null or aliased field"};
     vcycle<double>(g, rhs, x, zero != 0, g->alpha, 2, 2);
+    check_waits_if_not_capturing(g, "V-cycle");
     return IBRD_OK;
   });
 }
@@ -1680,6 +1719,7 @@ ibrd_status ibrd_vcycle_f32(ibrd_grid g, const float* rhs, float* x, int zero) {
   return guarded(g, "ibrd_vcycle_f32", [&]() {
     if (!rhs || !x || rhs == x) throw ArgError{IBRD_ERR_ARG, "null or aliased field"};
     vcycle<float>(g, rhs, x, zero != 0, g->alpha, 2, 2);
+    check_waits_if_not_capturing(g, "V-cycle");
     return IBRD_OK;
   });
 }
@@ -1745,6 +1785,7 @@ ibrd_status ibrd_solve_reaction(ibrd_grid g, const double* kappa, const double* 
     }
     if (info) info->history_len = hist.len;
     report(g, c, nullptr, kappa, info);
+    if (take_wait_flag(g)) R.st = IBRD_ERR_TIMEOUT;
     fill_info(info, R, g, t0);
     if (R.st != IBRD_OK) g->err = std::string("ibrd_solve_reaction: ") + ibrd_status_string(R.st);
     return R.st;
@@ -1821,6 +1862,7 @@ ibrd_status ibrd_solve_saddle(ibrd_grid g, const double* rhs, const double* f, d
     IBRD_CUDA(cudaMemcpyAsync(c, g->xs, sizeof(double) * nc, cudaMemcpyDeviceToDevice, g->s));
     IBRD_CUDA(cudaMemcpyAsync(lambda, g->xs + nc, sizeof(double) * N, cudaMemcpyDeviceToDevice, g->s));
     report(g, c, lambda, nullptr, info);
+    if (take_wait_flag(g)) R.st = IBRD_ERR_TIMEOUT;
     fill_info(info, R, g, t0);
     if (R.st != IBRD_OK) g->err = std::string("ibrd_solve_saddle: ") + ibrd_status_string(R.st);
     return R.st;
@@ -1901,8 +1943,10 @@ ibrd_status ibrd_autotune(ibrd_grid g, int precision, int retune, ibrd_tune_entr
 
 ibrd_status ibrd_tune_set(ibrd_grid g, int elem_bytes, int kind, int nx, int ny, int nz, int tx, int zc) {
   return guarded(g, "ibrd_tune_set", [&]() {
+    const bool rows = elem_bytes == 4 && kind == TUNE_SWEEP && tx == nx && rows_sweep_ok(Dims{nx, ny, nz});
     if ((elem_bytes != 4 && elem_bytes != 8) || (kind != TUNE_SWEEP && kind != TUNE_ZERO) || zc < 0 ||
-        (tx != 0 && tx != 32 && tx != 64) || (kind == TUNE_ZERO && tx != 0) || (elem_bytes == 8 && tx == 64))
+        (tx != 0 && tx != 32 && tx != 64 && !rows) || (kind == TUNE_ZERO && tx != 0) ||
+        (elem_bytes == 8 && tx == 64))
       throw ArgError{IBRD_ERR_ARG, "bad launch shape"};
     bool level = false;
     for (const Level& l : g->levels) level |= (l.d.nx == nx && l.d.ny == ny && l.d.nz == nz);
@@ -1915,6 +1959,14 @@ ibrd_status ibrd_tune_set(ibrd_grid g, int elem_bytes, int kind, int nx, int ny,
       slot = &g->tune.e.back().s;
     }
     *slot = SweepShape{tx, zc};
+    return IBRD_OK;
+  });
+}
+
+ibrd_status ibrd_set_wait_limit(ibrd_grid g, unsigned tries) {
+  return guarded(g, "ibrd_set_wait_limit", [&]() {
+    free_graphs(g);  // captured launches carry the old bound
+    g->tune.wait_limit = tries;
     return IBRD_OK;
   });
 }

@@ -100,8 +100,9 @@ int launch_rb_sweep(const T* xin, T* xout, const T* b, const double* bshift, Dim
 template <typename T>
 bool rb_sweep_fused_ok(Dims d);
 // Launch shape of a red-black sweep kernel picked by the autotuner: tile width
-// tx (cells, fused sweep only) and z-march depth zc (planes per CTA); 0 keeps
-// the built-in rule.
+// tx (cells, fused sweep only: 32 or 64 for the tiled kernel, nx for the
+// row-resident kernel on levels it serves) and z-march depth zc (planes per
+// CTA); 0 keeps the built-in rule (the row-resident kernel where it applies).
 struct SweepShape {
   int tx = 0;
   int zc = 0;
@@ -111,6 +112,20 @@ enum { TUNE_SWEEP = 0, TUNE_ZERO = 1 };
 // The tuned shape for kernel `kind` on elements of `elem` bytes and grid d in
 // the handle the calling thread is working for, or null.
 const SweepShape* tuned_sweep(int elem, int kind, Dims d);
+// Kernels with bounded device waits (the TMA ring of the row sweep) read the
+// calling handle's context: the device flag such a kernel sets when a wait
+// gives up (null outside a handle's call) and the number of tries a wait makes.
+constexpr unsigned kDefaultWaitLimit = 1u << 24;
+int* wait_error_flag();
+unsigned wait_limit();
+// Row-resident FP32 sweep (sweep_rows.cu): rows of 128 or 256 cells, ny a
+// multiple of 8, nz even; the same contract as the fused sweep of
+// launch_rb_sweep (out of place, per-CTA partial sums of the new x when part
+// holds enough entries; returns their count or 0). zc = planes per CTA.
+bool rows_sweep_ok(Dims d);
+int rows_sweep_default_zc(Dims d);
+int launch_rows_sweep(const float* xin, float* xout, const float* b, const double* bshift, Dims d, Stencil st,
+                      int zc, double* part, int part_cap, cudaStream_t s);
 // Levels handled by the single-CTA coarse V-cycle (shared-memory resident).
 constexpr int kMaxSmallLevels = 12;
 struct CoarseLevels {

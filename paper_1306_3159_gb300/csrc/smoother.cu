@@ -964,6 +964,21 @@ int launch_rb_sweep(const T* xin, T* xout, const T* b, const double* bshift, Dim
       return 0;
     }
   }
+  if constexpr (sizeof(T) == 4) {
+    // rows of 128 or 256 cells: the row-resident kernel unless a tiled shape
+    // was chosen for this level
+    if (!zero && rows_sweep_ok(d) && aligned16(xin) && aligned16(xout) && aligned16(b) && xin != xout &&
+        b != xout && wait_error_flag()) {
+      const SweepShape* tn = tuned_sweep(4, TUNE_SWEEP, d);
+      if (!tn || tn->tx == 0 || tn->tx == d.nx) {
+        const int zc = (tn && tn->zc >= 2) ? tn->zc : rows_sweep_default_zc(d);
+        prof_begin(c, s);
+        const int r = launch_rows_sweep(xin, xout, b, bshift, d, st, zc, part, part_cap, s);
+        prof_end(c, s, "rb_sweep_rows", 3.0 * sizeof(T) * d.n());
+        return r;
+      }
+    }
+  }
   if (rb_sweep_fused_ok<T>(d) && aligned16(xin) && aligned16(xout) && aligned16(b)) {
     // 64-wide tiles for FP32 (18 vectors per row), 32-wide for FP64
     const SweepShape* tn = tuned_sweep((int)sizeof(T), TUNE_SWEEP, d);

@@ -222,3 +222,69 @@ def test_autotune_report_and_parity(ibrd):
     assert all(r["cached"] == 1 for r in rep2) and len(rep2) == len(rep)
     ibrd.ibrd_tune_clear(g.handle)
     _vcycle_both(ibrd, g, 23)
+
+
+# Levels with rows of 128 or 256 cells (ny a multiple of 8, nz even) run the
+# row-resident FP32 sweep: (256, 16, 8) and (128, 8, 4) are both levels of the
+# first grid; (128, 8, 4) is a single 8-row tile whose halo rows wrap onto it,
+# with four planes in z.
+ROWS_CASES = [((256, 16, 8), 0.0), ((128, 8, 4), 0.0), ((256, 24, 16), 0.3), ((128, 40, 16), 0.0)]
+
+
+def _levels(dims):
+    out = [tuple(dims)]
+    while all(v % 2 == 0 and v >= 4 for v in out[-1]):
+        out.append(tuple(v // 2 for v in out[-1]))
+    return out
+
+
+@pytest.mark.parametrize("dims,alpha", ROWS_CASES)
+@pytest.mark.parametrize("zc", [0, 2, 3, 5, 64])
+def test_vcycle_f32_row_kernel(ibrd, dims, alpha, zc):
+    """The row-resident FP32 sweep (one warp per x-row, plane ring fed by TMA
+    tensor-map boxes, bounded mbarrier waits) inside the FP32 V-cycle gives the
+    oracle's V-cycle within FP32 rounding, for the built-in z-march depth and
+    depths with ragged last chunks, down to two planes per CTA; singular
+    (alpha = 0: the kernel's per-CTA sums feed the mean projection) and
+    shifted."""
+    import torch
+    nx, ny, nz = dims
+    rng = np.random.default_rng(31 + zc)
+    b = rng.standard_normal((nz, ny, nx)).astype(np.float32)
+    g = ibrd.Grid(*dims, alpha=alpha)
+    if zc:
+        for (lx, ly, lz) in _levels(dims):
+            if lx in (128, 256) and ly % 8 == 0 and lz % 2 == 0 and lz >= 4:
+                ibrd.ibrd_tune_set(g.handle, 4, 0, lx, ly, lz, lx, zc)
+    x = g.vcycle_f32(torch.from_numpy(b).cuda()).cpu().numpy().astype(np.float64)
+    want = mg.vcycle(b.astype(np.float64), 1.0, 1.0, alpha, exact_cells=32768, exact_side=64)
+    assert rel_max(x, want) < 2e-5
+
+
+def test_bounded_wait_gives_up_with_timeout_status(ibrd):
+    """A bound of zero polls makes every plane wait of the row sweep give up:
+    each CTA drains its copies in flight and stops, and the FP32 V-cycle and a
+    solve in the refinement mode report IBRD_ERR_TIMEOUT instead of hanging or
+    returning a wrong answer as a success. With the bound restored the same
+    handle solves to the oracle's solution."""
+    import torch
+    from oracle import direct
+    from synthetic import rsa_positions
+    dims = (128, 16, 8)
+    q = rsa_positions(4, dims, 1.0, 4.0, 41)
+    gsrc = np.ones((8, 16, 128))
+    g = ibrd.Grid(*dims)
+    g.set_blobs(dev(q))
+    b = torch.from_numpy(np.random.default_rng(42).standard_normal((8, 16, 128)).astype(np.float32)).cuda()
+    ibrd.ibrd_set_wait_limit(g.handle, 0)
+    with pytest.raises(ibrd.IbrdError) as e:
+        g.vcycle_f32(b)
+    assert e.value.status == 7
+    with pytest.raises(ibrd.IbrdError) as e:
+        g.solve_saddle(dev(gsrc), tol=1e-10, precision=ibrd.IBRD_MIXED_REFINE, max_iter=50)
+    assert e.value.status == 7
+    ibrd.ibrd_set_wait_limit(g.handle, 1 << 24)
+    c, lam, info = g.solve_saddle(dev(gsrc), tol=1e-10, precision=ibrd.IBRD_MIXED_REFINE, max_iter=400)
+    c_ref, lam_ref, _ = direct.solve_saddle(q, gsrc, 1.0, 1.0, 0.0)
+    assert rel_max(host(c), c_ref) < 1e-8 and rel_max(host(lam), lam_ref) < 1e-8
+    torch.cuda.synchronize()
