@@ -21,10 +21,13 @@
 //   the innermost coordinate holds).
 // * Each thread keeps its row of planes p-2 .. p+1 in registers (the
 //   z-neighbours); only the y-neighbour rows are read from shared memory: the
-//   old rows for the red update of plane p, and the red-updated rows (a
-//   separate double-buffered array, so no row is read while it is written)
-//   for the black update of plane p-1 in the same phase. One barrier per
-//   plane.
+//   old rows for the red update of plane p, and the red cells after that
+//   update (a separate double-buffered array holding two values per 4-cell
+//   group, so no row is read while it is written) for the black update of
+//   plane p-1 in the same step. One barrier per plane; thread 0 alone waits
+//   on the TMA barriers, one plane ahead.
+// * Odd z-chunks march downwards, so that adjacent chunks meet at their
+//   common halo planes at the same time (L2 hits, not DRAM re-reads).
 //
 // Every mbarrier wait is bounded: a wait that gives up sets *err, drains the
 // copies still in flight (again with a bound) and ends the CTA; the host
@@ -82,23 +85,35 @@ __device__ __forceinline__ int wrapm(int i, int n) {
 // per lane: active cells are e = a, a + 2 of every group (e = x mod 4). Their
 // x-neighbours are inactive cells (unchanged by this update): inside the
 // group, or the previous lane's last cell (a = 0) / the next lane's first
-// cell (a = 1), with lane 0 / lane 31 taking it from the adjacent slot. u and
-// dn are the rows j - 1 and j + 1, zm and zp the planes k - 1 and k + 1, bb
-// the right-hand side with its shift removed.
-template <int NS>
-__device__ __forceinline__ void rb_row(float4 (&v)[NS], const float4* u, const float4* dn, const float4 (&zm)[NS],
+// cell (a = 1), with lane 0 / lane 31 taking it from the adjacent slot. zm and
+// zp are the planes k - 1 and k + 1, bb the right-hand side with its shift
+// removed. The y-neighbours (rows j - 1, j + 1) are full rows (u, dn: float4
+// per group, the active cells' values at components a, a + 2) or, PACKED,
+// the neighbour rows' red-updated cells only (float2 per group: exactly the
+// values at this row's black positions).
+template <int NS, bool PACKED>
+__device__ __forceinline__ void rb_row(float4 (&v)[NS], const void* u, const void* dn, const float4 (&zm)[NS],
                                        const float4 (&zp)[NS], const float4 (&bb)[NS], int a, float off, float inv,
                                        int lane) {
   float t[NS];
+  auto nb = [&](const void* row, int s, int k) -> float {  // k-th active cell's neighbour in `row`
+    if constexpr (PACKED) {
+      const float2 q = reinterpret_cast<const float2*>(row)[32 * s];
+      return k == 0 ? q.x : q.y;
+    } else {
+      const float4 q = reinterpret_cast<const float4*>(row)[32 * s];
+      return a == 0 ? (k == 0 ? q.x : q.z) : (k == 0 ? q.y : q.w);
+    }
+  };
   if (a == 0) {
 #pragma unroll
     for (int s = 0; s < NS; ++s) t[s] = __shfl_sync(0xffffffffu, v[s].w, (lane + 31) & 31);
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
       const float L = lane == 0 ? t[(s + NS - 1) % NS] : t[s];
-      const float4 uu = u[32 * s], dd = dn[32 * s];
-      v[s].x = (bb[s].x + off * (((L + v[s].y) + (uu.x + dd.x)) + (zm[s].x + zp[s].x))) * inv;
-      v[s].z = (bb[s].z + off * (((v[s].y + v[s].w) + (uu.z + dd.z)) + (zm[s].z + zp[s].z))) * inv;
+      const float u0 = nb(u, s, 0), d0 = nb(dn, s, 0), u1 = nb(u, s, 1), d1 = nb(dn, s, 1);
+      v[s].x = (bb[s].x + off * (((L + v[s].y) + (u0 + d0)) + (zm[s].x + zp[s].x))) * inv;
+      v[s].z = (bb[s].z + off * (((v[s].y + v[s].w) + (u1 + d1)) + (zm[s].z + zp[s].z))) * inv;
     }
   } else {
 #pragma unroll
@@ -106,9 +121,9 @@ __device__ __forceinline__ void rb_row(float4 (&v)[NS], const float4* u, const f
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
       const float R = lane == 31 ? t[(s + 1) % NS] : t[s];
-      const float4 uu = u[32 * s], dd = dn[32 * s];
-      v[s].y = (bb[s].y + off * (((v[s].x + v[s].z) + (uu.y + dd.y)) + (zm[s].y + zp[s].y))) * inv;
-      v[s].w = (bb[s].w + off * (((v[s].z + R) + (uu.w + dd.w)) + (zm[s].w + zp[s].w))) * inv;
+      const float u0 = nb(u, s, 0), d0 = nb(dn, s, 0), u1 = nb(u, s, 1), d1 = nb(dn, s, 1);
+      v[s].y = (bb[s].y + off * (((v[s].x + v[s].z) + (u0 + d0)) + (zm[s].y + zp[s].y))) * inv;
+      v[s].w = (bb[s].w + off * (((v[s].z + R) + (u1 + d1)) + (zm[s].w + zp[s].w))) * inv;
     }
   }
 }
@@ -116,8 +131,17 @@ __device__ __forceinline__ void rb_row(float4 (&v)[NS], const float4* u, const f
 // Grid: (ny / TY, z-chunks). Block: (TY + 2) warps; warp w owns row
 // y0 - 1 + w (w = 0 and w = TY + 1 are the halo rows: red cells only).
 // Shared memory: XS[R][TY + 4][nx] (old x, rows y0-2 .. y0+TY+1),
-// BS[R][TY + 2][nx] (b, rows y0-1 .. y0+TY), RS[2][TY + 2][nx] (rows after the
-// red update), R mbarriers.
+// BS[R][TY + 2][nx] (b, rows y0-1 .. y0+TY), RS[2][TY + 2][nx / 2] (the red
+// cells of each row after the red update, two per 4-cell group), R mbarriers.
+//
+// March order: chunk c covers planes [k0, k1) and visits planes k0-2 .. k1+1
+// upwards when c is even and k1+1 .. k0-2 downwards when c is odd, so that
+// neighbouring chunks start (or end) at their common boundary at the same
+// time and the halo planes they share come from L2. The Gauss-Seidel result
+// does not depend on the order in which the cells of one colour are updated,
+// so both directions give the same sweep. March index i = 0 .. zc + 3 names
+// plane mp(i); step i updates the red cells of mp(i) and the black cells of
+// mp(i - 1) (when that plane is in the chunk) and stores mp(i - 1).
 template <int NS>
 __global__ void __launch_bounds__((kRowsTY + 2) * 32, 2)
     k_rbgs_rows(const __grid_constant__ CUtensorMap mx_tile, const __grid_constant__ CUtensorMap mx_pair,
@@ -125,23 +149,25 @@ __global__ void __launch_bounds__((kRowsTY + 2) * 32, 2)
                 float* __restrict__ xout, const double* __restrict__ bshift, int ny, int nz, int zc, float inv,
                 float off, double* __restrict__ part, int* __restrict__ err, unsigned wait_limit) {
   constexpr int TY = kRowsTY, R = kRowsRing, NX = 128 * NS;
-  constexpr int XROWS = TY + 4, BROWS = TY + 2, RROWS = TY + 2;
+  constexpr int XROWS = TY + 4, BROWS = TY + 2, RROWS = TY + 2, RW = NX / 2;
   constexpr unsigned XBYTES = XROWS * NX * 4, BBYTES = BROWS * NX * 4;
   extern __shared__ __align__(1024) unsigned char sm_raw[];
   float* XS = reinterpret_cast<float*>(sm_raw);
   float* BS = XS + R * XROWS * NX;
   float* RS = BS + R * BROWS * NX;
-  unsigned long long* bars = reinterpret_cast<unsigned long long*>(RS + 2 * RROWS * NX);
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(RS + 2 * RROWS * RW);
 
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int y0 = blockIdx.x * TY;
   const int k0 = blockIdx.y * zc, k1 = min(k0 + zc, nz);
+  const bool down = blockIdx.y & 1;
   const size_t plane = (size_t)NX * ny;
   const float sh = bshift ? (float)(*bshift) : 0.f;
   const bool interior = w >= 1 && w <= TY;
   // this warp's row: parity of y (ny is even, so the wrap keeps it)
   const int ypar = (y0 - 1 + w) & 1;
-  const int q0 = k0 - 2;  // first plane in the ring
+  const int last = k1 - k0 + 3;  // march index of the last plane
+  auto mp = [&](int i) { return down ? k1 + 1 - i : k0 - 2 + i; };
 
   if (tid == 0) {
     for (int s = 0; s < R; ++s) mbar_init(smem_u32(bars + s), 1);
@@ -149,11 +175,11 @@ __global__ void __launch_bounds__((kRowsTY + 2) * 32, 2)
   }
   __syncthreads();
 
-  // copies of plane q (x rows y0-2 .. y0+TY+1, b rows y0-1 .. y0+TY) into its slot
-  auto issue = [&](int q) {
-    const int s = (q - q0) % R;
+  // copies of march plane i (x rows y0-2 .. y0+TY+1, b rows y0-1 .. y0+TY) into its slot
+  auto issue = [&](int i) {
+    const int s = i % R;
     const unsigned bar = smem_u32(bars + s);
-    const int z = wrapm(q, nz);
+    const int z = wrapm(mp(i), nz);
     float* xs = XS + s * XROWS * NX;
     float* bs = BS + s * BROWS * NX;
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
@@ -165,89 +191,96 @@ __global__ void __launch_bounds__((kRowsTY + 2) * 32, 2)
     tma_load3(smem_u32(bs + NX), &mb_tile, 0, y0, z, bar);
     tma_load3(smem_u32(bs + (TY + 1) * NX), &mb_one, 0, wrapm(y0 + TY, ny), z, bar);
   };
-  auto wait_plane = [&](int q, unsigned limit) {
-    const int u = q - q0;
-    return mbar_wait(smem_u32(bars + (u % R)), (unsigned)((u / R) & 1), limit);
+  // thread 0 alone polls the barriers; the CTA barrier that follows every
+  // wait publishes the landed plane to the other threads
+  auto wait_plane = [&](int i, unsigned limit) {
+    return mbar_wait(smem_u32(bars + (i % R)), (unsigned)((i / R) & 1), limit);
   };
-  auto xrow = [&](int q, int r) { return reinterpret_cast<const float4*>(XS + ((q - q0) % R) * XROWS * NX + r * NX); };
-  auto brow = [&](int q, int r) { return reinterpret_cast<const float4*>(BS + ((q - q0) % R) * BROWS * NX + r * NX); };
-  auto rrow = [&](int q, int r) { return reinterpret_cast<float4*>(RS + (q & 1) * RROWS * NX + r * NX); };
+  auto xrow = [&](int i, int r) { return reinterpret_cast<const float4*>(XS + (i % R) * XROWS * NX + r * NX); };
+  auto brow = [&](int i, int r) { return reinterpret_cast<const float4*>(BS + (i % R) * BROWS * NX + r * NX); };
+  auto rrow = [&](int i, int r) { return reinterpret_cast<float2*>(RS + (i & 1) * RROWS * RW + r * RW); };
 
-  const int last = k1 + 1;  // last plane loaded
-  if (tid == 0)
-    for (int q = q0; q < q0 + R && q <= last; ++q) issue(q);
-  int issued = min(q0 + R - 1, last);
+  bool ok = true;
+  if (tid == 0) {
+    for (int i = 0; i < R && i <= last; ++i) issue(i);
+    ok = wait_plane(0, wait_limit) && wait_plane(1, wait_limit) && wait_plane(2, wait_limit);
+  }
+  int issued = min(R - 1, last);
+  ok = !__syncthreads_or(!ok);
+  // march planes up to `done` have landed (the same value in every thread:
+  // it only advances after a barrier that every thread passed)
+  int done = ok ? 2 : -1;
 
   float4 A[NS], B[NS], C[NS], D[NS], BX[NS], BY[NS];
-  bool ok = wait_plane(q0, wait_limit) && wait_plane(q0 + 1, wait_limit);
   if (ok) {
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-      B[s] = xrow(q0, w + 1)[lane + 32 * s];
-      C[s] = xrow(q0 + 1, w + 1)[lane + 32 * s];
+      B[s] = xrow(0, w + 1)[lane + 32 * s];
+      C[s] = xrow(1, w + 1)[lane + 32 * s];
     }
   }
-  ok = !__syncthreads_or(!ok);
-  // planes up to `done` have landed (the same value in every thread: it only
-  // advances after a barrier all threads passed with their waits met)
-  int done = ok ? q0 + 1 : q0 - 1;
+  __syncthreads();  // step 1 refills plane 0's slot
   float acc = 0.f, comp = 0.f;  // Kahan sum of the new x (tile rows)
 
-  // Phase p: red cells of plane p (all warps), black cells of plane p - 1
-  // (tile warps, p - 1 >= k0), store of plane p - 1. pm2 .. pp1 are this
-  // thread's row of planes p - 2 .. p + 1; bm1 / b0 its b of planes p - 1 / p.
-  auto phase = [&](float4 (&pm2)[NS], float4 (&pm1)[NS], float4 (&p0)[NS], float4 (&pp1)[NS],
-                   float4 (&bm1)[NS], float4 (&b0)[NS], int p) -> bool {
-    if (p > k1 || !ok) return false;
-    // plane p + 3 takes the slot of plane p - 1, last read before the barrier
-    // that ended phase p - 1
-    if (tid == 0 && p + 3 <= last) issue(p + 3);
-    if (p + 3 <= last) issued = p + 3;
-    bool good = wait_plane(p + 1, wait_limit);
-    if (good) {
+  // Step i: pm2 .. pp1 are this thread's row of march planes i - 2 .. i + 1,
+  // bm1 / b0 its b of march planes i - 1 / i. Planes i and i + 1 have landed.
+  auto step = [&](float4 (&pm2)[NS], float4 (&pm1)[NS], float4 (&p0)[NS], float4 (&pp1)[NS], float4 (&bm1)[NS],
+                  float4 (&b0)[NS], int i) -> bool {
+    if (i > last - 1 || !ok) return false;
+    // plane i + 3 takes the slot of plane i - 1, last read before the barrier
+    // that ended step i - 1
+    if (tid == 0 && i + 3 <= last) issue(i + 3);
+    if (i + 3 <= last) issued = i + 3;
+    const int z = mp(i);
 #pragma unroll
-      for (int s = 0; s < NS; ++s) {
-        pp1[s] = xrow(p + 1, w + 1)[lane + 32 * s];
-        float4 t = brow(p, w)[lane + 32 * s];
-        t.x -= sh, t.y -= sh, t.z -= sh, t.w -= sh;
-        b0[s] = t;
-      }
-      // red cells of plane p from the old rows y - 1, y + 1 of plane p
-      rb_row<NS>(p0, xrow(p, w) + lane, xrow(p, w + 2) + lane, pm1, pp1, b0, (ypar + p) & 1, off, inv, lane);
-      float4* rr = rrow(p, w);
+    for (int s = 0; s < NS; ++s) {
+      pp1[s] = xrow(i + 1, w + 1)[lane + 32 * s];
+      float4 t = brow(i, w)[lane + 32 * s];
+      t.x -= sh, t.y -= sh, t.z -= sh, t.w -= sh;
+      b0[s] = t;
+    }
+    const int a = (ypar + z) & 1;
+    // red cells of plane mp(i) from the old rows y - 1, y + 1 of that plane
+    rb_row<NS, false>(p0, xrow(i, w) + lane, xrow(i, w + 2) + lane, pm1, pp1, b0, a, off, inv, lane);
+    float2* rr = rrow(i, w);
 #pragma unroll
-      for (int s = 0; s < NS; ++s) rr[lane + 32 * s] = p0[s];
-      if (interior && p - 1 >= k0) {
-        // black cells of plane p - 1 from the red-updated rows of plane p - 1
-        rb_row<NS>(pm1, rrow(p - 1, w - 1) + lane, rrow(p - 1, w + 1) + lane, pm2, p0, bm1, (ypar + p) & 1, off,
-                   inv, lane);
-        float4* dst = reinterpret_cast<float4*>(xout + (size_t)(p - 1) * plane + (size_t)(y0 - 1 + w) * NX);
+    for (int s = 0; s < NS; ++s)
+      rr[lane + 32 * s] = a == 0 ? make_float2(p0[s].x, p0[s].z) : make_float2(p0[s].y, p0[s].w);
+    if (interior && i >= 3) {
+      // black cells of plane mp(i - 1) from the red cells of its rows y - 1, y + 1
+      rb_row<NS, true>(pm1, rrow(i - 1, w - 1) + lane, rrow(i - 1, w + 1) + lane, pm2, p0, bm1, a, off, inv,
+                       lane);
+      float4* dst = reinterpret_cast<float4*>(xout + (size_t)mp(i - 1) * plane + (size_t)(y0 - 1 + w) * NX);
 #pragma unroll
-        for (int s = 0; s < NS; ++s) dst[lane + 32 * s] = pm1[s];
-        if (part) {
-          float t = 0.f;
+      for (int s = 0; s < NS; ++s) dst[lane + 32 * s] = pm1[s];
+      if (part) {
+        float t = 0.f;
 #pragma unroll
-          for (int s = 0; s < NS; ++s) t += (pm1[s].x + pm1[s].y) + (pm1[s].z + pm1[s].w);
-          const float yk = t - comp, tk = acc + yk;
-          comp = (tk - acc) - yk;
-          acc = tk;
-        }
+        for (int s = 0; s < NS; ++s) t += (pm1[s].x + pm1[s].y) + (pm1[s].z + pm1[s].w);
+        const float yk = t - comp, tk = acc + yk;
+        comp = (tk - acc) - yk;
+        acc = tk;
       }
     }
+    bool good = true;
+    if (tid == 0 && i + 2 <= last) good = wait_plane(i + 2, wait_limit);
     ok = !__syncthreads_or(!good);
-    if (ok) done = p + 1;
+    if (ok) done = i + 2;
     return ok;
   };
-  for (int p = k0 - 1; p <= k1; p += 4) {
-    if (!phase(A, B, C, D, BX, BY, p)) break;
-    if (!phase(B, C, D, A, BY, BX, p + 1)) break;
-    if (!phase(C, D, A, B, BX, BY, p + 2)) break;
-    if (!phase(D, A, B, C, BY, BX, p + 3)) break;
+  for (int i = 1; i < last; i += 4) {
+    if (!step(A, B, C, D, BX, BY, i)) break;
+    if (!step(B, C, D, A, BY, BX, i + 1)) break;
+    if (!step(C, D, A, B, BX, BY, i + 2)) break;
+    if (!step(D, A, B, C, BY, BX, i + 3)) break;
   }
   if (!ok) {
     // a plane wait gave up: drain the copies still in flight, report, stop
-    for (int q = done + 1; q <= issued; ++q) wait_plane(q, kDrainLimit);
-    if (tid == 0) atomicOr(err, 1);
+    if (tid == 0) {
+      for (int i = done + 1; i <= issued; ++i) wait_plane(i, kDrainLimit);
+      atomicOr(err, 1);
+    }
+    __syncthreads();
     return;
   }
   if (part) {
@@ -298,7 +331,7 @@ CUtensorMap field_map(const float* f, Dims d, int rows) {
 template <int NS>
 constexpr size_t rows_smem() {
   constexpr int NX = 128 * NS;
-  return sizeof(float) * (size_t)NX * (kRowsRing * (kRowsTY + 4) + kRowsRing * (kRowsTY + 2) + 2 * (kRowsTY + 2)) +
+  return sizeof(float) * (size_t)NX * (kRowsRing * (kRowsTY + 4) + kRowsRing * (kRowsTY + 2) + (kRowsTY + 2)) +
          8 * kRowsRing;
 }
 
