@@ -188,11 +188,16 @@ ibrd_status ibrd_vcycle(ibrd_grid g, const double* rhs, double* x, int zero_init
    start-up, code inside another library that may only use the memory it is
    handed, or a process whose device memory already belongs to a framework's
    caching allocator. This entry point needs no grid handle and allocates
-   nothing: the V-cycle's workspaces come from one 16 MiB scratch array that
-   the library holds in static device memory on every GPU that loads it, until
-   the process exits. That limits the grid to about 1.4 million cells (96^3 and
-   112^3 fit; 128^3 does not); larger grids return IBRD_ERR_ARG without any
-   GPU work. The grid, h, chi and alpha are passed directly; rhs and x are
+   nothing: the V-cycle's workspaces come from one 16 MiB scratch array in
+   static device memory, which a GPU holds from the first call on it until the
+   process exits. Under CUDA's default lazy module loading the array is
+   reserved on a device by that first call, not when the library is loaded: a
+   caller whose memory budget is fixed at start-up must make one call on each
+   device before it locks the budget (or set CUDA_MODULE_LOADING=EAGER so the
+   array is reserved when the library's module is loaded). If that
+   reservation fails the call returns IBRD_ERR_OOM. The size limits the grid
+   to about 1.4 million cells (96^3 and 112^3 fit; 120^3 and 128^3 do not);
+   larger grids return IBRD_ERR_ARG without any GPU work. The grid, h, chi and alpha are passed directly; rhs and x are
    caller-owned device arrays as for ibrd_vcycle (rhs != x), and the result is
    the one ibrd_vcycle computes. stream is a cudaStream_t (NULL = legacy
    default stream); the call only enqueues work on it and does not synchronize.
@@ -201,7 +206,10 @@ ibrd_status ibrd_vcycle(ibrd_grid g, const double* rhs, double* x, int zero_init
    before any stream capture. Every call uses the same scratch and leaves its
    contents behind (nothing in it is read before the call writes it), so calls
    whose GPU work overlaps (different streams or host threads, same device)
-   race on it: serialize them. Returns IBRD_ERR_CUDA if a CUDA call fails. */
+   race on it: serialize them. The scratch address is cached per device for
+   the process, so do not call this entry point on a device after a
+   cudaDeviceReset of it. Returns IBRD_ERR_CUDA if a CUDA call fails
+   (IBRD_ERR_OOM for an allocation failure). */
 ibrd_status ibrd_vcycle_noalloc(int nx, int ny, int nz, double h, double chi, double alpha, const double* rhs,
                                 double* x, int zero_initial_guess, void* stream);
 

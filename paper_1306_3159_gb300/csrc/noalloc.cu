@@ -16,6 +16,7 @@
 // definition); only where the scratch lives differs.
 #include <cmath>
 #include <mutex>
+#include <new>
 #include <vector>
 
 #include "internal.h"
@@ -36,7 +37,11 @@ std::mutex g_scratch_mu;
 void* g_scratch_addr[kMaxDevices] = {};
 
 // Device address of the scratch on the current device, looked up once per
-// device (with that device current) on the first call that runs there.
+// device (with that device current) on the first call that runs there. With
+// CUDA's lazy module loading (the default) that lookup is also what loads
+// this file's module on the device and so reserves the array there; the
+// address is cached for the process, so a cudaDeviceReset, which unloads the
+// module, makes later calls on that device invalid.
 cudaError_t scratch_address(void** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
@@ -172,20 +177,31 @@ void na_level(const NaPlan& P, double* S, int l, const double* b, const double* 
 
 using namespace ibrd;
 
+namespace {
+ibrd_status cuda_status(cudaError_t e) {
+  cudaGetLastError();
+  return e == cudaErrorMemoryAllocation ? IBRD_ERR_OOM : IBRD_ERR_CUDA;
+}
+}  // namespace
+
 extern "C" ibrd_status ibrd_vcycle_noalloc(int nx, int ny, int nz, double h, double chi, double alpha,
                                            const double* rhs, double* x, int zero_initial_guess, void* stream) {
   if (nx < 4 || ny < 4 || nz < 4 || !(h > 0.0) || !(chi > 0.0) || !(alpha >= 0.0) || !std::isfinite(h) ||
       !std::isfinite(chi) || !std::isfinite(alpha))
     return IBRD_ERR_ARG;
+  // no exception leaves this function: host-side failures (the plan's small
+  // host vectors) and CUDA errors become status codes
+  try {
   NaPlan P;
   if (!make_plan(nx, ny, nz, h, P)) return IBRD_ERR_ARG;
   if (P.total * sizeof(double) > kNoAllocScratchBytes) return IBRD_ERR_ARG;  // grid too large for the scratch
   if (!rhs || !x || rhs == x) return IBRD_ERR_ARG;
   void* base = nullptr;
-  if (scratch_address(&base) != cudaSuccess) return IBRD_ERR_CUDA;
+  const cudaError_t ea = scratch_address(&base);
+  if (ea != cudaSuccess) return cuda_status(ea);
   double* S = static_cast<double*>(base);
   const cudaStream_t s = (cudaStream_t)stream;
-  try {
+  {
     // Nothing in the scratch is read before this call writes it (the coarse
     // table, the level fields, partials and scalars are all produced here),
     // so no part of it needs clearing.
@@ -202,8 +218,12 @@ extern "C" ibrd_status ibrd_vcycle_noalloc(int nx, int ny, int nz, double h, dou
       launch_sum<double>(x, n, S + P.partial, S + P.scal + 1, 1.0 / (double)n, s);
       launch_sub_scalar<double>(x, n, S + P.scal + 1, s);
     }
-  } catch (const CudaError&) {
-    cudaGetLastError();
+  }
+  } catch (const CudaError& e) {
+    return cuda_status(e.code);
+  } catch (const std::bad_alloc&) {
+    return IBRD_ERR_OOM;
+  } catch (...) {
     return IBRD_ERR_CUDA;
   }
   return IBRD_OK;

@@ -42,7 +42,8 @@ def _noalloc(lib, dims, h, chi, alpha, b, x, zero):
 @pytest.mark.parametrize("dims,h,chi,alpha,zero", [((64, 64, 64), 1.0, 1.0, 0.0, True),
                                                    ((32, 48, 16), 0.7, 1.3, 0.25, True),
                                                    ((64, 32, 32), 1.0, 1.0, 0.0, False),
-                                                   ((16, 16, 16), 1.0, 2.0, 0.0, True)])
+                                                   ((16, 16, 16), 1.0, 2.0, 0.0, True),
+                                                   ((112, 112, 112), 1.0, 1.0, 0.0, True)])
 def test_noalloc_vcycle_matches_vcycle(lib, dims, h, chi, alpha, zero):
     import paper_1306_3159_gb300 as p
     nx, ny, nz = dims
@@ -60,7 +61,9 @@ def test_noalloc_vcycle_matches_vcycle(lib, dims, h, chi, alpha, zero):
         assert rel_max(host(x), want) < 1e-12
 
 
-def test_noalloc_rejects_grids_beyond_the_scratch(lib):
-    # 128^3 needs more than the 16 MiB scratch: IBRD_ERR_ARG before any GPU work
-    st = lib.ibrd_vcycle_noalloc(128, 128, 128, 1.0, 1.0, 0.0, None, None, 1, None)
+@pytest.mark.parametrize("dims", [(128, 128, 128), (120, 120, 120), (128, 128, 96)])
+def test_noalloc_rejects_grids_beyond_the_scratch(lib, dims):
+    # 112^3 uses about 15.3 MiB of the 16 MiB scratch (its largest case above);
+    # these need more: IBRD_ERR_ARG before any GPU work
+    st = lib.ibrd_vcycle_noalloc(*dims, 1.0, 1.0, 0.0, None, None, 1, None)
     assert st == 1
