@@ -685,9 +685,9 @@ def run_kernel_case_fp64(args):
 
 
 def run_kernel_case(args):
-    """FP32 V-cycles on a 256^3 field (about 0.3 GB on the device) with a
-    profiler range around one V-cycle: the small case for full ncu captures of
-    the multigrid kernels."""
+    """FP32 V-cycles (nu = 1/1, as in the chosen solves) on a 256^3 field
+    (about 0.3 GB on the device) with a profiler range around one V-cycle: the
+    small case for full ncu captures of the multigrid kernels."""
     import torch
     from paper_1306_3159_gb300 import build as pbuild
     pbuild.build()
@@ -703,11 +703,12 @@ def run_kernel_case(args):
     b = torch.randn((n, n, n), dtype=torch.float32, device="cuda", generator=torch.Generator("cuda").manual_seed(1))
     b -= b.mean()
     x = torch.zeros_like(b)
+    # nu = 1/1, the sweep counts of the chosen solves' V-cycles
     for _ in range(3):
-        grid.vcycle_f32(b, x)
+        grid.vcycle_f32(b, x, nu1=1, nu2=1)
     torch.cuda.synchronize()
     torch.cuda.profiler.start()
-    grid.vcycle_f32(b, x)
+    grid.vcycle_f32(b, x, nu1=1, nu2=1)
     torch.cuda.synchronize()
     torch.cuda.profiler.stop()
     log("[bench] kernel case done")

@@ -220,6 +220,12 @@ ibrd_status ibrd_vcycle_noalloc(int nx, int ny, int nz, double h, double chi, do
    level it coarsens like the FP64 V-cycle. rhs, x: FP32 device fields. */
 ibrd_status ibrd_vcycle_f32(ibrd_grid g, const float* rhs, float* x, int zero_initial_guess);
 
+/* ibrd_vcycle_f32 with nu1 pre- and nu2 post-smoothing sweeps (0 to 16 each;
+   ibrd_vcycle_f32 uses 2 and 2): the V-cycle the mixed-precision solves run
+   with the ibrd_solve_opts sweep counts. Same arguments and errors. */
+ibrd_status ibrd_vcycle_f32_sweeps(ibrd_grid g, const float* rhs, float* x, int zero_initial_guess, int nu1,
+                                   int nu2);
+
 /* grid_out (+)= S lambda, (S lambda)_k = h^-3 sum_i phi(q_i - r_k) lambda_i
    (Sec. III.A). accumulate = 0 overwrites grid_out (zero away from blobs).
    Deterministic: each cell sums its blobs in increasing blob index. */

@@ -21,7 +21,7 @@ from ._abi import (
     ibrd_grid_create, ibrd_grid_destroy, ibrd_interp, ibrd_last_error, ibrd_profile_enable, ibrd_profile_read,
     ibrd_set_blobs, ibrd_solve_many, ibrd_solve_reaction, ibrd_solve_reaction_batch, ibrd_solve_saddle,
     ibrd_solve_saddle_batch, ibrd_spread, ibrd_set_wait_limit, ibrd_tune_clear, ibrd_tune_set, ibrd_vcycle,
-    ibrd_vcycle_f32,
+    ibrd_vcycle_f32, ibrd_vcycle_f32_sweeps,
     load_library)
 
 __all__ = [
@@ -32,5 +32,5 @@ __all__ = [
     "ibrd_interp", "ibrd_last_error", "ibrd_profile_enable", "ibrd_profile_read", "ibrd_set_blobs",
     "ibrd_solve_many", "ibrd_solve_reaction", "ibrd_solve_reaction_batch", "ibrd_solve_saddle",
     "ibrd_solve_saddle_batch", "ibrd_spread", "ibrd_set_wait_limit", "ibrd_tune_clear", "ibrd_tune_set", "ibrd_vcycle",
-    "ibrd_vcycle_f32", "load_library",
+    "ibrd_vcycle_f32", "ibrd_vcycle_f32_sweeps", "load_library",
 ]

@@ -21,7 +21,7 @@ STATUS = {0: "IBRD_OK", 1: "IBRD_ERR_ARG", 2: "IBRD_ERR_CUDA", 3: "IBRD_ERR_OOM"
 
 # Every entry point declared in include/ibrd.h.
 EXPORTED = ["ibrd_default_opts", "ibrd_grid_create", "ibrd_grid_destroy", "ibrd_set_blobs", "ibrd_apply_L",
-            "ibrd_vcycle", "ibrd_vcycle_f32", "ibrd_vcycle_noalloc", "ibrd_spread", "ibrd_interp", "ibrd_solve_reaction", "ibrd_solve_saddle",
+            "ibrd_vcycle", "ibrd_vcycle_f32", "ibrd_vcycle_f32_sweeps", "ibrd_vcycle_noalloc", "ibrd_spread", "ibrd_interp", "ibrd_solve_reaction", "ibrd_solve_saddle",
             "ibrd_solve_reaction_batch", "ibrd_solve_saddle_batch", "ibrd_solve_many", "ibrd_autotune", "ibrd_tune_set",
             "ibrd_tune_clear", "ibrd_set_wait_limit", "ibrd_gnn_num_params", "ibrd_gnn_create", "ibrd_gnn_destroy", "ibrd_gnn_last_error",
             "ibrd_gnn_set_params", "ibrd_gnn_get_params", "ibrd_gnn_init_params", "ibrd_gnn_neighbours", "ibrd_gnn_forward",
@@ -106,6 +106,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ibrd_vcycle.restype = i
     lib.ibrd_vcycle_f32.argtypes = [vp, vp, vp, i]
     lib.ibrd_vcycle_f32.restype = i
+    lib.ibrd_vcycle_f32_sweeps.argtypes = [vp, vp, vp, i, i, i]
+    lib.ibrd_vcycle_f32_sweeps.restype = i
     lib.ibrd_spread.argtypes = [vp, vp, vp, i]
     lib.ibrd_spread.restype = i
     lib.ibrd_interp.argtypes = [vp, vp, vp]
@@ -236,6 +238,11 @@ def ibrd_vcycle(g, rhs, x, zero_initial_guess=True):
 def ibrd_vcycle_f32(g, rhs, x, zero_initial_guess=True):
     _check(g, load_library().ibrd_vcycle_f32(g, _ptr(rhs, "float32"), _ptr(x, "float32"),
                                              int(bool(zero_initial_guess))))
+
+def ibrd_vcycle_f32_sweeps(g, rhs, x, zero_initial_guess=True, nu1=2, nu2=2):
+    """FP32 V-cycle with nu1 / nu2 smoothing sweeps (the solves' counts)."""
+    _check(g, load_library().ibrd_vcycle_f32_sweeps(g, _ptr(rhs, "float32"), _ptr(x, "float32"),
+                                                    int(bool(zero_initial_guess)), int(nu1), int(nu2)))
 
 
 def ibrd_spread(g, lam, out, accumulate=False):
@@ -477,10 +484,13 @@ class Grid:
         ibrd_vcycle(self.handle, rhs, x, zero_initial_guess)
         return x
 
-    def vcycle_f32(self, rhs, x=None, zero_initial_guess=True):
+    def vcycle_f32(self, rhs, x=None, zero_initial_guess=True, nu1=2, nu2=2):
         import torch
         x = torch.zeros_like(rhs) if x is None else x
-        ibrd_vcycle_f32(self.handle, rhs, x, zero_initial_guess)
+        if (nu1, nu2) == (2, 2):
+            ibrd_vcycle_f32(self.handle, rhs, x, zero_initial_guess)
+        else:
+            ibrd_vcycle_f32_sweeps(self.handle, rhs, x, zero_initial_guess, nu1, nu2)
         return x
 
     def spread(self, lam, out=None, accumulate=False):

@@ -402,8 +402,17 @@ int vcycle_level(ibrd_grid g, int l, const T* b, const double* bshift, T* x, boo
   T* oth = H.y[l];
   bool first = zero;
   int np = 0;
-  if (sizeof(T) == 4 && nu1 == 1 && zero && zero_restrict_ok(lv.d) && aligned16(b) && aligned16(cur) &&
-      lv.d.n() <= (size_t(1) << 21)) {
+  if (sizeof(T) == 4 && nu1 == 1 && zero && zero_restrict_rows_ok(lv.d) && aligned16(b) && aligned16(cur) &&
+      wait_error_flag()) {
+    // rows of 128 or 256 cells: the single pre-smoothing sweep from zero and
+    // the restriction in one pass, row-resident and fed by TMA
+    prof_begin(P_RBGS32, g->s);
+    launch_zero_restrict_rows(reinterpret_cast<const float*>(b), bshift, reinterpret_cast<float*>(cur),
+                              reinterpret_cast<float*>(H.b[l + 1]), lv.d, st, zero_restrict_rows_default_zc(lv.d),
+                              g->s);
+    prof_end(P_RBGS32, g->s, "zero_restrict_rows", 8.5 * sizeof(T) / 4.0 * lv.d.n());
+  } else if (sizeof(T) == 4 && nu1 == 1 && zero && zero_restrict_ok(lv.d) && aligned16(b) && aligned16(cur) &&
+             lv.d.n() <= (size_t(1) << 21)) {
     // the single pre-smoothing sweep from zero and the restriction in one pass
     // (levels up to 128^3 cells; on larger ones the kernel is bound by its
     // shared-memory traffic and the two streaming kernels are faster)
@@ -1719,6 +1728,16 @@ ibrd_status ibrd_vcycle_f32(ibrd_grid g, const float* rhs, float* x, int zero) {
   return guarded(g, "ibrd_vcycle_f32", [&]() {
     if (!rhs || !x || rhs == x) throw ArgError{IBRD_ERR_ARG, "null or aliased field"};
     vcycle<float>(g, rhs, x, zero != 0, g->alpha, 2, 2);
+    check_waits_if_not_capturing(g, "V-cycle");
+    return IBRD_OK;
+  });
+}
+
+ibrd_status ibrd_vcycle_f32_sweeps(ibrd_grid g, const float* rhs, float* x, int zero, int nu1, int nu2) {
+  return guarded(g, "ibrd_vcycle_f32_sweeps", [&]() {
+    if (!rhs || !x || rhs == x) throw ArgError{IBRD_ERR_ARG, "null or aliased field"};
+    if (nu1 < 0 || nu2 < 0 || nu1 > 16 || nu2 > 16) throw ArgError{IBRD_ERR_ARG, "bad sweep counts"};
+    vcycle<float>(g, rhs, x, zero != 0, g->alpha, nu1, nu2);
     check_waits_if_not_capturing(g, "V-cycle");
     return IBRD_OK;
   });

@@ -126,6 +126,13 @@ bool rows_sweep_ok(Dims d);
 int rows_sweep_default_zc(Dims d);
 int launch_rows_sweep(const float* xin, float* xout, const float* b, const double* bshift, Dims d, Stencil st,
                       int zc, double* part, int part_cap, cudaStream_t s);
+// The first sweep from zero fused with the residual restriction on the same
+// levels as the row-resident sweep: x = sweep(0), bc = mean over 8 children of
+// b - shift - A x (bc 8-byte aligned). zc = planes per CTA (made even).
+bool zero_restrict_rows_ok(Dims d);
+int zero_restrict_rows_default_zc(Dims d);
+void launch_zero_restrict_rows(const float* b, const double* bshift, float* x, float* bc, Dims d, Stencil st,
+                               int zc, cudaStream_t s);
 // Levels handled by the single-CTA coarse V-cycle (shared-memory resident).
 constexpr int kMaxSmallLevels = 12;
 struct CoarseLevels {

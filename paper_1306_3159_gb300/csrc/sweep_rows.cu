@@ -298,6 +298,244 @@ __global__ void __launch_bounds__((kRowsTY + 2) * 32, 2)
   }
 }
 
+// First red-black sweep from x = 0 fused with the residual restriction, for
+// the same levels as the sweep above: x = one sweep of A x = b - shift from
+// zero (red cells (b - shift) / diag, black cells from their red neighbours,
+// the arithmetic of k_rb_zero_f32v) and bc = mean over the 8 children of
+// b - shift - A x, in one pass over b (HBM: read b, write x and bc).
+//
+// Layout as in k_rbgs_rows: warp w owns row y0 - 1 + w of every plane; a ring
+// of R b-planes (rows y0-2 .. y0+TY+1) arrives by TMA; the march order
+// alternates between even and odd z-chunks. Step i forms x on march plane i
+// (all warps, rows y0-1 .. y0+TY: the edge rows' residuals need them) from b
+// of planes i-1 .. i+1, and the residual of march plane i-1 (tile warps) from
+// x of planes i-2 .. i; x rows go through shared memory (XB, double-buffered)
+// for the y-neighbours. Restriction: the two cells of a coarse cell along x
+// sit in one lane, the two planes along z are summed in registers over two
+// steps, and the two rows along y belong to warps w (even y) and w + 1 (odd
+// y): when a plane pair is complete the odd row's warp leaves its sums in
+// shared memory (RY) and the even row's warp adds them one step later (after
+// the step's barrier) and writes the coarse row. Chunks start on even planes
+// and hold an even number of them, so plane pairs never straddle chunks.
+template <int NS>
+__global__ void __launch_bounds__((kRowsTY + 2) * 32, 2)
+    k_zr_rows(const __grid_constant__ CUtensorMap mb_tile, const __grid_constant__ CUtensorMap mb_pair,
+              float* __restrict__ xout, float* __restrict__ bc, const double* __restrict__ bshift, int ny, int nz,
+              int zc, float inv, float off, float diag, int* __restrict__ err, unsigned wait_limit) {
+  constexpr int TY = kRowsTY, R = kRowsRing, NX = 128 * NS, NXC = NX / 2;
+  constexpr int XROWS = TY + 4, XBROWS = TY + 2;
+  constexpr unsigned BBYTES = XROWS * NX * 4;
+  extern __shared__ __align__(1024) unsigned char sm_raw[];
+  float* BSM = reinterpret_cast<float*>(sm_raw);        // R b planes, rows y0-2 .. y0+TY+1
+  float* XB = BSM + R * XROWS * NX;                      // 2 x planes, rows y0-1 .. y0+TY
+  float2* RY = reinterpret_cast<float2*>(XB + 2 * XBROWS * NX);  // TY/2 odd-row pair sums
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(RY + (TY / 2) * NXC / 2);
+
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int y0 = blockIdx.x * TY;
+  const int k0 = blockIdx.y * zc, k1 = min(k0 + zc, nz);
+  const bool down = blockIdx.y & 1;
+  const size_t plane = (size_t)NX * ny;
+  const int nyc = ny >> 1;
+  const float sh = bshift ? (float)(*bshift) : 0.f;
+  const bool interior = w >= 1 && w <= TY;
+  const int y = y0 - 1 + w;
+  const int ypar = y & 1;  // ny is even, so the wrap keeps it
+  const int last = k1 - k0 + 3;
+  auto mp = [&](int i) { return down ? k1 + 1 - i : k0 - 2 + i; };
+
+  if (tid == 0) {
+    for (int s = 0; s < R; ++s) mbar_init(smem_u32(bars + s), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  auto issue = [&](int i) {
+    const int s = i % R;
+    const unsigned bar = smem_u32(bars + s);
+    const int z = wrapm(mp(i), nz);
+    float* bs = BSM + s * XROWS * NX;
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    mbar_expect_tx(bar, BBYTES);
+    tma_load3(smem_u32(bs), &mb_pair, 0, wrapm(y0 - 2, ny), z, bar);
+    tma_load3(smem_u32(bs + 2 * NX), &mb_tile, 0, y0, z, bar);
+    tma_load3(smem_u32(bs + (TY + 2) * NX), &mb_pair, 0, wrapm(y0 + TY, ny), z, bar);
+  };
+  auto wait_plane = [&](int i, unsigned limit) {
+    return mbar_wait(smem_u32(bars + (i % R)), (unsigned)((i / R) & 1), limit);
+  };
+  auto brow = [&](int i, int r) { return reinterpret_cast<const float4*>(BSM + (i % R) * XROWS * NX + r * NX); };
+  auto xrow = [&](int i, int r) { return reinterpret_cast<float4*>(XB + (i & 1) * XBROWS * NX + r * NX); };
+
+  bool ok = true;
+  if (tid == 0) {
+    for (int i = 0; i < R && i <= last; ++i) issue(i);
+    ok = wait_plane(0, wait_limit) && wait_plane(1, wait_limit) && wait_plane(2, wait_limit);
+  }
+  int issued = min(R - 1, last);
+  ok = !__syncthreads_or(!ok);
+  int done = ok ? 2 : -1;
+
+  auto shifted = [&](float4 t) {
+    t.x -= sh, t.y -= sh, t.z -= sh, t.w -= sh;
+    return t;
+  };
+  // b - shift of this thread's row: planes i-1, i, i+1 (march order)
+  float4 B0[NS], B1[NS], B2[NS];
+  // x of this thread's row: planes i-2, i-1, i
+  float4 X0[NS], X1[NS], X2[NS];
+  float2 acc[NS], held[NS];  // restriction sums: plane pair in progress / completed (even rows)
+  if (ok) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      B0[s] = shifted(brow(0, w + 1)[lane + 32 * s]);
+      B1[s] = shifted(brow(1, w + 1)[lane + 32 * s]);
+    }
+  }
+  __syncthreads();  // step 1 refills plane 0's slot
+  bool pending = false;  // an even row holds a completed pair to combine
+
+  // x on march plane i from b' of planes i-1 (bm), i (b0), i+1 (bp) of this
+  // row and rows y -/+ 1 of plane i (shared memory): red cells b'/diag, black
+  // cells (b' + off * sum of the red neighbours' b'/diag) / diag.
+  auto form_x = [&](float4 (&xo)[NS], const float4 (&bm)[NS], const float4 (&b0)[NS], const float4 (&bp)[NS],
+                    int i, int a) {
+    const float4* u = brow(i, w) + lane;
+    const float4* dn = brow(i, w + 2) + lane;
+    float tl[NS], tr[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      tl[s] = __shfl_sync(0xffffffffu, b0[s].w, (lane + 31) & 31);
+      tr[s] = __shfl_sync(0xffffffffu, b0[s].x, (lane + 1) & 31);
+    }
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      const float L = (lane == 0 ? tl[(s + NS - 1) % NS] : tl[s]) * inv;
+      const float Rr = (lane == 31 ? tr[(s + 1) % NS] : tr[s]) * inv;
+      const float4 uu = shifted(u[32 * s]), dd = shifted(dn[32 * s]);
+      const float c0 = b0[s].x * inv, c1 = b0[s].y * inv, c2 = b0[s].z * inv, c3 = b0[s].w * inv;
+      auto blk = [&](float bv, float l, float r, float uv, float dv, float zm, float zp) {
+        return (bv + off * (((l + r) + (uv * inv + dv * inv)) + (zm * inv + zp * inv))) * inv;
+      };
+      float4 o;
+      if (a == 0) {  // red at e = 0, 2
+        o.x = c0;
+        o.y = blk(b0[s].y, c0, c2, uu.y, dd.y, bm[s].y, bp[s].y);
+        o.z = c2;
+        o.w = blk(b0[s].w, c2, Rr, uu.w, dd.w, bm[s].w, bp[s].w);
+      } else {  // red at e = 1, 3
+        o.x = blk(b0[s].x, L, c1, uu.x, dd.x, bm[s].x, bp[s].x);
+        o.y = c1;
+        o.z = blk(b0[s].z, c1, c3, uu.z, dd.z, bm[s].z, bp[s].z);
+        o.w = c3;
+      }
+      xo[s] = o;
+    }
+  };
+  // residual b' - A x of this row on march plane i - 1, x-pair sums
+  auto resid = [&](float2 (&p)[NS], const float4 (&xm)[NS], const float4 (&x0)[NS], const float4 (&xp)[NS],
+                   const float4 (&b0)[NS], int i) {
+    const float4* u = xrow(i - 1, w - 1) + lane;
+    const float4* dn = xrow(i - 1, w + 1) + lane;
+    float tl[NS], tr[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      tl[s] = __shfl_sync(0xffffffffu, x0[s].w, (lane + 31) & 31);
+      tr[s] = __shfl_sync(0xffffffffu, x0[s].x, (lane + 1) & 31);
+    }
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      const float L = lane == 0 ? tl[(s + NS - 1) % NS] : tl[s];
+      const float Rr = lane == 31 ? tr[(s + 1) % NS] : tr[s];
+      const float4 uu = u[32 * s], dd = dn[32 * s];
+      auto r = [&](float bv, float c, float l, float rr, float uv, float dv, float zm, float zp) {
+        return bv - (diag * c - off * (((l + rr) + (uv + dv)) + (zm + zp)));
+      };
+      const float r0 = r(b0[s].x, x0[s].x, L, x0[s].y, uu.x, dd.x, xm[s].x, xp[s].x);
+      const float r1 = r(b0[s].y, x0[s].y, x0[s].x, x0[s].z, uu.y, dd.y, xm[s].y, xp[s].y);
+      const float r2 = r(b0[s].z, x0[s].z, x0[s].y, x0[s].w, uu.z, dd.z, xm[s].z, xp[s].z);
+      const float r3 = r(b0[s].w, x0[s].w, x0[s].z, Rr, uu.w, dd.w, xm[s].w, xp[s].w);
+      p[s] = make_float2(r0 + r1, r2 + r3);
+    }
+  };
+  // coarse row of an even fine row y: its held sums plus the odd row's (RY)
+  auto combine = [&](int kc) {
+    const float2* ry = RY + ((w - 1) >> 1) * (NXC / 2);
+    float2* dst = reinterpret_cast<float2*>(bc + ((size_t)kc * nyc + (y >> 1)) * NXC);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      const float2 o = ry[lane + 32 * s];
+      dst[lane + 32 * s] = make_float2((held[s].x + o.x) * 0.125f, (held[s].y + o.y) * 0.125f);
+    }
+  };
+  int kc_pending = 0;
+
+  // Step i: bm, b0, bp = b' of march planes i-1, i, i+1 (bp is loaded here);
+  // xm2, xm1, x0 = x of march planes i-2, i-1, i (x0 is formed here).
+  auto step = [&](float4 (&bm)[NS], float4 (&b0)[NS], float4 (&bp)[NS], float4 (&xm2)[NS], float4 (&xm1)[NS],
+                  float4 (&x0)[NS], int i) -> bool {
+    if (i > last - 1 || !ok) return false;
+    if (tid == 0 && i + 3 <= last) issue(i + 3);
+    if (i + 3 <= last) issued = i + 3;
+    if (pending) {  // the odd row left its sums in RY before the last barrier
+      combine(kc_pending);
+      pending = false;
+    }
+#pragma unroll
+    for (int s = 0; s < NS; ++s) bp[s] = shifted(brow(i + 1, w + 1)[lane + 32 * s]);
+    const int z = mp(i);
+    form_x(x0, bm, b0, bp, i, (ypar + z) & 1);
+    float4* xr = xrow(i, w);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) xr[lane + 32 * s] = x0[s];
+    if (interior && i >= 3) {
+      const int zr = mp(i - 1);  // plane of the residual, in [k0, k1)
+      float4* dst = reinterpret_cast<float4*>(xout + (size_t)zr * plane + (size_t)y * NX);
+#pragma unroll
+      for (int s = 0; s < NS; ++s) dst[lane + 32 * s] = xm1[s];
+      float2 pr[NS];
+      resid(pr, xm2, xm1, x0, bm, i);
+      // march order visits a plane pair (2K, 2K + 1) upwards or downwards
+      const bool first = down ? (zr & 1) : !(zr & 1);
+#pragma unroll
+      for (int s = 0; s < NS; ++s) acc[s] = first ? pr[s] : make_float2(acc[s].x + pr[s].x, acc[s].y + pr[s].y);
+      if (!first) {
+        if (ypar) {
+          float2* ry = RY + ((w - 2) >> 1) * (NXC / 2);
+#pragma unroll
+          for (int s = 0; s < NS; ++s) ry[lane + 32 * s] = acc[s];
+        } else {
+#pragma unroll
+          for (int s = 0; s < NS; ++s) held[s] = acc[s];
+          pending = true;
+          kc_pending = zr >> 1;
+        }
+      }
+    }
+    bool good = true;
+    if (tid == 0 && i + 2 <= last) good = wait_plane(i + 2, wait_limit);
+    ok = !__syncthreads_or(!good);
+    if (ok) done = i + 2;
+    return ok;
+  };
+  for (int i = 1; i < last; i += 6) {
+    if (!step(B0, B1, B2, X0, X1, X2, i)) break;
+    if (!step(B1, B2, B0, X1, X2, X0, i + 1)) break;
+    if (!step(B2, B0, B1, X2, X0, X1, i + 2)) break;
+    if (!step(B0, B1, B2, X0, X1, X2, i + 3)) break;
+    if (!step(B1, B2, B0, X1, X2, X0, i + 4)) break;
+    if (!step(B2, B0, B1, X2, X0, X1, i + 5)) break;
+  }
+  if (!ok) {
+    if (tid == 0) {
+      for (int i = done + 1; i <= issued; ++i) wait_plane(i, kDrainLimit);
+      atomicOr(err, 1);
+    }
+    __syncthreads();
+    return;
+  }
+  if (pending) combine(kc_pending);  // the last pair (its RY write preceded the last barrier)
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   static std::once_flag once;
@@ -378,6 +616,40 @@ int launch_rows_sweep(const float* xin, float* xout, const float* b, const doubl
   else
     rows_launch<1>(g, s, m, xout, bshift, d, zc, inv, off, part, err, limit);
   return part ? nblk : 0;
+}
+
+
+bool zero_restrict_rows_ok(Dims d) { return rows_sweep_ok(d); }
+
+int zero_restrict_rows_default_zc(Dims d) {
+  int zc = rows_sweep_default_zc(d);
+  zc += zc & 1;  // even chunks: plane pairs of the restriction stay inside a chunk
+  return zc;
+}
+
+void launch_zero_restrict_rows(const float* b, const double* bshift, float* x, float* bc, Dims d, Stencil st,
+                               int zc, cudaStream_t s) {
+  if (!zero_restrict_rows_ok(d) || !aligned16(b) || !aligned16(x) || ((uintptr_t)bc & 7u) || b == x)
+    throw CudaError{cudaErrorInvalidValue, "fused zero sweep + restriction arguments"};
+  zc = zc < 2 ? 2 : (zc > d.nz ? d.nz : zc);
+  zc += zc & 1;
+  const CUtensorMap mt = field_map(b, d, kRowsTY), mpair = field_map(b, d, 2);
+  dim3 g(d.ny / kRowsTY, (d.nz + zc - 1) / zc);
+  const float inv = (float)(1.0 / st.diag), off = (float)st.off, diag = (float)st.diag;
+  int* err = wait_error_flag();
+  const unsigned limit = wait_limit();
+  auto go = [&](auto kern, int ns) {
+    const size_t sm = sizeof(float) * (size_t)(128 * ns) *
+                          (kRowsRing * (kRowsTY + 4) + 2 * (kRowsTY + 2) + kRowsTY / 2 / 2) +
+                      8 * kRowsRing;
+    static std::atomic<unsigned long long> attr1{0}, attr2{0};
+    ensure_smem_attr((const void*)kern, (int)sm, ns == 2 ? attr2 : attr1);
+    kern<<<g, (kRowsTY + 2) * 32, sm, s>>>(mt, mpair, x, bc, bshift, d.ny, d.nz, zc, inv, off, diag, err, limit);
+  };
+  if (d.nx == 256)
+    go(k_zr_rows<2>, 2);
+  else
+    go(k_zr_rows<1>, 1);
 }
 
 }  // namespace ibrd

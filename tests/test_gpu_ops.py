@@ -261,6 +261,27 @@ def test_vcycle_f32_row_kernel(ibrd, dims, alpha, zc):
     assert rel_max(x, want) < 2e-5
 
 
+@pytest.mark.parametrize("dims,alpha", ROWS_CASES + [((256, 64, 32), 0.0)])
+@pytest.mark.parametrize("nu1,nu2,zero", [(1, 1, True), (1, 2, True), (2, 1, True), (1, 1, False)])
+def test_vcycle_f32_sweep_counts(ibrd, dims, alpha, nu1, nu2, zero):
+    """The FP32 V-cycle with the sweep counts of the solves' preconditioners:
+    with one pre-smoothing sweep from zero on levels with 128- or 256-cell rows
+    that sweep and the residual restriction run as one row-resident kernel
+    (one pass over b, writing x and the coarse right-hand side); against the
+    oracle's V-cycle with the same counts, from zero and from a guess."""
+    import torch
+    nx, ny, nz = dims
+    rng = np.random.default_rng(61 + nu1 + 2 * nu2)
+    b = rng.standard_normal((nz, ny, nx)).astype(np.float32)
+    x0 = rng.standard_normal((nz, ny, nx)).astype(np.float32)
+    g = ibrd.Grid(*dims, alpha=alpha)
+    x = torch.from_numpy(x0).cuda()
+    g.vcycle_f32(torch.from_numpy(b).cuda(), x, zero_initial_guess=zero, nu1=nu1, nu2=nu2)
+    want = mg.vcycle(b.astype(np.float64), 1.0, 1.0, alpha, x0=None if zero else x0.astype(np.float64), nu1=nu1,
+                     nu2=nu2, exact_cells=32768, exact_side=64)
+    assert rel_max(x.cpu().numpy().astype(np.float64), want) < 2e-5
+
+
 def test_bounded_wait_gives_up_with_timeout_status(ibrd):
     """A bound of zero polls makes every plane wait of the row sweep give up:
     each CTA drains its copies in flight and stops, and the FP32 V-cycle and a
