@@ -463,6 +463,8 @@ def run_ours(args):
         result["batched"] = run_batched(p, torch, world, args, tune=not args.no_autotune)
     if not args.no_learned:
         result["learned"] = run_learned(p, torch, world, args)
+    if not args.no_physics:
+        result["physics"] = run_physics(p, torch, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline_run()
     if rank == 0:
@@ -662,6 +664,59 @@ def run_learned(p, torch, world, args):
     return out
 
 
+def run_physics(p, torch, args):
+    """Validation sweeps of Sec. IV.B and IV.D on the GPU path: the cubic
+    lattice's beta_0 against Eq. beta_cubic over the packing fractions of
+    Fig. PerDisp, and Omega (Eq. Omega) of one blob in a periodic 128^3 box
+    against P for finite reaction rates (Fig. finite_P_fit right; the paper
+    uses L = 100), with the exact line Omega = beta_0^-1 + P / (1 - phi) and
+    Lu's approximation (Eq. beta_P_theory)."""
+    import math
+    import numpy as np
+    from oracle import outputs
+    from synthetic import lattice_positions
+    a = 1.27
+    out = {"lattice": [], "finite_P": {}}
+    for L, sp in [(64, 4), (80, 5), (96, 6), (64, 8), (80, 10), (96, 12), (64, 16)]:
+        q = lattice_positions((L, L, L), 1.0, sp)
+        G = p.Grid(L, L, L)
+        G.set_blobs(torch.from_numpy(q).cuda())
+        V = L ** 3
+        t0 = time.perf_counter()
+        _, _, info = G.solve_saddle(torch.full((L, L, L), 1.0 / V, dtype=torch.float64, device="cuda"), tol=1e-10,
+                                    max_iter=500)
+        dt = time.perf_counter() - t0
+        phi = len(q) * (4 * math.pi * a ** 3 / 3) / V
+        b0 = outputs.beta0(info["cbar"], 1.0 / V, a, 1.0, len(q), V)
+        out["lattice"].append({"grid": L, "spacing": sp, "blobs": len(q), "phi": round(phi, 5), "beta0": round(b0, 5),
+                               "eq_beta_cubic": round(outputs.beta0_cubic_fit(phi), 5), "solve_ms": round(1e3 * dt, 2)})
+        G.close()
+    L = 128
+    V = L ** 3
+    phi = (4 * math.pi * a ** 3 / 3) / V
+    G = p.Grid(L, L, L)
+    G.set_blobs(torch.tensor([[L / 2, L / 2, L / 2]], dtype=torch.float64, device="cuda"))
+    src = torch.full((L, L, L), 1.0 / V, dtype=torch.float64, device="cuda")
+    _, _, info0 = G.solve_saddle(src, tol=2e-8, max_iter=500)
+    omega0 = 1.0 / outputs.beta0(info0["cbar"], 1.0 / V, a, 1.0, 1, V)
+    rows = []
+    for P in (0.1, 0.3, 1.0, 3.0, 10.0):
+        kappa = 4 * math.pi * a / P
+        _, info = G.solve_reaction(torch.tensor([kappa], dtype=torch.float64, device="cuda"), src, tol=2e-8,
+                                   max_iter=500)
+        om = 1.0 / outputs.beta0(info["cbar"], 1.0 / V, a, 1.0, 1, V)
+        rows.append({"P": P, "Omega": round(om, 6), "beta_P": round((1 + P) / om, 6),
+                     "eq_beta_P_theory": round((1 + P) / (omega0 + (1 - phi) * P), 6)})
+    G.close()
+    Ps = [r["P"] for r in rows]
+    slope, icept = np.polyfit(Ps, [r["Omega"] for r in rows], 1)
+    out["finite_P"] = {"grid": [L] * 3, "phi": phi, "omega0": round(omega0, 6), "rows": rows,
+                       "fit_slope": round(float(slope), 6), "fit_intercept": round(float(icept), 6),
+                       "exact_slope_1_over_1_minus_phi": 1 / (1 - phi), "lu_slope_1_minus_phi": 1 - phi}
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_kernel_case_fp64(args):
     """FP64 operator applications y = A c on a 256^3 field (about 0.27 GB on
     the device) with a profiler range around one of them: the small case for
@@ -819,6 +874,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-realisations leg")
     ap.add_argument("--no-autotune", action="store_true", help="built-in launch shapes only")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned warm-start leg")
+    ap.add_argument("--no-physics", action="store_true", help="skip the Sec. IV.B / IV.D validation sweeps")
     ap.add_argument("--cpu-steps", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--cpu-warmup", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--ncu-step", action="store_true", help="profiler range around one step, then exit")

@@ -56,7 +56,11 @@ typedef enum {
 
 enum { IBRD_PESKIN4 = 4, IBRD_PESKIN3 = 3 };          /* kernel width w */
 enum { IBRD_FP64 = 0, IBRD_MIXED_FP32 = 1, IBRD_MIXED_REFINE = 2 };  /* precision */
-enum { IBRD_PRECOND_SCHUR = 0, IBRD_PRECOND_DIAG = 1 }; /* saddle preconditioner */
+/* saddle preconditioner: approximate Schur complement, diagonal (Eq.
+   Schur_diagonal), or chosen by blob count (AUTO: diagonal for at most 512
+   blobs in the mixed-precision modes and at most 2048 in FP64, where it was
+   measured faster at 128^3 and 256^3; approximate Schur above) */
+enum { IBRD_PRECOND_SCHUR = 0, IBRD_PRECOND_DIAG = 1, IBRD_PRECOND_AUTO = 2 };
 enum { IBRD_GUESS_NONE = 0, IBRD_GUESS_UNIFORM = 1, IBRD_GUESS_GIVEN = 2, IBRD_GUESS_PENALTY = 3 }; /* saddle start */
 
 /* Solver options. ibrd_default_opts fills the defaults noted here. */
@@ -68,7 +72,12 @@ typedef struct {
   int mg_cycles;     /* n: V-cycles per approximate Helmholtz solve (1) */
   int schur_inner;   /* m: inner Krylov iterations of the approximate Schur
                         preconditioner (5, Sec. III.E / Appendix A) */
-  int precond;       /* IBRD_PRECOND_SCHUR (default) or IBRD_PRECOND_DIAG */
+  int precond;       /* IBRD_PRECOND_AUTO (default), _SCHUR or _DIAG. The
+                        diagonal preconditioner's gamma = M_11 is computed
+                        once per handle (40 FP64 V-cycles on the first blob
+                        the first such solve sees) and kept when the blobs
+                        change: it depends on the system size and only at the
+                        percent level on a blob's position (Sec. III.E) */
   double zeta;       /* scaling zeta of Eq. saddle_point (1) */
   double xi;         /* scaling xi; <= 0 selects zeta / h^3 (Eq. saddle_point) */
   int nu1, nu2;      /* red-black Gauss-Seidel sweeps before/after (2, 2) */
@@ -143,6 +152,8 @@ typedef struct {
   int history_cap;
   int refinements;     /* IBRD_MIXED_REFINE: refinement steps (FP32 solves) */
   double a_L;          /* reaction radius a_L = K / (4 pi chi) (Sec. IV.A) */
+  int precond;         /* saddle solves: the preconditioner that ran
+                          (IBRD_PRECOND_SCHUR or _DIAG); -1 for reaction solves */
 } ibrd_solve_info;
 
 /* Fill *opts with the defaults listed in ibrd_solve_opts. */

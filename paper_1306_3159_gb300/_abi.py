@@ -13,7 +13,7 @@ LIB_PATH = os.path.join(PKG, "libibrd.so")
 
 IBRD_PESKIN4, IBRD_PESKIN3 = 4, 3
 IBRD_FP64, IBRD_MIXED_FP32, IBRD_MIXED_REFINE = 0, 1, 2
-IBRD_PRECOND_SCHUR, IBRD_PRECOND_DIAG = 0, 1
+IBRD_PRECOND_SCHUR, IBRD_PRECOND_DIAG, IBRD_PRECOND_AUTO = 0, 1, 2
 IBRD_GUESS_NONE, IBRD_GUESS_UNIFORM, IBRD_GUESS_GIVEN, IBRD_GUESS_PENALTY = 0, 1, 2, 3
 
 STATUS = {0: "IBRD_OK", 1: "IBRD_ERR_ARG", 2: "IBRD_ERR_CUDA", 3: "IBRD_ERR_OOM", 4: "IBRD_ERR_NOT_CONVERGED",
@@ -47,7 +47,8 @@ class SolveInfo(ctypes.Structure):
                 ("vcycles", ctypes.c_int), ("reorths", ctypes.c_int), ("rel_residual", ctypes.c_double), ("sum_lambda", ctypes.c_double),
                 ("cbar", ctypes.c_double), ("rate_K", ctypes.c_double), ("seconds", ctypes.c_double),
                 ("residual_history", ctypes.POINTER(ctypes.c_double)), ("history_len", ctypes.c_int),
-                ("history_cap", ctypes.c_int), ("refinements", ctypes.c_int), ("a_L", ctypes.c_double)]
+                ("history_cap", ctypes.c_int), ("refinements", ctypes.c_int), ("a_L", ctypes.c_double),
+                ("precond", ctypes.c_int)]
 
 
 class Profile(ctypes.Structure):
@@ -266,7 +267,7 @@ def _info_dict(info, hist):
     return {"status": info.status, "outer_iters": info.outer_iters, "inner_iters": info.inner_iters,
             "vcycles": info.vcycles, "reorths": info.reorths, "rel_residual": info.rel_residual, "sum_lambda": info.sum_lambda,
             "cbar": info.cbar, "rate_K": info.rate_K, "a_L": info.a_L, "seconds": info.seconds,
-            "refinements": info.refinements,
+            "refinements": info.refinements, "precond": info.precond,
             "history": hist[:info.history_len].copy()}
 
 

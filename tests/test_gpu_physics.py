@@ -93,3 +93,76 @@ def test_reaction_radius_sweep_over_box_size(ibrd):
     assert all(x > y for x, y in zip(aLs, aLs[1:])) and all(r[1] > r[2] for r in rows), rows
     assert np.all((corr > 1.24) & (corr < 1.30)), rows
     assert (corr.max() - corr.min()) / corr.mean() < 0.01, rows
+
+
+# Cubic lattices of blobs at grid nodes (Sec. IV.B, Fig. PerDisp): (grid side,
+# lattice spacing). A lattice of spacing s is the periodic tiling of one blob
+# in an s^3 box, so each case is also checked against the oracle's direct
+# solve of that single cell.
+LATTICES = [(64, 4), (80, 5), (96, 6), (64, 8), (80, 10), (96, 12), (64, 16)]
+
+
+@pytest.mark.parametrize("L,sp", LATTICES)
+def test_cubic_lattice_phi_sweep(ibrd, L, sp):
+    """Sec. IV.B, Eq. beta_cubic, packing fractions 0.002-0.134 (the paper's
+    range is 0 < phi < 0.15): the GPU solve of a cubic lattice gives the mean
+    concentration of the oracle's single periodic cell within 1e-8, and
+    beta_0 follows the paper's fit to Lu's data within 1 % for phi < 0.02 and
+    within 5 % above (where the supports of neighbouring blobs come within a
+    few cells of each other)."""
+    from oracle import direct
+    q = lattice_positions((L, L, L), 1.0, sp)
+    g = ibrd.Grid(L, L, L)
+    g.set_blobs(dev(q))
+    V = L ** 3
+    src = np.full((L, L, L), 1.0 / V)
+    c, lam, info = g.solve_saddle(dev(src), tol=1e-10, max_iter=500)
+    a = 1.27
+    phi = len(q) * (4 * math.pi * a ** 3 / 3) / V
+    # the oracle's single cell: one blob at a node of an sp^3 box, same source density
+    v1 = sp ** 3
+    c1, _, _ = direct.solve_saddle(np.zeros((1, 3)), np.full((sp, sp, sp), 1.0 / V), 1.0, 1.0, 0.0)
+    assert abs(info["cbar"] - c1.mean()) < 1e-8 * abs(c1.mean())
+    b0 = outputs.beta0(info["cbar"], 1.0 / V, a, 1.0, len(q), V)
+    fit = outputs.beta0_cubic_fit(phi)
+    assert abs(b0 / fit - 1.0) < (0.01 if phi < 0.02 else 0.05), (phi, b0, fit)
+    assert v1 * len(q) == V
+
+
+def test_finite_rate_omega_linear_in_P(ibrd):
+    """Sec. IV.D (Fig. finite_P_fit right): one blob (4-point kernel, at a
+    node) in a periodic box, steady reaction-limited solves at P = 4 pi chi a /
+    kappa from 0.1 to 10. Eq. Omega's Omega = [s a^2 (1 - phi) / (3 phi chi
+    cbar)]^-1 is linear in P: for one periodic blob Sec. III.D gives c_P - c_0
+    = lambda / kappa exactly, so Omega = beta_0^-1 + P / (1 - phi), with
+    beta_0 from the diffusion-limited solve; Lu's approximation (Eq.
+    beta_P_theory) has slope (1 - phi), the same to O(phi). The paper uses
+    L = 100 grid cells; this multigrid needs sides that halve to a coarsest
+    level of at most 512 cells, so L = 128 (phi = 4e-6) stands in."""
+    L = 128
+    a = 1.27
+    V = L ** 3
+    phi = (4 * math.pi * a ** 3 / 3) / V
+    q = np.array([[L / 2, L / 2, L / 2]])
+    g = ibrd.Grid(L, L, L)
+    g.set_blobs(dev(q))
+    src = dev(np.full((L, L, L), 1.0 / V))
+    # the source is 1/V, so the FP64 floor of the relative residual is near
+    # 1e-8 here (c is of order 1); cbar is still fixed to far more digits than
+    # the 1e-6 checks below need
+    _, _, info0 = g.solve_saddle(src, tol=2e-8, max_iter=500)
+    omega0 = 1.0 / outputs.beta0(info0["cbar"], 1.0 / V, a, 1.0, 1, V)
+    Ps = [0.1, 0.3, 1.0, 3.0, 10.0]
+    om = []
+    for P in Ps:
+        kappa = 4 * math.pi * 1.0 * a / P
+        _, info = g.solve_reaction(dev(np.array([kappa])), src, tol=2e-8, max_iter=500)
+        om.append(1.0 / outputs.beta0(info["cbar"], 1.0 / V, a, 1.0, 1, V))
+    om = np.array(om)
+    np.testing.assert_allclose(om - omega0, np.array(Ps) / (1 - phi), rtol=1e-6)
+    slope, icept = np.polyfit(Ps, om, 1)
+    assert abs(slope - 1 / (1 - phi)) < 1e-6 and abs(icept - omega0) < 1e-6 * omega0
+    # Eq. beta_P_theory: beta_P = (1 + P) / Omega against (1 + P) / (beta_0^-1 + (1 - phi) P)
+    beta_p = (1 + np.array(Ps)) / om
+    theory = (1 + np.array(Ps)) / (omega0 + (1 - phi) * np.array(Ps))
+    assert np.abs(beta_p / theory - 1).max() < 5 * phi * max(Ps)

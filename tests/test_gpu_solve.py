@@ -64,12 +64,16 @@ SOLVE_CASES = [(0, 1e-12, 1e-11), (1, 1e-10, 1e-8), (1, 1e-12, 1e-11), (2, 1e-10
 
 
 @pytest.mark.parametrize("precision,tol,err", SOLVE_CASES)
-def test_saddle_small(ibrd, small, precision, tol, err):
+@pytest.mark.parametrize("precond", [0, 2])
+def test_saddle_small(ibrd, small, precision, tol, err, precond):
+    """precond 0: the approximate Schur preconditioner; 2: the library's
+    default choice by blob count (48 blobs: the diagonal one)."""
     w, M = small
     c_ref, lam_ref, _ = direct.solve_saddle(w.q, w.g, w.h, w.chi, 0.0, M=M)
     g = _grid(ibrd, w)
     tol = max(tol, floor_tol(c_ref, w.g, w.h, w.chi, 0.0))
-    c, lam, info = g.solve_saddle(dev(w.g), tol=tol, precision=precision, max_iter=400)
+    c, lam, info = g.solve_saddle(dev(w.g), tol=tol, precision=precision, max_iter=400, precond=precond)
+    assert info["precond"] == (0 if precond == 0 else 1)
     assert info["rel_residual"] <= tol
     assert (info["refinements"] >= 1) == (precision == 2)
     assert rel_err(host(c), c_ref) < err
@@ -129,6 +133,32 @@ def test_saddle_diagonal_preconditioner(ibrd, small):
     tol = floor_tol(c_ref, w.g, w.h, w.chi, 0.0)
     c, lam, info = g.solve_saddle(dev(w.g), tol=tol, precond=1, restart=60, max_iter=2000)
     assert rel_err(host(lam), lam_ref) < 1e-11
+
+
+def test_auto_preconditioner_choice_and_kept_gamma(ibrd):
+    """IBRD_PRECOND_AUTO (the default) picks the diagonal preconditioner up to
+    512 blobs in the mixed modes and up to 2048 in FP64, the approximate Schur
+    one above; the diagonal preconditioner's gamma, computed once per handle,
+    is kept when the blobs change and the solve still reaches the oracle's
+    solution for the new configuration."""
+    dims = (32, 32, 32)
+    g = ibrd.Grid(*dims)
+    src = np.ones((32, 32, 32))
+    q1 = rsa_positions(20, dims, 1.0, 3.0, 71)
+    q2 = rsa_positions(30, dims, 1.0, 3.0, 72)
+    for q in (q1, q2):
+        g.set_blobs(dev(q))
+        c_ref, lam_ref, _ = direct.solve_saddle(q, src, 1.0, 1.0, 0.0)
+        tol = floor_tol(c_ref, src, 1.0, 1.0, 0.0)
+        c, lam, info = g.solve_saddle(dev(src), tol=tol, max_iter=600, precision=2)
+        assert info["precond"] == 1
+        assert rel_err(host(c), c_ref) < 1e-11 and rel_err(host(lam), lam_ref) < 1e-11
+    big = ibrd.Grid(64, 64, 64)
+    q3 = rsa_positions(600, (64, 64, 64), 1.0, 3.0, 73)
+    big.set_blobs(dev(q3))
+    src3 = dev(np.ones((64, 64, 64)))
+    assert big.solve_saddle(src3, tol=1e-8, precision=2, max_iter=600)[2]["precond"] == 0
+    assert big.solve_saddle(src3, tol=1e-8, precision=0, max_iter=600)[2]["precond"] == 1
 
 
 def test_single_blob_finite_rate_shift(ibrd):
@@ -434,14 +464,17 @@ def test_random_configurations(ibrd, seed):
     g.set_blobs(dev(q))
     case = (dims, h, chi, n, w_k, alpha, precision)
     c_ref, lam_ref, _ = direct.solve_saddle(q, gsrc, h, chi, alpha, w=w_k)
-    tol = max(1e-12, floor_tol(c_ref, gsrc, h, chi, alpha))
+    # alpha > 0 has no large constant mode: solve below 1e-12, so that the
+    # residual bounds the 1e-11 error whatever the conditioning of the case
+    base = 1e-12 if alpha == 0.0 else 1e-14
+    tol = floor_tol(c_ref, gsrc, h, chi, alpha, base=base)
     c, lam, info = g.solve_saddle(dev(gsrc), tol=tol, precision=precision, max_iter=600)
     assert info["rel_residual"] <= tol, case
     # every precision mode forms its stopping residual in FP64 and is solved
     # here to the FP64 rounding floor, so all of them meet the FP64 bar
     assert rel_err(host(c), c_ref) < 1e-11 and rel_err(host(lam), lam_ref) < 1e-11, case
     cr_ref, u_ref, _ = direct.solve_reaction(q, kappa, gsrc, h, chi, alpha, w=w_k)
-    tol = max(1e-12, floor_tol(cr_ref, gsrc, h, chi, alpha))
+    tol = floor_tol(cr_ref, gsrc, h, chi, alpha, base=base)
     cr, info = g.solve_reaction(dev(kappa), dev(gsrc), tol=tol, precision=precision, max_iter=600)
     assert info["rel_residual"] <= tol, case
     assert rel_err(host(cr), cr_ref) < 1e-11, case
