@@ -157,7 +157,8 @@ FP64_PEAK_TFLOPS = 1.2   # FP64 FMA rate of GB300 (recipe: 1.25 TFLOP/s nominal)
 
 
 # source file that defines each kernel class (for matching committed ncu data)
-CLASS_SOURCE = {"rbgs": "smoother.cu", "restrict": "smoother.cu", "prolong": "smoother.cu",
+# (the FP32 sweep class's largest launches are the row-resident sweep's)
+CLASS_SOURCE = {"rbgs_f32": "sweep_rows.cu", "rbgs": "smoother.cu", "restrict": "smoother.cu", "prolong": "smoother.cu",
                 "apply": "grid_kernels.cu", "vector": "grid_kernels.cu", "reduce": "grid_kernels.cu",
                 "dot": "krylov_kernels.cu", "axpy": "krylov_kernels.cu", "small": "krylov_kernels.cu",
                 "spread": "blob_kernels.cu", "interp": "blob_kernels.cu"}
@@ -165,7 +166,7 @@ CLASS_SOURCE = {"rbgs": "smoother.cu", "restrict": "smoother.cu", "prolong": "sm
 
 def kernel_source_hash(kernel_class: str = "rbgs_f32"):
     """Hash of the source file (plus the shared internal header) of a class."""
-    f = CLASS_SOURCE.get(kernel_class.split("_")[0], "smoother.cu")
+    f = CLASS_SOURCE.get(kernel_class, CLASS_SOURCE.get(kernel_class.split("_")[0], "smoother.cu"))
     csrc = os.path.join(ROOT, "paper_1306_3159_gb300", "csrc")
     h = hashlib.sha256()
     for name in (f, "internal.h"):
