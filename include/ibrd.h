@@ -99,7 +99,12 @@ typedef struct {
                         0 never, >= 1 always */
   int graphs;        /* 1 (default): replay each preconditioner application
                         from a captured CUDA graph after its first use; 0: launch
-                        every kernel directly */
+                        every kernel directly; 2 (IBRD_MIXED_REFINE): from the
+                        second solve of a configuration on, run the whole solve
+                        as one CUDA graph whose refinement steps, restart cycles
+                        and iterations are conditional nodes decided on the
+                        device (no host read until the solve ends; the same
+                        iterates as 1, bit for bit) */
   double inner_tol;  /* IBRD_MIXED_REFINE: relative residual each FP32 FGMRES
                         solve aims for, unless less is needed to reach tol
                         (1e-4; the FP32 rounding floor of the operator is

@@ -9,6 +9,7 @@
 #include <atomic>
 #include <chrono>
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -250,6 +251,20 @@ struct ibrd_grid_s {
   };
   std::map<std::string, std::vector<GraphEntry>> graphs;  // by configuration key
   cudaStream_t cap_stream = nullptr;
+  // whole refinement solves as one graph each (opts.graphs == 2), by key
+  struct SolveGraph {
+    cudaGraph_t graph = nullptr;     // kept: a batch graph embeds it as a child graph
+    cudaGraphExec_t exec = nullptr;
+    int seen = 0;
+    // launches one pass of each part adds (for the launch counter)
+    long long l_init = 0, l_ref = 0, l_cyc = 0, l_true = 0;
+    std::vector<long long> l_it;     // per Krylov index
+    long vc_per_app = 0, inner_per_app = 0;
+  };
+  std::map<std::string, SolveGraph> sgraphs;
+  void* gst = nullptr;               // device state of a graph solve
+  double* ghist = nullptr;           // device residual history of a graph solve
+  std::vector<cudaStream_t> cap_pool;  // streams that capture conditional bodies
   std::string err;
 };
 
@@ -499,13 +514,23 @@ struct LinOp {
   virtual void precond(const E* v, E* z) = 0;
   // everything a preconditioner application depends on besides v and z
   virtual std::string key() const = 0;
+  // device operands apply and residual read beyond the handle's own arrays
+  virtual std::string operands() const { return std::string(); }
 };
 
+void drop_batch_graphs_of(ibrd_grid g);
+
 void free_graphs(ibrd_grid g) {
+  drop_batch_graphs_of(g);  // a batch graph bakes in this handle's launches too
   for (auto& kv : g->graphs)
     for (auto& e : kv.second)
       if (e.exec) cudaGraphExecDestroy(e.exec);
   g->graphs.clear();
+  for (auto& kv : g->sgraphs) {
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+  }
+  g->sgraphs.clear();
 }
 
 // Apply the preconditioner z = P(v) for Krylov index j. The launch sequence
@@ -930,6 +955,520 @@ SolveResult refine(ibrd_grid g, LinOp<double>& op64, LinOp<float>& op32, const d
   return R;
 }
 
+// ---------------------------------------------------------------- device-terminated refinement
+// The refinement solve of `refine` as ONE CUDA graph whose loops end on the
+// device: the refinement steps and the FGMRES restart cycles are conditional
+// WHILE nodes, Krylov index j of a cycle is a conditional IF node (its kernels
+// keep the fixed addresses of V[j], Z[j], H[:, j]), and the solution update of
+// a cycle with k columns is body k of a SWITCH node. One-thread control kernels
+// after each Givens rotation, cycle and refinement step take the decisions the
+// host loop takes (same tests, same order) and set the conditions, so a solve
+// is one graph launch and one host read at the end. The state lives in device
+// memory (GState); the residual history goes to a device buffer.
+enum : int { GF_MET = 1, GF_BREAKDOWN = 2, GF_NONFINITE = 4, GF_TIMEOUT = 8 };
+constexpr int kGHistCap = 4096;
+
+// Parameters of a graph solve, rewritten before every launch (the head of GState).
+struct GParams {
+  double tol, inner_tol, floor_sq;
+  int max_iter, restart;
+};
+struct GState {
+  double tol, inner_tol, floor_sq;
+  int max_iter, restart;
+  double bnorm, rnorm, sigma, rel;         // refinement: ||b||, ||r||, scale, ||r|| / ||b||
+  double tol_in, bn_in, rel_in, res_last;  // inner FGMRES of the current step
+  double hist_scale;
+  int iters, it_in, max_in, stalled, status, refinements, cycles, trues, k, flags, hist_len, zero_x;
+  long long upd_launches;
+  int jcount[64];                          // iterations run at each Krylov index
+};
+
+__device__ __forceinline__ void gset(cudaGraphConditionalHandle h, bool v) { cudaGraphSetConditional(h, v ? 1u : 0u); }
+
+// after ||b||^2 (scal[S_BB]) and, with a guess, ||sigma r||^2 (scal[S_TMP2])
+__global__ void k_g_init(GState* st, const double* __restrict__ scal, int zero_guess, int phase,
+                         cudaGraphConditionalHandle h_ref) {
+  if (threadIdx.x != 0) return;
+  if (phase == 0) {
+    st->iters = st->stalled = st->status = st->refinements = st->cycles = st->trues = st->hist_len = 0;
+    st->zero_x = 0;
+    st->upd_launches = 0;
+    for (int j = 0; j < 64; ++j) st->jcount[j] = 0;
+    const double bn = sqrt(scal[S_BB]);
+    st->bnorm = bn;
+    st->sigma = ldexp(1.0, -ilogb(fmax(bn, 1e-300)));
+    st->rnorm = bn;
+    st->rel = 1.0;
+  }
+  const double bn = st->bnorm;
+  bool go = false;
+  if (!isfinite(bn)) {
+    st->status = IBRD_ERR_NONFINITE;
+  } else if (bn == 0.0) {
+    st->rel = 0.0;
+    st->zero_x = 1;
+  } else if (phase == 0 && !zero_guess) {
+    go = false;  // the residual of the guess decides (phase 1)
+  } else {
+    if (phase == 1) {
+      st->rnorm = sqrt(scal[S_TMP2]) / st->sigma;
+      st->rel = st->rnorm / bn;
+    }
+    const double rel = st->rel;
+    if (!isfinite(rel))
+      st->status = IBRD_ERR_NONFINITE;
+    else if (rel <= st->tol)
+      st->status = IBRD_OK;
+    else if (st->iters >= st->max_iter)
+      st->status = IBRD_ERR_NOT_CONVERGED;
+    else
+      go = true;
+  }
+  gset(h_ref, go);
+}
+
+// start of a refinement step: the inner FGMRES solves for sigma r (norm in S_TMP2)
+__global__ void k_g_ref_begin(GState* st, double* __restrict__ scal, cudaGraphConditionalHandle h_cyc) {
+  if (threadIdx.x != 0) return;
+  st->tol_in = fmax(st->inner_tol, 0.5 * st->tol / st->rel);
+  st->hist_scale = st->rel;
+  const double bn = sqrt(scal[S_TMP2]);
+  st->bn_in = bn;
+  scal[S_NORM] = bn;
+  st->max_in = st->max_iter - st->iters;
+  st->it_in = 0;
+  st->flags = 0;
+  st->rel_in = 1.0;
+  bool go = true;
+  if (!isfinite(bn)) {
+    st->flags |= GF_NONFINITE;
+    go = false;
+  } else if (bn == 0.0 || st->max_in <= 0) {
+    go = false;
+  }
+  gset(h_cyc, go);
+}
+
+struct IfHandles {
+  cudaGraphConditionalHandle h[61];
+};
+
+// start of a restart cycle: index 0 runs, the others wait for their predecessor
+__global__ void k_g_cyc_begin(GState* st, IfHandles hs, int m) {
+  if (threadIdx.x != 0) return;
+  st->k = 0;
+  st->cycles++;
+  st->flags &= ~(GF_MET | GF_BREAKDOWN);
+  for (int j = 0; j < m; ++j) gset(hs.h[j], j == 0);
+}
+
+// after the Givens rotation of index j: the host loop's per-iteration tests
+__global__ void k_g_it_ctrl(GState* st, const double* __restrict__ scal, double* __restrict__ hist, int j, int m,
+                            cudaGraphConditionalHandle h_next, cudaGraphConditionalHandle h_k) {
+  if (threadIdx.x != 0) return;
+  const double res = scal[S_RES], sq = scal[S_SQ], ww = scal[S_TMP];
+  unsigned long long wb;
+  const double wv = scal[S_WAIT];
+  memcpy(&wb, &wv, sizeof(wb));
+  const bool tiny = !(sq > st->floor_sq * ww) || sq <= 0.0;
+  st->k = j + 1;
+  st->iters++;
+  st->it_in++;
+  st->jcount[j]++;
+  st->res_last = res;
+  if (st->hist_len < kGHistCap) hist[st->hist_len++] = st->hist_scale * (res / st->bn_in);
+  if (wb != 0)
+    st->flags |= GF_TIMEOUT;
+  else if (!isfinite(res) || !isfinite(sq))
+    st->flags |= GF_NONFINITE;
+  else if (tiny)
+    st->flags |= GF_BREAKDOWN;
+  else if (res / st->bn_in <= st->tol_in)
+    st->flags |= GF_MET;
+  const bool bad = st->flags & (GF_NONFINITE | GF_TIMEOUT);
+  const bool cont = !(st->flags & (GF_MET | GF_BREAKDOWN)) && !bad && st->it_in < st->max_in && j + 1 < m;
+  if (j + 1 < m) gset(h_next, cont);
+  if (!cont) {
+    // the cycle ends here: its update uses k columns (none after a fault)
+    const int k = bad ? 0 : j + 1;
+    cudaGraphSetConditional(h_k, (unsigned)k);
+    st->upd_launches += k ? 1 + (k + 7) / 8 : 0;
+  }
+}
+
+// end of a cycle's update: trust the estimate after convergence or breakdown
+// (as the refinement's inner solves do), else form the true residual
+__global__ void k_g_cyc_ctrl1(GState* st, cudaGraphConditionalHandle h_true, cudaGraphConditionalHandle h_cyc) {
+  if (threadIdx.x != 0) return;
+  const int f = st->flags;
+  bool tr = false;
+  if (f & (GF_NONFINITE | GF_TIMEOUT)) {
+  } else if (f & (GF_MET | GF_BREAKDOWN)) {
+    st->rel_in = st->res_last / st->bn_in;
+  } else {
+    tr = true;
+  }
+  if (tr) st->trues++;
+  gset(h_true, tr);
+  if (!tr) gset(h_cyc, false);
+}
+
+__global__ void k_g_cyc_ctrl2(GState* st, const double* __restrict__ scal, cudaGraphConditionalHandle h_cyc) {
+  if (threadIdx.x != 0) return;
+  const double beta = sqrt(scal[S_TMP2]);
+  st->rel_in = beta / st->bn_in;
+  bool go = false;
+  if (!isfinite(st->rel_in))
+    st->flags |= GF_NONFINITE;
+  else
+    go = st->rel_in > st->tol_in && st->it_in < st->max_in;
+  gset(h_cyc, go);
+}
+
+// after the inner solve: stop on a fault, else update x
+__global__ void k_g_upd_gate(GState* st, cudaGraphConditionalHandle h_upd, cudaGraphConditionalHandle h_ref) {
+  if (threadIdx.x != 0) return;
+  const int f = st->flags;
+  const bool bad = f & (GF_NONFINITE | GF_TIMEOUT);
+  if (bad) {
+    st->status = (f & GF_TIMEOUT) ? IBRD_ERR_TIMEOUT : IBRD_ERR_NONFINITE;
+    gset(h_ref, false);
+  }
+  gset(h_upd, !bad);
+}
+
+__global__ void k_g_sigma(GState* st) {
+  if (threadIdx.x != 0) return;
+  st->sigma = ldexp(1.0, -ilogb(fmax(st->rnorm * fmax(st->rel_in, 1e-7), 1e-300)));
+}
+
+__global__ void k_g_ref_ctrl(GState* st, const double* __restrict__ scal, cudaGraphConditionalHandle h_ref) {
+  if (threadIdx.x != 0) return;
+  st->refinements++;
+  const double rn = sqrt(scal[S_TMP2]) / st->sigma;
+  st->stalled = (rn > 0.5 * st->rnorm) ? st->stalled + 1 : 0;
+  st->rnorm = rn;
+  st->rel = rn / st->bnorm;
+  bool go = false;
+  if (!isfinite(st->rel))
+    st->status = IBRD_ERR_NONFINITE;
+  else if (st->rel <= st->tol)
+    st->status = IBRD_OK;
+  else if (st->iters >= st->max_iter || st->stalled >= 3)
+    st->status = IBRD_ERR_NOT_CONVERGED;
+  else
+    go = true;
+  gset(h_ref, go);
+}
+
+// Stream capture into conditional bodies: a conditional node is added after
+// the work captured so far on g->s; each body is captured on a stream of the
+// handle's pool (one per nesting depth) with g->s pointing at it.
+struct GCapture {
+  ibrd_grid g;
+  int depth = 0;
+  long long* counter;  // launch counter of the part being captured
+  cudaStream_t stream(int d) {
+    while ((int)g->cap_pool.size() <= d) {
+      cudaStream_t st = nullptr;
+      IBRD_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+      g->cap_pool.push_back(st);
+    }
+    return g->cap_pool[d];
+  }
+  cudaGraph_t current_graph() {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t graph = nullptr;
+    IBRD_CUDA(cudaStreamGetCaptureInfo(g->s, &cs, nullptr, &graph, nullptr, nullptr, nullptr));
+    if (cs != cudaStreamCaptureStatusActive) throw CudaError{cudaErrorStreamCaptureInvalidated, "graph solve capture"};
+    return graph;
+  }
+  cudaGraphConditionalHandle handle() {
+    cudaGraphConditionalHandle h;
+    IBRD_CUDA(cudaGraphConditionalHandleCreate(&h, current_graph(), 0, 0));
+    return h;
+  }
+  template <typename F>
+  void conditional(cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type, int nbody, F&& fill) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t graph = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* ed = nullptr;
+    size_t nd = 0;
+    IBRD_CUDA(cudaStreamGetCaptureInfo(g->s, &cs, nullptr, &graph, &deps, &ed, &nd));
+    cudaGraphNodeParams p{};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = type;
+    p.conditional.size = (unsigned)nbody;
+    cudaGraphNode_t node;
+    IBRD_CUDA(cudaGraphAddNode(&node, graph, deps, ed, nd, &p));
+    IBRD_CUDA(cudaStreamUpdateCaptureDependencies(g->s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    cudaStream_t outer = g->s;
+    ++depth;
+    for (int b = 0; b < nbody; ++b) {
+      cudaStream_t sb = stream(depth);
+      IBRD_CUDA(cudaStreamBeginCaptureToGraph(sb, p.conditional.phGraph_out[b], nullptr, nullptr, 0,
+                                              cudaStreamCaptureModeRelaxed));
+      g->s = sb;
+      try {
+        fill(b);
+      } catch (...) {
+        cudaGraph_t dummy;
+        cudaStreamEndCapture(sb, &dummy);
+        g->s = outer;
+        --depth;
+        throw;
+      }
+      cudaGraph_t out = nullptr;
+      IBRD_CUDA(cudaStreamEndCapture(sb, &out));
+      g->s = outer;
+    }
+    --depth;
+  }
+};
+
+// Record a refinement solve (b, x as in `refine`) onto g->s, which is being
+// captured; SG receives the launch counts of its parts.
+void capture_refine(ibrd_grid g, LinOp<double>& op64, LinOp<float>& op32, const double* b, double* x, size_t n,
+                    const ibrd_solve_opts& o, bool zero_guess, ibrd_grid_s::SolveGraph& SG) {
+  Profiler& p = g->prof;
+  const int m = std::max(1, o.restart);
+  const size_t ld = ensure_krylov<float>(g, n, m);
+  const int ldh = m + 1;
+  float* V = reinterpret_cast<float*>(g->V);
+  float* Z = reinterpret_cast<float*>(g->Z);
+  GState* st = reinterpret_cast<GState*>(g->gst);
+  double* sc = g->scal;
+  GCapture C{g, 0, nullptr};
+  const long long l00 = p.launches;
+  long long c00[P_NCLASS];
+  double b00[P_NCLASS];
+  for (int c = 0; c < P_NCLASS; ++c) {
+    c00[c] = p.count[c];
+    b00[c] = p.bytes[c];
+  }
+  const long v00 = g->vcycles, i00 = g->inner;
+  auto mark = [&]() { return p.launches; };  // counts library launches (the control kernels add 1 each below)
+  {
+    cudaGraphConditionalHandle h_ref = C.handle();
+    long long t0 = mark();
+    launch_dot<double>(b, b, n, g->partial, sc + S_BB, 1.0, g->s);
+    k_g_init<<<1, 32, 0, g->s>>>(st, sc, zero_guess ? 1 : 0, 0, h_ref);
+    if (zero_guess) {
+      IBRD_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, g->s));
+      launch_convert_sq(b, g->ir_r32, n, &st->sigma, g->partial, sc + S_TMP2, g->s);
+    } else {
+      op64.residual(b, x, g->ir_r);
+      launch_convert_sq(g->ir_r, g->ir_r32, n, &st->sigma, g->partial, sc + S_TMP2, g->s);
+      k_g_init<<<1, 32, 0, g->s>>>(st, sc, 0, 1, h_ref);
+    }
+    SG.l_init = mark() - t0 + (zero_guess ? 1 : 2);
+    C.conditional(h_ref, cudaGraphCondTypeWhile, 1, [&](int) {
+      cudaGraphConditionalHandle h_cyc = C.handle(), h_upd = C.handle();
+      k_g_ref_begin<<<1, 32, 0, g->s>>>(st, sc, h_cyc);
+      IBRD_CUDA(cudaMemsetAsync(g->ir_d32, 0, sizeof(float) * n, g->s));
+      IBRD_CUDA(cudaMemcpyAsync(V, g->ir_r32, sizeof(float) * n, cudaMemcpyDeviceToDevice, g->s));
+      C.conditional(h_cyc, cudaGraphCondTypeWhile, 1, [&](int) {
+        IfHandles hs{};
+        for (int j = 0; j < m; ++j) hs.h[j] = C.handle();
+        cudaGraphConditionalHandle h_k = C.handle(), h_true = C.handle();
+        const long long c0 = mark();
+        k_g_cyc_begin<<<1, 32, 0, g->s>>>(st, hs, m);
+        launch_scale_by_inv<float>(V, V, n, sc + S_NORM, 1.0, g->s);
+        prof_begin(P_SMALL, g->s);
+        k_set_gvec<<<1, 64, 0, g->s>>>(g->gvec, m, sc + S_NORM);
+        prof_end(P_SMALL, g->s, "set_gvec");
+        SG.l_cyc = mark() - c0 + 2;  // with the cycle's two control kernels
+        SG.l_it.assign(m, 0);
+        for (int j = 0; j < m; ++j) {
+          C.conditional(hs.h[j], cudaGraphCondTypeIf, 1, [&](int) {
+            const long long a0 = mark();
+            const long va = g->vcycles, ia = g->inner;
+            float* vj = V + (size_t)j * ld;
+            float* zj = Z + (size_t)j * ld;
+            float* w = V + (size_t)(j + 1) * ld;
+            op32.precond(vj, zj);
+            if (j == 0) {
+              SG.vc_per_app = g->vcycles - va;
+              SG.inner_per_app = g->inner - ia;
+            }
+            op32.apply(zj, w);
+            orthogonalize<float>(g, j, n, ld, ldh, o.reorth_eta);
+            double* hcol = g->H + (size_t)j * ldh;
+            launch_sqrt_scalar(sc + S_SQ, hcol + j + 1, g->s);
+            launch_scale_by_inv<float>(w, w, n, hcol + j + 1, 1.0, g->s);
+            launch_givens(g->H, ldh, j, g->cs, g->sn, g->gvec, sc + S_RES, g->s);
+            k_g_it_ctrl<<<1, 32, 0, g->s>>>(st, sc, g->ghist, j, m, j + 1 < m ? hs.h[j + 1] : hs.h[j], h_k);
+            SG.l_it[j] = mark() - a0 + 1;
+          });
+        }
+        C.conditional(h_k, cudaGraphCondTypeSwitch, m + 1, [&](int k) {
+          if (k == 0) return;
+          launch_backsolve(g->H, ldh, k, g->gvec, g->yv, g->s);
+          for (int g0 = 0; g0 < k; g0 += kDotGroup) {
+            const int mm = std::min(kDotGroup, k - g0);
+            launch_multi_axpy(g->ir_d32, Z + (size_t)g0 * ld, ld, mm, g->yv + g0, 1.0, n, nullptr, g->s);
+          }
+        });
+        k_g_cyc_ctrl1<<<1, 32, 0, g->s>>>(st, h_true, h_cyc);
+        C.conditional(h_true, cudaGraphCondTypeIf, 1, [&](int) {
+          const long long q0 = mark();
+          op32.residual(g->ir_r32, g->ir_d32, V);
+          launch_dot<float>(V, V, n, g->partial, sc + S_TMP2, 1.0, g->s);
+          launch_sqrt_scalar(sc + S_TMP2, sc + S_NORM, g->s);
+          k_g_cyc_ctrl2<<<1, 32, 0, g->s>>>(st, sc, h_cyc);
+          SG.l_true = mark() - q0 + 1;
+        });
+      });
+      k_g_upd_gate<<<1, 32, 0, g->s>>>(st, h_upd, h_ref);
+      C.conditional(h_upd, cudaGraphCondTypeIf, 1, [&](int) {
+        const long long u0 = mark();
+        launch_add_divided(&st->sigma, g->ir_d32, x, n, g->s);
+        op64.residual(b, x, g->ir_r);
+        k_g_sigma<<<1, 32, 0, g->s>>>(st);
+        launch_convert_sq(g->ir_r, g->ir_r32, n, &st->sigma, g->partial, sc + S_TMP2, g->s);
+        k_g_ref_ctrl<<<1, 32, 0, g->s>>>(st, sc, h_ref);
+        // a refinement step: its begin and gate kernels, this body and its two control kernels
+        SG.l_ref = mark() - u0 + 4;
+      });
+    });
+  }
+  // the capture counted launches and V-cycles that did not run
+  p.launches = l00;
+  for (int c = 0; c < P_NCLASS; ++c) {
+    p.count[c] = c00[c];
+    p.bytes[c] = b00[c];
+  }
+  g->vcycles = v00;
+  g->inner = i00;
+}
+
+void ensure_graph_state(ibrd_grid g) {
+  if (!g->gst) g->gst = dalloc<unsigned char>(sizeof(GState));
+  if (!g->ghist) g->ghist = dalloc<double>(kGHistCap);
+  if (!g->cap_stream) IBRD_CUDA(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
+}
+
+// Build the graph of one refinement solve.
+void build_refine_graph(ibrd_grid g, LinOp<double>& op64, LinOp<float>& op32, const double* b, double* x,
+                        size_t n, const ibrd_solve_opts& o, bool zero_guess, ibrd_grid_s::SolveGraph& SG) {
+  ensure_graph_state(g);
+  cudaStream_t user = g->s;
+  g->s = g->cap_stream;
+  cudaGraph_t graph = nullptr;
+  IBRD_CUDA(cudaStreamBeginCapture(g->s, cudaStreamCaptureModeRelaxed));
+  try {
+    capture_refine(g, op64, op32, b, x, n, o, zero_guess, SG);
+  } catch (...) {
+    cudaGraph_t dummy = nullptr;
+    cudaStreamEndCapture(g->s, &dummy);
+    if (dummy) cudaGraphDestroy(dummy);
+    g->s = user;
+    throw;
+  }
+  const cudaError_t ec = cudaStreamEndCapture(g->s, &graph);
+  g->s = user;
+  if (ec != cudaSuccess) throw CudaError{ec, "cudaStreamEndCapture (graph solve)"};
+  SG.graph = graph;
+  const cudaError_t ei = cudaGraphInstantiate(&SG.exec, graph, 0);
+  if (ei != cudaSuccess) {
+    SG.exec = nullptr;
+    throw CudaError{ei, "cudaGraphInstantiate (graph solve)"};
+  }
+}
+
+// Device state to host after a graph solve; fills R, the history and the
+// handle's counters.
+SolveResult finish_refine_graph(ibrd_grid g, const ibrd_grid_s::SolveGraph& SG, double* x, size_t n,
+                                History& hist) {
+  GState hs;
+  IBRD_CUDA(cudaMemcpyAsync(&hs, g->gst, sizeof(GState), cudaMemcpyDeviceToHost, g->s));
+  IBRD_CUDA(cudaStreamSynchronize(g->s));
+  SolveResult R;
+  R.st = (ibrd_status)hs.status;
+  R.iters = hs.iters;
+  R.rel = hs.rel;
+  if (hs.zero_x) IBRD_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, g->s));
+  const int nh = std::min(hs.hist_len, kGHistCap);
+  if (hist.buf && nh > 0) {
+    std::vector<double> hb(nh);
+    IBRD_CUDA(cudaMemcpy(hb.data(), g->ghist, sizeof(double) * nh, cudaMemcpyDeviceToHost));
+    for (double v : hb) {
+      if (hist.len < hist.cap) hist.buf[hist.len] = v;
+      hist.len++;
+    }
+    hist.len = std::min(hist.len, hist.cap);
+  }
+  g->refinements += hs.refinements;
+  g->vcycles += (long)hs.iters * SG.vc_per_app;
+  g->inner += (long)hs.iters * SG.inner_per_app;
+  long long launches = 1 + SG.l_init + (long long)hs.refinements * SG.l_ref + (long long)hs.cycles * SG.l_cyc +
+                       (long long)hs.trues * SG.l_true + hs.upd_launches;
+  for (int j = 0; j < (int)SG.l_it.size() && j < 64; ++j) launches += (long long)hs.jcount[j] * SG.l_it[j];
+  g->prof.launches += launches;
+  return R;
+}
+
+// Everything baked into the graph of a refinement solve.
+std::string refine_graph_key(ibrd_grid g, LinOp<double>& op64, LinOp<float>& op32, const double* b, double* x,
+                             size_t n, const ibrd_solve_opts& o, bool zero_guess) {
+  const BlobSet& bl = g->blobs;
+  char sig[640];
+  std::snprintf(sig, sizeof sig,
+                "|G|%d|%d|%p|%p|%p|%p|%p|%p|%p|%p|%zu|%p|%p|%zu|%d|%d|%d|%.17g|%.17g|%.17g|%p|%p|%p|%p|%p|%u",
+                bl.n, bl.n_cells, (void*)g->V, (void*)g->Z, (void*)bl.idx, (void*)bl.w32, (void*)bl.w64,
+                (void*)bl.cells, (void*)bl.cell_tile, (void*)bl.tile_blobs, g->vlen, (const void*)b, (void*)x, n,
+                o.restart, o.max_iter, zero_guess ? 1 : 0, o.tol, o.inner_tol, o.reorth_eta, (void*)g->ir_r,
+                (void*)g->ir_r32, (void*)g->ir_d32, g->gst, (void*)g->ghist, g->tune.wait_limit);
+  return op32.key() + op64.key() + op32.operands() + op64.operands() + sig;
+}
+
+// `refine` as one graph launch (built on the second solve of a configuration,
+// when every lazy allocation has happened); null when the host loop should run.
+ibrd_grid_s::SolveGraph* refine_graph_for(ibrd_grid g, LinOp<double>& op64, LinOp<float>& op32, const double* b,
+                                          double* x, size_t n, const ibrd_solve_opts& o, bool zero_guess) {
+  if (g->prof.timing || o.restart > 61) return nullptr;
+  ensure_krylov<float>(g, n, std::max(1, o.restart));  // grows (and drops graphs) only before a key is taken
+  ensure_graph_state(g);
+  const std::string key = refine_graph_key(g, op64, op32, b, x, n, o, zero_guess);
+  if (g->sgraphs.size() > 8 && !g->sgraphs.count(key)) free_graphs(g);
+  auto& SG = g->sgraphs[key];
+  if (SG.exec) return &SG;
+  if (SG.seen == 0) {
+    SG.seen = 1;
+    return nullptr;
+  }
+  build_refine_graph(g, op64, op32, b, x, n, o, zero_guess, SG);
+  return &SG;
+}
+
+static_assert(offsetof(GState, restart) == offsetof(GParams, restart) && sizeof(GParams) <= offsetof(GState, bnorm),
+              "GParams is the head of GState");
+
+// The parameters the control kernels read (before every launch of a solve graph).
+void set_graph_params(ibrd_grid g, const ibrd_solve_opts& o) {
+  GParams prm{o.tol, o.inner_tol, 1e-12, o.max_iter, o.restart};
+  IBRD_CUDA(cudaMemcpyAsync(g->gst, &prm, sizeof(GParams), cudaMemcpyHostToDevice, g->s));
+}
+
+// The refinement solve: one graph launch when opts.graphs == 2 and its graph
+// exists (from the second solve of a configuration on), else the host loop.
+SolveResult run_refine(ibrd_grid g, LinOp<double>& op64, LinOp<float>& op32, const double* b, double* x, size_t n,
+                       const ibrd_solve_opts& o, bool zero_guess, History& hist) {
+  if (o.graphs == 2) {
+    if (g->ir_cap >= n) {
+      if (auto* SG = refine_graph_for(g, op64, op32, b, x, n, o, zero_guess)) {
+        set_graph_params(g, o);
+        IBRD_CUDA(cudaGraphLaunch(SG->exec, g->s));
+        return finish_refine_graph(g, *SG, x, n, hist);
+      }
+    }
+  }
+  return refine(g, op64, op32, b, x, n, o, zero_guess, hist);
+}
+
 // ---------------------------------------------------------------- workspaces
 template <typename T>
 T* pfield(ibrd_grid g, int i);
@@ -987,6 +1526,11 @@ struct ReactionOp : LinOp<E> {
     char buf[160];
     std::snprintf(buf, sizeof buf, "reaction|%zu|%zu|%d|%d|%d|%.17g", sizeof(T), sizeof(E), o.mg_cycles, o.nu1,
                   o.nu2, sigma);
+    return buf;
+  }
+  std::string operands() const override {
+    char buf[40];
+    std::snprintf(buf, sizeof buf, "|k%p", (const void*)kappa);
     return buf;
   }
   void apply(const E* x, E* y) override {
@@ -1546,6 +2090,404 @@ void report(ibrd_grid g, const double* c, const double* lam_or_null, const doubl
   info->a_L = info->rate_K / (4.0 * 3.14159265358979323846 * g->chi);
 }
 
+// ---------------------------------------------------------------- solve set-up and report
+// Checks and set-up of a reaction-limited solve; returns the preconditioner's
+// shift sigma (alpha, or sum(kappa) / V_Omega when alpha = 0, R5).
+double reaction_setup(ibrd_grid g, const double* kappa, const double* rhs, double* c, const ibrd_solve_opts& o) {
+  const int N = g->blobs.n;
+  if (!rhs || !c || (N > 0 && !kappa)) throw ArgError{IBRD_ERR_ARG, "null pointer"};
+  g->vcycles = 0;
+  g->inner = 0;
+  g->reorths = 0;
+  g->refinements = 0;
+  ensure_nvec(g, o.schur_inner);
+  double sigma = g->alpha;
+  if (N > 0) {
+    IBRD_CUDA(cudaMemsetAsync(g->dflag, 0, sizeof(int), g->s));
+    prof_begin(P_SETUP, g->s);
+    k_check_rates<<<std::min(1024, (N + 255) / 256), 256, 0, g->s>>>(kappa, N, g->dflag);
+    prof_end(P_SETUP, g->s, "check_rates");
+    int flag = 0;
+    IBRD_CUDA(cudaMemcpyAsync(&flag, g->dflag, sizeof(int), cudaMemcpyDeviceToHost, g->s));
+    launch_sum<double>(kappa, N, g->partial, g->scal + S_TMP, 1.0, g->s);
+    const double ksum = host_scalar(g, S_TMP);
+    if (flag) throw ArgError{IBRD_ERR_NONFINITE, "kappa must be finite and >= 0"};
+    if (g->alpha == 0.0) sigma = ksum / ((double)g->d.n() * g->h * g->h * g->h);
+  }
+  if (!(sigma > 0.0)) throw ArgError{IBRD_ERR_ARG, "steady reaction system needs some kappa > 0"};
+  return sigma;
+}
+
+void reaction_report(ibrd_grid g, const double* kappa, double* c, SolveResult& R, ibrd_solve_info* info, double t0,
+                     const History& hist) {
+  if (info) info->history_len = hist.len;
+  report(g, c, nullptr, kappa, info);
+  if (take_wait_flag(g)) R.st = IBRD_ERR_TIMEOUT;
+  fill_info(info, R, g, t0);
+  if (info) info->precond = -1;
+  if (R.st != IBRD_OK) g->err = std::string("ibrd_solve_reaction: ") + ibrd_status_string(R.st);
+}
+
+// Checks and set-up of a saddle-point solve: [g; f] into bs, the guess or the
+// warm start into xs, gamma of the diagonal preconditioner. Returns whether
+// the solve starts from zero.
+bool saddle_setup(ibrd_grid g, const double* rhs, const double* f, double* c, double* lambda,
+                  const ibrd_solve_opts& o) {
+  const int N = g->blobs.n;
+  if (N < 1) throw ArgError{IBRD_ERR_STATE, "saddle solve needs at least one blob"};
+  if (!rhs || !c || !lambda) throw ArgError{IBRD_ERR_ARG, "null pointer"};
+  g->vcycles = 0;
+  g->inner = 0;
+  g->reorths = 0;
+  g->refinements = 0;
+  ensure_nvec(g, o.schur_inner);
+  const size_t nc = g->d.n();
+  const size_t n = nc + N;
+  if (g->xs_cap < n) {
+    cudaFree(g->xs);
+    cudaFree(g->bs);
+    g->xs = g->bs = nullptr;
+    g->xs = dalloc<double>(n);
+    g->bs = dalloc<double>(n);
+    g->xs_cap = n;
+  }
+  IBRD_CUDA(cudaMemcpyAsync(g->bs, rhs, sizeof(double) * nc, cudaMemcpyDeviceToDevice, g->s));
+  if (f)
+    IBRD_CUDA(cudaMemcpyAsync(g->bs + nc, f, sizeof(double) * N, cudaMemcpyDeviceToDevice, g->s));
+  else
+    IBRD_CUDA(cudaMemsetAsync(g->bs + nc, 0, sizeof(double) * N, g->s));
+  if (o.use_guess) {
+    IBRD_CUDA(cudaMemcpyAsync(g->xs, c, sizeof(double) * nc, cudaMemcpyDeviceToDevice, g->s));
+    IBRD_CUDA(cudaMemcpyAsync(g->xs + nc, lambda, sizeof(double) * N, cudaMemcpyDeviceToDevice, g->s));
+  }
+  const bool warm = !o.use_guess && o.lambda_guess != IBRD_GUESS_NONE;
+  if (warm) {
+    if (o.lambda_guess == IBRD_GUESS_GIVEN)
+      IBRD_CUDA(cudaMemcpyAsync(g->xs + nc, lambda, sizeof(double) * N, cudaMemcpyDeviceToDevice, g->s));
+    if (o.lambda_guess == IBRD_GUESS_PENALTY)
+      saddle_penalty_start(g, o, g->bs, g->xs);
+    else if (o.precision == IBRD_FP64)
+      saddle_warm_start<double>(g, o, g->bs, g->xs, o.lambda_guess, o.warm_cycles);
+    else
+      saddle_warm_start<float>(g, o, g->bs, g->xs, o.lambda_guess, o.warm_cycles);
+  }
+  if (o.precond == IBRD_PRECOND_DIAG && !g->gamma_valid) {
+    // gamma's V-cycles are set-up, not part of this solve's count
+    const long v = g->vcycles;
+    g->gamma_diag = compute_gamma(g, o);
+    g->gamma_valid = true;
+    g->vcycles = v;
+  }
+  return !o.use_guess && !warm;
+}
+
+void saddle_report(ibrd_grid g, double* c, double* lambda, SolveResult& R, ibrd_solve_info* info, double t0,
+                   const ibrd_solve_opts& o, const History& hist) {
+  const size_t nc = g->d.n();
+  const int N = g->blobs.n;
+  if (info) info->history_len = hist.len;
+  IBRD_CUDA(cudaMemcpyAsync(c, g->xs, sizeof(double) * nc, cudaMemcpyDeviceToDevice, g->s));
+  IBRD_CUDA(cudaMemcpyAsync(lambda, g->xs + nc, sizeof(double) * N, cudaMemcpyDeviceToDevice, g->s));
+  report(g, c, lambda, nullptr, info);
+  if (take_wait_flag(g)) R.st = IBRD_ERR_TIMEOUT;
+  fill_info(info, R, g, t0);
+  if (info) info->precond = o.precond;
+  if (R.st != IBRD_OK) g->err = std::string("ibrd_solve_saddle: ") + ibrd_status_string(R.st);
+}
+
+// ---------------------------------------------------------------- a batch as one graph
+// Refinement-mode solves of many handles (opts.graphs == 2) recorded into ONE
+// graph: after each problem's set-up (on the calling thread, in order), one
+// capture session forks a capture stream per problem from an origin stream and
+// records that problem's whole device-terminated solve on it, so the problems
+// are independent branches of one graph, launched once. A batch of a given
+// configuration runs its problems' host loops the first time (lazy
+// allocations), builds the graph the second time and replays it afterwards.
+struct BatchGraph {
+  cudaGraphExec_t exec = nullptr;
+  std::vector<ibrd_grid_s::SolveGraph> parts;  // launch counts of each problem's part
+  std::vector<ibrd_grid> grids;
+  int seen = 0;
+};
+std::mutex g_batch_mu;
+std::map<std::string, BatchGraph> g_batch;
+cudaStream_t g_batch_origin[64] = {};
+
+void drop_batch_graphs_of(ibrd_grid g) {
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  for (auto it = g_batch.begin(); it != g_batch.end();) {
+    if (std::find(it->second.grids.begin(), it->second.grids.end(), g) != it->second.grids.end()) {
+      if (it->second.exec) cudaGraphExecDestroy(it->second.exec);
+      it = g_batch.erase(it);
+    } else {
+      ++it;
+    }
+  }
+}
+
+struct BatchItem {
+  int kind;  // IBRD_SOLVE_REACTION or IBRD_SOLVE_SADDLE
+  ibrd_grid g;
+  const double* kappa;
+  const double* rhs;
+  const double* f;
+  double* c;
+  double* lambda;
+  ibrd_solve_info* info;
+  // set up by the batch
+  ibrd_solve_opts o{};
+  double t0 = 0.0;
+  bool zero_start = true;
+  size_t n = 0;
+  const double* b = nullptr;
+  double* x = nullptr;
+  std::unique_ptr<LinOp<double>> op64;
+  std::unique_ptr<LinOp<float>> op32;
+  History hist;
+  SolveResult R;
+};
+
+// Whether every item can run in a batch graph: refinement mode with
+// opts.graphs == 2, one device, no per-launch timing.
+bool batch_graph_eligible(const std::vector<BatchItem>& items, const ibrd_solve_opts* opts) {
+  if (items.empty() || !opts || opts->graphs != 2) return false;
+  const int dev = items[0].g->dev;
+  for (const auto& it : items) {
+    const int prec = opts->precision < 0 ? it.g->precision : opts->precision;
+    if (prec != IBRD_MIXED_REFINE || it.g->dev != dev || it.g->prof.timing || opts->restart > 61 ||
+        it.g->d.n() > (size_t(1) << 31))
+      return false;
+  }
+  return true;
+}
+
+// Set-up of one item (as the single-problem entry points do before solving).
+void batch_setup(BatchItem& it, const ibrd_solve_opts* opts) {
+  ibrd_grid g = it.g;
+  it.t0 = now_s();
+  it.o = resolve_opts(g, opts);
+  if (it.info) {
+    it.hist.buf = it.info->residual_history;
+    it.hist.cap = it.info->history_cap;
+  }
+  if (it.kind == IBRD_SOLVE_REACTION) {
+    const double sigma = reaction_setup(g, it.kappa, it.rhs, it.c, it.o);
+    it.op64.reset(new ReactionOp<double>(g, it.kappa, sigma, it.o));
+    it.op32.reset(new ReactionOp<float>(g, it.kappa, sigma, it.o));
+    it.b = it.rhs;
+    it.x = it.c;
+    it.n = g->d.n();
+    it.zero_start = !it.o.use_guess;
+  } else {
+    it.zero_start = saddle_setup(g, it.rhs, it.f, it.c, it.lambda, it.o);
+    it.op64.reset(new SaddleOp<double>(g, it.o, it.o.zeta, it.o.xi));
+    it.op32.reset(new SaddleOp<float>(g, it.o, it.o.zeta, it.o.xi));
+    it.b = g->bs;
+    it.x = g->xs;
+    it.n = g->d.n() + g->blobs.n;
+  }
+  if (g->ir_cap < it.n) {
+    // the refinement's residual fields (refine allocates them on first use)
+    cudaFree(g->ir_r);
+    cudaFree(g->ir_r32);
+    cudaFree(g->ir_d32);
+    g->ir_r = nullptr;
+    g->ir_r32 = g->ir_d32 = nullptr;
+    g->ir_r = dalloc<double>(it.n);
+    g->ir_r32 = dalloc<float>(it.n);
+    g->ir_d32 = dalloc<float>(it.n);
+    g->ir_cap = it.n;
+  }
+  ensure_krylov<float>(g, it.n, std::max(1, it.o.restart));
+  ensure_graph_state(g);
+}
+
+void batch_report(BatchItem& it) {
+  if (it.kind == IBRD_SOLVE_REACTION)
+    reaction_report(it.g, it.kappa, it.c, it.R, it.info, it.t0, it.hist);
+  else
+    saddle_report(it.g, it.c, it.lambda, it.R, it.info, it.t0, it.o, it.hist);
+}
+
+// Returns false when the items must run the per-problem path instead (not
+// eligible, or a set-up failed: nothing was launched for any item then).
+// fn(i) for i in [0, count) on up to `threads` host threads (the calling one included)
+template <typename F>
+void parallel_for(int count, int threads, F&& fn) {
+  if (threads <= 0) threads = 16;
+  threads = std::max(1, std::min(std::min(threads, 64), count));
+  std::atomic<int> next{0};
+  auto worker = [&]() {
+    for (;;) {
+      const int i = next.fetch_add(1, std::memory_order_relaxed);
+      if (i >= count) return;
+      fn(i);
+    }
+  };
+  std::vector<std::thread> pool;
+  try {
+    for (int t = 1; t < threads; ++t) pool.emplace_back(worker);
+  } catch (...) {
+  }
+  worker();
+  for (auto& th : pool) th.join();
+}
+
+bool batch_graph_solve(std::vector<BatchItem>& items, const ibrd_solve_opts* opts, std::vector<ibrd_status>& st,
+                       int threads) {
+  if (!batch_graph_eligible(items, opts)) return false;
+  const int dev = items[0].g->dev;
+  DeviceGuard dg(dev);
+  // set-up of every problem (each with its host reads) on the worker threads
+  std::atomic<bool> setup_ok{true};
+  parallel_for((int)items.size(), threads, [&](int i) {
+    BatchItem& it = items[i];
+    DeviceGuard dgi(it.g->dev);
+    ProfScope ps(&it.g->prof, &it.g->tune);
+    try {
+      batch_setup(it, opts);
+    } catch (...) {
+      setup_ok = false;
+    }
+  });
+  if (!setup_ok) return false;
+  std::string bkey;
+  for (auto& it : items) {
+    char hb[48];
+    std::snprintf(hb, sizeof hb, "#%p#%d#", (void*)it.g, it.kind);
+    bkey += hb + refine_graph_key(it.g, *it.op64, *it.op32, it.b, it.x, it.n, it.o, it.zero_start);
+  }
+  BatchGraph* B = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    if (g_batch.size() > 16 && !g_batch.count(bkey)) {
+      for (auto& kv : g_batch)
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+      g_batch.clear();
+    }
+    B = &g_batch[bkey];
+  }
+  if (!B->exec && B->seen == 0) {
+    // first encounter: the host loops, concurrently on the problems' streams
+    B->seen = 1;
+    B->grids.clear();
+    for (auto& it : items) B->grids.push_back(it.g);
+    std::vector<ibrd_grid> gs;
+    for (auto& it : items) gs.push_back(it.g);
+    run_batch((int)items.size(), gs.data(), threads, [&](int i) {
+      BatchItem& it = items[i];
+      DeviceGuard dgi(it.g->dev);
+      ProfScope ps(&it.g->prof, &it.g->tune);
+      try {
+        it.R = refine(it.g, *it.op64, *it.op32, it.b, it.x, it.n, it.o, it.zero_start, it.hist);
+        batch_report(it);
+        st[i] = it.R.st;
+      } catch (const ArgError& e) {
+        st[i] = fail(it.g, e.code, e.msg);
+      } catch (const CudaError& e) {
+        cudaGetLastError();
+        st[i] = fail(it.g, IBRD_ERR_CUDA, std::string("batch solve: ") + e.what);
+      }
+      if (it.info) it.info->status = st[i];
+      return st[i];
+    });
+    return true;
+  }
+  if (!g_batch_origin[dev & 63]) IBRD_CUDA(cudaStreamCreateWithFlags(&g_batch_origin[dev & 63], cudaStreamNonBlocking));
+  cudaStream_t origin = g_batch_origin[dev & 63];
+  std::vector<cudaEvent_t> evs(items.size() + 1, nullptr);
+  auto cleanup_events = [&]() {
+    for (auto e : evs)
+      if (e) cudaEventDestroy(e);
+  };
+  for (auto& e : evs) IBRD_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  try {
+    if (!B->exec) {
+      // build: every problem's solve on its own capture stream, forked from the origin
+      B->parts.assign(items.size(), ibrd_grid_s::SolveGraph{});
+      cudaGraph_t graph = nullptr;
+      IBRD_CUDA(cudaStreamBeginCapture(origin, cudaStreamCaptureModeRelaxed));
+      try {
+        IBRD_CUDA(cudaEventRecord(evs[0], origin));
+        for (size_t i = 0; i < items.size(); ++i) {
+          BatchItem& it = items[i];
+          ProfScope ps(&it.g->prof, &it.g->tune);
+          cudaStream_t user = it.g->s;
+          it.g->s = it.g->cap_stream;
+          try {
+            IBRD_CUDA(cudaStreamWaitEvent(it.g->s, evs[0], 0));
+            capture_refine(it.g, *it.op64, *it.op32, it.b, it.x, it.n, it.o, it.zero_start, B->parts[i]);
+            IBRD_CUDA(cudaEventRecord(evs[i + 1], it.g->s));
+            IBRD_CUDA(cudaStreamWaitEvent(origin, evs[i + 1], 0));
+          } catch (...) {
+            it.g->s = user;
+            throw;
+          }
+          it.g->s = user;
+        }
+      } catch (...) {
+        cudaGraph_t dummy = nullptr;
+        cudaStreamEndCapture(origin, &dummy);
+        if (dummy) cudaGraphDestroy(dummy);
+        throw;
+      }
+      IBRD_CUDA(cudaStreamEndCapture(origin, &graph));
+      const cudaError_t ei = cudaGraphInstantiate(&B->exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ei != cudaSuccess) {
+        B->exec = nullptr;
+        throw CudaError{ei, "cudaGraphInstantiate (batch graph)"};
+      }
+    }
+    // launch: after every problem's set-up on its stream; each stream then
+    // waits for the graph
+    for (size_t i = 0; i < items.size(); ++i) {
+      BatchItem& it = items[i];
+      set_graph_params(it.g, it.o);
+      IBRD_CUDA(cudaEventRecord(evs[i + 1], it.g->s));
+      IBRD_CUDA(cudaStreamWaitEvent(origin, evs[i + 1], 0));
+    }
+    IBRD_CUDA(cudaGraphLaunch(B->exec, origin));
+    IBRD_CUDA(cudaEventRecord(evs[0], origin));
+    for (auto& it : items) IBRD_CUDA(cudaStreamWaitEvent(it.g->s, evs[0], 0));
+  } catch (...) {
+    cleanup_events();
+    throw;
+  }
+  cleanup_events();
+  // each problem's state and report (host reads) on the worker threads
+  parallel_for((int)items.size(), threads, [&](int i) {
+    BatchItem& it = items[i];
+    DeviceGuard dgi(it.g->dev);
+    ProfScope ps(&it.g->prof, &it.g->tune);
+    try {
+      it.R = finish_refine_graph(it.g, B->parts[i], it.x, it.n, it.hist);
+      batch_report(it);
+      st[i] = it.R.st;
+    } catch (const CudaError& e) {
+      cudaGetLastError();
+      st[i] = fail(it.g, IBRD_ERR_CUDA, std::string("batch solve: ") + e.what);
+    }
+    if (it.info) it.info->status = st[i];
+  });
+  return true;
+}
+
+bool batch_grids_ok(int count, const ibrd_grid* grids) {
+  if (!grids) return false;
+  std::vector<ibrd_grid> seen(grids, grids + count);
+  std::sort(seen.begin(), seen.end());
+  for (int i = 0; i < count; ++i)
+    if (!seen[i] || (i > 0 && seen[i] == seen[i - 1])) return false;
+  return true;
+}
+
+ibrd_status first_failure(const std::vector<ibrd_status>& st) {
+  for (auto v : st)
+    if (v != IBRD_OK) return v;
+  return IBRD_OK;
+}
+
 }  // namespace
 }  // namespace ibrd
 
@@ -1609,7 +2551,7 @@ void ibrd_grid_destroy(ibrd_grid g) {
   BlobSet& b = g->blobs;
   F(b.q); F(b.idx); F(b.w64); F(b.w32); F(b.tile_count); F(b.tile_offset); F(b.tile_cursor); F(b.tile_blobs);
   F(b.active); F(b.d_meta); F(b.cell_count); F(b.cell_offset); F(b.cells); F(b.cell_tile);
-  F(g->scal); F(g->partial); F(g->dflag);
+  F(g->scal); F(g->partial); F(g->dflag); F(g->gst); F(g->ghist);
   if (g->host) cudaFreeHost(g->host);
   F(g->V); F(g->Z); F(g->H); F(g->cs); F(g->sn); F(g->gvec); F(g->yv); F(g->hb2); F(g->xs); F(g->bs);
   F(g->ir_r); F(g->ir_r32); F(g->ir_d32);
@@ -1618,8 +2560,10 @@ void ibrd_grid_destroy(ibrd_grid g) {
   for (auto p : g->nv) F(p);
   F(g->U); F(g->Hs); F(g->scs); F(g->ssn); F(g->sg);
   for (auto e : g->prof.pool) cudaEventDestroy(e);
+  drop_batch_graphs_of(g);
   free_graphs(g);
   if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
+  for (auto st : g->cap_pool) cudaStreamDestroy(st);
   delete g;
 }
 
@@ -1767,27 +2711,7 @@ ibrd_status ibrd_solve_reaction(ibrd_grid g, const double* kappa, const double* 
   return guarded(g, "ibrd_solve_reaction", [&]() {
     const double t0 = now_s();
     const ibrd_solve_opts o = resolve_opts(g, opts);
-    const int N = g->blobs.n;
-    if (!rhs || !c || (N > 0 && !kappa)) throw ArgError{IBRD_ERR_ARG, "null pointer"};
-    g->vcycles = 0;
-    g->inner = 0;
-    g->reorths = 0;
-    g->refinements = 0;
-    ensure_nvec(g, o.schur_inner);
-    double sigma = g->alpha;
-    if (N > 0) {
-      IBRD_CUDA(cudaMemsetAsync(g->dflag, 0, sizeof(int), g->s));
-      prof_begin(P_SETUP, g->s);
-      k_check_rates<<<std::min(1024, (N + 255) / 256), 256, 0, g->s>>>(kappa, N, g->dflag);
-      prof_end(P_SETUP, g->s, "check_rates");
-      int flag = 0;
-      IBRD_CUDA(cudaMemcpyAsync(&flag, g->dflag, sizeof(int), cudaMemcpyDeviceToHost, g->s));
-      launch_sum<double>(kappa, N, g->partial, g->scal + S_TMP, 1.0, g->s);
-      const double ksum = host_scalar(g, S_TMP);
-      if (flag) throw ArgError{IBRD_ERR_NONFINITE, "kappa must be finite and >= 0"};
-      if (g->alpha == 0.0) sigma = ksum / ((double)g->d.n() * g->h * g->h * g->h);
-    }
-    if (!(sigma > 0.0)) throw ArgError{IBRD_ERR_ARG, "steady reaction system needs some kappa > 0"};
+    const double sigma = reaction_setup(g, kappa, rhs, c, o);
     SolveResult R;
     History hist;
     if (info) {
@@ -1803,14 +2727,9 @@ ibrd_status ibrd_solve_reaction(ibrd_grid g, const double* kappa, const double* 
     } else {
       ReactionOp<double> op(g, kappa, sigma, o);
       ReactionOp<float> op32(g, kappa, sigma, o);
-      R = refine(g, op, op32, rhs, c, g->d.n(), o, !o.use_guess, hist);
+      R = run_refine(g, op, op32, rhs, c, g->d.n(), o, !o.use_guess, hist);
     }
-    if (info) info->history_len = hist.len;
-    report(g, c, nullptr, kappa, info);
-    if (take_wait_flag(g)) R.st = IBRD_ERR_TIMEOUT;
-    fill_info(info, R, g, t0);
-    if (info) info->precond = -1;
-    if (R.st != IBRD_OK) g->err = std::string("ibrd_solve_reaction: ") + ibrd_status_string(R.st);
+    reaction_report(g, kappa, c, R, info, t0, hist);
     return R.st;
   });
 }
@@ -1820,50 +2739,8 @@ ibrd_status ibrd_solve_saddle(ibrd_grid g, const double* rhs, const double* f, d
   return guarded(g, "ibrd_solve_saddle", [&]() {
     const double t0 = now_s();
     const ibrd_solve_opts o = resolve_opts(g, opts);
-    const int N = g->blobs.n;
-    if (N < 1) throw ArgError{IBRD_ERR_STATE, "saddle solve needs at least one blob"};
-    if (!rhs || !c || !lambda) throw ArgError{IBRD_ERR_ARG, "null pointer"};
-    g->vcycles = 0;
-    g->inner = 0;
-    g->reorths = 0;
-    g->refinements = 0;
-    ensure_nvec(g, o.schur_inner);
-    const size_t nc = g->d.n();
-    const size_t n = nc + N;
-    if (g->xs_cap < n) {
-      cudaFree(g->xs);
-      cudaFree(g->bs);
-      g->xs = g->bs = nullptr;
-      g->xs = dalloc<double>(n);
-      g->bs = dalloc<double>(n);
-      g->xs_cap = n;
-    }
-    IBRD_CUDA(cudaMemcpyAsync(g->bs, rhs, sizeof(double) * nc, cudaMemcpyDeviceToDevice, g->s));
-    if (f)
-      IBRD_CUDA(cudaMemcpyAsync(g->bs + nc, f, sizeof(double) * N, cudaMemcpyDeviceToDevice, g->s));
-    else
-      IBRD_CUDA(cudaMemsetAsync(g->bs + nc, 0, sizeof(double) * N, g->s));
-    if (o.use_guess) {
-      IBRD_CUDA(cudaMemcpyAsync(g->xs, c, sizeof(double) * nc, cudaMemcpyDeviceToDevice, g->s));
-      IBRD_CUDA(cudaMemcpyAsync(g->xs + nc, lambda, sizeof(double) * N, cudaMemcpyDeviceToDevice, g->s));
-    }
-    const bool warm = !o.use_guess && o.lambda_guess != IBRD_GUESS_NONE;
-    if (warm) {
-      if (o.lambda_guess == IBRD_GUESS_GIVEN)
-        IBRD_CUDA(cudaMemcpyAsync(g->xs + nc, lambda, sizeof(double) * N, cudaMemcpyDeviceToDevice, g->s));
-      if (o.lambda_guess == IBRD_GUESS_PENALTY)
-        saddle_penalty_start(g, o, g->bs, g->xs);
-      else if (o.precision == IBRD_FP64)
-        saddle_warm_start<double>(g, o, g->bs, g->xs, o.lambda_guess, o.warm_cycles);
-      else
-        saddle_warm_start<float>(g, o, g->bs, g->xs, o.lambda_guess, o.warm_cycles);
-    }
-    const bool zero_start = !o.use_guess && !warm;
-    if (o.precond == IBRD_PRECOND_DIAG && !g->gamma_valid) {
-      g->gamma_diag = compute_gamma(g, o);
-      g->gamma_valid = true;
-      g->vcycles = 0;
-    }
+    const bool zero_start = saddle_setup(g, rhs, f, c, lambda, o);
+    const size_t n = g->d.n() + g->blobs.n;
     SolveResult R;
     History hist;
     if (info) {
@@ -1879,16 +2756,9 @@ ibrd_status ibrd_solve_saddle(ibrd_grid g, const double* rhs, const double* f, d
     } else {
       SaddleOp<double> op(g, o, o.zeta, o.xi);
       SaddleOp<float> op32(g, o, o.zeta, o.xi);
-      R = refine(g, op, op32, g->bs, g->xs, n, o, zero_start, hist);
+      R = run_refine(g, op, op32, g->bs, g->xs, n, o, zero_start, hist);
     }
-    if (info) info->history_len = hist.len;
-    IBRD_CUDA(cudaMemcpyAsync(c, g->xs, sizeof(double) * nc, cudaMemcpyDeviceToDevice, g->s));
-    IBRD_CUDA(cudaMemcpyAsync(lambda, g->xs + nc, sizeof(double) * N, cudaMemcpyDeviceToDevice, g->s));
-    report(g, c, lambda, nullptr, info);
-    if (take_wait_flag(g)) R.st = IBRD_ERR_TIMEOUT;
-    fill_info(info, R, g, t0);
-    if (info) info->precond = o.precond;
-    if (R.st != IBRD_OK) g->err = std::string("ibrd_solve_saddle: ") + ibrd_status_string(R.st);
+    saddle_report(g, c, lambda, R, info, t0, o, hist);
     return R.st;
   });
 }
@@ -1897,6 +2767,19 @@ ibrd_status ibrd_solve_reaction_batch(int count, const ibrd_grid* grids, const d
                                       const double* const* rhs, double* const* c, const ibrd_solve_opts* opts,
                                       ibrd_solve_info* infos, int threads) {
   if (count > 0 && (!kappa || !rhs || !c)) return IBRD_ERR_ARG;
+  if (opts && opts->graphs == 2 && count > 0 && batch_grids_ok(count, grids)) {
+    std::vector<BatchItem> items((size_t)count);
+    for (int i = 0; i < count; ++i)
+      items[i] = BatchItem{IBRD_SOLVE_REACTION, grids[i], kappa[i], rhs[i], nullptr, c[i], nullptr,
+                           infos ? infos + i : nullptr};
+    std::vector<ibrd_status> st((size_t)count, IBRD_OK);
+    try {
+      if (batch_graph_solve(items, opts, st, threads)) return first_failure(st);
+    } catch (const CudaError& e) {
+      cudaGetLastError();
+      return fail(grids[0], IBRD_ERR_CUDA, std::string("ibrd_solve_reaction_batch: ") + e.what);
+    }
+  }
   return run_batch(count, grids, threads, [&](int i) {
     ibrd_solve_info* info = infos ? infos + i : nullptr;
     const ibrd_status st = ibrd_solve_reaction(grids[i], kappa[i], rhs[i], c[i], opts, info);
@@ -1909,6 +2792,19 @@ ibrd_status ibrd_solve_saddle_batch(int count, const ibrd_grid* grids, const dou
                                     const double* const* f, double* const* c, double* const* lambda,
                                     const ibrd_solve_opts* opts, ibrd_solve_info* infos, int threads) {
   if (count > 0 && (!rhs || !c || !lambda)) return IBRD_ERR_ARG;
+  if (opts && opts->graphs == 2 && count > 0 && batch_grids_ok(count, grids)) {
+    std::vector<BatchItem> items((size_t)count);
+    for (int i = 0; i < count; ++i)
+      items[i] = BatchItem{IBRD_SOLVE_SADDLE, grids[i], nullptr, rhs[i], f ? f[i] : nullptr, c[i], lambda[i],
+                           infos ? infos + i : nullptr};
+    std::vector<ibrd_status> st((size_t)count, IBRD_OK);
+    try {
+      if (batch_graph_solve(items, opts, st, threads)) return first_failure(st);
+    } catch (const CudaError& e) {
+      cudaGetLastError();
+      return fail(grids[0], IBRD_ERR_CUDA, std::string("ibrd_solve_saddle_batch: ") + e.what);
+    }
+  }
   return run_batch(count, grids, threads, [&](int i) {
     ibrd_solve_info* info = infos ? infos + i : nullptr;
     const ibrd_status st = ibrd_solve_saddle(grids[i], rhs[i], f ? f[i] : nullptr, c[i], lambda[i], opts, info);

@@ -574,7 +574,9 @@ __global__ void k_scale_by_inv(const E* __restrict__ x, E* __restrict__ y, size_
 // y = (float) x * sigma, with the sum of squares of y: FP32 over runs of 8
 // (stride apart), the runs in FP64.
 __global__ void __launch_bounds__(kRedThreads) k_convert_sq(const double* __restrict__ x, float* __restrict__ y,
-                                                            size_t n, float sigma, double* __restrict__ partial) {
+                                                            size_t n, float sigma, const double* __restrict__ sigma_dev,
+                                                            double* __restrict__ partial) {
+  if (sigma_dev) sigma = (float)*sigma_dev;
   double acc = 0.0;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
@@ -593,7 +595,9 @@ __global__ void __launch_bounds__(kRedThreads) k_convert_sq(const double* __rest
 }
 
 // x += a * (double) d: FP32 correction added to an FP64 field
-__global__ void k_add_scaled(double a, const float* __restrict__ d, double* __restrict__ x, size_t n) {
+__global__ void k_add_scaled(double a, const double* __restrict__ div_dev, const float* __restrict__ d,
+                             double* __restrict__ x, size_t n) {
+  if (div_dev) a = 1.0 / *div_dev;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     x[i] = fma(a, (double)d[i], x[i]);
 }
@@ -809,14 +813,28 @@ void launch_scale_by_inv(const E* x, E* y, size_t n, const double* den, double n
 void launch_convert_sq(const double* x, float* y, size_t n, double sigma, double* partial, double* out,
                        cudaStream_t s) {
   prof_begin(P_VEC, s);
-  k_convert_sq<<<kRedBlocks, kRedThreads, 0, s>>>(x, y, n, (float)sigma, partial);
+  k_convert_sq<<<kRedBlocks, kRedThreads, 0, s>>>(x, y, n, (float)sigma, nullptr, partial);
+  prof_end(P_VEC, s, "convert_sq", 12.0 * n);
+  launch_finalize(partial, kRedBlocks, out, 1.0, s);
+}
+
+void launch_convert_sq(const double* x, float* y, size_t n, const double* sigma_dev, double* partial, double* out,
+                       cudaStream_t s) {
+  prof_begin(P_VEC, s);
+  k_convert_sq<<<kRedBlocks, kRedThreads, 0, s>>>(x, y, n, 1.f, sigma_dev, partial);
   prof_end(P_VEC, s, "convert_sq", 12.0 * n);
   launch_finalize(partial, kRedBlocks, out, 1.0, s);
 }
 
 void launch_add_scaled(double a, const float* d, double* x, size_t n, cudaStream_t s) {
   prof_begin(P_VEC, s);
-  k_add_scaled<<<stream_blocks(n, 256), 256, 0, s>>>(a, d, x, n);
+  k_add_scaled<<<stream_blocks(n, 256), 256, 0, s>>>(a, nullptr, d, x, n);
+  prof_end(P_VEC, s, "add_scaled", 20.0 * n);
+}
+
+void launch_add_divided(const double* div_dev, const float* d, double* x, size_t n, cudaStream_t s) {
+  prof_begin(P_VEC, s);
+  k_add_scaled<<<stream_blocks(n, 256), 256, 0, s>>>(0.0, div_dev, d, x, n);
   prof_end(P_VEC, s, "add_scaled", 20.0 * n);
 }
 

@@ -210,8 +210,13 @@ void launch_scale_by_inv(const E* x, E* y, size_t n, const double* den, double n
 // y = (float) x * sigma and *out = sum of y^2 (partial: kRedBlocks doubles)
 void launch_convert_sq(const double* x, float* y, size_t n, double sigma, double* partial, double* out,
                        cudaStream_t s);
+// the same with sigma read from device memory
+void launch_convert_sq(const double* x, float* y, size_t n, const double* sigma_dev, double* partial, double* out,
+                       cudaStream_t s);
 // x += a * d  (FP32 d added to FP64 x)
 void launch_add_scaled(double a, const float* d, double* x, size_t n, cudaStream_t s);
+// x += d / *div_dev  (divisor read from device memory)
+void launch_add_divided(const double* div_dev, const float* d, double* x, size_t n, cudaStream_t s);
 // flag = any non-finite in x (writes 1 into *flag if so; *flag must start 0)
 template <typename T>
 void launch_nonfinite(const T* x, size_t n, int* flag, cudaStream_t s);

@@ -500,3 +500,102 @@ def test_backward_euler_steps(ibrd, small):
                                    max_iter=400)
         assert rel_err(host(c), c_ref) < 1e-11
     torch.cuda.synchronize()
+
+
+def test_device_terminated_graph_solve(ibrd, small):
+    """opts.graphs = 2: from the second solve of a configuration on, a
+    refinement-mode solve is ONE CUDA graph launch whose refinement steps,
+    restart cycles and Krylov iterations are conditional nodes decided on the
+    device. It gives bit for bit the iterates, iteration counts, refinement
+    counts, residual and history of the host-driven loop (graphs = 1), for the
+    reaction solve from zero and the saddle solve from a uniform-share warm
+    start, on a grid whose finest level runs the row-resident kernels; and the
+    oracle's solutions."""
+    import torch
+    dims = (128, 32, 16)
+    q = rsa_positions(12, dims, 1.0, 4.0, 91)
+    kappa = loguniform_rates(len(q), 0.1, 10.0, 92)
+    src = 1.0 + 0.2 * np.random.default_rng(93).standard_normal((16, 32, 128))
+    g = ibrd.Grid(*dims)
+    g.set_blobs(dev(q))
+    common = dict(tol=1e-10, precision=2, max_iter=600, restart=10, nu1=1, nu2=1, inner_tol=1e-3)
+    out = {}
+    for graphs in (1, 2, 2, 2):  # host loop; first encounter (host); graph built and launched; replay
+        c, info = g.solve_reaction(dev(kappa), dev(src), graphs=graphs, **common)
+        c2, lam, info2 = g.solve_saddle(dev(src), graphs=graphs, lambda_guess=1, warm_cycles=1, schur_inner=3,
+                                        **common)
+        out.setdefault(graphs, []).append((host(c), info, host(c2), host(lam), info2))
+    ref = out[1][0]
+    for run in out[2]:
+        assert np.array_equal(run[0], ref[0]) and np.array_equal(run[2], ref[2]) and np.array_equal(run[3], ref[3])
+        for a, b in ((run[1], ref[1]), (run[4], ref[4])):
+            assert a["status"] == b["status"] == 0
+            for k in ("outer_iters", "refinements", "vcycles", "rel_residual"):
+                assert a[k] == b[k], (k, a[k], b[k])
+            assert np.array_equal(a["history"], b["history"])
+    c_ref, _, _ = direct.solve_reaction(q, kappa, src, 1.0, 1.0, 0.0)
+    assert rel_err(out[2][-1][0], c_ref) < 1e-8
+    # limits and faults end the device loop with the host loop's statuses
+    info = ibrd.ibrd_solve_reaction(g.handle, dev(kappa), dev(src), g.field(),
+                                    ibrd.ibrd_default_opts(graphs=2, **dict(common, max_iter=3)),
+                                    raise_on_error=False)
+    info = ibrd.ibrd_solve_reaction(g.handle, dev(kappa), dev(src), g.field(),
+                                    ibrd.ibrd_default_opts(graphs=2, **dict(common, max_iter=3)),
+                                    raise_on_error=False)
+    assert info["status"] == 4 and info["outer_iters"] == 3
+    ibrd.ibrd_set_wait_limit(g.handle, 0)
+    for _ in range(2):  # host loop, then the graph (rebuilt: the bound is baked into its kernels)
+        info = ibrd.ibrd_solve_reaction(g.handle, dev(kappa), dev(src), g.field(),
+                                        ibrd.ibrd_default_opts(graphs=2, **common), raise_on_error=False)
+        assert info["status"] == 7
+    ibrd.ibrd_set_wait_limit(g.handle, 1 << 24)
+    torch.cuda.synchronize()
+
+
+def test_batch_as_one_graph(ibrd):
+    """Batched refinement-mode solves with opts.graphs = 2: the first call runs
+    the problems' host loops, the second records every problem's whole
+    device-terminated solve into ONE graph (one branch per problem) and
+    launches it, the third replays it. Every call gives, bit for bit, the
+    iterates and reports of the same solves run one at a time, for reaction
+    solves of uneven realisations (grid sides 32-64, 4-200 blobs) and
+    warm-started saddle solves."""
+    import torch
+    from synthetic import batch_workloads
+    ws = batch_workloads(5, sides=(32, 40, 48, 64), n_lo=4, n_hi=200, seed=14)
+    streams = [torch.cuda.Stream() for _ in ws]
+    grids = [ibrd.Grid(*w.dims, h=w.h, chi=w.chi, stream=s.cuda_stream) for w, s in zip(ws, streams)]
+    ks, gs = [dev(w.kappa) for w in ws], [dev(w.g) for w in ws]
+    torch.cuda.synchronize()
+    for g, w in zip(grids, ws):
+        g.set_blobs(dev(w.q))
+    hs = [g.handle for g in grids]
+    ro = dict(tol=1e-10, precision=2, max_iter=600, nu1=1, nu2=1, inner_tol=1e-3)
+    so = dict(ro, lambda_guess=1, warm_cycles=1, schur_inner=3)
+    singles = []
+    for i, g in enumerate(grids):
+        c = torch.zeros_like(gs[i])
+        r = ibrd.ibrd_solve_reaction(g.handle, ks[i], gs[i], c, ibrd.ibrd_default_opts(graphs=1, **ro))
+        c2, lam = torch.zeros_like(gs[i]), torch.zeros(len(ws[i].q), dtype=torch.float64, device="cuda")
+        s1 = ibrd.ibrd_solve_saddle(g.handle, gs[i], None, c2, lam, ibrd.ibrd_default_opts(graphs=1, **so))
+        singles.append((c, r, c2, lam, s1))
+    torch.cuda.synchronize()
+    for call in range(3):
+        cb = [torch.zeros_like(x) for x in gs]
+        rb = ibrd.ibrd_solve_reaction_batch(hs, ks, gs, cb, ibrd.ibrd_default_opts(graphs=2, **ro), threads=3)
+        cs = [torch.zeros_like(x) for x in gs]
+        lb = [torch.zeros(len(w.q), dtype=torch.float64, device="cuda") for w in ws]
+        sb = ibrd.ibrd_solve_saddle_batch(hs, gs, None, cs, lb, ibrd.ibrd_default_opts(graphs=2, **so), threads=3)
+        torch.cuda.synchronize()
+        for i in range(len(ws)):
+            c, r, c2, lam, s1 = singles[i]
+            assert torch.equal(cb[i], c) and torch.equal(cs[i], c2) and torch.equal(lb[i], lam), (call, i)
+            for a, b in ((rb[i], r), (sb[i], s1)):
+                assert a["status"] == b["status"] == 0
+                for k in ("outer_iters", "refinements", "vcycles", "rel_residual"):
+                    assert a[k] == b[k], (call, i, k, a[k], b[k])
+    k = min(range(len(ws)), key=lambda i: ws[i].dims[0] ** 3 + len(ws[i].q))
+    w = ws[k]
+    c_ref, _, _ = direct.solve_reaction(w.q, w.kappa, w.g, w.h, w.chi, 0.0)
+    assert rel_err(host(cb[k]), c_ref) < 1e-8
+    torch.cuda.synchronize()
