@@ -364,8 +364,13 @@ ibrd_status ibrd_autotune(ibrd_grid g, int precision, int retune, ibrd_tune_entr
    handle's hierarchy, tx in {0, 32, 64} or tx = nx (0 for kind 1; 64 only
    for FP32 and when 64 divides nx, else ignored; nx selects the row-resident
    FP32 sweep on levels whose rows are 128 or 256 cells, ny a multiple of 8
-   and nz even), zc >= 0 (0 = built-in; clamped to the level's nz). Drops the
-   handle's captured CUDA graphs. */
+   and nz even), zc >= 0 (0 = built-in; clamped to the level's nz).
+   kind 2 (FP32 only, zc = 0) is the coarse-grid correction of the level: on
+   levels the row-resident sweep serves, the V-cycle adds the prolongation of
+   the coarse correction inside the first post-smoothing sweep (one pass over
+   x instead of two; the same values bit for bit); tx = 1 keeps it a separate
+   kernel, tx = 0 restores the default. Drops the handle's captured CUDA
+   graphs. */
 ibrd_status ibrd_tune_set(ibrd_grid g, int elem_bytes, int kind, int nx, int ny, int nz, int tx, int zc);
 
 /* Bound on the device waits of this handle's kernels (not in the paper). The

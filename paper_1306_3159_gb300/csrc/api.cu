@@ -442,8 +442,19 @@ int vcycle_level(ibrd_grid g, int l, const T* b, const double* bshift, T* x, boo
     launch_resid_restrict<T>(cur, b, bshift, H.b[l + 1], lv.d, st, g->s);
   }
   vcycle_level<T>(g, l + 1, H.b[l + 1], nullptr, H.x[l + 1], true, shift, nu1, nu2, nullptr);
-  launch_prolong8<T>(H.x[l + 1], cur, lv.d, g->s);
-  for (int sweep = 0; sweep < nu2; ++sweep) {
+  int sweep = 0;
+  if (nu2 >= 1) {
+    // the coarse-grid correction inside the first post-smoothing sweep
+    const int r = launch_prolong_sweep<T>(H.x[l + 1], cur, oth, b, bshift, lv.d, st, nu2 == 1 ? part : nullptr,
+                                          part_cap, g->s);
+    if (r >= 0) {
+      std::swap(cur, oth);
+      np = nu2 == 1 ? r : 0;
+      sweep = 1;
+    }
+  }
+  if (sweep == 0) launch_prolong8<T>(H.x[l + 1], cur, lv.d, g->s);
+  for (; sweep < nu2; ++sweep) {
     const bool last = (sweep == nu2 - 1);
     const int r = launch_rb_sweep<T>(cur, oth, b, bshift, lv.d, st, false, last ? part : nullptr, part_cap, g->s);
     if (r >= 0) std::swap(cur, oth);
@@ -2864,9 +2875,10 @@ ibrd_status ibrd_autotune(ibrd_grid g, int precision, int retune, ibrd_tune_entr
 ibrd_status ibrd_tune_set(ibrd_grid g, int elem_bytes, int kind, int nx, int ny, int nz, int tx, int zc) {
   return guarded(g, "ibrd_tune_set", [&]() {
     const bool rows = elem_bytes == 4 && kind == TUNE_SWEEP && tx == nx && rows_sweep_ok(Dims{nx, ny, nz});
-    if ((elem_bytes != 4 && elem_bytes != 8) || (kind != TUNE_SWEEP && kind != TUNE_ZERO) || zc < 0 ||
-        (tx != 0 && tx != 32 && tx != 64 && !rows) || (kind == TUNE_ZERO && tx != 0) ||
-        (elem_bytes == 8 && tx == 64))
+    const bool pro = kind == TUNE_PROLONG;
+    if ((elem_bytes != 4 && elem_bytes != 8) || (kind != TUNE_SWEEP && kind != TUNE_ZERO && !pro) || zc < 0 ||
+        (!pro && tx != 0 && tx != 32 && tx != 64 && !rows) || (kind == TUNE_ZERO && tx != 0) ||
+        (elem_bytes == 8 && tx == 64) || (pro && (elem_bytes != 4 || (tx != 0 && tx != 1) || zc != 0)))
       throw ArgError{IBRD_ERR_ARG, "bad launch shape"};
     bool level = false;
     for (const Level& l : g->levels) level |= (l.d.nx == nx && l.d.ny == ny && l.d.nz == nz);

@@ -69,6 +69,22 @@ struct Dims {
   size_t n() const { return (size_t)nx * ny * nz; }
 };
 
+// The cell-centred trilinear prolongation (weights 3/4 near, 1/4 far per
+// axis) in the arithmetic every prolongation kernel shares (the stand-alone
+// ones, the single-CTA coarse V-cycle and the sweep with the correction
+// fused), so that they agree bit for bit: axes in the order z (parent plane
+// first), y (parent row first), x, each as t = 3 near + far in one FMA --
+// 4 (3/4 near + 1/4 far), and scaling by 4 commutes with rounding -- so the
+// three axes give 64 times the correction, added as x + t / 64 in one FMA.
+// Bit for bit the 3/4-1/4 form rounded after every step, away from underflow,
+// at one instruction per axis.
+#ifdef __CUDACC__
+__device__ __forceinline__ float prolong_axis(float nearv, float farv) { return __fmaf_rn(3.f, nearv, farv); }
+__device__ __forceinline__ double prolong_axis(double nearv, double farv) { return __fma_rn(3.0, nearv, farv); }
+__device__ __forceinline__ float prolong_add(float x, float t64) { return __fmaf_rn(0x1p-6f, t64, x); }
+__device__ __forceinline__ double prolong_add(double x, double t64) { return __fma_rn(0x1p-6, t64, x); }
+#endif
+
 // Coefficients of A_l = alpha I - chi L_{h_l}: diag = alpha + 6 chi/h^2,
 // off = chi/h^2, so (A x)_k = diag x_k - off * sum_{6 neighbours} x.
 struct Stencil {
@@ -107,8 +123,10 @@ struct SweepShape {
   int tx = 0;
   int zc = 0;
 };
-// Sweep kernels: the fused sweep and the stencil pass of a sweep from zero.
-enum { TUNE_SWEEP = 0, TUNE_ZERO = 1 };
+// Sweep kernels: the fused sweep and the stencil pass of a sweep from zero;
+// TUNE_PROLONG (set by hand only): tx = 1 keeps the prolongation a separate
+// kernel on a level where it would be fused into the first post-sweep.
+enum { TUNE_SWEEP = 0, TUNE_ZERO = 1, TUNE_PROLONG = 2 };
 // The tuned shape for kernel `kind` on elements of `elem` bytes and grid d in
 // the handle the calling thread is working for, or null.
 const SweepShape* tuned_sweep(int elem, int kind, Dims d);
@@ -126,6 +144,12 @@ bool rows_sweep_ok(Dims d);
 int rows_sweep_default_zc(Dims d);
 int launch_rows_sweep(const float* xin, float* xout, const float* b, const double* bshift, Dims d, Stencil st,
                       int zc, double* part, int part_cap, cudaStream_t s);
+// The same sweep of xin + P xc (P the trilinear prolongation of the coarse
+// field xc, as launch_prolong8 adds it) without writing the corrected field:
+// the coarse-grid correction fused into the first post-smoothing sweep.
+// zc is made even.
+int launch_rows_prolong_sweep(const float* xc, const float* xin, float* xout, const float* b, const double* bshift,
+                              Dims d, Stencil st, int zc, double* part, int part_cap, cudaStream_t s);
 // The first sweep from zero fused with the residual restriction on the same
 // levels as the row-resident sweep: x = sweep(0), bc = mean over 8 children of
 // b - shift - A x (bc 8-byte aligned). zc = planes per CTA (made even).
@@ -160,6 +184,14 @@ void launch_zero_restrict(const float* b, const double* bshift, float* x, float*
 // x (fine, dims d) += trilinear cell-centred prolongation of xc (dims d/2).
 template <typename T>
 void launch_prolong8(const T* xc, T* x, Dims d, cudaStream_t s);
+// The prolongation of xc added to xin fused with the red-black sweep that
+// follows it, on levels the row-resident FP32 sweep serves: writes the swept
+// field to xout (xin is left uncorrected) and returns the partial-sum count
+// as launch_rb_sweep does, or -1 without launching when it does not apply
+// (the caller then prolongs and sweeps separately).
+template <typename T>
+int launch_prolong_sweep(const T* xc, const T* xin, T* xout, const T* b, const double* bshift, Dims d, Stencil st,
+                         double* part, int part_cap, cudaStream_t s);
 // Coarsest exact solve x = G b with the circulant table G (dc.n() entries).
 template <typename T>
 void launch_coarse_solve(const T* table, const T* b, T* x, Dims dc, cudaStream_t s);

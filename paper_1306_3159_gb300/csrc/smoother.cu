@@ -616,34 +616,31 @@ __global__ void __launch_bounds__(256) k_prolong8(const T* __restrict__ xc, T* _
   const int J = blockIdx.y * blockDim.y + threadIdx.y;
   const int K = blockIdx.z * blockDim.z + threadIdx.z;
   if (I >= nxc || J >= nyc || K >= nzc) return;
-  const T w3 = (T)0.75, w1 = (T)0.25;
   const int Ix[3] = {wrap(I - 1, nxc), I, wrap(I + 1, nxc)};
   const int Jy[3] = {wrap(J - 1, nyc), J, wrap(J + 1, nyc)};
   const int Kz[3] = {wrap(K - 1, nzc), K, wrap(K + 1, nzc)};
-  // x interpolation on the 3 x 3 coarse rows: west child (uses I-1), east child (uses I+1)
-  T ex[3][3][2];
+  T c[3][3][3];  // [z][y][x] coarse neighbourhood
 #pragma unroll
-  for (int c = 0; c < 3; ++c)
+  for (int a = 0; a < 3; ++a)
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
-      const T* row = xc + (Kz[c] * nyc + Jy[r]) * nxc;
-      const T m = row[Ix[1]];
-      ex[c][r][0] = w3 * m + w1 * row[Ix[0]];
-      ex[c][r][1] = w3 * m + w1 * row[Ix[2]];
+      const T* row = xc + (Kz[a] * nyc + Jy[r]) * nxc;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) c[a][r][q] = row[Ix[q]];
     }
 #pragma unroll
   for (int dz = 0; dz < 2; ++dz)
 #pragma unroll
     for (int dy = 0; dy < 2; ++dy) {
-      const int k = 2 * K + dz, j = 2 * J + dy;
-      T* dst = x + ((size_t)k * ny + j) * nx + 2 * I;
+      const int k = 2 * K + dz, j = 2 * J + dy, o = dz ? 2 : 0, n = dy ? 2 : 0;
+      // z, then y (parent plane / row first), then x, each axis scaled by 4
+      T zy[3];
 #pragma unroll
-      for (int dx = 0; dx < 2; ++dx) {
-        // y then z interpolation
-        const T yA = w3 * ex[1][1][dx] + w1 * ex[1][dy ? 2 : 0][dx];
-        const T yB = w3 * ex[dz ? 2 : 0][1][dx] + w1 * ex[dz ? 2 : 0][dy ? 2 : 0][dx];
-        dst[dx] += w3 * yA + w1 * yB;
-      }
+      for (int q = 0; q < 3; ++q)
+        zy[q] = prolong_axis(prolong_axis(c[1][1][q], c[o][1][q]), prolong_axis(c[1][n][q], c[o][n][q]));
+      T* dst = x + ((size_t)k * ny + j) * nx + 2 * I;
+      dst[0] = prolong_add(dst[0], prolong_axis(zy[1], zy[0]));
+      dst[1] = prolong_add(dst[1], prolong_axis(zy[1], zy[2]));
     }
 }
 
@@ -726,44 +723,44 @@ __global__ void __launch_bounds__(256) k_prolong8x2(const T* __restrict__ xc, T*
   const int K = blockIdx.z * blockDim.z + threadIdx.z;
   if (2 * I2 >= nxc || J >= nyc || K >= nzc) return;
   const int I = 2 * I2;
-  const T w3 = (T)0.75, w1 = (T)0.25;
   const int Ix[4] = {wrap(I - 1, nxc), I, I + 1, wrap(I + 2, nxc)};
   const int Jy[3] = {wrap(J - 1, nyc), J, wrap(J + 1, nyc)};
   const int Kz[3] = {wrap(K - 1, nzc), K, wrap(K + 1, nzc)};
-  // x interpolation on the 3 x 3 coarse rows: fine cells 2I .. 2I+3
-  T ex[3][3][4];
+  T c[3][3][4];  // [z][y][x] coarse neighbourhood of the pair
 #pragma unroll
-  for (int c = 0; c < 3; ++c)
+  for (int a = 0; a < 3; ++a)
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
-      const T* row = xc + (Kz[c] * nyc + Jy[r]) * nxc;
-      const T a0 = row[Ix[0]], a1 = row[Ix[1]], a2 = row[Ix[2]], a3 = row[Ix[3]];
-      ex[c][r][0] = w3 * a1 + w1 * a0;
-      ex[c][r][1] = w3 * a1 + w1 * a2;
-      ex[c][r][2] = w3 * a2 + w1 * a1;
-      ex[c][r][3] = w3 * a2 + w1 * a3;
+      const T* row = xc + (Kz[a] * nyc + Jy[r]) * nxc;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) c[a][r][q] = row[Ix[q]];
     }
 #pragma unroll
   for (int dz = 0; dz < 2; ++dz)
 #pragma unroll
     for (int dy = 0; dy < 2; ++dy) {
-      const int k = 2 * K + dz, j = 2 * J + dy;
+      const int k = 2 * K + dz, j = 2 * J + dy, o = dz ? 2 : 0, n = dy ? 2 : 0;
       T* dst = x + ((size_t)k * ny + j) * nx + 4 * I2;
-      T v[4];
+      // z, then y (parent plane / row first), then x, each axis scaled by 4:
+      // fine cells 2I .. 2I+3
+      T zy[4], v[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const T yA = w3 * ex[1][1][q] + w1 * ex[1][dy ? 2 : 0][q];
-        const T yB = w3 * ex[dz ? 2 : 0][1][q] + w1 * ex[dz ? 2 : 0][dy ? 2 : 0][q];
-        v[q] = w3 * yA + w1 * yB;
-      }
+      for (int q = 0; q < 4; ++q)
+        zy[q] = prolong_axis(prolong_axis(c[1][1][q], c[o][1][q]), prolong_axis(c[1][n][q], c[o][n][q]));
+      v[0] = prolong_axis(zy[1], zy[0]);
+      v[1] = prolong_axis(zy[1], zy[2]);
+      v[2] = prolong_axis(zy[2], zy[1]);
+      v[3] = prolong_axis(zy[2], zy[3]);
       if constexpr (sizeof(T) == 4) {
         float4 t = *reinterpret_cast<float4*>(dst);
-        t.x += v[0]; t.y += v[1]; t.z += v[2]; t.w += v[3];
+        t.x = prolong_add(t.x, v[0]); t.y = prolong_add(t.y, v[1]);
+        t.z = prolong_add(t.z, v[2]); t.w = prolong_add(t.w, v[3]);
         *reinterpret_cast<float4*>(dst) = t;
       } else {
         double2 t0 = *reinterpret_cast<double2*>(dst);
         double2 t1 = *reinterpret_cast<double2*>(dst + 2);
-        t0.x += v[0]; t0.y += v[1]; t1.x += v[2]; t1.y += v[3];
+        t0.x = prolong_add(t0.x, v[0]); t0.y = prolong_add(t0.y, v[1]);
+        t1.x = prolong_add(t1.x, v[2]); t1.y = prolong_add(t1.y, v[3]);
         *reinterpret_cast<double2*>(dst) = t0;
         *reinterpret_cast<double2*>(dst + 2) = t1;
       }
@@ -894,7 +891,6 @@ __device__ void vcycle_small_body(const CoarseLevels& lv, const T* __restrict__ 
     const int nxc = nx >> 1, nyc = ny >> 1, nzc = nz >> 1;
     T* x = X + lv.off[l];
     const T* xc = X + lv.off[l + 1];
-    const T w3 = (T)0.75, w1 = (T)0.25;
     for (int c = tid; c < n; c += nt) {
       int i, j, k;
       decode(l, c, i, j, k);
@@ -903,9 +899,11 @@ __device__ void vcycle_small_body(const CoarseLevels& lv, const T* __restrict__ 
       const int J2 = (j & 1) ? wrap(J + 1, nyc) : wrap(J - 1, nyc);
       const int K2 = (k & 1) ? wrap(K + 1, nzc) : wrap(K - 1, nzc);
       auto e = [&](int kk, int jj, int ii) { return xc[(kk * nyc + jj) * nxc + ii]; };
-      const T yA = w3 * (w3 * e(K, J, I) + w1 * e(K, J, I2)) + w1 * (w3 * e(K, J2, I) + w1 * e(K, J2, I2));
-      const T yB = w3 * (w3 * e(K2, J, I) + w1 * e(K2, J, I2)) + w1 * (w3 * e(K2, J2, I) + w1 * e(K2, J2, I2));
-      x[c] += w3 * yA + w1 * yB;
+      // z, then y, then x (each axis scaled by 4)
+      auto zy = [&](int ii) {
+        return prolong_axis(prolong_axis(e(K, J, ii), e(K2, J, ii)), prolong_axis(e(K, J2, ii), e(K2, J2, ii)));
+      };
+      x[c] = prolong_add(x[c], prolong_axis(zy(I), zy(I2)));
     }
     __syncthreads();
     for (int sw = 0; sw < nu2; ++sw) sweep(l);
@@ -1087,6 +1085,29 @@ void launch_zero_restrict(const float* b, const double* bshift, float* x, float*
 }
 
 template <typename T>
+int launch_prolong_sweep(const T* xc, const T* xin, T* xout, const T* b, const double* bshift, Dims d, Stencil st,
+                         double* part, int part_cap, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    if (rows_sweep_ok(d) && aligned16(xin) && aligned16(xout) && aligned16(b) && aligned16(xc) && xin != xout &&
+        b != xout && xc != xout && wait_error_flag()) {
+      // the row-resident sweep serves this level unless a tiled shape was
+      // chosen or the fusion was switched off for it
+      const SweepShape* tn = tuned_sweep(4, TUNE_SWEEP, d);
+      const SweepShape* tp = tuned_sweep(4, TUNE_PROLONG, d);
+      if ((!tn || tn->tx == 0 || tn->tx == d.nx) && !(tp && tp->tx == 1)) {
+        const int zc = (tn && tn->zc >= 2) ? tn->zc : rows_sweep_default_zc(d);
+        prof_begin(P_RBGS32, s);
+        const int r = launch_rows_prolong_sweep(xc, xin, xout, b, bshift, d, st, zc, part, part_cap, s);
+        // x, b and the coarse field read once, x written once
+        prof_end(P_RBGS32, s, "prolong_sweep_rows", (3.0 + 0.125) * sizeof(T) * d.n());
+        return r;
+      }
+    }
+  }
+  return -1;
+}
+
+template <typename T>
 void launch_prolong8(const T* xc, T* x, Dims d, cudaStream_t s) {
   const int nxc = d.nx / 2, nyc = d.ny / 2, nzc = d.nz / 2;
   if (d.nx % 4 == 0 && d.nx >= 8 && aligned16(x)) {
@@ -1126,6 +1147,8 @@ void launch_vcycle_small(const CoarseLevels& lv, const T* b, T* x, const double*
                                   cudaStream_t);                                                            \
   template void launch_resid_restrict<T>(const T*, const T*, const double*, T*, Dims, Stencil, cudaStream_t); \
   template void launch_prolong8<T>(const T*, T*, Dims, cudaStream_t);                                       \
+  template int launch_prolong_sweep<T>(const T*, const T*, T*, const T*, const double*, Dims, Stencil, double*,   \
+                                       int, cudaStream_t);                                                   \
   template bool rb_sweep_fused_ok<T>(Dims);
 IBRD_INST(double)
 IBRD_INST(float)

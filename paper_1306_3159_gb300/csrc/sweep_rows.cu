@@ -45,6 +45,7 @@ namespace {
 
 constexpr int kRowsTY = 8;    // tile rows per CTA
 constexpr int kRowsRing = 4;  // planes in the TMA ring (prefetch distance 2)
+constexpr int kCoarseRing = 3;  // coarse planes in the ring of the fused prolongation
 constexpr unsigned kDrainLimit = 1u << 26;
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -128,6 +129,46 @@ __device__ __forceinline__ void rb_row(float4 (&v)[NS], const void* u, const voi
   }
 }
 
+// Adds to the fine row v the coarse correction of Sec. III.E (cell-centred
+// trilinear prolongation) in the order every prolongation kernel uses: z
+// between the row's parent coarse plane cp and the other plane co, then y
+// between the parent coarse row cr and its neighbour nr on the row's side
+// (coarse planes in shared memory, NX / 2 floats per row), then x. Lane l
+// holds, per slot s, fine cells 4 g .. 4 g + 3 of group g = l + 32 s, over
+// coarse cells 2 g, 2 g + 1; their x-neighbours 2 g - 1 and 2 g + 2 come from
+// the adjacent lanes (lane 0 / 31 from the adjacent slot: the periodic wrap).
+template <int NS>
+__device__ __forceinline__ void add_correction(float4 (&v)[NS], const float* cp, const float* co, int cr, int nr,
+                                               int lane) {
+  constexpr int NXC = 64 * NS;
+  float2 zy[NS];  // the pair after z and y (16 times its value)
+  float tp[NS], tn[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    const int o = 2 * (lane + 32 * s);
+    const float2 pp = *reinterpret_cast<const float2*>(cp + cr * NXC + o);
+    const float2 op = *reinterpret_cast<const float2*>(co + cr * NXC + o);
+    const float2 pn = *reinterpret_cast<const float2*>(cp + nr * NXC + o);
+    const float2 on = *reinterpret_cast<const float2*>(co + nr * NXC + o);
+    zy[s] = make_float2(prolong_axis(prolong_axis(pp.x, op.x), prolong_axis(pn.x, on.x)),
+                        prolong_axis(prolong_axis(pp.y, op.y), prolong_axis(pn.y, on.y)));
+  }
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    tp[s] = __shfl_sync(0xffffffffu, zy[s].y, (lane + 31) & 31);
+    tn[s] = __shfl_sync(0xffffffffu, zy[s].x, (lane + 1) & 31);
+  }
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    const float z0 = lane == 0 ? tp[(s + NS - 1) % NS] : tp[s];
+    const float z3 = lane == 31 ? tn[(s + 1) % NS] : tn[s];
+    v[s].x = prolong_add(v[s].x, prolong_axis(zy[s].x, z0));
+    v[s].y = prolong_add(v[s].y, prolong_axis(zy[s].x, zy[s].y));
+    v[s].z = prolong_add(v[s].z, prolong_axis(zy[s].y, zy[s].x));
+    v[s].w = prolong_add(v[s].w, prolong_axis(zy[s].y, z3));
+  }
+}
+
 // Grid: (ny / TY, z-chunks). Block: (TY + 2) warps; warp w owns row
 // y0 - 1 + w (w = 0 and w = TY + 1 are the halo rows: red cells only).
 // Shared memory: XS[R][TY + 4][nx] (old x, rows y0-2 .. y0+TY+1),
@@ -142,20 +183,38 @@ __device__ __forceinline__ void rb_row(float4 (&v)[NS], const void* u, const voi
 // so both directions give the same sweep. March index i = 0 .. zc + 3 names
 // plane mp(i); step i updates the red cells of mp(i) and the black cells of
 // mp(i - 1) (when that plane is in the chunk) and stores mp(i - 1).
-template <int NS>
+//
+// PRO: the sweep that follows the coarse-grid correction, with the
+// correction fused: x (xin) arrives uncorrected, and every x value the sweep
+// reads is x + P xc, P the cell-centred trilinear prolongation of the coarse
+// field xc, in the arithmetic of the stand-alone prolongation kernel. The
+// coarse planes arrive by TMA into a ring of kCoarseRing slots of TY / 2 + 4
+// coarse rows (the parents of the tile's rows and their neighbours), riding
+// on the barriers of the fine planes. Fine planes 2K - 1 and 2K share the
+// coarse pair {K - 1, K}, so in march order every second fine plane brings a
+// new coarse plane (coarse march plane j = i / 2 + 2 first serves the
+// correction of fine march plane i + 1, i even). Each thread corrects its own
+// row of plane i + 1 in registers when it loads it and writes it back for the
+// y-neighbour reads of step i + 1; the halo warps also correct the two outer
+// x rows. Chunks hold an even number of planes so that the pairing is the same
+// in both march directions.
+template <int NS, bool PRO>
 __global__ void __launch_bounds__((kRowsTY + 2) * 32, 2)
     k_rbgs_rows(const __grid_constant__ CUtensorMap mx_tile, const __grid_constant__ CUtensorMap mx_pair,
                 const __grid_constant__ CUtensorMap mb_tile, const __grid_constant__ CUtensorMap mb_one,
+                const __grid_constant__ CUtensorMap mc_half, const __grid_constant__ CUtensorMap mc_pair,
                 float* __restrict__ xout, const double* __restrict__ bshift, int ny, int nz, int zc, float inv,
                 float off, double* __restrict__ part, int* __restrict__ err, unsigned wait_limit) {
   constexpr int TY = kRowsTY, R = kRowsRing, NX = 128 * NS;
   constexpr int XROWS = TY + 4, BROWS = TY + 2, RROWS = TY + 2, RW = NX / 2;
-  constexpr unsigned XBYTES = XROWS * NX * 4, BBYTES = BROWS * NX * 4;
+  constexpr int NXC = NX / 2, CROWS = TY / 2 + 4;
+  constexpr unsigned XBYTES = XROWS * NX * 4, BBYTES = BROWS * NX * 4, CBYTES = CROWS * NXC * 4;
   extern __shared__ __align__(1024) unsigned char sm_raw[];
   float* XS = reinterpret_cast<float*>(sm_raw);
   float* BS = XS + R * XROWS * NX;
   float* RS = BS + R * BROWS * NX;
-  unsigned long long* bars = reinterpret_cast<unsigned long long*>(RS + 2 * RROWS * RW);
+  float* CS = RS + 2 * RROWS * RW;
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(CS + (PRO ? kCoarseRing * CROWS * NXC : 0));
 
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int y0 = blockIdx.x * TY;
@@ -168,6 +227,11 @@ __global__ void __launch_bounds__((kRowsTY + 2) * 32, 2)
   const int ypar = (y0 - 1 + w) & 1;
   const int last = k1 - k0 + 3;  // march index of the last plane
   auto mp = [&](int i) { return down ? k1 + 1 - i : k0 - 2 + i; };
+  // coarse march plane j and the one a fine plane's copy brings (-1: none)
+  auto cmp = [&](int j) { return down ? (k1 >> 1) + 1 - j : (k0 >> 1) - 2 + j; };
+  auto cj_of = [&](int i) { return i <= 3 ? i : ((i & 1) ? (i + 3) >> 1 : -1); };
+  // coarse rows of this warp's own row: its parent and the parent's neighbour
+  const int cr = ((w + 1) >> 1) + 1, nr = (w & 1) ? cr - 1 : cr + 1;
 
   if (tid == 0) {
     for (int s = 0; s < R; ++s) mbar_init(smem_u32(bars + s), 1);
@@ -176,20 +240,36 @@ __global__ void __launch_bounds__((kRowsTY + 2) * 32, 2)
   __syncthreads();
 
   // copies of march plane i (x rows y0-2 .. y0+TY+1, b rows y0-1 .. y0+TY) into its slot
+  // box start rows, wrapped once (march planes lie in [-2, nz + 1], coarse
+  // march planes in [-2, nz / 2 + 1]: one compare wraps them)
+  const int ya = wrapm(y0 - 2, ny), yb = wrapm(y0 + TY, ny), yh = wrapm(y0 - 1, ny);
+  const int nyc = ny >> 1, nzc = nz >> 1, yc = y0 >> 1;
+  const int yca = wrapm(yc - 2, nyc), ycb = wrapm(yc + TY / 2, nyc);
   auto issue = [&](int i) {
     const int s = i % R;
     const unsigned bar = smem_u32(bars + s);
-    const int z = wrapm(mp(i), nz);
+    int z = mp(i);
+    z += z < 0 ? nz : (z >= nz ? -nz : 0);
     float* xs = XS + s * XROWS * NX;
     float* bs = BS + s * BROWS * NX;
+    const int j = PRO ? cj_of(i) : -1;
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    mbar_expect_tx(bar, XBYTES + BBYTES);
-    tma_load3(smem_u32(xs), &mx_pair, 0, wrapm(y0 - 2, ny), z, bar);
+    mbar_expect_tx(bar, XBYTES + BBYTES + (j >= 0 ? CBYTES : 0u));
+    tma_load3(smem_u32(xs), &mx_pair, 0, ya, z, bar);
     tma_load3(smem_u32(xs + 2 * NX), &mx_tile, 0, y0, z, bar);
-    tma_load3(smem_u32(xs + (TY + 2) * NX), &mx_pair, 0, wrapm(y0 + TY, ny), z, bar);
-    tma_load3(smem_u32(bs), &mb_one, 0, wrapm(y0 - 1, ny), z, bar);
+    tma_load3(smem_u32(xs + (TY + 2) * NX), &mx_pair, 0, yb, z, bar);
+    tma_load3(smem_u32(bs), &mb_one, 0, yh, z, bar);
     tma_load3(smem_u32(bs + NX), &mb_tile, 0, y0, z, bar);
-    tma_load3(smem_u32(bs + (TY + 1) * NX), &mb_one, 0, wrapm(y0 + TY, ny), z, bar);
+    tma_load3(smem_u32(bs + (TY + 1) * NX), &mb_one, 0, yb, z, bar);
+    if (PRO && j >= 0) {
+      // coarse rows y0/2 - 2 .. y0/2 + TY/2 + 1 of coarse plane cmp(j)
+      float* cs = CS + (j % kCoarseRing) * CROWS * NXC;
+      int kc = cmp(j);
+      kc += kc < 0 ? nzc : (kc >= nzc ? -nzc : 0);
+      tma_load3(smem_u32(cs), &mc_pair, 0, yca, kc, bar);
+      tma_load3(smem_u32(cs + 2 * NXC), &mc_half, 0, yc, kc, bar);
+      tma_load3(smem_u32(cs + (TY / 2 + 2) * NXC), &mc_pair, 0, ycb, kc, bar);
+    }
   };
   // thread 0 alone polls the barriers; the CTA barrier that follows every
   // wait publishes the landed plane to the other threads
@@ -199,13 +279,30 @@ __global__ void __launch_bounds__((kRowsTY + 2) * 32, 2)
   auto xrow = [&](int i, int r) { return reinterpret_cast<const float4*>(XS + (i % R) * XROWS * NX + r * NX); };
   auto brow = [&](int i, int r) { return reinterpret_cast<const float4*>(BS + (i % R) * BROWS * NX + r * NX); };
   auto rrow = [&](int i, int r) { return reinterpret_cast<float2*>(RS + (i & 1) * RROWS * RW + r * RW); };
+  auto xroww = [&](int i, int r) { return reinterpret_cast<float4*>(XS + (i % R) * XROWS * NX + r * NX); };
+  auto cslot = [&](int j) -> const float* { return CS + (j % kCoarseRing) * CROWS * NXC; };
+  // PRO, halo warps: correct x row 0 (warp 0) or TY + 3 (warp TY + 1) of
+  // march plane i in shared memory; cp / co: parent / other coarse plane
+  const bool outer = w == 0 || w == TY + 1;
+  auto fix_outer = [&](int i, const float* cp, const float* co) {
+    const bool top = w == 0;
+    float4 v[NS];
+    float4* row = xroww(i, top ? 0 : TY + 3) + lane;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) v[s] = row[32 * s];
+    add_correction<NS>(v, cp, co, top ? 1 : CROWS - 2, top ? 0 : CROWS - 1, lane);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) row[32 * s] = v[s];
+  };
 
   bool ok = true;
   if (tid == 0) {
-    for (int i = 0; i < R && i <= last; ++i) issue(i);
+    // PRO: plane 3's copy brings coarse plane 3 into the slot of coarse
+    // plane 0, which the prologue still reads: it is issued after it
+    for (int i = 0; i < (PRO ? 3 : R) && i <= last; ++i) issue(i);
     ok = wait_plane(0, wait_limit) && wait_plane(1, wait_limit) && wait_plane(2, wait_limit);
   }
-  int issued = min(R - 1, last);
+  int issued = PRO ? 2 : min(R - 1, last);
   ok = !__syncthreads_or(!ok);
   // march planes up to `done` have landed (the same value in every thread:
   // it only advances after a barrier that every thread passed)
@@ -218,23 +315,47 @@ __global__ void __launch_bounds__((kRowsTY + 2) * 32, 2)
       B[s] = xrow(0, w + 1)[lane + 32 * s];
       C[s] = xrow(1, w + 1)[lane + 32 * s];
     }
+    if constexpr (PRO) {
+      // fine march planes 0 and 1 have the parent coarse plane 1; the other
+      // plane is 0 for plane 0 and 2 for plane 1
+      add_correction<NS>(B, cslot(1), cslot(0), cr, nr, lane);
+      add_correction<NS>(C, cslot(1), cslot(2), cr, nr, lane);
+#pragma unroll
+      for (int s = 0; s < NS; ++s) xroww(1, w + 1)[lane + 32 * s] = C[s];
+      if (outer) fix_outer(1, cslot(1), cslot(2));
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    }
   }
   __syncthreads();  // step 1 refills plane 0's slot
+  if (PRO && ok) {
+    if (tid == 0) issue(3);
+    issued = 3;
+  }
   float acc = 0.f, comp = 0.f;  // Kahan sum of the new x (tile rows)
 
   // Step i: pm2 .. pp1 are this thread's row of march planes i - 2 .. i + 1,
   // bm1 / b0 its b of march planes i - 1 / i. Planes i and i + 1 have landed.
   auto step = [&](float4 (&pm2)[NS], float4 (&pm1)[NS], float4 (&p0)[NS], float4 (&pp1)[NS], float4 (&bm1)[NS],
-                  float4 (&b0)[NS], int i) -> bool {
+                  float4 (&b0)[NS], int i, bool odd) -> bool {
     if (i > last - 1 || !ok) return false;
     // plane i + 3 takes the slot of plane i - 1, last read before the barrier
-    // that ended step i - 1
+    // that ended step i - 1 (PRO, even i: its copy brings coarse plane
+    // i / 2 + 3 into the slot of coarse plane i / 2, last read in step i - 1)
     if (tid == 0 && i + 3 <= last) issue(i + 3);
     if (i + 3 <= last) issued = i + 3;
     const int z = mp(i);
 #pragma unroll
+    for (int s = 0; s < NS; ++s) pp1[s] = xrow(i + 1, w + 1)[lane + 32 * s];
+    if constexpr (PRO) {
+      // correct plane i + 1: odd i keeps the coarse pair of step i - 1, whose
+      // newer plane is the parent; even i brings coarse plane i / 2 + 2 (the
+      // other) and the parent is the plane before it
+      const int jp = odd ? ((i - 1) >> 1) + 2 : (i >> 1) + 1;
+      const int jo = odd ? jp - 1 : jp + 1;
+      add_correction<NS>(pp1, cslot(jp), cslot(jo), cr, nr, lane);
+    }
+#pragma unroll
     for (int s = 0; s < NS; ++s) {
-      pp1[s] = xrow(i + 1, w + 1)[lane + 32 * s];
       float4 t = brow(i, w)[lane + 32 * s];
       t.x -= sh, t.y -= sh, t.z -= sh, t.w -= sh;
       b0[s] = t;
@@ -262,6 +383,18 @@ __global__ void __launch_bounds__((kRowsTY + 2) * 32, 2)
         acc = tk;
       }
     }
+    if constexpr (PRO) {
+      // the corrected rows of plane i + 1 for the y-neighbour reads of step
+      // i + 1 (nothing reads that plane's rows in this step); the outer rows
+      // from the halo warps; then the writers' proxy fence, as TMA later
+      // refills the slot
+      const int jp = odd ? ((i - 1) >> 1) + 2 : (i >> 1) + 1;
+      const int jo = odd ? jp - 1 : jp + 1;
+#pragma unroll
+      for (int s = 0; s < NS; ++s) xroww(i + 1, w + 1)[lane + 32 * s] = pp1[s];
+      if (outer) fix_outer(i + 1, cslot(jp), cslot(jo));
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    }
     bool good = true;
     if (tid == 0 && i + 2 <= last) good = wait_plane(i + 2, wait_limit);
     ok = !__syncthreads_or(!good);
@@ -269,10 +402,10 @@ __global__ void __launch_bounds__((kRowsTY + 2) * 32, 2)
     return ok;
   };
   for (int i = 1; i < last; i += 4) {
-    if (!step(A, B, C, D, BX, BY, i)) break;
-    if (!step(B, C, D, A, BY, BX, i + 1)) break;
-    if (!step(C, D, A, B, BX, BY, i + 2)) break;
-    if (!step(D, A, B, C, BY, BX, i + 3)) break;
+    if (!step(A, B, C, D, BX, BY, i, true)) break;
+    if (!step(B, C, D, A, BY, BX, i + 1, false)) break;
+    if (!step(C, D, A, B, BX, BY, i + 2, true)) break;
+    if (!step(D, A, B, C, BY, BX, i + 3, false)) break;
   }
   if (!ok) {
     // a plane wait gave up: drain the copies still in flight, report, stop
@@ -287,7 +420,7 @@ __global__ void __launch_bounds__((kRowsTY + 2) * 32, 2)
     double v = (double)acc;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    __shared__ double ws[TY + 2];
+    double* ws = reinterpret_cast<double*>(RS);  // no step reads RS after the last barrier
     if (lane == 0) ws[w] = v;
     __syncthreads();
     if (tid == 0) {
@@ -349,16 +482,19 @@ __global__ void __launch_bounds__((kRowsTY + 2) * 32, 2)
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   __syncthreads();
+  // box start rows wrapped once; march planes lie in [-2, nz + 1]
+  const int ya = wrapm(y0 - 2, ny), yb = wrapm(y0 + TY, ny);
   auto issue = [&](int i) {
     const int s = i % R;
     const unsigned bar = smem_u32(bars + s);
-    const int z = wrapm(mp(i), nz);
+    int z = mp(i);
+    z += z < 0 ? nz : (z >= nz ? -nz : 0);
     float* bs = BSM + s * XROWS * NX;
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     mbar_expect_tx(bar, BBYTES);
-    tma_load3(smem_u32(bs), &mb_pair, 0, wrapm(y0 - 2, ny), z, bar);
+    tma_load3(smem_u32(bs), &mb_pair, 0, ya, z, bar);
     tma_load3(smem_u32(bs + 2 * NX), &mb_tile, 0, y0, z, bar);
-    tma_load3(smem_u32(bs + (TY + 2) * NX), &mb_pair, 0, wrapm(y0 + TY, ny), z, bar);
+    tma_load3(smem_u32(bs + (TY + 2) * NX), &mb_pair, 0, yb, z, bar);
   };
   auto wait_plane = [&](int i, unsigned limit) {
     return mbar_wait(smem_u32(bars + (i % R)), (unsigned)((i / R) & 1), limit);
@@ -566,21 +702,53 @@ CUtensorMap field_map(const float* f, Dims d, int rows) {
   return m;
 }
 
-template <int NS>
+template <int NS, bool PRO>
 constexpr size_t rows_smem() {
   constexpr int NX = 128 * NS;
-  return sizeof(float) * (size_t)NX * (kRowsRing * (kRowsTY + 4) + kRowsRing * (kRowsTY + 2) + (kRowsTY + 2)) +
+  return sizeof(float) * (size_t)NX *
+             (kRowsRing * (kRowsTY + 4) + kRowsRing * (kRowsTY + 2) + (kRowsTY + 2) +
+              (PRO ? kCoarseRing * (kRowsTY / 2 + 4) / 2 : 0)) +
          8 * kRowsRing;
 }
+// two CTAs per SM (228 KB of shared memory, 1 KB reserved per CTA)
+static_assert(2 * (rows_smem<2, true>() + 1024) <= 228 * 1024, "two CTAs per SM");
 
-template <int NS>
-void rows_launch(dim3 g, cudaStream_t s, const CUtensorMap (&m)[4], float* xout, const double* bshift, Dims d,
+template <int NS, bool PRO>
+void rows_launch(dim3 g, cudaStream_t s, const CUtensorMap (&m)[6], float* xout, const double* bshift, Dims d,
                  int zc, float inv, float off, double* part, int* err, unsigned limit) {
-  constexpr size_t sm = rows_smem<NS>();
+  constexpr size_t sm = rows_smem<NS, PRO>();
   static std::atomic<unsigned long long> attr{0};
-  ensure_smem_attr((const void*)k_rbgs_rows<NS>, (int)sm, attr);
-  k_rbgs_rows<NS><<<g, (kRowsTY + 2) * 32, sm, s>>>(m[0], m[1], m[2], m[3], xout, bshift, d.ny, d.nz, zc, inv, off,
-                                                     part, err, limit);
+  ensure_smem_attr((const void*)k_rbgs_rows<NS, PRO>, (int)sm, attr);
+  k_rbgs_rows<NS, PRO><<<g, (kRowsTY + 2) * 32, sm, s>>>(m[0], m[1], m[2], m[3], m[4], m[5], xout, bshift, d.ny,
+                                                          d.nz, zc, inv, off, part, err, limit);
+}
+
+// The row sweep of xin into xout; with xc non-null, of xin + P xc (the fused
+// prolongation, zc even).
+int rows_sweep_any(const float* xin, const float* xc, float* xout, const float* b, const double* bshift, Dims d,
+                   Stencil st, int zc, double* part, int part_cap, cudaStream_t s) {
+  const Dims dc{d.nx / 2, d.ny / 2, d.nz / 2};
+  const CUtensorMap mx = field_map(xin, d, kRowsTY), mx2 = field_map(xin, d, 2);
+  const CUtensorMap m[6] = {mx, mx2, field_map(b, d, kRowsTY), field_map(b, d, 1),
+                            xc ? field_map(xc, dc, kRowsTY / 2) : mx, xc ? field_map(xc, dc, 2) : mx2};
+  dim3 g(d.ny / kRowsTY, (d.nz + zc - 1) / zc);
+  const int nblk = (int)(g.x * g.y);
+  if (nblk > part_cap) part = nullptr;
+  const float inv = (float)(1.0 / st.diag), off = (float)st.off;
+  int* err = wait_error_flag();
+  const unsigned limit = wait_limit();
+  if (d.nx == 256) {
+    if (xc)
+      rows_launch<2, true>(g, s, m, xout, bshift, d, zc, inv, off, part, err, limit);
+    else
+      rows_launch<2, false>(g, s, m, xout, bshift, d, zc, inv, off, part, err, limit);
+  } else {
+    if (xc)
+      rows_launch<1, true>(g, s, m, xout, bshift, d, zc, inv, off, part, err, limit);
+    else
+      rows_launch<1, false>(g, s, m, xout, bshift, d, zc, inv, off, part, err, limit);
+  }
+  return part ? nblk : 0;
 }
 
 }  // namespace
@@ -590,11 +758,14 @@ bool rows_sweep_ok(Dims d) {
 }
 
 int rows_sweep_default_zc(Dims d) {
-  // about one wave of two resident CTAs per SM
+  // about one wave of two resident CTAs per SM; an even number of planes, as
+  // the sweep with the prolongation fused needs, so that both kernels split
+  // a level into the same CTAs (and per-CTA partial sums)
   const int cols = d.ny / kRowsTY;
   int chunks = (2 * 152) / cols;
   chunks = chunks < 1 ? 1 : chunks;
   int zc = (d.nz + chunks - 1) / chunks;
+  zc += zc & 1;
   return zc < 2 ? 2 : zc;
 }
 
@@ -603,28 +774,24 @@ int launch_rows_sweep(const float* xin, float* xout, const float* b, const doubl
   if (!rows_sweep_ok(d) || !aligned16(xin) || !aligned16(xout) || !aligned16(b) || xin == xout || b == xout)
     throw CudaError{cudaErrorInvalidValue, "row sweep arguments"};
   zc = zc < 2 ? 2 : (zc > d.nz ? d.nz : zc);
-  const CUtensorMap m[4] = {field_map(xin, d, kRowsTY), field_map(xin, d, 2), field_map(b, d, kRowsTY),
-                            field_map(b, d, 1)};
-  dim3 g(d.ny / kRowsTY, (d.nz + zc - 1) / zc);
-  const int nblk = (int)(g.x * g.y);
-  if (nblk > part_cap) part = nullptr;
-  const float inv = (float)(1.0 / st.diag), off = (float)st.off;
-  int* err = wait_error_flag();
-  const unsigned limit = wait_limit();
-  if (d.nx == 256)
-    rows_launch<2>(g, s, m, xout, bshift, d, zc, inv, off, part, err, limit);
-  else
-    rows_launch<1>(g, s, m, xout, bshift, d, zc, inv, off, part, err, limit);
-  return part ? nblk : 0;
+  return rows_sweep_any(xin, nullptr, xout, b, bshift, d, st, zc, part, part_cap, s);
+}
+
+int launch_rows_prolong_sweep(const float* xc, const float* xin, float* xout, const float* b, const double* bshift,
+                              Dims d, Stencil st, int zc, double* part, int part_cap, cudaStream_t s) {
+  if (!rows_sweep_ok(d) || !aligned16(xin) || !aligned16(xout) || !aligned16(b) || !aligned16(xc) || xin == xout ||
+      b == xout || xc == xout)
+    throw CudaError{cudaErrorInvalidValue, "prolongation + row sweep arguments"};
+  zc = zc < 2 ? 2 : (zc > d.nz ? d.nz : zc);
+  zc += zc & 1;  // even chunks: fine planes 2K - 1, 2K share their coarse pair in both march directions
+  return rows_sweep_any(xin, xc, xout, b, bshift, d, st, zc, part, part_cap, s);
 }
 
 
 bool zero_restrict_rows_ok(Dims d) { return rows_sweep_ok(d); }
 
 int zero_restrict_rows_default_zc(Dims d) {
-  int zc = rows_sweep_default_zc(d);
-  zc += zc & 1;  // even chunks: plane pairs of the restriction stay inside a chunk
-  return zc;
+  return rows_sweep_default_zc(d);  // even: plane pairs of the restriction stay inside a chunk
 }
 
 void launch_zero_restrict_rows(const float* b, const double* bshift, float* x, float* bc, Dims d, Stencil st,

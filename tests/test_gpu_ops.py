@@ -282,6 +282,57 @@ def test_vcycle_f32_sweep_counts(ibrd, dims, alpha, nu1, nu2, zero):
     assert rel_max(x.cpu().numpy().astype(np.float64), want) < 2e-5
 
 
+def _rows_levels(dims):
+    return [lv for lv in _levels(dims) if lv[0] in (128, 256) and lv[1] % 8 == 0 and lv[2] % 2 == 0 and lv[2] >= 4]
+
+
+@pytest.mark.parametrize("dims,alpha", ROWS_CASES + [((256, 64, 32), 0.0)])
+@pytest.mark.parametrize("nu2,zero", [(1, True), (2, True), (1, False)])
+@pytest.mark.parametrize("zc", [0, 2, 6])
+def test_prolongation_fused_into_row_sweep(ibrd, dims, alpha, nu2, zero, zc):
+    """On levels the row-resident sweep serves, the V-cycle adds the coarse-grid
+    correction (the trilinear prolongation of the coarse solution, Sec. III.E)
+    inside the first post-smoothing sweep, whose x reads then see x + P x_c,
+    instead of writing the corrected field with a separate kernel first. The
+    result equals, bit for bit, the V-cycle with the fusion switched off level
+    by level (same sweep kernel and CTAs, so the same per-CTA sums feed the mean
+    projection when alpha = 0), for one and two post-sweeps, from zero and from
+    a guess, at the built-in z-march depth and at depths with ragged last chunks
+    (nz = 8, 16, 32 with 6 planes per CTA); and it is the oracle's V-cycle
+    within FP32 rounding."""
+    import torch
+    nx, ny, nz = dims
+    rng = np.random.default_rng(71 + nu2 + 3 * zc)
+    b = rng.standard_normal((nz, ny, nx)).astype(np.float32)
+    x0 = rng.standard_normal((nz, ny, nx)).astype(np.float32)
+    out = []
+    for fused in (True, False):
+        g = ibrd.Grid(*dims, alpha=alpha)
+        for (lx, ly, lz) in _rows_levels(dims):
+            if zc:
+                ibrd.ibrd_tune_set(g.handle, 4, 0, lx, ly, lz, lx, zc)
+            if not fused:
+                ibrd.ibrd_tune_set(g.handle, 4, 2, lx, ly, lz, 1, 0)
+        x = torch.from_numpy(x0).cuda()
+        g.vcycle_f32(torch.from_numpy(b).cuda(), x, zero_initial_guess=zero, nu1=1, nu2=nu2)
+        out.append(x.cpu().numpy())
+    assert np.array_equal(out[0], out[1])
+    want = mg.vcycle(b.astype(np.float64), 1.0, 1.0, alpha, x0=None if zero else x0.astype(np.float64), nu1=1,
+                     nu2=nu2, exact_cells=32768, exact_side=64)
+    assert rel_max(out[0].astype(np.float64), want) < 2e-5
+
+
+def test_prolongation_switch_arguments(ibrd):
+    """The fusion switch is an FP32-only, hand-set entry: tx 0 or 1, zc 0."""
+    g = ibrd.Grid(128, 16, 8)
+    ibrd.ibrd_tune_set(g.handle, 4, 2, 128, 16, 8, 1, 0)
+    ibrd.ibrd_tune_set(g.handle, 4, 2, 128, 16, 8, 0, 0)
+    for bad in [(8, 2, 128, 16, 8, 1, 0), (4, 2, 128, 16, 8, 2, 0), (4, 2, 128, 16, 8, 1, 3),
+                (4, 3, 128, 16, 8, 0, 0)]:
+        with pytest.raises(ibrd.IbrdError):
+            ibrd.ibrd_tune_set(g.handle, *bad)
+
+
 def test_bounded_wait_gives_up_with_timeout_status(ibrd):
     """A bound of zero polls makes every plane wait of the row sweep give up:
     each CTA drains its copies in flight and stops, and the FP32 V-cycle and a
