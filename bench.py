@@ -769,6 +769,45 @@ def run_kernel_case_fp64(args):
     log("[bench] FP64 kernel case done")
 
 
+def run_kernel_case_resid(args):
+    """FP64 residuals r = b - A c through ibrd_residual on a 256^3 field (c =
+    1000 + N(0, 1), b = N(0, 1); about 0.4 GB on the device), timed against
+    FP64 apply_L with CUDA events over ten calls each (printed), then one
+    residual inside a profiler range: the small case for ncu captures of the
+    fixed-point residual and its max pass."""
+    import torch
+    from paper_1306_3159_gb300 import build as pbuild
+    pbuild.build()
+    import paper_1306_3159_gb300 as p
+    n = 256
+    grid = p.Grid(n, n, n, stream=torch.cuda.current_stream().cuda_stream)
+    gen = torch.Generator("cuda").manual_seed(3)
+    c = 1e3 + torch.randn((n, n, n), dtype=torch.float64, device="cuda", generator=gen)
+    b = torch.randn((n, n, n), dtype=torch.float64, device="cuda", generator=gen)
+    r = torch.empty_like(c)
+    y = torch.empty_like(c)
+    for _ in range(3):
+        grid.residual(b, c, r)
+        grid.apply_L(c, y)
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    e[0].record()
+    for _ in range(10):
+        grid.residual(b, c, r)
+    e[1].record()
+    for _ in range(10):
+        grid.apply_L(c, y)
+    e[2].record()
+    torch.cuda.synchronize()
+    log(f"[bench] residual {e[0].elapsed_time(e[1]) * 100:.1f} us per call, FP64 apply_L "
+        f"{e[1].elapsed_time(e[2]) * 100:.1f} us per call")
+    torch.cuda.profiler.start()
+    grid.residual(b, c, r)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    log("[bench] residual kernel case done")
+
+
 def run_kernel_case(args):
     """FP32 V-cycles (nu = 1/1, as in the chosen solves) on a 256^3 field
     (about 0.3 GB on the device) with a profiler range around one V-cycle: the
@@ -910,6 +949,7 @@ def main():
     ap.add_argument("--ncu-step", action="store_true", help="profiler range around one step, then exit")
     ap.add_argument("--kernel-case", action="store_true", help="FP32 V-cycles at 256^3 for ncu, then exit")
     ap.add_argument("--kernel-case-fp64", action="store_true", help="FP64 A c at 256^3 for ncu, then exit")
+    ap.add_argument("--kernel-case-resid", action="store_true", help="FP64 residual at 256^3 for ncu, then exit")
     args = ap.parse_args()
     if args.cpu_steps:
         print(json.dumps(run_cpu_steps(args.cpu_warmup, args.cpu_steps)), flush=True)
@@ -921,6 +961,8 @@ def main():
         run_kernel_case(args)
     elif args.kernel_case_fp64:
         run_kernel_case_fp64(args)
+    elif args.kernel_case_resid:
+        run_kernel_case_resid(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -190,6 +190,20 @@ ibrd_status ibrd_set_blobs(ibrd_grid g, const double* q, int n_blobs);
    overlap. */
 ibrd_status ibrd_apply_L(ibrd_grid g, const double* c, double* y);
 
+/* r = rhs - A c (Sec. III.A, Eq. Helmholtz), the grid part of every FP64
+   residual the solvers form (each refinement step's, each restart's, for
+   tolerances of 1e-13 and above). On grids with nx a multiple of 32 and ny a
+   multiple of 8, while the largest |c| lies in [2^-900, 2^900]: c scaled by a
+   power of two into 64-bit integers, so that L c (the neighbour sums) is
+   exact, then r = fma(-alpha, c, fma(chi / h^2 2^-S, L c, rhs)) -- within
+   2^-52 of |r| + |alpha c| + chi / h^2 |L c| per cell plus 2^-55 chi / h^2
+   max|c|, where the FP64 form rounds terms of size 6 chi / h^2 |c| -- with
+   one or two FP64 instructions per cell (GB300's FP64 pipe issues about two
+   per SM per clock). Elsewhere the FP64 form. Non-finite c gives non-finite
+   r. All fields device, N_c doubles, non-overlapping; asynchronous on the
+   handle's stream. */
+ibrd_status ibrd_residual(ibrd_grid g, const double* rhs, const double* c, double* r);
+
 /* One multigrid V-cycle (FP64) for A x = rhs (Sec. III.E): red-black
    Gauss-Seidel (nu1 = nu2 = 2), 8-cell-mean restriction, trilinear
    cell-centred prolongation, exact coarsest solve. With alpha = 0 the

@@ -21,6 +21,7 @@ STATUS = {0: "IBRD_OK", 1: "IBRD_ERR_ARG", 2: "IBRD_ERR_CUDA", 3: "IBRD_ERR_OOM"
 
 # Every entry point declared in include/ibrd.h.
 EXPORTED = ["ibrd_default_opts", "ibrd_grid_create", "ibrd_grid_destroy", "ibrd_set_blobs", "ibrd_apply_L",
+            "ibrd_residual",
             "ibrd_vcycle", "ibrd_vcycle_f32", "ibrd_vcycle_f32_sweeps", "ibrd_vcycle_noalloc", "ibrd_spread", "ibrd_interp", "ibrd_solve_reaction", "ibrd_solve_saddle",
             "ibrd_solve_reaction_batch", "ibrd_solve_saddle_batch", "ibrd_solve_many", "ibrd_autotune", "ibrd_tune_set",
             "ibrd_tune_clear", "ibrd_set_wait_limit", "ibrd_gnn_num_params", "ibrd_gnn_create", "ibrd_gnn_destroy", "ibrd_gnn_last_error",
@@ -103,6 +104,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ibrd_set_blobs.restype = i
     lib.ibrd_apply_L.argtypes = [vp, vp, vp]
     lib.ibrd_apply_L.restype = i
+    lib.ibrd_residual.argtypes = [vp, vp, vp, vp]
+    lib.ibrd_residual.restype = i
     lib.ibrd_vcycle.argtypes = [vp, vp, vp, i]
     lib.ibrd_vcycle.restype = i
     lib.ibrd_vcycle_f32.argtypes = [vp, vp, vp, i]
@@ -230,6 +233,10 @@ def ibrd_set_blobs(g, q, n=None):
 
 def ibrd_apply_L(g, c, y):
     _check(g, load_library().ibrd_apply_L(g, _ptr(c), _ptr(y)))
+
+
+def ibrd_residual(g, rhs, c, r):
+    _check(g, load_library().ibrd_residual(g, _ptr(rhs), _ptr(c), _ptr(r)))
 
 
 def ibrd_vcycle(g, rhs, x, zero_initial_guess=True):
@@ -479,6 +486,11 @@ class Grid:
         y = self.field() if y is None else y
         ibrd_apply_L(self.handle, c, y)
         return y
+
+    def residual(self, rhs, c, r=None):
+        r = self.field() if r is None else r
+        ibrd_residual(self.handle, rhs, c, r)
+        return r
 
     def vcycle(self, rhs, x=None, zero_initial_guess=True):
         x = self.field() if x is None else x

@@ -52,6 +52,7 @@ enum Slot {
   S_RFLAG,    // Gram-Schmidt second pass taken in this iteration (0/1)
   S_RCOUNT,   // second passes taken in this solve
   S_WAIT,     // nonzero bits: a bounded device wait gave up (written as an int)
+  S_XMAX,     // largest |x| of a residual's iterate (its bits; fixed-point scale)
   S_UB = 64,  // mean of S U_j for the inner iterations j = 0..m (64 slots)
   S_UX = 128, // mean of A~^-1 S U_j (64 slots)
   S_COUNT = 192
@@ -1523,6 +1524,14 @@ void ensure_nvec(ibrd_grid g, int m) {
 }
 
 // ---------------------------------------------------------------- operators
+// The FP64 residual of a solve in fixed point (launch_residual): within
+// 2^-52 of its terms per cell, plus 2^-55 chi / h^2 max|c| from the scaling,
+// which in cells far below the largest |c| can exceed the FP64 stencil's
+// rounding; solves asking for relative residuals below kFxTolMin form it with
+// the FP64 stencil.
+constexpr double kFxTolMin = 1e-13;
+double* fx_scratch(ibrd_grid g, const ibrd_solve_opts& o) { return o.tol >= kFxTolMin ? g->scal + S_XMAX : nullptr; }
+
 // B c = alpha c - chi L c + S (kappa * J c)  (Eq. unsteady_system / steady_state)
 // on Krylov vectors of type E; the preconditioner is V-cycles in T (FP32
 // V-cycles inside FP64 FGMRES convert on the way in and out).
@@ -1551,7 +1560,7 @@ struct ReactionOp : LinOp<E> {
   }
   void residual(const E* b, const E* x, E* r) override {
     launch_interp<E>(g->blobs, g->d, x, 1.0, g->nv[0], g->s);
-    launch_residual<E>(x, b, r, g->d, stencil(g->h, g->chi, g->alpha), g->s);
+    launch_residual<E>(x, b, r, g->d, stencil(g->h, g->chi, g->alpha), fx_scratch(g, o), g->s);
     launch_spread<E>(g->blobs, g->d, g->nv[0], kappa, -inv_h3(g), r, 1, g->s);
   }
   // n V-cycles of (sigma I - chi L) (Eq. Pinv_Poisson)
@@ -1594,7 +1603,7 @@ struct SaddleOp : LinOp<E> {
   }
   void residual(const E* b, const E* x, E* r) override {
     const size_t nc = g->d.n();
-    launch_residual<E>(x, b, r, g->d, stencil(g->h, g->chi, g->alpha), g->s);
+    launch_residual<E>(x, b, r, g->d, stencil(g->h, g->chi, g->alpha), fx_scratch(g, o), g->s);
     launch_spread<E, E>(g->blobs, g->d, x + nc, nullptr, -zeta * inv_h3(g), r, 1, g->s);
     launch_interp<E, E>(g->blobs, g->d, x, -xi, r + nc, g->s);
     launch_axpby<E>(1.0, b + nc, 1.0, r + nc, g->blobs.n, g->s);
@@ -2669,6 +2678,14 @@ ibrd_status ibrd_apply_L(ibrd_grid g, const double* c, double* y) {
   return guarded(g, "ibrd_apply_L", [&]() {
     if (!c || !y || c == y) throw ArgError{IBRD_ERR_ARG, "null or aliased field"};
     launch_apply_A<double>(c, y, g->d, stencil(g->h, g->chi, g->alpha), g->s);
+    return IBRD_OK;
+  });
+}
+
+ibrd_status ibrd_residual(ibrd_grid g, const double* rhs, const double* c, double* r) {
+  return guarded(g, "ibrd_residual", [&]() {
+    if (!rhs || !c || !r || c == r || rhs == r) throw ArgError{IBRD_ERR_ARG, "null or aliased field"};
+    launch_residual<double>(c, rhs, r, g->d, stencil(g->h, g->chi, g->alpha), g->scal + S_XMAX, g->s);
     return IBRD_OK;
   });
 }

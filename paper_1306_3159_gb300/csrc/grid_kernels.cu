@@ -49,6 +49,222 @@ __global__ void __launch_bounds__(BX* BY) k_apply(const T* __restrict__ x, const
   }
 }
 
+// ---------------------------------------------------------------- FP64 residual, fixed point
+// r = b - A x = b - alpha x + off L x with L x = (sum of the 6 neighbours) -
+// 6 x. Every x is scaled by 2^S into a 64-bit integer X (S from the field's
+// largest |x|, so that |X| < 2^59): L X is then an exact integer sum, where
+// the FP64 form diag x - off s rounds terms of size 6 off |x|, far above |r|
+// near convergence. r = fma(-alpha, x, fma(off 2^-S, double(L X), b)) then
+// rounds once per FMA: within 2^-52 of |r| + off |L x| plus the scaling's
+// 2^-56 off max|x|, with one or two FP64 instructions per cell (the integer
+// work runs on the integer pipe; GB300's FP64 pipe issues about two
+// instructions per SM per clock).
+
+// v 2^S rounded to an integer, for |v| 2^S < 2^59
+__device__ __forceinline__ long long to_fixed(double v, int S) {
+  const unsigned hi = (unsigned)__double2hiint(v), lo = (unsigned)__double2loint(v);
+  const int e = (hi >> 20) & 0x7FF;
+  if (e == 0) return 0;
+  const unsigned long long m = ((unsigned long long)((hi & 0xFFFFFu) | 0x100000u) << 32) | lo;
+  const int sh = e - 1075 + S;  // v 2^S = m 2^sh, sh <= 6
+  unsigned long long X;
+  if (sh >= 0)
+    X = m << sh;
+  else if (sh > -63)
+    X = ((m >> (-sh - 1)) + 1) >> 1;  // nearest, ties up
+  else
+    X = 0;
+  return (int)hi < 0 ? -(long long)X : (long long)X;
+}
+// a 64-bit integer as the nearest double (ties to even), from the bits
+__device__ __forceinline__ double ll2d_bits(long long L) {
+  if (L == 0) return 0.0;
+  const unsigned long long sgn = (unsigned long long)L & 0x8000000000000000ull;
+  unsigned long long a = L < 0 ? 0ull - (unsigned long long)L : (unsigned long long)L;
+  const int lz = __clzll((long long)a);
+  a <<= lz;  // leading one at bit 63
+  const unsigned long long mant = (a >> 11) & 0xFFFFFFFFFFFFFull;
+  const unsigned rest = (unsigned)a & 0x7FFu;
+  const unsigned long long up = (rest > 0x400u) | ((rest == 0x400u) & ((unsigned)mant & 1u));
+  return __longlong_as_double((long long)(sgn | ((((unsigned long long)(1086 - lz)) << 52) + mant + up)));
+}
+
+// Largest |x| as the bits of a double (monotonic in |x| for the magnitude bits),
+// into *out (zeroed before). Bits at or above those of infinity: x not finite.
+__global__ void __launch_bounds__(256) k_absmax_bits(const double* __restrict__ x, size_t n, int vec,
+                                                     unsigned long long* __restrict__ out) {
+  unsigned long long m = 0;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  auto take = [&](double v) {
+    const unsigned long long a = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
+    m = a > m ? a : m;
+  };
+  if (vec) {  // 16-byte aligned: pairs, then the odd last entry
+    for (size_t i = t; i < n / 2; i += stride) {
+      const double2 v = reinterpret_cast<const double2*>(x)[i];
+      take(v.x);
+      take(v.y);
+    }
+    if ((n & 1) && t == 0) take(x[n - 1]);
+  } else {
+    for (size_t i = t; i < n; i += stride) take(x[i]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long v = __shfl_xor_sync(0xffffffffu, m, o);
+    m = v > m ? v : m;
+  }
+  __shared__ unsigned long long wm[8];
+  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = wm[w] > m ? wm[w] : m;
+    atomicMax(out, m);
+  }
+}
+
+// exponent fields of the largest |x| the fixed-point form takes (off 2^-S
+// and the scaled values stay far inside the double range)
+constexpr int kFxEmin = 1023 - 900, kFxEmax = 1023 + 900;
+
+// y = b - A x. Block: 32 x TY threads; a thread owns CPT consecutive cells of
+// a row (tile 32 CPT x TY) and marches zc planes in z with the z-neighbours
+// as fixed-point values in registers, loading the next plane's x, b, halo row
+// and tile-edge value one plane ahead. A plane's values go through a
+// double-buffered shared tile for the y-neighbours (warps 0 and TY - 1 also
+// convert the halo rows); x-neighbours come from the thread itself, its
+// lanes' neighbours (shuffles), or, at the tile's edges, from the edge value
+// every lane loads (lane 0 the left one, lane 31 the right one). Needs
+// nx % (32 CPT) == 0 and ny % TY == 0.
+template <int TY, int CPT>
+__global__ void __launch_bounds__(32 * TY) k_resid_fx(const double* __restrict__ x, const double* __restrict__ b,
+                                                      double* __restrict__ y, int nx, int ny, int nz, int zc,
+                                                      double alpha, double off, double diag,
+                                                      const unsigned long long* __restrict__ xmax) {
+  constexpr int TW = 32 * CPT;
+  __shared__ long long XS[2][TY + 2][TW];
+  const int lane = threadIdx.x, ty = threadIdx.y;
+  const int i0 = blockIdx.x * TW, ic = i0 + lane * CPT, j0 = blockIdx.y * TY, j = j0 + ty;
+  const int k0 = blockIdx.z * zc, k1 = min(k0 + zc, nz);
+  const size_t plane = (size_t)nx * ny, rj = (size_t)j * nx;
+  auto at = [&](int k, size_t row, int i) { return (size_t)k * plane + row + i; };
+  const int emax = (int)(*xmax >> 52);
+  if (emax < kFxEmin || emax > kFxEmax) {
+    // the largest |x| is outside the fixed-point range (or x is not finite):
+    // the FP64 stencil
+    const size_t rjm = (size_t)wrap_dec(j, ny) * nx, rjp = (size_t)wrap_inc(j, ny) * nx;
+    for (int k = k0; k < k1; ++k) {
+      const int km = wrap_dec(k, nz), kp = wrap_inc(k, nz);
+#pragma unroll
+      for (int q = 0; q < CPT; ++q) {
+        const int i = ic + q;
+        const double s = ((x[at(k, rj, wrap_dec(i, nx))] + x[at(k, rj, wrap_inc(i, nx))]) +
+                          (x[at(k, rjm, i)] + x[at(k, rjp, i)])) + (x[at(km, rj, i)] + x[at(kp, rj, i)]);
+        y[at(k, rj, i)] = b[at(k, rj, i)] - (diag * x[at(k, rj, i)] - off * s);
+      }
+    }
+    return;
+  }
+  const int S = 1081 - emax;  // |x| < 2^(emax - 1022), so |x| 2^S < 2^59
+  const double offs = off * __hiloint2double((1023 - S) << 20, 0);  // off 2^-S, exactly
+  const bool halo = ty == 0 || ty == TY - 1;
+  const int hrow = ty == 0 ? 0 : TY + 1;
+  const size_t rh = (size_t)(ty == 0 ? wrap_dec(j0, ny) : wrap_inc(j0 + TY - 1, ny)) * nx;
+  const int ie = lane == 0 ? wrap_dec(i0, nx) : wrap_inc(i0 + TW - 1, nx);  // this lane's tile-edge cell
+  const bool use_alpha = alpha != 0.0;
+  struct Vals {
+    double v[CPT];
+  };
+  auto load_row = [&](size_t o) {
+    Vals r;
+    if constexpr (CPT == 2) {
+      const double2 t = *reinterpret_cast<const double2*>(x + o);
+      r.v[0] = t.x;
+      r.v[1] = t.y;
+    } else {
+#pragma unroll
+      for (int q = 0; q < CPT; ++q) r.v[q] = x[o + q];
+    }
+    return r;
+  };
+  auto load_b = [&](size_t o) {
+    Vals r;
+    if constexpr (CPT == 2) {
+      const double2 t = *reinterpret_cast<const double2*>(b + o);
+      r.v[0] = t.x;
+      r.v[1] = t.y;
+    } else {
+#pragma unroll
+      for (int q = 0; q < CPT; ++q) r.v[q] = b[o + q];
+    }
+    return r;
+  };
+  long long Xm[CPT], X0[CPT], Xp[CPT];
+  Vals xc = load_row(at(k0, rj, ic));       // plane k (the alpha term)
+  Vals xn = load_row(at(wrap_inc(k0, nz), rj, ic));  // plane k + 1
+  {
+    const Vals t = load_row(at(wrap_dec(k0, nz), rj, ic));
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) {
+      Xm[q] = to_fixed(t.v[q], S);
+      X0[q] = to_fixed(xc.v[q], S);
+    }
+  }
+  Vals bv = load_b(at(k0, rj, ic));
+  Vals hv = halo ? load_row(at(k0, rh, ic)) : Vals{};
+  double ev = x[at(k0, rj, ie)];
+  for (int k = k0; k < k1; ++k) {
+    const int buf = (k - k0) & 1;
+    // next plane's loads first (they land while this plane is computed)
+    const bool more = k + 1 < k1;
+    const int kn = more ? k + 1 : k;
+    const Vals xn2 = load_row(at(wrap_inc(kn, nz), rj, ic));
+    const Vals bn = load_b(at(kn, rj, ic));
+    const Vals hn = halo ? load_row(at(kn, rh, ic)) : Vals{};
+    const double en = x[at(kn, rj, ie)];
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) {
+      Xp[q] = to_fixed(xn.v[q], S);
+      XS[buf][ty + 1][lane * CPT + q] = X0[q];
+    }
+    if (halo) {
+#pragma unroll
+      for (int q = 0; q < CPT; ++q) XS[buf][hrow][lane * CPT + q] = to_fixed(hv.v[q], S);
+    }
+    const long long Xedge = to_fixed(ev, S);
+    long long Xw = __shfl_up_sync(0xffffffffu, X0[CPT - 1], 1), Xe = __shfl_down_sync(0xffffffffu, X0[0], 1);
+    if (lane == 0) Xw = Xedge;
+    if (lane == 31) Xe = Xedge;
+    __syncthreads();
+    double r[CPT];
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) {
+      const long long w = q == 0 ? Xw : X0[q - 1], e = q == CPT - 1 ? Xe : X0[q + 1];
+      const long long L = ((w + e) + (XS[buf][ty][lane * CPT + q] + XS[buf][ty + 2][lane * CPT + q])) +
+                          (Xm[q] + Xp[q]) - 6 * X0[q];
+      r[q] = fma(offs, ll2d_bits(L), bv.v[q]);
+      if (use_alpha) r[q] = fma(-alpha, xc.v[q], r[q]);
+    }
+    if constexpr (CPT == 2) {
+      *reinterpret_cast<double2*>(y + at(k, rj, ic)) = make_double2(r[0], r[1]);
+    } else {
+#pragma unroll
+      for (int q = 0; q < CPT; ++q) y[at(k, rj, ic + q)] = r[q];
+    }
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) {
+      Xm[q] = X0[q];
+      X0[q] = Xp[q];
+    }
+    xc = xn;
+    xn = xn2;
+    bv = bn;
+    hv = hn;
+    ev = en;
+  }
+}
+
 // FP32 y = A x with 4 cells per thread (16-byte rows; nx % 4 == 0, aligned
 // fields): z-march over zc planes with the z-neighbour 4-vectors in registers,
 // y-neighbour 4-vectors and the two x-edge scalars from L1/L2.
@@ -509,8 +725,14 @@ __global__ void k_convert(const Tx* __restrict__ x, Ty* __restrict__ y, size_t n
                           const double* __restrict__ shift) {
   const double sh = shift ? *shift : 0.0;
   if (a == 1.0 && sh == 0.0) {
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-      y[i] = (Ty)x[i];
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+      if constexpr (sizeof(Tx) == 8 && sizeof(Ty) == 4)
+        y[i] = d2f_bits(x[i]);
+      else if constexpr (sizeof(Tx) == 4 && sizeof(Ty) == 8)
+        y[i] = f2d_bits(x[i]);
+      else
+        y[i] = (Ty)x[i];
+    }
   } else if (sizeof(Ty) == 4 && sizeof(Tx) == 4) {
     const float af = (float)a, sf = (float)sh;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
@@ -584,7 +806,7 @@ __global__ void __launch_bounds__(kRedThreads) k_convert_sq(const double* __rest
     float run = 0.f;
 #pragma unroll 4
     for (int r = 0; r < 8 && i < n; ++r, i += stride) {
-      const float v = (float)x[i] * sigma;
+      const float v = d2f_bits(x[i]) * sigma;
       y[i] = v;
       run = fmaf(v, v, run);
     }
@@ -599,7 +821,7 @@ __global__ void k_add_scaled(double a, const double* __restrict__ div_dev, const
                              double* __restrict__ x, size_t n) {
   if (div_dev) a = 1.0 / *div_dev;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    x[i] = fma(a, (double)d[i], x[i]);
+    x[i] = fma(a, f2d_bits(d[i]), x[i]);
 }
 
 template <typename T>
@@ -646,10 +868,42 @@ void launch_apply_A(const T* x, T* y, Dims d, Stencil st, cudaStream_t s) {
   prof_end(c, s, "apply_A", 2.0 * sizeof(T) * d.n());
 }
 
+bool resid_fx_ok(Dims d, Stencil st) {
+  return d.nx % 32 == 0 && d.ny % 8 == 0 && st.off > 0.0 && std::isfinite(st.diag) && std::isfinite(st.off);
+}
+
 template <typename T>
-void launch_residual(const T* x, const T* b, T* y, Dims d, Stencil st, cudaStream_t s) {
-  dim3 g((d.nx + BX - 1) / BX, (d.ny + BY - 1) / BY, (d.nz + ZCH - 1) / ZCH);
+void launch_residual(const T* x, const T* b, T* y, Dims d, Stencil st, double* scratch, cudaStream_t s) {
   const int c = pcls<T>(P_APPLY64, P_APPLY32);
+  if constexpr (sizeof(T) == 8) {
+    if (scratch && resid_fx_ok(d, st)) {
+      // the field's largest |x| (its bits) sets the fixed-point scale
+      unsigned long long* xmax = reinterpret_cast<unsigned long long*>(scratch);
+      IBRD_CUDA(cudaMemsetAsync(xmax, 0, sizeof(unsigned long long), s));
+      prof_begin(P_REDUCE, s);
+      k_absmax_bits<<<stream_blocks(d.n() / 2, 256), 256, 0, s>>>(x, d.n(), aligned16(x) ? 1 : 0, xmax);
+      prof_end(P_REDUCE, s, "absmax", 8.0 * d.n());
+      const double alpha = st.diag - 6.0 * st.off;
+      constexpr int TY = 8;
+      auto go = [&](auto kern, int cpt) {
+        const int cols = (d.nx / (32 * cpt)) * (d.ny / TY);
+        int chunks = (152 * 6) / cols;  // about one wave of 6 resident blocks per SM
+        chunks = chunks < 1 ? 1 : chunks;
+        int zc = (d.nz + chunks - 1) / chunks;
+        zc = zc < 1 ? 1 : zc;
+        dim3 g(d.nx / (32 * cpt), d.ny / TY, (d.nz + zc - 1) / zc);
+        prof_begin(c, s);
+        kern<<<g, dim3(32, TY), 0, s>>>(x, b, y, d.nx, d.ny, d.nz, zc, alpha, st.off, st.diag, xmax);
+        prof_end(c, s, "residual_fx", 3.0 * sizeof(T) * d.n());
+      };
+      if (d.nx % 64 == 0 && aligned16(x) && aligned16(b) && aligned16(y))
+        go(k_resid_fx<TY, 2>, 2);
+      else
+        go(k_resid_fx<TY, 1>, 1);
+      return;
+    }
+  }
+  dim3 g((d.nx + BX - 1) / BX, (d.ny + BY - 1) / BY, (d.nz + ZCH - 1) / ZCH);
   prof_begin(c, s);
   k_apply<T, true><<<g, dim3(BX, BY), 0, s>>>(x, b, y, d.nx, d.ny, d.nz, (T)st.diag, (T)st.off);
   prof_end(c, s, "residual", 3.0 * sizeof(T) * d.n());
@@ -847,7 +1101,7 @@ void launch_nonfinite(const T* x, size_t n, int* flag, cudaStream_t s) {
 
 #define IBRD_INST(T)                                                                                   \
   template void launch_apply_A<T>(const T*, T*, Dims, Stencil, cudaStream_t);                         \
-  template void launch_residual<T>(const T*, const T*, T*, Dims, Stencil, cudaStream_t);              \
+  template void launch_residual<T>(const T*, const T*, T*, Dims, Stencil, double*, cudaStream_t);     \
   template void launch_coarse_solve<T>(const T*, const T*, T*, Dims, cudaStream_t);                   \
   template void launch_coarse_table<T>(T*, Dims, Stencil, int, cudaStream_t);                         \
   template void launch_sum<T>(const T*, size_t, double*, double*, double, cudaStream_t);              \

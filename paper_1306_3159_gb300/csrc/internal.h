@@ -91,6 +91,39 @@ struct Stencil {
   double diag, off;
 };
 
+// ---------------------------------------------------------------- FP64 off the FP64 pipe
+// GB300 issues about two FP64 instructions per SM per clock -- FP64
+// arithmetic and the double <-> float conversion instructions alike --
+// against 128 FP32 operations. Streaming FP64 kernels therefore convert with
+// integer operations on the bit patterns and do their arithmetic in FP32
+// (float-float pairs where FP64 accuracy is needed).
+#ifdef __CUDACC__
+// double -> float, rounded to nearest even, from the bits (the conversion
+// instruction only for values whose float is zero, subnormal or not finite)
+__device__ __forceinline__ float d2f_bits(double v) {
+  const unsigned hi = (unsigned)__double2hiint(v), lo = (unsigned)__double2loint(v);
+  const int E = (int)((hi >> 20) & 0x7FF) - 896;  // float exponent field
+  if (E >= 1 && E <= 254) {
+    const unsigned t = ((hi & 0xFFFFF) << 3) | (lo >> 29);  // top 23 fraction bits
+    const unsigned rest = lo & 0x1FFFFFFFu;                 // the 29 dropped ones
+    const unsigned up = (rest > 0x10000000u) | ((rest == 0x10000000u) & t);
+    return __uint_as_float((hi & 0x80000000u) | (((unsigned)E << 23) + t + up));  // a carry moves the exponent
+  }
+  if (((hi & 0x7FFFFFFFu) | lo) == 0) return __uint_as_float(hi & 0x80000000u);
+  return (float)v;
+}
+// float -> double, exact
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned E = (b >> 23) & 0xFF;
+  if (E - 1u < 254u)
+    return __hiloint2double((int)((b & 0x80000000u) | ((E + 896u) << 20) | ((b & 0x7FFFFFu) >> 3)),
+                            (int)((b & 7u) << 29));
+  if ((b & 0x7FFFFFFFu) == 0) return __hiloint2double((int)(b & 0x80000000u), 0);
+  return (double)f;
+}
+#endif
+
 // ---------------------------------------------------------------- reductions
 // Deterministic two-stage reductions use a fixed grid of kRedBlocks blocks.
 constexpr int kRedBlocks = 608;   // 4 x 152 SMs
@@ -100,9 +133,13 @@ constexpr int kRedThreads = 256;
 // All launchers enqueue on `s` and check the launch.
 template <typename T>
 void launch_apply_A(const T* x, T* y, Dims d, Stencil st, cudaStream_t s);
-// y = b - A x
+// y = b - A x. FP64 with scratch (one device double) on grids with nx % 32 ==
+// 0 and ny % 8 == 0 (resid_fx_ok): the Laplacian in 64-bit fixed point (exact
+// neighbour sums), then two FMAs, mostly off the FP64 pipe; otherwise, and
+// for FP32, the plain stencil.
 template <typename T>
-void launch_residual(const T* x, const T* b, T* y, Dims d, Stencil st, cudaStream_t s);
+void launch_residual(const T* x, const T* b, T* y, Dims d, Stencil st, double* scratch, cudaStream_t s);
+bool resid_fx_ok(Dims d, Stencil st);
 // One full red-black Gauss-Seidel sweep (red = (i+j+k) even) for A x = b -
 // *bshift (bshift nullable). On levels where the fused one-pass kernel
 // applies it reads xin and writes xout (xin != xout) and returns the number

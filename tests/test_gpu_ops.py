@@ -38,6 +38,103 @@ def test_apply_L(ibrd, dims, h, chi, alpha):
     assert rel_max(y, op.apply_A(c, h, chi, alpha)) < 1e-14
 
 
+def _exact_residual(b, c, h, chi, alpha):
+    """r = b - (diag c - off * sum of the 6 neighbours) in exact rational
+    arithmetic on the library's double coefficients (off = chi / h^2, diag =
+    alpha + 6 off, as the library rounds them)."""
+    from fractions import Fraction as F
+    off = chi / (h * h)
+    diag = alpha + 6.0 * off
+    to_q = np.vectorize(F, otypes=[object])
+    cq = to_q(c)
+    s = sum(np.roll(cq, sh, axis=a) for a in range(3) for sh in (1, -1))
+    return to_q(b) - (F(diag) * cq - F(off) * s)
+
+
+def _abs_err(r, exact):
+    from fractions import Fraction as F
+    return np.vectorize(lambda g, e: float(abs(F(float(g)) - e)), otypes=[float])(r, exact)
+
+
+# dims, h, chi, alpha, whether the fixed-point form applies (nx % 32 == 0 and ny % 8 == 0)
+RESID_CASES = [((32, 8, 4), 1.0, 1.0, 0.0, True), ((64, 32, 12), 0.5, 1.3, 0.7, True),
+               ((96, 16, 8), 1.0, 2.0, 0.0, True), ((20, 12, 24), 0.7, 1.3, 0.25, False)]
+
+
+@pytest.mark.parametrize("dims,h,chi,alpha,fx", RESID_CASES)
+@pytest.mark.parametrize("field", ["random", "cancelling"])
+def test_residual_against_exact_arithmetic(ibrd, dims, h, chi, alpha, fx, field):
+    """ibrd_residual (the grid part of every FP64 residual of the solvers)
+    against r = b - A c in exact rational arithmetic, cell by cell. Where the
+    fixed-point form applies the error is within 2^-52 of |r| + |alpha c| +
+    chi/h^2 |L c| plus 2^-55 chi/h^2 max|c| from the scaling (bounded here by
+    2^-50 and 2^-54), and with alpha = 0 on a smooth field of size 1e6 (the
+    neighbour sums cancel to 1e-4 of their terms, as near convergence) it is
+    over ten times below the FP64 stencil's error. Elsewhere the FP64
+    stencil's bound holds (2^-49 of diag |c| + chi/h^2 sum |c_nb| + |b|)."""
+    nx, ny, nz = dims
+    rng = np.random.default_rng(5 + nx)
+    off = chi / (h * h)
+    if field == "random":
+        c = rng.standard_normal((nz, ny, nx))
+        b = rng.standard_normal((nz, ny, nx))
+    else:
+        k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+        smooth = np.sin(2 * np.pi * i / nx) * np.cos(2 * np.pi * j / ny) + np.sin(2 * np.pi * k / nz)
+        c = 1e6 + 1e2 * smooth + 1e-3 * rng.standard_normal((nz, ny, nx))
+        b = op.apply_A(c, h, chi, alpha) + 1e-3 * rng.standard_normal((nz, ny, nx))
+    g = ibrd.Grid(*dims, h=h, chi=chi, alpha=alpha)
+    r = host(g.residual(dev(b), dev(c)))
+    exact = _exact_residual(b, c, h, chi, alpha)
+    err = _abs_err(r, exact)
+    nb_abs_diff = sum(np.abs(np.roll(c, sh, axis=a) - c) for a in range(3) for sh in (1, -1))
+    nb_abs = sum(np.abs(np.roll(c, sh, axis=a)) for a in range(3) for sh in (1, -1))
+    if fx:
+        bound = 2.0 ** -50 * (np.abs(b) + abs(alpha) * np.abs(c) + off * nb_abs_diff) \
+            + 2.0 ** -54 * off * np.abs(c).max()
+    else:
+        bound = 2.0 ** -49 * (np.abs(b) + (alpha + 6 * off) * np.abs(c) + off * nb_abs)
+    assert (err <= bound).all(), float((err / bound).max())
+    if fx and field == "cancelling" and alpha == 0.0:
+        err64 = _abs_err(b - op.apply_A(c, h, chi, alpha), exact)
+        assert err.max() < 0.1 * err64.max(), (err.max(), err64.max())
+
+
+def test_residual_special_values(ibrd):
+    """The fixed-point residual's edges: integer fields with binary
+    coefficients come out exact; c = 0 gives b bit for bit; a NaN in c makes
+    its cell and its six neighbours NaN and leaves the rest finite; c beyond
+    the fixed-point window (1e300) takes the FP64 stencil, within its bound;
+    right-hand sides of very different sizes (1e-30 next to 1) stay within the
+    fixed-point bound."""
+    dims = (64, 16, 8)
+    nx, ny, nz = dims
+    rng = np.random.default_rng(77)
+    g = ibrd.Grid(*dims, h=1.0, chi=1.0, alpha=0.5)
+    c = rng.integers(-2 ** 20, 2 ** 20, (nz, ny, nx)).astype(np.float64)
+    b = rng.integers(-2 ** 20, 2 ** 20, (nz, ny, nx)).astype(np.float64)
+    r = host(g.residual(dev(b), dev(c)))
+    assert np.array_equal(r, b - op.apply_A(c, 1.0, 1.0, 0.5))  # every value exact in FP64 here
+    bf = rng.standard_normal((nz, ny, nx))
+    assert np.array_equal(host(g.residual(dev(bf), dev(np.zeros_like(bf)))), bf)
+    cn = rng.standard_normal((nz, ny, nx))
+    cn[3, 5, 7] = np.nan
+    rn = host(g.residual(dev(bf), dev(cn)))
+    bad = np.zeros_like(rn, dtype=bool)
+    for (kk, jj, ii) in [(3, 5, 7), (2, 5, 7), (4, 5, 7), (3, 4, 7), (3, 6, 7), (3, 5, 6), (3, 5, 8)]:
+        bad[kk, jj, ii] = True
+    assert np.isnan(rn[bad]).all() and np.isfinite(rn[~bad]).all()
+    cc = 1e300 * rng.standard_normal((nz, ny, nx))
+    rr = host(g.residual(dev(bf), dev(cc)))
+    nb = sum(np.abs(np.roll(cc, sh, axis=a)) for a in range(3) for sh in (1, -1))
+    assert (np.abs(rr - (bf - op.apply_A(cc, 1.0, 1.0, 0.5))) <= 2.0 ** -49 * (np.abs(bf) + 6.5 * np.abs(cc) + nb)).all()
+    bt = np.where(rng.random((nz, ny, nx)) < 0.1, 1e-30, 1.0)
+    rt = host(g.residual(dev(bt), dev(bf)))
+    exact = _exact_residual(bt, bf, 1.0, 1.0, 0.5)
+    d = sum(np.abs(np.roll(bf, sh, axis=a) - bf) for a in range(3) for sh in (1, -1))
+    assert (_abs_err(rt, exact) <= 2.0 ** -50 * (np.abs(bt) + 0.5 * np.abs(bf) + d) + 2.0 ** -54 * np.abs(bf).max()).all()
+
+
 def _blobs(dims, h, n, seed):
     q = np.random.default_rng(seed).random((n, 3)) * np.array(dims) * h
     # include grid nodes, the domain edge and wrapped coordinates
