@@ -56,9 +56,9 @@ __global__ void __launch_bounds__(BX* BY) k_apply(const T* __restrict__ x, const
 // the FP64 form diag x - off s rounds terms of size 6 off |x|, far above |r|
 // near convergence. r = fma(-alpha, x, fma(off 2^-S, double(L X), b)) then
 // rounds once per FMA: within 2^-52 of |r| + off |L x| plus the scaling's
-// 2^-56 off max|x|, with one or two FP64 instructions per cell (the integer
-// work runs on the integer pipe; GB300's FP64 pipe issues about two
-// instructions per SM per clock).
+// 2^-56 off max|x|, with one FP64 instruction per cell (two with alpha != 0;
+// the integer work runs on the integer pipe; GB300's FP64 pipe does about 1.6
+// additions, multiplications or FMAs per SM per clock).
 
 // v 2^S rounded to an integer, for |v| 2^S < 2^59
 __device__ __forceinline__ long long to_fixed(double v, int S) {
@@ -137,7 +137,7 @@ constexpr int kFxEmin = 1023 - 900, kFxEmax = 1023 + 900;
 // lanes' neighbours (shuffles), or, at the tile's edges, from the edge value
 // every lane loads (lane 0 the left one, lane 31 the right one). Needs
 // nx % (32 CPT) == 0 and ny % TY == 0.
-template <int TY, int CPT>
+template <int TY, int CPT, bool ALPHA>
 __global__ void __launch_bounds__(32 * TY) k_resid_fx(const double* __restrict__ x, const double* __restrict__ b,
                                                       double* __restrict__ y, int nx, int ny, int nz, int zc,
                                                       double alpha, double off, double diag,
@@ -172,7 +172,6 @@ __global__ void __launch_bounds__(32 * TY) k_resid_fx(const double* __restrict__
   const int hrow = ty == 0 ? 0 : TY + 1;
   const size_t rh = (size_t)(ty == 0 ? wrap_dec(j0, ny) : wrap_inc(j0 + TY - 1, ny)) * nx;
   const int ie = lane == 0 ? wrap_dec(i0, nx) : wrap_inc(i0 + TW - 1, nx);  // this lane's tile-edge cell
-  const bool use_alpha = alpha != 0.0;
   struct Vals {
     double v[CPT];
   };
@@ -244,7 +243,8 @@ __global__ void __launch_bounds__(32 * TY) k_resid_fx(const double* __restrict__
       const long long L = ((w + e) + (XS[buf][ty][lane * CPT + q] + XS[buf][ty + 2][lane * CPT + q])) +
                           (Xm[q] + Xp[q]) - 6 * X0[q];
       r[q] = fma(offs, ll2d_bits(L), bv.v[q]);
-      if (use_alpha) r[q] = fma(-alpha, xc.v[q], r[q]);
+      if constexpr (ALPHA) r[q] = fma(-alpha, xc.v[q], r[q]);  // a separate instantiation: a predicated
+                                                               // DFMA would still take the FP64 pipe
     }
     if constexpr (CPT == 2) {
       *reinterpret_cast<double2*>(y + at(k, rj, ic)) = make_double2(r[0], r[1]);
@@ -896,10 +896,18 @@ void launch_residual(const T* x, const T* b, T* y, Dims d, Stencil st, double* s
         kern<<<g, dim3(32, TY), 0, s>>>(x, b, y, d.nx, d.ny, d.nz, zc, alpha, st.off, st.diag, xmax);
         prof_end(c, s, "residual_fx", 3.0 * sizeof(T) * d.n());
       };
-      if (d.nx % 64 == 0 && aligned16(x) && aligned16(b) && aligned16(y))
-        go(k_resid_fx<TY, 2>, 2);
-      else
-        go(k_resid_fx<TY, 1>, 1);
+      const bool vec = d.nx % 64 == 0 && aligned16(x) && aligned16(b) && aligned16(y);
+      if (alpha != 0.0) {
+        if (vec)
+          go(k_resid_fx<TY, 2, true>, 2);
+        else
+          go(k_resid_fx<TY, 1, true>, 1);
+      } else {
+        if (vec)
+          go(k_resid_fx<TY, 2, false>, 2);
+        else
+          go(k_resid_fx<TY, 1, false>, 1);
+      }
       return;
     }
   }

@@ -92,9 +92,9 @@ struct Stencil {
 };
 
 // ---------------------------------------------------------------- FP64 off the FP64 pipe
-// GB300 issues about two FP64 instructions per SM per clock -- FP64
-// arithmetic and the double <-> float conversion instructions alike --
-// against 128 FP32 operations. Streaming FP64 kernels therefore convert with
+// GB300's FP64 pipe does about 1.6 additions, multiplications or FMAs per SM
+// per clock (measured), and the double <-> float conversion instructions run
+// at a similar rate, against 128 FP32 operations. Streaming FP64 kernels therefore convert with
 // integer operations on the bit patterns and do their arithmetic in FP32
 // (float-float pairs where FP64 accuracy is needed).
 #ifdef __CUDACC__
