@@ -60,7 +60,7 @@ enum { IBRD_FP64 = 0, IBRD_MIXED_FP32 = 1, IBRD_MIXED_REFINE = 2 };  /* precisio
    Schur_diagonal), or chosen by blob count (AUTO: diagonal for at most 512
    blobs in the mixed-precision modes and at most 2048 in FP64, where it was
    measured faster at 128^3 and 256^3; approximate Schur above) */
-enum { IBRD_PRECOND_SCHUR = 0, IBRD_PRECOND_DIAG = 1, IBRD_PRECOND_AUTO = 2 };
+enum { IBRD_PRECOND_SCHUR = 0, IBRD_PRECOND_DIAG = 1, IBRD_PRECOND_AUTO = 2, IBRD_PRECOND_BLOCK = 3 };
 enum { IBRD_GUESS_NONE = 0, IBRD_GUESS_UNIFORM = 1, IBRD_GUESS_GIVEN = 2, IBRD_GUESS_PENALTY = 3 }; /* saddle start */
 
 /* Solver options. ibrd_default_opts fills the defaults noted here. */
@@ -72,12 +72,27 @@ typedef struct {
   int mg_cycles;     /* n: V-cycles per approximate Helmholtz solve (1) */
   int schur_inner;   /* m: inner Krylov iterations of the approximate Schur
                         preconditioner (5, Sec. III.E / Appendix A) */
-  int precond;       /* IBRD_PRECOND_AUTO (default), _SCHUR or _DIAG. The
-                        diagonal preconditioner's gamma = M_11 is computed
+  int precond;       /* IBRD_PRECOND_AUTO (default), _SCHUR, _DIAG or _BLOCK.
+                        The diagonal preconditioner's gamma = M_11 is computed
                         once per handle (40 FP64 V-cycles on the first blob
                         the first such solve sees) and kept when the blobs
                         change: it depends on the system size and only at the
-                        percent level on a blob's position (Sec. III.E) */
+                        percent level on a blob's position (Sec. III.E).
+                        _BLOCK (not in the paper; alpha = 0 only, else it runs
+                        as _SCHUR): the approximate Schur preconditioner whose
+                        m inner GMRES iterations are left-preconditioned by a
+                        sparse approximate inverse P of M = J A^-1 S. Row i of
+                        P is row i of the inverse of M restricted to blob i
+                        and its neighbours within block_cutoff (at most 31,
+                        the nearest), with M_ij for i != j from the periodic
+                        Green's function of chi L at the blobs' distance r:
+                        1 / (4 pi chi r) + C_box / chi + r^2 / (6 chi V)
+                        (C_box = ibrd_periodic_constant of the box) and
+                        M_ii = gamma as above. Built on the first such solve
+                        after the blobs change. _AUTO: _DIAG up to 512 blobs
+                        (2048 in IBRD_FP64), _BLOCK above (_SCHUR when
+                        alpha != 0), from timings at 128^3 and 256^3 with
+                        m = 5. */
   double zeta;       /* scaling zeta of Eq. saddle_point (1) */
   double xi;         /* scaling xi; <= 0 selects zeta / h^3 (Eq. saddle_point) */
   int nu1, nu2;      /* red-black Gauss-Seidel sweeps before/after (2, 2) */
@@ -134,6 +149,11 @@ typedef struct {
   int warm_cycles;   /* V-cycles forming c0 of a warm start (2) */
   double penalty_kappa; /* kappa_p of IBRD_GUESS_PENALTY (1000) */
   double penalty_tol;   /* relative residual of its reaction solve (1e-2) */
+  double block_cutoff;  /* IBRD_PRECOND_BLOCK: neighbour cutoff, same unit as
+                           the positions; <= 0 (default) chooses about 12
+                           neighbours per blob at the mean blob density:
+                           (9 V / (pi N))^(1/3); at most half the shortest
+                           box side */
 } ibrd_solve_opts;
 
 /* Solve report. residual_history, if non-NULL, is a caller-owned HOST array
@@ -158,7 +178,8 @@ typedef struct {
   int refinements;     /* IBRD_MIXED_REFINE: refinement steps (FP32 solves) */
   double a_L;          /* reaction radius a_L = K / (4 pi chi) (Sec. IV.A) */
   int precond;         /* saddle solves: the preconditioner that ran
-                          (IBRD_PRECOND_SCHUR or _DIAG); -1 for reaction solves */
+                          (IBRD_PRECOND_SCHUR, _DIAG or _BLOCK); -1 for reaction
+                          solves */
 } ibrd_solve_info;
 
 /* Fill *opts with the defaults listed in ibrd_solve_opts. */
@@ -372,6 +393,14 @@ typedef struct {
 } ibrd_tune_entry;
 
 ibrd_status ibrd_autotune(ibrd_grid g, int precision, int retune, ibrd_tune_entry* out, int cap, int* n_out);
+
+/* The constant C of the zero-mean periodic Green's function of -Laplace in a
+   box lx x ly x lz (all > 0): G(r) = 1 / (4 pi r) + C + r^2 / (6 V) + ... for
+   small r. For a cube of side L, C = -2.837297 / (4 pi L): the constant of
+   the finite-size correction of the reaction radius (Sec. IV.A, Eq. a_phi).
+   By an Ewald sum to double precision (image and reciprocal shells per axis
+   from the box's shape). Host only; NaN for a non-positive side. */
+double ibrd_periodic_constant(double lx, double ly, double lz);
 
 /* Set one launch shape by hand (as ibrd_autotune would keep it): elem_bytes
    4 or 8, kind 0 or 1 as in ibrd_tune_entry, (nx, ny, nz) a level of the

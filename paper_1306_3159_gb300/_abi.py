@@ -13,7 +13,7 @@ LIB_PATH = os.path.join(PKG, "libibrd.so")
 
 IBRD_PESKIN4, IBRD_PESKIN3 = 4, 3
 IBRD_FP64, IBRD_MIXED_FP32, IBRD_MIXED_REFINE = 0, 1, 2
-IBRD_PRECOND_SCHUR, IBRD_PRECOND_DIAG, IBRD_PRECOND_AUTO = 0, 1, 2
+IBRD_PRECOND_SCHUR, IBRD_PRECOND_DIAG, IBRD_PRECOND_AUTO, IBRD_PRECOND_BLOCK = 0, 1, 2, 3
 IBRD_GUESS_NONE, IBRD_GUESS_UNIFORM, IBRD_GUESS_GIVEN, IBRD_GUESS_PENALTY = 0, 1, 2, 3
 
 STATUS = {0: "IBRD_OK", 1: "IBRD_ERR_ARG", 2: "IBRD_ERR_CUDA", 3: "IBRD_ERR_OOM", 4: "IBRD_ERR_NOT_CONVERGED",
@@ -21,7 +21,7 @@ STATUS = {0: "IBRD_OK", 1: "IBRD_ERR_ARG", 2: "IBRD_ERR_CUDA", 3: "IBRD_ERR_OOM"
 
 # Every entry point declared in include/ibrd.h.
 EXPORTED = ["ibrd_default_opts", "ibrd_grid_create", "ibrd_grid_destroy", "ibrd_set_blobs", "ibrd_apply_L",
-            "ibrd_residual",
+            "ibrd_residual", "ibrd_periodic_constant",
             "ibrd_vcycle", "ibrd_vcycle_f32", "ibrd_vcycle_f32_sweeps", "ibrd_vcycle_noalloc", "ibrd_spread", "ibrd_interp", "ibrd_solve_reaction", "ibrd_solve_saddle",
             "ibrd_solve_reaction_batch", "ibrd_solve_saddle_batch", "ibrd_solve_many", "ibrd_autotune", "ibrd_tune_set",
             "ibrd_tune_clear", "ibrd_set_wait_limit", "ibrd_gnn_num_params", "ibrd_gnn_create", "ibrd_gnn_destroy", "ibrd_gnn_last_error",
@@ -40,7 +40,8 @@ class SolveOpts(ctypes.Structure):
                 ("precision", ctypes.c_int), ("use_guess", ctypes.c_int),
                 ("reorth_eta", ctypes.c_double), ("graphs", ctypes.c_int), ("inner_tol", ctypes.c_double),
                 ("lambda_guess", ctypes.c_int), ("warm_cycles", ctypes.c_int),
-                ("penalty_kappa", ctypes.c_double), ("penalty_tol", ctypes.c_double)]
+                ("penalty_kappa", ctypes.c_double), ("penalty_tol", ctypes.c_double),
+                ("block_cutoff", ctypes.c_double)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -106,6 +107,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ibrd_apply_L.restype = i
     lib.ibrd_residual.argtypes = [vp, vp, vp, vp]
     lib.ibrd_residual.restype = i
+    lib.ibrd_periodic_constant.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
+    lib.ibrd_periodic_constant.restype = ctypes.c_double
     lib.ibrd_vcycle.argtypes = [vp, vp, vp, i]
     lib.ibrd_vcycle.restype = i
     lib.ibrd_vcycle_f32.argtypes = [vp, vp, vp, i]
@@ -233,6 +236,10 @@ def ibrd_set_blobs(g, q, n=None):
 
 def ibrd_apply_L(g, c, y):
     _check(g, load_library().ibrd_apply_L(g, _ptr(c), _ptr(y)))
+
+
+def ibrd_periodic_constant(lx, ly, lz) -> float:
+    return float(load_library().ibrd_periodic_constant(float(lx), float(ly), float(lz)))
 
 
 def ibrd_residual(g, rhs, c, r):

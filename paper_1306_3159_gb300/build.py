@@ -21,7 +21,7 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libibrd.so")
 STAMP = os.path.join(BUILD, "stamp.txt")
 SOURCES = ["grid_kernels.cu", "smoother.cu", "sweep_rows.cu", "blob_kernels.cu", "krylov_kernels.cu", "api.cu",
-           "noalloc.cu", "gnn.cu"]
+           "noalloc.cu", "gnn.cu", "schur_block.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fno-strict-aliasing",
          "-Wno-deprecated-declarations"]

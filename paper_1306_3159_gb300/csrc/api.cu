@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "schur_block.h"
 
 namespace ibrd {
 
@@ -53,6 +54,7 @@ enum Slot {
   S_RCOUNT,   // second passes taken in this solve
   S_WAIT,     // nonzero bits: a bounded device wait gave up (written as an int)
   S_XMAX,     // largest |x| of a residual's iterate (its bits; fixed-point scale)
+  S_PMEAN,    // mean of a block-preconditioned inner vector (IBRD_PRECOND_BLOCK)
   S_UB = 64,  // mean of S U_j for the inner iterations j = 0..m (64 slots)
   S_UX = 128, // mean of A~^-1 S U_j (64 slots)
   S_COUNT = 192
@@ -234,6 +236,17 @@ struct ibrd_grid_s {
   int ncap = -1, ucap = 0;
   double gamma_diag = 0.0;      // M_11 for the diagonal preconditioner
   bool gamma_valid = false;
+  // block preconditioner of the Schur complement (IBRD_PRECOND_BLOCK): slots
+  // (kBlockMax per blob), counts, rows, FP32 positions; built for one blob
+  // configuration (blob_version, bumped by ibrd_set_blobs) and cutoff
+  int* blk_idx = nullptr;
+  int* blk_cnt = nullptr;
+  float* blk_val = nullptr;
+  float4* blk_pos = nullptr;
+  int blk_cap = 0;
+  long blob_version = 0;
+  long blk_version = -1;
+  double blk_cutoff = 0.0;
   // counters of the current solve
   long vcycles = 0;
   long inner = 0;
@@ -1593,7 +1606,12 @@ struct SaddleOp : LinOp<E> {
     char buf[200];
     std::snprintf(buf, sizeof buf, "saddle|%zu|%zu|%d|%d|%d|%d|%d|%.17g|%.17g|%.17g|%.17g", sizeof(T), sizeof(E),
                   o.mg_cycles, o.nu1, o.nu2, o.schur_inner, o.precond, zeta, xi, g->alpha, g->gamma_diag);
-    return buf;
+    std::string k = buf;
+    if (o.precond == IBRD_PRECOND_BLOCK) {
+      std::snprintf(buf, sizeof buf, "|B%p|%p|%p", (void*)g->blk_idx, (void*)g->blk_cnt, (void*)g->blk_val);
+      k += buf;
+    }
+    return k;
   }
   void apply(const E* x, E* y) override {
     const size_t nc = g->d.n();
@@ -1672,15 +1690,39 @@ struct SaddleOp : LinOp<E> {
       const double ub_scale = ih3 / (double)nc;
       // the inner basis has the Krylov vectors' precision E
       E* U = reinterpret_cast<E*>(g->U);
-      launch_small_start<E>(rhs, U, N, g->sg, m, singular ? sc + S_UB : nullptr, ub_scale, g->s);
+      // IBRD_PRECOND_BLOCK (alpha = 0 only): GMRES on P M~ lambda = P rhs, P
+      // the block preconditioner, its outputs made mean-free like M~'s
+      const bool blk = o.precond == IBRD_PRECOND_BLOCK;
+      const double* start = rhs;
+      if (blk) {
+        double* prhs = g->nv[2];
+        launch_block_apply<double, double>(g->blk_idx, g->blk_cnt, g->blk_val, rhs, nullptr, N, prhs, g->partial,
+                                           g->s);
+        launch_finalize(g->partial, kBlockApplyBlocks, sc + S_PMEAN, 1.0 / N, g->s);
+        launch_sub_scalar<double>(prhs, N, sc + S_PMEAN, g->s);
+        start = prhs;
+      }
+      launch_small_start<E>(start, U, N, g->sg, m, singular ? sc + S_UB : nullptr, ub_scale, g->s);
       for (int j = 0; j < m; ++j) {
         launch_spread<T, E>(g->blobs, g->d, U + (size_t)j * N, nullptr, ih3, fs, 0, g->s);
         if (singular)
           vcycle<T>(g, fs, fx, true, shift, o.nu1, o.nu2, sc + S_UB + j, XMean::Report, sc + S_UX + j);
         else
           vcycle<T>(g, fs, fx, true, shift, o.nu1, o.nu2);
-        launch_interp<T, E>(g->blobs, g->d, fx, 1.0, U + (size_t)(j + 1) * N, g->s);
-        launch_small_arnoldi<E>(U, N, j, g->Hs, m + 1, g->scs, g->ssn, g->sg, singular ? sc + S_UX + j : nullptr,
+        const double* wshift = singular ? sc + S_UX + j : nullptr;
+        if (blk) {
+          // J of the V-cycle result into scratch, P of it minus the result's
+          // mean into the basis, whose own mean the Arnoldi step removes
+          E* w = reinterpret_cast<E*>(g->nv[2]);
+          launch_interp<T, E>(g->blobs, g->d, fx, 1.0, w, g->s);
+          launch_block_apply<E, E>(g->blk_idx, g->blk_cnt, g->blk_val, w, wshift, N, U + (size_t)(j + 1) * N,
+                                   g->partial, g->s);
+          launch_finalize(g->partial, kBlockApplyBlocks, sc + S_PMEAN, 1.0 / N, g->s);
+          wshift = sc + S_PMEAN;
+        } else {
+          launch_interp<T, E>(g->blobs, g->d, fx, 1.0, U + (size_t)(j + 1) * N, g->s);
+        }
+        launch_small_arnoldi<E>(U, N, j, g->Hs, m + 1, g->scs, g->ssn, g->sg, wshift,
                              singular && j + 1 < m ? sc + S_UB + j + 1 : nullptr, ub_scale, g->s);
         g->inner++;
       }
@@ -1820,6 +1862,46 @@ double compute_gamma(ibrd_grid g, const ibrd_solve_opts& o) {
   return g->host[0];
 }
 
+// The block preconditioner of the Schur complement for the current blobs
+// (IBRD_PRECOND_BLOCK; rebuilt when the blobs or the cutoff change): the
+// Green's function model of M off the diagonal (Sec. IV.A's periodic
+// constant, here for any box by an Ewald sum), gamma on it.
+void ensure_block(ibrd_grid g, const ibrd_solve_opts& o) {
+  const int N = g->blobs.n;
+  if (N <= 0) return;
+  const double lx = g->d.nx * g->h, ly = g->d.ny * g->h, lz = g->d.nz * g->h, V = lx * ly * lz;
+  const double pi = 3.14159265358979323846;
+  // by default about 12 neighbours at the mean density: (4/3) pi rc^3 N / V = 12
+  double rc = o.block_cutoff > 0.0 ? o.block_cutoff : std::cbrt(9.0 * V / (pi * N));
+  rc = std::min(rc, 0.5 * std::min(lx, std::min(ly, lz)));  // a unique minimum image
+  if (g->blk_version == g->blob_version && g->blk_cutoff == rc && g->blk_cap >= N) return;
+  if (g->blk_cap < N) {
+    free_graphs(g);  // captured applications hold the old arrays' addresses
+    cudaFree(g->blk_idx);
+    cudaFree(g->blk_cnt);
+    cudaFree(g->blk_val);
+    cudaFree(g->blk_pos);
+    g->blk_idx = g->blk_cnt = nullptr;
+    g->blk_val = nullptr;
+    g->blk_pos = nullptr;
+    g->blk_cap = 0;
+    g->blk_idx = dalloc<int>((size_t)N * kBlockMax);
+    g->blk_cnt = dalloc<int>(N);
+    g->blk_val = dalloc<float>((size_t)N * kBlockMax);
+    g->blk_pos = dalloc<float4>(N);
+    g->blk_cap = N;
+  }
+  BlockModel m;
+  m.a = (float)(1.0 / (4.0 * pi * g->chi));
+  m.c0 = (float)(periodic_constant(lx, ly, lz) / g->chi);
+  m.c2 = (float)(1.0 / (6.0 * g->chi * V));
+  m.diag = (float)g->gamma_diag;
+  m.rmin = (float)(2.0 * g->h);  // inside two cells the kernels overlap and 1/r is no model
+  launch_block_setup(g->blobs.q, N, lx, ly, lz, rc, m, g->blk_pos, g->blk_idx, g->blk_cnt, g->blk_val, g->s);
+  g->blk_version = g->blob_version;
+  g->blk_cutoff = rc;
+}
+
 // Whether a bounded device wait of this handle's kernels gave up since the
 // last check (then the flag is cleared). Waits for the handle's stream.
 bool take_wait_flag(ibrd_grid g) {
@@ -1884,16 +1966,22 @@ ibrd_solve_opts resolve_opts(ibrd_grid g, const ibrd_solve_opts* in) {
       o.schur_inner < 1 || o.schur_inner > 60 || o.nu1 < 0 || o.nu2 < 0 || !(o.zeta != 0.0) ||
       !(o.reorth_eta >= 0.0) || !(o.inner_tol > 0.0 && o.inner_tol < 1.0) ||
       (o.precision != IBRD_FP64 && o.precision != IBRD_MIXED_FP32 && o.precision != IBRD_MIXED_REFINE) ||
-      (o.precond != IBRD_PRECOND_SCHUR && o.precond != IBRD_PRECOND_DIAG && o.precond != IBRD_PRECOND_AUTO) ||
+      (o.precond != IBRD_PRECOND_SCHUR && o.precond != IBRD_PRECOND_DIAG && o.precond != IBRD_PRECOND_AUTO &&
+       o.precond != IBRD_PRECOND_BLOCK) || !std::isfinite(o.block_cutoff) ||
       (o.lambda_guess != IBRD_GUESS_NONE && o.lambda_guess != IBRD_GUESS_UNIFORM &&
        o.lambda_guess != IBRD_GUESS_GIVEN && o.lambda_guess != IBRD_GUESS_PENALTY) || o.warm_cycles < 1 ||
       o.warm_cycles > 64 || !(o.penalty_kappa > 0.0) || !std::isfinite(o.penalty_kappa) ||
       !(o.penalty_tol > 0.0 && o.penalty_tol < 1.0))
     throw ArgError{IBRD_ERR_ARG, "invalid solver options"};
   // blob counts up to which the diagonal preconditioner solved faster than the
-  // approximate Schur one (measured at 128^3 and 256^3, both precisions)
+  // approximate Schur one at m = 5 (measured at 128^3 and 256^3, both
+  // precisions, with the plain and the block-preconditioned inner GMRES;
+  // above them the block-preconditioned one was never slower than the plain)
   if (o.precond == IBRD_PRECOND_AUTO)
-    o.precond = g->blobs.n <= (o.precision == IBRD_FP64 ? 2048 : 512) ? IBRD_PRECOND_DIAG : IBRD_PRECOND_SCHUR;
+    o.precond = g->blobs.n <= (o.precision == IBRD_FP64 ? 2048 : 512) ? IBRD_PRECOND_DIAG : IBRD_PRECOND_BLOCK;
+  // the block preconditioner's model is the Green's function of -chi L
+  // (alpha = 0); with a shift the plain inner GMRES runs
+  if (o.precond == IBRD_PRECOND_BLOCK && g->alpha != 0.0) o.precond = IBRD_PRECOND_SCHUR;
   return o;
 }
 
@@ -2191,13 +2279,14 @@ bool saddle_setup(ibrd_grid g, const double* rhs, const double* f, double* c, do
     else
       saddle_warm_start<float>(g, o, g->bs, g->xs, o.lambda_guess, o.warm_cycles);
   }
-  if (o.precond == IBRD_PRECOND_DIAG && !g->gamma_valid) {
+  if ((o.precond == IBRD_PRECOND_DIAG || o.precond == IBRD_PRECOND_BLOCK) && !g->gamma_valid) {
     // gamma's V-cycles are set-up, not part of this solve's count
     const long v = g->vcycles;
     g->gamma_diag = compute_gamma(g, o);
     g->gamma_valid = true;
     g->vcycles = v;
   }
+  if (o.precond == IBRD_PRECOND_BLOCK) ensure_block(g, o);
   return !o.use_guess && !warm;
 }
 
@@ -2536,6 +2625,7 @@ void ibrd_default_opts(ibrd_solve_opts* o) {
   o->warm_cycles = 2;
   o->penalty_kappa = 1000.0;
   o->penalty_tol = 1e-2;
+  o->block_cutoff = 0.0;
 }
 
 const char* ibrd_status_string(int st) {
@@ -2579,6 +2669,7 @@ void ibrd_grid_destroy(ibrd_grid g) {
   for (auto p : g->p32) F(p);
   for (auto p : g->nv) F(p);
   F(g->U); F(g->Hs); F(g->scs); F(g->ssn); F(g->sg);
+  F(g->blk_idx); F(g->blk_cnt); F(g->blk_val); F(g->blk_pos);
   for (auto e : g->prof.pool) cudaEventDestroy(e);
   drop_batch_graphs_of(g);
   free_graphs(g);
@@ -2670,6 +2761,7 @@ ibrd_status ibrd_set_blobs(ibrd_grid g, const double* q, int n) {
     IBRD_CUDA(cudaStreamSynchronize(g->s));
     if (flag) throw ArgError{IBRD_ERR_NONFINITE, "non-finite blob position"};
     blobs_setup(g->blobs, g->d, g->h, q, n, g->s);
+    g->blob_version++;
     return IBRD_OK;
   });
 }
@@ -2680,6 +2772,11 @@ ibrd_status ibrd_apply_L(ibrd_grid g, const double* c, double* y) {
     launch_apply_A<double>(c, y, g->d, stencil(g->h, g->chi, g->alpha), g->s);
     return IBRD_OK;
   });
+}
+
+double ibrd_periodic_constant(double lx, double ly, double lz) {
+  if (!(lx > 0.0 && ly > 0.0 && lz > 0.0) || !std::isfinite(lx * ly * lz)) return std::nan("");
+  return periodic_constant(lx, ly, lz);
 }
 
 ibrd_status ibrd_residual(ibrd_grid g, const double* rhs, const double* c, double* r) {

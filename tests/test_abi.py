@@ -96,3 +96,45 @@ def test_solve_many_rejects_bad_items_without_touching_gpu(lib):
             items[k].kind = kinds[k]
             items[k].grid = grids[k] or None
         assert fn(2, items, 2) == 1
+
+
+def _ewald_constant(lx, ly, lz, beta_scale, nr, nk):
+    """C of G(r) = 1/(4 pi r) + C + ... for the zero-mean periodic Green's
+    function of -Laplace: an independent NumPy Ewald sum with its own
+    splitting parameter and fixed shells."""
+    import numpy as np
+    from scipy.special import erfc
+    V = lx * ly * lz
+    beta = beta_scale / V ** (1 / 3)
+    a = np.arange(-nr, nr + 1)
+    n = np.stack(np.meshgrid(a * lx, a * ly, a * lz, indexing="ij"), -1).reshape(-1, 3)
+    r = np.sqrt((n ** 2).sum(1))
+    r = r[r > 0]
+    real = np.sum(erfc(beta * r) / (4 * np.pi * r))
+    m = np.arange(-nk, nk + 1)
+    k = np.stack(np.meshgrid(2 * np.pi * m / lx, 2 * np.pi * m / ly, 2 * np.pi * m / lz, indexing="ij"), -1)
+    k2 = (k.reshape(-1, 3) ** 2).sum(1)
+    k2 = k2[k2 > 0]
+    recip = np.sum(np.exp(-k2 / (4 * beta ** 2)) / k2) / V
+    return real + recip - beta / (2 * np.pi ** 1.5) - 1 / (4 * beta ** 2 * V)
+
+
+def test_periodic_constant(lib):
+    """ibrd_periodic_constant (the block preconditioner's model constant and
+    the finite-size constant of Sec. IV.A's Eq. a_phi): a cube gives
+    -2.837297 / (4 pi L) (the simple cubic lattice constant; the paper prints
+    2.84), it scales as 1 / L, and boxes of other shapes agree with an
+    independent Ewald sum (another splitting parameter, fixed shells) to
+    1e-10; a non-positive side gives NaN."""
+    import math
+    f = lib.ibrd_periodic_constant
+    f.argtypes = [ctypes.c_double] * 3
+    f.restype = ctypes.c_double
+    for L in (1.0, 64.0, 256.0):
+        assert abs(f(L, L, L) * 4 * math.pi * L + 2.837297) < 1e-6
+    assert abs(-f(1, 1, 1) * 4 * math.pi - 2.84) < 5e-3
+    assert abs(f(3.0, 2.0, 5.0) - 7.0 * f(21.0, 14.0, 35.0)) < 1e-13 * abs(f(3.0, 2.0, 5.0))
+    for box in [(2.0, 1.0, 1.0), (1.0, 1.0, 0.5), (64.0, 32.0, 96.0), (40.0, 24.0, 16.0), (128.0, 32.0, 32.0)]:
+        want = _ewald_constant(*box, beta_scale=2.2, nr=12, nk=16)
+        assert abs(f(*box) - want) < 1e-10 * abs(want), box
+    assert math.isnan(f(0.0, 1.0, 1.0)) and math.isnan(f(1.0, -2.0, 1.0))

@@ -137,10 +137,11 @@ def test_saddle_diagonal_preconditioner(ibrd, small):
 
 def test_auto_preconditioner_choice_and_kept_gamma(ibrd):
     """IBRD_PRECOND_AUTO (the default) picks the diagonal preconditioner up to
-    512 blobs in the mixed modes and up to 2048 in FP64, the approximate Schur
-    one above; the diagonal preconditioner's gamma, computed once per handle,
-    is kept when the blobs change and the solve still reaches the oracle's
-    solution for the new configuration."""
+    512 blobs in the mixed modes and up to 2048 in FP64, above them the
+    approximate Schur one with the block-preconditioned inner GMRES (the plain
+    inner GMRES when alpha > 0); the diagonal preconditioner's gamma, computed
+    once per handle, is kept when the blobs change and the solve still reaches
+    the oracle's solution for the new configuration."""
     dims = (32, 32, 32)
     g = ibrd.Grid(*dims)
     src = np.ones((32, 32, 32))
@@ -157,8 +158,68 @@ def test_auto_preconditioner_choice_and_kept_gamma(ibrd):
     q3 = rsa_positions(600, (64, 64, 64), 1.0, 3.0, 73)
     big.set_blobs(dev(q3))
     src3 = dev(np.ones((64, 64, 64)))
-    assert big.solve_saddle(src3, tol=1e-8, precision=2, max_iter=600)[2]["precond"] == 0
+    assert big.solve_saddle(src3, tol=1e-8, precision=2, max_iter=600)[2]["precond"] == 3
     assert big.solve_saddle(src3, tol=1e-8, precision=0, max_iter=600)[2]["precond"] == 1
+    shifted = ibrd.Grid(64, 64, 64, alpha=0.1)
+    shifted.set_blobs(dev(q3))
+    assert shifted.solve_saddle(src3, tol=1e-8, precision=2, max_iter=600)[2]["precond"] == 0
+
+
+@pytest.mark.parametrize("precision,tol,err", [(0, 1e-12, 1e-11), (2, 1e-10, 1e-8), (2, 1e-12, 1e-11)])
+def test_saddle_block_preconditioner(ibrd, small, precision, tol, err):
+    """IBRD_PRECOND_BLOCK: the approximate Schur preconditioner (Appendix A)
+    whose inner GMRES runs on P M~ with P the sparse approximate inverse of
+    M = J A^-1 S from the periodic Green's function of the box (and gamma on
+    the diagonal). The saddle solve of the 48-blob workload reaches the
+    oracle's direct solution (FP64 and refinement modes), reports the
+    preconditioner that ran, and with one inner iteration takes fewer outer
+    iterations than the plain inner GMRES."""
+    w, M = small
+    c_ref, lam_ref, _ = direct.solve_saddle(w.q, w.g, w.h, w.chi, 0.0, M=M)
+    g = _grid(ibrd, w)
+    tol = max(tol, floor_tol(c_ref, w.g, w.h, w.chi, 0.0))
+    outer = {}
+    for pc in (0, 3):
+        c, lam, info = g.solve_saddle(dev(w.g), tol=tol, precision=precision, max_iter=400, precond=pc,
+                                      schur_inner=1)
+        assert info["precond"] == pc and info["rel_residual"] <= tol
+        assert rel_err(host(c), c_ref) < err and rel_err(host(lam), lam_ref) < err
+        assert abs(info["sum_lambda"] - w.g.sum()) < 1e-9 * w.g.sum()
+        outer[pc] = info["outer_iters"]
+    assert outer[3] < outer[0], outer
+
+
+def test_block_preconditioner_follows_the_blobs(ibrd):
+    """The block preconditioner is rebuilt when the blobs move: a handle that
+    solved one configuration with it and then another gives, bit for bit,
+    the solve of a handle that saw only the second one with the same gamma
+    (gamma is kept per handle, so the second handle takes it from the first
+    configuration through a diagonal-preconditioned solve). An explicit
+    block_cutoff solves too, to the oracle's solution, and a non-finite one
+    is rejected."""
+    dims = (64, 64, 32)
+    src = np.ones((32, 64, 64))
+    q1 = rsa_positions(300, dims, 1.0, 3.0, 81)
+    q2 = rsa_positions(300, dims, 1.0, 3.0, 82)
+    kw = dict(tol=1e-9, precision=2, max_iter=600, schur_inner=2)
+    a = ibrd.Grid(*dims)
+    a.set_blobs(dev(q1))
+    a.solve_saddle(dev(src), precond=3, **kw)
+    a.set_blobs(dev(q2))
+    ca, la, ia = a.solve_saddle(dev(src), precond=3, **kw)
+    b = ibrd.Grid(*dims)
+    b.set_blobs(dev(q1))
+    b.solve_saddle(dev(src), precond=1, **kw)
+    b.set_blobs(dev(q2))
+    cb, lb, ib = b.solve_saddle(dev(src), precond=3, **kw)
+    assert ia["outer_iters"] == ib["outer_iters"]
+    assert np.array_equal(host(ca), host(cb)) and np.array_equal(host(la), host(lb))
+    c_ref, lam_ref, _ = direct.solve_saddle(q2, src, 1.0, 1.0, 0.0)
+    c, lam, info = a.solve_saddle(dev(src), precond=3, block_cutoff=9.0, **kw)
+    assert info["precond"] == 3
+    assert rel_err(host(c), c_ref) < 1e-7 and rel_err(host(lam), lam_ref) < 1e-7
+    with pytest.raises(ibrd.IbrdError):
+        a.solve_saddle(dev(src), precond=3, block_cutoff=float("nan"), **kw)
 
 
 def test_single_blob_finite_rate_shift(ibrd):
