@@ -577,14 +577,16 @@ def run_batched(p, torch, world, args, tune=True):
 
 
 LEARNED_CUTOFF = 24.0
+LEARNED_EPOCHS = 12
 
 
 def run_learned(p, torch, world, args):
     """The learned multiplier predictor (and the penalty form) as the start of
     the saddle solve.
-    Training data: 64 saddle solves at 128^3 (blob density 1.2e-4 to 2e-3 per
+    Training data: 512 saddle solves at 128^3 (blob density 1.2e-4 to 2e-3 per
     h^3, RSA spacing 3h-4h, unit source) from the batched entry point in the
-    chosen mode; 56 train the network (80 epochs of Adam), 8 are held out.
+    chosen mode, 64 at a time; 448 train the network (LEARNED_EPOCHS epochs of
+    Adam), 64 are held out.
     Evaluation: time to 1e-8 of the chosen saddle solve from a zero start, the
     uniform share, the learned prediction (its inference inside the timed
     region) and the penalty form (a reaction-limited solve with the uniform
@@ -594,23 +596,28 @@ def run_learned(p, torch, world, args):
     import numpy as np
     from synthetic import rsa_positions, workload
     side = 128
+    n_cfg, n_train, batch = 512, 448, 64
     rng = np.random.default_rng(5)
     cfgs = []
-    for s in range(64):
+    for s in range(n_cfg):
         n = int(round(np.exp(rng.uniform(np.log(side ** 3 * 1.2e-4), np.log(side ** 3 * 2e-3)))))
         cfgs.append(rsa_positions(n, (side,) * 3, 1.0, float(rng.uniform(3.0, 4.0)), 1000 + s))
-    streams = [torch.cuda.Stream() for _ in cfgs]
+    streams = [torch.cuda.Stream() for _ in range(batch)]
     grids = [p.Grid(side, side, side, precision=p.IBRD_MIXED_REFINE, stream=st.cuda_stream) for st in streams]
     qs = [torch.from_numpy(q).cuda() for q in cfgs]
-    gs = [torch.ones((side,) * 3, dtype=torch.float64, device="cuda") for _ in cfgs]
+    gs = [torch.ones((side,) * 3, dtype=torch.float64, device="cuda") for _ in range(batch)]
     cs = [torch.zeros_like(x) for x in gs]
     ls = [torch.zeros(len(q), dtype=torch.float64, device="cuda") for q in cfgs]
-    torch.cuda.synchronize()
-    for g, q in zip(grids, qs):
-        g.set_blobs(q)
     opts = p.ibrd_default_opts(tol=1e-8, precision=p.IBRD_MIXED_REFINE, max_iter=3000, **CHOSEN_SADDLE)
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
-    p.ibrd_solve_saddle_batch([g.handle for g in grids], gs, None, cs, ls, opts)
+    for b0 in range(0, n_cfg, batch):
+        for g, q in zip(grids, qs[b0:b0 + batch]):
+            g.set_blobs(q)
+        for c in cs:
+            c.zero_()
+        torch.cuda.synchronize()
+        p.ibrd_solve_saddle_batch([g.handle for g in grids], gs, None, cs, ls[b0:b0 + batch], opts)
     t_data = time.perf_counter() - t0
     for g in grids:
         g.close()
@@ -620,20 +627,22 @@ def run_learned(p, torch, world, args):
     m = p.GNN(LEARNED_CUTOFF, 256)
     m.init_params(1)
     t0 = time.perf_counter()
-    losses = m.train(qs[:56], [box] * 56, ls[:56], epochs=80, lr=2e-3)
+    losses = m.train(qs[:n_train], [box] * n_train, ls[:n_train], epochs=LEARNED_EPOCHS, lr=2e-3)
     t_train = time.perf_counter() - t0
 
     def err(a, b):
         return float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
 
-    held = {"learned": float(np.mean([err(m.predict(qs[i], box, float(ls[i].sum())), ls[i]) for i in range(56, 64)])),
+    held = {"learned": float(np.mean([err(m.predict(qs[i], box, float(ls[i].sum())), ls[i])
+                                      for i in range(n_train, n_cfg)])),
             "uniform": float(np.mean([err(torch.full_like(ls[i], float(ls[i].mean())), ls[i])
-                                      for i in range(56, 64)]))}
-    out = {"model": f"radial-basis graph network, width 64, cutoff {LEARNED_CUTOFF:g}h, {p.ibrd_gnn_num_params()} "
-                    "FP32 parameters; hand-written CUDA training and inference",
-           "training": {"configs": 56, "held_out": 8, "grid": [side] * 3, "data_s": round(t_data, 3),
-                        "train_s": round(t_train, 3), "epochs": 80, "loss_first": float(losses[0]),
-                        "loss_last": float(losses[-1])},
+                                      for i in range(n_train, n_cfg)]))}
+    out = {"model": f"radial-basis graph network, 3 message-passing layers, width 64, cutoff {LEARNED_CUTOFF:g}h, "
+                    f"{p.ibrd_gnn_num_params()} parameters; hand-written CUDA training (FP32) and inference "
+                    "(bfloat16 mma.sync, FP32 accumulation)",
+           "training": {"configs": n_train, "held_out": n_cfg - n_train, "grid": [side] * 3,
+                        "data_s": round(t_data, 3), "train_s": round(t_train, 3), "epochs": LEARNED_EPOCHS,
+                        "loss_first": float(losses[0]), "loss_last": float(losses[-1])},
            "held_out_rel_error": {k: round(v, 4) for k, v in held.items()}, "eval": {}}
     for name, nblob, spacing in [("256^3, 4096 blobs, spacing 4h", 4096, 4.0),
                                  ("256^3, 16384 blobs, spacing 3h", 16384, 3.0)]:

@@ -441,23 +441,30 @@ ibrd_status ibrd_tune_clear(ibrd_grid g);
    box) that predicts the relative sink strengths lambda_i / <lambda>, used as
    the initial guess of the multipliers (ibrd_solve_opts.lambda_guess =
    IBRD_GUESS_GIVEN). Definition, with s = r / R, f_c = (1 - s)^2 and K = 16
-   radial bases b_k = f_c exp(-((s - k/15) / 0.1)^2), width 64:
-     x_i = sum_j b(r_ij);  h1_i = relu(W1 x_i + c1);
-     m_i = sum_j f_c(r_ij) relu(E b(r_ij) + e) * h1_j (elementwise);
-     h2_i = h1_i + relu(W2 m_i + V2 h1_i + c2);  y_i = o . h2_i + o0;
-     lambda0_i = total exp(y_i) / sum_k exp(y_k).
+   radial bases b_k = f_c exp(-((s - k/15) / 0.1)^2), width 64, L = 3
+   message-passing layers:
+     x_i = sum_j b(r_ij);  h0_i = relu(W0 x_i + c0);
+     for l = 1 .. 3:
+       m_i = sum_j f_c(r_ij) relu(E_l b(r_ij) + e_l) * h_{l-1,j} (elementwise);
+       h_{l,i} = h_{l-1,i} + relu(W_l m_i + V_l h_{l-1,i} + c_l);
+     y_i = o . h_{3,i} + o0;  lambda0_i = total exp(y_i) / sum_k exp(y_k).
    Training minimises <((y - <y>) - (t - <t>))^2>, t_i = log lambda_i, over
    (configuration, lambda) pairs from saddle solves, by Adam (beta 0.9,
-   0.999, eps 1e-8). Parameters are FP32, in the order W1 (64 x 16, row
-   major), c1 (64), E (64 x 16), e (64), W2 (64 x 64), V2 (64 x 64), c2 (64),
-   o (64), o0 (1). Positions q are DEVICE arrays of n x 3 FP64 values (as for
+   0.999, eps 1e-8). Parameters are FP32, in the order W0 (64 x 16, row
+   major), c0 (64), then per layer l = 1, 2, 3: E_l (64 x 16), e_l (64), W_l
+   (64 x 64), V_l (64 x 64), c_l (64); then o (64), o0 (1). Training,
+   ibrd_gnn_loss_grad and ibrd_gnn_forward compute in FP32;
+   ibrd_gnn_predict runs the products E_l b, W_l m and V_l h on the tensor
+   cores with bfloat16 operands (the FP32 values rounded to nearest, ties to
+   even) and FP32 accumulation, everything else in FP32.
+   Positions q are DEVICE arrays of n x 3 FP64 values (as for
    ibrd_set_blobs) in a periodic box lx x ly x lz, within 100 box lengths of
    the origin; the cutoff must not exceed half the shortest side. A blob with more than max_neighbours neighbours
    makes the call fail with IBRD_ERR_ARG. Multipliers lam must be > 0. Every
    call orders its work on the handle's stream and synchronizes it. */
 typedef struct ibrd_gnn_s* ibrd_gnn;
 
-/* Number of parameters (10497). */
+/* Number of parameters (29185). */
 int ibrd_gnn_num_params(void);
 
 /* New model with all parameters 0 (set them with ibrd_gnn_set_params).
@@ -483,10 +490,11 @@ ibrd_status ibrd_gnn_init_params(ibrd_gnn m, unsigned long long seed);
 ibrd_status ibrd_gnn_neighbours(ibrd_gnn m, const double* q, int n, double lx, double ly, double lz, int* count,
                                 int* index, float* dist);
 
-/* y (DEVICE, n FP32 values): the network's outputs. */
+/* y (DEVICE, n FP32 values): the network's outputs (FP32 arithmetic). */
 ibrd_status ibrd_gnn_forward(ibrd_gnn m, const double* q, int n, double lx, double ly, double lz, float* y);
 
-/* lambda0 (DEVICE, n FP64 values) = total * softmax(y). */
+/* lambda0 (DEVICE, n FP64 values) = total * softmax(y), y from the
+   bfloat16 tensor-core inference path. */
 ibrd_status ibrd_gnn_predict(ibrd_gnn m, const double* q, int n, double lx, double ly, double lz, double total,
                              double* lambda0);
 

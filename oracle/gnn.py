@@ -22,14 +22,22 @@ sigma = 1.5 / (K - 1):
 
     b_k(r)  = f_c(s) exp(-((s - mu_k) / sigma)^2)
 
-Network (width H = 64):
+Network (width H = 64, L = 3 message-passing layers):
 
-    x_i    = sum_j b(r_ij)                                  (K)
-    a1_i   = W1 x_i + c1,        h1_i = relu(a1_i)          (H)
-    P_ij   = E b(r_ij) + e,      F_ij = relu(P_ij)          (H, per edge)
-    m_i    = sum_j f_c(s_ij) F_ij * h1_j                    (H, elementwise)
-    a2_i   = W2 m_i + V2 h1_i + c2,  h2_i = h1_i + relu(a2_i)
-    y_i    = o . h2_i + o0
+    x_i    = sum_j b(r_ij)                                       (K)
+    a0_i   = W0 x_i + c0,          h0_i = relu(a0_i)             (H)
+    for l = 1 .. L:
+      P_ij = E_l b(r_ij) + e_l,    F_ij = relu(P_ij)             (H, per edge)
+      m_i  = sum_j f_c(s_ij) F_ij * h_{l-1,j}                    (H, elementwise)
+      a_i  = W_l m_i + V_l h_{l-1,i} + c_l
+      h_{l,i} = h_{l-1,i} + relu(a_i)
+    y_i    = o . h_{L,i} + o0
+
+Inference on tensor cores (forward(..., bf16=True)): the operands of the
+dense products E_l b, W_l m and V_l h -- the weights and the vectors they
+multiply -- are rounded to bfloat16 (the nearest, ties to even, of their
+FP32 values), the products summed exactly and the biases, relus and
+residual sums kept at full precision; the embedding and output stay exact.
 
 Prediction: lambda0_i = T exp(y_i) / sum_k exp(y_k), with T the total the
 solvability condition fixes (zeta sum lambda = h^3 sum g, Appendix A).
@@ -45,12 +53,16 @@ import numpy as np
 
 H = 64
 K = 16
+LAYERS = 3
 SIGMA = 1.5 / (K - 1)
 MU = np.arange(K, dtype=np.float64) / (K - 1)
 
 # Flat parameter layout shared with the library: name, shape.
-LAYOUT = [("W1", (H, K)), ("c1", (H,)), ("E", (H, K)), ("e", (H,)), ("W2", (H, H)), ("V2", (H, H)),
-          ("c2", (H,)), ("o", (H,)), ("o0", (1,))]
+LAYOUT = [("W0", (H, K)), ("c0", (H,))]
+for _l in range(1, LAYERS + 1):
+    LAYOUT += [(f"E{_l}", (H, K)), (f"e{_l}", (H,)), (f"W{_l}", (H, H)), (f"V{_l}", (H, H)), (f"c{_l}", (H,))]
+LAYOUT += [("o", (H,)), ("o0", (1,))]
+BIASES = ["c0"] + [f"{n}{l}" for l in range(1, LAYERS + 1) for n in ("e", "c")]
 
 
 def n_params() -> int:
@@ -85,6 +97,16 @@ def init_params(seed: int) -> np.ndarray:
     return pack(p)
 
 
+def bf16(v) -> np.ndarray:
+    """The bfloat16 nearest to each value's FP32 rounding (ties to even), as
+    float64: the top 16 bits of the FP32 pattern after rounding."""
+    f = np.asarray(v, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    lsb = (u >> 16) & 1
+    u = ((u + 0x7FFF + lsb) >> 16) << 16
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
 def neighbours(q: np.ndarray, box, R: float):
     """Per blob, the neighbours j != i with minimum-image distance < R, in
     increasing j, and those distances (brute force over all pairs)."""
@@ -113,34 +135,38 @@ def cutoff(r: np.ndarray, R: float) -> np.ndarray:
     return (1.0 - np.asarray(r, dtype=np.float64) / R) ** 2
 
 
-def forward(theta: np.ndarray, q: np.ndarray, box, R: float):
+def forward(theta: np.ndarray, q: np.ndarray, box, R: float, bf16_products: bool = False):
     """Outputs y (N,) and the intermediate values the gradient needs."""
     p = unpack(theta)
+    rd = bf16 if bf16_products else (lambda v: v)
     nb, rr = neighbours(q, box, R)
     n = len(q)
     x = np.zeros((n, K))
     for i in range(n):
         if len(nb[i]):
             x[i] = basis(rr[i], R).sum(0)
-    a1 = x @ p["W1"].T + p["c1"]
-    h1 = np.maximum(a1, 0.0)
-    m = np.zeros((n, H))
-    for i in range(n):
-        if len(nb[i]):
-            b = basis(rr[i], R)
-            P = b @ p["E"].T + p["e"]
-            F = np.maximum(P, 0.0)
-            m[i] = (cutoff(rr[i], R)[:, None] * F * h1[nb[i]]).sum(0)
-    a2 = m @ p["W2"].T + h1 @ p["V2"].T + p["c2"]
-    h2 = h1 + np.maximum(a2, 0.0)
-    y = h2 @ p["o"] + p["o0"][0]
-    cache = dict(p=p, nb=nb, rr=rr, x=x, a1=a1, h1=h1, m=m, a2=a2, h2=h2)
+    a0 = x @ p["W0"].T + p["c0"]
+    h = [np.maximum(a0, 0.0)]
+    ms, as_ = [], []
+    for l in range(1, LAYERS + 1):
+        E, e, W, V, c = p[f"E{l}"], p[f"e{l}"], p[f"W{l}"], p[f"V{l}"], p[f"c{l}"]
+        m = np.zeros((n, H))
+        for i in range(n):
+            if len(nb[i]):
+                P = rd(basis(rr[i], R)) @ rd(E).T + e
+                m[i] = (cutoff(rr[i], R)[:, None] * np.maximum(P, 0.0) * h[-1][nb[i]]).sum(0)
+        a = rd(m) @ rd(W).T + rd(h[-1]) @ rd(V).T + c
+        ms.append(m)
+        as_.append(a)
+        h.append(h[-1] + np.maximum(a, 0.0))
+    y = h[-1] @ p["o"] + p["o0"][0]
+    cache = dict(p=p, nb=nb, rr=rr, x=x, a0=a0, h=h, m=ms, a=as_)
     return y, cache
 
 
-def predict(theta, q, box, R, total):
+def predict(theta, q, box, R, total, bf16_products: bool = False):
     """lambda0_i = total * softmax(y)_i."""
-    y, _ = forward(theta, q, box, R)
+    y, _ = forward(theta, q, box, R, bf16_products)
     e = np.exp(y - y.max())
     return total * e / e.sum()
 
@@ -162,31 +188,34 @@ def loss_and_grad(theta, q, box, R, lam):
     L = float(np.mean(r ** 2))
     dy = 2.0 * r / n                       # r already has mean zero
     g = {k: np.zeros_like(v) for k, v in p.items()}
-    g["o"] = dy @ c["h2"]
+    g["o"] = dy @ c["h"][-1]
     g["o0"] = np.array([dy.sum()])
-    dh2 = dy[:, None] * p["o"][None, :]
-    da2 = dh2 * (c["a2"] > 0)
-    g["W2"] = da2.T @ c["m"]
-    g["V2"] = da2.T @ c["h1"]
-    g["c2"] = da2.sum(0)
-    dm = da2 @ p["W2"]
-    dh1 = dh2 + da2 @ p["V2"]
-    for i in range(n):
-        if not len(c["nb"][i]):
-            continue
-        b = basis(c["rr"][i], R)
-        fc = cutoff(c["rr"][i], R)
-        P = b @ p["E"].T + p["e"]
-        F = np.maximum(P, 0.0)
-        hj = c["h1"][c["nb"][i]]
-        # m_i = sum_j fc_ij F_ij * h1_j
-        dh1[c["nb"][i]] += fc[:, None] * F * dm[i][None, :]
-        dP = fc[:, None] * dm[i][None, :] * hj * (P > 0)
-        g["E"] += dP.T @ b
-        g["e"] += dP.sum(0)
-    da1 = dh1 * (c["a1"] > 0)
-    g["W1"] = da1.T @ c["x"]
-    g["c1"] = da1.sum(0)
+    dh = dy[:, None] * p["o"][None, :]     # dL/dh_L
+    for l in range(LAYERS, 0, -1):
+        E, e, W, V = p[f"E{l}"], p[f"e{l}"], p[f"W{l}"], p[f"V{l}"]
+        hprev, m, a = c["h"][l - 1], c["m"][l - 1], c["a"][l - 1]
+        da = dh * (a > 0)
+        g[f"W{l}"] = da.T @ m
+        g[f"V{l}"] = da.T @ hprev
+        g[f"c{l}"] = da.sum(0)
+        dm = da @ W
+        dprev = dh + da @ V               # the residual path and V's
+        for i in range(n):
+            if not len(c["nb"][i]):
+                continue
+            b = basis(c["rr"][i], R)
+            fc = cutoff(c["rr"][i], R)
+            P = b @ E.T + e
+            F = np.maximum(P, 0.0)
+            # m_i = sum_j fc_ij F_ij * h_{l-1,j}
+            dprev[c["nb"][i]] += fc[:, None] * F * dm[i][None, :]
+            dP = fc[:, None] * dm[i][None, :] * hprev[c["nb"][i]] * (P > 0)
+            g[f"E{l}"] += dP.T @ b
+            g[f"e{l}"] += dP.sum(0)
+        dh = dprev
+    da0 = dh * (c["a0"] > 0)
+    g["W0"] = da0.T @ c["x"]
+    g["c0"] = da0.sum(0)
     return L, pack(g)
 
 

@@ -1,25 +1,31 @@
-// Learned multiplier predictor: a small graph network over each blob's
-// neighbours that predicts the relative sink strengths lambda_i / <lambda> of
-// the diffusion-limited saddle point (Eq. saddle_point), used as the initial
+// Learned multiplier predictor: a graph network over each blob's neighbours
+// that predicts the relative sink strengths lambda_i / <lambda> of the
+// diffusion-limited saddle point (Eq. saddle_point), used as the initial
 // guess of the multipliers. The paper names a good treatment of the Schur
 // complement for many blobs as open (Sec. III.E, Sec. V); this network is
 // trained on (configuration, lambda) pairs produced by the saddle solver.
 //
-// Definition (width H = 64, K = 16 radial bases, cutoff R, s = r / R,
-// f_c = (1 - s)^2, b_k = f_c exp(-((s - k/(K-1)) / sigma)^2), sigma = 1.5/(K-1)):
+// Definition (width H = 64, K = 16 radial bases, L = 3 message-passing
+// layers, cutoff R, s = r / R, f_c = (1 - s)^2,
+// b_k = f_c exp(-((s - k/(K-1)) / sigma)^2), sigma = 1.5/(K-1)):
 //   x_i  = sum_j b(r_ij)
-//   h1_i = relu(W1 x_i + c1)
-//   m_i  = sum_j f_c(r_ij) relu(E b(r_ij) + e) * h1_j
-//   h2_i = h1_i + relu(W2 m_i + V2 h1_i + c2)
-//   y_i  = o . h2_i + o0,   lambda0_i = T softmax(y)_i
+//   h0_i = relu(W0 x_i + c0)
+//   layer l: m_i = sum_j f_c(r_ij) relu(E_l b(r_ij) + e_l) * h_{l-1,j}
+//            h_{l,i} = h_{l-1,i} + relu(W_l m_i + V_l h_{l-1,i} + c_l)
+//   y_i  = o . h_{L,i} + o0,   lambda0_i = T softmax(y)_i
 // Loss: <((y - <y>) - (t - <t>))^2>, t = log lambda. Adam updates.
 //
-// Kernels: one warp per blob (lane l owns hidden rows l and l + 32); the
-// neighbour lists are symmetric, so the backward pass gathers every edge
-// contribution at its own node (no atomics). Parameters, activations and
-// gradients are FP32; positions and the predicted multipliers FP64. The dense
-// layers are 64-wide products over a few thousand blobs (a few MFLOP): they
-// run on the FP32 pipes, well inside one launch's latency.
+// Training (and ibrd_gnn_forward) runs in FP32: one warp per blob (lane l
+// owns hidden rows l and l + 32); the neighbour lists are symmetric, so the
+// backward pass gathers every edge contribution at its own node (no
+// atomics). Inference (ibrd_gnn_predict) runs the dense products on the
+// tensor cores with bfloat16 operands and FP32 accumulation (mma.sync
+// m16n8k16): the edge filters E_l b as 16-edge x 16-basis x 64 tiles, one
+// warp per blob, and the node update [W_l V_l] [m; h] as 16-blob x 128 x 64
+// tiles, one warp per 16 blobs, the weights staged in shared memory; biases,
+// relus and the residual sums stay FP32, the embedding and output too.
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -34,20 +40,26 @@ namespace {
 
 constexpr int H = 64;
 constexpr int K = 16;
+constexpr int L = 3;
 constexpr float kSigmaInv = (K - 1) / 1.5f;
-// flat parameter layout (as in the FP64 reference)
-constexpr int OFF_W1 = 0;
-constexpr int OFF_C1 = OFF_W1 + H * K;
-constexpr int OFF_E = OFF_C1 + H;
-constexpr int OFF_EB = OFF_E + H * K;
-constexpr int OFF_W2 = OFF_EB + H;
-constexpr int OFF_V2 = OFF_W2 + H * H;
-constexpr int OFF_C2 = OFF_V2 + H * H;
-constexpr int OFF_O = OFF_C2 + H;
+// flat parameter layout (as in the FP64 reference): W0, c0, per layer
+// (E, e, W, V, c), o, o0
+constexpr int OFF_W0 = 0;
+constexpr int OFF_C0 = OFF_W0 + H * K;
+constexpr int LSZ = H * K + H + 2 * H * H + H;
+__host__ __device__ constexpr int lbase(int l) { return OFF_C0 + H + (l - 1) * LSZ; }  // l = 1 .. L
+__host__ __device__ constexpr int offE(int l) { return lbase(l); }
+__host__ __device__ constexpr int offEB(int l) { return lbase(l) + H * K; }
+__host__ __device__ constexpr int offW(int l) { return lbase(l) + H * K + H; }
+__host__ __device__ constexpr int offV(int l) { return lbase(l) + H * K + H + H * H; }
+__host__ __device__ constexpr int offC(int l) { return lbase(l) + H * K + H + 2 * H * H; }
+constexpr int OFF_O = OFF_C0 + H + L * LSZ;
 constexpr int OFF_O0 = OFF_O + H;
 constexpr int NPARAM = OFF_O0 + 1;
 constexpr int kWarps = 8;  // blobs per CTA
 constexpr int kPad = H + 1; // shared-memory row stride of the 64 x 64 matrices
+// bfloat16 weights for inference, per layer: E_l (H x K), then [W_l V_l] (H x 2H)
+constexpr int BLSZ = H * K + 2 * H * H;
 
 __device__ __forceinline__ float basis_k(float s, int k) {
   const float fc = (1.f - s) * (1.f - s);
@@ -144,11 +156,11 @@ __global__ void __launch_bounds__(kWarps * 32) k_gnn_neighbours(const double* __
   }
 }
 
-// x_i, a1_i = W1 x_i + c1, h1_i = relu(a1_i).
-__global__ void __launch_bounds__(kWarps * 32) k_gnn_layer1(const float* __restrict__ th, int n, float invR,
+// x_i, a0_i = W0 x_i + c0, h0_i = relu(a0_i).
+__global__ void __launch_bounds__(kWarps * 32) k_gnn_layer0(const float* __restrict__ th, int n, float invR,
                                                             int kmax, const int* __restrict__ cnt,
                                                             const float* __restrict__ nr, float* __restrict__ x,
-                                                            float* __restrict__ a1, float* __restrict__ h1) {
+                                                            float* __restrict__ a0, float* __restrict__ h0) {
   const int lane = threadIdx.x & 31;
   const int i = blockIdx.x * kWarps + (threadIdx.x >> 5);
   if (i >= n) return;
@@ -160,36 +172,37 @@ __global__ void __launch_bounds__(kWarps * 32) k_gnn_layer1(const float* __restr
 #pragma unroll
   for (int half = 0; half < 2; ++half) {
     const int row = lane + 32 * half;
-    float a = th[OFF_C1 + row];
-    for (int kk = 0; kk < K; ++kk) a = fmaf(th[OFF_W1 + row * K + kk], __shfl_sync(0xffffffffu, xk, kk), a);
-    a1[(size_t)i * H + row] = a;
-    h1[(size_t)i * H + row] = fmaxf(a, 0.f);
+    float a = th[OFF_C0 + row];
+    for (int kk = 0; kk < K; ++kk) a = fmaf(th[OFF_W0 + row * K + kk], __shfl_sync(0xffffffffu, xk, kk), a);
+    a0[(size_t)i * H + row] = a;
+    h0[(size_t)i * H + row] = fmaxf(a, 0.f);
   }
 }
 
-// Loads W2 and V2 into shared memory with a padded row stride.
-__device__ __forceinline__ void load_mats(const float* __restrict__ th, float* sW2, float* sV2) {
+// Loads W_l and V_l into shared memory with a padded row stride.
+__device__ __forceinline__ void load_mats(const float* __restrict__ th, int l, float* sW, float* sV) {
   for (int t = threadIdx.x; t < H * H; t += blockDim.x) {
     const int r = t / H, c = t - r * H;
-    sW2[r * kPad + c] = th[OFF_W2 + t];
-    sV2[r * kPad + c] = th[OFF_V2 + t];
+    sW[r * kPad + c] = th[offW(l) + t];
+    sV[r * kPad + c] = th[offV(l) + t];
   }
 }
 
-// m_i, a2_i = W2 m_i + V2 h1_i + c2, y_i = o . (h1_i + relu(a2_i)) + o0.
-__global__ void __launch_bounds__(kWarps * 32) k_gnn_layer2(const float* __restrict__ th, int n, float invR,
-                                                            int kmax, const int* __restrict__ cnt,
-                                                            const int* __restrict__ nidx,
-                                                            const float* __restrict__ nr,
-                                                            const float* __restrict__ h1, float* __restrict__ m,
-                                                            float* __restrict__ a2, float* __restrict__ y) {
-  __shared__ float sW2[H * kPad], sV2[H * kPad];
-  load_mats(th, sW2, sV2);
+// Layer l (FP32): m_i, a_i = W_l m_i + V_l hp_i + c_l, h_i = hp_i + relu(a_i).
+__global__ void __launch_bounds__(kWarps * 32) k_gnn_mp(const float* __restrict__ th, int l, int n, float invR,
+                                                        int kmax, const int* __restrict__ cnt,
+                                                        const int* __restrict__ nidx, const float* __restrict__ nr,
+                                                        const float* __restrict__ hp, float* __restrict__ m,
+                                                        float* __restrict__ a, float* __restrict__ h) {
+  __shared__ float sW[H * kPad], sV[H * kPad];
+  load_mats(th, l, sW, sV);
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int i = blockIdx.x * kWarps + (threadIdx.x >> 5);
   if (i >= n) return;
   const int k = lane & (K - 1);
+  const float* E = th + offE(l);
+  const float* eb = th + offEB(l);
   float m0 = 0.f, m1 = 0.f;
   const int c = cnt[i];
   for (int e = 0; e < c; ++e) {
@@ -197,28 +210,38 @@ __global__ void __launch_bounds__(kWarps * 32) k_gnn_layer2(const float* __restr
     const float s = nr[(size_t)i * kmax + e] * invR;
     const float bk = basis_k(s, k);
     const float fc = (1.f - s) * (1.f - s);
-    float p0 = th[OFF_EB + lane], p1 = th[OFF_EB + lane + 32];
+    float p0 = eb[lane], p1 = eb[lane + 32];
     for (int kk = 0; kk < K; ++kk) {
       const float b = __shfl_sync(0xffffffffu, bk, kk);
-      p0 = fmaf(th[OFF_E + lane * K + kk], b, p0);
-      p1 = fmaf(th[OFF_E + (lane + 32) * K + kk], b, p1);
+      p0 = fmaf(E[lane * K + kk], b, p0);
+      p1 = fmaf(E[(lane + 32) * K + kk], b, p1);
     }
-    m0 = fmaf(fc * fmaxf(p0, 0.f), h1[(size_t)j * H + lane], m0);
-    m1 = fmaf(fc * fmaxf(p1, 0.f), h1[(size_t)j * H + lane + 32], m1);
+    m0 = fmaf(fc * fmaxf(p0, 0.f), hp[(size_t)j * H + lane], m0);
+    m1 = fmaf(fc * fmaxf(p1, 0.f), hp[(size_t)j * H + lane + 32], m1);
   }
-  const float hi0 = h1[(size_t)i * H + lane], hi1 = h1[(size_t)i * H + lane + 32];
-  float s0 = th[OFF_C2 + lane], s1 = th[OFF_C2 + lane + 32];
+  const float hi0 = hp[(size_t)i * H + lane], hi1 = hp[(size_t)i * H + lane + 32];
+  float s0 = th[offC(l) + lane], s1 = th[offC(l) + lane + 32];
   for (int kk = 0; kk < H; ++kk) {
     const float mk = __shfl_sync(0xffffffffu, kk < 32 ? m0 : m1, kk & 31);
     const float hk = __shfl_sync(0xffffffffu, kk < 32 ? hi0 : hi1, kk & 31);
-    s0 = fmaf(sW2[lane * kPad + kk], mk, fmaf(sV2[lane * kPad + kk], hk, s0));
-    s1 = fmaf(sW2[(lane + 32) * kPad + kk], mk, fmaf(sV2[(lane + 32) * kPad + kk], hk, s1));
+    s0 = fmaf(sW[lane * kPad + kk], mk, fmaf(sV[lane * kPad + kk], hk, s0));
+    s1 = fmaf(sW[(lane + 32) * kPad + kk], mk, fmaf(sV[(lane + 32) * kPad + kk], hk, s1));
   }
   m[(size_t)i * H + lane] = m0;
   m[(size_t)i * H + lane + 32] = m1;
-  a2[(size_t)i * H + lane] = s0;
-  a2[(size_t)i * H + lane + 32] = s1;
-  float v = th[OFF_O + lane] * (hi0 + fmaxf(s0, 0.f)) + th[OFF_O + lane + 32] * (hi1 + fmaxf(s1, 0.f));
+  a[(size_t)i * H + lane] = s0;
+  a[(size_t)i * H + lane + 32] = s1;
+  h[(size_t)i * H + lane] = hi0 + fmaxf(s0, 0.f);
+  h[(size_t)i * H + lane + 32] = hi1 + fmaxf(s1, 0.f);
+}
+
+// y_i = o . h_i + o0.
+__global__ void __launch_bounds__(kWarps * 32) k_gnn_out(const float* __restrict__ th, int n,
+                                                         const float* __restrict__ h, float* __restrict__ y) {
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * kWarps + (threadIdx.x >> 5);
+  if (i >= n) return;
+  float v = th[OFF_O + lane] * h[(size_t)i * H + lane] + th[OFF_O + lane + 32] * h[(size_t)i * H + lane + 32];
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   if (lane == 0) y[i] = v + th[OFF_O0];
 }
@@ -286,56 +309,67 @@ __global__ void __launch_bounds__(1024) k_gnn_softmax(const float* __restrict__ 
   for (int i = threadIdx.x; i < n; i += blockDim.x) lam0[i] = total * exp((double)y[i] - ymax) / S;
 }
 
-// Backward through the node layers: da2 = dy o * [a2 > 0], dm = W2^T da2,
-// dh1 (direct) = dy o + V2^T da2.
-__global__ void __launch_bounds__(kWarps * 32) k_gnn_back_node(const float* __restrict__ th, int n,
+// Backward through layer l's node update: dh = dh_in (or dy o at the last
+// layer), da = dh [a > 0], dm = W_l^T da, dhv = dh + V_l^T da.
+__global__ void __launch_bounds__(kWarps * 32) k_gnn_back_node(const float* __restrict__ th, int l, int n,
+                                                               const float* __restrict__ dh_in,
                                                                const float* __restrict__ dy,
-                                                               const float* __restrict__ a2,
-                                                               float* __restrict__ da2, float* __restrict__ dm,
-                                                               float* __restrict__ dh1) {
-  __shared__ float sW2[H * kPad], sV2[H * kPad];
-  load_mats(th, sW2, sV2);
+                                                               const float* __restrict__ a,
+                                                               float* __restrict__ da, float* __restrict__ dm,
+                                                               float* __restrict__ dhv) {
+  __shared__ float sW[H * kPad], sV[H * kPad];
+  load_mats(th, l, sW, sV);
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int i = blockIdx.x * kWarps + (threadIdx.x >> 5);
   if (i >= n) return;
-  const float g = dy[i];
-  const float dh0 = g * th[OFF_O + lane], dh1v = g * th[OFF_O + lane + 32];
-  const float d0 = a2[(size_t)i * H + lane] > 0.f ? dh0 : 0.f;
-  const float d1 = a2[(size_t)i * H + lane + 32] > 0.f ? dh1v : 0.f;
-  float dm0 = 0.f, dm1 = 0.f, dv0 = dh0, dv1 = dh1v;
+  float dh0, dh1;
+  if (dh_in) {
+    dh0 = dh_in[(size_t)i * H + lane];
+    dh1 = dh_in[(size_t)i * H + lane + 32];
+  } else {
+    const float g = dy[i];
+    dh0 = g * th[OFF_O + lane];
+    dh1 = g * th[OFF_O + lane + 32];
+  }
+  const float d0 = a[(size_t)i * H + lane] > 0.f ? dh0 : 0.f;
+  const float d1 = a[(size_t)i * H + lane + 32] > 0.f ? dh1 : 0.f;
+  float dm0 = 0.f, dm1 = 0.f, dv0 = dh0, dv1 = dh1;
   for (int r = 0; r < H; ++r) {
     const float dr = __shfl_sync(0xffffffffu, r < 32 ? d0 : d1, r & 31);
-    dm0 = fmaf(sW2[r * kPad + lane], dr, dm0);
-    dm1 = fmaf(sW2[r * kPad + lane + 32], dr, dm1);
-    dv0 = fmaf(sV2[r * kPad + lane], dr, dv0);
-    dv1 = fmaf(sV2[r * kPad + lane + 32], dr, dv1);
+    dm0 = fmaf(sW[r * kPad + lane], dr, dm0);
+    dm1 = fmaf(sW[r * kPad + lane + 32], dr, dm1);
+    dv0 = fmaf(sV[r * kPad + lane], dr, dv0);
+    dv1 = fmaf(sV[r * kPad + lane + 32], dr, dv1);
   }
-  da2[(size_t)i * H + lane] = d0;
-  da2[(size_t)i * H + lane + 32] = d1;
+  da[(size_t)i * H + lane] = d0;
+  da[(size_t)i * H + lane + 32] = d1;
   dm[(size_t)i * H + lane] = dm0;
   dm[(size_t)i * H + lane + 32] = dm1;
-  dh1[(size_t)i * H + lane] = dv0;
-  dh1[(size_t)i * H + lane + 32] = dv1;
+  dhv[(size_t)i * H + lane] = dv0;
+  dhv[(size_t)i * H + lane + 32] = dv1;
 }
 
-// Backward through the message layer at blob i, over its own neighbour list
-// (symmetric): dh1_i += sum_j f_c F_ij * dm_j (the messages of the j that used
-// h1_i), and the filter gradient dP_ij = f_c dm_i * h1_j * [P_ij > 0] gives
-// this CTA's partial sums of dE (H x K) and de (H). Then da1_i = dh1_i [a1 > 0].
-__global__ void __launch_bounds__(kWarps * 32) k_gnn_back_edges(const float* __restrict__ th, int n, float invR,
-                                                                int kmax, const int* __restrict__ cnt,
+// Backward through layer l's messages at blob i, over its own neighbour list
+// (symmetric): dh_out_i = dhv_i + sum_j f_c F_ij * dm_j (the messages of the j
+// that used hp_i), and the filter gradient dP_ij = f_c dm_i * hp_j * [P_ij > 0]
+// gives this CTA's partial sums of dE_l (H x K) and de_l (H). With a0 (the
+// first layer) dh_out is the embedding's da0 = dh_0 [a0 > 0].
+__global__ void __launch_bounds__(kWarps * 32) k_gnn_back_edges(const float* __restrict__ th, int l, int n,
+                                                                float invR, int kmax, const int* __restrict__ cnt,
                                                                 const int* __restrict__ nidx,
                                                                 const float* __restrict__ nr,
-                                                                const float* __restrict__ h1,
-                                                                const float* __restrict__ a1,
+                                                                const float* __restrict__ hp,
                                                                 const float* __restrict__ dm,
-                                                                const float* __restrict__ dh1,
-                                                                float* __restrict__ da1,
+                                                                const float* __restrict__ dhv,
+                                                                const float* __restrict__ a0,
+                                                                float* __restrict__ dh_out,
                                                                 float* __restrict__ part) {
   __shared__ float sE[kWarps][H * (K + 1)];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int i = blockIdx.x * kWarps + w;
+  const float* E = th + offE(l);
+  const float* eb = th + offEB(l);
   float gE0[K], gE1[K];
 #pragma unroll
   for (int kk = 0; kk < K; ++kk) gE0[kk] = gE1[kk] = 0.f;
@@ -343,26 +377,26 @@ __global__ void __launch_bounds__(kWarps * 32) k_gnn_back_edges(const float* __r
   if (i < n) {
     const int k = lane & (K - 1);
     const float dmi0 = dm[(size_t)i * H + lane], dmi1 = dm[(size_t)i * H + lane + 32];
-    float acc0 = dh1[(size_t)i * H + lane], acc1 = dh1[(size_t)i * H + lane + 32];
+    float acc0 = dhv[(size_t)i * H + lane], acc1 = dhv[(size_t)i * H + lane + 32];
     const int c = cnt[i];
     for (int e = 0; e < c; ++e) {
       const int j = nidx[(size_t)i * kmax + e];
       const float s = nr[(size_t)i * kmax + e] * invR;
       const float bk = basis_k(s, k);
       const float fc = (1.f - s) * (1.f - s);
-      float p0 = th[OFF_EB + lane], p1 = th[OFF_EB + lane + 32];
+      float p0 = eb[lane], p1 = eb[lane + 32];
       float b[K];
 #pragma unroll
       for (int kk = 0; kk < K; ++kk) {
         b[kk] = __shfl_sync(0xffffffffu, bk, kk);
-        p0 = fmaf(th[OFF_E + lane * K + kk], b[kk], p0);
-        p1 = fmaf(th[OFF_E + (lane + 32) * K + kk], b[kk], p1);
+        p0 = fmaf(E[lane * K + kk], b[kk], p0);
+        p1 = fmaf(E[(lane + 32) * K + kk], b[kk], p1);
       }
       const float F0 = fmaxf(p0, 0.f), F1 = fmaxf(p1, 0.f);
       acc0 = fmaf(fc * F0, dm[(size_t)j * H + lane], acc0);
       acc1 = fmaf(fc * F1, dm[(size_t)j * H + lane + 32], acc1);
-      const float q0 = p0 > 0.f ? fc * dmi0 * h1[(size_t)j * H + lane] : 0.f;
-      const float q1 = p1 > 0.f ? fc * dmi1 * h1[(size_t)j * H + lane + 32] : 0.f;
+      const float q0 = p0 > 0.f ? fc * dmi0 * hp[(size_t)j * H + lane] : 0.f;
+      const float q1 = p1 > 0.f ? fc * dmi1 * hp[(size_t)j * H + lane + 32] : 0.f;
       ge0 += q0;
       ge1 += q1;
 #pragma unroll
@@ -371,8 +405,12 @@ __global__ void __launch_bounds__(kWarps * 32) k_gnn_back_edges(const float* __r
         gE1[kk] = fmaf(q1, b[kk], gE1[kk]);
       }
     }
-    da1[(size_t)i * H + lane] = a1[(size_t)i * H + lane] > 0.f ? acc0 : 0.f;
-    da1[(size_t)i * H + lane + 32] = a1[(size_t)i * H + lane + 32] > 0.f ? acc1 : 0.f;
+    if (a0) {
+      acc0 = a0[(size_t)i * H + lane] > 0.f ? acc0 : 0.f;
+      acc1 = a0[(size_t)i * H + lane + 32] > 0.f ? acc1 : 0.f;
+    }
+    dh_out[(size_t)i * H + lane] = acc0;
+    dh_out[(size_t)i * H + lane + 32] = acc1;
   }
   // this CTA's partial sums, warps added in a fixed order
 #pragma unroll
@@ -390,47 +428,230 @@ __global__ void __launch_bounds__(kWarps * 32) k_gnn_back_edges(const float* __r
   }
 }
 
+// Activations and gradients the parameter gradients read.
+struct GradArgs {
+  int n, nblk;
+  const float* x;     // N x K
+  const float* da0;   // N x H
+  const float* h;     // (L + 1) x N x H: h_0 .. h_L
+  const float* m;     // L x N x H
+  const float* da;    // L x N x H
+  const float* dy;    // N
+  const float* part;  // L x nblk x H x (K + 1)
+};
+
 // Parameter gradients that are sums over blobs, one thread per parameter,
-// blobs added in increasing order: dW1 = sum da1 x^T, dc1 = sum da1,
-// dW2 = sum da2 m^T, dV2 = sum da2 h1^T, dc2 = sum da2, do = sum dy h2,
-// do0 = sum dy, and dE / de from the per-CTA partials.
-__global__ void k_gnn_param_grads(int n, int nblk, const float* __restrict__ x, const float* __restrict__ h1,
-                                  const float* __restrict__ m, const float* __restrict__ a2,
-                                  const float* __restrict__ dy, const float* __restrict__ da1,
-                                  const float* __restrict__ da2, const float* __restrict__ part,
-                                  float* __restrict__ grad) {
+// blobs added in increasing order: dW0 = sum da0 x^T, dc0 = sum da0, per layer
+// dW_l = sum da_l m_l^T, dV_l = sum da_l h_{l-1}^T, dc_l = sum da_l and dE_l /
+// de_l from the per-CTA partials, do = sum dy h_L, do0 = sum dy.
+__global__ void k_gnn_param_grads(GradArgs ga, float* __restrict__ grad) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= NPARAM) return;
+  const int n = ga.n;
+  const size_t NH = (size_t)n * H;
   float s = 0.f;
-  if (p < OFF_C1) {
+  if (p < OFF_C0) {
     const int r = p / K, c = p - r * K;
-    for (int i = 0; i < n; ++i) s = fmaf(da1[(size_t)i * H + r], x[(size_t)i * K + c], s);
-  } else if (p < OFF_E) {
-    const int r = p - OFF_C1;
-    for (int i = 0; i < n; ++i) s += da1[(size_t)i * H + r];
-  } else if (p < OFF_W2) {
-    // E (row r, col c) and e (row r) from the CTA partials
-    const int q = p - OFF_E;
-    const int r = q < H * K ? q / K : q - H * K;
-    const int c = q < H * K ? q - (q / K) * K : K;
-    for (int b = 0; b < nblk; ++b) s += part[(size_t)b * H * (K + 1) + r * (K + 1) + c];
-  } else if (p < OFF_V2) {
-    const int q = p - OFF_W2, r = q / H, c = q - r * H;
-    for (int i = 0; i < n; ++i) s = fmaf(da2[(size_t)i * H + r], m[(size_t)i * H + c], s);
-  } else if (p < OFF_C2) {
-    const int q = p - OFF_V2, r = q / H, c = q - r * H;
-    for (int i = 0; i < n; ++i) s = fmaf(da2[(size_t)i * H + r], h1[(size_t)i * H + c], s);
+    for (int i = 0; i < n; ++i) s = fmaf(ga.da0[(size_t)i * H + r], ga.x[(size_t)i * K + c], s);
+  } else if (p < OFF_C0 + H) {
+    const int r = p - OFF_C0;
+    for (int i = 0; i < n; ++i) s += ga.da0[(size_t)i * H + r];
   } else if (p < OFF_O) {
-    const int r = p - OFF_C2;
-    for (int i = 0; i < n; ++i) s += da2[(size_t)i * H + r];
+    const int l = (p - lbase(1)) / LSZ + 1;
+    const int q = p - lbase(l);
+    const float* da = ga.da + (size_t)(l - 1) * NH;
+    if (q < H * K + H) {
+      // E (row r, col c) and e (row r) from the CTA partials
+      const int r = q < H * K ? q / K : q - H * K;
+      const int c = q < H * K ? q - (q / K) * K : K;
+      const float* part = ga.part + (size_t)(l - 1) * ga.nblk * H * (K + 1);
+      for (int b = 0; b < ga.nblk; ++b) s += part[(size_t)b * H * (K + 1) + r * (K + 1) + c];
+    } else if (q < H * K + H + H * H) {
+      const int t = q - (H * K + H), r = t / H, c = t - r * H;
+      const float* m = ga.m + (size_t)(l - 1) * NH;
+      for (int i = 0; i < n; ++i) s = fmaf(da[(size_t)i * H + r], m[(size_t)i * H + c], s);
+    } else if (q < H * K + H + 2 * H * H) {
+      const int t = q - (H * K + H + H * H), r = t / H, c = t - r * H;
+      const float* hp = ga.h + (size_t)(l - 1) * NH;
+      for (int i = 0; i < n; ++i) s = fmaf(da[(size_t)i * H + r], hp[(size_t)i * H + c], s);
+    } else {
+      const int r = q - (H * K + H + 2 * H * H);
+      for (int i = 0; i < n; ++i) s += da[(size_t)i * H + r];
+    }
   } else if (p < OFF_O0) {
     const int r = p - OFF_O;
-    for (int i = 0; i < n; ++i)
-      s = fmaf(dy[i], h1[(size_t)i * H + r] + fmaxf(a2[(size_t)i * H + r], 0.f), s);
+    const float* hL = ga.h + (size_t)L * NH;
+    for (int i = 0; i < n; ++i) s = fmaf(ga.dy[i], hL[(size_t)i * H + r], s);
   } else {
-    for (int i = 0; i < n; ++i) s += dy[i];
+    for (int i = 0; i < n; ++i) s += ga.dy[i];
   }
   grad[p] = s;
+}
+
+// ---------------------------------------------------------------- inference on tensor cores
+// bfloat16 copies of the layers' weights: per layer E_l (H x K), then
+// [W_l V_l] (H x 2H, row n = W_l row n followed by V_l row n).
+__global__ void k_gnn_weights_bf16(const float* __restrict__ th, __nv_bfloat16* __restrict__ wb) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= L * BLSZ) return;
+  const int l = t / BLSZ + 1, q = t - (l - 1) * BLSZ;
+  float v;
+  if (q < H * K) {
+    v = th[offE(l) + q];
+  } else {
+    const int r = (q - H * K) / (2 * H), c = (q - H * K) - r * 2 * H;
+    v = c < H ? th[offW(l) + r * H + c] : th[offV(l) + r * H + c - H];
+  }
+  wb[t] = __float2bfloat16_rn(v);
+}
+
+__device__ __forceinline__ unsigned bf16x2(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);  // .x (low half) = lo
+  return *reinterpret_cast<const unsigned*>(&v);
+}
+
+// D += A B for one m16n8k16 tile: A 16 x 16 bfloat16 (row), B 16 x 8 (col),
+// FP32 accumulators.
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Layer l's messages on tensor cores: one warp per blob i; its edges in tiles
+// of 16 (rows) against the 64 filter outputs (8 column tiles of 8), K = 16
+// bases deep. Fragment ownership (m16n8k16): lane = 4 g + t holds A at rows
+// g, g + 8 and columns 2t, 2t + 1, 2t + 8, 2t + 9; B at rows 2t, 2t + 1,
+// 2t + 8, 2t + 9 and column g; D at rows g, g + 8 and columns 2t, 2t + 1.
+// Each lane then sums relu(P + e) f_c hp_j over its two edge rows, and the
+// eight lanes of a column pair add theirs.
+__global__ void __launch_bounds__(kWarps * 32) k_gnn_msg_tc(const float* __restrict__ th,
+                                                            const __nv_bfloat16* __restrict__ wb, int l, int n,
+                                                            float invR, int kmax, const int* __restrict__ cnt,
+                                                            const int* __restrict__ nidx,
+                                                            const float* __restrict__ nr,
+                                                            const float* __restrict__ hp, float* __restrict__ m) {
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * kWarps + (threadIdx.x >> 5);
+  if (i >= n) return;
+  const int g = lane >> 2, t = lane & 3;
+  const __nv_bfloat16* E = wb + (size_t)(l - 1) * BLSZ;
+  const float* eb = th + offEB(l);
+  unsigned b0[8], b1[8];
+  float2 bias[8];
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) {
+    const int col = 8 * nt + g;  // B column = filter output
+    b0[nt] = *reinterpret_cast<const unsigned*>(E + col * K + 2 * t);
+    b1[nt] = *reinterpret_cast<const unsigned*>(E + col * K + 2 * t + 8);
+    bias[nt] = make_float2(eb[8 * nt + 2 * t], eb[8 * nt + 2 * t + 1]);
+  }
+  float acc[8][2];
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) acc[nt][0] = acc[nt][1] = 0.f;
+  const int c = cnt[i];
+  for (int e0 = 0; e0 < c; e0 += 16) {
+    const int r0 = e0 + g, r1 = e0 + g + 8;
+    const bool v0 = r0 < c, v1 = r1 < c;
+    const float s0 = v0 ? nr[(size_t)i * kmax + r0] * invR : 1.f;
+    const float s1 = v1 ? nr[(size_t)i * kmax + r1] * invR : 1.f;
+    const int j0 = v0 ? nidx[(size_t)i * kmax + r0] : 0, j1 = v1 ? nidx[(size_t)i * kmax + r1] : 0;
+    // s = 1 (no edge): every basis and the cutoff vanish
+    unsigned a[4];
+    a[0] = bf16x2(basis_k(s0, 2 * t), basis_k(s0, 2 * t + 1));
+    a[1] = bf16x2(basis_k(s1, 2 * t), basis_k(s1, 2 * t + 1));
+    a[2] = bf16x2(basis_k(s0, 2 * t + 8), basis_k(s0, 2 * t + 9));
+    a[3] = bf16x2(basis_k(s1, 2 * t + 8), basis_k(s1, 2 * t + 9));
+    const float fc0 = (1.f - s0) * (1.f - s0), fc1 = (1.f - s1) * (1.f - s1);
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      float d[4] = {0.f, 0.f, 0.f, 0.f};
+      mma_bf16(d, a, b0[nt], b1[nt]);
+      const int col = 8 * nt + 2 * t;
+      const float2 h0 = *reinterpret_cast<const float2*>(hp + (size_t)j0 * H + col);
+      const float2 h1 = *reinterpret_cast<const float2*>(hp + (size_t)j1 * H + col);
+      acc[nt][0] += fc0 * fmaxf(d[0] + bias[nt].x, 0.f) * h0.x + fc1 * fmaxf(d[2] + bias[nt].x, 0.f) * h1.x;
+      acc[nt][1] += fc0 * fmaxf(d[1] + bias[nt].y, 0.f) * h0.y + fc1 * fmaxf(d[3] + bias[nt].y, 0.f) * h1.y;
+    }
+  }
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) {
+#pragma unroll
+    for (int o = 4; o < 32; o <<= 1) {
+      acc[nt][0] += __shfl_xor_sync(0xffffffffu, acc[nt][0], o);
+      acc[nt][1] += __shfl_xor_sync(0xffffffffu, acc[nt][1], o);
+    }
+    if (g == 0)
+      *reinterpret_cast<float2*>(m + (size_t)i * H + 8 * nt + 2 * t) = make_float2(acc[nt][0], acc[nt][1]);
+  }
+}
+
+// Layer l's node update on tensor cores: one warp per 16 blobs, a = [m hp]
+// (16 x 128) times [W_l V_l]^T (128 x 64) in 8 k-steps and 8 column tiles,
+// the weights staged in shared memory; h = hp + relu(a + c_l).
+// The staged rows are padded to 136 elements (68 words) so that the eight
+// rows one B fragment load touches fall in distinct banks.
+constexpr int kNodeWarps = 4;
+constexpr int kWVStride = 2 * H + 8;
+__global__ void __launch_bounds__(kNodeWarps * 32) k_gnn_node_tc(const float* __restrict__ th,
+                                                                 const __nv_bfloat16* __restrict__ wb, int l, int n,
+                                                                 const float* __restrict__ m,
+                                                                 const float* __restrict__ hp,
+                                                                 float* __restrict__ h) {
+  __shared__ __align__(16) __nv_bfloat16 sWV[H * kWVStride];
+  const __nv_bfloat16* WV = wb + (size_t)(l - 1) * BLSZ + H * K;
+  for (int q = threadIdx.x; q < H * 2 * H / 8; q += blockDim.x) {
+    const int r = q / (2 * H / 8), c8 = q - r * (2 * H / 8);
+    *reinterpret_cast<uint4*>(sWV + r * kWVStride + 8 * c8) = reinterpret_cast<const uint4*>(WV)[q];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int g = lane >> 2, t = lane & 3;
+  const int base = (blockIdx.x * kNodeWarps + (threadIdx.x >> 5)) * 16;
+  if (base >= n) return;
+  const int r0 = base + g, r1 = base + g + 8;
+  const bool v0 = r0 < n, v1 = r1 < n;
+  float d[8][4];
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) d[nt][0] = d[nt][1] = d[nt][2] = d[nt][3] = 0.f;
+  auto src = [&](int row, int kc) -> float2 {  // [m hp] at (row, kc), kc even
+    const float* p = kc < H ? m + (size_t)row * H + kc : hp + (size_t)row * H + kc - H;
+    return *reinterpret_cast<const float2*>(p);
+  };
+#pragma unroll
+  for (int ks = 0; ks < 8; ++ks) {
+    const int kc = 16 * ks + 2 * t;
+    const float2 z = make_float2(0.f, 0.f);
+    const float2 x00 = v0 ? src(r0, kc) : z, x10 = v1 ? src(r1, kc) : z;
+    const float2 x01 = v0 ? src(r0, kc + 8) : z, x11 = v1 ? src(r1, kc + 8) : z;
+    const unsigned a[4] = {bf16x2(x00.x, x00.y), bf16x2(x10.x, x10.y), bf16x2(x01.x, x01.y),
+                           bf16x2(x11.x, x11.y)};
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      const int col = 8 * nt + g;
+      const unsigned b0 = *reinterpret_cast<const unsigned*>(sWV + col * kWVStride + kc);
+      const unsigned b1 = *reinterpret_cast<const unsigned*>(sWV + col * kWVStride + kc + 8);
+      mma_bf16(d[nt], a, b0, b1);
+    }
+  }
+  const float* cb = th + offC(l);
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) {
+    const int col = 8 * nt + 2 * t;
+    const float2 c = make_float2(cb[col], cb[col + 1]);
+    if (v0) {
+      const float2 p = *reinterpret_cast<const float2*>(hp + (size_t)r0 * H + col);
+      *reinterpret_cast<float2*>(h + (size_t)r0 * H + col) =
+          make_float2(p.x + fmaxf(d[nt][0] + c.x, 0.f), p.y + fmaxf(d[nt][1] + c.y, 0.f));
+    }
+    if (v1) {
+      const float2 p = *reinterpret_cast<const float2*>(hp + (size_t)r1 * H + col);
+      *reinterpret_cast<float2*>(h + (size_t)r1 * H + col) =
+          make_float2(p.x + fmaxf(d[nt][2] + c.x, 0.f), p.y + fmaxf(d[nt][3] + c.y, 0.f));
+    }
+  }
 }
 
 // Adam with bias correction; c1 = 1 - beta1^t, c2 = 1 - beta2^t.
@@ -466,8 +687,13 @@ struct ibrd_gnn_s {
   int cap = 0;
   int *cnt = nullptr, *nidx = nullptr, *oflow = nullptr;
   float4* p32 = nullptr;
-  float *nr = nullptr, *x = nullptr, *a1 = nullptr, *h1 = nullptr, *m = nullptr, *a2 = nullptr, *y = nullptr;
-  float *dy = nullptr, *da1 = nullptr, *da2 = nullptr, *dm = nullptr, *dh1 = nullptr, *part = nullptr;
+  // forward: x (N x K), a0 (N x H), h_0 .. h_L ((L + 1) x N x H), m_l and
+  // a_l (L x N x H each), y (N); backward: dy, da0, da_l, dm, dhv, dh, and
+  // the per-CTA filter-gradient partials (L x CTAs x H x (K + 1))
+  float *nr = nullptr, *x = nullptr, *a0 = nullptr, *h = nullptr, *m = nullptr, *a = nullptr, *y = nullptr;
+  float *dy = nullptr, *da0 = nullptr, *da = nullptr, *dm = nullptr, *dhv = nullptr, *dh = nullptr;
+  float* part = nullptr;
+  __nv_bfloat16* wb = nullptr;  // bfloat16 layer weights for inference
   double* loss = nullptr;  // device scalar
   double* host = nullptr;  // pinned
   std::string err;
@@ -521,17 +747,18 @@ void ensure_cap(ibrd_gnn m, int n) {
   galloc(&m->nidx, N * m->kmax);
   galloc(&m->nr, N * m->kmax);
   galloc(&m->x, N * K);
-  galloc(&m->a1, N * H);
-  galloc(&m->h1, N * H);
-  galloc(&m->m, N * H);
-  galloc(&m->a2, N * H);
+  galloc(&m->a0, N * H);
+  galloc(&m->h, (L + 1) * N * H);
+  galloc(&m->m, L * N * H);
+  galloc(&m->a, L * N * H);
   galloc(&m->y, N);
   galloc(&m->dy, N);
-  galloc(&m->da1, N * H);
-  galloc(&m->da2, N * H);
+  galloc(&m->da0, N * H);
+  galloc(&m->da, L * N * H);
   galloc(&m->dm, N * H);
-  galloc(&m->dh1, N * H);
-  galloc(&m->part, nb * H * (K + 1));
+  galloc(&m->dhv, N * H);
+  galloc(&m->dh, N * H);
+  galloc(&m->part, L * nb * H * (K + 1));
   m->cap = n;
 }
 
@@ -543,11 +770,10 @@ void check_config(ibrd_gnn m, const double* q, int n, double lx, double ly, doub
     throw GnnArgError{IBRD_ERR_ARG, "cutoff above half the shortest box side"};
 }
 
-// Neighbour lists and the forward pass for one configuration.
-void forward(ibrd_gnn m, const double* q, int n, double lx, double ly, double lz) {
+// Neighbour lists of one configuration.
+void neighbour_lists(ibrd_gnn m, const double* q, int n, double lx, double ly, double lz) {
   ensure_cap(m, n);
   const int nb = (n + kWarps - 1) / kWarps;
-  const float invR = (float)(1.0 / m->cutoff);
   IBRD_CUDA(cudaMemsetAsync(m->oflow, 0, sizeof(int), m->s));
   prof_begin(P_SETUP, m->s);
   // FP32 screen margin: well above the FP32 error of a minimum-image distance
@@ -559,13 +785,46 @@ void forward(ibrd_gnn m, const double* q, int n, double lx, double ly, double lz
   k_gnn_neighbours<<<nb, kWarps * 32, 0, m->s>>>(q, m->p32, n, lx, ly, lz, m->cutoff, margin, m->kmax, m->cnt,
                                                  m->nidx, m->nr, m->oflow);
   prof_end(P_SETUP, m->s, "gnn_neighbours");
+}
+
+float* hbuf(ibrd_gnn m, int n, int l) { return m->h + (size_t)l * n * H; }
+float* lbuf(float* base, int n, int l) { return base + (size_t)(l - 1) * n * H; }  // l = 1 .. L
+
+// Neighbour lists and the FP32 forward pass (y in m->y); with bf16 the
+// layers' dense products run on the tensor cores instead.
+void forward(ibrd_gnn m, const double* q, int n, double lx, double ly, double lz, bool bf16 = false) {
+  neighbour_lists(m, q, n, lx, ly, lz);
+  const int nb = (n + kWarps - 1) / kWarps;
+  const float invR = (float)(1.0 / m->cutoff);
   prof_begin(P_SETUP, m->s);
-  k_gnn_layer1<<<nb, kWarps * 32, 0, m->s>>>(m->th, n, invR, m->kmax, m->cnt, m->nr, m->x, m->a1, m->h1);
-  prof_end(P_SETUP, m->s, "gnn_layer1");
+  k_gnn_layer0<<<nb, kWarps * 32, 0, m->s>>>(m->th, n, invR, m->kmax, m->cnt, m->nr, m->x, m->a0, hbuf(m, n, 0));
+  prof_end(P_SETUP, m->s, "gnn_layer0");
+  if (bf16) {
+    prof_begin(P_SETUP, m->s);
+    k_gnn_weights_bf16<<<(L * BLSZ + 255) / 256, 256, 0, m->s>>>(m->th, m->wb);
+    prof_end(P_SETUP, m->s, "gnn_weights_bf16");
+  }
+  for (int l = 1; l <= L; ++l) {
+    if (bf16) {
+      prof_begin(P_SETUP, m->s);
+      k_gnn_msg_tc<<<nb, kWarps * 32, 0, m->s>>>(m->th, m->wb, l, n, invR, m->kmax, m->cnt, m->nidx, m->nr,
+                                                 hbuf(m, n, l - 1), lbuf(m->m, n, l));
+      prof_end(P_SETUP, m->s, "gnn_msg_tc");
+      prof_begin(P_SETUP, m->s);
+      const int nt = (n + 16 * kNodeWarps - 1) / (16 * kNodeWarps);
+      k_gnn_node_tc<<<nt, kNodeWarps * 32, 0, m->s>>>(m->th, m->wb, l, n, lbuf(m->m, n, l), hbuf(m, n, l - 1),
+                                                      hbuf(m, n, l));
+      prof_end(P_SETUP, m->s, "gnn_node_tc");
+    } else {
+      prof_begin(P_SETUP, m->s);
+      k_gnn_mp<<<nb, kWarps * 32, 0, m->s>>>(m->th, l, n, invR, m->kmax, m->cnt, m->nidx, m->nr, hbuf(m, n, l - 1),
+                                             lbuf(m->m, n, l), lbuf(m->a, n, l), hbuf(m, n, l));
+      prof_end(P_SETUP, m->s, "gnn_mp");
+    }
+  }
   prof_begin(P_SETUP, m->s);
-  k_gnn_layer2<<<nb, kWarps * 32, 0, m->s>>>(m->th, n, invR, m->kmax, m->cnt, m->nidx, m->nr, m->h1, m->m, m->a2,
-                                             m->y);
-  prof_end(P_SETUP, m->s, "gnn_layer2");
+  k_gnn_out<<<nb, kWarps * 32, 0, m->s>>>(m->th, n, hbuf(m, n, L), m->y);
+  prof_end(P_SETUP, m->s, "gnn_out");
 }
 
 void check_overflow(ibrd_gnn m) {
@@ -575,23 +834,30 @@ void check_overflow(ibrd_gnn m) {
   if (of) throw GnnArgError{IBRD_ERR_ARG, "a blob has more neighbours than max_neighbours"};
 }
 
-// Loss and gradient of one configuration (after forward); gradient in m->g.
+// Loss and gradient of one configuration (after the FP32 forward); gradient
+// in m->g. Layers run in reverse: dh enters layer l (dy o at the last), its
+// node update gives da_l, dm and dhv, its messages the dh entering layer l - 1
+// (at the first, da0) and the filter partials.
 void backward(ibrd_gnn m, int n, const double* lam) {
   const int nb = (n + kWarps - 1) / kWarps;
   const float invR = (float)(1.0 / m->cutoff);
   prof_begin(P_SETUP, m->s);
   k_gnn_loss<<<1, 1024, 0, m->s>>>(m->y, lam, n, m->dy, m->loss);
   prof_end(P_SETUP, m->s, "gnn_loss");
+  for (int l = L; l >= 1; --l) {
+    prof_begin(P_SETUP, m->s);
+    k_gnn_back_node<<<nb, kWarps * 32, 0, m->s>>>(m->th, l, n, l == L ? nullptr : m->dh, m->dy, lbuf(m->a, n, l),
+                                                  lbuf(m->da, n, l), m->dm, m->dhv);
+    prof_end(P_SETUP, m->s, "gnn_back_node");
+    prof_begin(P_SETUP, m->s);
+    k_gnn_back_edges<<<nb, kWarps * 32, 0, m->s>>>(
+        m->th, l, n, invR, m->kmax, m->cnt, m->nidx, m->nr, hbuf(m, n, l - 1), m->dm, m->dhv,
+        l == 1 ? m->a0 : nullptr, l == 1 ? m->da0 : m->dh, m->part + (size_t)(l - 1) * nb * H * (K + 1));
+    prof_end(P_SETUP, m->s, "gnn_back_edges");
+  }
+  GradArgs ga{n, nb, m->x, m->da0, m->h, m->m, m->da, m->dy, m->part};
   prof_begin(P_SETUP, m->s);
-  k_gnn_back_node<<<nb, kWarps * 32, 0, m->s>>>(m->th, n, m->dy, m->a2, m->da2, m->dm, m->dh1);
-  prof_end(P_SETUP, m->s, "gnn_back_node");
-  prof_begin(P_SETUP, m->s);
-  k_gnn_back_edges<<<nb, kWarps * 32, 0, m->s>>>(m->th, n, invR, m->kmax, m->cnt, m->nidx, m->nr, m->h1, m->a1,
-                                                 m->dm, m->dh1, m->da1, m->part);
-  prof_end(P_SETUP, m->s, "gnn_back_edges");
-  prof_begin(P_SETUP, m->s);
-  k_gnn_param_grads<<<(NPARAM + 255) / 256, 256, 0, m->s>>>(n, nb, m->x, m->h1, m->m, m->a2, m->dy, m->da1,
-                                                            m->da2, m->part, m->g);
+  k_gnn_param_grads<<<(NPARAM + 255) / 256, 256, 0, m->s>>>(ga, m->g);
   prof_end(P_SETUP, m->s, "gnn_param_grads");
 }
 
@@ -637,6 +903,7 @@ ibrd_status ibrd_gnn_create(ibrd_gnn* out, double cutoff, int max_neighbours, vo
     galloc(&m->m2, NPARAM);
     galloc(&m->oflow, 1);
     galloc(&m->loss, 1);
+    galloc(&m->wb, L * BLSZ);
     IBRD_CUDA(cudaMallocHost(&m->host, sizeof(double) * 8));
     IBRD_CUDA(cudaMemsetAsync(m->th, 0, sizeof(float) * NPARAM, m->s));
     IBRD_CUDA(cudaMemsetAsync(m->m1, 0, sizeof(float) * NPARAM, m->s));
@@ -658,9 +925,9 @@ void ibrd_gnn_destroy(ibrd_gnn m) {
   cudaGetDevice(&prev);
   if (prev != m->dev) cudaSetDevice(m->dev);
   for (void* p : {(void*)m->th, (void*)m->g, (void*)m->m1, (void*)m->m2, (void*)m->cnt, (void*)m->nidx,
-                  (void*)m->oflow, (void*)m->nr, (void*)m->x, (void*)m->a1, (void*)m->h1, (void*)m->m,
-                  (void*)m->a2, (void*)m->y, (void*)m->dy, (void*)m->da1, (void*)m->da2, (void*)m->dm,
-                  (void*)m->dh1, (void*)m->part, (void*)m->loss, (void*)m->p32})
+                  (void*)m->oflow, (void*)m->nr, (void*)m->x, (void*)m->a0, (void*)m->h, (void*)m->m,
+                  (void*)m->a, (void*)m->y, (void*)m->dy, (void*)m->da0, (void*)m->da, (void*)m->dm,
+                  (void*)m->dhv, (void*)m->dh, (void*)m->part, (void*)m->loss, (void*)m->p32, (void*)m->wb})
     if (p) cudaFree(p);
   if (m->host) cudaFreeHost(m->host);
   if (prev >= 0 && prev != m->dev) cudaSetDevice(prev);
@@ -698,10 +965,12 @@ ibrd_status ibrd_gnn_init_params(ibrd_gnn m, unsigned long long seed) {
     auto fill = [&](int off, int count, double lim) {
       for (int k = 0; k < count; ++k) th[off + k] = (float)(lim * next());
     };
-    fill(OFF_W1, H * K, 1.0 / std::sqrt((double)K));
-    fill(OFF_E, H * K, 1.0 / std::sqrt((double)K));
-    fill(OFF_W2, H * H, 1.0 / std::sqrt((double)H));
-    fill(OFF_V2, H * H, 1.0 / std::sqrt((double)H));
+    fill(OFF_W0, H * K, 1.0 / std::sqrt((double)K));
+    for (int l = 1; l <= L; ++l) {
+      fill(offE(l), H * K, 1.0 / std::sqrt((double)K));
+      fill(offW(l), H * H, 1.0 / std::sqrt((double)H));
+      fill(offV(l), H * H, 1.0 / std::sqrt((double)H));
+    }
     fill(OFF_O, H, 1.0 / std::sqrt((double)H));
     IBRD_CUDA(cudaMemcpyAsync(m->th, th.data(), sizeof(float) * NPARAM, cudaMemcpyHostToDevice, m->s));
     IBRD_CUDA(cudaMemsetAsync(m->m1, 0, sizeof(float) * NPARAM, m->s));
@@ -726,7 +995,7 @@ ibrd_status ibrd_gnn_neighbours(ibrd_gnn m, const double* q, int n, double lx, d
   return gnn_guarded(m, "ibrd_gnn_neighbours", [&]() {
     check_config(m, q, n, lx, ly, lz);
     if (!count || !index || !dist) throw GnnArgError{IBRD_ERR_ARG, "null output"};
-    forward(m, q, n, lx, ly, lz);
+    neighbour_lists(m, q, n, lx, ly, lz);
     check_overflow(m);
     IBRD_CUDA(cudaMemcpyAsync(count, m->cnt, sizeof(int) * n, cudaMemcpyDeviceToDevice, m->s));
     IBRD_CUDA(cudaMemcpyAsync(index, m->nidx, sizeof(int) * (size_t)n * m->kmax, cudaMemcpyDeviceToDevice, m->s));
@@ -751,7 +1020,7 @@ ibrd_status ibrd_gnn_predict(ibrd_gnn m, const double* q, int n, double lx, doub
   return gnn_guarded(m, "ibrd_gnn_predict", [&]() {
     check_config(m, q, n, lx, ly, lz);
     if (!lambda0 || !std::isfinite(total)) throw GnnArgError{IBRD_ERR_ARG, "bad output or total"};
-    forward(m, q, n, lx, ly, lz);
+    forward(m, q, n, lx, ly, lz, /*bf16=*/true);
     prof_begin(P_SETUP, m->s);
     k_gnn_softmax<<<1, 1024, 0, m->s>>>(m->y, n, total, lambda0);
     prof_end(P_SETUP, m->s, "gnn_softmax");

@@ -1,7 +1,8 @@
 """The learned multiplier predictor's CUDA kernels against its FP64 definition
-(oracle/gnn.py), through the C ABI: neighbour sets exactly, the forward
-pass, loss and gradient within FP32 rounding, Adam's update, the softmax
-prediction, training, and its use as the warm start of a saddle solve."""
+(oracle/gnn.py), through the C ABI: neighbour sets exactly, the FP32 forward
+pass, loss and gradient within FP32 rounding, Adam's update, the bfloat16
+tensor-core prediction against the definition with bfloat16 operands,
+training, and its use as the warm start of a saddle solve."""
 import numpy as np
 import pytest
 
@@ -26,7 +27,7 @@ def _theta(seed):
     th = gnn.init_params(seed)
     p = gnn.unpack(th)
     rng = np.random.default_rng(seed + 100)
-    for k in ("c1", "e", "c2"):
+    for k in gnn.BIASES:
         p[k] = rng.uniform(-0.3, 0.3, size=p[k].shape)
     p["o0"] = np.array([0.2])
     # the FP32 model holds FP32 weights: give the reference the same values
@@ -82,10 +83,37 @@ def test_forward_loss_gradient_and_adam(ibrd):
     z = np.zeros_like(th)
     want, _, _ = gnn.adam_step(th, g.astype(np.float32).astype(np.float64), z, z, 1, 1e-3)
     assert np.abs(th1 - want).max() < 1e-6
-    # prediction: softmax of y scaled to the total
+    # prediction: softmax of y scaled to the total, on the tensor-core path
     lam0 = host(m.predict(qd, box, 123.0))
     assert abs(lam0.sum() - 123.0) < 1e-9 * 123.0
-    assert rel_err(lam0, gnn.predict(gnn.pack(gnn.unpack(th1)), q, box, R, 123.0)) < 1e-5
+    th1 = gnn.pack(gnn.unpack(th1))
+    assert rel_err(lam0, gnn.predict(th1, q, box, R, 123.0, bf16_products=True)) < 2e-4
+
+
+@pytest.mark.parametrize("n,side,R", [(500, 40, 10.0), (300, 48, 10.0), (37, 20, 9.5), (1, 24, 6.0)])
+def test_predict_bfloat16_tensor_cores(ibrd, n, side, R):
+    """The inference path (bfloat16 operands on mma.sync, FP32 accumulation)
+    against the definition with bfloat16-rounded operands and exact sums: 500
+    blobs have about 33 neighbours each (three 16-edge tiles, the last ragged),
+    and none of the blob counts fills whole 16-blob node tiles. It must also be
+    much closer to that definition than to the exact FP64 one, which it
+    differs from by bfloat16 rounding (about 1e-3 of lambda)."""
+    q, box = _config(n, side, 5)
+    th = _theta(7)
+    m = ibrd.GNN(R, 64)
+    m.set_params(th.astype(np.float32))
+    lam0 = host(m.predict(dev(q), box, 123.0))
+    want = gnn.predict(th, q, box, R, 123.0, bf16_products=True)
+    exact = gnn.predict(th, q, box, R, 123.0)
+    err = rel_err(lam0, want)
+    assert err < 2e-4, err
+    gap = rel_err(want, exact)
+    if gap > 1e-5:
+        assert err < 0.25 * gap, (err, gap)
+    # the FP32 forward of the same model stays on the exact definition
+    y = host(m.forward(dev(q), box)).astype(np.float64)
+    y_ref, _ = gnn.forward(th, q, box, R)
+    assert np.abs(y - y_ref).max() < 2e-5 * max(1.0, np.abs(y_ref).max())
 
 
 def test_too_many_neighbours_is_an_argument_error(ibrd):
@@ -159,7 +187,10 @@ def test_seeded_init(ibrd):
     c = m.get_params()
     assert np.array_equal(a, b) and not np.array_equal(a, c)
     p = gnn.unpack(a.astype(np.float64))
-    for name, lim in [("W1", 0.25), ("E", 0.25), ("W2", 0.125), ("V2", 0.125), ("o", 0.125)]:
+    lims = [("W0", 0.25), ("o", 0.125)]
+    for l in range(1, gnn.LAYERS + 1):
+        lims += [(f"E{l}", 0.25), (f"W{l}", 0.125), (f"V{l}", 0.125)]
+    for name, lim in lims:
         assert np.abs(p[name]).max() <= lim and np.abs(p[name]).max() > 0.9 * lim
-    for name in ("c1", "e", "c2", "o0"):
+    for name in gnn.BIASES + ["o0"]:
         assert not p[name].any()

@@ -19,14 +19,45 @@ def _theta(seed=1):
     # non-zero biases so that both sides of every relu are exercised
     p = gnn.unpack(th)
     rng = np.random.default_rng(seed + 100)
-    for k in ("c1", "e", "c2"):
+    for k in gnn.BIASES:
         p[k] = rng.uniform(-0.3, 0.3, size=p[k].shape)
     p["o0"] = np.array([0.2])
     return gnn.pack(p)
 
 
 def test_layout_size():
-    assert gnn.n_params() == 64 * 16 * 2 + 64 * 64 * 2 + 64 * 4 + 1
+    # embedding, three layers (filter E, e; W, V, c), output
+    assert gnn.n_params() == (64 * 16 + 64) + 3 * (64 * 16 + 64 + 2 * 64 * 64 + 64) + 64 + 1
+
+
+def test_bf16_rounding_matches_torch():
+    """The oracle's bfloat16 rounding (nearest, ties to even, of the FP32
+    value) against torch's float32 -> bfloat16 conversion."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(12)
+    v = np.concatenate([rng.standard_normal(4000) * 10.0 ** rng.integers(-6, 6, 4000),
+                        [1.0, 1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -9, -0.0, 2.0 ** -130]])
+    want = torch.from_numpy(v.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(gnn.bf16(v), want)
+
+
+def test_bf16_forward_is_close_and_exact_on_representable_values():
+    """Inference with bfloat16 operands stays within a few bfloat16 ulps of
+    the exact forward, and equals it when every weight is representable and
+    the inputs of each product happen to be too (a zero-layer check: with all
+    layer weights zero only biases and the exact embedding act)."""
+    q, box = _config()
+    th = _theta()
+    y, _ = gnn.forward(th, q, box, 8.0)
+    yb, _ = gnn.forward(th, q, box, 8.0, bf16_products=True)
+    assert not np.array_equal(y, yb)
+    assert np.abs(y - yb).max() < 3 * 2.0 ** -8 * (np.abs(y).max() + 1.0)
+    p = gnn.unpack(th)
+    for l in range(1, gnn.LAYERS + 1):
+        for k in ("E", "W", "V"):
+            p[f"{k}{l}"] = np.zeros_like(p[f"{k}{l}"])
+    t0 = gnn.pack(p)
+    assert np.array_equal(gnn.forward(t0, q, box, 8.0)[0], gnn.forward(t0, q, box, 8.0, bf16_products=True)[0])
 
 
 def test_neighbours_match_kdtree():
