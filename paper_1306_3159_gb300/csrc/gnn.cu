@@ -80,21 +80,57 @@ __device__ __forceinline__ double min_image_dist(const double* q, int i, int j, 
   return sqrt(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
 }
 
-// FP32 copies of the positions (x, y, z, 0) for the neighbour screen.
-__global__ void k_gnn_pos32(const double* __restrict__ q, int n, float4* __restrict__ p) {
+// FP32 copies of the positions (x, y, z, 0) for the neighbour screen, each
+// coordinate first brought into the box (about [0, L): the screen takes the
+// minimum image anyway), so that its FP32 rounding is a few ulps of L.
+__global__ void k_gnn_pos32(const double* __restrict__ q, int n, double lx, double ly, double lz,
+                            float4* __restrict__ p) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < n) p[j] = make_float4((float)q[3 * j], (float)q[3 * j + 1], (float)q[3 * j + 2], 0.f);
+  if (j >= n) return;
+  const double x = q[3 * j], y = q[3 * j + 1], z = q[3 * j + 2];
+  p[j] = make_float4((float)(x - lx * floor(x * (1.0 / lx))), (float)(y - ly * floor(y * (1.0 / ly))),
+                     (float)(z - lz * floor(z * (1.0 / lz))), 0.f);
 }
 
 constexpr int kNbTile = 1024;  // positions staged in shared memory per pass
 
+// One candidate pair of the neighbour test: FP32 minimum-image distance
+// first; only pairs within a margin of R take the exact FP64 test, so the
+// neighbour sets are the FP64 definition's, and a stored distance is the FP32
+// one (within a few ulps of the box side) away from the boundary.
+struct PairScreen {
+  float flx, fly, flz, ilx, ily, ilz, rs2, ri2;
+  double lx, ly, lz, R;
+  __device__ PairScreen(double lx_, double ly_, double lz_, double R_, float margin)
+      : lx(lx_), ly(ly_), lz(lz_), R(R_) {
+    flx = (float)lx;
+    fly = (float)ly;
+    flz = (float)lz;
+    ilx = 1.f / flx;
+    ily = 1.f / fly;
+    ilz = 1.f / flz;
+    const float rs = (float)R + margin, ri = (float)R - margin;
+    rs2 = rs * rs;
+    ri2 = ri > 0.f ? ri * ri : 0.f;
+  }
+  // the distance of a neighbour pair, -1 for any other
+  __device__ __forceinline__ float dist(const double* q, int i, int j, float4 pi, float4 pj) const {
+    float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
+    dx -= flx * rintf(dx * ilx);
+    dy -= fly * rintf(dy * ily);
+    dz -= flz * rintf(dz * ilz);
+    const float d2 = dx * dx + dy * dy + dz * dz;
+    if (!(d2 < rs2)) return -1.f;
+    if (d2 < ri2) return sqrtf(d2);  // clearly inside: the FP32 distance is kept
+    const double r = min_image_dist(q, i, j, lx, ly, lz);  // within the margin of R
+    return r < R ? (float)r : -1.f;
+  }
+};
+
 // Neighbours j != i with r_ij < R, in increasing j; count clipped to kmax,
-// *overflow set when a list was clipped. FP64 is slow on this GPU, so every
-// pair is measured in FP32 and only pairs within a margin of R (the margin far
-// above the FP32 rounding of the coordinates) take the exact FP64 test: the
-// neighbour sets are the FP64 definition's; a stored distance is the FP32 one
-// (within a few ulps of the box side) away from the boundary. The CTA's 8 blobs
-// scan tiles of FP32 positions staged in shared memory.
+// *overflow set when a list was clipped. All pairs: the CTA's 8 blobs scan
+// tiles of FP32 positions staged in shared memory. Used when the box holds
+// fewer than 3 cells of side R along an axis.
 __global__ void __launch_bounds__(kWarps * 32) k_gnn_neighbours(const double* __restrict__ q,
                                                                 const float4* __restrict__ p32, int n, double lx,
                                                                 double ly, double lz, double R, float margin,
@@ -106,10 +142,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_gnn_neighbours(const double* __
   const int i = blockIdx.x * kWarps + (threadIdx.x >> 5);
   const bool active = i < n;
   const float4 pi = active ? p32[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-  const float flx = (float)lx, fly = (float)ly, flz = (float)lz;
-  const float ilx = 1.f / flx, ily = 1.f / fly, ilz = 1.f / flz;
-  const float rs = (float)R + margin, rs2 = rs * rs;
-  const float ri = (float)R - margin, ri2 = ri > 0.f ? ri * ri : 0.f;
+  const PairScreen ps(lx, ly, lz, R, margin);
   int c = 0;
   for (int t0 = 0; t0 < n; t0 += kNbTile) {
     const int tn = min(kNbTile, n - t0);
@@ -120,32 +153,13 @@ __global__ void __launch_bounds__(kWarps * 32) k_gnn_neighbours(const double* __
     for (int j0 = 0; j0 < tn; j0 += 32) {
       const int jl = j0 + lane;
       const int j = t0 + jl;
-      double r = 0.0;
-      bool in = false;
-      if (jl < tn && j != i) {
-        const float4 pj = tile[jl];
-        float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
-        dx -= flx * rintf(dx * ilx);
-        dy -= fly * rintf(dy * ily);
-        dz -= flz * rintf(dz * ilz);
-        const float d2 = dx * dx + dy * dy + dz * dz;
-        if (d2 < rs2) {
-          if (d2 < ri2) {
-            // clearly inside: the FP32 distance is kept
-            r = (double)sqrtf(d2);
-            in = true;
-          } else {
-            // within the margin of R: the exact FP64 test decides
-            r = min_image_dist(q, i, j, lx, ly, lz);
-            in = r < R;
-          }
-        }
-      }
+      const float r = jl < tn && j != i ? ps.dist(q, i, j, pi, tile[jl]) : -1.f;
+      const bool in = r >= 0.f;
       const unsigned bal = __ballot_sync(0xffffffffu, in);
       const int slot = c + __popc(bal & ((1u << lane) - 1u));
       if (in && slot < kmax) {
         nidx[(size_t)i * kmax + slot] = j;
-        nr[(size_t)i * kmax + slot] = (float)r;
+        nr[(size_t)i * kmax + slot] = r;
       }
       c += __popc(bal);
     }
@@ -156,24 +170,195 @@ __global__ void __launch_bounds__(kWarps * 32) k_gnn_neighbours(const double* __
   }
 }
 
-// x_i, a0_i = W0 x_i + c0, h0_i = relu(a0_i).
+// Cell list: the box split into ncx x ncy x ncz cells (3 to 32 per axis,
+// each side at least R), every blob in the cell of its wrapped position; a
+// pair closer than R then lies in the same or adjacent cells (periodically).
+struct Cells {
+  int nx, ny, nz;
+  double lx, ly, lz;
+  __device__ __forceinline__ int axis(double x, double L, int nc) const {
+    double f = x / L;
+    f -= floor(f);
+    const int c = (int)(f * nc);
+    return c < 0 ? 0 : (c < nc ? c : nc - 1);
+  }
+  __device__ __forceinline__ void of(const double* q, int j, int& cx, int& cy, int& cz) const {
+    cx = axis(q[3 * j], lx, nx);
+    cy = axis(q[3 * j + 1], ly, ny);
+    cz = axis(q[3 * j + 2], lz, nz);
+  }
+};
+
+__global__ void k_gnn_cell_count(const double* __restrict__ q, int n, Cells cl, int* __restrict__ cell_of,
+                                 int* __restrict__ cell_cnt) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  int cx, cy, cz;
+  cl.of(q, j, cx, cy, cz);
+  const int c = (cz * cl.ny + cy) * cl.nx + cx;
+  cell_of[j] = c;
+  atomicAdd(&cell_cnt[c], 1);
+}
+
+// Exclusive scan of the cell counts (one CTA): start[c], start[ncell] = n;
+// cursor[c] = start[c] for the fill.
+__global__ void __launch_bounds__(1024) k_gnn_cell_scan(const int* __restrict__ cell_cnt, int ncell,
+                                                        int* __restrict__ start, int* __restrict__ cursor) {
+  __shared__ int part[1024];
+  const int per = (ncell + 1023) / 1024;
+  const int b = threadIdx.x * per, e = min(ncell, b + per);
+  int sum = 0;
+  for (int c = b; c < e; ++c) sum += cell_cnt[c];
+  part[threadIdx.x] = sum;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    const int v = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int run = part[threadIdx.x] - sum;
+  for (int c = b; c < e; ++c) {
+    start[c] = run;
+    cursor[c] = run;
+    run += cell_cnt[c];
+  }
+  if (threadIdx.x == 1023) start[ncell] = part[1023];
+}
+
+__global__ void k_gnn_cell_fill(int n, const int* __restrict__ cell_of, int* __restrict__ cursor,
+                                int* __restrict__ cell_blobs) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) cell_blobs[atomicAdd(&cursor[cell_of[j]], 1)] = j;
+}
+
+// Neighbours from the cell list, one CTA per cell: the candidates of its 27
+// surrounding cells (distinct, as every axis has at least 3) are staged in
+// shared memory, up to kNbTile at a time, as (x, y, z, index), and its blobs
+// screen them one warp each. A blob's neighbours are collected in scratch
+// lists (tj, tr) in staging order, then placed in increasing j by their rank
+// (the j are distinct).
+__global__ void __launch_bounds__(kWarps * 32) k_gnn_neighbours_cells(
+    const double* __restrict__ q, const float4* __restrict__ p32, Cells cl, double R, float margin,
+    const int* __restrict__ start, const int* __restrict__ cell_blobs, int kmax, int* __restrict__ tj,
+    float* __restrict__ tr, int* __restrict__ cnt, int* __restrict__ nidx, float* __restrict__ nr,
+    int* __restrict__ overflow) {
+  __shared__ float4 tile[kNbTile];
+  __shared__ int nb_cell[27], pre[28];
+  const int cell = blockIdx.x;
+  const int cb = start[cell], nown = start[cell + 1] - cb;
+  if (nown == 0) return;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (threadIdx.x < 27) {
+    const int cx = cell % cl.nx, cy = (cell / cl.nx) % cl.ny, cz = cell / (cl.nx * cl.ny);
+    const int t = threadIdx.x;
+    int x = cx + t % 3 - 1, y = cy + (t / 3) % 3 - 1, z = cz + t / 9 - 1;
+    x = x < 0 ? cl.nx - 1 : (x == cl.nx ? 0 : x);
+    y = y < 0 ? cl.ny - 1 : (y == cl.ny ? 0 : y);
+    z = z < 0 ? cl.nz - 1 : (z == cl.nz ? 0 : z);
+    nb_cell[t] = (z * cl.ny + y) * cl.nx + x;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int run = 0;
+    for (int t = 0; t < 27; ++t) {
+      pre[t] = run;
+      run += start[nb_cell[t] + 1] - start[nb_cell[t]];
+    }
+    pre[27] = run;
+  }
+  __syncthreads();
+  const int T = pre[27];
+  const PairScreen ps(cl.lx, cl.ly, cl.lz, R, margin);
+  for (int g0 = 0; g0 < nown; g0 += kWarps) {
+    const int i = g0 + w < nown ? cell_blobs[cb + g0 + w] : -1;
+    const float4 pi = i >= 0 ? p32[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    int* li = tj + (size_t)(i >= 0 ? i : 0) * kmax;
+    float* lr = tr + (size_t)(i >= 0 ? i : 0) * kmax;
+    int c = 0;
+    for (int t0 = 0; t0 < T; t0 += kNbTile) {
+      const int tn = min(kNbTile, T - t0);
+      if (g0 == 0 || T > kNbTile) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < tn; t += blockDim.x) {
+          const int u = t0 + t;
+          int k = 0;
+          while (pre[k + 1] <= u) ++k;
+          const int j = cell_blobs[start[nb_cell[k]] + u - pre[k]];
+          const float4 pj = p32[j];
+          tile[t] = make_float4(pj.x, pj.y, pj.z, __int_as_float(j));
+        }
+        __syncthreads();
+      }
+      if (i < 0) continue;
+      for (int j0 = 0; j0 < tn; j0 += 32) {
+        const int jl = j0 + lane;
+        const float4 pj = jl < tn ? tile[jl] : make_float4(0.f, 0.f, 0.f, __int_as_float(i));
+        const int j = __float_as_int(pj.w);
+        const float r = j != i ? ps.dist(q, i, j, pi, pj) : -1.f;
+        const bool in = r >= 0.f;
+        const unsigned bal = __ballot_sync(0xffffffffu, in);
+        const int slot = c + __popc(bal & ((1u << lane) - 1u));
+        if (in && slot < kmax) {
+          li[slot] = j;
+          lr[slot] = r;
+        }
+        c += __popc(bal);
+      }
+    }
+    if (i < 0) continue;
+    const int cc = c < kmax ? c : kmax;
+    __syncwarp();
+    for (int e = lane; e < cc; e += 32) {
+      const int je = li[e];
+      int rank = 0;
+      for (int f = 0; f < cc; ++f) rank += li[f] < je;
+      nidx[(size_t)i * kmax + rank] = je;
+      nr[(size_t)i * kmax + rank] = lr[e];
+    }
+    if (lane == 0) {
+      cnt[i] = cc;
+      if (c > kmax) atomicOr(overflow, 1);
+    }
+  }
+}
+
+// x_i, a0_i = W0 x_i + c0, h0_i = relu(a0_i). The lanes take the edges in
+// turn (all K bases of each), then the warp adds its lanes' partial sums.
 __global__ void __launch_bounds__(kWarps * 32) k_gnn_layer0(const float* __restrict__ th, int n, float invR,
                                                             int kmax, const int* __restrict__ cnt,
                                                             const float* __restrict__ nr, float* __restrict__ x,
                                                             float* __restrict__ a0, float* __restrict__ h0) {
+  __shared__ float sW0[H * (K + 1)];
+  for (int t = threadIdx.x; t < H * K; t += blockDim.x) sW0[(t / K) * (K + 1) + t % K] = th[OFF_W0 + t];
+  __syncthreads();
   const int lane = threadIdx.x & 31;
   const int i = blockIdx.x * kWarps + (threadIdx.x >> 5);
   if (i >= n) return;
-  const int k = lane & (K - 1);
-  float xk = 0.f;
+  float xk[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) xk[k] = 0.f;
   const int c = cnt[i];
-  for (int e = 0; e < c; ++e) xk += basis_k(nr[(size_t)i * kmax + e] * invR, k);
-  if (lane < K) x[(size_t)i * K + lane] = xk;
+  for (int e = lane; e < c; e += 32) {
+    const float s = nr[(size_t)i * kmax + e] * invR;
+#pragma unroll
+    for (int k = 0; k < K; ++k) xk[k] += basis_k(s, k);
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+    for (int o = 16; o > 0; o >>= 1) xk[k] += __shfl_xor_sync(0xffffffffu, xk[k], o);
+  if (lane < K) {
+    float v = 0.f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) v = lane == k ? xk[k] : v;
+    x[(size_t)i * K + lane] = v;
+  }
 #pragma unroll
   for (int half = 0; half < 2; ++half) {
     const int row = lane + 32 * half;
     float a = th[OFF_C0 + row];
-    for (int kk = 0; kk < K; ++kk) a = fmaf(th[OFF_W0 + row * K + kk], __shfl_sync(0xffffffffu, xk, kk), a);
+#pragma unroll
+    for (int kk = 0; kk < K; ++kk) a = fmaf(sW0[row * (K + 1) + kk], xk[kk], a);
     a0[(size_t)i * H + row] = a;
     h0[(size_t)i * H + row] = fmaxf(a, 0.f);
   }
@@ -264,34 +449,48 @@ __device__ double block_sum(double v, double* sh) {
   return r;
 }
 
+// log v for v > 0 (FP64 in, FP64 out) with one FP32 logarithm: v = f 2^e,
+// f in [0.5, 1), log v = log f + e log 2; absolute error about 1e-7, far below
+// the spread of the log-multipliers the loss compares.
+__device__ __forceinline__ double log_pos(double v) {
+  int e;
+  const double f = frexp(v, &e);
+  return (double)logf((float)f) + (double)e * 0.69314718055994530942;
+}
+
 // Loss of one configuration and dL/dy (one CTA): r = (y - <y>) - (t - <t>),
 // L = <r^2>, dy = 2 r / n. out[0] = L.
 __global__ void __launch_bounds__(1024) k_gnn_loss(const float* __restrict__ y, const double* __restrict__ lam,
                                                    int n, float* __restrict__ dy, double* __restrict__ out) {
   __shared__ double sh[32];
   double sy = 0.0, st = 0.0;
+#pragma unroll 4
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     sy += (double)y[i];
-    st += log(lam[i]);
+    st += log_pos(lam[i]);
   }
-  const double my = block_sum(sy, sh) / n;
-  const double mt = block_sum(st, sh) / n;
+  const double inv_n = 1.0 / n;
+  const double my = block_sum(sy, sh) * inv_n;
+  const double mt = block_sum(st, sh) * inv_n;
   double l2 = 0.0;
+#pragma unroll 4
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const double r = ((double)y[i] - my) - (log(lam[i]) - mt);
-    dy[i] = (float)(2.0 * r / n);
+    const double r = ((double)y[i] - my) - (log_pos(lam[i]) - mt);
+    dy[i] = (float)(2.0 * inv_n * r);
     l2 += r * r;
   }
-  const double L = block_sum(l2, sh) / n;
+  const double L = block_sum(l2, sh) * inv_n;
   if (threadIdx.x == 0) out[0] = L;
 }
 
-// lambda0_i = total * exp(y_i - max y) / sum_k exp(y_k - max y) (one CTA).
+// lambda0_i = total * exp(y_i - max y) / sum_k exp(y_k - max y) (one CTA;
+// the exponentials of the FP32 outputs in FP32, their sum in FP64).
 __global__ void __launch_bounds__(1024) k_gnn_softmax(const float* __restrict__ y, int n, double total,
                                                       double* __restrict__ lam0) {
   __shared__ double sh[32];
   __shared__ float smax[32];
   float mx = -INFINITY;
+#pragma unroll 4
   for (int i = threadIdx.x; i < n; i += blockDim.x) mx = fmaxf(mx, y[i]);
   for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = mx;
@@ -302,11 +501,13 @@ __global__ void __launch_bounds__(1024) k_gnn_softmax(const float* __restrict__ 
     smax[0] = t;
   }
   __syncthreads();
-  const double ymax = (double)smax[0];
+  const float ymax = smax[0];
   double s = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) s += exp((double)y[i] - ymax);
-  const double S = block_sum(s, sh);
-  for (int i = threadIdx.x; i < n; i += blockDim.x) lam0[i] = total * exp((double)y[i] - ymax) / S;
+#pragma unroll 4
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += (double)expf(y[i] - ymax);
+  const double scale = total / block_sum(s, sh);
+#pragma unroll 4
+  for (int i = threadIdx.x; i < n; i += blockDim.x) lam0[i] = scale * (double)expf(y[i] - ymax);
 }
 
 // Backward through layer l's node update: dh = dh_in (or dy o at the last
@@ -526,54 +727,72 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], 
 // g, g + 8 and columns 2t, 2t + 1, 2t + 8, 2t + 9; B at rows 2t, 2t + 1,
 // 2t + 8, 2t + 9 and column g; D at rows g, g + 8 and columns 2t, 2t + 1.
 // Each lane then sums relu(P + e) f_c hp_j over its two edge rows, and the
-// eight lanes of a column pair add theirs.
-__global__ void __launch_bounds__(kWarps * 32) k_gnn_msg_tc(const float* __restrict__ th,
-                                                            const __nv_bfloat16* __restrict__ wb, int l, int n,
-                                                            float invR, int kmax, const int* __restrict__ cnt,
-                                                            const int* __restrict__ nidx,
-                                                            const float* __restrict__ nr,
-                                                            const float* __restrict__ hp, float* __restrict__ m) {
+// eight lanes of a column pair add theirs. The gathers are latency-bound:
+// each tile issues all of its neighbour rows' loads before any arithmetic,
+// and the next tile's indices are fetched before the current one's products.
+__global__ void __launch_bounds__(kWarps * 32, 3) k_gnn_msg_tc(const float* __restrict__ th,
+                                                               const __nv_bfloat16* __restrict__ wb, int l, int n,
+                                                               float invR, int kmax, const int* __restrict__ cnt,
+                                                               const int* __restrict__ nidx,
+                                                               const float* __restrict__ nr,
+                                                               const float* __restrict__ hp, float* __restrict__ m) {
+  static_assert(kWarps == 8, "one warp per column tile fills the staged fragments");
+  __shared__ unsigned sB[8][2][32];  // per column tile, the two B registers of each lane
+  __shared__ float2 sBias[8][4];     // per column tile, e_l at columns 2t, 2t + 1
+  {
+    const __nv_bfloat16* E = wb + (size_t)(l - 1) * BLSZ;
+    const int nt = threadIdx.x >> 5, ln = threadIdx.x & 31;
+    const int col = 8 * nt + (ln >> 2), t2 = 2 * (ln & 3);  // B column = filter output
+    sB[nt][0][ln] = *reinterpret_cast<const unsigned*>(E + col * K + t2);
+    sB[nt][1][ln] = *reinterpret_cast<const unsigned*>(E + col * K + t2 + 8);
+    if (threadIdx.x < 32) {
+      const float* eb = th + offEB(l);
+      sBias[threadIdx.x >> 2][threadIdx.x & 3] =
+          make_float2(eb[8 * (threadIdx.x >> 2) + 2 * (threadIdx.x & 3)],
+                      eb[8 * (threadIdx.x >> 2) + 2 * (threadIdx.x & 3) + 1]);
+    }
+  }
+  __syncthreads();
   const int lane = threadIdx.x & 31;
   const int i = blockIdx.x * kWarps + (threadIdx.x >> 5);
   if (i >= n) return;
   const int g = lane >> 2, t = lane & 3;
-  const __nv_bfloat16* E = wb + (size_t)(l - 1) * BLSZ;
-  const float* eb = th + offEB(l);
-  unsigned b0[8], b1[8];
-  float2 bias[8];
-#pragma unroll
-  for (int nt = 0; nt < 8; ++nt) {
-    const int col = 8 * nt + g;  // B column = filter output
-    b0[nt] = *reinterpret_cast<const unsigned*>(E + col * K + 2 * t);
-    b1[nt] = *reinterpret_cast<const unsigned*>(E + col * K + 2 * t + 8);
-    bias[nt] = make_float2(eb[8 * nt + 2 * t], eb[8 * nt + 2 * t + 1]);
-  }
   float acc[8][2];
 #pragma unroll
   for (int nt = 0; nt < 8; ++nt) acc[nt][0] = acc[nt][1] = 0.f;
   const int c = cnt[i];
+  const int* ni = nidx + (size_t)i * kmax;
+  const float* ri = nr + (size_t)i * kmax;
+  // edge rows g and g + 8 of a tile; s = 1 (no edge): every basis and the
+  // cutoff vanish, and row 0 of hp stands in for the neighbour
+  int j0 = g < c ? ni[g] : 0, j1 = g + 8 < c ? ni[g + 8] : 0;
+  float s0 = g < c ? ri[g] * invR : 1.f, s1 = g + 8 < c ? ri[g + 8] * invR : 1.f;
   for (int e0 = 0; e0 < c; e0 += 16) {
-    const int r0 = e0 + g, r1 = e0 + g + 8;
-    const bool v0 = r0 < c, v1 = r1 < c;
-    const float s0 = v0 ? nr[(size_t)i * kmax + r0] * invR : 1.f;
-    const float s1 = v1 ? nr[(size_t)i * kmax + r1] * invR : 1.f;
-    const int j0 = v0 ? nidx[(size_t)i * kmax + r0] : 0, j1 = v1 ? nidx[(size_t)i * kmax + r1] : 0;
-    // s = 1 (no edge): every basis and the cutoff vanish
+    float2 h0[8], h1[8];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      h0[nt] = *reinterpret_cast<const float2*>(hp + (size_t)j0 * H + 8 * nt + 2 * t);
+      h1[nt] = *reinterpret_cast<const float2*>(hp + (size_t)j1 * H + 8 * nt + 2 * t);
+    }
+    const float cs0 = s0, cs1 = s1;
+    const int r0 = e0 + 16 + g, r1 = e0 + 24 + g;
+    j0 = r0 < c ? ni[r0] : 0;
+    j1 = r1 < c ? ni[r1] : 0;
+    s0 = r0 < c ? ri[r0] * invR : 1.f;
+    s1 = r1 < c ? ri[r1] * invR : 1.f;
     unsigned a[4];
-    a[0] = bf16x2(basis_k(s0, 2 * t), basis_k(s0, 2 * t + 1));
-    a[1] = bf16x2(basis_k(s1, 2 * t), basis_k(s1, 2 * t + 1));
-    a[2] = bf16x2(basis_k(s0, 2 * t + 8), basis_k(s0, 2 * t + 9));
-    a[3] = bf16x2(basis_k(s1, 2 * t + 8), basis_k(s1, 2 * t + 9));
-    const float fc0 = (1.f - s0) * (1.f - s0), fc1 = (1.f - s1) * (1.f - s1);
+    a[0] = bf16x2(basis_k(cs0, 2 * t), basis_k(cs0, 2 * t + 1));
+    a[1] = bf16x2(basis_k(cs1, 2 * t), basis_k(cs1, 2 * t + 1));
+    a[2] = bf16x2(basis_k(cs0, 2 * t + 8), basis_k(cs0, 2 * t + 9));
+    a[3] = bf16x2(basis_k(cs1, 2 * t + 8), basis_k(cs1, 2 * t + 9));
+    const float fc0 = (1.f - cs0) * (1.f - cs0), fc1 = (1.f - cs1) * (1.f - cs1);
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {
       float d[4] = {0.f, 0.f, 0.f, 0.f};
-      mma_bf16(d, a, b0[nt], b1[nt]);
-      const int col = 8 * nt + 2 * t;
-      const float2 h0 = *reinterpret_cast<const float2*>(hp + (size_t)j0 * H + col);
-      const float2 h1 = *reinterpret_cast<const float2*>(hp + (size_t)j1 * H + col);
-      acc[nt][0] += fc0 * fmaxf(d[0] + bias[nt].x, 0.f) * h0.x + fc1 * fmaxf(d[2] + bias[nt].x, 0.f) * h1.x;
-      acc[nt][1] += fc0 * fmaxf(d[1] + bias[nt].y, 0.f) * h0.y + fc1 * fmaxf(d[3] + bias[nt].y, 0.f) * h1.y;
+      mma_bf16(d, a, sB[nt][0][lane], sB[nt][1][lane]);
+      const float2 bias = sBias[nt][t];
+      acc[nt][0] += fc0 * fmaxf(d[0] + bias.x, 0.f) * h0[nt].x + fc1 * fmaxf(d[2] + bias.x, 0.f) * h1[nt].x;
+      acc[nt][1] += fc0 * fmaxf(d[1] + bias.y, 0.f) * h0[nt].y + fc1 * fmaxf(d[3] + bias.y, 0.f) * h1[nt].y;
     }
   }
 #pragma unroll
@@ -694,6 +913,12 @@ struct ibrd_gnn_s {
   float *dy = nullptr, *da0 = nullptr, *da = nullptr, *dm = nullptr, *dhv = nullptr, *dh = nullptr;
   float* part = nullptr;
   __nv_bfloat16* wb = nullptr;  // bfloat16 layer weights for inference
+  // cell list (grow only): per blob its cell, the blobs sorted by cell, the
+  // scratch candidate lists; per cell its count, start and fill cursor
+  int *cell_of = nullptr, *cell_blobs = nullptr, *tj = nullptr;
+  float* tr = nullptr;
+  int cell_cap = 0;
+  int *cell_cnt = nullptr, *cell_start = nullptr, *cell_cursor = nullptr;
   double* loss = nullptr;  // device scalar
   double* host = nullptr;  // pinned
   std::string err;
@@ -759,6 +984,10 @@ void ensure_cap(ibrd_gnn m, int n) {
   galloc(&m->dhv, N * H);
   galloc(&m->dh, N * H);
   galloc(&m->part, L * nb * H * (K + 1));
+  galloc(&m->cell_of, N);
+  galloc(&m->cell_blobs, N);
+  galloc(&m->tj, N * m->kmax);
+  galloc(&m->tr, N * m->kmax);
   m->cap = n;
 }
 
@@ -770,21 +999,57 @@ void check_config(ibrd_gnn m, const double* q, int n, double lx, double ly, doub
     throw GnnArgError{IBRD_ERR_ARG, "cutoff above half the shortest box side"};
 }
 
-// Neighbour lists of one configuration.
+// Cells per axis for the cell list: each side at least R (with room for
+// rounding), at most 32; 0 when fewer than 3 fit.
+int cells_per_axis(double L, double R) {
+  const double c = std::floor(L / (R * (1.0 + 1e-6)));
+  return c < 3.0 ? 0 : (int)std::min(c, 32.0);
+}
+
+// Neighbour lists of one configuration: from a cell list when every axis
+// holds at least 3 cells of side R, else all pairs.
 void neighbour_lists(ibrd_gnn m, const double* q, int n, double lx, double ly, double lz) {
   ensure_cap(m, n);
   const int nb = (n + kWarps - 1) / kWarps;
   IBRD_CUDA(cudaMemsetAsync(m->oflow, 0, sizeof(int), m->s));
   prof_begin(P_SETUP, m->s);
-  // FP32 screen margin: well above the FP32 error of a minimum-image distance
-  // (a few ulps of the box side)
-  const float margin = (float)(1e-3 * m->cutoff + 1e-5 * std::max(lx, std::max(ly, lz)));
-  k_gnn_pos32<<<(n + 255) / 256, 256, 0, m->s>>>(q, n, m->p32);
+  // FP32 screen margin: the wrapped FP32 coordinates carry half an ulp of the
+  // box side each (6e-8 L), a minimum-image difference a few ulps, the
+  // distance under 1e-6 L with its own rounding; the margin is ten times that
+  const float margin = (float)(1e-5 * std::max(lx, std::max(ly, lz)) + 1e-6 * m->cutoff);
+  k_gnn_pos32<<<(n + 255) / 256, 256, 0, m->s>>>(q, n, lx, ly, lz, m->p32);
   prof_end(P_SETUP, m->s, "gnn_pos32");
-  prof_begin(P_SETUP, m->s);
-  k_gnn_neighbours<<<nb, kWarps * 32, 0, m->s>>>(q, m->p32, n, lx, ly, lz, m->cutoff, margin, m->kmax, m->cnt,
-                                                 m->nidx, m->nr, m->oflow);
-  prof_end(P_SETUP, m->s, "gnn_neighbours");
+  Cells cl{cells_per_axis(lx, m->cutoff), cells_per_axis(ly, m->cutoff), cells_per_axis(lz, m->cutoff), lx, ly,
+           lz};
+  if (cl.nx && cl.ny && cl.nz) {
+    const int ncell = cl.nx * cl.ny * cl.nz;
+    if (ncell > m->cell_cap) {
+      galloc(&m->cell_cnt, ncell);
+      galloc(&m->cell_start, ncell + 1);
+      galloc(&m->cell_cursor, ncell);
+      m->cell_cap = ncell;
+    }
+    IBRD_CUDA(cudaMemsetAsync(m->cell_cnt, 0, sizeof(int) * ncell, m->s));
+    prof_begin(P_SETUP, m->s);
+    k_gnn_cell_count<<<(n + 255) / 256, 256, 0, m->s>>>(q, n, cl, m->cell_of, m->cell_cnt);
+    prof_end(P_SETUP, m->s, "gnn_cell_count");
+    prof_begin(P_SETUP, m->s);
+    k_gnn_cell_scan<<<1, 1024, 0, m->s>>>(m->cell_cnt, ncell, m->cell_start, m->cell_cursor);
+    prof_end(P_SETUP, m->s, "gnn_cell_scan");
+    prof_begin(P_SETUP, m->s);
+    k_gnn_cell_fill<<<(n + 255) / 256, 256, 0, m->s>>>(n, m->cell_of, m->cell_cursor, m->cell_blobs);
+    prof_end(P_SETUP, m->s, "gnn_cell_fill");
+    prof_begin(P_SETUP, m->s);
+    k_gnn_neighbours_cells<<<ncell, kWarps * 32, 0, m->s>>>(q, m->p32, cl, m->cutoff, margin, m->cell_start,
+                                                            m->cell_blobs, m->kmax, m->tj, m->tr, m->cnt,
+                                                            m->nidx, m->nr, m->oflow);
+    prof_end(P_SETUP, m->s, "gnn_neighbours_cells");
+  } else {
+    prof_begin(P_SETUP, m->s);
+    k_gnn_neighbours<<<nb, kWarps * 32, 0, m->s>>>(q, m->p32, n, lx, ly, lz, m->cutoff, margin, m->kmax, m->cnt,
+                                                   m->nidx, m->nr, m->oflow);
+    prof_end(P_SETUP, m->s, "gnn_neighbours");
+  }
 }
 
 float* hbuf(ibrd_gnn m, int n, int l) { return m->h + (size_t)l * n * H; }
@@ -927,7 +1192,9 @@ void ibrd_gnn_destroy(ibrd_gnn m) {
   for (void* p : {(void*)m->th, (void*)m->g, (void*)m->m1, (void*)m->m2, (void*)m->cnt, (void*)m->nidx,
                   (void*)m->oflow, (void*)m->nr, (void*)m->x, (void*)m->a0, (void*)m->h, (void*)m->m,
                   (void*)m->a, (void*)m->y, (void*)m->dy, (void*)m->da0, (void*)m->da, (void*)m->dm,
-                  (void*)m->dhv, (void*)m->dh, (void*)m->part, (void*)m->loss, (void*)m->p32, (void*)m->wb})
+                  (void*)m->dhv, (void*)m->dh, (void*)m->part, (void*)m->loss, (void*)m->p32, (void*)m->wb,
+                  (void*)m->cell_of, (void*)m->cell_blobs, (void*)m->tj, (void*)m->tr, (void*)m->cell_cnt,
+                  (void*)m->cell_start, (void*)m->cell_cursor})
     if (p) cudaFree(p);
   if (m->host) cudaFreeHost(m->host);
   if (prev >= 0 && prev != m->dev) cudaSetDevice(prev);

@@ -39,7 +39,11 @@ def _config(n, side, seed, spacing=2.0):
     return q, np.array([side, side, side], dtype=np.float64)
 
 
-@pytest.mark.parametrize("n,side,R", [(200, 40, 8.0), (37, 20, 9.5), (1, 24, 6.0)])
+# 40 / 8: five cells of the cell list per axis; 40 / 10 and 30 / 9.99: three
+# (the fewest it takes, the last with cells barely longer than R); 20 / 9.5:
+# two, so all pairs are screened; one blob: no neighbour at all
+@pytest.mark.parametrize("n,side,R", [(200, 40, 8.0), (500, 40, 10.0), (150, 30, 9.99), (37, 20, 9.5),
+                                      (1, 24, 6.0)])
 def test_neighbours_exact(ibrd, n, side, R):
     q, box = _config(n, side, 3)
     m = ibrd.GNN(R, 64)
