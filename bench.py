@@ -823,6 +823,39 @@ def run_kernel_case_resid(args):
     log("[bench] residual kernel case done")
 
 
+def run_kernel_case_gnn(args):
+    """Inference of the learned multiplier predictor (seeded weights; the
+    bfloat16 tensor-core path) on 16384 RSA blobs in a 256^3 box, cutoff 24h:
+    timed with CUDA events over ten calls (printed), then one call inside a
+    profiler range: the small case for ncu captures of its kernels."""
+    import torch
+    import numpy as np
+    from paper_1306_3159_gb300 import build as pbuild
+    from synthetic import rsa_positions
+    pbuild.build()
+    import paper_1306_3159_gb300 as p
+    q = torch.from_numpy(rsa_positions(16384, (256,) * 3, 1.0, 3.0, 77)).cuda()
+    box = np.array([256.0] * 3)
+    m = p.GNN(LEARNED_CUTOFF, 256, stream=torch.cuda.current_stream().cuda_stream)
+    m.init_params(1)
+    lam = torch.zeros(q.shape[0], dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        m.predict(q, box, 1.0, out=lam)
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    e[0].record()
+    for _ in range(10):
+        m.predict(q, box, 1.0, out=lam)
+    e[1].record()
+    torch.cuda.synchronize()
+    log(f"[bench] learned predictor inference {e[0].elapsed_time(e[1]) * 100:.1f} us per call (16384 blobs)")
+    torch.cuda.profiler.start()
+    m.predict(q, box, 1.0, out=lam)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    log("[bench] learned predictor kernel case done")
+
+
 def run_kernel_case(args):
     """FP32 V-cycles (nu = 1/1, as in the chosen solves) on a 256^3 field
     (about 0.3 GB on the device) with a profiler range around one V-cycle: the
@@ -965,6 +998,8 @@ def main():
     ap.add_argument("--kernel-case", action="store_true", help="FP32 V-cycles at 256^3 for ncu, then exit")
     ap.add_argument("--kernel-case-fp64", action="store_true", help="FP64 A c at 256^3 for ncu, then exit")
     ap.add_argument("--kernel-case-resid", action="store_true", help="FP64 residual at 256^3 for ncu, then exit")
+    ap.add_argument("--kernel-case-gnn", action="store_true",
+                    help="learned predictor inference on 16384 blobs for ncu, then exit")
     args = ap.parse_args()
     if args.cpu_steps:
         print(json.dumps(run_cpu_steps(args.cpu_warmup, args.cpu_steps)), flush=True)
@@ -978,6 +1013,8 @@ def main():
         run_kernel_case_fp64(args)
     elif args.kernel_case_resid:
         run_kernel_case_resid(args)
+    elif args.kernel_case_gnn:
+        run_kernel_case_gnn(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
