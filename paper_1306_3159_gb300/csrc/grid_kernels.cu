@@ -476,10 +476,65 @@ __global__ void __launch_bounds__(1024) k_hartley_solve(const float* __restrict_
 // planes (H_y H_x per z-plane, one CTA each), columns (H_z, scale by w, H_z,
 // one CTA per y-row), planes again (H_y H_x). In shared memory a 2-D slice is
 // padded to a row stride of cols + 1, H rows to m + 1 (conflict-free).
+//
+// Shared-memory size (floats) reserved for one H table of order m: m (m + 1),
+// rounded up to a multiple of 4 so that the next table stays 16-byte aligned.
+__host__ __device__ __forceinline__ int hartley_hsz(int m) { return (m * (m + 1) + 3) & ~3; }
+
+// Orders whose transforms run register-blocked (hartley_pass_reg).
+__device__ __forceinline__ bool hartley_reg(int m) { return m == 16 || m == 32; }
+
+// H of order m into shared memory: unpadded for the register-blocked pass,
+// rows padded to m + 1 for the generic one.
+__device__ void hartley_stage(float* __restrict__ dst, const float* __restrict__ src, int m) {
+  if (hartley_reg(m))
+    for (int i = threadIdx.x; i < m * m; i += blockDim.x) dst[i] = src[i];
+  else
+    for (int i = threadIdx.x; i < m * m; i += blockDim.x) dst[(i / m) * (m + 1) + i % m] = src[i];
+}
+
+// Register-blocked pass for lines of M values: a thread holds one line's
+// inputs in registers and forms 4 consecutive outputs k0 .. k0 + 3, reading H
+// (symmetric: row j holds H[k][j] at column k) as 4-vectors, a quarter of a
+// shared-memory load per multiply-add. Each output is the same chain of FMAs
+// over j = 0 .. M - 1 as in the generic pass, so the results are identical.
+template <int M>
+__device__ __forceinline__ void hartley_pass_reg(const float* __restrict__ in, float* __restrict__ out, const float* __restrict__ h,
+                                 int lines, int st, int lstride) {
+  constexpr int G = M / 4;
+  for (int it = threadIdx.x; it < lines * G; it += blockDim.x) {
+    const int line = it / G, k0 = 4 * (it - line * G);
+    const float* ip = in + line * lstride;
+    float xin[M];
+#pragma unroll
+    for (int j = 0; j < M; ++j) xin[j] = ip[j * st];
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+      const float4 hv = *reinterpret_cast<const float4*>(h + j * M + k0);
+      acc.x = fmaf(hv.x, xin[j], acc.x);
+      acc.y = fmaf(hv.y, xin[j], acc.y);
+      acc.z = fmaf(hv.z, xin[j], acc.z);
+      acc.w = fmaf(hv.w, xin[j], acc.w);
+    }
+    float* op = out + line * lstride;
+    op[(k0 + 0) * st] = acc.x;
+    op[(k0 + 1) * st] = acc.y;
+    op[(k0 + 2) * st] = acc.z;
+    op[(k0 + 3) * st] = acc.w;
+  }
+  __syncthreads();
+}
+
 // Transform along one axis of a padded 2-D slice: `lines` lines of m values,
-// element j of line l at base(l) + j * st.
-__device__ void hartley_pass2d(const float* __restrict__ in, float* __restrict__ out, const float* __restrict__ h,
-                               int m, int lines, int st, int lstride) {
+// element j of line l at l * lstride + j * st; h as staged by hartley_stage.
+// Generic pass: one thread per output (line, k), consecutive threads on
+// consecutive k, so H rows (padded) are read without bank conflicts and each
+// input as a broadcast.
+__device__ __forceinline__ void hartley_pass2d(const float* __restrict__ in, float* __restrict__ out,
+                                               const float* __restrict__ h, int m, int lines, int st, int lstride) {
+  if (m == 32) return hartley_pass_reg<32>(in, out, h, lines, st, lstride);
+  if (m == 16) return hartley_pass_reg<16>(in, out, h, lines, st, lstride);
   for (int it = threadIdx.x; it < lines * m; it += blockDim.x) {
     const int line = it / m, k = it - line * m;
     const int base = line * lstride;
@@ -498,11 +553,11 @@ __global__ void __launch_bounds__(1024) k_hartley_planes(const float* __restrict
   extern __shared__ __align__(16) float hs[];
   const int px = nx + 1, pn = px * ny;
   float* hx = hs;
-  float* hy = hx + nx * (nx + 1);
-  float* A = hy + ny * (ny + 1);
+  float* hy = hx + hartley_hsz(nx);
+  float* A = hy + hartley_hsz(ny);
   float* Bf = A + pn;
-  for (int i = threadIdx.x; i < nx * nx; i += blockDim.x) hx[(i / nx) * (nx + 1) + i % nx] = tab[i];
-  for (int i = threadIdx.x; i < ny * ny; i += blockDim.x) hy[(i / ny) * (ny + 1) + i % ny] = tab[nx * nx + i];
+  hartley_stage(hx, tab, nx);
+  hartley_stage(hy, tab + nx * nx, ny);
   const float sh = bshift ? (float)(*bshift) : 0.f;
   const float* sp = src + (size_t)blockIdx.x * nx * ny;
   for (int c = threadIdx.x; c < nx * ny; c += blockDim.x) A[(c / nx) * px + c % nx] = sp[c] - sh;
@@ -519,11 +574,11 @@ __global__ void __launch_bounds__(1024) k_hartley_columns(float* __restrict__ f,
   extern __shared__ __align__(16) float hs[];
   const int px = nx + 1, pn = px * nz, j = blockIdx.x;
   float* hz = hs;
-  float* A = hz + nz * (nz + 1);
+  float* A = hz + hartley_hsz(nz);
   float* Bf = A + pn;
   const float* tz = tab + nx * nx + ny * ny;
   const float* W = tz + nz * nz;
-  for (int i = threadIdx.x; i < nz * nz; i += blockDim.x) hz[(i / nz) * (nz + 1) + i % nz] = tz[i];
+  hartley_stage(hz, tz, nz);
   for (int c = threadIdx.x; c < nx * nz; c += blockDim.x) {
     const int i = c % nx, k = c / nx;
     A[k * px + i] = f[((size_t)k * ny + j) * nx + i];
@@ -951,8 +1006,9 @@ void launch_hartley_solve(const float* tab, const float* b, const double* bshift
   if (d.n() > 4096) {
     // three launches through the scratch field behind the tables
     float* tmp = const_cast<float*>(tab) + ((size_t)d.nx * d.nx + (size_t)d.ny * d.ny + (size_t)d.nz * d.nz + d.n());
-    const size_t smp = sizeof(float) * ((size_t)d.nx * (d.nx + 1) + (size_t)d.ny * (d.ny + 1) + 2 * (size_t)(d.nx + 1) * d.ny);
-    const size_t smc = sizeof(float) * ((size_t)d.nz * (d.nz + 1) + 2 * (size_t)(d.nx + 1) * d.nz);
+    const size_t smp = sizeof(float) * ((size_t)hartley_hsz((int)d.nx) + hartley_hsz((int)d.ny) +
+                                        2 * (size_t)(d.nx + 1) * d.ny);
+    const size_t smc = sizeof(float) * ((size_t)hartley_hsz((int)d.nz) + 2 * (size_t)(d.nx + 1) * d.nz);
     // sides up to 64 need more than the default 48 KB (at most 67 KB)
     static std::atomic<unsigned long long> attrp{0}, attrc{0};
     ensure_smem_attr((const void*)k_hartley_planes, 200 * 1024, attrp);

@@ -236,14 +236,16 @@ def test_vcycle_f32(ibrd, dims, alpha):
 
 
 @pytest.mark.parametrize("dims,alpha", [((16, 16, 16), 0.0), ((12, 8, 20), 0.3), ((40, 40, 40), 0.0),
-                                        ((24, 24, 24), 0.0), ((40, 40, 20), 0.2), ((64, 64, 8), 0.0)])
+                                        ((24, 24, 24), 0.0), ((40, 40, 20), 0.2), ((64, 64, 8), 0.0),
+                                        ((32, 32, 32), 0.1), ((64, 32, 16), 0.0)])
 def test_vcycle_f32_exact_level(ibrd, dims, alpha):
     """FP32 V-cycles whose hierarchy ends in the exact Hartley-transform solve:
     at 16^3 and 12 x 8 x 20 the finest level itself is exact (one CTA; the
     result is the FFT Green's function solution); at 40^3 the exact level is
-    10^3 below two smoothed levels; 24^3, 40 x 40 x 20 and 64 x 64 x 8 are
-    exact levels above 4096 cells (three launches: plane transforms, column
-    transforms with the scaling, plane transforms)."""
+    10^3 below two smoothed levels; 24^3, 32^3, 40 x 40 x 20, 64 x 32 x 16 and
+    64 x 64 x 8 are exact levels above 4096 cells (three launches: plane
+    transforms, column transforms with the scaling, plane transforms; lines
+    of 16 and 32 values register-blocked, the others generic)."""
     import torch
     nx, ny, nz = dims
     rng = np.random.default_rng(17)
