@@ -55,6 +55,9 @@ enum Slot {
   S_WAIT,     // nonzero bits: a bounded device wait gave up (written as an int)
   S_XMAX,     // largest |x| of a residual's iterate (its bits; fixed-point scale)
   S_PMEAN,    // mean of a block-preconditioned inner vector (IBRD_PRECOND_BLOCK)
+  S_HHAT,     // Gram-Schmidt: the new basis vector's norm estimated before the pass
+  S_HINV,     // its reciprocal
+  S_RHO2,     // squared norm of the stored (scaled) new basis vector
   S_UB = 64,  // mean of S U_j for the inner iterations j = 0..m (64 slots)
   S_UX = 128, // mean of A~^-1 S U_j (64 slots)
   S_COUNT = 192
@@ -220,6 +223,7 @@ struct ibrd_grid_s {
   size_t vlen = 0;        // length of the current solve's vectors
   size_t vcap_elems = 0;  // capacity of V and Z (doubles each)
   double *H = nullptr, *cs = nullptr, *sn = nullptr, *gvec = nullptr, *yv = nullptr, *hb2 = nullptr;
+  double* vsc = nullptr;  // inverse norms of the stored Krylov basis vectors (restart + 2)
   int hcap = 0;
   double *xs = nullptr, *bs = nullptr;  // saddle [c; lambda] solution and rhs
   size_t xs_cap = 0;
@@ -674,57 +678,84 @@ size_t ensure_krylov(ibrd_grid g, size_t n, int restart) {
     cudaFree(g->gvec);
     cudaFree(g->yv);
     cudaFree(g->hb2);
+    cudaFree(g->vsc);
     g->H = dalloc<double>((size_t)(restart + 1) * restart);
     g->cs = dalloc<double>(restart);
     g->sn = dalloc<double>(restart);
     g->gvec = dalloc<double>(restart + 1);
     g->yv = dalloc<double>(restart);
     g->hb2 = dalloc<double>(restart + 1);
+    g->vsc = dalloc<double>(restart + 2);
+    const std::vector<double> ones((size_t)restart + 2, 1.0);  // V[0] is always normalised exactly
+    IBRD_CUDA(cudaMemcpyAsync(g->vsc, ones.data(), sizeof(double) * ones.size(), cudaMemcpyHostToDevice, g->s));
+    IBRD_CUDA(cudaStreamSynchronize(g->s));
     g->hcap = restart;
   }
   return ld;
 }
 
-// w (= V[j+1]) <- w - sum_{i<=j} h_i V[i], h written into H[:, j]; ||w||^2
-// after orthogonalisation lands in S_SQ, ||w||^2 before in S_TMP. Classical
-// Gram-Schmidt; the second pass (DGKS test with threshold eta) is decided on
-// the device and its kernels return at once when it is not needed, so the
-// host does not wait here. Vectors of length n, stride ld.
+// w (= V[j+1]) <- w - sum_{i<=j} h_i v_i, the projections h written into
+// H[:, j], h_{j+1,j} (the norm of w after) into H[j+1, j], ||w||^2 before into
+// S_TMP and h_{j+1,j}^2 into S_SQ; then V[j+1] is the new basis vector. Stored
+// basis vectors need not have norm 1: V[i] = v_i / vsc[i], vsc[i] its inverse
+// norm, and every projection and coefficient carries that factor. Classical
+// Gram-Schmidt. Without a second pass (eta <= 0) the pass that subtracts the
+// projections also scales the new vector by the reciprocal of its norm as
+// estimated from them, and the exact norm of what it stored, taken in the same
+// pass, fixes h_{j+1,j} and vsc[j+1] (no separate normalisation pass). With the
+// DGKS second pass (threshold eta, decided on the device, its kernels
+// returning at once when it is not needed) the vector is normalised after it.
 template <typename E>
 void orthogonalize(ibrd_grid g, int j, size_t n, size_t ld, int ldh, double eta) {
   E* V = reinterpret_cast<E*>(g->V);
   E* w = V + (size_t)(j + 1) * ld;
   double* hcol = g->H + (size_t)j * ldh;
+  double* vs = g->vsc;
+  double* sc = g->scal;
   const int nb = j + 1;  // basis vectors V[0..j]
-  // pass 1: dots of V[0..j+1] (the last is <w, w>)
+  // pass 1: dots of V[0..j+1] (the last is <w, w>, unscaled)
   for (int g0 = 0; g0 < nb + 1; g0 += kDotGroup) {
     const int m = std::min(kDotGroup, nb + 1 - g0);
     launch_multidot(V + (size_t)g0 * ld, ld, m, w, n, g->partial, g->s);
-    launch_reduce_partials(g->partial, m, hcol + g0, g->s);
+    launch_reduce_partials(g->partial, m, hcol + g0, g->s, nullptr, vs + g0, std::max(0, std::min(m, nb - g0)));
   }
-  IBRD_CUDA(cudaMemcpyAsync(g->scal + S_TMP, hcol + nb, sizeof(double), cudaMemcpyDeviceToDevice, g->s));
+  if (eta <= 0.0) {
+    launch_gs_norm_estimate(hcol, nb, sc + S_TMP, sc + S_HHAT, sc + S_HINV, g->s);
+    for (int g0 = 0; g0 < nb; g0 += kDotGroup) {
+      const int m = std::min(kDotGroup, nb - g0);
+      const bool last = g0 + m >= nb;
+      launch_multi_axpy(w, V + (size_t)g0 * ld, ld, m, hcol + g0, -1.0, n, last ? g->partial : nullptr, g->s,
+                        nullptr, vs + g0, last ? sc + S_HINV : nullptr);
+    }
+    launch_reduce_partials(g->partial, 1, sc + S_RHO2, g->s);
+    launch_gs_norm_fix(sc + S_RHO2, sc + S_HHAT, hcol + nb, vs + nb, sc + S_SQ, g->s);
+    return;
+  }
+  IBRD_CUDA(cudaMemcpyAsync(sc + S_TMP, hcol + nb, sizeof(double), cudaMemcpyDeviceToDevice, g->s));
   for (int g0 = 0; g0 < nb; g0 += kDotGroup) {
     const int m = std::min(kDotGroup, nb - g0);
     const bool last = g0 + m >= nb;
-    launch_multi_axpy(w, V + (size_t)g0 * ld, ld, m, hcol + g0, -1.0, n, last ? g->partial : nullptr, g->s);
+    launch_multi_axpy(w, V + (size_t)g0 * ld, ld, m, hcol + g0, -1.0, n, last ? g->partial : nullptr, g->s,
+                      nullptr, vs + g0);
   }
-  launch_reduce_partials(g->partial, 1, g->scal + S_SQ, g->s);
-  if (eta <= 0.0) return;
-  const double* gate = g->scal + S_RFLAG;
-  launch_reorth_flag(g->scal + S_TMP, g->scal + S_SQ, eta, g->scal + S_RFLAG, g->scal + S_RCOUNT, g->s);
+  launch_reduce_partials(g->partial, 1, sc + S_SQ, g->s);
+  const double* gate = sc + S_RFLAG;
+  launch_reorth_flag(sc + S_TMP, sc + S_SQ, eta, sc + S_RFLAG, sc + S_RCOUNT, g->s);
   for (int g0 = 0; g0 < nb; g0 += kDotGroup) {
     const int m = std::min(kDotGroup, nb - g0);
     launch_multidot(V + (size_t)g0 * ld, ld, m, w, n, g->partial, g->s, gate);
-    launch_reduce_partials(g->partial, m, g->hb2 + g0, g->s, gate);
+    launch_reduce_partials(g->partial, m, g->hb2 + g0, g->s, gate, vs + g0, m);
   }
   for (int g0 = 0; g0 < nb; g0 += kDotGroup) {
     const int m = std::min(kDotGroup, nb - g0);
     const bool last = g0 + m >= nb;
     launch_multi_axpy(w, V + (size_t)g0 * ld, ld, m, g->hb2 + g0, -1.0, n, last ? g->partial : nullptr, g->s,
-                      gate);
+                      gate, vs + g0);
   }
-  launch_reduce_partials(g->partial, 1, g->scal + S_SQ, g->s, gate);
+  launch_reduce_partials(g->partial, 1, sc + S_SQ, g->s, gate);
   launch_vec_add_small(hcol, g->hb2, nb, g->s, gate);
+  launch_gs_norm_unit(sc + S_SQ, hcol + nb, vs + nb, g->s);
+  launch_scale_by_inv<E>(w, w, n, hcol + nb, 1.0, g->s);
 }
 
 struct SolveResult {
@@ -824,9 +855,6 @@ SolveResult fgmres(ibrd_grid g, LinOp<E>& op, const E* b, E* x, size_t n, const 
       run_precond<E>(g, op, j, vj, zj, o.graphs != 0);
       op.apply(zj, w);
       orthogonalize<E>(g, j, n, ld, ldh, o.reorth_eta);
-      double* hcol = g->H + (size_t)j * ldh;
-      launch_sqrt_scalar(g->scal + S_SQ, hcol + j + 1, g->s);
-      launch_scale_by_inv<E>(w, w, n, hcol + j + 1, 1.0, g->s);
       launch_givens(g->H, ldh, j, g->cs, g->sn, g->gvec, g->scal + S_RES, g->s);
       // one host read per iteration: residual estimate and the norms
       IBRD_CUDA(cudaMemcpyAsync(g->host, g->scal, sizeof(double) * (S_WAIT + 1), cudaMemcpyDeviceToHost, g->s));
@@ -1321,9 +1349,6 @@ void capture_refine(ibrd_grid g, LinOp<double>& op64, LinOp<float>& op32, const 
             }
             op32.apply(zj, w);
             orthogonalize<float>(g, j, n, ld, ldh, o.reorth_eta);
-            double* hcol = g->H + (size_t)j * ldh;
-            launch_sqrt_scalar(sc + S_SQ, hcol + j + 1, g->s);
-            launch_scale_by_inv<float>(w, w, n, hcol + j + 1, 1.0, g->s);
             launch_givens(g->H, ldh, j, g->cs, g->sn, g->gvec, sc + S_RES, g->s);
             k_g_it_ctrl<<<1, 32, 0, g->s>>>(st, sc, g->ghist, j, m, j + 1 < m ? hs.h[j + 1] : hs.h[j], h_k);
             SG.l_it[j] = mark() - a0 + 1;
@@ -2663,7 +2688,7 @@ void ibrd_grid_destroy(ibrd_grid g) {
   F(b.active); F(b.d_meta); F(b.cell_count); F(b.cell_offset); F(b.cells); F(b.cell_tile);
   F(g->scal); F(g->partial); F(g->dflag); F(g->gst); F(g->ghist);
   if (g->host) cudaFreeHost(g->host);
-  F(g->V); F(g->Z); F(g->H); F(g->cs); F(g->sn); F(g->gvec); F(g->yv); F(g->hb2); F(g->xs); F(g->bs);
+  F(g->V); F(g->Z); F(g->H); F(g->cs); F(g->sn); F(g->gvec); F(g->yv); F(g->hb2); F(g->vsc); F(g->xs); F(g->bs);
   F(g->ir_r); F(g->ir_r32); F(g->ir_d32);
   for (auto p : g->p64) F(p);
   for (auto p : g->p32) F(p);

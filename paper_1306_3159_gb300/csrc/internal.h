@@ -342,15 +342,29 @@ void launch_multidot(const double* V, size_t ldv, int nvec, const double* w, siz
 // FP32 basis: V and w 16-byte aligned, ldv % 4 == 0.
 void launch_multidot(const float* V, size_t ldv, int nvec, const float* w, size_t n, double* partial,
                      cudaStream_t s, const double* gate = nullptr);
-// out[g] = sum_blk partial[g*kRedBlocks + blk]   (g < nvec)
+// out[g] = sum_blk partial[g*kRedBlocks + blk]   (g < nvec), times scale[g]
+// for g < nscale when scale is given
 void launch_reduce_partials(const double* partial, int nvec, double* out, cudaStream_t s,
-                            const double* gate = nullptr);
-// w += sign * sum_g coef[g] V[g]; optional partial sums of squares of new w.
+                            const double* gate = nullptr, const double* scale = nullptr, int nscale = 0);
+// w += sign * sum_g coef[g] cscale[g] V[g] (cscale optional), then w *= *post
+// (optional); optional partial sums of squares of the new w.
 void launch_multi_axpy(double* w, const double* V, size_t ldv, int nvec, const double* coef, double sign,
-                       size_t n, double* partial_sq, cudaStream_t s, const double* gate = nullptr);
+                       size_t n, double* partial_sq, cudaStream_t s, const double* gate = nullptr,
+                       const double* cscale = nullptr, const double* post = nullptr);
 // FP32 basis: V and w 16-byte aligned, ldv % 4 == 0.
 void launch_multi_axpy(float* w, const float* V, size_t ldv, int nvec, const double* coef, double sign, size_t n,
-                       double* partial_sq, cudaStream_t s, const double* gate = nullptr);
+                       double* partial_sq, cudaStream_t s, const double* gate = nullptr,
+                       const double* cscale = nullptr, const double* post = nullptr);
+// Gram-Schmidt norm bookkeeping (one-warp kernels): the estimate of the norm
+// after one pass from the projections h[0..nb) and h[nb] = ||w||^2 (writes
+// ||w||^2, the estimate and its reciprocal); after a pass that stored the
+// vector scaled by the estimate's reciprocal, with squared norm *rho2:
+// h_{j+1,j}, the stored vector's inverse norm and h_{j+1,j}^2; for a vector
+// normalised exactly afterwards: h_{j+1,j} = sqrt(*sq) and scale 1.
+void launch_gs_norm_estimate(const double* h, int nb, double* ww, double* hhat, double* hinv, cudaStream_t s);
+void launch_gs_norm_fix(const double* rho2, const double* hhat, double* hsub, double* vscale, double* sq,
+                        cudaStream_t s);
+void launch_gs_norm_unit(const double* sq, double* hsub, double* vscale, cudaStream_t s);
 // Givens step j on column H[:, j] (ldh = restart + 1): rotations cs/sn,
 // residual vector gvec; writes |gvec[j+1]| to *res.
 void launch_givens(double* H, int ldh, int j, double* cs, double* sn, double* gvec, double* res,

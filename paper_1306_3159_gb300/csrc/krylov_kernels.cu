@@ -91,29 +91,34 @@ __global__ void __launch_bounds__(kRedThreads) k_multidot_f32(const float* __res
 
 __global__ void __launch_bounds__(kRedThreads) k_reduce_partials(const double* __restrict__ partial,
                                                                  double* __restrict__ out,
-                                                                 const double* __restrict__ gate) {
+                                                                 const double* __restrict__ gate,
+                                                                 const double* __restrict__ scale, int nscale) {
   if (gate && *gate == 0.0) return;
   // blockIdx.x = vector g
   double acc = 0.0;
   for (int i = threadIdx.x; i < kRedBlocks; i += blockDim.x) acc += partial[blockIdx.x * kRedBlocks + i];
   acc = block_sum(acc);
-  if (threadIdx.x == 0) out[blockIdx.x] = acc;
+  if (threadIdx.x == 0) out[blockIdx.x] = ((int)blockIdx.x < nscale) ? acc * scale[blockIdx.x] : acc;
 }
 
 template <int NV, bool SQ>
 __global__ void __launch_bounds__(kRedThreads) k_multi_axpy(double* __restrict__ w, const double* __restrict__ V,
                                                             size_t ldv, const double* __restrict__ coef,
                                                             double sign, size_t n, double* __restrict__ partial_sq,
-                                                            const double* __restrict__ gate) {
+                                                            const double* __restrict__ gate,
+                                                            const double* __restrict__ cscale,
+                                                            const double* __restrict__ post) {
   if (gate && *gate == 0.0) return;
   double c[NV];
 #pragma unroll
-  for (int g = 0; g < NV; ++g) c[g] = sign * coef[g];
+  for (int g = 0; g < NV; ++g) c[g] = sign * coef[g] * (cscale ? cscale[g] : 1.0);
+  const double ps = post ? *post : 1.0;
   double sq = 0.0;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     double wi = w[i];
 #pragma unroll
     for (int g = 0; g < NV; ++g) wi = fma(c[g], V[g * ldv + i], wi);
+    if (post) wi *= ps;
     w[i] = wi;
     if (SQ) sq = fma(wi, wi, sq);
   }
@@ -130,11 +135,15 @@ __global__ void __launch_bounds__(kRedThreads) k_multi_axpy_f32(float* __restric
                                                                 size_t ldv, const double* __restrict__ coef,
                                                                 double sign, size_t n,
                                                                 double* __restrict__ partial_sq,
-                                                                const double* __restrict__ gate) {
+                                                                const double* __restrict__ gate,
+                                                                const double* __restrict__ cscale,
+                                                                const double* __restrict__ post) {
   if (gate && *gate == 0.0) return;
   float c[NV];
 #pragma unroll
-  for (int g = 0; g < NV; ++g) c[g] = (float)(sign * coef[g]);
+  for (int g = 0; g < NV; ++g) c[g] = (float)(sign * coef[g] * (cscale ? cscale[g] : 1.0));
+  const bool scaled = post != nullptr;
+  const float ps = scaled ? (float)*post : 1.f;
   float sq = 0.f;
   const size_t n4 = n >> 2, stride = (size_t)gridDim.x * blockDim.x;
   const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
@@ -148,6 +157,7 @@ __global__ void __launch_bounds__(kRedThreads) k_multi_axpy_f32(float* __restric
       wi.z = fmaf(c[g], v.z, wi.z);
       wi.w = fmaf(c[g], v.w, wi.w);
     }
+    if (scaled) wi.x *= ps, wi.y *= ps, wi.z *= ps, wi.w *= ps;
     reinterpret_cast<float4*>(w)[i] = wi;
     if (SQ) sq = fmaf(wi.x, wi.x, fmaf(wi.y, wi.y, fmaf(wi.z, wi.z, fmaf(wi.w, wi.w, sq))));
   }
@@ -156,6 +166,7 @@ __global__ void __launch_bounds__(kRedThreads) k_multi_axpy_f32(float* __restric
     float wi = w[i];
 #pragma unroll
     for (int g = 0; g < NV; ++g) wi = fmaf(c[g], V[g * ldv + i], wi);
+    if (scaled) wi *= ps;
     w[i] = wi;
     if (SQ) sq = fmaf(wi, wi, sq);
   }
@@ -221,6 +232,49 @@ __global__ void k_reorth_flag(const double* __restrict__ ww, const double* __res
 
 __global__ void k_sqrt_scalar(const double* __restrict__ src, double* __restrict__ dst) {
   if (threadIdx.x == 0) *dst = sqrt(fmax(*src, 0.0));
+}
+
+// The norm of w after one classical Gram-Schmidt pass, estimated before the
+// pass from its projections h[0..nb) and h[nb] = ||w||^2: ||w||^2 - sum h_i^2,
+// floored at 1e-8 ||w||^2 (where cancellation leaves no digits the floor only
+// changes the stored vector's scale, which the exact norm taken in the same
+// pass then records). Writes ||w||^2, the estimate and its reciprocal (0 for
+// w = 0). One warp.
+__global__ void k_gs_norm_estimate(const double* __restrict__ h, int nb, double* __restrict__ ww,
+                                   double* __restrict__ hhat, double* __restrict__ hinv) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nb; i += 32) s = fma(h[i], h[i], s);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (threadIdx.x != 0) return;
+  const double w2 = h[nb];
+  const double e = fmax(w2 - s, 1e-8 * w2);
+  const double r = e > 0.0 ? sqrt(e) : 0.0;
+  *ww = w2;
+  *hhat = r;
+  *hinv = r > 0.0 ? 1.0 / r : 0.0;
+}
+
+// After the pass wrote the new basis vector scaled by 1 / hhat with squared
+// norm rho2: the Hessenberg entry h_{j+1,j} = hhat sqrt(rho2) (the norm of the
+// unscaled vector), the stored vector's inverse norm, and h_{j+1,j}^2 into sq.
+__global__ void k_gs_norm_fix(const double* __restrict__ rho2, const double* __restrict__ hhat,
+                              double* __restrict__ hsub, double* __restrict__ vscale, double* __restrict__ sq) {
+  if (threadIdx.x != 0) return;
+  const double r = sqrt(fmax(*rho2, 0.0));
+  const double hs = *hhat * r;
+  *hsub = hs;
+  *vscale = r > 0.0 ? 1.0 / r : 0.0;
+  *sq = hs * hs;
+}
+
+// h_{j+1,j} = sqrt(sq), for a basis vector that is then normalised exactly
+// (stored scale 1).
+__global__ void k_gs_norm_unit(const double* __restrict__ sq, double* __restrict__ hsub,
+                               double* __restrict__ vscale) {
+  if (threadIdx.x != 0) return;
+  *hsub = sqrt(fmax(*sq, 0.0));
+  *vscale = 1.0;
 }
 
 // ---------------------------------------------------------------- small GMRES
@@ -492,31 +546,56 @@ void launch_multidot(const float* V, size_t ldv, int nvec, const float* w, size_
   prof_end(P_DOT, s, "multidot_f32", 4.0 * (nvec + 1) * n);
 }
 
-void launch_reduce_partials(const double* partial, int nvec, double* out, cudaStream_t s, const double* gate) {
+void launch_reduce_partials(const double* partial, int nvec, double* out, cudaStream_t s, const double* gate,
+                            const double* scale, int nscale) {
   if (nvec <= 0) return;
   prof_begin(P_REDUCE, s);
-  k_reduce_partials<<<nvec, kRedThreads, 0, s>>>(partial, out, gate);
+  k_reduce_partials<<<nvec, kRedThreads, 0, s>>>(partial, out, gate, scale, scale ? nscale : 0);
   prof_end(P_REDUCE, s, "reduce_partials");
 }
 
+void launch_gs_norm_estimate(const double* h, int nb, double* ww, double* hhat, double* hinv, cudaStream_t s) {
+  prof_begin(P_SMALL, s);
+  k_gs_norm_estimate<<<1, 32, 0, s>>>(h, nb, ww, hhat, hinv);
+  prof_end(P_SMALL, s, "gs_norm_estimate");
+}
+
+void launch_gs_norm_fix(const double* rho2, const double* hhat, double* hsub, double* vscale, double* sq,
+                        cudaStream_t s) {
+  prof_begin(P_SMALL, s);
+  k_gs_norm_fix<<<1, 32, 0, s>>>(rho2, hhat, hsub, vscale, sq);
+  prof_end(P_SMALL, s, "gs_norm_fix");
+}
+
+void launch_gs_norm_unit(const double* sq, double* hsub, double* vscale, cudaStream_t s) {
+  prof_begin(P_SMALL, s);
+  k_gs_norm_unit<<<1, 32, 0, s>>>(sq, hsub, vscale);
+  prof_end(P_SMALL, s, "gs_norm_unit");
+}
+
 void launch_multi_axpy(double* w, const double* V, size_t ldv, int nvec, const double* coef, double sign, size_t n,
-                       double* partial_sq, cudaStream_t s, const double* gate) {
+                       double* partial_sq, cudaStream_t s, const double* gate, const double* cscale,
+                       const double* post) {
   if (nvec < 1 || nvec > kDotGroup) return;
   prof_begin(P_AXPY, s);
   if (partial_sq) {
     switch (nvec) {
-#define IBRD_CASE(k)                                                                                       \
-  case k:                                                                                                  \
-    k_multi_axpy<k, true><<<kRedBlocks, kRedThreads, 0, s>>>(w, V, ldv, coef, sign, n, partial_sq, gate); break;
+#define IBRD_CASE(k)                                                                                     \
+  case k:                                                                                                \
+    k_multi_axpy<k, true><<<kRedBlocks, kRedThreads, 0, s>>>(w, V, ldv, coef, sign, n, partial_sq, gate, \
+                                                             cscale, post);                              \
+    break;
       IBRD_CASE(1) IBRD_CASE(2) IBRD_CASE(3) IBRD_CASE(4) IBRD_CASE(5) IBRD_CASE(6) IBRD_CASE(7) IBRD_CASE(8)
 #undef IBRD_CASE
       default: return;
     }
   } else {
     switch (nvec) {
-#define IBRD_CASE(k)                                                                                        \
-  case k:                                                                                                   \
-    k_multi_axpy<k, false><<<kRedBlocks, kRedThreads, 0, s>>>(w, V, ldv, coef, sign, n, nullptr, gate); break;
+#define IBRD_CASE(k)                                                                                      \
+  case k:                                                                                                 \
+    k_multi_axpy<k, false><<<kRedBlocks, kRedThreads, 0, s>>>(w, V, ldv, coef, sign, n, nullptr, gate,   \
+                                                              cscale, post);                              \
+    break;
       IBRD_CASE(1) IBRD_CASE(2) IBRD_CASE(3) IBRD_CASE(4) IBRD_CASE(5) IBRD_CASE(6) IBRD_CASE(7) IBRD_CASE(8)
 #undef IBRD_CASE
       default: return;
@@ -526,7 +605,8 @@ void launch_multi_axpy(double* w, const double* V, size_t ldv, int nvec, const d
 }
 
 void launch_multi_axpy(float* w, const float* V, size_t ldv, int nvec, const double* coef, double sign, size_t n,
-                       double* partial_sq, cudaStream_t s, const double* gate) {
+                       double* partial_sq, cudaStream_t s, const double* gate, const double* cscale,
+                       const double* post) {
   if (nvec < 1 || nvec > kDotGroup) return;
   if (ldv % 4 != 0 || !aligned16(V) || !aligned16(w)) throw CudaError{cudaErrorMisalignedAddress, "multi_axpy_f32"};
   prof_begin(P_AXPY, s);
@@ -534,7 +614,8 @@ void launch_multi_axpy(float* w, const float* V, size_t ldv, int nvec, const dou
     switch (nvec) {
 #define IBRD_CASE(k)                                                                                           \
   case k:                                                                                                      \
-    k_multi_axpy_f32<k, true><<<kRedBlocks, kRedThreads, 0, s>>>(w, V, ldv, coef, sign, n, partial_sq, gate); \
+    k_multi_axpy_f32<k, true><<<kRedBlocks, kRedThreads, 0, s>>>(w, V, ldv, coef, sign, n, partial_sq, gate, \
+                                                                 cscale, post);                              \
     break;
       IBRD_CASE(1) IBRD_CASE(2) IBRD_CASE(3) IBRD_CASE(4) IBRD_CASE(5) IBRD_CASE(6) IBRD_CASE(7) IBRD_CASE(8)
 #undef IBRD_CASE
@@ -544,7 +625,8 @@ void launch_multi_axpy(float* w, const float* V, size_t ldv, int nvec, const dou
     switch (nvec) {
 #define IBRD_CASE(k)                                                                                            \
   case k:                                                                                                       \
-    k_multi_axpy_f32<k, false><<<kRedBlocks, kRedThreads, 0, s>>>(w, V, ldv, coef, sign, n, nullptr, gate); \
+    k_multi_axpy_f32<k, false><<<kRedBlocks, kRedThreads, 0, s>>>(w, V, ldv, coef, sign, n, nullptr, gate, \
+                                                                  cscale, post);                             \
     break;
       IBRD_CASE(1) IBRD_CASE(2) IBRD_CASE(3) IBRD_CASE(4) IBRD_CASE(5) IBRD_CASE(6) IBRD_CASE(7) IBRD_CASE(8)
 #undef IBRD_CASE

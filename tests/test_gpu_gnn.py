@@ -120,6 +120,25 @@ def test_predict_bfloat16_tensor_cores(ibrd, n, side, R):
     assert np.abs(y - y_ref).max() < 2e-5 * max(1.0, np.abs(y_ref).max())
 
 
+def test_predict_full_size_workload(ibrd):
+    """The benchmark's evaluation case: the 256^3 workload's 4096 blobs with
+    the cutoff 24h and the library's seeded weights; the tensor-core
+    prediction against the definition with bfloat16 operands, every blob."""
+    w = workload("scale")
+    R = 24.0
+    box = np.array([256.0, 256.0, 256.0])
+    m = ibrd.GNN(R, 256)
+    m.init_params(1)
+    th = m.get_params().astype(np.float64)
+    total = float(w.g.sum())
+    lam0 = host(m.predict(dev(w.q), box, total))
+    want = gnn.predict(th, w.q, box, R, total, bf16_products=True)
+    assert rel_err(lam0, want) < 2e-4
+    y = host(m.forward(dev(w.q), box)).astype(np.float64)
+    y_ref, _ = gnn.forward(th, w.q, box, R)
+    assert np.abs(y - y_ref).max() < 2e-5 * max(1.0, np.abs(y_ref).max())
+
+
 def test_too_many_neighbours_is_an_argument_error(ibrd):
     q, box = _config(60, 20, 9, spacing=1.0)
     m = ibrd.GNN(9.9, 4)
