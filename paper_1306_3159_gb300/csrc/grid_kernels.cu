@@ -617,6 +617,23 @@ __device__ __forceinline__ double block_sum(double v) {
   return v;
 }
 
+// Block sum of FP32 per-thread values (blockDim.x == kRedThreads), result
+// valid in thread 0: the warps add in FP32, the block adds the warps' totals
+// in FP64 (one warp of FP64 shuffles per block instead of all of them: the
+// FP64 pipe is about 64 times narrower than the FP32 one).
+__device__ __forceinline__ double block_sum_f(float v) {
+  __shared__ double sw[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sw[wid] = (double)v;
+  __syncthreads();
+  double d = (threadIdx.x < (blockDim.x >> 5)) ? sw[threadIdx.x] : 0.0;
+  if (wid == 0) d = warp_sum(d);
+  __syncthreads();
+  return d;
+}
+
 // Sum of x: each thread folds 8-element runs (FP32 inputs summed in FP32 within
 // a run, then in FP64) from a grid-stride loop with 4 independent runs in flight.
 template <typename T>
@@ -635,36 +652,34 @@ __global__ void __launch_bounds__(kRedThreads) k_sum_partial(const T* __restrict
   if (threadIdx.x == 0) partial[blockIdx.x] = acc;
 }
 
-// FP64: one FMA per element; FP32: products summed in FP32 over runs of 4
-// (stride apart) and the runs in FP64.
+// FP64: one FMA per element, sums in FP64; FP32: products summed per thread
+// and across a warp in FP32 (a thread holds a few dozen products of a 256^3
+// field), across warps and blocks in FP64.
 template <typename E>
 __global__ void __launch_bounds__(kRedThreads) k_dot_partial(const E* __restrict__ x, const E* __restrict__ y,
                                                              size_t n, double* __restrict__ partial, int vec) {
-  double acc = 0.0;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if constexpr (sizeof(E) == 4) {
+    float acc = 0.f;
     if (vec) {
-      // 16-byte aligned: 4-vectors, FP32 sums of one vector each
+      // 16-byte aligned: 4-vectors
       const size_t n4 = n >> 2, t = i;
       for (size_t v = t; v < n4; v += stride) {
         const float4 a = reinterpret_cast<const float4*>(x)[v], b = reinterpret_cast<const float4*>(y)[v];
-        acc += (double)fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, a.w * b.w)));
+        acc = fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, fmaf(a.w, b.w, acc))));
       }
       i = 4 * n4 + t;
     }
-    for (; i + 3 * stride < n; i += 4 * stride) {
-      const float r = fmaf(x[i], y[i], fmaf(x[i + stride], y[i + stride],
-                                            fmaf(x[i + 2 * stride], y[i + 2 * stride],
-                                                 x[i + 3 * stride] * y[i + 3 * stride])));
-      acc += (double)r;
-    }
-    for (; i < n; i += stride) acc += (double)(x[i] * y[i]);
+    for (; i < n; i += stride) acc = fmaf(x[i], y[i], acc);
+    const double s = block_sum_f(acc);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
   } else {
+    double acc = 0.0;
     for (; i < n; i += stride) acc = fma(x[i], y[i], acc);
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) partial[blockIdx.x] = acc;
   }
-  acc = block_sum(acc);
-  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
 }
 
 __global__ void __launch_bounds__(kRedThreads) k_finalize(const double* __restrict__ partial, int np,
@@ -848,27 +863,23 @@ __global__ void k_scale_by_inv(const E* __restrict__ x, E* __restrict__ y, size_
   for (size_t i = i0 + t; i < n; i += stride) y[i] = x[i] * ff;
 }
 
-// y = (float) x * sigma, with the sum of squares of y: FP32 over runs of 8
-// (stride apart), the runs in FP64.
+// y = (float) x * sigma, with the sum of squares of y: per thread and across
+// a warp in FP32 (terms of one sign; a thread holds about a hundred of a
+// 256^3 field), across warps and blocks in FP64.
 __global__ void __launch_bounds__(kRedThreads) k_convert_sq(const double* __restrict__ x, float* __restrict__ y,
                                                             size_t n, float sigma, const double* __restrict__ sigma_dev,
                                                             double* __restrict__ partial) {
   if (sigma_dev) sigma = (float)*sigma_dev;
-  double acc = 0.0;
+  float acc = 0.f;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
-  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  while (i < n) {
-    float run = 0.f;
 #pragma unroll 4
-    for (int r = 0; r < 8 && i < n; ++r, i += stride) {
-      const float v = d2f_bits(x[i]) * sigma;
-      y[i] = v;
-      run = fmaf(v, v, run);
-    }
-    acc += (double)run;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+    const float v = d2f_bits(x[i]) * sigma;
+    y[i] = v;
+    acc = fmaf(v, v, acc);
   }
-  acc = block_sum(acc);
-  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+  const double s = block_sum_f(acc);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
 // x += a * (double) d: FP32 correction added to an FP64 field

@@ -34,6 +34,24 @@ __device__ __forceinline__ double block_sum(double v) {
   return v;
 }
 
+// Block sum of FP32 per-thread values, result valid in thread 0: each warp
+// adds its 32 values in FP32, the block adds the warps' totals in FP64. The
+// FP64 pipe of GB300 is about 64 times narrower than the FP32 one, so five
+// FP64 shuffle levels over every warp of every block cost microseconds at the
+// end of a reduction over a 256^3 field; this keeps them to one warp per block.
+__device__ __forceinline__ double block_sum_f(float v) {
+  __shared__ double sw[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sw[wid] = (double)v;
+  __syncthreads();
+  double d = (threadIdx.x < (blockDim.x >> 5)) ? sw[threadIdx.x] : 0.0;
+  if (wid == 0) d = warp_sum(d);
+  return d;
+}
+
 // FP64 vectors: one FMA per element and vector.
 template <int NV>
 __global__ void __launch_bounds__(kRedThreads) k_multidot(const double* __restrict__ V, size_t ldv,
@@ -56,7 +74,7 @@ __global__ void __launch_bounds__(kRedThreads) k_multidot(const double* __restri
 }
 
 // FP32 vectors (16-byte aligned, ldv % 4 == 0): 4-vectors, FP32 products
-// summed per thread in FP32 and across threads in FP64.
+// summed per thread and across a warp in FP32, across warps and blocks in FP64.
 template <int NV>
 __global__ void __launch_bounds__(kRedThreads) k_multidot_f32(const float* __restrict__ V, size_t ldv,
                                                               const float* __restrict__ w, size_t n,
@@ -84,7 +102,7 @@ __global__ void __launch_bounds__(kRedThreads) k_multidot_f32(const float* __res
   }
 #pragma unroll
   for (int g = 0; g < NV; ++g) {
-    const double s = block_sum((double)acc[g]);
+    const double s = block_sum_f(acc[g]);
     if (threadIdx.x == 0) partial[g * kRedBlocks + blockIdx.x] = s;
   }
 }
@@ -129,7 +147,7 @@ __global__ void __launch_bounds__(kRedThreads) k_multi_axpy(double* __restrict__
 }
 
 // FP32 vectors (16-byte aligned, ldv % 4 == 0), 4-vectors; the sum of squares
-// is taken per thread in FP32 and across threads in FP64.
+// is taken per thread and across a warp in FP32, across warps in FP64.
 template <int NV, bool SQ>
 __global__ void __launch_bounds__(kRedThreads) k_multi_axpy_f32(float* __restrict__ w, const float* __restrict__ V,
                                                                 size_t ldv, const double* __restrict__ coef,
@@ -171,7 +189,7 @@ __global__ void __launch_bounds__(kRedThreads) k_multi_axpy_f32(float* __restric
     if (SQ) sq = fmaf(wi, wi, sq);
   }
   if (SQ) {
-    const double b = block_sum((double)sq);
+    const double b = block_sum_f(sq);
     if (threadIdx.x == 0) partial_sq[blockIdx.x] = b;
   }
 }
