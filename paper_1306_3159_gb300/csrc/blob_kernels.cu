@@ -111,46 +111,70 @@ __global__ void k_tile_pairs(const int* __restrict__ idx, int n, int ntx, int nt
       }
 }
 
-// Single-block exclusive scan of tile counts; also lists occupied tiles in
-// increasing tile id. meta[0] = number of (tile, blob) pairs, meta[1] = number
-// of occupied tiles.
-__global__ void __launch_bounds__(1024) k_scan_tiles(const int* __restrict__ count, int nt,
-                                                     int* __restrict__ offset, int* __restrict__ active,
-                                                     int* __restrict__ meta) {
-  __shared__ int s_sum[1024], s_act[1024];
-  const int t = threadIdx.x;
-  const int chunk = (nt + blockDim.x - 1) / blockDim.x;
-  const int lo = min(nt, t * chunk), hi = min(nt, lo + chunk);
-  int sum = 0, act = 0;
-  for (int i = lo; i < hi; ++i) {
-    sum += count[i];
-    act += count[i] > 0;
-  }
-  s_sum[t] = sum;
-  s_act[t] = act;
-  __syncthreads();
-  // Hillis-Steele inclusive scan over 1024 entries.
-  for (int o = 1; o < 1024; o <<= 1) {
-    int vs = 0, va = 0;
-    if (t >= o) {
-      vs = s_sum[t - o];
-      va = s_act[t - o];
+// Single-block exclusive scan of n counts into offset[0..n] (offset[n] = the
+// total, also *total), optionally listing the indices with a nonzero count in
+// increasing order into active (their number into *nactive). The counts pass
+// through shared memory in segments of 4096, loaded and stored coalesced;
+// thread t scans entries 4t .. 4t + 3 of a segment, warps scan their threads'
+// sums with shuffles, warp 0 the warps' totals, and a carry joins segments.
+constexpr int kScanSeg = 4096;
+template <bool ACTIVE>
+__global__ void __launch_bounds__(1024) k_scan_counts(const int* __restrict__ count, int n, int* __restrict__ offset,
+                                                      int* __restrict__ total, int* __restrict__ active,
+                                                      int* __restrict__ nactive) {
+  __shared__ int sc[kScanSeg];
+  __shared__ int wsum[32], wact[32];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  int carry = 0, carry_a = 0;
+  for (int base = 0; base < n; base += kScanSeg) {
+    const int len = min(kScanSeg, n - base);
+    for (int k = t; k < kScanSeg; k += blockDim.x) sc[k] = k < len ? count[base + k] : 0;
+    __syncthreads();
+    const int v0 = sc[4 * t], v1 = sc[4 * t + 1], v2 = sc[4 * t + 2], v3 = sc[4 * t + 3];
+    const int sum = (v0 + v1) + (v2 + v3);
+    const int act = ACTIVE ? (v0 > 0) + (v1 > 0) + (v2 > 0) + (v3 > 0) : 0;
+    int is = sum, ia = act;  // inclusive scans over the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int us = __shfl_up_sync(0xffffffffu, is, o), ua = __shfl_up_sync(0xffffffffu, ia, o);
+      if (lane >= o) is += us, ia += ua;
+    }
+    if (lane == 31) wsum[w] = is, wact[w] = ia;
+    __syncthreads();
+    if (w == 0) {
+      int ws = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0, wa = lane < (int)(blockDim.x >> 5) ? wact[lane] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int us = __shfl_up_sync(0xffffffffu, ws, o), ua = __shfl_up_sync(0xffffffffu, wa, o);
+        if (lane >= o) ws += us, wa += ua;
+      }
+      wsum[lane] = ws;  // inclusive over warps
+      wact[lane] = wa;
     }
     __syncthreads();
-    s_sum[t] += vs;
-    s_act[t] += va;
+    const int before = carry + (w > 0 ? wsum[w - 1] : 0) + is - sum;
+    sc[4 * t] = before;
+    sc[4 * t + 1] = before + v0;
+    sc[4 * t + 2] = before + v0 + v1;
+    sc[4 * t + 3] = before + v0 + v1 + v2;
+    if (ACTIVE) {
+      int ra = carry_a + (w > 0 ? wact[w - 1] : 0) + ia - act;
+      const int i0 = base + 4 * t;
+      if (v0 > 0) active[ra++] = i0;
+      if (v1 > 0) active[ra++] = i0 + 1;
+      if (v2 > 0) active[ra++] = i0 + 2;
+      if (v3 > 0) active[ra] = i0 + 3;
+    }
+    carry += wsum[(blockDim.x >> 5) - 1];
+    carry_a += wact[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    for (int k = t; k < len; k += blockDim.x) offset[base + k] = sc[k];
     __syncthreads();
   }
-  int run = s_sum[t] - sum, ra = s_act[t] - act;
-  for (int i = lo; i < hi; ++i) {
-    offset[i] = run;
-    run += count[i];
-    if (count[i] > 0) active[ra++] = i;
-  }
-  if (t == blockDim.x - 1) {
-    offset[nt] = s_sum[t];
-    meta[0] = s_sum[t];
-    meta[1] = s_act[t];
+  if (t == 0) {
+    offset[n] = carry;
+    *total = carry;
+    if (ACTIVE) *nactive = carry_a;
   }
 }
 
@@ -222,34 +246,6 @@ __global__ void __launch_bounds__(512) k_cover(const int* __restrict__ active, c
     const int r = coff[a] + base + __popc(bal & ((1u << lane) - 1u));
     cells[r] = (k * ny + j) * nx + i;
     cell_tile[r] = tile;
-  }
-}
-
-// Exclusive scan of n ints (single block), total into *total.
-__global__ void __launch_bounds__(1024) k_scan_ints(const int* __restrict__ in, int n, int* __restrict__ out,
-                                                    int* __restrict__ total) {
-  __shared__ int s_sum[1024];
-  const int t = threadIdx.x;
-  const int chunk = (n + blockDim.x - 1) / blockDim.x;
-  const int lo = min(n, t * chunk), hi = min(n, lo + chunk);
-  int sum = 0;
-  for (int i = lo; i < hi; ++i) sum += in[i];
-  s_sum[t] = sum;
-  __syncthreads();
-  for (int o = 1; o < 1024; o <<= 1) {
-    const int v = t >= o ? s_sum[t - o] : 0;
-    __syncthreads();
-    s_sum[t] += v;
-    __syncthreads();
-  }
-  int run = s_sum[t] - sum;
-  for (int i = lo; i < hi; ++i) {
-    out[i] = run;
-    run += in[i];
-  }
-  if (t == blockDim.x - 1) {
-    out[n] = s_sum[t];
-    *total = s_sum[t];
   }
 }
 
@@ -355,7 +351,7 @@ void blobs_setup(BlobSet& b, Dims d, double h, const double* q_in, int n, cudaSt
     prof_end(P_SETUP, s, "tile_count");
   }
   prof_begin(P_SETUP, s);
-  k_scan_tiles<<<1, 1024, 0, s>>>(b.tile_count, nt, b.tile_offset, b.active, b.d_meta);
+  k_scan_counts<true><<<1, 1024, 0, s>>>(b.tile_count, nt, b.tile_offset, b.d_meta, b.active, b.d_meta + 1);
   prof_end(P_SETUP, s, "scan_tiles");
   int meta[2];
   IBRD_CUDA(cudaMemcpyAsync(meta, b.d_meta, sizeof(meta), cudaMemcpyDeviceToHost, s));
@@ -387,7 +383,8 @@ void blobs_setup(BlobSet& b, Dims d, double h, const double* q_in, int n, cudaSt
                                              b.nty, b.cell_count, nullptr, nullptr, nullptr);
     prof_end(P_SETUP, s, "cover_count");
     prof_begin(P_SETUP, s);
-    k_scan_ints<<<1, 1024, 0, s>>>(b.cell_count, b.n_active, b.cell_offset, b.d_meta + 2);
+    k_scan_counts<false><<<1, 1024, 0, s>>>(b.cell_count, b.n_active, b.cell_offset, b.d_meta + 2, nullptr,
+                                            nullptr);
     prof_end(P_SETUP, s, "cover_scan");
     int nc = 0;
     IBRD_CUDA(cudaMemcpyAsync(&nc, b.d_meta + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
