@@ -361,6 +361,39 @@ __global__ void __launch_bounds__(kSmallThreads) k_small_start(const double* __r
   }
 }
 
+// Thread 0's part of an Arnoldi step: column j of the Hessenberg matrix from
+// the projections hacc[0..j] and the new norm, the earlier rotations applied,
+// a new Givens rotation formed and applied to the residual vector.
+template <typename S>
+__device__ void small_givens(double* __restrict__ Hs, int ldh, int j, double* __restrict__ cs, double* __restrict__ sn,
+                             double* __restrict__ gvec, const S* hacc, S nrm) {
+  double* h = Hs + (size_t)j * ldh;
+  S hc[kSmallMaxBasis + 1];
+  for (int i = 0; i <= j; ++i) hc[i] = hacc[i];
+  hc[j + 1] = nrm;
+  for (int i = 0; i < j; ++i) {
+    const S c = (S)cs[i], sg = (S)sn[i];
+    const S tt = c * hc[i] + sg * hc[i + 1];
+    hc[i + 1] = -sg * hc[i] + c * hc[i + 1];
+    hc[i] = tt;
+  }
+  const S a = hc[j], b = hc[j + 1];
+  const S r = hypot(a, b);
+  S c = 1, sg = 0;
+  if (r > (S)0) {
+    c = a / r;
+    sg = b / r;
+  }
+  hc[j] = r;
+  hc[j + 1] = 0;
+  for (int i = 0; i <= j + 1; ++i) h[i] = (double)hc[i];
+  cs[j] = (double)c;
+  sn[j] = (double)sg;
+  const S gj = (S)gvec[j];
+  gvec[j + 1] = (double)(-sg * gj);
+  gvec[j] = (double)(c * gj);
+}
+
 // Arnoldi step j: w = U[j+1] holds (J A~^-1 S) U[j]. Classical Gram-Schmidt
 // against U[0..j] (all projections in one pass and one block reduction),
 // repeated once when the norm falls below 1/sqrt(2) of its value before
@@ -462,33 +495,99 @@ __global__ void __launch_bounds__(kSmallThreads) k_small_arnoldi(S* __restrict__
     finish_sums<S>(1, red, nv + 1);
     if (tid == 0) *usum = usum_scale * (double)nv[1];
   }
-  if (tid == 0) {
-    double* h = Hs + (size_t)j * ldh;
-    S hc[kSmallMaxBasis + 1];
-    for (int i = 0; i < nb; ++i) hc[i] = hacc[i];
-    hc[j + 1] = nrm;
-    for (int i = 0; i < j; ++i) {
-      const S c = (S)cs[i], sg = (S)sn[i];
-      const S tt = c * hc[i] + sg * hc[i + 1];
-      hc[i + 1] = -sg * hc[i] + c * hc[i + 1];
-      hc[i] = tt;
-    }
-    const S a = hc[j], b = hc[j + 1];
-    const S r = hypot(a, b);
-    S c = 1, sg = 0;
-    if (r > (S)0) {
-      c = a / r;
-      sg = b / r;
-    }
-    hc[j] = r;
-    hc[j + 1] = 0;
-    for (int i = 0; i <= j + 1; ++i) h[i] = (double)hc[i];
-    cs[j] = (double)c;
-    sn[j] = (double)sg;
-    const S gj = (S)gvec[j];
-    gvec[j + 1] = (double)(-sg * gj);
-    gvec[j] = (double)(c * gj);
+  if (tid == 0) small_givens<S>(Hs, ldh, j, cs, sn, gvec, hacc, nrm);
+}
+
+// Register-resident Arnoldi step for vectors of at most 4 * kSmallThreads
+// entries and NB = j + 1 basis vectors (the inner Schur GMRES of a few
+// thousand blobs): each thread loads its entries t + kSmallThreads k of w
+// and of U[0..NB) once, and the projections, the update, the second pass,
+// the normalisation and the sums run on registers; w is stored once. The
+// per-entry arithmetic and the reductions are those of k_small_arnoldi, in
+// the same order, so the results are the same bit for bit.
+template <typename S, int NB>
+__global__ void __launch_bounds__(kSmallThreads) k_small_arnoldi_r(S* __restrict__ U, int n, double* __restrict__ Hs,
+                                                                    int ldh, double* __restrict__ cs,
+                                                                    double* __restrict__ sn, double* __restrict__ gvec,
+                                                                    const double* __restrict__ wshift,
+                                                                    double* __restrict__ usum, double usum_scale) {
+  constexpr int PER = 4, j = NB - 1;
+  __shared__ S red[32][kSmallMaxBasis + 1];
+  __shared__ S hv[NB + 1], hacc[NB], nv[2];
+  S* w = U + (size_t)NB * n;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, wid = tid >> 5;
+  const S sh = wshift ? (S)*wshift : (S)0;
+  S x[PER], u[NB][PER];
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    const int t = tid + k * nt;
+    const bool in = t < n;
+    x[k] = in ? (wshift ? w[t] - sh : w[t]) : (S)0;
+#pragma unroll
+    for (int v = 0; v < NB; ++v) u[v][k] = in ? U[(size_t)v * n + t] : (S)0;
   }
+  if (tid < NB) hacc[tid] = 0;
+  // hv[v] = <U_v, w> (v < NB) and, with ww, hv[NB] = <w, w>
+  auto dots = [&](bool ww) {
+    S acc[NB + 1];
+#pragma unroll
+    for (int v = 0; v <= NB; ++v) acc[v] = 0;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+#pragma unroll
+      for (int v = 0; v < NB; ++v) acc[v] += u[v][k] * x[k];
+      acc[NB] += x[k] * x[k];
+    }
+#pragma unroll
+    for (int v = 0; v <= NB; ++v) {
+      const S sv = warp_sum_t<S>(acc[v]);
+      if (lane == 0 && (v < NB || ww)) red[wid][v] = sv;
+    }
+    finish_sums<S>(NB + (ww ? 1 : 0), red, hv);
+  };
+  auto update = [&]() {
+    S h[NB];
+#pragma unroll
+    for (int v = 0; v < NB; ++v) h[v] = hv[v];
+    S sq = 0;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+#pragma unroll
+      for (int v = 0; v < NB; ++v) x[k] -= h[v] * u[v][k];
+      sq += x[k] * x[k];
+    }
+    if (tid < NB) hacc[tid] += hv[tid];
+    sq = warp_sum_t<S>(sq);
+    if (lane == 0) red[wid][0] = sq;
+    finish_sums<S>(1, red, nv);
+  };
+  dots(true);
+  const S before = hv[NB];
+  update();
+  if (nv[0] < (S)0.5 * before) {
+    dots(false);
+    update();
+  }
+  const S nrm = sqrt(nv[0]);
+  const S inv = nrm > (S)0 ? (S)1 / nrm : (S)0;
+  S su = 0;
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    const int t = tid + k * nt;
+    if (t < n) {
+      const S y = x[k] * inv;
+      w[t] = y;
+      su += y;
+    }
+  }
+  if (usum) {
+    su = warp_sum_t<S>(su);
+    if (lane == 0) red[wid][0] = su;
+    finish_sums<S>(1, red, nv + 1);
+    if (tid == 0) *usum = usum_scale * (double)nv[1];
+  }
+  if (tid == 0) small_givens<S>(Hs, ldh, j, cs, sn, gvec, hacc, nrm);
 }
 
 template <typename S>
@@ -697,7 +796,21 @@ void launch_small_arnoldi(S* U, int n, int j, double* Hs, int ldh, double* cs, d
                           const double* wshift, double* usum, double usum_scale, cudaStream_t s) {
   if (j + 2 > kSmallMaxBasis) throw CudaError{cudaErrorInvalidValue, "small_arnoldi: basis too large"};
   prof_begin(P_SMALL, s);
-  k_small_arnoldi<S><<<1, kSmallThreads, 0, s>>>(U, n, j, Hs, ldh, cs, sn, gvec, wshift, usum, usum_scale);
+  // registers: up to 6 FP32 or 5 FP64 basis vectors of 4 entries per thread
+  constexpr int kMaxRegBasis = sizeof(S) == 4 ? 6 : 5;
+  if (n <= 4 * kSmallThreads && j + 1 <= kMaxRegBasis) {
+    switch (j + 1) {
+#define IBRD_CASE(k)                                                                                           \
+  case k:                                                                                                      \
+    if constexpr (k <= kMaxRegBasis)                                                                           \
+      k_small_arnoldi_r<S, k><<<1, kSmallThreads, 0, s>>>(U, n, Hs, ldh, cs, sn, gvec, wshift, usum, usum_scale); \
+    break;
+      IBRD_CASE(1) IBRD_CASE(2) IBRD_CASE(3) IBRD_CASE(4) IBRD_CASE(5) IBRD_CASE(6)
+#undef IBRD_CASE
+    }
+  } else {
+    k_small_arnoldi<S><<<1, kSmallThreads, 0, s>>>(U, n, j, Hs, ldh, cs, sn, gvec, wshift, usum, usum_scale);
+  }
   prof_end(P_SMALL, s, "small_arnoldi");
 }
 
