@@ -217,6 +217,7 @@ struct ibrd_grid_s {
   double* partial = nullptr;    // kRedBlocks * kDotGroup
   double* host = nullptr;       // pinned host scalars
   int* dflag = nullptr;
+  unsigned* ticket = nullptr;  // last-CTA ticket of the fused reduction tails (0 between uses)
   // Krylov workspace
   double* V = nullptr;
   double* Z = nullptr;
@@ -705,14 +706,46 @@ size_t ensure_krylov(ibrd_grid g, size_t n, int restart) {
 // pass, fixes h_{j+1,j} and vsc[j+1] (no separate normalisation pass). With the
 // DGKS second pass (threshold eta, decided on the device, its kernels
 // returning at once when it is not needed) the vector is normalised after it.
+// Without the second pass and with at most kDotGroup - 1 basis vectors the
+// reductions of both passes, the norm bookkeeping and the Givens step of
+// column j run in the last CTA of the multi-dot and multi-axpy launches;
+// returns true when the Givens step is done.
 template <typename E>
-void orthogonalize(ibrd_grid g, int j, size_t n, size_t ld, int ldh, double eta) {
+bool orthogonalize(ibrd_grid g, int j, size_t n, size_t ld, int ldh, double eta) {
   E* V = reinterpret_cast<E*>(g->V);
   E* w = V + (size_t)(j + 1) * ld;
   double* hcol = g->H + (size_t)j * ldh;
   double* vs = g->vsc;
   double* sc = g->scal;
   const int nb = j + 1;  // basis vectors V[0..j]
+  if (eta <= 0.0 && nb + 1 <= kDotGroup) {
+    DotTail dt;
+    dt.ticket = g->ticket;
+    dt.out = hcol;
+    dt.scale = vs;
+    dt.nscale = nb;
+    dt.nb = nb;
+    dt.ww = sc + S_TMP;
+    dt.hhat = sc + S_HHAT;
+    dt.hinv = sc + S_HINV;
+    launch_multidot(V, ld, nb + 1, w, n, g->partial, g->s, nullptr, &dt);
+    AxpyTail at;
+    at.ticket = g->ticket;
+    at.rho2 = sc + S_RHO2;
+    at.hhat = sc + S_HHAT;
+    at.hsub = hcol + nb;
+    at.vscale = vs + nb;
+    at.sq = sc + S_SQ;
+    at.H = g->H;
+    at.ldh = ldh;
+    at.j = j;
+    at.cs = g->cs;
+    at.sn = g->sn;
+    at.gvec = g->gvec;
+    at.res = sc + S_RES;
+    launch_multi_axpy(w, V, ld, nb, hcol, -1.0, n, g->partial, g->s, nullptr, vs, sc + S_HINV, &at);
+    return true;
+  }
   // pass 1: dots of V[0..j+1] (the last is <w, w>, unscaled)
   for (int g0 = 0; g0 < nb + 1; g0 += kDotGroup) {
     const int m = std::min(kDotGroup, nb + 1 - g0);
@@ -729,7 +762,7 @@ void orthogonalize(ibrd_grid g, int j, size_t n, size_t ld, int ldh, double eta)
     }
     launch_reduce_partials(g->partial, 1, sc + S_RHO2, g->s);
     launch_gs_norm_fix(sc + S_RHO2, sc + S_HHAT, hcol + nb, vs + nb, sc + S_SQ, g->s);
-    return;
+    return false;
   }
   IBRD_CUDA(cudaMemcpyAsync(sc + S_TMP, hcol + nb, sizeof(double), cudaMemcpyDeviceToDevice, g->s));
   for (int g0 = 0; g0 < nb; g0 += kDotGroup) {
@@ -756,6 +789,7 @@ void orthogonalize(ibrd_grid g, int j, size_t n, size_t ld, int ldh, double eta)
   launch_vec_add_small(hcol, g->hb2, nb, g->s, gate);
   launch_gs_norm_unit(sc + S_SQ, hcol + nb, vs + nb, g->s);
   launch_scale_by_inv<E>(w, w, n, hcol + nb, 1.0, g->s);
+  return false;
 }
 
 struct SolveResult {
@@ -854,8 +888,8 @@ SolveResult fgmres(ibrd_grid g, LinOp<E>& op, const E* b, E* x, size_t n, const 
       E* w = V + (size_t)(j + 1) * ld;
       run_precond<E>(g, op, j, vj, zj, o.graphs != 0);
       op.apply(zj, w);
-      orthogonalize<E>(g, j, n, ld, ldh, o.reorth_eta);
-      launch_givens(g->H, ldh, j, g->cs, g->sn, g->gvec, g->scal + S_RES, g->s);
+      if (!orthogonalize<E>(g, j, n, ld, ldh, o.reorth_eta))
+        launch_givens(g->H, ldh, j, g->cs, g->sn, g->gvec, g->scal + S_RES, g->s);
       // one host read per iteration: residual estimate and the norms
       IBRD_CUDA(cudaMemcpyAsync(g->host, g->scal, sizeof(double) * (S_WAIT + 1), cudaMemcpyDeviceToHost, g->s));
       IBRD_CUDA(cudaStreamSynchronize(g->s));
@@ -1348,8 +1382,8 @@ void capture_refine(ibrd_grid g, LinOp<double>& op64, LinOp<float>& op32, const 
               SG.inner_per_app = g->inner - ia;
             }
             op32.apply(zj, w);
-            orthogonalize<float>(g, j, n, ld, ldh, o.reorth_eta);
-            launch_givens(g->H, ldh, j, g->cs, g->sn, g->gvec, sc + S_RES, g->s);
+            if (!orthogonalize<float>(g, j, n, ld, ldh, o.reorth_eta))
+              launch_givens(g->H, ldh, j, g->cs, g->sn, g->gvec, sc + S_RES, g->s);
             k_g_it_ctrl<<<1, 32, 0, g->s>>>(st, sc, g->ghist, j, m, j + 1 < m ? hs.h[j + 1] : hs.h[j], h_k);
             SG.l_it[j] = mark() - a0 + 1;
           });
@@ -2686,7 +2720,7 @@ void ibrd_grid_destroy(ibrd_grid g) {
   BlobSet& b = g->blobs;
   F(b.q); F(b.idx); F(b.w64); F(b.w32); F(b.tile_count); F(b.tile_offset); F(b.tile_cursor); F(b.tile_blobs);
   F(b.active); F(b.d_meta); F(b.cell_count); F(b.cell_offset); F(b.cells); F(b.cell_tile);
-  F(g->scal); F(g->partial); F(g->dflag); F(g->gst); F(g->ghist);
+  F(g->scal); F(g->partial); F(g->dflag); F(g->ticket); F(g->gst); F(g->ghist);
   if (g->host) cudaFreeHost(g->host);
   F(g->V); F(g->Z); F(g->H); F(g->cs); F(g->sn); F(g->gvec); F(g->yv); F(g->hb2); F(g->vsc); F(g->xs); F(g->bs);
   F(g->ir_r); F(g->ir_r32); F(g->ir_d32);
@@ -2762,6 +2796,8 @@ ibrd_status ibrd_grid_create(ibrd_grid* out, int nx, int ny, int nz, double h, d
     g->partial = dalloc<double>((size_t)kRedBlocks * kDotGroup);
     g->dflag = dalloc<int>(4);
     IBRD_CUDA(cudaMemsetAsync(g->dflag, 0, sizeof(int) * 4, g->s));
+    g->ticket = dalloc<unsigned>(1);
+    IBRD_CUDA(cudaMemsetAsync(g->ticket, 0, sizeof(unsigned), g->s));
     g->tune.wait_err = reinterpret_cast<int*>(g->scal + S_WAIT);
     IBRD_CUDA(cudaMallocHost(&g->host, sizeof(double) * 64));
     IBRD_CUDA(cudaMemsetAsync(g->scal, 0, sizeof(double) * S_COUNT, g->s));

@@ -335,13 +335,35 @@ void launch_interp(const BlobSet& b, Dims d, const T* x, double scale, O* out, c
 
 // ---------------------------------------------------------------- Krylov kernels
 constexpr int kDotGroup = 8;
+// Work that the last CTA of a multi-dot or multi-axpy launch to finish does
+// after the others (it takes the last ticket of a per-handle counter after a
+// fence; no CTA waits for another), so that an FGMRES iteration needs no
+// separate single-CTA launches for it. ticket: 0 between uses, reset by that
+// CTA. The arithmetic is that of the separate kernels it replaces.
+struct DotTail {
+  unsigned* ticket = nullptr;
+  double* out = nullptr;  // out[g] = the sum of partial row g, times scale[g] for g < nscale
+  const double* scale = nullptr;
+  int nscale = 0;
+  int nb = 0;  // > 0: then launch_gs_norm_estimate's work on out[0..nb]
+  double *ww = nullptr, *hhat = nullptr, *hinv = nullptr;
+};
+struct AxpyTail {
+  unsigned* ticket = nullptr;
+  double* rho2 = nullptr;  // the sum of the squares partials, then launch_gs_norm_fix's work
+  const double* hhat = nullptr;
+  double *hsub = nullptr, *vscale = nullptr, *sq = nullptr;
+  double* H = nullptr;  // then launch_givens' work on column j
+  int ldh = 0, j = 0;
+  double *cs = nullptr, *sn = nullptr, *gvec = nullptr, *res = nullptr;
+};
 // partial[g * kRedBlocks + blk] for g < nvec (nvec <= kDotGroup)
 // gate (nullable device scalar): the kernel does nothing when *gate == 0.
 void launch_multidot(const double* V, size_t ldv, int nvec, const double* w, size_t n, double* partial,
-                     cudaStream_t s, const double* gate = nullptr);
+                     cudaStream_t s, const double* gate = nullptr, const DotTail* tail = nullptr);
 // FP32 basis: V and w 16-byte aligned, ldv % 4 == 0.
 void launch_multidot(const float* V, size_t ldv, int nvec, const float* w, size_t n, double* partial,
-                     cudaStream_t s, const double* gate = nullptr);
+                     cudaStream_t s, const double* gate = nullptr, const DotTail* tail = nullptr);
 // out[g] = sum_blk partial[g*kRedBlocks + blk]   (g < nvec), times scale[g]
 // for g < nscale when scale is given
 void launch_reduce_partials(const double* partial, int nvec, double* out, cudaStream_t s,
@@ -350,11 +372,13 @@ void launch_reduce_partials(const double* partial, int nvec, double* out, cudaSt
 // (optional); optional partial sums of squares of the new w.
 void launch_multi_axpy(double* w, const double* V, size_t ldv, int nvec, const double* coef, double sign,
                        size_t n, double* partial_sq, cudaStream_t s, const double* gate = nullptr,
-                       const double* cscale = nullptr, const double* post = nullptr);
+                       const double* cscale = nullptr, const double* post = nullptr,
+                       const AxpyTail* tail = nullptr);
 // FP32 basis: V and w 16-byte aligned, ldv % 4 == 0.
 void launch_multi_axpy(float* w, const float* V, size_t ldv, int nvec, const double* coef, double sign, size_t n,
                        double* partial_sq, cudaStream_t s, const double* gate = nullptr,
-                       const double* cscale = nullptr, const double* post = nullptr);
+                       const double* cscale = nullptr, const double* post = nullptr,
+                       const AxpyTail* tail = nullptr);
 // Gram-Schmidt norm bookkeeping (one-warp kernels): the estimate of the norm
 // after one pass from the projections h[0..nb) and h[nb] = ||w||^2 (writes
 // ||w||^2, the estimate and its reciprocal); after a pass that stored the

@@ -52,11 +52,112 @@ __device__ __forceinline__ double block_sum_f(float v) {
   return d;
 }
 
-// FP64 vectors: one FMA per element and vector.
+// Givens step j on column H[:, j] (ldh = restart + 1): the earlier rotations
+// cs/sn applied, a new one formed and applied to the residual vector gvec;
+// |gvec[j+1]| into *res. One thread.
+__device__ void givens_step(double* __restrict__ H, int ldh, int j, double* __restrict__ cs,
+                            double* __restrict__ sn, double* __restrict__ gvec, double* __restrict__ res) {
+  double* h = H + (size_t)j * ldh;
+  for (int i = 0; i < j; ++i) {
+    const double t = cs[i] * h[i] + sn[i] * h[i + 1];
+    h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
+    h[i] = t;
+  }
+  const double a = h[j], b = h[j + 1];
+  const double r = hypot(a, b);
+  double c = 1.0, s = 0.0;
+  if (r > 0.0) {
+    c = a / r;
+    s = b / r;
+  }
+  h[j] = r;
+  h[j + 1] = 0.0;
+  cs[j] = c;
+  sn[j] = s;
+  const double gj = gvec[j];
+  gvec[j + 1] = -s * gj;
+  gvec[j] = c * gj;
+  *res = fabs(gvec[j + 1]);
+}
+
+// The Gram-Schmidt norm estimate (see k_gs_norm_estimate), by one warp.
+__device__ void gs_norm_estimate_warp(const double* __restrict__ h, int nb, double* __restrict__ ww,
+                                      double* __restrict__ hhat, double* __restrict__ hinv) {
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  for (int i = lane; i < nb; i += 32) s = fma(h[i], h[i], s);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane != 0) return;
+  const double w2 = h[nb];
+  const double e = fmax(w2 - s, 1e-8 * w2);
+  const double r = e > 0.0 ? sqrt(e) : 0.0;
+  *ww = w2;
+  *hhat = r;
+  *hinv = r > 0.0 ? 1.0 / r : 0.0;
+}
+
+// The Gram-Schmidt norm fix (see k_gs_norm_fix) for rho2 = ||stored||^2. One thread.
+__device__ void gs_norm_fix_one(double rho2, const double* __restrict__ hhat, double* __restrict__ hsub,
+                                double* __restrict__ vscale, double* __restrict__ sq) {
+  const double r = sqrt(fmax(rho2, 0.0));
+  const double hs = *hhat * r;
+  *hsub = hs;
+  *vscale = r > 0.0 ? 1.0 / r : 0.0;
+  *sq = hs * hs;
+}
+
+// Whether this CTA is the last of the grid to finish; thread 0 wrote the
+// CTA's partials before the call. A fence orders them before the ticket.
+__device__ __forceinline__ bool last_cta(unsigned* ticket) {
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last) __threadfence();
+  return last;
+}
+
+// Sum of partial row g (kRedBlocks values) in the order of k_reduce_partials;
+// valid in thread 0. Read through L2: other CTAs wrote the row.
+__device__ __forceinline__ double partial_row_sum(const double* partial, int g) {
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < kRedBlocks; i += blockDim.x) acc += __ldcg(partial + (size_t)g * kRedBlocks + i);
+  return block_sum(acc);
+}
+
+// Tail of a multi-dot launch (last CTA): the rows' sums into tail.out, then
+// the norm estimate.
+__device__ void dot_tail(const double* partial, int nv, const DotTail& tail) {
+  for (int g = 0; g < nv; ++g) {
+    const double v = partial_row_sum(partial, g);
+    if (threadIdx.x == 0) tail.out[g] = (g < tail.nscale) ? v * tail.scale[g] : v;
+  }
+  __syncthreads();
+  if (tail.nb > 0 && threadIdx.x < 32) gs_norm_estimate_warp(tail.out, tail.nb, tail.ww, tail.hhat, tail.hinv);
+  if (threadIdx.x == 0) *tail.ticket = 0u;
+}
+
+// Tail of a multi-axpy launch (last CTA): the squares' sum, the norm fix and
+// the Givens step.
+__device__ void axpy_tail(const double* partial_sq, const AxpyTail& tail) {
+  const double v = partial_row_sum(partial_sq, 0);
+  if (threadIdx.x == 0) {
+    *tail.rho2 = v;
+    gs_norm_fix_one(v, tail.hhat, tail.hsub, tail.vscale, tail.sq);
+    givens_step(tail.H, tail.ldh, tail.j, tail.cs, tail.sn, tail.gvec, tail.res);
+    *tail.ticket = 0u;
+  }
+}
+
+// FP64 vectors: one FMA per element and vector.// FP64 vectors: one FMA per element and vector.
 template <int NV>
 __global__ void __launch_bounds__(kRedThreads) k_multidot(const double* __restrict__ V, size_t ldv,
                                                           const double* __restrict__ w, size_t n,
-                                                          double* __restrict__ partial, const double* __restrict__ gate) {
+                                                          double* __restrict__ partial, const double* __restrict__ gate,
+                                                          DotTail tail) {
   if (gate && *gate == 0.0) return;
   double acc[NV];
 #pragma unroll
@@ -71,6 +172,7 @@ __global__ void __launch_bounds__(kRedThreads) k_multidot(const double* __restri
     const double s = block_sum(acc[g]);
     if (threadIdx.x == 0) partial[g * kRedBlocks + blockIdx.x] = s;
   }
+  if (tail.ticket && last_cta(tail.ticket)) dot_tail(partial, NV, tail);
 }
 
 // FP32 vectors (16-byte aligned, ldv % 4 == 0): 4-vectors, FP32 products
@@ -79,7 +181,7 @@ template <int NV>
 __global__ void __launch_bounds__(kRedThreads) k_multidot_f32(const float* __restrict__ V, size_t ldv,
                                                               const float* __restrict__ w, size_t n,
                                                               double* __restrict__ partial,
-                                                              const double* __restrict__ gate) {
+                                                              const double* __restrict__ gate, DotTail tail) {
   if (gate && *gate == 0.0) return;
   float acc[NV];
 #pragma unroll
@@ -105,6 +207,7 @@ __global__ void __launch_bounds__(kRedThreads) k_multidot_f32(const float* __res
     const double s = block_sum_f(acc[g]);
     if (threadIdx.x == 0) partial[g * kRedBlocks + blockIdx.x] = s;
   }
+  if (tail.ticket && last_cta(tail.ticket)) dot_tail(partial, NV, tail);
 }
 
 __global__ void __launch_bounds__(kRedThreads) k_reduce_partials(const double* __restrict__ partial,
@@ -125,7 +228,7 @@ __global__ void __launch_bounds__(kRedThreads) k_multi_axpy(double* __restrict__
                                                             double sign, size_t n, double* __restrict__ partial_sq,
                                                             const double* __restrict__ gate,
                                                             const double* __restrict__ cscale,
-                                                            const double* __restrict__ post) {
+                                                            const double* __restrict__ post, AxpyTail tail) {
   if (gate && *gate == 0.0) return;
   double c[NV];
 #pragma unroll
@@ -143,6 +246,7 @@ __global__ void __launch_bounds__(kRedThreads) k_multi_axpy(double* __restrict__
   if (SQ) {
     sq = block_sum(sq);
     if (threadIdx.x == 0) partial_sq[blockIdx.x] = sq;
+    if (tail.ticket && last_cta(tail.ticket)) axpy_tail(partial_sq, tail);
   }
 }
 
@@ -155,7 +259,7 @@ __global__ void __launch_bounds__(kRedThreads) k_multi_axpy_f32(float* __restric
                                                                 double* __restrict__ partial_sq,
                                                                 const double* __restrict__ gate,
                                                                 const double* __restrict__ cscale,
-                                                                const double* __restrict__ post) {
+                                                                const double* __restrict__ post, AxpyTail tail) {
   if (gate && *gate == 0.0) return;
   float c[NV];
 #pragma unroll
@@ -191,33 +295,14 @@ __global__ void __launch_bounds__(kRedThreads) k_multi_axpy_f32(float* __restric
   if (SQ) {
     const double b = block_sum_f(sq);
     if (threadIdx.x == 0) partial_sq[blockIdx.x] = b;
+    if (tail.ticket && last_cta(tail.ticket)) axpy_tail(partial_sq, tail);
   }
 }
 
 __global__ void k_givens(double* __restrict__ H, int ldh, int j, double* __restrict__ cs, double* __restrict__ sn,
                          double* __restrict__ gvec, double* __restrict__ res) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double* h = H + (size_t)j * ldh;
-  for (int i = 0; i < j; ++i) {
-    const double t = cs[i] * h[i] + sn[i] * h[i + 1];
-    h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
-    h[i] = t;
-  }
-  const double a = h[j], b = h[j + 1];
-  const double r = hypot(a, b);
-  double c = 1.0, s = 0.0;
-  if (r > 0.0) {
-    c = a / r;
-    s = b / r;
-  }
-  h[j] = r;
-  h[j + 1] = 0.0;
-  cs[j] = c;
-  sn[j] = s;
-  const double gj = gvec[j];
-  gvec[j + 1] = -s * gj;
-  gvec[j] = c * gj;
-  *res = fabs(gvec[j + 1]);
+  givens_step(H, ldh, j, cs, sn, gvec, res);
 }
 
 __global__ void k_backsolve(const double* __restrict__ H, int ldh, int k, const double* __restrict__ gvec,
@@ -260,17 +345,7 @@ __global__ void k_sqrt_scalar(const double* __restrict__ src, double* __restrict
 // w = 0). One warp.
 __global__ void k_gs_norm_estimate(const double* __restrict__ h, int nb, double* __restrict__ ww,
                                    double* __restrict__ hhat, double* __restrict__ hinv) {
-  double s = 0.0;
-  for (int i = threadIdx.x; i < nb; i += 32) s = fma(h[i], h[i], s);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (threadIdx.x != 0) return;
-  const double w2 = h[nb];
-  const double e = fmax(w2 - s, 1e-8 * w2);
-  const double r = e > 0.0 ? sqrt(e) : 0.0;
-  *ww = w2;
-  *hhat = r;
-  *hinv = r > 0.0 ? 1.0 / r : 0.0;
+  gs_norm_estimate_warp(h, nb, ww, hhat, hinv);
 }
 
 // After the pass wrote the new basis vector scaled by 1 / hhat with squared
@@ -278,12 +353,7 @@ __global__ void k_gs_norm_estimate(const double* __restrict__ h, int nb, double*
 // unscaled vector), the stored vector's inverse norm, and h_{j+1,j}^2 into sq.
 __global__ void k_gs_norm_fix(const double* __restrict__ rho2, const double* __restrict__ hhat,
                               double* __restrict__ hsub, double* __restrict__ vscale, double* __restrict__ sq) {
-  if (threadIdx.x != 0) return;
-  const double r = sqrt(fmax(*rho2, 0.0));
-  const double hs = *hhat * r;
-  *hsub = hs;
-  *vscale = r > 0.0 ? 1.0 / r : 0.0;
-  *sq = hs * hs;
+  if (threadIdx.x == 0) gs_norm_fix_one(*rho2, hhat, hsub, vscale, sq);
 }
 
 // h_{j+1,j} = sqrt(sq), for a basis vector that is then normalised exactly
@@ -607,8 +677,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_small_finish(const S* __restr
     }
   }
   __syncthreads();
-  S s = 0;
-  for (int t = tid; t < n; t += nt) {
+  auto combo = [&](int t) {
     S v = 0;
     if (k <= kSmallRegBasis) {
       S u[kSmallRegBasis];
@@ -620,14 +689,41 @@ __global__ void __launch_bounds__(kSmallThreads) k_small_finish(const S* __restr
     } else {
       for (int l = 0; l < k; ++l) v += y[l] * U[(size_t)l * n + t];
     }
+    return v;
+  };
+  auto mean_of = [&](S s) {
+    s = warp_sum_t<S>(s);
+    if (lane == 0) red[wid][0] = s;
+    finish_sums<S>(1, red, out);
+    return (double)out[0] / n;
+  };
+  if (n <= 4 * nt) {
+    // short vectors (the inner Schur GMRES of a few thousand blobs): the
+    // combination stays in registers until the mean is known, x is written once
+    S v[4];
+    S s = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int t = tid + q * nt;
+      v[q] = t < n ? combo(t) : (S)0;
+      s += v[q];
+    }
+    const double mean = project_mean ? mean_of(s) : 0.0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int t = tid + q * nt;
+      if (t < n) x[t] = project_mean ? (double)v[q] - mean : (double)v[q];
+    }
+    return;
+  }
+  S s = 0;
+  for (int t = tid; t < n; t += nt) {
+    const S v = combo(t);
     x[t] = (double)v;
     s += v;
   }
   if (project_mean) {
-    s = warp_sum_t<S>(s);
-    if (lane == 0) red[wid][0] = s;
-    finish_sums<S>(1, red, out);
-    const double mean = (double)out[0] / n;
+    const double mean = mean_of(s);
     for (int t = tid; t < n; t += nt) x[t] -= mean;
   }
 }
@@ -635,12 +731,13 @@ __global__ void __launch_bounds__(kSmallThreads) k_small_finish(const S* __restr
 }  // namespace
 
 void launch_multidot(const double* V, size_t ldv, int nvec, const double* w, size_t n, double* partial,
-                     cudaStream_t s, const double* gate) {
+                     cudaStream_t s, const double* gate, const DotTail* tail) {
+  const DotTail t = tail ? *tail : DotTail{};
   if (nvec < 1 || nvec > kDotGroup) return;
   prof_begin(P_DOT, s);
   switch (nvec) {
 #define IBRD_CASE(k) \
-  case k: k_multidot<k><<<kRedBlocks, kRedThreads, 0, s>>>(V, ldv, w, n, partial, gate); break;
+  case k: k_multidot<k><<<kRedBlocks, kRedThreads, 0, s>>>(V, ldv, w, n, partial, gate, t); break;
     IBRD_CASE(1) IBRD_CASE(2) IBRD_CASE(3) IBRD_CASE(4) IBRD_CASE(5) IBRD_CASE(6) IBRD_CASE(7) IBRD_CASE(8)
 #undef IBRD_CASE
     default: return;
@@ -649,13 +746,14 @@ void launch_multidot(const double* V, size_t ldv, int nvec, const double* w, siz
 }
 
 void launch_multidot(const float* V, size_t ldv, int nvec, const float* w, size_t n, double* partial,
-                     cudaStream_t s, const double* gate) {
+                     cudaStream_t s, const double* gate, const DotTail* tail) {
+  const DotTail t = tail ? *tail : DotTail{};
   if (nvec < 1 || nvec > kDotGroup) return;
   if (ldv % 4 != 0 || !aligned16(V) || !aligned16(w)) throw CudaError{cudaErrorMisalignedAddress, "multidot_f32"};
   prof_begin(P_DOT, s);
   switch (nvec) {
 #define IBRD_CASE(k) \
-  case k: k_multidot_f32<k><<<kRedBlocks, kRedThreads, 0, s>>>(V, ldv, w, n, partial, gate); break;
+  case k: k_multidot_f32<k><<<kRedBlocks, kRedThreads, 0, s>>>(V, ldv, w, n, partial, gate, t); break;
     IBRD_CASE(1) IBRD_CASE(2) IBRD_CASE(3) IBRD_CASE(4) IBRD_CASE(5) IBRD_CASE(6) IBRD_CASE(7) IBRD_CASE(8)
 #undef IBRD_CASE
     default: return;
@@ -692,7 +790,8 @@ void launch_gs_norm_unit(const double* sq, double* hsub, double* vscale, cudaStr
 
 void launch_multi_axpy(double* w, const double* V, size_t ldv, int nvec, const double* coef, double sign, size_t n,
                        double* partial_sq, cudaStream_t s, const double* gate, const double* cscale,
-                       const double* post) {
+                       const double* post, const AxpyTail* tail) {
+  const AxpyTail t = (tail && partial_sq) ? *tail : AxpyTail{};
   if (nvec < 1 || nvec > kDotGroup) return;
   prof_begin(P_AXPY, s);
   if (partial_sq) {
@@ -700,7 +799,7 @@ void launch_multi_axpy(double* w, const double* V, size_t ldv, int nvec, const d
 #define IBRD_CASE(k)                                                                                     \
   case k:                                                                                                \
     k_multi_axpy<k, true><<<kRedBlocks, kRedThreads, 0, s>>>(w, V, ldv, coef, sign, n, partial_sq, gate, \
-                                                             cscale, post);                              \
+                                                             cscale, post, t);                           \
     break;
       IBRD_CASE(1) IBRD_CASE(2) IBRD_CASE(3) IBRD_CASE(4) IBRD_CASE(5) IBRD_CASE(6) IBRD_CASE(7) IBRD_CASE(8)
 #undef IBRD_CASE
@@ -711,7 +810,7 @@ void launch_multi_axpy(double* w, const double* V, size_t ldv, int nvec, const d
 #define IBRD_CASE(k)                                                                                      \
   case k:                                                                                                 \
     k_multi_axpy<k, false><<<kRedBlocks, kRedThreads, 0, s>>>(w, V, ldv, coef, sign, n, nullptr, gate,   \
-                                                              cscale, post);                              \
+                                                              cscale, post, t);                           \
     break;
       IBRD_CASE(1) IBRD_CASE(2) IBRD_CASE(3) IBRD_CASE(4) IBRD_CASE(5) IBRD_CASE(6) IBRD_CASE(7) IBRD_CASE(8)
 #undef IBRD_CASE
@@ -723,7 +822,8 @@ void launch_multi_axpy(double* w, const double* V, size_t ldv, int nvec, const d
 
 void launch_multi_axpy(float* w, const float* V, size_t ldv, int nvec, const double* coef, double sign, size_t n,
                        double* partial_sq, cudaStream_t s, const double* gate, const double* cscale,
-                       const double* post) {
+                       const double* post, const AxpyTail* tail) {
+  const AxpyTail t = (tail && partial_sq) ? *tail : AxpyTail{};
   if (nvec < 1 || nvec > kDotGroup) return;
   if (ldv % 4 != 0 || !aligned16(V) || !aligned16(w)) throw CudaError{cudaErrorMisalignedAddress, "multi_axpy_f32"};
   prof_begin(P_AXPY, s);
@@ -732,7 +832,7 @@ void launch_multi_axpy(float* w, const float* V, size_t ldv, int nvec, const dou
 #define IBRD_CASE(k)                                                                                           \
   case k:                                                                                                      \
     k_multi_axpy_f32<k, true><<<kRedBlocks, kRedThreads, 0, s>>>(w, V, ldv, coef, sign, n, partial_sq, gate, \
-                                                                 cscale, post);                              \
+                                                                 cscale, post, t);                           \
     break;
       IBRD_CASE(1) IBRD_CASE(2) IBRD_CASE(3) IBRD_CASE(4) IBRD_CASE(5) IBRD_CASE(6) IBRD_CASE(7) IBRD_CASE(8)
 #undef IBRD_CASE
@@ -743,7 +843,7 @@ void launch_multi_axpy(float* w, const float* V, size_t ldv, int nvec, const dou
 #define IBRD_CASE(k)                                                                                            \
   case k:                                                                                                       \
     k_multi_axpy_f32<k, false><<<kRedBlocks, kRedThreads, 0, s>>>(w, V, ldv, coef, sign, n, nullptr, gate, \
-                                                                  cscale, post);                             \
+                                                                  cscale, post, t);                          \
     break;
       IBRD_CASE(1) IBRD_CASE(2) IBRD_CASE(3) IBRD_CASE(4) IBRD_CASE(5) IBRD_CASE(6) IBRD_CASE(7) IBRD_CASE(8)
 #undef IBRD_CASE
