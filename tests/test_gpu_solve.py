@@ -100,6 +100,33 @@ def test_reaction_small(ibrd, small, precision, tol, err, alpha):
     assert abs(info["sum_lambda"] - u_ref.sum()) < err * abs(u_ref.sum())
 
 
+@pytest.mark.parametrize("precision", [0, 2])
+def test_single_pass_gram_schmidt(ibrd, small, precision):
+    """Classical Gram-Schmidt without the second pass (reorth_eta = 0): each
+    new basis vector is scaled inside the pass that subtracts its projections
+    and its exact norm recorded as the stored vector's scale; up to 7 basis
+    vectors the reductions, that bookkeeping and the Givens step run in the
+    last CTA of the two Gram-Schmidt launches, from the eighth on in separate
+    kernels. The FP64 solves to 1e-12 run one long restart cycle and so take
+    both; both modes reach the oracle's solutions at 1e-11."""
+    w, M = small
+    c_ref, lam_ref, _ = direct.solve_saddle(w.q, w.g, w.h, w.chi, 0.0, M=M)
+    g = _grid(ibrd, w)
+    tol = max(1e-12, floor_tol(c_ref, w.g, w.h, w.chi, 0.0))
+    c, lam, info = g.solve_saddle(dev(w.g), tol=tol, precision=precision, max_iter=400, reorth_eta=0.0,
+                                  precond=0)
+    assert info["rel_residual"] <= tol and info["reorths"] == 0
+    assert rel_err(host(c), c_ref) < 1e-11 and rel_err(host(lam), lam_ref) < 1e-11
+    cr_ref, u_ref, _ = direct.solve_reaction(w.q, w.kappa, w.g, w.h, w.chi, 0.0, M=M)
+    tol = max(1e-12, floor_tol(cr_ref, w.g, w.h, w.chi, 0.0))
+    cr, info = g.solve_reaction(dev(w.kappa), dev(w.g), tol=tol, precision=precision, max_iter=400,
+                                reorth_eta=0.0, nu1=1, nu2=1)
+    assert info["rel_residual"] <= tol and info["reorths"] == 0
+    assert rel_err(host(cr), cr_ref) < 1e-11
+    if precision == 0:
+        assert info["outer_iters"] >= 9, info["outer_iters"]
+
+
 def test_saddle_alpha_positive_nonunit_scales(ibrd):
     """alpha > 0, h != 1, chi != 1, zeta != 1 and a nonzero f."""
     dims, h, chi, alpha, zeta = (24, 16, 20), 0.5, 1.7, 0.8, 0.3
