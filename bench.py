@@ -252,12 +252,16 @@ def run_ours(args):
                   p.ibrd_default_opts(tol=tol, precision=pr, max_iter=3000, **ks))
             for arm, (pr, kr, ks) in settings.items()}
 
-    def step(precision, concurrent=True, download=False):
-        # each item sets its handle's blobs, solves and (end to end) downloads
-        # its solution, so that one solve's download overlaps the other solve
+    def step(precision, concurrent=True, download=False, set_blobs=True):
+        # each item sets its handle's blobs (unless the caller has), solves
+        # and (end to end) downloads its solution, so that one solve's
+        # download overlaps the other solve
         o_r, o_s = opts[precision]
-        items = [dict(kind="reaction", grid=grid_r.handle, kappa=k_d, rhs=g_d, c=c_r, opts=o_r, q=q_d),
-                 dict(kind="saddle", grid=grid_s.handle, rhs=g_d, c=c_s, lam=lam, opts=o_s, q=q_d)]
+        items = [dict(kind="reaction", grid=grid_r.handle, kappa=k_d, rhs=g_d, c=c_r, opts=o_r),
+                 dict(kind="saddle", grid=grid_s.handle, rhs=g_d, c=c_s, lam=lam, opts=o_s)]
+        if set_blobs:
+            for it in items:
+                it["q"] = q_d
         if download:
             items[0]["c_host"] = out_cr
             items[1]["c_host"], items[1]["lam_host"] = out_cs, out_l
@@ -268,19 +272,29 @@ def run_ours(args):
         infos[precision] = (out[0], out[1])
 
     copy_stream = torch.cuda.Stream()
+    from concurrent.futures import ThreadPoolExecutor
+    setup_pool = ThreadPoolExecutor(max_workers=2)
 
     def step_e2e(precision):
-        # host -> device on a copy stream that both solver streams wait for;
-        # each solution comes down on its solver stream inside its item
+        # host -> device on a copy stream: the positions and rates first, so
+        # that both handles' blob setup (ibrd_set_blobs, from two host
+        # threads) runs while the source field is still on its way; the solves
+        # wait for the source; each solution comes down on its solver stream
+        # inside its item
         with torch.cuda.stream(copy_stream):
             q_d.copy_(q_h, non_blocking=True)
             k_d.copy_(k_h, non_blocking=True)
+            ev_q = torch.cuda.Event()
+            ev_q.record(copy_stream)
             g_d.copy_(g_h, non_blocking=True)
-        ev_in = torch.cuda.Event()
-        ev_in.record(copy_stream)
-        stream_r.wait_event(ev_in)
-        stream_s.wait_event(ev_in)
-        step(precision, download=True)
+            ev_g = torch.cuda.Event()
+            ev_g.record(copy_stream)
+        stream_r.wait_event(ev_q)
+        stream_s.wait_event(ev_q)
+        list(setup_pool.map(lambda gr: gr.set_blobs(q_d), grids))
+        stream_r.wait_event(ev_g)
+        stream_s.wait_event(ev_g)
+        step(precision, download=True, set_blobs=False)
 
     def barrier():
         rank_barrier(world)
