@@ -57,6 +57,30 @@ def test_neighbours_exact(ibrd, n, side, R):
         assert np.abs(dist[i, :cnt[i]] - rr[i]).max(initial=0.0) < 4e-6 * side
 
 
+@pytest.mark.parametrize("box,R", [((40.0, 30.0, 50.0), 9.0), ((40.0, 18.0, 50.0), 8.5)])
+def test_neighbours_non_cubic_box_and_shifted_positions(ibrd, box, R):
+    """A box with three different sides (4 x 3 x 5 cells of the cell list; with
+    18 along y only two fit, so all pairs are screened) and blobs given
+    anywhere within a few box lengths of the origin: the lists are the FP64
+    minimum-image definition's, and so is the forward pass."""
+    box = np.array(box)
+    q = rsa_positions(150, tuple(box), 1.0, 2.0, 17)
+    rng = np.random.default_rng(4)
+    q = q + box * rng.integers(-3, 4, size=q.shape)
+    m = ibrd.GNN(R, 64)
+    cnt, idx, dist = (host(t) for t in m.neighbours(dev(q), box))
+    nb, rr = gnn.neighbours(q, box, R)
+    for i in range(len(q)):
+        assert cnt[i] == len(nb[i])
+        assert list(idx[i, :cnt[i]]) == list(nb[i])
+        assert np.abs(dist[i, :cnt[i]] - rr[i]).max(initial=0.0) < 4e-6 * box.max()
+    th = _theta(3)
+    m.set_params(th.astype(np.float32))
+    y = host(m.forward(dev(q), box)).astype(np.float64)
+    y_ref, _ = gnn.forward(th, q, box, R)
+    assert np.abs(y - y_ref).max() < 2e-5 * max(1.0, np.abs(y_ref).max())
+
+
 def test_forward_loss_gradient_and_adam(ibrd):
     import torch
     q, box = _config(300, 48, 5)
