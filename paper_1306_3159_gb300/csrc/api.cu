@@ -503,7 +503,7 @@ void vcycle(ibrd_grid g, const T* b, T* x, bool zero, double shift, int nu1, int
   const double* bshift = nullptr;
   if (singular) {
     if (!bmean) {
-      launch_sum<T>(b, d.n(), g->partial, g->scal + S_MEAN, 1.0 / (double)d.n(), g->s);
+      launch_sum<T>(b, d.n(), g->partial, g->scal + S_MEAN, 1.0 / (double)d.n(), g->s, g->ticket);
       bmean = g->scal + S_MEAN;
     }
     bshift = bmean;
@@ -515,7 +515,7 @@ void vcycle(ibrd_grid g, const T* b, T* x, bool zero, double shift, int nu1, int
     if (np > 0)
       launch_finalize(g->partial, np, mout, 1.0 / (double)d.n(), g->s);
     else
-      launch_sum<T>(x, d.n(), g->partial, mout, 1.0 / (double)d.n(), g->s);
+      launch_sum<T>(x, d.n(), g->partial, mout, 1.0 / (double)d.n(), g->s, g->ticket);
     if (xm == XMean::Project) launch_sub_scalar<T>(x, d.n(), mout, g->s);
   }
   g->vcycles++;
@@ -831,7 +831,7 @@ SolveResult fgmres(ibrd_grid g, LinOp<E>& op, const E* b, E* x, size_t n, const 
   const bool known = b_sq && b_norm >= 0.0;
   double bnorm = b_norm;
   if (!known) {
-    launch_dot<E>(b, b, n, g->partial, g->scal + S_BB, 1.0, g->s);
+    launch_dot<E>(b, b, n, g->partial, g->scal + S_BB, 1.0, g->s, g->ticket);
     bnorm = std::sqrt(host_scalar(g, S_BB));
   }
   if (!std::isfinite(bnorm)) {
@@ -858,7 +858,7 @@ SolveResult fgmres(ibrd_grid g, LinOp<E>& op, const E* b, E* x, size_t n, const 
     } else {
       op.residual(b, x, V);
     }
-    launch_dot<E>(V, V, n, g->partial, g->scal + S_TMP2, 1.0, g->s);
+    launch_dot<E>(V, V, n, g->partial, g->scal + S_TMP2, 1.0, g->s, g->ticket);
     launch_sqrt_scalar(g->scal + S_TMP2, g->scal + S_NORM, g->s);
     beta = std::sqrt(host_scalar(g, S_TMP2));
   }
@@ -933,7 +933,7 @@ SolveResult fgmres(ibrd_grid g, LinOp<E>& op, const E* b, E* x, size_t n, const 
     }
     // true residual
     op.residual(b, x, V);
-    launch_dot<E>(V, V, n, g->partial, g->scal + S_TMP2, 1.0, g->s);
+    launch_dot<E>(V, V, n, g->partial, g->scal + S_TMP2, 1.0, g->s, g->ticket);
     launch_sqrt_scalar(g->scal + S_TMP2, g->scal + S_NORM, g->s);
     beta = std::sqrt(host_scalar(g, S_TMP2));
     if (breakdown && beta / bnorm > tol) {
@@ -972,7 +972,7 @@ SolveResult refine(ibrd_grid g, LinOp<double>& op64, LinOp<float>& op32, const d
     g->ir_cap = n;
   }
   double* r = g->ir_r;
-  launch_dot<double>(b, b, n, g->partial, g->scal + S_BB, 1.0, g->s);
+  launch_dot<double>(b, b, n, g->partial, g->scal + S_BB, 1.0, g->s, g->ticket);
   const double bnorm = std::sqrt(host_scalar(g, S_BB));
   if (!std::isfinite(bnorm)) {
     R.st = IBRD_ERR_NONFINITE;
@@ -989,7 +989,7 @@ SolveResult refine(ibrd_grid g, LinOp<double>& op64, LinOp<float>& op32, const d
   auto set_sigma = [&](double expect) { sigma = std::ldexp(1.0, -std::ilogb(std::max(expect, 1e-300))); };
   double r32norm = 0.0;  // ||sigma r|| of the FP32 right-hand side, ||.||^2 kept in S_TMP2
   auto to_f32 = [&](const double* v) {
-    launch_convert_sq(v, g->ir_r32, n, sigma, g->partial, g->scal + S_TMP2, g->s);
+    launch_convert_sq(v, g->ir_r32, n, sigma, g->partial, g->scal + S_TMP2, g->s, g->ticket);
     r32norm = std::sqrt(host_scalar(g, S_TMP2));
     return r32norm / sigma;
   };
@@ -1341,14 +1341,14 @@ void capture_refine(ibrd_grid g, LinOp<double>& op64, LinOp<float>& op32, const 
   {
     cudaGraphConditionalHandle h_ref = C.handle();
     long long t0 = mark();
-    launch_dot<double>(b, b, n, g->partial, sc + S_BB, 1.0, g->s);
+    launch_dot<double>(b, b, n, g->partial, sc + S_BB, 1.0, g->s, g->ticket);
     k_g_init<<<1, 32, 0, g->s>>>(st, sc, zero_guess ? 1 : 0, 0, h_ref);
     if (zero_guess) {
       IBRD_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, g->s));
-      launch_convert_sq(b, g->ir_r32, n, &st->sigma, g->partial, sc + S_TMP2, g->s);
+      launch_convert_sq(b, g->ir_r32, n, &st->sigma, g->partial, sc + S_TMP2, g->s, g->ticket);
     } else {
       op64.residual(b, x, g->ir_r);
-      launch_convert_sq(g->ir_r, g->ir_r32, n, &st->sigma, g->partial, sc + S_TMP2, g->s);
+      launch_convert_sq(g->ir_r, g->ir_r32, n, &st->sigma, g->partial, sc + S_TMP2, g->s, g->ticket);
       k_g_init<<<1, 32, 0, g->s>>>(st, sc, 0, 1, h_ref);
     }
     SG.l_init = mark() - t0 + (zero_guess ? 1 : 2);
@@ -1400,7 +1400,7 @@ void capture_refine(ibrd_grid g, LinOp<double>& op64, LinOp<float>& op32, const 
         C.conditional(h_true, cudaGraphCondTypeIf, 1, [&](int) {
           const long long q0 = mark();
           op32.residual(g->ir_r32, g->ir_d32, V);
-          launch_dot<float>(V, V, n, g->partial, sc + S_TMP2, 1.0, g->s);
+          launch_dot<float>(V, V, n, g->partial, sc + S_TMP2, 1.0, g->s, g->ticket);
           launch_sqrt_scalar(sc + S_TMP2, sc + S_NORM, g->s);
           k_g_cyc_ctrl2<<<1, 32, 0, g->s>>>(st, sc, h_cyc);
           SG.l_true = mark() - q0 + 1;
@@ -1412,7 +1412,7 @@ void capture_refine(ibrd_grid g, LinOp<double>& op64, LinOp<float>& op32, const 
         launch_add_divided(&st->sigma, g->ir_d32, x, n, g->s);
         op64.residual(b, x, g->ir_r);
         k_g_sigma<<<1, 32, 0, g->s>>>(st);
-        launch_convert_sq(g->ir_r, g->ir_r32, n, &st->sigma, g->partial, sc + S_TMP2, g->s);
+        launch_convert_sq(g->ir_r, g->ir_r32, n, &st->sigma, g->partial, sc + S_TMP2, g->s, g->ticket);
         k_g_ref_ctrl<<<1, 32, 0, g->s>>>(st, sc, h_ref);
         // a refinement step: its begin and gate kernels, this body and its two control kernels
         SG.l_ref = mark() - u0 + 4;
@@ -1713,7 +1713,7 @@ struct SaddleOp : LinOp<E> {
     const double* bmean = nullptr;
     const double* xshift = nullptr;
     if (singular) {
-      launch_convert_sum<E, T>(vc, gt, nc, g->partial, sc + S_GSUM, sc + S_G32SUM, g->s);
+      launch_convert_sum<E, T>(vc, gt, nc, g->partial, sc + S_GSUM, sc + S_G32SUM, g->s, g->ticket);
       // zeta S (lambda-bar 1) = (V / (N N_c)) sum(g) S 1; its total is sum(g)
       launch_spread_const<T>(g->blobs, g->d, sc + S_GSUM, -volume / ((double)N * (double)nc) * ih3, gt, g->s);
       prof_begin(P_SMALL, g->s);
@@ -1738,7 +1738,7 @@ struct SaddleOp : LinOp<E> {
     if (o.precond == IBRD_PRECOND_DIAG) {
       launch_convert<double, double>(rhs, lam, N, 1.0 / g->gamma_diag, nullptr, g->s);
       if (singular) {
-        launch_sum<double>(lam, N, g->partial, sc + S_TMP, 1.0 / N, g->s);
+        launch_sum<double>(lam, N, g->partial, sc + S_TMP, 1.0 / N, g->s, g->ticket);
         launch_sub_scalar<double>(lam, N, sc + S_TMP, g->s);
       }
     } else {
@@ -1756,8 +1756,7 @@ struct SaddleOp : LinOp<E> {
       if (blk) {
         double* prhs = g->nv[2];
         launch_block_apply<double, double>(g->blk_idx, g->blk_cnt, g->blk_val, rhs, nullptr, N, prhs, g->partial,
-                                           g->s);
-        launch_finalize(g->partial, kBlockApplyBlocks, sc + S_PMEAN, 1.0 / N, g->s);
+                                           g->s, g->ticket, sc + S_PMEAN, 1.0 / N);
         launch_sub_scalar<double>(prhs, N, sc + S_PMEAN, g->s);
         start = prhs;
       }
@@ -1775,8 +1774,7 @@ struct SaddleOp : LinOp<E> {
           E* w = reinterpret_cast<E*>(g->nv[2]);
           launch_interp<T, E>(g->blobs, g->d, fx, 1.0, w, g->s);
           launch_block_apply<E, E>(g->blk_idx, g->blk_cnt, g->blk_val, w, wshift, N, U + (size_t)(j + 1) * N,
-                                   g->partial, g->s);
-          launch_finalize(g->partial, kBlockApplyBlocks, sc + S_PMEAN, 1.0 / N, g->s);
+                                   g->partial, g->s, g->ticket, sc + S_PMEAN, 1.0 / N);
           wshift = sc + S_PMEAN;
         } else {
           launch_interp<T, E>(g->blobs, g->d, fx, 1.0, U + (size_t)(j + 1) * N, g->s);
@@ -1799,7 +1797,7 @@ struct SaddleOp : LinOp<E> {
       double* t = g->nv[2];
       launch_interp<T>(g->blobs, g->d, cs, 1.0, t, g->s);
       launch_nvec_affine(t, t, N, -1.0, nullptr, vf, 1.0 / xi, g->s);
-      launch_sum<double>(t, N, g->partial, sc + S_CBAR, 1.0 / N, g->s);
+      launch_sum<double>(t, N, g->partial, sc + S_CBAR, 1.0 / N, g->s, g->ticket);
       launch_convert<double, E>(lam, zl, N, 1.0, sc + S_LBAR, g->s);
       launch_convert<T, E>(cs, zc, nc, 1.0, sc + S_CBAR, g->s);
     } else {
@@ -1829,8 +1827,8 @@ void saddle_warm_start(ibrd_grid g, const ibrd_solve_opts& o, const double* b, d
   const double h3 = g->h * g->h * g->h;
   double* sc = g->scal;
   double* lam = x + nc;
-  launch_sum<double>(b, nc, g->partial, sc + S_TMP, h3 / o.zeta, g->s);
-  if (mode == 2) launch_sum<double>(lam, N, g->partial, sc + S_TMP2, 1.0, g->s);
+  launch_sum<double>(b, nc, g->partial, sc + S_TMP, h3 / o.zeta, g->s, g->ticket);
+  if (mode == 2) launch_sum<double>(lam, N, g->partial, sc + S_TMP2, 1.0, g->s, g->ticket);
   IBRD_CUDA(cudaMemcpyAsync(g->host, sc + S_TMP, sizeof(double) * 2, cudaMemcpyDeviceToHost, g->s));
   IBRD_CUDA(cudaStreamSynchronize(g->s));
   const double total = g->host[0], lsum = mode == 2 ? g->host[1] : 0.0;
@@ -1852,7 +1850,7 @@ void saddle_warm_start(ibrd_grid g, const ibrd_solve_opts& o, const double* b, d
     double* t = g->nv[2];
     launch_interp<T>(g->blobs, g->d, ct, 1.0, t, g->s);
     launch_nvec_affine(t, t, N, -1.0, nullptr, b + nc, 1.0 / o.xi, g->s);
-    launch_sum<double>(t, N, g->partial, sc + S_CBAR, 1.0 / N, g->s);
+    launch_sum<double>(t, N, g->partial, sc + S_CBAR, 1.0 / N, g->s, g->ticket);
     launch_convert<T, double>(ct, x, nc, 1.0, sc + S_CBAR, g->s);
   } else {
     launch_convert<T, double>(ct, x, nc, 1.0, nullptr, g->s);
@@ -2242,12 +2240,12 @@ void report(ibrd_grid g, const double* c, const double* lam_or_null, const doubl
   if (!info) return;
   const size_t nc = g->d.n();
   const int N = g->blobs.n;
-  launch_sum<double>(c, nc, g->partial, g->scal + S_TMP, 1.0 / (double)nc, g->s);
+  launch_sum<double>(c, nc, g->partial, g->scal + S_TMP, 1.0 / (double)nc, g->s, g->ticket);
   if (lam_or_null) {
-    launch_sum<double>(lam_or_null, N, g->partial, g->scal + S_TMP2, 1.0, g->s);
+    launch_sum<double>(lam_or_null, N, g->partial, g->scal + S_TMP2, 1.0, g->s, g->ticket);
   } else if (N > 0) {
     launch_interp<double>(g->blobs, g->d, c, 1.0, g->nv[2], g->s);
-    launch_dot(g->nv[2], kappa, N, g->partial, g->scal + S_TMP2, 1.0, g->s);
+    launch_dot(g->nv[2], kappa, N, g->partial, g->scal + S_TMP2, 1.0, g->s, g->ticket);
   }
   IBRD_CUDA(cudaMemcpyAsync(g->host, g->scal + S_TMP, sizeof(double) * 2, cudaMemcpyDeviceToHost, g->s));
   IBRD_CUDA(cudaStreamSynchronize(g->s));
@@ -2276,7 +2274,7 @@ double reaction_setup(ibrd_grid g, const double* kappa, const double* rhs, doubl
     prof_end(P_SETUP, g->s, "check_rates");
     int flag = 0;
     IBRD_CUDA(cudaMemcpyAsync(&flag, g->dflag, sizeof(int), cudaMemcpyDeviceToHost, g->s));
-    launch_sum<double>(kappa, N, g->partial, g->scal + S_TMP, 1.0, g->s);
+    launch_sum<double>(kappa, N, g->partial, g->scal + S_TMP, 1.0, g->s, g->ticket);
     const double ksum = host_scalar(g, S_TMP);
     if (flag) throw ArgError{IBRD_ERR_NONFINITE, "kappa must be finite and >= 0"};
     if (g->alpha == 0.0) sigma = ksum / ((double)g->d.n() * g->h * g->h * g->h);

@@ -634,11 +634,45 @@ __device__ __forceinline__ double block_sum_f(float v) {
   return d;
 }
 
+// Optional tail of a partial-sum kernel: the last CTA of the grid to finish
+// (a ticket taken after a fence; no CTA waits) adds the CTAs' partials in the
+// order of k_finalize into *out0 (times scale0) and, with out1, the second
+// row of partials (partial + gridDim.x) into *out1, then resets the ticket.
+struct FinTail {
+  unsigned* ticket = nullptr;
+  double* out0 = nullptr;
+  double scale0 = 1.0;
+  double* out1 = nullptr;
+  double scale1 = 1.0;
+};
+
+__device__ void fin_tail(const double* partial, const FinTail& t) {
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(t.ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) acc += __ldcg(partial + i);
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) *t.out0 = acc * t.scale0;
+  if (t.out1) {
+    acc = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) acc += __ldcg(partial + gridDim.x + i);
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) *t.out1 = acc * t.scale1;
+  }
+  if (threadIdx.x == 0) *t.ticket = 0u;
+}
+
 // Sum of x: each thread folds 8-element runs (FP32 inputs summed in FP32 within
 // a run, then in FP64) from a grid-stride loop with 4 independent runs in flight.
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads) k_sum_partial(const T* __restrict__ x, size_t n,
-                                                             double* __restrict__ partial) {
+                                                             double* __restrict__ partial, FinTail tail) {
   double acc = 0.0;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
@@ -650,6 +684,7 @@ __global__ void __launch_bounds__(kRedThreads) k_sum_partial(const T* __restrict
   for (; i < n; i += stride) acc += (double)x[i];
   acc = block_sum(acc);
   if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+  if (tail.ticket) fin_tail(partial, tail);
 }
 
 // FP64: one FMA per element, sums in FP64; FP32: products summed per thread
@@ -657,7 +692,8 @@ __global__ void __launch_bounds__(kRedThreads) k_sum_partial(const T* __restrict
 // field), across warps and blocks in FP64.
 template <typename E>
 __global__ void __launch_bounds__(kRedThreads) k_dot_partial(const E* __restrict__ x, const E* __restrict__ y,
-                                                             size_t n, double* __restrict__ partial, int vec) {
+                                                             size_t n, double* __restrict__ partial, int vec,
+                                                             FinTail tail) {
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if constexpr (sizeof(E) == 4) {
@@ -680,6 +716,7 @@ __global__ void __launch_bounds__(kRedThreads) k_dot_partial(const E* __restrict
     acc = block_sum(acc);
     if (threadIdx.x == 0) partial[blockIdx.x] = acc;
   }
+  if (tail.ticket) fin_tail(partial, tail);
 }
 
 __global__ void __launch_bounds__(kRedThreads) k_finalize(const double* __restrict__ partial, int np,
@@ -694,7 +731,7 @@ __global__ void __launch_bounds__(kRedThreads) k_finalize(const double* __restri
 template <typename X, typename T>
 __global__ void __launch_bounds__(kRedThreads) k_convert_sum(const X* __restrict__ x, T* __restrict__ y,
                                                              size_t n, double* __restrict__ pin,
-                                                             double* __restrict__ pout) {
+                                                             double* __restrict__ pout, FinTail tail) {
   // FP64 input is summed with one FP64 add per value; FP32 values (input or
   // converted) are summed in FP32 over runs of 8 and the runs in FP64
   double si = 0.0, so = 0.0;
@@ -721,6 +758,7 @@ __global__ void __launch_bounds__(kRedThreads) k_convert_sum(const X* __restrict
   if (threadIdx.x == 0) pin[blockIdx.x] = si;
   so = block_sum(so);
   if (threadIdx.x == 0) pout[blockIdx.x] = so;
+  if (tail.ticket) fin_tail(pin, tail);  // pout = pin + gridDim.x
 }
 
 template <typename F>
@@ -762,7 +800,7 @@ __global__ void k_convert_f32v(const float* __restrict__ x, float* __restrict__ 
 // 4-vectors summed in FP32 over runs of 2 vectors, the runs in FP64.
 __global__ void __launch_bounds__(kRedThreads) k_copy_sum_f32v(const float* __restrict__ x, float* __restrict__ y,
                                                                size_t n, double* __restrict__ pin,
-                                                               double* __restrict__ pout) {
+                                                               double* __restrict__ pout, FinTail tail) {
   double acc = 0.0;
   const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
   const size_t n4 = n >> 2;
@@ -788,6 +826,7 @@ __global__ void __launch_bounds__(kRedThreads) k_copy_sum_f32v(const float* __re
     pin[blockIdx.x] = acc;
     pout[blockIdx.x] = acc;
   }
+  if (tail.ticket) fin_tail(pin, tail);  // pout = pin + gridDim.x
 }
 
 template <typename Tx, typename Ty>
@@ -868,7 +907,7 @@ __global__ void k_scale_by_inv(const E* __restrict__ x, E* __restrict__ y, size_
 // 256^3 field), across warps and blocks in FP64.
 __global__ void __launch_bounds__(kRedThreads) k_convert_sq(const double* __restrict__ x, float* __restrict__ y,
                                                             size_t n, float sigma, const double* __restrict__ sigma_dev,
-                                                            double* __restrict__ partial) {
+                                                            double* __restrict__ partial, FinTail tail) {
   if (sigma_dev) sigma = (float)*sigma_dev;
   float acc = 0.f;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
@@ -880,6 +919,7 @@ __global__ void __launch_bounds__(kRedThreads) k_convert_sq(const double* __rest
   }
   const double s = block_sum_f(acc);
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
+  if (tail.ticket) fin_tail(partial, tail);
 }
 
 // x += a * (double) d: FP32 correction added to an FP64 field
@@ -1050,10 +1090,13 @@ void launch_hartley_solve(const float* tab, const float* b, const double* bshift
 }
 
 template <typename T>
-void launch_sum(const T* x, size_t n, double* partial, double* out, double scale, cudaStream_t s) {
+void launch_sum(const T* x, size_t n, double* partial, double* out, double scale, cudaStream_t s, unsigned* ticket) {
+  FinTail t;
+  if (ticket) t = FinTail{ticket, out, scale, nullptr, 1.0};
   prof_begin(P_DOT, s);
-  k_sum_partial<T><<<kRedBlocks, kRedThreads, 0, s>>>(x, n, partial);
+  k_sum_partial<T><<<kRedBlocks, kRedThreads, 0, s>>>(x, n, partial, t);
   prof_end(P_DOT, s, "sum_partial", 1.0 * sizeof(T) * n);
+  if (ticket) return;
   prof_begin(P_REDUCE, s);
   k_finalize<<<1, kRedThreads, 0, s>>>(partial, kRedBlocks, out, scale);
   prof_end(P_REDUCE, s, "finalize");
@@ -1067,17 +1110,20 @@ void launch_finalize(const double* partial, int np, double* out, double scale, c
 
 template <typename X, typename T>
 void launch_convert_sum(const X* x, T* y, size_t n, double* partial, double* out_in, double* out_out,
-                        cudaStream_t s) {
+                        cudaStream_t s, unsigned* ticket) {
+  FinTail t;
+  if (ticket) t = FinTail{ticket, out_in, 1.0, out_out, 1.0};
   prof_begin(P_VEC, s);
   if constexpr (sizeof(X) == 4 && sizeof(T) == 4) {
     if (aligned16(x) && aligned16(y))
-      k_copy_sum_f32v<<<kRedBlocks, kRedThreads, 0, s>>>(x, y, n, partial, partial + kRedBlocks);
+      k_copy_sum_f32v<<<kRedBlocks, kRedThreads, 0, s>>>(x, y, n, partial, partial + kRedBlocks, t);
     else
-      k_convert_sum<X, T><<<kRedBlocks, kRedThreads, 0, s>>>(x, y, n, partial, partial + kRedBlocks);
+      k_convert_sum<X, T><<<kRedBlocks, kRedThreads, 0, s>>>(x, y, n, partial, partial + kRedBlocks, t);
   } else {
-    k_convert_sum<X, T><<<kRedBlocks, kRedThreads, 0, s>>>(x, y, n, partial, partial + kRedBlocks);
+    k_convert_sum<X, T><<<kRedBlocks, kRedThreads, 0, s>>>(x, y, n, partial, partial + kRedBlocks, t);
   }
   prof_end(P_VEC, s, "convert_sum", (double)(sizeof(X) + sizeof(T)) * n);
+  if (ticket) return;
   launch_finalize(partial, kRedBlocks, out_in, 1.0, s);
   launch_finalize(partial + kRedBlocks, kRedBlocks, out_out, 1.0, s);
 }
@@ -1092,10 +1138,14 @@ void launch_nvec_affine(const double* in, double* out, int n, double a, const do
 }
 
 template <typename E>
-void launch_dot(const E* x, const E* y, size_t n, double* partial, double* out, double scale, cudaStream_t s) {
+void launch_dot(const E* x, const E* y, size_t n, double* partial, double* out, double scale, cudaStream_t s,
+                unsigned* ticket) {
+  FinTail t;
+  if (ticket) t = FinTail{ticket, out, scale, nullptr, 1.0};
   prof_begin(P_DOT, s);
-  k_dot_partial<E><<<kRedBlocks, kRedThreads, 0, s>>>(x, y, n, partial, aligned16(x) && aligned16(y));
+  k_dot_partial<E><<<kRedBlocks, kRedThreads, 0, s>>>(x, y, n, partial, aligned16(x) && aligned16(y), t);
   prof_end(P_DOT, s, "dot_partial", 2.0 * sizeof(E) * n);
+  if (ticket) return;
   prof_begin(P_REDUCE, s);
   k_finalize<<<1, kRedThreads, 0, s>>>(partial, kRedBlocks, out, scale);
   prof_end(P_REDUCE, s, "finalize");
@@ -1140,18 +1190,24 @@ void launch_scale_by_inv(const E* x, E* y, size_t n, const double* den, double n
 }
 
 void launch_convert_sq(const double* x, float* y, size_t n, double sigma, double* partial, double* out,
-                       cudaStream_t s) {
+                       cudaStream_t s, unsigned* ticket) {
+  FinTail t;
+  if (ticket) t = FinTail{ticket, out, 1.0, nullptr, 1.0};
   prof_begin(P_VEC, s);
-  k_convert_sq<<<kRedBlocks, kRedThreads, 0, s>>>(x, y, n, (float)sigma, nullptr, partial);
+  k_convert_sq<<<kRedBlocks, kRedThreads, 0, s>>>(x, y, n, (float)sigma, nullptr, partial, t);
   prof_end(P_VEC, s, "convert_sq", 12.0 * n);
+  if (ticket) return;
   launch_finalize(partial, kRedBlocks, out, 1.0, s);
 }
 
 void launch_convert_sq(const double* x, float* y, size_t n, const double* sigma_dev, double* partial, double* out,
-                       cudaStream_t s) {
+                       cudaStream_t s, unsigned* ticket) {
+  FinTail t;
+  if (ticket) t = FinTail{ticket, out, 1.0, nullptr, 1.0};
   prof_begin(P_VEC, s);
-  k_convert_sq<<<kRedBlocks, kRedThreads, 0, s>>>(x, y, n, 1.f, sigma_dev, partial);
+  k_convert_sq<<<kRedBlocks, kRedThreads, 0, s>>>(x, y, n, 1.f, sigma_dev, partial, t);
   prof_end(P_VEC, s, "convert_sq", 12.0 * n);
+  if (ticket) return;
   launch_finalize(partial, kRedBlocks, out, 1.0, s);
 }
 
@@ -1179,24 +1235,26 @@ void launch_nonfinite(const T* x, size_t n, int* flag, cudaStream_t s) {
   template void launch_residual<T>(const T*, const T*, T*, Dims, Stencil, double*, cudaStream_t);     \
   template void launch_coarse_solve<T>(const T*, const T*, T*, Dims, cudaStream_t);                   \
   template void launch_coarse_table<T>(T*, Dims, Stencil, int, cudaStream_t);                         \
-  template void launch_sum<T>(const T*, size_t, double*, double*, double, cudaStream_t);              \
+  template void launch_sum<T>(const T*, size_t, double*, double*, double, cudaStream_t, unsigned*);   \
   template void launch_sub_scalar<T>(T*, size_t, const double*, cudaStream_t);                        \
   template void launch_nonfinite<T>(const T*, size_t, int*, cudaStream_t);
 IBRD_INST(double)
 IBRD_INST(float)
 #undef IBRD_INST
 template void launch_convert_sum<double, float>(const double*, float*, size_t, double*, double*, double*,
-                                                cudaStream_t);
+                                                cudaStream_t, unsigned*);
 template void launch_convert_sum<double, double>(const double*, double*, size_t, double*, double*, double*,
-                                                 cudaStream_t);
+                                                 cudaStream_t, unsigned*);
 template void launch_convert_sum<float, float>(const float*, float*, size_t, double*, double*, double*,
-                                               cudaStream_t);
+                                               cudaStream_t, unsigned*);
 template void launch_nvec_affine<double>(const double*, double*, int, double, const double*, const double*, double,
                                          cudaStream_t);
 template void launch_nvec_affine<float>(const double*, double*, int, double, const double*, const float*, double,
                                         cudaStream_t);
-template void launch_dot<double>(const double*, const double*, size_t, double*, double*, double, cudaStream_t);
-template void launch_dot<float>(const float*, const float*, size_t, double*, double*, double, cudaStream_t);
+template void launch_dot<double>(const double*, const double*, size_t, double*, double*, double, cudaStream_t,
+                                 unsigned*);
+template void launch_dot<float>(const float*, const float*, size_t, double*, double*, double, cudaStream_t,
+                                unsigned*);
 template void launch_axpby<double>(double, const double*, double, double*, size_t, cudaStream_t);
 template void launch_axpby<float>(double, const float*, double, float*, size_t, cudaStream_t);
 template void launch_scale_by_inv<double>(const double*, double*, size_t, const double*, double, cudaStream_t);

@@ -247,23 +247,29 @@ void launch_hartley_tables(float* tab, Dims d, Stencil st, int singular, cudaStr
 void launch_hartley_solve(const float* tab, const float* b, const double* bshift, float* x, Dims d, cudaStream_t s);
 
 // ---------------------------------------------------------------- vector kernels
+// Reductions below that take a ticket (a per-handle counter, 0 between uses)
+// form their result in the last CTA of the partial-sum launch, with the
+// arithmetic of launch_finalize, instead of in a separate launch.
+//
 // Sum of x[0..n) into partials (kRedBlocks doubles); then finalize into *out.
 template <typename T>
-void launch_sum(const T* x, size_t n, double* partial, double* out, double scale, cudaStream_t s);
+void launch_sum(const T* x, size_t n, double* partial, double* out, double scale, cudaStream_t s,
+                unsigned* ticket = nullptr);
 // *out = scale * sum(partial[0..np))
 void launch_finalize(const double* partial, int np, double* out, double scale, cudaStream_t s);
 // y = (T)x with sums: *out_in = sum(x), *out_out = sum(y), both in FP64
 // (partial uses 2 * kRedBlocks doubles).
 template <typename X, typename T>
 void launch_convert_sum(const X* x, T* y, size_t n, double* partial, double* out_in, double* out_out,
-                        cudaStream_t s);
+                        cudaStream_t s, unsigned* ticket = nullptr);
 // out[i] = a * (in[i] - *shift) + bcoef * f[i]   (shift, f nullable; N-vectors)
 template <typename F>
 void launch_nvec_affine(const double* in, double* out, int n, double a, const double* shift, const F* f,
                         double bcoef, cudaStream_t s);
 // out[0] = scale * sum(x*y)  (FP32 vectors: FP32 products, FP64 sums of runs)
 template <typename E>
-void launch_dot(const E* x, const E* y, size_t n, double* partial, double* out, double scale, cudaStream_t s);
+void launch_dot(const E* x, const E* y, size_t n, double* partial, double* out, double scale, cudaStream_t s,
+                unsigned* ticket = nullptr);
 // x[i] -= *mean (device scalar)
 template <typename T>
 void launch_sub_scalar(T* x, size_t n, const double* mean, cudaStream_t s);
@@ -278,10 +284,10 @@ template <typename E>
 void launch_scale_by_inv(const E* x, E* y, size_t n, const double* den, double num, cudaStream_t s);
 // y = (float) x * sigma and *out = sum of y^2 (partial: kRedBlocks doubles)
 void launch_convert_sq(const double* x, float* y, size_t n, double sigma, double* partial, double* out,
-                       cudaStream_t s);
+                       cudaStream_t s, unsigned* ticket = nullptr);
 // the same with sigma read from device memory
 void launch_convert_sq(const double* x, float* y, size_t n, const double* sigma_dev, double* partial, double* out,
-                       cudaStream_t s);
+                       cudaStream_t s, unsigned* ticket = nullptr);
 // x += a * d  (FP32 d added to FP64 x)
 void launch_add_scaled(double a, const float* d, double* x, size_t n, cudaStream_t s);
 // x += d / *div_dev  (divisor read from device memory)

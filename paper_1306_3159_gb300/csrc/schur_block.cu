@@ -184,13 +184,34 @@ __global__ void __launch_bounds__(kWarps * 32) k_block_rows(const float4* __rest
   if (lane < k) val[(size_t)i * kBlockMax + lane] = xa;
 }
 
+// Sum over the block (256 threads) in the order of the library's two-stage
+// reductions (warps by shuffles, then warp 0 over the warps' sums); thread 0.
+__device__ __forceinline__ double block_sum256(double v) {
+  __shared__ double sw[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sw[wid] = v;
+  __syncthreads();
+  v = (threadIdx.x < (blockDim.x >> 5)) ? sw[threadIdx.x] : 0.0;
+  if (wid == 0)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __syncthreads();
+  return v;
+}
+
 // y = P (x - shift): one warp per blob (grid-stride), lane = slot; per-CTA
-// sums of y for the mean.
+// sums of y for the mean. With a ticket, the last CTA to finish (ticket taken
+// after a fence; no CTA waits) also adds the per-CTA sums, as the library's
+// finalize kernel does, into *mean = scale * sum(y), and resets the ticket.
 template <typename Tin, typename Tout>
 __global__ void __launch_bounds__(kWarps * 32) k_block_apply(const int* __restrict__ idx, const int* __restrict__ cnt,
                                                              const float* __restrict__ val, const Tin* __restrict__ x,
                                                              const double* __restrict__ shift, int n,
-                                                             Tout* __restrict__ y, double* __restrict__ partial) {
+                                                             Tout* __restrict__ y, double* __restrict__ partial,
+                                                             unsigned* __restrict__ ticket, double* __restrict__ mean,
+                                                             double scale) {
   __shared__ double ws[kWarps];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const double sh = shift ? *shift : 0.0;
@@ -215,6 +236,22 @@ __global__ void __launch_bounds__(kWarps * 32) k_block_apply(const int* __restri
     double s = 0.0;
     for (int v = 0; v < kWarps; ++v) s += ws[v];
     partial[blockIdx.x] = s;
+  }
+  if (!ticket) return;
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) acc += __ldcg(partial + i);
+  acc = block_sum256(acc);
+  if (threadIdx.x == 0) {
+    *mean = acc * scale;
+    *ticket = 0u;
   }
 }
 
@@ -268,16 +305,18 @@ void launch_block_setup(const double* q, int n, double lx, double ly, double lz,
 
 template <typename Tin, typename Tout>
 void launch_block_apply(const int* idx, const int* cnt, const float* val, const Tin* x, const double* shift, int n,
-                        Tout* y, double* partial, cudaStream_t s) {
+                        Tout* y, double* partial, cudaStream_t s, unsigned* ticket, double* mean, double mean_scale) {
+  static_assert(kWarps * 32 == kRedThreads, "the mean's reduction follows the finalize kernel's thread mapping");
   prof_begin(P_SMALL, s);
-  k_block_apply<Tin, Tout><<<kBlockApplyBlocks, kWarps * 32, 0, s>>>(idx, cnt, val, x, shift, n, y, partial);
+  k_block_apply<Tin, Tout><<<kBlockApplyBlocks, kWarps * 32, 0, s>>>(idx, cnt, val, x, shift, n, y, partial,
+                                                                     mean ? ticket : nullptr, mean, mean_scale);
   // slots (index and value) read once, x gathered, y written
   prof_end(P_SMALL, s, "block_apply", (8.0 * kBlockMax + 2.0 * sizeof(Tin) + sizeof(Tout)) * n);
 }
 
 template void launch_block_apply<double, double>(const int*, const int*, const float*, const double*, const double*,
-                                                 int, double*, double*, cudaStream_t);
+                                                 int, double*, double*, cudaStream_t, unsigned*, double*, double);
 template void launch_block_apply<float, float>(const int*, const int*, const float*, const float*, const double*,
-                                               int, float*, double*, cudaStream_t);
+                                               int, float*, double*, cudaStream_t, unsigned*, double*, double);
 
 }  // namespace ibrd

@@ -24,10 +24,13 @@ void launch_block_setup(const double* q, int n, double lx, double ly, double lz,
                         float4* pos, int* idx, int* cnt, float* val, cudaStream_t s);
 
 // y = P (x - *shift) (shift nullable; y must not overlap x), and per-CTA sums
-// of y in partial[0 .. kBlockApplyBlocks) (their total is sum(y)).
+// of y in partial[0 .. kBlockApplyBlocks) (their total is sum(y)); with mean
+// non-null also *mean = mean_scale * sum(y), formed by the launch's last CTA
+// (ticket: a per-handle counter, 0 between uses).
 constexpr int kBlockApplyBlocks = 608;
 template <typename Tin, typename Tout>
 void launch_block_apply(const int* idx, const int* cnt, const float* val, const Tin* x, const double* shift, int n,
-                        Tout* y, double* partial, cudaStream_t s);
+                        Tout* y, double* partial, cudaStream_t s, unsigned* ticket = nullptr,
+                        double* mean = nullptr, double mean_scale = 0.0);
 
 }  // namespace ibrd
