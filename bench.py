@@ -217,7 +217,9 @@ def run_ours(args):
     torch.cuda.set_stream(stream)
     # the step's two solves are independent: each has its own handle and
     # stream, and ibrd_solve_many runs them together
-    stream_r, stream_s = torch.cuda.Stream(), torch.cuda.Stream()
+    # the saddle solve is the longer of the two: its stream has the higher
+    # priority, so the reaction solve's kernels fill the gaps around it
+    stream_r, stream_s = torch.cuda.Stream(), torch.cuda.Stream(priority=-1)
     grid_r = p.Grid(nx, ny, nz, h=w.h, chi=w.chi, alpha=0.0, precision=p.IBRD_MIXED_FP32,
                     stream=stream_r.cuda_stream)
     grid_s = p.Grid(nx, ny, nz, h=w.h, chi=w.chi, alpha=0.0, precision=p.IBRD_MIXED_FP32,
